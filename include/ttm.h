@@ -1,0 +1,238 @@
+/*
+ * ttm.h -- C ABI of the GB300 (sm_103a) tensorial template matching engine.
+ *
+ * Tensorial template matching (TTM) is the method of Almira, Phelippeau and
+ * Martinez-Sanchez, "Fast Normalized Cross-Correlation for Template Matching
+ * with Rotations" (arXiv 2311.07561).  A template t is rotated through SO(3)
+ * once, and every rotated, masked, normalised copy is folded into one
+ * symmetric tensor template with K = C(n+3, n) independent components
+ * (Sec. 3.2).  A volume f is then correlated with those K components instead
+ * of with thousands of rotated copies; each voxel's K normalised correlations
+ * C_n(x) give a position score (the Frobenius norm, Sec. 3.4) and a rotation
+ * (the dominant Z-eigenvector of C_n(x), Sec. 3.3, Theorem 3.1).
+ *
+ * Conventions used by every entry point
+ * -------------------------------------
+ * - Volumes are float32, laid out [Z][Y][X] contiguous (x fastest).  Their
+ *   sizes are given as (X, Y, Z).
+ * - A template box is a cube of edge s, laid out [s][s][s] the same way; its
+ *   centre is voxel c = floor(s/2) on every axis.  The mask m is a float32
+ *   array of the same shape.
+ * - Quaternions are four float32 (a, b, c, d), real part first.  The rotation
+ *   R of a unit quaternion q maps a column vector v = (x, y, z) to q v q*.  The
+ *   rotated template is t_R(u) = t(c + R^-1 (u - c)) (Sec. 2: t_R = O_{R^-1} t),
+ *   resampled trilinearly with zero outside the box.
+ * - Tensor components are indexed by sorted index tuples i1 <= ... <= in over
+ *   {0, 1, 2, 3} (the quaternion components a, b, c, d), in lexicographic
+ *   order: for n = 4, component 0 is (0,0,0,0), component 1 is (0,0,0,1), ...,
+ *   component 34 is (3,3,3,3).
+ * - Correlation values are defined on the interior of a volume: voxels whose
+ *   whole s^3 template box lies inside it.  Every output map is written in
+ *   full; voxels outside the interior get score 0, lambda 0, quaternion
+ *   (1, 0, 0, 0) and w = 0.
+ * - Pointers named d_* are device pointers (cudaMalloc or any allocator on
+ *   the current device); h_* are host pointers.  The caller owns every buffer
+ *   it passes in, including the workspaces; the library never frees them.
+ * - stream is a cudaStream_t passed as void* (NULL = the legacy default
+ *   stream).  Calls are asynchronous on that stream unless stated otherwise.
+ *   Argument errors are detected on the host and returned before any work is
+ *   queued.
+ * - Every call returns a ttm_status; TTM_OK is 0, errors are negative.
+ *
+ * The library is compiled for sm_103a only.  There is no CPU fallback: on a
+ * machine without a suitable GPU every compute entry point returns
+ * TTM_ERR_CUDA.
+ */
+#ifndef TTM_H_
+#define TTM_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int ttm_status;
+
+#define TTM_OK                 0
+#define TTM_ERR_INVALID_ARG   -1  /* null pointer, bad size, misaligned buffer */
+#define TTM_ERR_UNSUPPORTED   -2  /* odd order n, n > 8, non-binary mask, ...   */
+#define TTM_ERR_OUT_OF_MEMORY -3  /* a plan-owned allocation failed            */
+#define TTM_ERR_CUDA          -4  /* a CUDA runtime call or launch failed       */
+#define TTM_ERR_TIMEOUT       -5  /* a bounded device-side wait ran out         */
+#define TTM_ERR_NUMERIC       -6  /* non-finite values where finite are needed  */
+#define TTM_ERR_WORKSPACE     -7  /* workspace missing or smaller than required */
+
+/* Description of a built tensor template (filled by ttm_build_tensor_template). */
+typedef struct ttm_tt_desc {
+    int n_order;      /* tensor order n (even, 2..8)                          */
+    int K;            /* number of independent components, C(n+3, n)          */
+    int s;            /* edge of the cubic template box                       */
+    int centre;       /* floor(s/2)                                           */
+    int n_rot;        /* number of quadrature rotations folded in             */
+    int reserved;
+    double mask_sum;  /* <1, m>, the squared S-norm of the constant image     */
+} ttm_tt_desc;
+
+/* One detected peak (ttm_extract_peaks). */
+typedef struct ttm_peak {
+    int x, y, z;      /* voxel                                                */
+    float score;      /* ||C_n(x)||_F                                         */
+    float lambda;     /* dominant Z-eigenvalue, phi(q)                        */
+    float q[4];       /* dominant Z-eigenvector, canonical (a >= 0)           */
+} ttm_peak;
+
+/* Correlation path. */
+#define TTM_PATH_AUTO   0   /* planner picks FFT or direct per problem         */
+#define TTM_PATH_DIRECT 1   /* direct sum over the mask support                */
+#define TTM_PATH_FFT    2   /* FFT with the fused K-way spectrum multiply      */
+
+/* Precision of the correlation step. */
+#define TTM_PREC_FP32   0   /* FP32 throughout                                 */
+#define TTM_PREC_MIXED  1   /* FP16/BF16 storage or products, FP32 accumulate  */
+
+typedef struct ttm_plan_opts {
+    int path;           /* TTM_PATH_*                                          */
+    int precision;      /* TTM_PREC_*                                          */
+    int n_grid;         /* rotation search grid size; 0 = default (2048)       */
+    int n_cells;        /* regions of the grid; 0 = default (128)              */
+    int n_candidates;   /* regions polished per voxel; 0 = default (8)         */
+    int newton_steps;   /* Newton steps per candidate; 0 = default (6)         */
+    int reserved[4];
+} ttm_plan_opts;
+
+typedef struct ttm_plan_s* ttm_plan_t;
+
+/* Human-readable name of a status code (static storage). */
+const char* ttm_status_string(ttm_status status);
+
+/* Number of CUDA devices the library's runtime sees (0 when none). */
+int ttm_device_count(void);
+
+/* ------------------------------------------------------------------------
+ * Tensor template (Sec. 3.2; normalisation as in Algorithm 1 and the
+ * formulas for ||P_S t||_S and <t, 1>_S at the end of Sec. 2).
+ *
+ * For every quadrature node j the template is rotated (t_j = t_{R_j}),
+ * masked and S-normalised,
+ *     t~_j = m (t_j - <t_j, m>/<1, m>) / sqrt(<t_j^2, m> - <t_j, m>^2/<1, m>),
+ * and folded into the components
+ *     T_alpha(z) = sum_j w_j q_j^alpha t~_j(z),   q^alpha = q_i1 ... q_in,
+ * a quadrature of T(z) = int R^(n) S(t)_R(z) dR for the normalised Haar
+ * measure.  The low-pass filter h of Sec. 2 is the identity.
+ *
+ * ttm_build_workspace_size: bytes of device workspace ttm_build_tensor_template
+ *   needs for (s, n_order, n_rot).
+ * ttm_build_tensor_template:
+ *   d_template   s^3 float32, the raw template.
+ *   d_mask       s^3 float32, the mask m (any non-negative values).
+ *   s            box edge, 3 <= s <= 128.
+ *   n_order      even, 2 <= n_order <= 8.
+ *   d_quats      n_rot x 4 float32 unit quaternions (normalised on use).
+ *   d_weights    n_rot float32 weights, or NULL for 1/n_rot each.
+ *   d_components output, K x s^3 float32, component order as above.
+ *   d_workspace  >= ttm_build_workspace_size bytes, 256-byte aligned.
+ *   desc         output (host), filled on success.
+ * Synchronises the stream (the descriptor needs <1, m> on the host).
+ * Errors: TTM_ERR_INVALID_ARG (null pointer, s or n_rot out of range),
+ * TTM_ERR_UNSUPPORTED (n_order odd or out of range), TTM_ERR_WORKSPACE,
+ * TTM_ERR_NUMERIC (a rotated copy has zero variance under the mask),
+ * TTM_ERR_CUDA.
+ * ---------------------------------------------------------------------- */
+ttm_status ttm_build_workspace_size(int s, int n_order, int n_rot, size_t* bytes);
+ttm_status ttm_build_tensor_template(const float* d_template, const float* d_mask, int s,
+                                     int n_order, const float* d_quats, const float* d_weights,
+                                     int n_rot, float* d_components, void* d_workspace,
+                                     size_t workspace_bytes, ttm_tt_desc* desc, void* stream);
+
+/* ------------------------------------------------------------------------
+ * Plan.  A plan fixes a batch of problems; problem p matches volume p (size
+ * vol_dims[3p..3p+2] = X, Y, Z) against template tmpl_index[p].  Template k
+ * is described by descs[k], its components by d_components[k] (K x s^3,
+ * caller-owned, read during ttm_plan only when the FFT path is chosen and
+ * kept referenced by the direct path: they must stay valid until
+ * ttm_plan_destroy) and its mask by d_masks[k] (s^3, read during ttm_plan).
+ * The mask must be binary (0 or 1); soft masks return TTM_ERR_UNSUPPORTED.
+ * opts may be NULL (defaults).  The plan allocates and owns only its tables
+ * and precomputed template spectra.  Synchronises the stream.
+ * ---------------------------------------------------------------------- */
+ttm_status ttm_plan(ttm_plan_t* out, int n_problems, const int* vol_dims, const int* tmpl_index,
+                    int n_templates, const ttm_tt_desc* descs, const float* const* d_components,
+                    const float* const* d_masks, const ttm_plan_opts* opts, void* stream);
+
+/* Bytes of device workspace ttm_local_stats, ttm_correlate and
+ * ttm_extract_peaks need (one workspace serves all three). */
+ttm_status ttm_plan_workspace_size(ttm_plan_t plan, size_t* bytes);
+
+/* Path the plan chose for problem p (TTM_PATH_DIRECT or TTM_PATH_FFT). */
+ttm_status ttm_plan_problem_path(ttm_plan_t plan, int problem, int* path);
+
+/* Kernel launches the plan has queued so far (for accounting). */
+ttm_status ttm_plan_launch_count(ttm_plan_t plan, long long* launches);
+
+/* Frees everything the plan owns.  NULL is ignored. */
+void ttm_plan_destroy(ttm_plan_t plan);
+
+/* ------------------------------------------------------------------------
+ * Local statistics: the NCC denominators (Sec. 2,
+ *   ||P_S tau_x f||_S^2 = <(tau_x f)^2, m> - <tau_x f, m>^2 / <1, m>,
+ * and Algorithm 1, image block).  For every problem p writes
+ *   w(x) = 1 / sqrt(S2(x) - S1(x)^2 / <1, m>),
+ *   S1(x) = sum_u m(u) f(x + u - c),  S2(x) = sum_u m(u) f(x + u - c)^2,
+ * into d_w[p] (X*Y*Z float32).  w = 0 outside the interior and where the
+ * local variance S2 - S1^2/<1,m> is at most 1e-6 * <1,m> * var(f), var(f)
+ * being the variance of the whole volume.  S1 and S2 are accumulated in FP32
+ * after subtracting a per-tile reference value; the variance is formed in
+ * FP64.  d_vols[p] is read, never written.
+ * Errors: TTM_ERR_INVALID_ARG, TTM_ERR_WORKSPACE, TTM_ERR_CUDA.
+ * ---------------------------------------------------------------------- */
+ttm_status ttm_local_stats(ttm_plan_t plan, const float* const* d_vols, float* const* d_w,
+                           void* d_workspace, size_t workspace_bytes, void* stream);
+
+/* ------------------------------------------------------------------------
+ * Correlation with the K components, TTM score and rotation (Sec. 3.2-3.4).
+ * For every problem p and interior voxel x:
+ *   C_alpha(x) = w(x) sum_u f(x + u - c) T_alpha(u)          (Sec. 3.2)
+ *   score(x)   = ||C_n(x)||_F = sqrt(sum_alpha mu_alpha C_alpha^2),
+ *                mu_alpha = n! / prod(multiplicities)         (Sec. 3.4)
+ *   lambda(x)  = max_{|Q|=1} phi(Q), phi(Q) = sum_alpha mu_alpha C_alpha Q^alpha
+ *   q(x)       = its maximiser, the dominant Z-eigenvector     (Sec. 3.3)
+ * The maximum is searched on a fixed grid of n_grid unit quaternions split
+ * into n_cells regions; the best grid point of each of the n_candidates best
+ * regions is refined by shifted power iterations (shift (n-1) score,
+ * Kolda & Mayo 2011) and Riemannian Newton steps, and the largest refined
+ * value is kept.  q is canonical: a >= 0.
+ *   d_w          from ttm_local_stats.
+ *   d_score      X*Y*Z float32 per problem (required).
+ *   d_quat       X*Y*Z*4 float32 per problem, (a,b,c,d) per voxel (required).
+ *   d_lambda     X*Y*Z float32 per problem, or NULL.
+ *   d_components_out  NULL, or per problem K*X*Y*Z float32 receiving C_alpha
+ *                (component-major) for inspection.
+ * Errors: TTM_ERR_INVALID_ARG, TTM_ERR_WORKSPACE, TTM_ERR_CUDA.
+ * ---------------------------------------------------------------------- */
+ttm_status ttm_correlate(ttm_plan_t plan, const float* const* d_vols, const float* const* d_w,
+                         float* const* d_score, float* const* d_quat, float* const* d_lambda,
+                         float* const* d_components_out, void* d_workspace,
+                         size_t workspace_bytes, void* stream);
+
+/* ------------------------------------------------------------------------
+ * Peaks of the position score (Sec. 3.4).  A voxel is a peak when its score
+ * exceeds threshold and beats every other voxel of the (2*radius+1)^3 cube
+ * around it (equal scores: the lower linear index wins).  Up to max_peaks
+ * peaks, highest score first (equal scores: lower index first), are written
+ * to h_out with their lambda and quaternion; *n_out receives the count.
+ * d_lambda may be NULL (lambda reported as 0).  Synchronises the stream.
+ * Errors: TTM_ERR_INVALID_ARG (radius < 0 or > 32, max_peaks < 0),
+ * TTM_ERR_WORKSPACE, TTM_ERR_CUDA.
+ * ---------------------------------------------------------------------- */
+ttm_status ttm_extract_peaks(ttm_plan_t plan, int problem, const float* d_score,
+                             const float* d_quat, const float* d_lambda, float threshold,
+                             int radius, int max_peaks, ttm_peak* h_out, int* n_out,
+                             void* d_workspace, size_t workspace_bytes, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TTM_H_ */

@@ -1,0 +1,329 @@
+// Per-voxel TTM score and rotation (kernel template; instantiated per order n
+// in k_rotation_n*.cu) (Sec. 3.2-3.4 of the paper).
+//
+//   C_alpha(x) = w(x) Corr_alpha(x)
+//   score(x)   = ||C_n(x)||_F = sqrt(sum_alpha mu_alpha C_alpha^2)          (Sec. 3.4)
+//   lambda(x)  = max_{|Q|=1} phi(Q),  phi(Q) = C_n(x) . Q^(n)                (Sec. 3.3)
+//   q(x)       = argmax, the dominant Z-eigenvector of C_n(x)                (Sec. 3.1)
+//
+// One thread per voxel.  The maximum is searched on a fixed grid of unit
+// quaternions (half sphere, sorted into regions): phi at every grid point is a
+// dot product with a precomputed row mu_alpha q_g^alpha staged in shared memory
+// and read as a broadcast.  The best point of each region competes for a short
+// list of n_cand candidates.  Each candidate is refined by two shifted power
+// steps (x <- normalise(C x^{n-1} + sigma x), sigma = (n-1) score, the SS-HOPM
+// step of Kolda & Mayo 2011, monotone for this shift) and then by Riemannian
+// Newton steps on the sphere, each accepted only if phi does not decrease
+// (otherwise the power step is taken).  The largest refined value wins.
+#pragma once
+#include "ttm_internal.h"
+
+namespace ttm {
+
+namespace rot {
+
+constexpr int kRotThreads = 128;
+constexpr int kChunk = 128;       // grid points staged per step
+constexpr int kMaxCand = 8;
+
+struct RotArgs {
+    const float* corr;      // K x nvox
+    const float* w;
+    size_t nvox;
+    float* score;
+    float* quat;            // 4 x nvox interleaved (a, b, c, d) per voxel
+    float* lambda;          // nullable
+    float* comp_out;        // nullable, K x nvox
+    const float* gq;        // n_grid x 4
+    const float* gm;        // n_grid x K4
+    const int* cell_end;    // n_grid
+    int n_grid, n_cand, newton;
+};
+
+template <int N>
+struct Geo {
+    static constexpr int K = n_comp(N);
+    static constexpr int K4 = (K + 3) & ~3;
+};
+
+// H = C x^{N-2} (symmetric 4x4, 10 entries in the order of HessTab pairs)
+template <int N>
+__device__ __forceinline__ void hess(const float (&C)[Geo<N>::K4], const float x[4], float h[10]) {
+    constexpr HessTab<N> T{};
+    Monomials<N - 2> mb;
+    monomials<N - 2>(x, mb);
+    float mw[HessTab<N>::KB];
+#pragma unroll
+    for (int b = 0; b < HessTab<N>::KB; ++b) mw[b] = (float)T.mult[b] * mb.v[b];
+#pragma unroll
+    for (int p = 0; p < 10; ++p) {
+        float acc = 0.f;
+#pragma unroll
+        for (int b = 0; b < HessTab<N>::KB; ++b) acc = fmaf(mw[b], C[T.comp[p][b]], acc);
+        h[p] = acc;
+    }
+}
+
+// full 4x4 from the 10 stored entries (pairs i <= j in row order)
+static __device__ __forceinline__ void unpack(const float h[10], float H[4][4]) {
+    int p = 0;
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = i; j < 4; ++j) {
+            H[i][j] = h[p];
+            H[j][i] = h[p];
+            ++p;
+        }
+}
+
+static __device__ __forceinline__ void normalise4(float x[4]) {
+    float n2 = x[0] * x[0] + x[1] * x[1] + x[2] * x[2] + x[3] * x[3];
+    float inv = rsqrtf(n2);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) x[i] *= inv;
+}
+
+// value and gradient pieces at x: H = C x^{N-2}, g = H x = C x^{N-1}, lam = x.g
+template <int N>
+__device__ __forceinline__ void eval_at(const float (&C)[Geo<N>::K4], const float x[4],
+                                        float H[4][4], float g[4], float& lam) {
+    float h[10];
+    hess<N>(C, x, h);
+    unpack(h, H);
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+        g[i] = H[i][0] * x[0] + H[i][1] * x[1] + H[i][2] * x[2] + H[i][3] * x[3];
+    lam = g[0] * x[0] + g[1] * x[1] + g[2] * x[2] + g[3] * x[3];
+}
+
+// Riemannian Newton direction on the unit sphere for maximising phi:
+//   P ((N-1) H - lam I) P eta = -(g - lam x),  eta orthogonal to x,
+// solved as A eta = (g - lam x) with A = -P B P + sig x x^T, which is SPD
+// exactly when the tangent Hessian is negative definite.  Returns false if
+// the Cholesky factorisation breaks down (not near a maximum).
+template <int N>
+__device__ __forceinline__ bool newton_dir(const float H[4][4], const float g[4], const float x[4],
+                                           float lam, float sig, float eta[4]) {
+    float B[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) B[i][j] = (float)(N - 1) * H[i][j] - (i == j ? lam : 0.f);
+    float Bx[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) Bx[i] = B[i][0] * x[0] + B[i][1] * x[1] + B[i][2] * x[2] + B[i][3] * x[3];
+    const float xBx = x[0] * Bx[0] + x[1] * Bx[1] + x[2] * Bx[2] + x[3] * Bx[3];
+    float A[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+            A[i][j] = -(B[i][j] - x[i] * Bx[j] - Bx[i] * x[j] + xBx * x[i] * x[j]) + sig * x[i] * x[j];
+    float r[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) r[i] = g[i] - lam * x[i];
+    // Cholesky A = L L^T
+    const float tiny = 1e-9f * sig;
+    float L[4][4] = {};
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        float d = A[j][j];
+#pragma unroll
+        for (int k = 0; k < j; ++k) d -= L[j][k] * L[j][k];
+        if (!(d > tiny)) return false;
+        const float ljj = sqrtf(d);
+        L[j][j] = ljj;
+        const float inv = 1.f / ljj;
+#pragma unroll
+        for (int i = j + 1; i < 4; ++i) {
+            float v = A[i][j];
+#pragma unroll
+            for (int k = 0; k < j; ++k) v -= L[i][k] * L[j][k];
+            L[i][j] = v * inv;
+        }
+    }
+    float y[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        float v = r[i];
+#pragma unroll
+        for (int k = 0; k < i; ++k) v -= L[i][k] * y[k];
+        y[i] = v / L[i][i];
+    }
+#pragma unroll
+    for (int i = 3; i >= 0; --i) {
+        float v = y[i];
+#pragma unroll
+        for (int k = i + 1; k < 4; ++k) v -= L[k][i] * eta[k];
+        eta[i] = v / L[i][i];
+    }
+    return true;
+}
+
+template <int N>
+__device__ void refine(const float (&C)[Geo<N>::K4], float sigma, int newton, float x[4],
+                       float& lam_out) {
+    float H[4][4], g[4], lam;
+    // two shifted power (SS-HOPM) steps
+#pragma unroll 1
+    for (int it = 0; it < 2; ++it) {
+        eval_at<N>(C, x, H, g, lam);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) x[i] = g[i] + sigma * x[i];
+        normalise4(x);
+    }
+    eval_at<N>(C, x, H, g, lam);
+    const float eps = 1e-6f * sigma;
+#pragma unroll 1
+    for (int it = 0; it < newton; ++it) {
+        float eta[4];
+        float xn[4];
+        bool ok = newton_dir<N>(H, g, x, lam, sigma, eta);
+        if (ok) {
+            float en = sqrtf(eta[0] * eta[0] + eta[1] * eta[1] + eta[2] * eta[2] + eta[3] * eta[3]);
+            const float clip = en > 0.25f ? 0.25f / en : 1.f;
+#pragma unroll
+            for (int i = 0; i < 4; ++i) xn[i] = x[i] + clip * eta[i];
+            normalise4(xn);
+        }
+        float Hn[4][4], gn[4], ln;
+        if (ok) {
+            eval_at<N>(C, xn, Hn, gn, ln);
+            ok = ln >= lam - eps;
+        }
+        if (!ok) {
+#pragma unroll
+            for (int i = 0; i < 4; ++i) xn[i] = g[i] + sigma * x[i];
+            normalise4(xn);
+            eval_at<N>(C, xn, Hn, gn, ln);
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            x[i] = xn[i];
+            g[i] = gn[i];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) H[i][j] = Hn[i][j];
+        }
+        lam = ln;
+    }
+    lam_out = lam;
+}
+
+template <int N>
+__global__ void __launch_bounds__(kRotThreads) rotation_kernel(RotArgs a) {
+    constexpr int K = Geo<N>::K;
+    constexpr int K4 = Geo<N>::K4;
+    constexpr Sym<N> S{};
+    extern __shared__ __align__(16) float sm[];
+    float* Mt = sm;                                   // kChunk x K4
+    int* ends = reinterpret_cast<int*>(sm + kChunk * K4);
+
+    const size_t v = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool in_range = v < a.nvox;
+    const float wv = in_range ? __ldg(a.w + v) : 0.f;
+    float C[K4];
+#pragma unroll
+    for (int k = 0; k < K4; ++k) C[k] = 0.f;
+    float ss = 0.f;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        float c = in_range ? wv * __ldg(a.corr + (size_t)k * a.nvox + v) : 0.f;
+        C[k] = c;
+        ss = fmaf((float)S.mu[k], c * c, ss);
+        if (a.comp_out && in_range) a.comp_out[(size_t)k * a.nvox + v] = c;
+    }
+    const float score = sqrtf(ss);
+    const bool active = in_range && score > 0.f;
+
+    float tv[kMaxCand];
+    int ti[kMaxCand];
+#pragma unroll
+    for (int k = 0; k < kMaxCand; ++k) { tv[k] = -INFINITY; ti[k] = -1; }
+    float cur = -INFINITY;
+    int curi = 0;
+    const bool any_active = __syncthreads_or(active);
+    for (int g0 = 0; g0 < a.n_grid && any_active; g0 += kChunk) {
+        const int gn = min(kChunk, a.n_grid - g0);
+        __syncthreads();
+        const float4* src = reinterpret_cast<const float4*>(a.gm + (size_t)g0 * K4);
+        float4* dst = reinterpret_cast<float4*>(Mt);
+        for (int e = threadIdx.x; e < gn * (K4 / 4); e += blockDim.x) dst[e] = __ldg(src + e);
+        for (int e = threadIdx.x; e < gn; e += blockDim.x) ends[e] = __ldg(a.cell_end + g0 + e);
+        __syncthreads();
+        for (int gg = 0; gg < gn; ++gg) {
+            const float4* row = reinterpret_cast<const float4*>(Mt + gg * K4);
+            float phi = 0.f;
+#pragma unroll
+            for (int c4 = 0; c4 < K4 / 4; ++c4) {
+                const float4 m = row[c4];
+                phi = fmaf(m.x, C[4 * c4 + 0], phi);
+                phi = fmaf(m.y, C[4 * c4 + 1], phi);
+                phi = fmaf(m.z, C[4 * c4 + 2], phi);
+                phi = fmaf(m.w, C[4 * c4 + 3], phi);
+            }
+            if (phi > cur) { cur = phi; curi = g0 + gg; }
+            if (ends[gg]) {
+                float val = cur;
+                int idx = curi;
+#pragma unroll
+                for (int k = 0; k < kMaxCand; ++k) {
+                    if (val > tv[k]) {
+                        float t = tv[k]; tv[k] = val; val = t;
+                        int u = ti[k]; ti[k] = idx; idx = u;
+                    }
+                }
+                cur = -INFINITY;
+            }
+        }
+    }
+    if (!in_range) return;
+
+    float best_l = 0.f;
+    float best_q[4] = {1.f, 0.f, 0.f, 0.f};
+    if (active) {
+        const float sigma = (float)(N - 1) * score;
+        best_l = -INFINITY;
+        for (int k = 0; k < a.n_cand && k < kMaxCand; ++k) {
+            if (ti[k] < 0) break;
+            float x[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) x[i] = __ldg(a.gq + 4 * ti[k] + i);
+            float l;
+            refine<N>(C, sigma, a.newton, x, l);
+            if (l > best_l) {
+                best_l = l;
+#pragma unroll
+                for (int i = 0; i < 4; ++i) best_q[i] = x[i];
+            }
+        }
+        // canonical representative of {q, -q}: first non-zero component positive
+        float sgn = 1.f;
+        if (best_q[0] != 0.f) sgn = best_q[0] < 0.f ? -1.f : 1.f;
+        else if (best_q[1] != 0.f) sgn = best_q[1] < 0.f ? -1.f : 1.f;
+        else if (best_q[2] != 0.f) sgn = best_q[2] < 0.f ? -1.f : 1.f;
+        else sgn = best_q[3] < 0.f ? -1.f : 1.f;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) best_q[i] *= sgn;
+    }
+    a.score[v] = score;
+    reinterpret_cast<float4*>(a.quat)[v] = make_float4(best_q[0], best_q[1], best_q[2], best_q[3]);
+    if (a.lambda) a.lambda[v] = best_l;
+}
+
+template <int N>
+ttm_status launch_n(const RotArgs& a, cudaStream_t st, long long* cnt) {
+    const size_t smem = (size_t)kChunk * Geo<N>::K4 * sizeof(float) + kChunk * sizeof(int);
+    TTM_CUDA_TRY(cudaFuncSetAttribute(rotation_kernel<N>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    const unsigned blocks = (unsigned)((a.nvox + kRotThreads - 1) / kRotThreads);
+    rotation_kernel<N><<<blocks, kRotThreads, smem, st>>>(a);
+    return after_launch(cnt);
+}
+
+}  // namespace rot
+
+template <int N>
+ttm_status launch_rotation_n(const rot::RotArgs& a, cudaStream_t st, long long* cnt);
+
+}  // namespace ttm

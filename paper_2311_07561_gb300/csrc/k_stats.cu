@@ -1,0 +1,191 @@
+// Local statistics: the NCC denominators (Sec. 2 of the paper,
+//   ||P_S tau_x f||_S^2 = <(tau_x f)^2, m> - <tau_x f, m>^2 / <1, m>,
+// Algorithm 1, image block), for a binary mask given as x-runs.
+//
+// A CTA owns a 64 x 8 tile of output voxels in one z-plane.  For every mask
+// plane dz it stages the rows the tile's windows touch, subtracts a reference
+// value (the input voxel at the tile centre; the variance does not change under
+// a constant shift and the shift removes the cancellation of large offsets),
+// and builds exclusive prefix sums of (f - mu) and (f - mu)^2 along x in
+// shared memory.  Each x-run of the mask then costs two prefix lookups per
+// statistic.  S1 and S2 accumulate in FP32; V = S2 - S1^2/m_sum is formed in
+// FP64.  The degenerate-variance floor is 1e-6 * m_sum * var(f) with var(f)
+// from launch_volume_moments.
+#include "ttm_internal.h"
+
+namespace ttm {
+
+namespace {
+
+constexpr int kTX = 64;
+constexpr int kTY = 8;
+constexpr int kStatThreads = 256;   // each thread: x = tid % 64, y = tid / 64 and +4
+
+__global__ void __launch_bounds__(256) moments_kernel(const float* __restrict__ f, size_t n,
+                                                      double* acc) {
+    __shared__ double r1[8], r2[8];
+    float s1 = 0.f, s2 = 0.f;
+    double d1 = 0.0, d2 = 0.0;
+    int cntr = 0;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
+         i += (size_t)gridDim.x * blockDim.x) {
+        float v = f[i];
+        s1 += v;
+        s2 += v * v;
+        if (++cntr == 64) {          // flush the FP32 partials to FP64 regularly
+            d1 += s1; d2 += s2; s1 = 0.f; s2 = 0.f; cntr = 0;
+        }
+    }
+    d1 += s1;
+    d2 += s2;
+    for (int o = 16; o > 0; o >>= 1) {
+        d1 += __shfl_down_sync(0xffffffffu, d1, o);
+        d2 += __shfl_down_sync(0xffffffffu, d2, o);
+    }
+    int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) { r1[wid] = d1; r2[wid] = d2; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double a = 0.0, b = 0.0;
+        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) { a += r1[k]; b += r2[k]; }
+        atomicAdd(acc, a);
+        atomicAdd(acc + 1, b);
+    }
+}
+
+struct StatsArgs {
+    const float* f;
+    float* w;
+    int X, Y, Z, s;
+    const MaskRun* runs;
+    const int* dz_run0;      // runs of plane dz start at dz_run0[dz - dz_min]
+    int dz_min, dz_max, dy_min, dy_max, x_min, x_max;
+    double mask_sum;
+    const double* moments;   // sum f, sum f^2 over the volume
+};
+
+__global__ void __launch_bounds__(kStatThreads) local_stats_kernel(StatsArgs a) {
+    extern __shared__ float smem[];
+    const int rows = kTY + (a.dy_max - a.dy_min);
+    const int width = kTX + (a.x_max - a.x_min);     // staged values per row
+    const int pitch = width + 1;                     // exclusive prefix length
+    float* P1 = smem;
+    float* P2 = smem + rows * pitch;
+
+    const int x0 = blockIdx.x * kTX;
+    const int y0 = blockIdx.y * kTY;
+    const int z = blockIdx.z;
+    const int lx = threadIdx.x % kTX;
+    const int ly = threadIdx.x / kTX;                // 0..3, second voxel at ly + 4
+
+    // reference value: the input voxel nearest the tile centre (clamped)
+    const int cx = min(x0 + kTX / 2, a.X - 1), cy = min(y0 + kTY / 2, a.Y - 1);
+    const float mu = __ldg(a.f + ((size_t)z * a.Y + cy) * a.X + cx);
+
+    float s1[2] = {0.f, 0.f}, s2[2] = {0.f, 0.f};
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int nwarps = kStatThreads / 32;
+
+    for (int dz = a.dz_min; dz <= a.dz_max; ++dz) {
+        const int zz = z + dz;
+        __syncthreads();
+        // stage rows and build exclusive prefix sums, one warp per row
+        for (int r = warp; r < rows; r += nwarps) {
+            const int yy = y0 + a.dy_min + r;
+            const bool row_ok = zz >= 0 && zz < a.Z && yy >= 0 && yy < a.Y;
+            const float* src = a.f + ((size_t)(row_ok ? zz : 0) * a.Y + (row_ok ? yy : 0)) * a.X;
+            float run1 = 0.f, run2 = 0.f;
+            for (int base = 0; base < width; base += 32) {
+                const int i = base + lane;
+                const int xx = x0 + a.x_min + i;
+                float v = 0.f;
+                if (i < width && row_ok && xx >= 0 && xx < a.X) v = __ldg(src + xx) - mu;
+                float v2 = v * v;
+                // inclusive warp scan
+                float c1 = v, c2 = v2;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    float t1 = __shfl_up_sync(0xffffffffu, c1, o);
+                    float t2 = __shfl_up_sync(0xffffffffu, c2, o);
+                    if (lane >= o) { c1 += t1; c2 += t2; }
+                }
+                if (i < width) {
+                    P1[r * pitch + i + 1] = run1 + c1;
+                    P2[r * pitch + i + 1] = run2 + c2;
+                }
+                run1 += __shfl_sync(0xffffffffu, c1, 31);
+                run2 += __shfl_sync(0xffffffffu, c2, 31);
+            }
+            if (lane == 0) {
+                P1[r * pitch] = 0.f;
+                P2[r * pitch] = 0.f;
+            }
+        }
+        __syncthreads();
+        const int rb = a.dz_run0[dz - a.dz_min], re = a.dz_run0[dz - a.dz_min + 1];
+        for (int k = rb; k < re; ++k) {
+            const MaskRun run = a.runs[k];
+            const int i0 = lx + run.x0 - a.x_min;        // first staged index
+            const int i1 = lx + run.x1 - a.x_min + 1;    // one past the last
+#pragma unroll
+            for (int v = 0; v < 2; ++v) {
+                const int r = ly + 4 * v + run.dy - a.dy_min;
+                s1[v] += P1[r * pitch + i1] - P1[r * pitch + i0];
+                s2[v] += P2[r * pitch + i1] - P2[r * pitch + i0];
+            }
+        }
+    }
+
+    const double nvox = (double)a.X * a.Y * a.Z;
+    const double mean = a.moments[0] / nvox;
+    const double var_f = fmax(a.moments[1] / nvox - mean * mean, 0.0);
+    const double floor_v = 1e-6 * a.mask_sum * var_f;
+    const int x = x0 + lx;
+    if (x >= a.X) return;
+#pragma unroll
+    for (int v = 0; v < 2; ++v) {
+        const int y = y0 + ly + 4 * v;
+        if (y >= a.Y) continue;
+        float wv = 0.f;
+        if (interior(x, a.X, a.s) && interior(y, a.Y, a.s) && interior(z, a.Z, a.s)) {
+            const double S1 = s1[v], S2 = s2[v];
+            const double V = S2 - S1 * S1 / a.mask_sum;
+            if (V > floor_v) wv = rsqrtf((float)V);
+        }
+        a.w[((size_t)z * a.Y + y) * a.X + x] = wv;
+    }
+}
+
+}  // namespace
+
+ttm_status launch_volume_moments(const float* f, size_t n, double* d_acc, cudaStream_t st,
+                                 long long* cnt) {
+    int blocks = (int)((n + 255) / 256);
+    if (blocks > 152 * 8) blocks = 152 * 8;
+    if (blocks < 1) blocks = 1;
+    moments_kernel<<<blocks, 256, 0, st>>>(f, n, d_acc);
+    return after_launch(cnt);
+}
+
+ttm_status launch_local_stats(const float* f, int X, int Y, int Z, const TemplateData& T,
+                              const double* d_moments, float* w, cudaStream_t st,
+                              long long* cnt) {
+    StatsArgs a;
+    a.f = f; a.w = w; a.X = X; a.Y = Y; a.Z = Z; a.s = T.desc.s;
+    a.runs = T.d_runs; a.dz_run0 = T.d_dz_run0;
+    a.dz_min = T.dz_min; a.dz_max = T.dz_max; a.dy_min = T.dy_min; a.dy_max = T.dy_max;
+    a.x_min = T.x_min; a.x_max = T.x_max;
+    a.mask_sum = T.desc.mask_sum;
+    a.moments = d_moments;
+    const int rows = kTY + (T.dy_max - T.dy_min);
+    const int pitch = kTX + (T.x_max - T.x_min) + 1;
+    const size_t smem = (size_t)2 * rows * pitch * sizeof(float);
+    if (smem > 200 * 1024) return TTM_ERR_UNSUPPORTED;
+    TTM_CUDA_TRY(cudaFuncSetAttribute(local_stats_kernel,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    dim3 grid((X + kTX - 1) / kTX, (Y + kTY - 1) / kTY, Z);
+    local_stats_kernel<<<grid, kStatThreads, smem, st>>>(a);
+    return after_launch(cnt);
+}
+
+}  // namespace ttm

@@ -1,0 +1,509 @@
+// C ABI of the engine (declared in include/ttm.h): argument validation, plan
+// construction (mask runs, tap-major template tables, rotation search grid),
+// workspace layout and dispatch of the kernels.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <numeric>
+#include <vector>
+
+#include "ttm_internal.h"
+
+namespace ttm {
+
+namespace {
+thread_local char g_last_error[256] = {0};
+}
+
+void note_cuda_error(cudaError_t e, const char* what, const char* file, int line) {
+    snprintf(g_last_error, sizeof(g_last_error), "%s: %s (%s:%d)", what, cudaGetErrorString(e),
+             file, line);
+}
+
+ttm_status after_launch(long long* counter) {
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        note_cuda_error(e, "kernel launch", __FILE__, __LINE__);
+        return TTM_ERR_CUDA;
+    }
+    if (counter) ++*counter;
+    return TTM_OK;
+}
+
+namespace {
+
+bool aligned(const void* p, size_t a) { return ((uintptr_t)p % a) == 0; }
+
+// Super-Fibonacci spiral on S^3 (Alexa, CVPR 2022): point i uses s = i + 1/2,
+// radii sqrt(s/n), sqrt(1 - s/n) and angles 2 pi s / sqrt(2), 2 pi s / psi
+// with psi^4 = psi + 4.  Every point is flipped to the half sphere a >= 0.
+void half_sphere_points(int n, std::vector<double>& q) {
+    const double psi = 1.533751168755204288118041;
+    const double phi = std::sqrt(2.0);
+    const double two_pi = 6.283185307179586476925287;
+    q.assign((size_t)4 * n, 0.0);
+    for (int i = 0; i < n; ++i) {
+        double s = i + 0.5;
+        double r = std::sqrt(s / n), R = std::sqrt(1.0 - s / n);
+        double al = two_pi * s / phi, be = two_pi * s / psi;
+        double v[4] = {r * std::sin(al), r * std::cos(al), R * std::sin(be), R * std::cos(be)};
+        double nn = std::sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2] + v[3] * v[3]);
+        double sg = v[0] < 0 ? -1.0 : 1.0;
+        for (int k = 0; k < 4; ++k) q[4 * i + k] = sg * v[k] / nn;
+    }
+}
+
+// Exponent vectors and multinomial weights of S^n(R^4) in C-ABI order
+// (host-side enumeration for the tables built at plan time).
+void sym_table(int n, std::vector<int>& e, std::vector<double>& mu) {
+    e.clear();
+    mu.clear();
+    std::vector<int> t(n, 0);
+    auto fact = [](int k) { double r = 1; for (int i = 2; i <= k; ++i) r *= i; return r; };
+    while (true) {
+        int ex[4] = {0, 0, 0, 0};
+        for (int p = 0; p < n; ++p) ex[t[p]]++;
+        for (int i = 0; i < 4; ++i) e.push_back(ex[i]);
+        mu.push_back(fact(n) / (fact(ex[0]) * fact(ex[1]) * fact(ex[2]) * fact(ex[3])));
+        int p = n - 1;
+        while (p >= 0 && t[p] == 3) --p;
+        if (p < 0) break;
+        t[p]++;
+        for (int k = p + 1; k < n; ++k) t[k] = t[p];
+    }
+}
+
+template <typename T>
+ttm_status dev_upload(T** dst, const std::vector<T>& src) {
+    *dst = nullptr;
+    if (src.empty()) return TTM_OK;
+    cudaError_t e = cudaMalloc((void**)dst, src.size() * sizeof(T));
+    if (e != cudaSuccess) {
+        note_cuda_error(e, "cudaMalloc", __FILE__, __LINE__);
+        cudaGetLastError();
+        return TTM_ERR_OUT_OF_MEMORY;
+    }
+    TTM_CUDA_TRY(cudaMemcpy(*dst, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice));
+    return TTM_OK;
+}
+
+ttm_status build_grid(ttm_plan_s* P) {
+    RotGrid& g = P->grid;
+    const int n = P->opts.n_grid > 0 ? P->opts.n_grid : 2048;
+    const int nc = P->opts.n_cells > 0 ? P->opts.n_cells : 128;
+    const int cand = P->opts.n_candidates > 0 ? P->opts.n_candidates : 8;
+    const int newton = P->opts.newton_steps > 0 ? P->opts.newton_steps : 6;
+    if (n > (1 << 20) || nc > n || cand > 8 || newton > 64) return TTM_ERR_INVALID_ARG;
+    std::vector<double> pts, ctr;
+    half_sphere_points(n, pts);
+    half_sphere_points(nc, ctr);
+    std::vector<int> label(n);
+    for (int i = 0; i < n; ++i) {
+        double best = -1.0;
+        int bl = 0;
+        for (int c = 0; c < nc; ++c) {
+            double d = std::fabs(pts[4 * i] * ctr[4 * c] + pts[4 * i + 1] * ctr[4 * c + 1] +
+                                 pts[4 * i + 2] * ctr[4 * c + 2] + pts[4 * i + 3] * ctr[4 * c + 3]);
+            if (d > best) { best = d; bl = c; }
+        }
+        label[i] = bl;
+    }
+    std::vector<int> order(n);
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return label[a] < label[b]; });
+    std::vector<int> e;
+    std::vector<double> mu;
+    sym_table(P->n_order, e, mu);
+    const int K = (int)mu.size();
+    const int K4 = rotation_row_stride(P->n_order);
+    std::vector<float> hq((size_t)4 * n), hm((size_t)K4 * n, 0.f);
+    std::vector<int> ends(n);
+    for (int g_i = 0; g_i < n; ++g_i) {
+        const double* q = &pts[4 * order[g_i]];
+        for (int k = 0; k < 4; ++k) hq[4 * g_i + k] = (float)q[k];
+        for (int a = 0; a < K; ++a) {
+            double v = mu[a];
+            for (int i = 0; i < 4; ++i)
+                for (int r = 0; r < e[4 * a + i]; ++r) v *= q[i];
+            hm[(size_t)g_i * K4 + a] = (float)v;
+        }
+        ends[g_i] = (g_i == n - 1 || label[order[g_i + 1]] != label[order[g_i]]) ? 1 : 0;
+    }
+    g.n_grid = n;
+    g.n_cells = nc;
+    g.n_cand = cand;
+    g.newton = newton;
+    TTM_TRY(dev_upload(&g.d_q, hq));
+    TTM_TRY(dev_upload(&g.d_m, hm));
+    TTM_TRY(dev_upload(&g.d_cell_end, ends));
+    return TTM_OK;
+}
+
+// Mask -> x-runs and tap-major component table.
+ttm_status prepare_template(ttm_plan_s* P, TemplateData& T, const float* d_mask) {
+    const int s = T.desc.s, c = T.desc.centre, K = T.desc.K;
+    const size_t s3 = (size_t)s * s * s;
+    std::vector<float> m(s3), comp((size_t)K * s3);
+    TTM_CUDA_TRY(cudaMemcpy(m.data(), d_mask, s3 * sizeof(float), cudaMemcpyDeviceToHost));
+    TTM_CUDA_TRY(cudaMemcpy(comp.data(), T.d_comp, comp.size() * sizeof(float),
+                            cudaMemcpyDeviceToHost));
+    for (float v : m)
+        if (!(v == 0.f || v == 1.f)) return TTM_ERR_UNSUPPORTED;
+    for (float v : comp)
+        if (!std::isfinite(v)) return TTM_ERR_NUMERIC;
+    std::vector<MaskRun> runs;
+    std::vector<int> tap0;
+    std::vector<float> taps;
+    int ntap = 0;
+    for (int uz = 0; uz < s; ++uz)
+        for (int uy = 0; uy < s; ++uy) {
+            int ux = 0;
+            while (ux < s) {
+                if (m[((size_t)uz * s + uy) * s + ux] != 1.f) { ++ux; continue; }
+                int u1 = ux;
+                while (u1 + 1 < s && m[((size_t)uz * s + uy) * s + u1 + 1] == 1.f) ++u1;
+                MaskRun r{uy - c, uz - c, ux - c, u1 - c};
+                runs.push_back(r);
+                tap0.push_back(ntap);
+                for (int xx = ux; xx <= u1; ++xx) {
+                    for (int a = 0; a < K; ++a)
+                        taps.push_back(comp[(size_t)a * s3 + ((size_t)uz * s + uy) * s + xx]);
+                    ++ntap;
+                }
+                ux = u1 + 1;
+            }
+        }
+    if (runs.empty()) return TTM_ERR_INVALID_ARG;
+    T.runs = runs;
+    T.n_taps = ntap;
+    T.dz_min = T.dy_min = T.x_min = 1 << 30;
+    T.dz_max = T.dy_max = T.x_max = -(1 << 30);
+    for (const MaskRun& r : runs) {
+        T.dz_min = std::min(T.dz_min, r.dz); T.dz_max = std::max(T.dz_max, r.dz);
+        T.dy_min = std::min(T.dy_min, r.dy); T.dy_max = std::max(T.dy_max, r.dy);
+        T.x_min = std::min(T.x_min, r.x0); T.x_max = std::max(T.x_max, r.x1);
+    }
+    std::vector<int> dz0(T.dz_max - T.dz_min + 2, 0);
+    {
+        size_t k = 0;
+        for (int dz = T.dz_min; dz <= T.dz_max; ++dz) {
+            dz0[dz - T.dz_min] = (int)k;
+            while (k < runs.size() && runs[k].dz == dz) ++k;
+        }
+        dz0[T.dz_max - T.dz_min + 1] = (int)runs.size();
+    }
+    (void)P;
+    TTM_TRY(dev_upload(&T.d_runs, runs));
+    TTM_TRY(dev_upload(&T.d_run_tap0, tap0));
+    TTM_TRY(dev_upload(&T.d_dz_run0, dz0));
+    TTM_TRY(dev_upload(&T.d_taps, taps));
+    return TTM_OK;
+}
+
+void free_plan(ttm_plan_s* P) {
+    for (TemplateData& T : P->tmpl) {
+        cudaFree(T.d_runs);
+        cudaFree(T.d_run_tap0);
+        cudaFree(T.d_dz_run0);
+        cudaFree(T.d_taps);
+        cudaFree(T.d_spec);
+    }
+    cudaFree(P->grid.d_q);
+    cudaFree(P->grid.d_m);
+    cudaFree(P->grid.d_cell_end);
+    delete P;
+}
+
+// workspace layout: [0, 256) header (moments, counters); [256, ...) scratch
+constexpr size_t kHeader = 256;
+constexpr int kPeakCapMax = 1 << 22;
+
+size_t peak_cap(size_t nvox) { return std::min(nvox, (size_t)kPeakCapMax); }
+
+size_t scratch_bytes(const ttm_plan_s* P, const ProblemData& pr) {
+    const size_t nv = pr.nvox();
+    size_t corr = align256((size_t)P->K * nv * sizeof(float));
+    size_t peaks = 2 * align256(nv * sizeof(float)) + align256(peak_cap(nv) * peak_record_bytes());
+    return std::max(corr, peaks);
+}
+
+ttm_status check_ws(const ttm_plan_s* P, void* ws, size_t bytes) {
+    if (!ws || bytes < P->ws_bytes) return TTM_ERR_WORKSPACE;
+    if (!aligned(ws, 256)) return TTM_ERR_INVALID_ARG;
+    return TTM_OK;
+}
+
+}  // namespace
+}  // namespace ttm
+
+using namespace ttm;
+
+extern "C" {
+
+const char* ttm_status_string(ttm_status s) {
+    switch (s) {
+        case TTM_OK: return "TTM_OK";
+        case TTM_ERR_INVALID_ARG: return "TTM_ERR_INVALID_ARG";
+        case TTM_ERR_UNSUPPORTED: return "TTM_ERR_UNSUPPORTED";
+        case TTM_ERR_OUT_OF_MEMORY: return "TTM_ERR_OUT_OF_MEMORY";
+        case TTM_ERR_CUDA: return "TTM_ERR_CUDA";
+        case TTM_ERR_TIMEOUT: return "TTM_ERR_TIMEOUT";
+        case TTM_ERR_NUMERIC: return "TTM_ERR_NUMERIC";
+        case TTM_ERR_WORKSPACE: return "TTM_ERR_WORKSPACE";
+        default: return "TTM_ERR_UNKNOWN";
+    }
+}
+
+int ttm_device_count(void) {
+    int n = 0;
+    if (cudaGetDeviceCount(&n) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return n;
+}
+
+static int build_chunk(int s, int n_rot) {
+    const size_t s3 = (size_t)s * s * s;
+    size_t nj = ((size_t)128 << 20) / (s3 * sizeof(float));
+    if (nj < 1) nj = 1;
+    if (nj > (size_t)n_rot) nj = (size_t)n_rot;
+    return (int)nj;
+}
+
+ttm_status ttm_build_workspace_size(int s, int n_order, int n_rot, size_t* bytes) {
+    if (!bytes || s < 3 || s > 128 || n_rot < 1) return TTM_ERR_INVALID_ARG;
+    if (n_order < 2 || n_order > 8 || (n_order & 1)) return TTM_ERR_UNSUPPORTED;
+    const size_t s3 = (size_t)s * s * s;
+    *bytes = kHeader + align256((size_t)build_chunk(s, n_rot) * s3 * sizeof(float));
+    return TTM_OK;
+}
+
+ttm_status ttm_build_tensor_template(const float* d_template, const float* d_mask, int s,
+                                     int n_order, const float* d_quats, const float* d_weights,
+                                     int n_rot, float* d_components, void* d_workspace,
+                                     size_t workspace_bytes, ttm_tt_desc* desc, void* stream) {
+    if (!d_template || !d_mask || !d_quats || !d_components || !desc) return TTM_ERR_INVALID_ARG;
+    size_t need = 0;
+    TTM_TRY(ttm_build_workspace_size(s, n_order, n_rot, &need));
+    if (!d_workspace || workspace_bytes < need) return TTM_ERR_WORKSPACE;
+    if (!aligned(d_workspace, 256) || !aligned(d_template, 4) || !aligned(d_mask, 4) ||
+        !aligned(d_quats, 4) || !aligned(d_components, 4))
+        return TTM_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    long long cnt = 0;
+    char* ws = (char*)d_workspace;
+    double* d_msum = (double*)ws;
+    int* d_bad = (int*)(ws + 8);
+    float* rot = (float*)(ws + kHeader);
+    TTM_CUDA_TRY(cudaMemsetAsync(ws, 0, kHeader, st));
+    TTM_TRY(launch_mask_sum(d_mask, s, d_msum, st, &cnt));
+    double msum = 0.0;
+    TTM_CUDA_TRY(cudaMemcpyAsync(&msum, d_msum, sizeof(double), cudaMemcpyDeviceToHost, st));
+    TTM_CUDA_TRY(cudaStreamSynchronize(st));
+    if (!(msum > 0.0)) return TTM_ERR_INVALID_ARG;
+    const int nj = build_chunk(s, n_rot);
+    const int s3 = s * s * s;
+    for (int j0 = 0; j0 < n_rot; j0 += nj) {
+        const int cnt_j = std::min(nj, n_rot - j0);
+        TTM_TRY(launch_rotate_normalise(d_template, d_mask, s, d_quats, j0, cnt_j, rot, msum, d_bad,
+                                        st, &cnt));
+        TTM_TRY(launch_fold_components(n_order, d_quats, d_weights, n_rot, j0, cnt_j, rot, s3,
+                                       d_components, j0 == 0, st, &cnt));
+    }
+    int bad = 0;
+    TTM_CUDA_TRY(cudaMemcpyAsync(&bad, d_bad, sizeof(int), cudaMemcpyDeviceToHost, st));
+    TTM_CUDA_TRY(cudaStreamSynchronize(st));
+    if (bad) return TTM_ERR_NUMERIC;
+    desc->n_order = n_order;
+    desc->K = n_comp(n_order);
+    desc->s = s;
+    desc->centre = s / 2;
+    desc->n_rot = n_rot;
+    desc->reserved = 0;
+    desc->mask_sum = msum;
+    return TTM_OK;
+}
+
+ttm_status ttm_plan(ttm_plan_t* out, int n_problems, const int* vol_dims, const int* tmpl_index,
+                    int n_templates, const ttm_tt_desc* descs, const float* const* d_components,
+                    const float* const* d_masks, const ttm_plan_opts* opts, void* stream) {
+    if (!out) return TTM_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (n_problems < 1 || n_templates < 1 || !vol_dims || !tmpl_index || !descs ||
+        !d_components || !d_masks)
+        return TTM_ERR_INVALID_ARG;
+    const int n_order = descs[0].n_order;
+    for (int k = 0; k < n_templates; ++k) {
+        const ttm_tt_desc& d = descs[k];
+        if (d.n_order != n_order) return TTM_ERR_UNSUPPORTED;  // one order per plan
+        if (d.n_order < 2 || d.n_order > 8 || (d.n_order & 1)) return TTM_ERR_UNSUPPORTED;
+        if (d.K != n_comp(d.n_order) || d.s < 3 || d.s > 128 || d.centre != d.s / 2 ||
+            !(d.mask_sum > 0.0) || !d_components[k] || !d_masks[k])
+            return TTM_ERR_INVALID_ARG;
+    }
+    for (int p = 0; p < n_problems; ++p) {
+        const int X = vol_dims[3 * p], Y = vol_dims[3 * p + 1], Z = vol_dims[3 * p + 2];
+        if (tmpl_index[p] < 0 || tmpl_index[p] >= n_templates) return TTM_ERR_INVALID_ARG;
+        const int s = descs[tmpl_index[p]].s;
+        if (X < s || Y < s || Z < s) return TTM_ERR_INVALID_ARG;
+        if ((size_t)X * Y * Z >= ((size_t)1 << 31)) return TTM_ERR_UNSUPPORTED;
+    }
+    ttm_plan_s* P = new (std::nothrow) ttm_plan_s();
+    if (!P) return TTM_ERR_OUT_OF_MEMORY;
+    if (opts) P->opts = *opts;
+    P->n_order = n_order;
+    P->K = n_comp(n_order);
+    cudaStream_t st = (cudaStream_t)stream;
+    ttm_status s_ = TTM_OK;
+    if (cudaStreamSynchronize(st) != cudaSuccess) { cudaGetLastError(); free_plan(P); return TTM_ERR_CUDA; }
+    P->tmpl.resize(n_templates);
+    for (int k = 0; k < n_templates && s_ == TTM_OK; ++k) {
+        P->tmpl[k].desc = descs[k];
+        P->tmpl[k].d_comp = d_components[k];
+        s_ = prepare_template(P, P->tmpl[k], d_masks[k]);
+    }
+    if (s_ == TTM_OK) s_ = build_grid(P);
+    if (s_ != TTM_OK) { free_plan(P); return s_; }
+    P->prob.resize(n_problems);
+    size_t ws = 0;
+    for (int p = 0; p < n_problems; ++p) {
+        ProblemData& pr = P->prob[p];
+        pr.X = vol_dims[3 * p]; pr.Y = vol_dims[3 * p + 1]; pr.Z = vol_dims[3 * p + 2];
+        pr.tmpl = tmpl_index[p];
+        pr.path = TTM_PATH_DIRECT;
+        ws = std::max(ws, scratch_bytes(P, pr));
+    }
+    P->ws_bytes = kHeader + ws;
+    *out = P;
+    return TTM_OK;
+}
+
+ttm_status ttm_plan_workspace_size(ttm_plan_t plan, size_t* bytes) {
+    if (!plan || !bytes) return TTM_ERR_INVALID_ARG;
+    *bytes = plan->ws_bytes;
+    return TTM_OK;
+}
+
+ttm_status ttm_plan_problem_path(ttm_plan_t plan, int problem, int* path) {
+    if (!plan || !path || problem < 0 || problem >= (int)plan->prob.size())
+        return TTM_ERR_INVALID_ARG;
+    *path = plan->prob[problem].path;
+    return TTM_OK;
+}
+
+ttm_status ttm_plan_launch_count(ttm_plan_t plan, long long* launches) {
+    if (!plan || !launches) return TTM_ERR_INVALID_ARG;
+    *launches = plan->launches;
+    return TTM_OK;
+}
+
+void ttm_plan_destroy(ttm_plan_t plan) {
+    if (plan) free_plan(plan);
+}
+
+ttm_status ttm_local_stats(ttm_plan_t plan, const float* const* d_vols, float* const* d_w,
+                           void* d_workspace, size_t workspace_bytes, void* stream) {
+    if (!plan || !d_vols || !d_w) return TTM_ERR_INVALID_ARG;
+    TTM_TRY(check_ws(plan, d_workspace, workspace_bytes));
+    const int np = (int)plan->prob.size();
+    for (int p = 0; p < np; ++p)
+        if (!d_vols[p] || !d_w[p] || !aligned(d_vols[p], 4) || !aligned(d_w[p], 4))
+            return TTM_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    double* d_mom = (double*)d_workspace;
+    for (int p = 0; p < np; ++p) {
+        const ProblemData& pr = plan->prob[p];
+        TTM_CUDA_TRY(cudaMemsetAsync(d_mom, 0, 2 * sizeof(double), st));
+        TTM_TRY(launch_volume_moments(d_vols[p], pr.nvox(), d_mom, st, &plan->launches));
+        TTM_TRY(launch_local_stats(d_vols[p], pr.X, pr.Y, pr.Z, plan->tmpl[pr.tmpl], d_mom, d_w[p],
+                                   st, &plan->launches));
+    }
+    return TTM_OK;
+}
+
+ttm_status ttm_correlate(ttm_plan_t plan, const float* const* d_vols, const float* const* d_w,
+                         float* const* d_score, float* const* d_quat, float* const* d_lambda,
+                         float* const* d_components_out, void* d_workspace,
+                         size_t workspace_bytes, void* stream) {
+    if (!plan || !d_vols || !d_w || !d_score || !d_quat) return TTM_ERR_INVALID_ARG;
+    TTM_TRY(check_ws(plan, d_workspace, workspace_bytes));
+    const int np = (int)plan->prob.size();
+    for (int p = 0; p < np; ++p) {
+        if (!d_vols[p] || !d_w[p] || !d_score[p] || !d_quat[p]) return TTM_ERR_INVALID_ARG;
+        if (!aligned(d_quat[p], 16) || !aligned(d_vols[p], 4) || !aligned(d_score[p], 4))
+            return TTM_ERR_INVALID_ARG;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    float* corr = (float*)((char*)d_workspace + kHeader);
+    for (int p = 0; p < np; ++p) {
+        const ProblemData& pr = plan->prob[p];
+        const TemplateData& T = plan->tmpl[pr.tmpl];
+        TTM_TRY(launch_direct_corr(d_vols[p], pr.X, pr.Y, pr.Z, T, plan->K, corr, st,
+                                   &plan->launches));
+        TTM_TRY(launch_rotation(plan->n_order, corr, d_w[p], pr.nvox(), pr.X, pr.Y, pr.Z,
+                                T.desc.s, plan->grid, d_score[p], d_quat[p],
+                                d_lambda ? d_lambda[p] : nullptr,
+                                d_components_out ? d_components_out[p] : nullptr, st,
+                                &plan->launches));
+    }
+    return TTM_OK;
+}
+
+ttm_status ttm_extract_peaks(ttm_plan_t plan, int problem, const float* d_score,
+                             const float* d_quat, const float* d_lambda, float threshold,
+                             int radius, int max_peaks, ttm_peak* h_out, int* n_out,
+                             void* d_workspace, size_t workspace_bytes, void* stream) {
+    if (!plan || problem < 0 || problem >= (int)plan->prob.size() || !d_score || !d_quat ||
+        !n_out || radius < 0 || radius > 32 || max_peaks < 0 || (max_peaks > 0 && !h_out))
+        return TTM_ERR_INVALID_ARG;
+    if (!aligned(d_quat, 16)) return TTM_ERR_INVALID_ARG;
+    TTM_TRY(check_ws(plan, d_workspace, workspace_bytes));
+    const ProblemData& pr = plan->prob[problem];
+    const size_t nv = pr.nvox();
+    cudaStream_t st = (cudaStream_t)stream;
+    char* ws = (char*)d_workspace;
+    int* d_count = (int*)(ws + 16);
+    float* tmp_a = (float*)(ws + kHeader);
+    float* tmp_b = (float*)(ws + kHeader + align256(nv * sizeof(float)));
+    void* list = ws + kHeader + 2 * align256(nv * sizeof(float));
+    const int cap = (int)peak_cap(nv);
+    TTM_CUDA_TRY(cudaMemsetAsync(d_count, 0, sizeof(int), st));
+    TTM_TRY(launch_peak_candidates_full(d_score, d_quat, d_lambda, pr.X, pr.Y, pr.Z, threshold,
+                                        radius, tmp_a, tmp_b, list, cap, d_count, st,
+                                        &plan->launches));
+    int count = 0;
+    TTM_CUDA_TRY(cudaMemcpyAsync(&count, d_count, sizeof(int), cudaMemcpyDeviceToHost, st));
+    TTM_CUDA_TRY(cudaStreamSynchronize(st));
+    if (count > cap) return TTM_ERR_WORKSPACE;
+    struct Rec { int idx; float score, lambda, q[4]; int pad; };
+    static_assert(sizeof(Rec) == 32, "peak record layout");
+    if (peak_record_bytes() != sizeof(Rec)) return TTM_ERR_CUDA;
+    std::vector<Rec> recs(count);
+    if (count > 0) {
+        TTM_CUDA_TRY(cudaMemcpyAsync(recs.data(), list, (size_t)count * sizeof(Rec),
+                                     cudaMemcpyDeviceToHost, st));
+        TTM_CUDA_TRY(cudaStreamSynchronize(st));
+    }
+    std::sort(recs.begin(), recs.end(), [](const Rec& a, const Rec& b) {
+        if (a.score != b.score) return a.score > b.score;
+        return a.idx < b.idx;
+    });
+    const int nout = std::min(count, max_peaks);
+    for (int i = 0; i < nout; ++i) {
+        const Rec& r = recs[i];
+        ttm_peak& o = h_out[i];
+        o.x = (int)(r.idx % pr.X);
+        o.y = (int)((r.idx / pr.X) % pr.Y);
+        o.z = (int)(r.idx / ((size_t)pr.X * pr.Y));
+        o.score = r.score;
+        o.lambda = r.lambda;
+        for (int k = 0; k < 4; ++k) o.q[k] = r.q[k];
+    }
+    *n_out = nout;
+    return TTM_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,103 @@
+// Internal declarations shared by the C ABI and the kernel files.
+#pragma once
+
+#include <vector>
+
+#include "ttm_common.cuh"
+
+namespace ttm {
+
+// One x-run of a binary mask: mask(c + dx, c + dy, c + dz) = 1 for
+// dx in [x0, x1], all offsets relative to the box centre c.
+struct MaskRun {
+    int dy, dz, x0, x1;
+};
+
+// Plan-side image of one template.
+struct TemplateData {
+    ttm_tt_desc desc{};
+    const float* d_comp = nullptr;      // caller-owned K x s^3 components
+    std::vector<MaskRun> runs;          // mask as x-runs, sorted by (dz, dy)
+    int n_taps = 0;                     // mask voxels
+    int dz_min = 0, dz_max = -1, dy_min = 0, dy_max = -1, x_min = 0, x_max = -1;
+    MaskRun* d_runs = nullptr;          // device copy of runs
+    int* d_run_tap0 = nullptr;          // first tap index of every run
+    int* d_dz_run0 = nullptr;           // first run of every dz plane (dz_max-dz_min+2)
+    float* d_taps = nullptr;            // n_taps x K component values, tap-major
+    // FFT path (allocated when some problem with this template uses it)
+    void* d_spec = nullptr;             // K template spectra per FFT shape
+    int spec_shape[3] = {0, 0, 0};
+};
+
+struct ProblemData {
+    int X = 0, Y = 0, Z = 0;
+    int tmpl = 0;
+    int path = TTM_PATH_DIRECT;
+    size_t nvox() const { return (size_t)X * Y * Z; }
+};
+
+// Rotation search grid (device tables owned by the plan).
+struct RotGrid {
+    int n_grid = 0, n_cells = 0, n_cand = 0, newton = 0;
+    float* d_q = nullptr;        // n_grid x 4 unit quaternions, a >= 0, sorted by cell
+    float* d_m = nullptr;        // n_grid x K: mu_alpha q_g^alpha
+    int* d_cell_end = nullptr;   // n_grid: 1 if the next point starts a new cell
+};
+
+}  // namespace ttm
+
+struct ttm_plan_s {
+    std::vector<ttm::TemplateData> tmpl;
+    std::vector<ttm::ProblemData> prob;
+    ttm_plan_opts opts{};
+    int n_order = 4;
+    int K = 35;
+    ttm::RotGrid grid;
+    size_t ws_bytes = 0;
+    long long launches = 0;
+};
+
+namespace ttm {
+
+// ---- workspace layout helpers ----
+inline size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+// ---- kernel launchers (each returns TTM_OK or TTM_ERR_CUDA) ----
+
+// sum f and sum f^2 over a whole volume into d_acc[0..1] (FP64, must be zeroed)
+ttm_status launch_volume_moments(const float* f, size_t n, double* d_acc, cudaStream_t st,
+                                 long long* cnt);
+
+ttm_status launch_local_stats(const float* f, int X, int Y, int Z, const TemplateData& T,
+                              const double* d_moments, float* w, cudaStream_t st,
+                              long long* cnt);
+
+ttm_status launch_direct_corr(const float* f, int X, int Y, int Z, const TemplateData& T,
+                              int K, float* corr, cudaStream_t st, long long* cnt);
+
+ttm_status launch_rotation(int n_order, const float* corr, const float* w, size_t nvox,
+                           int X, int Y, int Z, int s, const RotGrid& g, float* score,
+                           float* quat, float* lambda, float* comp_out, cudaStream_t st,
+                           long long* cnt);
+
+// tensor template build
+ttm_status launch_rotate_normalise(const float* t, const float* m, int s, const float* quats,
+                                   int j0, int nj, float* out, double mask_sum, int* d_bad,
+                                   cudaStream_t st, long long* cnt);
+ttm_status launch_mask_sum(const float* m, int s, double* d_out, cudaStream_t st,
+                           long long* cnt);
+ttm_status launch_fold_components(int n_order, const float* quats, const float* weights,
+                                  int n_rot_total, int j0, int nj, const float* rot, int s3,
+                                  float* comp, bool first, cudaStream_t st, long long* cnt);
+
+// peaks
+size_t peak_record_bytes();
+ttm_status launch_peak_candidates_full(const float* score, const float* quat, const float* lam,
+                                       int X, int Y, int Z, float thr, int radius, float* tmp_a,
+                                       float* tmp_b, void* list, int cap, int* d_count,
+                                       cudaStream_t st, long long* cnt);
+
+// padded row length of the rotation-grid monomial table
+int rotation_row_stride(int n_order);
+
+}  // namespace ttm

@@ -1,0 +1,138 @@
+"""Convenience layer over the C ABI: owns torch-allocated buffers and a plan.
+
+A :class:`Matcher` is what a user calls: it builds one plan for a batch of
+(volume, template) problems, keeps the output maps and the workspace on the
+GPU, and runs local statistics + correlation/score/rotation on a stream.  All
+computation happens in libttm.so.
+"""
+
+from __future__ import annotations
+
+from typing import Dict, List, Optional, Sequence, Tuple
+
+import numpy as np
+
+from . import _binding as B
+
+
+def _torch():
+    import torch
+    if not torch.cuda.is_available():
+        raise RuntimeError("paper_2311_07561_gb300 needs a CUDA device (sm_103a); none is visible")
+    return torch
+
+
+def build_template(template, mask, n_order: int, quats, weights=None, stream=None):
+    """Fold a template into its K tensor components on the GPU (Sec. 3.2).
+
+    template, mask: (s, s, s) float32 arrays (numpy or torch); quats: (n_rot, 4).
+    Returns (components (K, s, s, s) cuda tensor, TTDesc).
+    """
+    torch = _torch()
+    dev = torch.device("cuda")
+    t = torch.as_tensor(np.asarray(template, dtype=np.float32)).to(dev).contiguous()
+    m = torch.as_tensor(np.asarray(mask, dtype=np.float32)).to(dev).contiguous()
+    q = torch.as_tensor(np.asarray(quats, dtype=np.float32)).to(dev).contiguous()
+    wt = None
+    if weights is not None:
+        wt = torch.as_tensor(np.asarray(weights, dtype=np.float32)).to(dev).contiguous()
+    s = int(t.shape[0])
+    n_rot = int(q.shape[0])
+    K = (n_order + 1) * (n_order + 2) * (n_order + 3) // 6
+    comp = torch.empty((K, s, s, s), dtype=torch.float32, device=dev)
+    ws = torch.empty(B.ttm_build_workspace_size(s, n_order, n_rot), dtype=torch.uint8, device=dev)
+    desc = B.ttm_build_tensor_template(t, m, s, n_order, q, wt, n_rot, comp, ws, stream)
+    return comp, desc
+
+
+class Matcher:
+    """A plan over a batch of problems plus its output buffers.
+
+    templates: list of (components, desc, mask) with components/mask on the GPU
+    problems:  list of ((X, Y, Z), template_index)
+    """
+
+    def __init__(self, templates: Sequence[Tuple], problems: Sequence[Tuple[Tuple[int, int, int], int]],
+                 opts: Optional[B.PlanOpts] = None, want_lambda: bool = True, stream=None):
+        torch = _torch()
+        dev = torch.device("cuda")
+        self._keep = [(c, torch.as_tensor(np.asarray(m, dtype=np.float32)).to(dev).contiguous()
+                       if not hasattr(m, "data_ptr") else m) for c, _, m in templates]
+        self.descs = [d for _, d, _ in templates]
+        self.problems = [(tuple(int(v) for v in dims), int(k)) for dims, k in problems]
+        self.plan = B.ttm_plan([p[0] for p in self.problems], [p[1] for p in self.problems],
+                               self.descs, [c for c, _ in self._keep], [m for _, m in self._keep],
+                               opts, stream)
+        self.ws = torch.empty(B.ttm_plan_workspace_size(self.plan), dtype=torch.uint8, device=dev)
+        self.w, self.score, self.quat, self.lam = [], [], [], []
+        for (X, Y, Z), _ in self.problems:
+            shape = (Z, Y, X)
+            self.w.append(torch.empty(shape, dtype=torch.float32, device=dev))
+            self.score.append(torch.empty(shape, dtype=torch.float32, device=dev))
+            self.quat.append(torch.empty(shape + (4,), dtype=torch.float32, device=dev))
+            self.lam.append(torch.empty(shape, dtype=torch.float32, device=dev) if want_lambda else None)
+        self.want_lambda = want_lambda
+
+    def _check_inputs(self, vols: Sequence, components_out: Optional[Sequence]) -> None:
+        if len(vols) != len(self.problems):
+            raise ValueError(f"expected {len(self.problems)} volumes, got {len(vols)}")
+        for p, ((X, Y, Z), k) in enumerate(self.problems):
+            v = vols[p]
+            if tuple(v.shape) != (Z, Y, X) or not v.is_cuda or not v.is_contiguous() \
+                    or v.dtype != self.w[p].dtype:
+                raise ValueError(f"volume {p} must be a contiguous float32 cuda tensor of "
+                                 f"shape (Z, Y, X) = {(Z, Y, X)}")
+            if components_out is not None:
+                c = components_out[p]
+                if tuple(c.shape) != (self.descs[k].K, Z, Y, X) or not c.is_contiguous():
+                    raise ValueError(f"components_out[{p}] must be (K, Z, Y, X) contiguous")
+
+    def run(self, vols: Sequence, components_out: Optional[Sequence] = None, stream=None) -> None:
+        """Local statistics, correlation, score and rotation for every problem."""
+        self._check_inputs(vols, components_out)
+        B.ttm_local_stats(self.plan, vols, self.w, self.ws, stream)
+        B.ttm_correlate(self.plan, vols, self.w, self.score, self.quat,
+                        self.lam if self.want_lambda else None, components_out, self.ws, stream)
+
+    def match_host(self, host_vols: Sequence[np.ndarray], pinned_in: Optional[List] = None,
+                   pinned_out: Optional[List] = None, stream=None) -> Dict[str, List]:
+        """End-to-end call from host memory: copy in, run, copy the maps out."""
+        torch = _torch()
+        dev = torch.device("cuda")
+        vols = []
+        for i, hv in enumerate(host_vols):
+            src = pinned_in[i] if pinned_in is not None else torch.from_numpy(np.ascontiguousarray(hv, dtype=np.float32))
+            vols.append(src.to(dev, non_blocking=True))
+        self.run(vols, stream=stream)
+        outs = {"score": [], "quat": [], "lambda": []}
+        for i in range(len(self.problems)):
+            if pinned_out is not None:
+                so, qo, lo = pinned_out[i]
+                so.copy_(self.score[i], non_blocking=True)
+                qo.copy_(self.quat[i], non_blocking=True)
+                if self.want_lambda and lo is not None:
+                    lo.copy_(self.lam[i], non_blocking=True)
+                outs["score"].append(so); outs["quat"].append(qo); outs["lambda"].append(lo)
+            else:
+                outs["score"].append(self.score[i].cpu())
+                outs["quat"].append(self.quat[i].cpu())
+                outs["lambda"].append(self.lam[i].cpu() if self.want_lambda else None)
+        return outs
+
+    def peaks(self, problem: int, threshold: float, radius: int, max_peaks: int, stream=None):
+        return B.ttm_extract_peaks(self.plan, problem, self.score[problem], self.quat[problem],
+                                   self.lam[problem], threshold, radius, max_peaks, self.ws, stream)
+
+    def launch_count(self) -> int:
+        return B.ttm_plan_launch_count(self.plan)
+
+    def close(self) -> None:
+        if self.plan:
+            B.ttm_plan_destroy(self.plan)
+            self.plan = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

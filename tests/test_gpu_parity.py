@@ -1,0 +1,268 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Tolerances: |dC|, |dscore|, |dlambda| <= 1e-4 (the FP32 gate), w to 1e-5
+relative, template components to 2e-5 of their largest magnitude; index work
+(peaks) bit-exact.  Where several results are correct (two rotations with the
+same phi to within 1e-5) the test checks the rotation is a valid maximiser.
+"""
+
+import numpy as np
+import pytest
+
+import synth
+from oracle import ttm_oracle as o
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-4
+
+
+@pytest.fixture(scope="module")
+def ttm():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    import paper_2311_07561_gb300 as ttm
+    import os
+    if not os.path.exists(ttm.LIB_PATH):
+        import __graft_entry__
+        __graft_entry__.build()
+    ttm.load_library()
+    return ttm
+
+
+def _cuda(a):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).cuda()
+
+
+def _run(ttm, wl, comp, desc, opts=None, want_comp=True):
+    import torch
+    X = wl.volume.shape[2]; Y = wl.volume.shape[1]; Z = wl.volume.shape[0]
+    m = ttm.Matcher([(comp, desc, wl.mask)], [((X, Y, Z), 0)], opts=opts)
+    vol = _cuda(wl.volume)
+    comps = [torch.empty((desc.K, Z, Y, X), dtype=torch.float32, device="cuda")] if want_comp else None
+    m.run([vol], components_out=comps)
+    torch.cuda.synchronize()
+    out = dict(w=m.w[0].cpu().numpy(), score=m.score[0].cpu().numpy(),
+               quat=m.quat[0].cpu().numpy(), lam=m.lam[0].cpu().numpy(),
+               comp=comps[0].cpu().numpy() if want_comp else None, matcher=m)
+    return out
+
+
+@pytest.fixture(scope="module")
+def c1(ttm):
+    """Config-1 shape: 64^3, 15^3 template (5 blobs), r = 7, 4 copies, SNR 1, n = 4."""
+    wl = synth.config_workload("c1", n_rot=1000)
+    T = o.tensor_template(wl.template, wl.mask, wl.quadrature.astype(np.float64), wl.weights, 4)
+    comp, desc = ttm.build_template(wl.template, wl.mask, 4, wl.quadrature)
+    res = _run(ttm, wl, comp, desc)
+    w_o, C_o = o.ttm_components(wl.volume, T, wl.mask)
+    return dict(wl=wl, T=T, comp=comp, desc=desc, res=res, w_o=w_o, C_o=C_o)
+
+
+def test_tensor_template_matches_oracle(c1):
+    g = c1["comp"].cpu().numpy()
+    T = c1["T"]
+    assert g.shape == T.shape
+    err = np.abs(g - T).max()
+    assert err <= 2e-5 * np.abs(T).max(), err
+    assert c1["desc"].K == 35 and c1["desc"].s == 15 and c1["desc"].centre == 7
+    assert c1["desc"].mask_sum == pytest.approx(c1["wl"].mask.sum())
+
+
+@pytest.mark.parametrize("n,s,r,nrot", [(2, 11, 5, 400), (6, 9, 4, 300)])
+def test_tensor_template_other_orders(ttm, n, s, r, nrot):
+    t = synth.blob_template(s, 4, seed=n)
+    m = synth.ball_mask(s, r)
+    q = synth.super_fibonacci_quaternions(nrot).astype(np.float32)
+    w = np.full(nrot, 1.0 / nrot)
+    comp, desc = ttm.build_template(t, m, n, q)
+    T = o.tensor_template(t, m, q.astype(np.float64), w, n)
+    err = np.abs(comp.cpu().numpy() - T).max()
+    assert err <= 2e-5 * np.abs(T).max(), err
+    assert desc.K == len(o.multi_indices(n))
+
+
+def test_local_stats_match_oracle(c1):
+    w = c1["res"]["w"]
+    w_o = c1["w_o"]
+    assert np.array_equal(w > 0, w_o > 0)
+    nz = w_o > 0
+    rel = np.abs(w[nz] - w_o[nz]) / w_o[nz]
+    assert rel.max() <= 1e-5, rel.max()
+
+
+def test_components_and_score_match_oracle(c1):
+    C = c1["res"]["comp"]
+    C_o = c1["C_o"]
+    err = np.abs(C - C_o).max()
+    assert err <= TOL, err
+    score_o = o.frobenius_score(C_o, 4)
+    serr = np.abs(c1["res"]["score"] - score_o).max()
+    assert serr <= TOL, serr
+    # outside the interior everything is zero / identity
+    keep = o.interior_mask(c1["wl"].volume.shape, 15)
+    assert np.all(c1["res"]["score"][~keep] == 0)
+    assert np.all(c1["res"]["quat"][~keep] == np.array([1, 0, 0, 0], dtype=np.float32))
+    assert np.all(c1["res"]["lam"][~keep] == 0)
+
+
+def _rotation_check(C_o_pts, lam, q, n, planted=()):
+    lam_o, q_o = o.dominant_z_eigenpair(C_o_pts, n)
+    dl = np.abs(lam - lam_o)
+    assert dl.max() <= TOL, (dl.max(), np.argmax(dl))
+    # the reported rotation attains the reported value and the maximum
+    phi_at_gpu = o.phi_unique(C_o_pts, q.astype(np.float64), n)
+    assert np.all(phi_at_gpu >= lam_o - TOL), (lam_o - phi_at_gpu).max()
+    assert np.allclose(np.linalg.norm(q, axis=1), 1.0, atol=1e-5)
+    assert np.all(q[:, 0] >= 0)
+    for i in planted:
+        ang = o.rotation_angle_deg(q[i], q_o[i])
+        assert ang <= 1.0 or phi_at_gpu[i] >= lam_o[i] - 1e-5, (i, ang)
+    return lam_o, q_o
+
+
+def test_rotation_matches_oracle(c1):
+    wl = c1["wl"]
+    rng = np.random.default_rng(21)
+    lo, hi = 7, 64 - 15 + 7
+    pts = np.concatenate([wl.positions, rng.integers(lo, hi + 1, size=(300, 3))])
+    C_o_pts = c1["C_o"][:, pts[:, 2], pts[:, 1], pts[:, 0]].T
+    lam = c1["res"]["lam"][pts[:, 2], pts[:, 1], pts[:, 0]]
+    q = c1["res"]["quat"][pts[:, 2], pts[:, 1], pts[:, 0]]
+    _rotation_check(C_o_pts, lam, q, 4, planted=range(len(wl.positions)))
+
+
+def test_peaks_kernel_is_exact_on_given_scores(ttm, c1):
+    """Peak extraction on a score map given as input, with many exact ties."""
+    import torch
+    m = c1["res"]["matcher"]
+    rng = np.random.default_rng(3)
+    score = np.round(rng.random((64, 64, 64)), 2).astype(np.float32)
+    quat = np.zeros((64, 64, 64, 4), dtype=np.float32)
+    quat[..., 0] = 1.0
+    quat[..., 1] = np.arange(64 ** 3, dtype=np.float32).reshape(64, 64, 64)
+    lam = (score * 0.5).astype(np.float32)
+    for radius in (0, 1, 3):
+        got = ttm.ttm_extract_peaks(m.plan, 0, _cuda(score), _cuda(quat), _cuda(lam), 0.5, radius,
+                                    100000, m.ws)
+        expect = o.extract_peaks(score.astype(np.float64), 0.5, radius, 100000)
+        lin = (got["z"].astype(np.int64) * 64 + got["y"]) * 64 + got["x"]
+        assert np.array_equal(lin, expect), radius
+        assert np.array_equal(got["score"], score.ravel()[expect])
+        assert np.array_equal(got["q"][:, 1], quat[..., 1].ravel()[expect])
+        assert np.array_equal(got["lambda"], lam.ravel()[expect])
+    few = ttm.ttm_extract_peaks(m.plan, 0, _cuda(score), _cuda(quat), None, 0.5, 3, 7, m.ws)
+    assert len(few) == 7 and np.all(few["lambda"] == 0)
+
+
+def test_peaks_on_planted_volume(ttm, c1):
+    m = c1["res"]["matcher"]
+    got = m.peaks(0, 0.0, 7, 4)
+    score_o = o.frobenius_score(c1["C_o"], 4)
+    expect = o.extract_peaks(score_o, 0.0, 7, 4)
+    lin = (got["z"].astype(np.int64) * 64 + got["y"]) * 64 + got["x"]
+    assert np.array_equal(lin, expect)
+
+
+def test_ragged_volume_and_order_two(ttm):
+    wl = synth.make_workload((39, 45, 70), 11, 4, 2, 1.0, 2, 300, radius=5, seeds=(7, 8, 9))
+    T = o.tensor_template(wl.template, wl.mask, wl.quadrature.astype(np.float64), wl.weights, 2)
+    comp, desc = ttm.build_template(wl.template, wl.mask, 2, wl.quadrature)
+    res = _run(ttm, wl, comp, desc)
+    w_o, C_o = o.ttm_components(wl.volume, T, wl.mask)
+    assert np.abs(res["comp"] - C_o).max() <= TOL
+    nz = w_o > 0
+    assert np.array_equal(res["w"] > 0, nz)
+    assert (np.abs(res["w"][nz] - w_o[nz]) / w_o[nz]).max() <= 1e-5
+    pts = np.argwhere(nz)[::97][:200][:, ::-1]
+    _rotation_check(C_o[:, pts[:, 2], pts[:, 1], pts[:, 0]].T,
+                    res["lam"][pts[:, 2], pts[:, 1], pts[:, 0]],
+                    res["quat"][pts[:, 2], pts[:, 1], pts[:, 0]], 2)
+
+
+def test_order_six(ttm):
+    wl = synth.make_workload((30, 28, 26), 9, 3, 1, 1.0, 6, 300, radius=4, seeds=(2, 3, 4))
+    T = o.tensor_template(wl.template, wl.mask, wl.quadrature.astype(np.float64), wl.weights, 6)
+    comp, desc = ttm.build_template(wl.template, wl.mask, 6, wl.quadrature)
+    res = _run(ttm, wl, comp, desc)
+    w_o, C_o = o.ttm_components(wl.volume, T, wl.mask)
+    assert np.abs(res["comp"] - C_o).max() <= TOL
+    assert np.abs(res["score"] - o.frobenius_score(C_o, 6)).max() <= TOL
+    pts = np.argwhere(w_o > 0)[::53][:120][:, ::-1]
+    _rotation_check(C_o[:, pts[:, 2], pts[:, 1], pts[:, 0]].T,
+                    res["lam"][pts[:, 2], pts[:, 1], pts[:, 0]],
+                    res["quat"][pts[:, 2], pts[:, 1], pts[:, 0]], 6)
+
+
+def test_degenerate_inputs(ttm):
+    """A volume exactly one box wide (a single interior voxel) and a constant
+    volume (zero variance everywhere: w = 0, score 0, identity rotation)."""
+    s = 9
+    t = synth.blob_template(s, 3, seed=1)
+    m = synth.ball_mask(s, 4)
+    q = synth.super_fibonacci_quaternions(200).astype(np.float32)
+    comp, desc = ttm.build_template(t, m, 4, q)
+    T = o.tensor_template(t, m, q.astype(np.float64), np.full(200, 1 / 200), 4)
+    rng = np.random.default_rng(0)
+    one = synth.Workload("one", rng.normal(size=(s, s, s)).astype(np.float32), t, m, 4, 4, q,
+                         np.full(200, 1 / 200), np.zeros((0, 3), int), np.zeros((0, 4)), 0.0, 0.0)
+    res = _run(ttm, one, comp, desc)
+    w_o, C_o = o.ttm_components(one.volume, T, m)
+    assert np.count_nonzero(res["score"]) == 1
+    assert np.abs(res["comp"] - C_o).max() <= TOL
+    const = synth.Workload("const", np.full((20, 21, 22), 2.5, np.float32), t, m, 4, 4, q,
+                           np.full(200, 1 / 200), np.zeros((0, 3), int), np.zeros((0, 4)), 0.0, 0.0)
+    res = _run(ttm, const, comp, desc)
+    assert np.all(res["w"] == 0) and np.all(res["score"] == 0) and np.all(res["lam"] == 0)
+    assert np.all(res["quat"] == np.array([1, 0, 0, 0], np.float32))
+
+
+def test_batched_plan_matches_single_problems(ttm):
+    import torch
+    wa = synth.make_workload((40, 36, 34), 11, 4, 2, 1.0, 4, 200, radius=5, seeds=(1, 2, 3))
+    wb = synth.make_workload((33, 47, 29), 9, 3, 1, 1.0, 4, 200, radius=4, seeds=(4, 5, 6))
+    ca, da = ttm.build_template(wa.template, wa.mask, 4, wa.quadrature)
+    cb, db = ttm.build_template(wb.template, wb.mask, 4, wb.quadrature)
+    vols = [wa.volume, wb.volume]
+    dims_a = wa.volume.shape[::-1]
+    dims_b = wb.volume.shape[::-1]
+    probs = [(dims_a, 0), (dims_a, 1), (dims_b, 0), (dims_b, 1)]
+    mb = ttm.Matcher([(ca, da, wa.mask), (cb, db, wb.mask)], probs)
+    dv = [_cuda(vols[0]), _cuda(vols[0]), _cuda(vols[1]), _cuda(vols[1])]
+    mb.run(dv)
+    for p, ((X, Y, Z), k) in enumerate(probs):
+        single = ttm.Matcher([((ca, da, wa.mask), (cb, db, wb.mask))[k]], [((X, Y, Z), 0)])
+        single.run([dv[p]])
+        torch.cuda.synchronize()
+        assert torch.equal(single.score[0], mb.score[p])
+        assert torch.equal(single.quat[0], mb.quat[p])
+        assert torch.equal(single.w[0], mb.w[p])
+        single.close()
+    mb.close()
+
+
+def test_gpu_argument_errors(ttm):
+    import torch
+    s = 9
+    t = synth.blob_template(s, 3, seed=1)
+    m = synth.ball_mask(s, 4)
+    q = synth.super_fibonacci_quaternions(50).astype(np.float32)
+    comp, desc = ttm.build_template(t, m, 4, q)
+    # soft mask is not supported by the plan
+    soft = m * 0.5
+    with pytest.raises(ttm.TTMError) as e:
+        ttm.Matcher([(comp, desc, soft)], [((20, 20, 20), 0)])
+    assert e.value.status == -2
+    mt = ttm.Matcher([(comp, desc, m)], [((20, 20, 20), 0)])
+    vol = _cuda(np.random.default_rng(1).normal(size=(20, 20, 20)))
+    small_ws = torch.empty(64, dtype=torch.uint8, device="cuda")
+    with pytest.raises(ttm.TTMError) as e:
+        ttm.ttm_local_stats(mt.plan, [vol], mt.w, small_ws)
+    assert e.value.status == -7
+    ttm.ttm_local_stats(mt.plan, [vol], mt.w, mt.ws)
+    bad_q = torch.empty(20 * 20 * 20 * 4 + 1, dtype=torch.float32, device="cuda")[1:]
+    with pytest.raises(ttm.TTMError) as e:
+        ttm.ttm_correlate(mt.plan, [vol], mt.w, mt.score, [bad_q], None, None, mt.ws)
+    assert e.value.status == -1
+    mt.close()
