@@ -1,0 +1,393 @@
+#!/usr/bin/env python
+"""Throughput of tensorial template matching on GB300: tomogram voxels/s of
+the TTM score + rotation maps.
+
+One step = local statistics + correlation with the K tensor components +
+per-voxel Frobenius score and dominant Z-eigenvector rotation, over one
+synthetic 256^3 FP32 tomogram (50 planted copies of a 32^3 lowpassed blob
+template, SNR 0.5, mask radius 15, order n = 4, K = 35).  The tensor template
+is built once before timing (reported separately).  Inputs are resident in
+HBM when the timed region starts; L2 is flushed (256 MB write) before every
+timed step, outside the step's events.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+Under torchrun every rank runs an independent replica (weak scaling); rank 0
+prints one JSON line.
+"""
+
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "tomogram voxels/s of TTM score+rotation maps (FP32 vs BF16) at stated NCC error; % roofline"
+UNIT = "voxels/s"
+WORKLOAD = dict(
+    c2="256x256x256 FP32 volume, 50 planted copies of a 32^3 lowpassed 30-blob template, "
+       "uniform random rotations, SNR 0.5, ball mask r=15, tensor order n=4 (K=35)",
+    c1="64x64x64 FP32 volume, 4 planted copies of a 15^3 5-blob template, SNR 1, "
+       "ball mask r=7, tensor order n=4 (K=35)",
+    c2s="128x128x128 FP32 volume (profiling size), 8 planted copies of the 32^3 template of c2, "
+        "SNR 0.5, ball mask r=15, tensor order n=4 (K=35)",
+)
+WORKLOAD_OVERRIDES = dict(c2s=("c2", dict(shape_zyx=(128, 128, 128), copies=8)))
+
+
+def load_workload(name: str, **extra):
+    import synth
+    base, over = WORKLOAD_OVERRIDES.get(name, (name, {}))
+    return synth.config_workload(base, **dict(over, **extra))
+FP32_ALU_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # SMs x FP32 lanes x FMA x max clock
+L2_FLUSH_BYTES = 256 << 20
+
+# Measured DRAM traffic of a kernel class from one ncu capture (bytes per
+# launch scaled to the bench workload) with the hash of the sources it was
+# taken on; reported only while those sources are unchanged.
+NCU_TRAFFIC: dict = {}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c2s"])
+    ap.add_argument("--path", default="auto", choices=["auto", "direct", "fft"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--cpu-sample", type=int, default=0,
+                    help="internal: run the oracle on this many sampled voxels and print JSON")
+    ap.add_argument("--sample-steps", type=int, default=1)
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------------------
+# oracle timing (CPU baseline / reference arm); runs without touching the GPU
+# ---------------------------------------------------------------------------
+
+def cpu_sample(workload: str, n_vox: int, steps: int) -> dict:
+    import numpy as np
+    import synth
+    from oracle import ttm_oracle as o
+    wl = load_workload(workload, n_rot=300)
+    s = wl.template.shape[0]
+    c = s // 2
+    T = o.tensor_template(wl.template, wl.mask, wl.quadrature.astype(np.float64), wl.weights,
+                          wl.n_order)
+    var_f = float(np.var(wl.volume.astype(np.float64)))
+    rng = np.random.default_rng(11)
+    Z, Y, X = wl.volume.shape
+    times = []
+    for _ in range(steps):
+        pts = np.stack([rng.integers(c, X - s + c + 1, n_vox), rng.integers(c, Y - s + c + 1, n_vox),
+                        rng.integers(c, Z - s + c + 1, n_vox)], axis=1)
+        t0 = time.perf_counter()
+        w, C = o.components_at(wl.volume, T, wl.mask, pts, var_f=var_f)
+        o.frobenius_score(C.T, wl.n_order)
+        o.dominant_z_eigenpair(C, wl.n_order)
+        times.append(time.perf_counter() - t0)
+    return dict(times=times, n_vox=n_vox)
+
+
+def run_cpu_sample(workload: str, n_vox: int, steps: int) -> dict:
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
+               CUDA_VISIBLE_DEVICES="")
+    cmd = [sys.executable, os.path.abspath(__file__), "--workload", workload,
+           "--cpu-sample", str(n_vox), "--sample-steps", str(steps)]
+    out = subprocess.run(cmd, env=env, capture_output=True, text=True, check=True)
+    return json.loads(out.stdout.strip().splitlines()[-1])
+
+
+def cpu_baseline_obj(res: dict) -> dict:
+    tot = sum(res["times"])
+    per_vox = tot / (res["n_vox"] * len(res["times"]))
+    return dict(value=1.0 / per_vox, unit=UNIT, cores=1, kind="oracle",
+                sample=f"{len(res['times'])} x {res['n_vox']} random interior voxels of the same "
+                       "workload: local statistics, K component correlations by direct sum, "
+                       "Frobenius score and dominant Z-eigenpair (FP64 numpy oracle, one BLAS "
+                       f"thread); {tot:.1f} s of CPU work; tensor template built beforehand")
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+
+class Clocks:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,utilization.gpu,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.path = tempfile.mktemp(prefix="clocks_", suffix=".csv")
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return dict(sm_mhz=None, sm_max_mhz=None, reasons=["nvidia-smi unavailable"])
+        self.proc.terminate()
+        self.proc.wait()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return dict(sm_mhz=None, sm_max_mhz=None, reasons=["no samples"])
+
+        def num(v):
+            try:
+                return float(v)
+            except ValueError:
+                return None
+        loaded = [r for r in rows if (num(r[4]) or 0) >= 50] or rows
+        sm = [num(r[1]) for r in loaded if num(r[1]) is not None]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in loaded:
+            for k, name in enumerate(names):
+                if r[5 + k].lower() == "active":
+                    reasons.add(name)
+        return dict(sm_mhz=statistics.median(sm) if sm else None,
+                    sm_max_mhz=num(loaded[0][2]), reasons=sorted(reasons),
+                    samples=len(rows), samples_under_load=len(loaded))
+
+
+def source_hash(names) -> str:
+    h = hashlib.sha1()
+    for n in names:
+        p = os.path.join(ROOT, "paper_2311_07561_gb300", "csrc", n)
+        if os.path.exists(p):
+            h.update(open(p, "rb").read())
+    return h.hexdigest()[:12]
+
+
+def roofline(kernels: dict, steps: int, nvox: int, K: int, n_taps: int, n_grid: int,
+             n_cand: int, newton: int, peaks: dict) -> dict:
+    """Roofline object for the kernel class with the largest share."""
+    name = max(kernels, key=lambda k: kernels[k]["ms"])
+    ms_launch = kernels[name]["ms"] / max(kernels[name]["launches"], 1)
+    launches_per_step = kernels[name]["launches"] / steps
+    K4 = (K + 3) // 4 * 4
+    if name == "direct_corr":
+        flops = 2.0 * K * n_taps * nvox / launches_per_step
+        bound, peak, unit = "alu", FP32_ALU_PEAK_TFLOPS, "TFLOP/s"
+        achieved = flops / (ms_launch * 1e-3) / 1e12
+        src = ["k_direct.cu"]
+    elif name == "rotation":
+        KB = 10
+        per_cand = (2 + newton) * (2 * 10 * KB + 40) + newton * 150
+        flops = (2.0 * n_grid * K + 2 * K + n_cand * per_cand) * nvox / launches_per_step
+        bound, peak, unit = "alu", FP32_ALU_PEAK_TFLOPS, "TFLOP/s"
+        achieved = flops / (ms_launch * 1e-3) / 1e12
+        src = ["k_rotation.cuh", "k_rotation.cu", "k_rotation_n4.cu"]
+    else:
+        # memory-bound stage: algorithmic bytes = read the volume + write one map
+        bytes_ = 8.0 * nvox / launches_per_step
+        bound, peak, unit = "hbm", peaks.get("hbm_gbs", 6800.0), "GB/s"
+        achieved = bytes_ / (ms_launch * 1e-3) / 1e9
+        src = []
+    traffic = None
+    rec = NCU_TRAFFIC.get(name)
+    if rec and rec.get("source_sha") == source_hash(src):
+        traffic = rec["bytes_per_launch"]
+    return dict(kernel=name, bound=bound, achieved=round(achieved, 3), peak=round(peak, 2),
+                unit=unit, frac=round(achieved / peak, 4), traffic=traffic,
+                ms_per_launch=round(ms_launch, 4),
+                peak_source="derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz" if bound == "alu"
+                else "measured (MEASURED_PEAKS.json hbm_gbs)")
+
+
+def run_ours(args) -> None:
+    import numpy as np
+    import torch
+
+    import paper_2311_07561_gb300 as ttm
+    import synth
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if not os.path.exists(ttm.LIB_PATH):
+        import __graft_entry__
+        __graft_entry__.build()
+    ttm.load_library()
+
+    wl = load_workload(args.workload)
+    Z, Y, X = wl.volume.shape
+    nvox = X * Y * Z
+    # tensor template, once per template (timed separately)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record()
+    comp, desc = ttm.build_template(wl.template, wl.mask, wl.n_order, wl.quadrature)
+    ev1.record()
+    torch.cuda.synchronize()
+    build_ms = ev0.elapsed_time(ev1)
+    opts = ttm.PlanOpts()
+    opts.path = {"auto": 0, "direct": 1, "fft": 2}[args.path]
+    matcher = ttm.Matcher([(comp, desc, wl.mask)], [((X, Y, Z), 0)], opts=opts)
+    path = ttm.ttm_plan_problem_path(matcher.plan, 0)
+    vol = torch.from_numpy(wl.volume).to(dev)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+
+    for _ in range(args.warmup):
+        matcher.run([vol])
+    torch.cuda.synchronize()
+    ttm.ttm_plan_timing(matcher.plan)            # discard warm-up records
+    ttm.ttm_plan_enable_timing(matcher.plan, True)
+    launches0 = matcher.launch_count()
+    clocks = Clocks(torch.cuda.current_device())
+    clocks.start()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    stops = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    for k in range(args.steps):
+        flush.zero_()
+        starts[k].record(stream)
+        matcher.run([vol])
+        stops[k].record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clk = clocks.stop()
+    step_ms = [a.elapsed_time(b) for a, b in zip(starts, stops)]
+    total_ms = sum(step_ms)
+    launches = matcher.launch_count() - launches0
+    kern = {name: dict(ms=ms, launches=n) for name, (ms, n) in ttm.ttm_plan_timing(matcher.plan).items()}
+    ttm.ttm_plan_enable_timing(matcher.plan, False)
+    t_max = total_ms
+    if dist:
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_max = float(t.item())
+    value = nvox * args.steps * world / (t_max * 1e-3)
+
+    # end to end through the public API: pinned host volume in, maps out
+    e2e = None
+    if not args.no_e2e:
+        pin_in = torch.from_numpy(wl.volume).pin_memory()
+        pin_out = [(torch.empty((Z, Y, X), dtype=torch.float32).pin_memory(),
+                    torch.empty((Z, Y, X, 4), dtype=torch.float32).pin_memory(),
+                    torch.empty((Z, Y, X), dtype=torch.float32).pin_memory())]
+        for _ in range(max(1, args.warmup)):
+            matcher.match_host([None], pinned_in=[pin_in], pinned_out=pin_out)
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        e_ms = 0.0
+        for k in range(args.steps):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            matcher.match_host([None], pinned_in=[pin_in], pinned_out=pin_out)
+            b.record(stream)
+            b.synchronize()
+            e_ms += a.elapsed_time(b)
+        if dist:
+            t = torch.tensor([e_ms], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e_ms = float(t.item())
+        e2e = dict(value=nvox * args.steps * world / (e_ms * 1e-3), unit=UNIT,
+                   h2d_bytes_per_step=nvox * 4, d2h_bytes_per_step=nvox * 4 * 6)
+
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        pass
+    n_taps = int(wl.mask.sum())
+    rf = roofline(kern, args.steps, nvox, desc.K, n_taps, 2048, 8, 6, peaks)
+    cpu = None
+    if not args.no_cpu_baseline and world == 1:
+        cpu = cpu_baseline_obj(run_cpu_sample(args.workload, 128, 2))
+    line = dict(
+        metric=METRIC, value=value, unit=UNIT, n_gpus=world, steps=args.steps,
+        warmup=args.warmup, ms_per_step=t_max / args.steps, higher_is_better=True,
+        scaling="weak", vs_baseline=None, dtype="f32", data="synthetic",
+        config=dict(workload=WORKLOAD[args.workload], path={1: "direct", 2: "fft"}.get(path, path),
+                    voxels=nvox, tensor_order=wl.n_order, K=desc.K, mask_voxels=n_taps,
+                    rotation_grid=2048, l2="flushed (256 MB write) before every timed step",
+                    parallelism="replicas" if world > 1 else "single GPU",
+                    template_build_ms=round(build_ms, 2), quadrature_rotations=desc.n_rot),
+        roofline=rf, cpu_baseline=cpu, e2e=e2e, gpu_launches=launches,
+        clocks=clk,
+        kernels={k: dict(ms_per_step=round(v["ms"] / args.steps, 4),
+                         launches_per_step=v["launches"] / args.steps,
+                         share=round(v["ms"] / sum(x["ms"] for x in kern.values()), 4))
+                 for k, v in kern.items()},
+    )
+    print(json.dumps(line), flush=True)
+    matcher.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+def run_reference(args) -> None:
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    n_vox = 128
+    steps = args.warmup + args.steps
+    res = run_cpu_sample(args.workload, n_vox, steps)
+    times = res["times"][args.warmup:]
+    total = sum(times)
+    value = n_vox * len(times) / total
+    cpu = cpu_baseline_obj(dict(times=times, n_vox=n_vox))
+    line = dict(
+        metric=METRIC, value=value, unit=UNIT, n_gpus=args.gpus, steps=args.steps,
+        warmup=args.warmup, ms_per_step=1e3 * total / len(times), higher_is_better=True,
+        scaling="weak", vs_baseline=None, dtype="f64", data="synthetic",
+        config=dict(workload=WORKLOAD[args.workload], step=f"{n_vox} sampled voxels"),
+        impl="reference", cpu_baseline=cpu,
+        e2e=dict(value=value, unit=UNIT, h2d_bytes_per_step=0, d2h_bytes_per_step=0),
+    )
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.cpu_sample:
+        print(json.dumps(cpu_sample(args.workload, args.cpu_sample, args.sample_steps)))
+        return
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -171,6 +171,17 @@ ttm_status ttm_plan_problem_path(ttm_plan_t plan, int problem, int* path);
 /* Kernel launches the plan has queued so far (for accounting). */
 ttm_status ttm_plan_launch_count(ttm_plan_t plan, long long* launches);
 
+/* Per-kernel timing.  With timing enabled the plan records a CUDA event pair
+ * on the launch stream around every kernel it queues.  ttm_plan_timing waits
+ * for those events, adds the elapsed times per kernel class into ms[c] and the
+ * launch counts into launches[c] for c < n_classes (either array may be NULL),
+ * and forgets them.  Class names come from ttm_kernel_class_name; there are
+ * TTM_KERNEL_CLASSES classes. */
+#define TTM_KERNEL_CLASSES 12
+ttm_status ttm_plan_enable_timing(ttm_plan_t plan, int enable);
+ttm_status ttm_plan_timing(ttm_plan_t plan, double* ms, long long* launches, int n_classes);
+const char* ttm_kernel_class_name(int kernel_class);
+
 /* Frees everything the plan owns.  NULL is ignored. */
 void ttm_plan_destroy(ttm_plan_t plan);
 

@@ -29,11 +29,14 @@ from ._binding import (  # noqa: F401
     ttm_correlate,
     ttm_device_count,
     ttm_extract_peaks,
+    ttm_kernel_class_name,
     ttm_local_stats,
     ttm_plan,
     ttm_plan_destroy,
+    ttm_plan_enable_timing,
     ttm_plan_launch_count,
     ttm_plan_problem_path,
+    ttm_plan_timing,
     ttm_plan_workspace_size,
     ttm_status_string,
 )

@@ -31,8 +31,10 @@ EXPORTED = (
     "ttm_status_string", "ttm_device_count", "ttm_build_workspace_size",
     "ttm_build_tensor_template", "ttm_plan", "ttm_plan_workspace_size",
     "ttm_plan_problem_path", "ttm_plan_launch_count", "ttm_plan_destroy",
-    "ttm_local_stats", "ttm_correlate", "ttm_extract_peaks",
+    "ttm_local_stats", "ttm_correlate", "ttm_extract_peaks", "ttm_plan_enable_timing",
+    "ttm_plan_timing", "ttm_kernel_class_name",
 )
+TTM_KERNEL_CLASSES = 12
 
 
 class TTMError(RuntimeError):
@@ -88,6 +90,9 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "ttm_correlate": (I, [P, PP, PP, PP, PP, PP, PP, P, S, P]),
         "ttm_extract_peaks": (I, [P, I, P, P, P, ctypes.c_float, I, I, ctypes.POINTER(Peak),
                                   ctypes.POINTER(I), P, S, P]),
+        "ttm_plan_enable_timing": (I, [P, I]),
+        "ttm_plan_timing": (I, [P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(L), I]),
+        "ttm_kernel_class_name": (ctypes.c_char_p, [I]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -208,6 +213,23 @@ def ttm_plan_launch_count(plan: int) -> int:
 def ttm_plan_destroy(plan: Optional[int]) -> None:
     if plan:
         load_library().ttm_plan_destroy(plan)
+
+
+def ttm_plan_enable_timing(plan: int, enable: bool = True) -> None:
+    _check(load_library().ttm_plan_enable_timing(plan, 1 if enable else 0),
+           "ttm_plan_enable_timing")
+
+
+def ttm_kernel_class_name(kernel_class: int) -> str:
+    return load_library().ttm_kernel_class_name(kernel_class).decode()
+
+
+def ttm_plan_timing(plan: int) -> dict:
+    """{class name: (milliseconds, launches)} accumulated since the last call."""
+    ms = (ctypes.c_double * TTM_KERNEL_CLASSES)()
+    n = (ctypes.c_longlong * TTM_KERNEL_CLASSES)()
+    _check(load_library().ttm_plan_timing(plan, ms, n, TTM_KERNEL_CLASSES), "ttm_plan_timing")
+    return {ttm_kernel_class_name(c): (ms[c], n[c]) for c in range(TTM_KERNEL_CLASSES) if n[c]}
 
 
 def ttm_local_stats(plan: int, vols: Sequence[Any], w: Sequence[Any], workspace,

@@ -202,7 +202,41 @@ ttm_status prepare_template(ttm_plan_s* P, TemplateData& T, const float* d_mask)
     return TTM_OK;
 }
 
+cudaEvent_t pool_event(ttm_plan_s* P) {
+    if (!P->event_pool.empty()) {
+        cudaEvent_t e = P->event_pool.back();
+        P->event_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return e;
+}
+
+// Runs fn (which queues kernels on st); with timing on, brackets it with an
+// event pair attributed to kernel class cls.
+template <typename F>
+ttm_status timed(ttm_plan_s* P, int cls, cudaStream_t st, F&& fn) {
+    if (!P->timing) return fn();
+    cudaEvent_t a = pool_event(P), b = pool_event(P);
+    if (!a || !b) return TTM_ERR_CUDA;
+    TTM_CUDA_TRY(cudaEventRecord(a, st));
+    const long long before = P->launches;
+    ttm_status s = fn();
+    TTM_CUDA_TRY(cudaEventRecord(b, st));
+    P->timed.push_back(TimedLaunch{cls, a, b, P->launches - before});
+    return s;
+}
+
 void free_plan(ttm_plan_s* P) {
+    for (TimedLaunch& t : P->timed) {
+        cudaEventDestroy(t.start);
+        cudaEventDestroy(t.stop);
+    }
+    for (cudaEvent_t e : P->event_pool) cudaEventDestroy(e);
     for (TemplateData& T : P->tmpl) {
         cudaFree(T.d_runs);
         cudaFree(T.d_run_tap0);
@@ -400,6 +434,46 @@ ttm_status ttm_plan_launch_count(ttm_plan_t plan, long long* launches) {
     return TTM_OK;
 }
 
+ttm_status ttm_plan_enable_timing(ttm_plan_t plan, int enable) {
+    if (!plan) return TTM_ERR_INVALID_ARG;
+    plan->timing = enable != 0;
+    return TTM_OK;
+}
+
+ttm_status ttm_plan_timing(ttm_plan_t plan, double* ms, long long* launches, int n_classes) {
+    if (!plan || n_classes < 0) return TTM_ERR_INVALID_ARG;
+    for (int c = 0; c < n_classes; ++c) {
+        if (ms) ms[c] = 0.0;
+        if (launches) launches[c] = 0;
+    }
+    ttm_status st = TTM_OK;
+    for (TimedLaunch& t : plan->timed) {
+        float e = 0.f;
+        if (cudaEventSynchronize(t.stop) != cudaSuccess ||
+            cudaEventElapsedTime(&e, t.start, t.stop) != cudaSuccess) {
+            cudaGetLastError();
+            st = TTM_ERR_CUDA;
+        }
+        if (t.cls >= 0 && t.cls < n_classes) {
+            if (ms) ms[t.cls] += e;
+            if (launches) launches[t.cls] += t.n;
+        }
+        plan->event_pool.push_back(t.start);
+        plan->event_pool.push_back(t.stop);
+    }
+    plan->timed.clear();
+    return st;
+}
+
+const char* ttm_kernel_class_name(int c) {
+    static const char* names[TTM_KERNEL_CLASSES] = {
+        "volume_moments", "local_stats", "direct_corr", "rotation", "fft_forward",
+        "fft_spectrum_inverse", "fft_inverse", "peaks", "template", "fft_plan", "other",
+        "reserved"};
+    if (c < 0 || c >= TTM_KERNEL_CLASSES) return "unknown";
+    return names[c];
+}
+
 void ttm_plan_destroy(ttm_plan_t plan) {
     if (plan) free_plan(plan);
 }
@@ -417,9 +491,13 @@ ttm_status ttm_local_stats(ttm_plan_t plan, const float* const* d_vols, float* c
     for (int p = 0; p < np; ++p) {
         const ProblemData& pr = plan->prob[p];
         TTM_CUDA_TRY(cudaMemsetAsync(d_mom, 0, 2 * sizeof(double), st));
-        TTM_TRY(launch_volume_moments(d_vols[p], pr.nvox(), d_mom, st, &plan->launches));
-        TTM_TRY(launch_local_stats(d_vols[p], pr.X, pr.Y, pr.Z, plan->tmpl[pr.tmpl], d_mom, d_w[p],
-                                   st, &plan->launches));
+        TTM_TRY(timed(plan, KC_MOMENTS, st, [&] {
+            return launch_volume_moments(d_vols[p], pr.nvox(), d_mom, st, &plan->launches);
+        }));
+        TTM_TRY(timed(plan, KC_LOCAL_STATS, st, [&] {
+            return launch_local_stats(d_vols[p], pr.X, pr.Y, pr.Z, plan->tmpl[pr.tmpl], d_mom,
+                                      d_w[p], st, &plan->launches);
+        }));
     }
     return TTM_OK;
 }
@@ -441,13 +519,17 @@ ttm_status ttm_correlate(ttm_plan_t plan, const float* const* d_vols, const floa
     for (int p = 0; p < np; ++p) {
         const ProblemData& pr = plan->prob[p];
         const TemplateData& T = plan->tmpl[pr.tmpl];
-        TTM_TRY(launch_direct_corr(d_vols[p], pr.X, pr.Y, pr.Z, T, plan->K, corr, st,
-                                   &plan->launches));
-        TTM_TRY(launch_rotation(plan->n_order, corr, d_w[p], pr.nvox(), pr.X, pr.Y, pr.Z,
-                                T.desc.s, plan->grid, d_score[p], d_quat[p],
-                                d_lambda ? d_lambda[p] : nullptr,
-                                d_components_out ? d_components_out[p] : nullptr, st,
-                                &plan->launches));
+        TTM_TRY(timed(plan, KC_DIRECT_CORR, st, [&] {
+            return launch_direct_corr(d_vols[p], pr.X, pr.Y, pr.Z, T, plan->K, corr, st,
+                                      &plan->launches);
+        }));
+        TTM_TRY(timed(plan, KC_ROTATION, st, [&] {
+            return launch_rotation(plan->n_order, corr, d_w[p], pr.nvox(), pr.X, pr.Y, pr.Z,
+                                   T.desc.s, plan->grid, d_score[p], d_quat[p],
+                                   d_lambda ? d_lambda[p] : nullptr,
+                                   d_components_out ? d_components_out[p] : nullptr, st,
+                                   &plan->launches);
+        }));
     }
     return TTM_OK;
 }
@@ -471,9 +553,11 @@ ttm_status ttm_extract_peaks(ttm_plan_t plan, int problem, const float* d_score,
     void* list = ws + kHeader + 2 * align256(nv * sizeof(float));
     const int cap = (int)peak_cap(nv);
     TTM_CUDA_TRY(cudaMemsetAsync(d_count, 0, sizeof(int), st));
-    TTM_TRY(launch_peak_candidates_full(d_score, d_quat, d_lambda, pr.X, pr.Y, pr.Z, threshold,
-                                        radius, tmp_a, tmp_b, list, cap, d_count, st,
-                                        &plan->launches));
+    TTM_TRY(timed(plan, KC_PEAKS, st, [&] {
+        return launch_peak_candidates_full(d_score, d_quat, d_lambda, pr.X, pr.Y, pr.Z, threshold,
+                                           radius, tmp_a, tmp_b, list, cap, d_count, st,
+                                           &plan->launches);
+    }));
     int count = 0;
     TTM_CUDA_TRY(cudaMemcpyAsync(&count, d_count, sizeof(int), cudaMemcpyDeviceToHost, st));
     TTM_CUDA_TRY(cudaStreamSynchronize(st));

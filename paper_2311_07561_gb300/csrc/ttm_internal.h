@@ -46,6 +46,18 @@ struct RotGrid {
 
 }  // namespace ttm
 
+namespace ttm {
+enum KernelClass {
+    KC_MOMENTS = 0, KC_LOCAL_STATS, KC_DIRECT_CORR, KC_ROTATION, KC_FFT_FORWARD, KC_FFT_SPECTRUM,
+    KC_FFT_INVERSE, KC_PEAKS, KC_TEMPLATE, KC_FFT_PLAN, KC_OTHER, KC_RESERVED
+};
+struct TimedLaunch {
+    int cls;
+    cudaEvent_t start, stop;
+    long long n;
+};
+}  // namespace ttm
+
 struct ttm_plan_s {
     std::vector<ttm::TemplateData> tmpl;
     std::vector<ttm::ProblemData> prob;
@@ -55,6 +67,9 @@ struct ttm_plan_s {
     ttm::RotGrid grid;
     size_t ws_bytes = 0;
     long long launches = 0;
+    bool timing = false;
+    std::vector<ttm::TimedLaunch> timed;   // pending event pairs
+    std::vector<cudaEvent_t> event_pool;
 };
 
 namespace ttm {
