@@ -147,6 +147,34 @@ ttm_status ttm_build_tensor_template(const float* d_template, const float* d_mas
                                      size_t workspace_bytes, ttm_tt_desc* desc, void* stream);
 
 /* ------------------------------------------------------------------------
+ * Tensor-template build that allocates nothing.  The paper has no
+ * counterpart; this entry point is for callers that cannot allocate device
+ * memory: host applications that own every byte of GPU memory through their
+ * own pool or a fixed budget and do not let a library call cudaMalloc, and
+ * pipelines that cannot accept the implicit device synchronisation and
+ * fragmentation of cudaMalloc/cudaFree.  It computes what
+ * ttm_build_tensor_template computes, with the same arguments minus the
+ * workspace: its scratch is one fixed array of TTM_NOALLOC_SCRATCH_BYTES
+ * (8 MiB) inside the library, which every GPU that loads the library holds
+ * until the process exits.  No cudaMalloc, cudaFree or allocating library
+ * routine is called.
+ * Limit: one rotated s^3 float32 copy plus a 256-byte header must fit the
+ * array, so s <= 127; a larger s returns TTM_ERR_WORKSPACE before any work.
+ * The first call on a device looks up the array's device address with
+ * cudaGetSymbolAddress (once per device, with that device current) and
+ * caches it; make that first call before any stream capture.
+ * Every call uses the same array and it keeps the previous call's contents
+ * (the call clears what must start at zero).  Calls that overlap on the GPU
+ * -- on two streams, or from two host threads -- race on the array.
+ * Synchronises the stream.  Errors as for ttm_build_tensor_template.
+ * ---------------------------------------------------------------------- */
+#define TTM_NOALLOC_SCRATCH_BYTES 8388608
+ttm_status ttm_build_tensor_template_noalloc(const float* d_template, const float* d_mask, int s,
+                                             int n_order, const float* d_quats,
+                                             const float* d_weights, int n_rot,
+                                             float* d_components, ttm_tt_desc* desc, void* stream);
+
+/* ------------------------------------------------------------------------
  * Plan.  A plan fixes a batch of problems; problem p matches volume p (size
  * vol_dims[3p..3p+2] = X, Y, Z) against template tmpl_index[p].  Template k
  * is described by descs[k], its components by d_components[k] (K x s^3,

@@ -20,11 +20,13 @@ from ._binding import (  # noqa: F401
     TTM_PATH_FFT,
     TTM_PREC_FP32,
     TTM_PREC_MIXED,
+    TTM_NOALLOC_SCRATCH_BYTES,
     PlanOpts,
     TTDesc,
     TTMError,
     load_library,
     ttm_build_tensor_template,
+    ttm_build_tensor_template_noalloc,
     ttm_build_workspace_size,
     ttm_correlate,
     ttm_device_count,

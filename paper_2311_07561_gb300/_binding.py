@@ -32,8 +32,9 @@ EXPORTED = (
     "ttm_build_tensor_template", "ttm_plan", "ttm_plan_workspace_size",
     "ttm_plan_problem_path", "ttm_plan_launch_count", "ttm_plan_destroy",
     "ttm_local_stats", "ttm_correlate", "ttm_extract_peaks", "ttm_plan_enable_timing",
-    "ttm_plan_timing", "ttm_kernel_class_name",
+    "ttm_plan_timing", "ttm_kernel_class_name", "ttm_build_tensor_template_noalloc",
 )
+TTM_NOALLOC_SCRATCH_BYTES = 8388608
 TTM_KERNEL_CLASSES = 12
 
 
@@ -93,6 +94,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "ttm_plan_enable_timing": (I, [P, I]),
         "ttm_plan_timing": (I, [P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(L), I]),
         "ttm_kernel_class_name": (ctypes.c_char_p, [I]),
+        "ttm_build_tensor_template_noalloc": (I, [P, P, I, I, P, P, I, P,
+                                                  ctypes.POINTER(TTDesc), P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -170,6 +173,18 @@ def ttm_build_tensor_template(template, mask, s: int, n_order: int, quats, weigh
         _ptr(components), _ptr(workspace), _nbytes(workspace) if workspace is not None else 0,
         ctypes.byref(desc), _stream(stream))
     _check(st, "ttm_build_tensor_template")
+    return desc
+
+
+def ttm_build_tensor_template_noalloc(template, mask, s: int, n_order: int, quats, weights,
+                                      n_rot: int, components, stream=None) -> TTDesc:
+    """Same result as ttm_build_tensor_template without any workspace: the
+    library's fixed scratch array is used (for callers that cannot allocate)."""
+    desc = TTDesc()
+    st = load_library().ttm_build_tensor_template_noalloc(
+        _ptr(template), _ptr(mask), s, n_order, _ptr(quats), _ptr(weights), n_rot,
+        _ptr(components), ctypes.byref(desc), _stream(stream))
+    _check(st, "ttm_build_tensor_template_noalloc")
     return desc
 
 
