@@ -1,0 +1,374 @@
+// Batched 3D FFTs for the correlation with the K tensor components (Sec. 2 of
+// the paper: <f, g> = F^-1(F f . conj F g)(0); Algorithm 1 uses it for every
+// rotation, TTM for every component, Sec. 3.2).
+//
+// Layouts.  A real volume is [Zp][Yp][Xp] (padded sizes, zero beyond the
+// data); its half spectrum is [Zp][Yp][Xh] complex64 with Xh = Xp/2 + 1.
+//
+// Every pass moves a tile of whole 1D lines into shared memory, transforms
+// them there with Stockham autosort stages (radix 4, one radix-2 stage when
+// the length needs it; two shared-memory buffers ping-pong between stages),
+// and writes the tile back, so each pass reads and writes HBM once:
+//   rows_r2c      x lines of the real volume -> half-spectrum rows
+//   cols          y or z lines of a half spectrum (strided), in place
+//   cols_mul      z lines of the image spectrum times conj(template spectrum)
+//                 for all K components: the image tile is read once and kept
+//                 in shared memory while the K component tiles stream through
+//   rows_c2r      half-spectrum rows -> real x lines (Hermitian extension)
+// Twiddles exp(-2 pi i k / L) come from a table computed on the host in FP64.
+#include "ttm_internal.h"
+
+namespace ttm {
+
+namespace {
+
+constexpr int kFftThreads = 256;
+constexpr int kTileElems = 4096;   // complex elements per shared-memory buffer
+
+struct Radices {
+    int n;          // number of stages
+    int r[16];      // radix of each stage (4 or 2), in order
+};
+
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+    return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ float2 cmulc(float2 a, float2 b) {   // a * conj(b)
+    return make_float2(a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y);
+}
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+
+// NB independent transforms of length L stored as buf[i * pitch + b].  The
+// result ends in *out (one of a, b).  sign = -1 forward, +1 inverse.
+__device__ void fft_lines(float2* a, float2* b, float2** out, int L, int NB, int pitch,
+                          const Radices& rd, const float2* __restrict__ tw, int sign) {
+    float2* src = a;
+    float2* dst = b;
+    int Ns = 1;
+    for (int st = 0; st < rd.n; ++st) {
+        const int R = rd.r[st];
+        const int nbf = L / R;                    // butterflies per line
+        const int stride_tw = L / (Ns * R);
+        for (int idx = threadIdx.x; idx < nbf * NB; idx += blockDim.x) {
+            const int line = idx % NB;
+            const int j = idx / NB;
+            const int jm = j % Ns;
+            const int idxD = (j / Ns) * Ns * R + jm;
+            if (R == 4) {
+                float2 v[4];
+#pragma unroll
+                for (int r = 0; r < 4; ++r) {
+                    float2 x = src[(j + r * nbf) * pitch + line];
+                    if (r) {
+                        float2 w = __ldg(tw + jm * r * stride_tw);
+                        w.y *= (float)(-sign);      // forward: table value, inverse: conjugate
+                        x = cmul(x, w);
+                    }
+                    v[r] = x;
+                }
+                float2 s02 = cadd(v[0], v[2]), d02 = csub(v[0], v[2]);
+                float2 s13 = cadd(v[1], v[3]), d13 = csub(v[1], v[3]);
+                // d = -i*d13 (forward) or +i*d13 (inverse)
+                float2 d = sign < 0 ? make_float2(d13.y, -d13.x) : make_float2(-d13.y, d13.x);
+                dst[(idxD + 0 * Ns) * pitch + line] = cadd(s02, s13);
+                dst[(idxD + 1 * Ns) * pitch + line] = cadd(d02, d);
+                dst[(idxD + 2 * Ns) * pitch + line] = csub(s02, s13);
+                dst[(idxD + 3 * Ns) * pitch + line] = csub(d02, d);
+            } else {  // R == 2
+                float2 x0 = src[j * pitch + line];
+                float2 x1 = src[(j + nbf) * pitch + line];
+                float2 w = __ldg(tw + jm * stride_tw);
+                w.y *= (float)(-sign);
+                x1 = cmul(x1, w);
+                dst[(idxD) * pitch + line] = cadd(x0, x1);
+                dst[(idxD + Ns) * pitch + line] = csub(x0, x1);
+            }
+        }
+        __syncthreads();
+        float2* t = src; src = dst; dst = t;
+        Ns *= R;
+    }
+    *out = src;
+}
+
+struct FftGeom {
+    int Xp, Yp, Zp, Xh;
+};
+
+// ---- rows: real x lines -> half-spectrum rows --------------------------
+// The source volume has X, Y, Z <= Xp, Yp, Zp; lines and samples beyond the
+// data are zero.  Rows are (y, z) pairs of the padded volume.
+__global__ void __launch_bounds__(kFftThreads) rows_r2c_kernel(
+    const float* __restrict__ f, int X, int Y, int Z, FftGeom g, float2* __restrict__ out,
+    Radices rd, const float2* __restrict__ tw, int NB) {
+    extern __shared__ float2 sm[];
+    const int pitch = NB + 1;
+    float2* A = sm;
+    float2* B = sm + g.Xp * pitch;
+    const int row0 = blockIdx.x * NB;
+    const int nrows = g.Yp * g.Zp;
+    for (int e = threadIdx.x; e < NB * g.Xp; e += blockDim.x) {
+        const int r = e / g.Xp, x = e % g.Xp;
+        const int row = row0 + r;
+        float v = 0.f;
+        if (row < nrows) {
+            const int y = row % g.Yp, z = row / g.Yp;
+            if (x < X && y < Y && z < Z) v = __ldg(f + ((size_t)z * Y + y) * X + x);
+        }
+        A[x * pitch + r] = make_float2(v, 0.f);
+    }
+    __syncthreads();
+    float2* res;
+    fft_lines(A, B, &res, g.Xp, NB, pitch, rd, tw, -1);
+    for (int e = threadIdx.x; e < NB * g.Xh; e += blockDim.x) {
+        const int r = e / g.Xh, k = e % g.Xh;
+        const int row = row0 + r;
+        if (row < nrows) out[(size_t)row * g.Xh + k] = res[k * pitch + r];
+    }
+}
+
+// ---- columns: lines of length L with element stride B, batch A ----------
+// data[(a * L + l) * B + b]; CTA = (b tile of TB, a).
+__global__ void __launch_bounds__(kFftThreads) cols_kernel(float2* __restrict__ data, int L,
+                                                           int B, Radices rd,
+                                                           const float2* __restrict__ tw, int TB,
+                                                           int sign) {
+    extern __shared__ float2 sm[];
+    float2* P = sm;
+    float2* Q = sm + L * TB;
+    const int b0 = blockIdx.x * TB;
+    const size_t base = (size_t)blockIdx.y * L * B;
+    const int tb = min(TB, B - b0);
+    for (int e = threadIdx.x; e < L * TB; e += blockDim.x) {
+        const int l = e / TB, bb = e % TB;
+        P[e] = bb < tb ? data[base + (size_t)l * B + b0 + bb] : make_float2(0.f, 0.f);
+    }
+    __syncthreads();
+    float2* res;
+    fft_lines(P, Q, &res, L, TB, TB, rd, tw, sign);
+    for (int e = threadIdx.x; e < L * TB; e += blockDim.x) {
+        const int l = e / TB, bb = e % TB;
+        if (bb < tb) data[base + (size_t)l * B + b0 + bb] = res[e];
+    }
+}
+
+// ---- z lines of F(f) * conj(T^_k) for every component k, inverse -------
+// spec: image spectrum [Zp][Yp*Xh]; tspec: K template spectra (same shape,
+// already scaled by 1/N); out: K products after the inverse z transform.
+__global__ void __launch_bounds__(kFftThreads) cols_mul_kernel(
+    const float2* __restrict__ spec, const float2* __restrict__ tspec, float2* __restrict__ out,
+    int L, int B, int K, Radices rd, const float2* __restrict__ tw, int TB) {
+    extern __shared__ float2 sm[];
+    float2* Fimg = sm;
+    float2* P = sm + L * TB;
+    float2* Q = sm + 2 * L * TB;
+    const int b0 = blockIdx.x * TB;
+    const int tb = min(TB, B - b0);
+    const size_t plane = (size_t)L * B;
+    for (int e = threadIdx.x; e < L * TB; e += blockDim.x) {
+        const int l = e / TB, bb = e % TB;
+        Fimg[e] = bb < tb ? spec[(size_t)l * B + b0 + bb] : make_float2(0.f, 0.f);
+    }
+    for (int k = 0; k < K; ++k) {
+        __syncthreads();
+        const float2* ts = tspec + (size_t)k * plane;
+        for (int e = threadIdx.x; e < L * TB; e += blockDim.x) {
+            const int l = e / TB, bb = e % TB;
+            float2 t = bb < tb ? __ldg(ts + (size_t)l * B + b0 + bb) : make_float2(0.f, 0.f);
+            P[e] = cmulc(Fimg[e], t);
+        }
+        __syncthreads();
+        float2* res;
+        fft_lines(P, Q, &res, L, TB, TB, rd, tw, +1);
+        float2* o = out + (size_t)k * plane;
+        for (int e = threadIdx.x; e < L * TB; e += blockDim.x) {
+            const int l = e / TB, bb = e % TB;
+            if (bb < tb) o[(size_t)l * B + b0 + bb] = res[e];
+        }
+    }
+}
+
+// ---- half-spectrum rows -> real x lines (inverse) ------------------------
+// in: batch of nb_planes * Yp rows of Xh complex; writes the X x Y x Z data
+// region of every plane into out (batch-major, X*Y*Z floats per batch item).
+__global__ void __launch_bounds__(kFftThreads) rows_c2r_kernel(
+    const float2* __restrict__ in, int X, int Y, int Z, FftGeom g, float* __restrict__ out,
+    int n_batch, Radices rd, const float2* __restrict__ tw, int NB) {
+    extern __shared__ float2 sm[];
+    const int pitch = NB + 1;
+    float2* A = sm;
+    float2* Bf = sm + g.Xp * pitch;
+    const size_t rows_per_item = (size_t)g.Yp * g.Zp;
+    const size_t nrows = rows_per_item * n_batch;
+    const size_t row0 = (size_t)blockIdx.x * NB;
+    for (int e = threadIdx.x; e < NB * g.Xp; e += blockDim.x) {
+        const int r = e / g.Xp, x = e % g.Xp;
+        const size_t row = row0 + r;
+        float2 v = make_float2(0.f, 0.f);
+        if (row < nrows) {
+            const float2* src = in + row * g.Xh;
+            if (x < g.Xh) v = src[x];
+            else { float2 c = src[g.Xp - x]; v = make_float2(c.x, -c.y); }
+        }
+        A[x * pitch + r] = v;
+    }
+    __syncthreads();
+    float2* res;
+    fft_lines(A, Bf, &res, g.Xp, NB, pitch, rd, tw, +1);
+    const size_t vox = (size_t)X * Y * Z;
+    for (int e = threadIdx.x; e < NB * g.Xp; e += blockDim.x) {
+        const int r = e / g.Xp, x = e % g.Xp;
+        const size_t row = row0 + r;
+        if (row >= nrows || x >= X) continue;
+        const size_t item = row / rows_per_item;
+        const int rr = (int)(row % rows_per_item);
+        const int y = rr % g.Yp, z = rr / g.Yp;
+        if (y < Y && z < Z) out[item * vox + ((size_t)z * Y + y) * X + x] = res[x * pitch + r].x;
+    }
+}
+
+// place a component box into a zeroed padded volume at (u - c) mod N
+__global__ void scatter_component_kernel(const float* __restrict__ comp, int s, FftGeom g,
+                                         float* __restrict__ pad) {
+    const int s3 = s * s * s;
+    const int u = blockIdx.x * blockDim.x + threadIdx.x;
+    if (u >= s3) return;
+    const int c = s / 2;
+    const int ux = u % s, uy = (u / s) % s, uz = u / (s * s);
+    const int x = ((ux - c) % g.Xp + g.Xp) % g.Xp;
+    const int y = ((uy - c) % g.Yp + g.Yp) % g.Yp;
+    const int z = ((uz - c) % g.Zp + g.Zp) % g.Zp;
+    pad[((size_t)z * g.Yp + y) * g.Xp + x] = comp[u];
+}
+
+__global__ void scale_kernel(float2* __restrict__ a, size_t n, float s) {
+    size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) { a[i].x *= s; a[i].y *= s; }
+}
+
+Radices radices_for(int L) {
+    Radices rd{};
+    int n = L;
+    while (n % 4 == 0 && n > 1) { rd.r[rd.n++] = 4; n /= 4; }
+    while (n % 2 == 0 && n > 1) { rd.r[rd.n++] = 2; n /= 2; }
+    return rd;
+}
+
+int rows_per_cta(int L) {
+    int nb = kTileElems / L;
+    if (nb > 16) nb = 16;
+    if (nb < 1) nb = 1;
+    return nb;
+}
+
+int cols_per_cta(int L) {
+    int tb = kTileElems / L;
+    if (tb > 32) tb = 32;
+    if (tb < 1) tb = 1;
+    return tb;
+}
+
+}  // namespace
+
+bool fft_length_ok(int L) { return L >= 2 && L <= 4096 && (L & (L - 1)) == 0; }
+
+int fft_good_length(int n) {
+    int L = 2;
+    while (L < n) L <<= 1;
+    return L;
+}
+
+ttm_status launch_fft_forward(const float* f, int X, int Y, int Z, const FftShape& S,
+                              float2* spec, cudaStream_t st, long long* cnt) {
+    FftGeom g{S.Xp, S.Yp, S.Zp, S.Xp / 2 + 1};
+    {
+        const int NB = rows_per_cta(S.Xp);
+        const size_t smem = (size_t)2 * S.Xp * (NB + 1) * sizeof(float2);
+        TTM_CUDA_TRY(cudaFuncSetAttribute(rows_r2c_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        const int nrows = S.Yp * S.Zp;
+        rows_r2c_kernel<<<(nrows + NB - 1) / NB, kFftThreads, smem, st>>>(
+            f, X, Y, Z, g, spec, radices_for(S.Xp), S.d_tw_x, NB);
+        TTM_TRY(after_launch(cnt));
+    }
+    {   // y lines: batch Zp, length Yp, stride Xh
+        const int TB = cols_per_cta(S.Yp);
+        const size_t smem = (size_t)2 * S.Yp * TB * sizeof(float2);
+        TTM_CUDA_TRY(cudaFuncSetAttribute(cols_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        dim3 grid((g.Xh + TB - 1) / TB, S.Zp);   // Zp <= 4096
+        cols_kernel<<<grid, kFftThreads, smem, st>>>(spec, S.Yp, g.Xh, radices_for(S.Yp), S.d_tw_y, TB, -1);
+        TTM_TRY(after_launch(cnt));
+    }
+    {   // z lines: batch 1, length Zp, stride Yp*Xh
+        const int TB = cols_per_cta(S.Zp);
+        const size_t smem = (size_t)2 * S.Zp * TB * sizeof(float2);
+        const int Bz = S.Yp * g.Xh;
+        TTM_CUDA_TRY(cudaFuncSetAttribute(cols_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        dim3 grid((Bz + TB - 1) / TB, 1);
+        cols_kernel<<<grid, kFftThreads, smem, st>>>(spec, S.Zp, Bz, radices_for(S.Zp), S.d_tw_z, TB, -1);
+        TTM_TRY(after_launch(cnt));
+    }
+    return TTM_OK;
+}
+
+ttm_status launch_fft_spectrum_inverse_z(const float2* spec, const float2* tspec, int K,
+                                         const FftShape& S, float2* prod, cudaStream_t st,
+                                         long long* cnt) {
+    const int Xh = S.Xp / 2 + 1;
+    const int TB = cols_per_cta(S.Zp);
+    const size_t smem = (size_t)3 * S.Zp * TB * sizeof(float2);
+    TTM_CUDA_TRY(cudaFuncSetAttribute(cols_mul_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    const int Bz = S.Yp * Xh;
+    dim3 grid((Bz + TB - 1) / TB, 1);
+    cols_mul_kernel<<<grid, kFftThreads, smem, st>>>(spec, tspec, prod, S.Zp, Bz, K,
+                                                     radices_for(S.Zp), S.d_tw_z, TB);
+    return after_launch(cnt);
+}
+
+ttm_status launch_fft_inverse_yx(float2* prod, int K, int X, int Y, int Z, const FftShape& S,
+                                 float* corr, cudaStream_t st, long long* cnt) {
+    FftGeom g{S.Xp, S.Yp, S.Zp, S.Xp / 2 + 1};
+    {   // y lines of every component: batch K*Zp, length Yp, stride Xh
+        const int TB = cols_per_cta(S.Yp);
+        const size_t smem = (size_t)2 * S.Yp * TB * sizeof(float2);
+        TTM_CUDA_TRY(cudaFuncSetAttribute(cols_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        const int batch = K * S.Zp;
+        for (int a0 = 0; a0 < batch; a0 += 65535) {
+            const int na = batch - a0 < 65535 ? batch - a0 : 65535;
+            dim3 grid((g.Xh + TB - 1) / TB, na);
+            cols_kernel<<<grid, kFftThreads, smem, st>>>(prod + (size_t)a0 * S.Yp * g.Xh, S.Yp, g.Xh,
+                                                         radices_for(S.Yp), S.d_tw_y, TB, +1);
+            TTM_TRY(after_launch(cnt));
+        }
+    }
+    {
+        const int NB = rows_per_cta(S.Xp);
+        const size_t smem = (size_t)2 * S.Xp * (NB + 1) * sizeof(float2);
+        TTM_CUDA_TRY(cudaFuncSetAttribute(rows_c2r_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        const size_t nrows = (size_t)S.Yp * S.Zp * K;
+        rows_c2r_kernel<<<(unsigned)((nrows + NB - 1) / NB), kFftThreads, smem, st>>>(
+            prod, X, Y, Z, g, corr, K, radices_for(S.Xp), S.d_tw_x, NB);
+        TTM_TRY(after_launch(cnt));
+    }
+    return TTM_OK;
+}
+
+ttm_status launch_template_spectra(const float* comp, int K, int s, const FftShape& S,
+                                   float* pad, float2* tspec, cudaStream_t st, long long* cnt) {
+    FftGeom g{S.Xp, S.Yp, S.Zp, S.Xp / 2 + 1};
+    const size_t nreal = (size_t)S.Xp * S.Yp * S.Zp;
+    const size_t nspec = (size_t)g.Xh * S.Yp * S.Zp;
+    const int s3 = s * s * s;
+    for (int k = 0; k < K; ++k) {
+        TTM_CUDA_TRY(cudaMemsetAsync(pad, 0, nreal * sizeof(float), st));
+        scatter_component_kernel<<<(s3 + 255) / 256, 256, 0, st>>>(comp + (size_t)k * s3, s, g, pad);
+        TTM_TRY(after_launch(cnt));
+        float2* dst = tspec + (size_t)k * nspec;
+        TTM_TRY(launch_fft_forward(pad, S.Xp, S.Yp, S.Zp, S, dst, st, cnt));
+        scale_kernel<<<(unsigned)((nspec + 255) / 256), 256, 0, st>>>(dst, nspec, 1.0f / (float)nreal);
+        TTM_TRY(after_launch(cnt));
+    }
+    return TTM_OK;
+}
+
+}  // namespace ttm

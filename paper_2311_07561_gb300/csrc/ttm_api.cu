@@ -202,6 +202,72 @@ ttm_status prepare_template(ttm_plan_s* P, TemplateData& T, const float* d_mask)
     return TTM_OK;
 }
 
+const float2* twiddle_table(ttm_plan_s* P, int L, ttm_status* err) {
+    for (auto& t : P->twiddles)
+        if (t.first == L) return t.second;
+    std::vector<float2> h(L);
+    const double two_pi = 6.283185307179586476925287;
+    for (int k = 0; k < L; ++k) {
+        double a = -two_pi * (double)k / (double)L;
+        h[k] = make_float2((float)std::cos(a), (float)std::sin(a));
+    }
+    float2* d = nullptr;
+    *err = dev_upload(&d, h);
+    if (*err != TTM_OK) return nullptr;
+    P->twiddles.push_back({L, d});
+    return d;
+}
+
+// Bytes per voxel each path moves or computes, for the automatic choice.
+bool prefer_fft(const ttm_plan_s* P, const ProblemData& pr, const TemplateData& T) {
+    const double pad = (double)pr.fft.Xp * pr.fft.Yp * pr.fft.Zp / (double)pr.nvox();
+    const double fft_ns = pad * (40.0 * P->K + 40.0) / 5000.0;        // ~5 TB/s effective
+    const double direct_ns = 2.0 * P->K * T.n_taps / 30000.0;         // ~30 TFLOP/s FP32
+    return fft_ns < direct_ns;
+}
+
+ttm_status prepare_fft(ttm_plan_s* P, ProblemData& pr, cudaStream_t st) {
+    ttm_status err = TTM_OK;
+    pr.fft.Xp = fft_good_length(pr.X);
+    pr.fft.Yp = fft_good_length(pr.Y);
+    pr.fft.Zp = fft_good_length(pr.Z);
+    if (!fft_length_ok(pr.fft.Xp) || !fft_length_ok(pr.fft.Yp) || !fft_length_ok(pr.fft.Zp))
+        return TTM_ERR_UNSUPPORTED;
+    pr.fft.d_tw_x = twiddle_table(P, pr.fft.Xp, &err); TTM_TRY(err);
+    pr.fft.d_tw_y = twiddle_table(P, pr.fft.Yp, &err); TTM_TRY(err);
+    pr.fft.d_tw_z = twiddle_table(P, pr.fft.Zp, &err); TTM_TRY(err);
+    for (size_t i = 0; i < P->specs.size(); ++i) {
+        const SpecSet& sp = P->specs[i];
+        if (sp.tmpl == pr.tmpl && sp.Xp == pr.fft.Xp && sp.Yp == pr.fft.Yp && sp.Zp == pr.fft.Zp) {
+            pr.spec_index = (int)i;
+            return TTM_OK;
+        }
+    }
+    const TemplateData& T = P->tmpl[pr.tmpl];
+    SpecSet sp;
+    sp.tmpl = pr.tmpl; sp.Xp = pr.fft.Xp; sp.Yp = pr.fft.Yp; sp.Zp = pr.fft.Zp;
+    const size_t nspec = pr.fft.nspec();
+    const size_t nreal = (size_t)pr.fft.Xp * pr.fft.Yp * pr.fft.Zp;
+    if (cudaMalloc((void**)&sp.d_spec, (size_t)P->K * nspec * sizeof(float2)) != cudaSuccess) {
+        cudaGetLastError();
+        return TTM_ERR_OUT_OF_MEMORY;
+    }
+    P->specs.push_back(sp);
+    pr.spec_index = (int)P->specs.size() - 1;
+    float* pad = nullptr;
+    if (cudaMalloc((void**)&pad, nreal * sizeof(float)) != cudaSuccess) {
+        cudaGetLastError();
+        return TTM_ERR_OUT_OF_MEMORY;
+    }
+    ttm_status s = launch_template_spectra(T.d_comp, P->K, T.desc.s, pr.fft, pad, sp.d_spec, st,
+                                           &P->launches);
+    cudaError_t e = cudaStreamSynchronize(st);
+    cudaFree(pad);
+    if (s != TTM_OK) return s;
+    if (e != cudaSuccess) { cudaGetLastError(); return TTM_ERR_CUDA; }
+    return TTM_OK;
+}
+
 cudaEvent_t pool_event(ttm_plan_s* P) {
     if (!P->event_pool.empty()) {
         cudaEvent_t e = P->event_pool.back();
@@ -244,6 +310,8 @@ void free_plan(ttm_plan_s* P) {
         cudaFree(T.d_taps);
         cudaFree(T.d_spec);
     }
+    for (SpecSet& sp : P->specs) cudaFree(sp.d_spec);
+    for (auto& t : P->twiddles) cudaFree(t.second);
     cudaFree(P->grid.d_q);
     cudaFree(P->grid.d_m);
     cudaFree(P->grid.d_cell_end);
@@ -256,9 +324,14 @@ constexpr int kPeakCapMax = 1 << 22;
 
 size_t peak_cap(size_t nvox) { return std::min(nvox, (size_t)kPeakCapMax); }
 
+// Correlation maps first (both paths), then for the FFT path the image
+// spectrum and the K product spectra.
 size_t scratch_bytes(const ttm_plan_s* P, const ProblemData& pr) {
     const size_t nv = pr.nvox();
     size_t corr = align256((size_t)P->K * nv * sizeof(float));
+    if (pr.path == TTM_PATH_FFT)
+        corr += align256(pr.fft.nspec() * sizeof(float2)) +
+                align256((size_t)P->K * pr.fft.nspec() * sizeof(float2));
     size_t peaks = 2 * align256(nv * sizeof(float)) + align256(peak_cap(nv) * peak_record_bytes());
     return std::max(corr, peaks);
 }
@@ -407,7 +480,21 @@ ttm_status ttm_plan(ttm_plan_t* out, int n_problems, const int* vol_dims, const 
         ProblemData& pr = P->prob[p];
         pr.X = vol_dims[3 * p]; pr.Y = vol_dims[3 * p + 1]; pr.Z = vol_dims[3 * p + 2];
         pr.tmpl = tmpl_index[p];
-        pr.path = TTM_PATH_DIRECT;
+        const TemplateData& T = P->tmpl[pr.tmpl];
+        pr.fft.Xp = fft_good_length(pr.X);
+        pr.fft.Yp = fft_good_length(pr.Y);
+        pr.fft.Zp = fft_good_length(pr.Z);
+        const bool fft_ok = fft_length_ok(pr.fft.Xp) && fft_length_ok(pr.fft.Yp) &&
+                            fft_length_ok(pr.fft.Zp);
+        int path = P->opts.path;
+        if (path == TTM_PATH_AUTO) path = (fft_ok && prefer_fft(P, pr, T)) ? TTM_PATH_FFT : TTM_PATH_DIRECT;
+        if (path == TTM_PATH_FFT && !fft_ok) { free_plan(P); return TTM_ERR_UNSUPPORTED; }
+        if (path != TTM_PATH_FFT && path != TTM_PATH_DIRECT) { free_plan(P); return TTM_ERR_INVALID_ARG; }
+        pr.path = path;
+        if (path == TTM_PATH_FFT) {
+            s_ = prepare_fft(P, pr, st);
+            if (s_ != TTM_OK) { free_plan(P); return s_; }
+        }
         ws = std::max(ws, scratch_bytes(P, pr));
     }
     P->ws_bytes = kHeader + ws;
@@ -519,10 +606,29 @@ ttm_status ttm_correlate(ttm_plan_t plan, const float* const* d_vols, const floa
     for (int p = 0; p < np; ++p) {
         const ProblemData& pr = plan->prob[p];
         const TemplateData& T = plan->tmpl[pr.tmpl];
-        TTM_TRY(timed(plan, KC_DIRECT_CORR, st, [&] {
-            return launch_direct_corr(d_vols[p], pr.X, pr.Y, pr.Z, T, plan->K, corr, st,
-                                      &plan->launches);
-        }));
+        if (pr.path == TTM_PATH_FFT) {
+            char* base = (char*)corr + align256((size_t)plan->K * pr.nvox() * sizeof(float));
+            float2* spec = (float2*)base;
+            float2* prod = (float2*)(base + align256(pr.fft.nspec() * sizeof(float2)));
+            const float2* tspec = plan->specs[pr.spec_index].d_spec;
+            TTM_TRY(timed(plan, KC_FFT_FORWARD, st, [&] {
+                return launch_fft_forward(d_vols[p], pr.X, pr.Y, pr.Z, pr.fft, spec, st,
+                                          &plan->launches);
+            }));
+            TTM_TRY(timed(plan, KC_FFT_SPECTRUM, st, [&] {
+                return launch_fft_spectrum_inverse_z(spec, tspec, plan->K, pr.fft, prod, st,
+                                                     &plan->launches);
+            }));
+            TTM_TRY(timed(plan, KC_FFT_INVERSE, st, [&] {
+                return launch_fft_inverse_yx(prod, plan->K, pr.X, pr.Y, pr.Z, pr.fft, corr, st,
+                                             &plan->launches);
+            }));
+        } else {
+            TTM_TRY(timed(plan, KC_DIRECT_CORR, st, [&] {
+                return launch_direct_corr(d_vols[p], pr.X, pr.Y, pr.Z, T, plan->K, corr, st,
+                                          &plan->launches);
+            }));
+        }
         TTM_TRY(timed(plan, KC_ROTATION, st, [&] {
             return launch_rotation(plan->n_order, corr, d_w[p], pr.nvox(), pr.X, pr.Y, pr.Z,
                                    T.desc.s, plan->grid, d_score[p], d_quat[p],

@@ -29,11 +29,28 @@ struct TemplateData {
     int spec_shape[3] = {0, 0, 0};
 };
 
+// Padded FFT box of a problem and its twiddle tables (plan-owned).
+struct FftShape {
+    int Xp = 0, Yp = 0, Zp = 0;
+    const float2* d_tw_x = nullptr;   // exp(-2 pi i k / Xp), k < Xp
+    const float2* d_tw_y = nullptr;
+    const float2* d_tw_z = nullptr;
+    size_t nspec() const { return (size_t)(Xp / 2 + 1) * Yp * Zp; }
+};
+
 struct ProblemData {
     int X = 0, Y = 0, Z = 0;
     int tmpl = 0;
     int path = TTM_PATH_DIRECT;
+    FftShape fft;
+    int spec_index = -1;               // template spectra set used (FFT path)
     size_t nvox() const { return (size_t)X * Y * Z; }
+};
+
+// Template spectra for one (template, FFT box): K half spectra, scaled by 1/N.
+struct SpecSet {
+    int tmpl = 0, Xp = 0, Yp = 0, Zp = 0;
+    float2* d_spec = nullptr;
 };
 
 // Rotation search grid (device tables owned by the plan).
@@ -65,6 +82,8 @@ struct ttm_plan_s {
     int n_order = 4;
     int K = 35;
     ttm::RotGrid grid;
+    std::vector<ttm::SpecSet> specs;
+    std::vector<std::pair<int, float2*>> twiddles;   // length -> device table
     size_t ws_bytes = 0;
     long long launches = 0;
     bool timing = false;
@@ -104,6 +123,19 @@ ttm_status launch_mask_sum(const float* m, int s, double* d_out, cudaStream_t st
 ttm_status launch_fold_components(int n_order, const float* quats, const float* weights,
                                   int n_rot_total, int j0, int nj, const float* rot, int s3,
                                   float* comp, bool first, cudaStream_t st, long long* cnt);
+
+// FFT path
+bool fft_length_ok(int L);
+int fft_good_length(int n);
+ttm_status launch_fft_forward(const float* f, int X, int Y, int Z, const FftShape& S,
+                              float2* spec, cudaStream_t st, long long* cnt);
+ttm_status launch_fft_spectrum_inverse_z(const float2* spec, const float2* tspec, int K,
+                                         const FftShape& S, float2* prod, cudaStream_t st,
+                                         long long* cnt);
+ttm_status launch_fft_inverse_yx(float2* prod, int K, int X, int Y, int Z, const FftShape& S,
+                                 float* corr, cudaStream_t st, long long* cnt);
+ttm_status launch_template_spectra(const float* comp, int K, int s, const FftShape& S,
+                                   float* pad, float2* tspec, cudaStream_t st, long long* cnt);
 
 // peaks
 size_t peak_record_bytes();

@@ -35,6 +35,15 @@ def _cuda(a):
     return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).cuda()
 
 
+PATHS = ["direct", "fft"]
+
+
+def _opts(ttm, path):
+    o_ = ttm.PlanOpts()
+    o_.path = {"direct": ttm.TTM_PATH_DIRECT, "fft": ttm.TTM_PATH_FFT}[path]
+    return o_
+
+
 def _run(ttm, wl, comp, desc, opts=None, want_comp=True):
     import torch
     X = wl.volume.shape[2]; Y = wl.volume.shape[1]; Z = wl.volume.shape[0]
@@ -50,14 +59,22 @@ def _run(ttm, wl, comp, desc, opts=None, want_comp=True):
 
 
 @pytest.fixture(scope="module")
-def c1(ttm):
+def c1_oracle(ttm):
     """Config-1 shape: 64^3, 15^3 template (5 blobs), r = 7, 4 copies, SNR 1, n = 4."""
     wl = synth.config_workload("c1", n_rot=1000)
     T = o.tensor_template(wl.template, wl.mask, wl.quadrature.astype(np.float64), wl.weights, 4)
     comp, desc = ttm.build_template(wl.template, wl.mask, 4, wl.quadrature)
-    res = _run(ttm, wl, comp, desc)
     w_o, C_o = o.ttm_components(wl.volume, T, wl.mask)
-    return dict(wl=wl, T=T, comp=comp, desc=desc, res=res, w_o=w_o, C_o=C_o)
+    return dict(wl=wl, T=T, comp=comp, desc=desc, w_o=w_o, C_o=C_o)
+
+
+@pytest.fixture(scope="module", params=PATHS)
+def c1(ttm, c1_oracle, request):
+    d = dict(c1_oracle)
+    d["res"] = _run(ttm, d["wl"], d["comp"], d["desc"], opts=_opts(ttm, request.param))
+    d["path"] = request.param
+    assert ttm.ttm_plan_problem_path(d["res"]["matcher"].plan, 0) == _opts(ttm, request.param).path
+    return d
 
 
 def test_tensor_template_matches_oracle(c1):
@@ -165,11 +182,12 @@ def test_peaks_on_planted_volume(ttm, c1):
     assert np.array_equal(lin, expect)
 
 
-def test_ragged_volume_and_order_two(ttm):
+@pytest.mark.parametrize("path", PATHS)
+def test_ragged_volume_and_order_two(ttm, path):
     wl = synth.make_workload((39, 45, 70), 11, 4, 2, 1.0, 2, 300, radius=5, seeds=(7, 8, 9))
     T = o.tensor_template(wl.template, wl.mask, wl.quadrature.astype(np.float64), wl.weights, 2)
     comp, desc = ttm.build_template(wl.template, wl.mask, 2, wl.quadrature)
-    res = _run(ttm, wl, comp, desc)
+    res = _run(ttm, wl, comp, desc, opts=_opts(ttm, path))
     w_o, C_o = o.ttm_components(wl.volume, T, wl.mask)
     assert np.abs(res["comp"] - C_o).max() <= TOL
     nz = w_o > 0
@@ -181,11 +199,12 @@ def test_ragged_volume_and_order_two(ttm):
                     res["quat"][pts[:, 2], pts[:, 1], pts[:, 0]], 2)
 
 
-def test_order_six(ttm):
+@pytest.mark.parametrize("path", PATHS)
+def test_order_six(ttm, path):
     wl = synth.make_workload((30, 28, 26), 9, 3, 1, 1.0, 6, 300, radius=4, seeds=(2, 3, 4))
     T = o.tensor_template(wl.template, wl.mask, wl.quadrature.astype(np.float64), wl.weights, 6)
     comp, desc = ttm.build_template(wl.template, wl.mask, 6, wl.quadrature)
-    res = _run(ttm, wl, comp, desc)
+    res = _run(ttm, wl, comp, desc, opts=_opts(ttm, path))
     w_o, C_o = o.ttm_components(wl.volume, T, wl.mask)
     assert np.abs(res["comp"] - C_o).max() <= TOL
     assert np.abs(res["score"] - o.frobenius_score(C_o, 6)).max() <= TOL
@@ -195,7 +214,8 @@ def test_order_six(ttm):
                     res["quat"][pts[:, 2], pts[:, 1], pts[:, 0]], 6)
 
 
-def test_degenerate_inputs(ttm):
+@pytest.mark.parametrize("path", PATHS)
+def test_degenerate_inputs(ttm, path):
     """A volume exactly one box wide (a single interior voxel) and a constant
     volume (zero variance everywhere: w = 0, score 0, identity rotation)."""
     s = 9
@@ -207,18 +227,19 @@ def test_degenerate_inputs(ttm):
     rng = np.random.default_rng(0)
     one = synth.Workload("one", rng.normal(size=(s, s, s)).astype(np.float32), t, m, 4, 4, q,
                          np.full(200, 1 / 200), np.zeros((0, 3), int), np.zeros((0, 4)), 0.0, 0.0)
-    res = _run(ttm, one, comp, desc)
+    res = _run(ttm, one, comp, desc, opts=_opts(ttm, path))
     w_o, C_o = o.ttm_components(one.volume, T, m)
     assert np.count_nonzero(res["score"]) == 1
     assert np.abs(res["comp"] - C_o).max() <= TOL
     const = synth.Workload("const", np.full((20, 21, 22), 2.5, np.float32), t, m, 4, 4, q,
                            np.full(200, 1 / 200), np.zeros((0, 3), int), np.zeros((0, 4)), 0.0, 0.0)
-    res = _run(ttm, const, comp, desc)
+    res = _run(ttm, const, comp, desc, opts=_opts(ttm, path))
     assert np.all(res["w"] == 0) and np.all(res["score"] == 0) and np.all(res["lam"] == 0)
     assert np.all(res["quat"] == np.array([1, 0, 0, 0], np.float32))
 
 
-def test_batched_plan_matches_single_problems(ttm):
+@pytest.mark.parametrize("path", PATHS)
+def test_batched_plan_matches_single_problems(ttm, path):
     import torch
     wa = synth.make_workload((40, 36, 34), 11, 4, 2, 1.0, 4, 200, radius=5, seeds=(1, 2, 3))
     wb = synth.make_workload((33, 47, 29), 9, 3, 1, 1.0, 4, 200, radius=4, seeds=(4, 5, 6))
@@ -228,11 +249,12 @@ def test_batched_plan_matches_single_problems(ttm):
     dims_a = wa.volume.shape[::-1]
     dims_b = wb.volume.shape[::-1]
     probs = [(dims_a, 0), (dims_a, 1), (dims_b, 0), (dims_b, 1)]
-    mb = ttm.Matcher([(ca, da, wa.mask), (cb, db, wb.mask)], probs)
+    mb = ttm.Matcher([(ca, da, wa.mask), (cb, db, wb.mask)], probs, opts=_opts(ttm, path))
     dv = [_cuda(vols[0]), _cuda(vols[0]), _cuda(vols[1]), _cuda(vols[1])]
     mb.run(dv)
     for p, ((X, Y, Z), k) in enumerate(probs):
-        single = ttm.Matcher([((ca, da, wa.mask), (cb, db, wb.mask))[k]], [((X, Y, Z), 0)])
+        single = ttm.Matcher([((ca, da, wa.mask), (cb, db, wb.mask))[k]], [((X, Y, Z), 0)],
+                             opts=_opts(ttm, path))
         single.run([dv[p]])
         torch.cuda.synchronize()
         assert torch.equal(single.score[0], mb.score[p])
