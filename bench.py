@@ -184,39 +184,51 @@ def source_hash(names) -> str:
 
 
 def roofline(kernels: dict, steps: int, nvox: int, K: int, n_taps: int, n_grid: int,
-             n_cand: int, newton: int, peaks: dict) -> dict:
+             n_cand: int, newton: int, peaks: dict, spectrum_bytes: float = 0.0) -> dict:
     """Roofline object for the kernel class with the largest share."""
     name = max(kernels, key=lambda k: kernels[k]["ms"])
     ms_launch = kernels[name]["ms"] / max(kernels[name]["launches"], 1)
     launches_per_step = kernels[name]["launches"] / steps
-    K4 = (K + 3) // 4 * 4
+    src = []
     if name == "direct_corr":
-        flops = 2.0 * K * n_taps * nvox / launches_per_step
-        bound, peak, unit = "alu", FP32_ALU_PEAK_TFLOPS, "TFLOP/s"
-        achieved = flops / (ms_launch * 1e-3) / 1e12
+        work = 2.0 * K * n_taps * nvox / launches_per_step
+        bound, peak, unit, scale = "alu", FP32_ALU_PEAK_TFLOPS, "TFLOP/s", 1e12
         src = ["k_direct.cu"]
-    elif name == "rotation":
+        peak_source = "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz"
+    elif name == "rotation_search" and K == 35 and n_grid == 2048:
+        work = 2.0 * n_grid * 48 * nvox / launches_per_step      # FP16 MMA, K padded to 48
+        bound, peak, unit, scale = "tensor", peaks.get("bf16_tflops", 1900.0), "TFLOP/s", 1e12
+        src = ["k_search_tc.cu", "k_rotation.cuh"]
+        peak_source = "measured dense bf16 (MEASURED_PEAKS.json bf16_tflops); fp16 runs at the bf16 rate"
+    elif name in ("rotation_search", "rotation_polish"):
         KB = 10
         per_cand = (2 + newton) * (2 * 10 * KB + 40) + newton * 150
-        flops = (2.0 * n_grid * K + 2 * K + n_cand * per_cand) * nvox / launches_per_step
-        bound, peak, unit = "alu", FP32_ALU_PEAK_TFLOPS, "TFLOP/s"
-        achieved = flops / (ms_launch * 1e-3) / 1e12
+        work = ((2.0 * n_grid * K + 2 * K) if name == "rotation_search" else n_cand * per_cand) \
+            * nvox / launches_per_step
+        bound, peak, unit, scale = "alu", FP32_ALU_PEAK_TFLOPS, "TFLOP/s", 1e12
         src = ["k_rotation.cuh", "k_rotation.cu", "k_rotation_n4.cu"]
+        peak_source = "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz"
     else:
-        # memory-bound stage: algorithmic bytes = read the volume + write one map
-        bytes_ = 8.0 * nvox / launches_per_step
-        bound, peak, unit = "hbm", peaks.get("hbm_gbs", 6800.0), "GB/s"
-        achieved = bytes_ / (ms_launch * 1e-3) / 1e9
-        src = []
+        # memory-bound stage: algorithmic bytes
+        if name == "local_stats":
+            per = 8.0 * nvox
+        elif name == "fft_spectrum_inverse":
+            per = spectrum_bytes * (1 + 2 * K)
+        elif name == "fft_inverse":
+            per = spectrum_bytes * 3 * K + 4.0 * K * nvox
+        else:
+            per = 8.0 * nvox
+        work = per / launches_per_step
+        bound, peak, unit, scale = "hbm", peaks.get("hbm_gbs", 6800.0), "GB/s", 1e9
+        peak_source = "measured (MEASURED_PEAKS.json hbm_gbs)"
+    achieved = work / (ms_launch * 1e-3) / scale
     traffic = None
     rec = NCU_TRAFFIC.get(name)
-    if rec and rec.get("source_sha") == source_hash(src):
+    if rec and src and rec.get("source_sha") == source_hash(src):
         traffic = rec["bytes_per_launch"]
     return dict(kernel=name, bound=bound, achieved=round(achieved, 3), peak=round(peak, 2),
                 unit=unit, frac=round(achieved / peak, 4), traffic=traffic,
-                ms_per_launch=round(ms_launch, 4),
-                peak_source="derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz" if bound == "alu"
-                else "measured (MEASURED_PEAKS.json hbm_gbs)")
+                ms_per_launch=round(ms_launch, 4), peak_source=peak_source)
 
 
 def run_ours(args) -> None:
@@ -280,6 +292,9 @@ def run_ours(args) -> None:
     if dist:
         dist.barrier()
     clk = clocks.stop()
+    status = ttm.ttm_plan_device_status(matcher.plan, matcher.ws)
+    if status != 0:
+        raise RuntimeError(f"device status {ttm.ttm_status_string(status)}")
     step_ms = [a.elapsed_time(b) for a, b in zip(starts, stops)]
     total_ms = sum(step_ms)
     launches = matcher.launch_count() - launches0
@@ -330,7 +345,9 @@ def run_ours(args) -> None:
     except (OSError, ValueError):
         pass
     n_taps = int(wl.mask.sum())
-    rf = roofline(kern, args.steps, nvox, desc.K, n_taps, 2048, 8, 6, peaks)
+    Xh = X // 2 + 1
+    spec_bytes = 8.0 * Xh * Y * Z if path == 2 else 0.0
+    rf = roofline(kern, args.steps, nvox, desc.K, n_taps, 2048, 8, 6, peaks, spec_bytes)
     cpu = None
     if not args.no_cpu_baseline and world == 1:
         cpu = cpu_baseline_obj(run_cpu_sample(args.workload, 128, 2))

@@ -95,8 +95,8 @@ typedef struct ttm_peak {
 typedef struct ttm_plan_opts {
     int path;           /* TTM_PATH_*                                          */
     int precision;      /* TTM_PREC_*                                          */
-    int n_grid;         /* rotation search grid size; 0 = default (2048)       */
-    int n_cells;        /* regions of the grid; 0 = default (128)              */
+    int n_grid;         /* rotation search grid size; 0 = default (2048), <= 65535 */
+    int n_cells;        /* regions of the grid; 0 = default (128); must divide n_grid */
     int n_candidates;   /* regions polished per voxel; 0 = default (8)         */
     int newton_steps;   /* Newton steps per candidate; 0 = default (6)         */
     int reserved[4];
@@ -199,6 +199,13 @@ ttm_status ttm_plan_problem_path(ttm_plan_t plan, int problem, int* path);
 /* Kernel launches the plan has queued so far (for accounting). */
 ttm_status ttm_plan_launch_count(ttm_plan_t plan, long long* launches);
 
+/* Status recorded by the device during the calls queued since the last
+ * ttm_correlate on this workspace (a bounded wait inside a kernel that ran
+ * out records TTM_ERR_TIMEOUT there instead of hanging).  Synchronises the
+ * stream; returns TTM_OK or the recorded error. */
+ttm_status ttm_plan_device_status(ttm_plan_t plan, void* d_workspace, size_t workspace_bytes,
+                                  void* stream);
+
 /* Per-kernel timing.  With timing enabled the plan records a CUDA event pair
  * on the launch stream around every kernel it queues.  ttm_plan_timing waits
  * for those events, adds the elapsed times per kernel class into ms[c] and the
@@ -238,8 +245,9 @@ ttm_status ttm_local_stats(ttm_plan_t plan, const float* const* d_vols, float* c
  *   lambda(x)  = max_{|Q|=1} phi(Q), phi(Q) = sum_alpha mu_alpha C_alpha Q^alpha
  *   q(x)       = its maximiser, the dominant Z-eigenvector     (Sec. 3.3)
  * The maximum is searched on a fixed grid of n_grid unit quaternions split
- * into n_cells regions; the best grid point of each of the n_candidates best
- * regions is refined by shifted power iterations (shift (n-1) score,
+ * into n_cells regions of equal size (for order 4 with the default grid this
+ * search runs on the tensor cores in FP16 with FP32 accumulation); the best
+ * grid point of each of the n_candidates best regions is refined by shifted power iterations (shift (n-1) score,
  * Kolda & Mayo 2011) and Riemannian Newton steps, and the largest refined
  * value is kept.  q is canonical: a >= 0.
  *   d_w          from ttm_local_stats.

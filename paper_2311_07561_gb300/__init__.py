@@ -35,6 +35,7 @@ from ._binding import (  # noqa: F401
     ttm_local_stats,
     ttm_plan,
     ttm_plan_destroy,
+    ttm_plan_device_status,
     ttm_plan_enable_timing,
     ttm_plan_launch_count,
     ttm_plan_problem_path,

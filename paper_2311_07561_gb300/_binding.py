@@ -33,6 +33,7 @@ EXPORTED = (
     "ttm_plan_problem_path", "ttm_plan_launch_count", "ttm_plan_destroy",
     "ttm_local_stats", "ttm_correlate", "ttm_extract_peaks", "ttm_plan_enable_timing",
     "ttm_plan_timing", "ttm_kernel_class_name", "ttm_build_tensor_template_noalloc",
+    "ttm_plan_device_status",
 )
 TTM_NOALLOC_SCRATCH_BYTES = 8388608
 TTM_KERNEL_CLASSES = 12
@@ -94,6 +95,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "ttm_plan_enable_timing": (I, [P, I]),
         "ttm_plan_timing": (I, [P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(L), I]),
         "ttm_kernel_class_name": (ctypes.c_char_p, [I]),
+        "ttm_plan_device_status": (I, [P, P, S, P]),
         "ttm_build_tensor_template_noalloc": (I, [P, P, I, I, P, P, I, P,
                                                   ctypes.POINTER(TTDesc), P]),
     }
@@ -233,6 +235,12 @@ def ttm_plan_destroy(plan: Optional[int]) -> None:
 def ttm_plan_enable_timing(plan: int, enable: bool = True) -> None:
     _check(load_library().ttm_plan_enable_timing(plan, 1 if enable else 0),
            "ttm_plan_enable_timing")
+
+
+def ttm_plan_device_status(plan: int, workspace, stream=None) -> int:
+    """Status the kernels recorded since the last ttm_correlate (0 = fine)."""
+    return load_library().ttm_plan_device_status(plan, _ptr(workspace), _nbytes(workspace),
+                                                   _stream(stream))
 
 
 def ttm_kernel_class_name(kernel_class: int) -> str:

@@ -7,7 +7,7 @@
 //   q(x)       = argmax, the dominant Z-eigenvector of C_n(x)                (Sec. 3.1)
 //
 // One thread per voxel.  The maximum is searched on a fixed grid of unit
-// quaternions (half sphere, sorted into regions): phi at every grid point is a
+// quaternions (half sphere, sorted into regions of equal size): phi at every grid point is a
 // dot product with a precomputed row mu_alpha q_g^alpha staged in shared memory
 // and read as a broadcast.  The best point of each region competes for a short
 // list of n_cand candidates.  Each candidate is refined by two shifted power
@@ -26,19 +26,53 @@ constexpr int kRotThreads = 128;
 constexpr int kChunk = 128;       // grid points staged per step
 constexpr int kMaxCand = 8;
 
-struct RotArgs {
+struct SearchArgs {
     const float* corr;      // K x nvox
     const float* w;
     size_t nvox;
     float* score;
+    uint16_t* cand;         // nvox x 8 candidate grid indices
+    const float* gm;        // n_grid x K4 (SIMT search)
+    const int* cell_end;    // n_grid
+    int n_grid;
+};
+
+struct PolishArgs {
+    const float* corr;
+    const float* w;
+    size_t nvox;
+    const float* score;
+    const uint16_t* cand;
     float* quat;            // 4 x nvox interleaved (a, b, c, d) per voxel
     float* lambda;          // nullable
     float* comp_out;        // nullable, K x nvox
     const float* gq;        // n_grid x 4
-    const float* gm;        // n_grid x K4
-    const int* cell_end;    // n_grid
-    int n_grid, n_cand, newton;
+    int n_cand, newton;
 };
+
+// keep the kMaxCand largest (value, index) pairs, sorted descending
+static __device__ __forceinline__ void insert_candidate(float (&tv)[kMaxCand], int (&ti)[kMaxCand],
+                                                 float val, int idx) {
+#pragma unroll
+    for (int k = 0; k < kMaxCand; ++k) {
+        if (val > tv[k]) {
+            float t = tv[k]; tv[k] = val; val = t;
+            int u = ti[k]; ti[k] = idx; idx = u;
+        }
+    }
+}
+
+static __device__ __forceinline__ void store_candidates(uint16_t* cand, size_t v, const int (&ti)[kMaxCand],
+                                                 bool active) {
+    uint32_t w[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        uint32_t lo = active ? (uint32_t)(ti[2 * k] & 0xFFFF) : 0xFFFFu;
+        uint32_t hi = active ? (uint32_t)(ti[2 * k + 1] & 0xFFFF) : 0xFFFFu;
+        w[k] = lo | (hi << 16);
+    }
+    reinterpret_cast<uint4*>(cand)[v] = make_uint4(w[0], w[1], w[2], w[3]);
+}
 
 template <int N>
 struct Geo {
@@ -101,7 +135,8 @@ __device__ __forceinline__ void eval_at(const float (&C)[Geo<N>::K4], const floa
 //   P ((N-1) H - lam I) P eta = -(g - lam x),  eta orthogonal to x,
 // solved as A eta = (g - lam x) with A = -P B P + sig x x^T, which is SPD
 // exactly when the tangent Hessian is negative definite.  Returns false if
-// the Cholesky factorisation breaks down (not near a maximum).
+// the Cholesky factorisation breaks down (not near a maximum).  Pivots are
+// inverted with rsqrt, so the solve has no division.
 template <int N>
 __device__ __forceinline__ bool newton_dir(const float H[4][4], const float g[4], const float x[4],
                                            float lam, float sig, float eta[4]) {
@@ -123,24 +158,22 @@ __device__ __forceinline__ bool newton_dir(const float H[4][4], const float g[4]
     float r[4];
 #pragma unroll
     for (int i = 0; i < 4; ++i) r[i] = g[i] - lam * x[i];
-    // Cholesky A = L L^T
     const float tiny = 1e-9f * sig;
     float L[4][4] = {};
+    float inv[4];
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
         float d = A[j][j];
 #pragma unroll
         for (int k = 0; k < j; ++k) d -= L[j][k] * L[j][k];
         if (!(d > tiny)) return false;
-        const float ljj = sqrtf(d);
-        L[j][j] = ljj;
-        const float inv = 1.f / ljj;
+        inv[j] = rsqrtf(d);
 #pragma unroll
         for (int i = j + 1; i < 4; ++i) {
             float v = A[i][j];
 #pragma unroll
             for (int k = 0; k < j; ++k) v -= L[i][k] * L[j][k];
-            L[i][j] = v * inv;
+            L[i][j] = v * inv[j];
         }
     }
     float y[4];
@@ -149,69 +182,78 @@ __device__ __forceinline__ bool newton_dir(const float H[4][4], const float g[4]
         float v = r[i];
 #pragma unroll
         for (int k = 0; k < i; ++k) v -= L[i][k] * y[k];
-        y[i] = v / L[i][i];
+        y[i] = v * inv[i];
     }
 #pragma unroll
     for (int i = 3; i >= 0; --i) {
         float v = y[i];
 #pragma unroll
         for (int k = i + 1; k < 4; ++k) v -= L[k][i] * eta[k];
-        eta[i] = v / L[i][i];
+        eta[i] = v * inv[i];
     }
     return true;
 }
 
+// Refinement of one start point: two shifted power (SS-HOPM) steps, then
+// Riemannian Newton steps; a Newton trial that lowers phi is rejected and
+// replaced by a power step from the last accepted point (power steps with
+// this shift never lower phi).  One evaluation site per iteration keeps the
+// code small.
 template <int N>
 __device__ void refine(const float (&C)[Geo<N>::K4], float sigma, int newton, float x[4],
                        float& lam_out) {
-    float H[4][4], g[4], lam;
-    // two shifted power (SS-HOPM) steps
-#pragma unroll 1
-    for (int it = 0; it < 2; ++it) {
-        eval_at<N>(C, x, H, g, lam);
-#pragma unroll
-        for (int i = 0; i < 4; ++i) x[i] = g[i] + sigma * x[i];
-        normalise4(x);
-    }
-    eval_at<N>(C, x, H, g, lam);
+    float xa[4] = {x[0], x[1], x[2], x[3]};
+    float Ha[4][4], ga[4], la = -INFINITY;
+    float xt[4] = {x[0], x[1], x[2], x[3]};
+    bool trial_newton = false;
+    int ss_left = 2;
     const float eps = 1e-6f * sigma;
+    const int iters = 3 + newton;
 #pragma unroll 1
-    for (int it = 0; it < newton; ++it) {
-        float eta[4];
-        float xn[4];
-        bool ok = newton_dir<N>(H, g, x, lam, sigma, eta);
-        if (ok) {
-            float en = sqrtf(eta[0] * eta[0] + eta[1] * eta[1] + eta[2] * eta[2] + eta[3] * eta[3]);
-            const float clip = en > 0.25f ? 0.25f / en : 1.f;
+    for (int it = 0; it < iters; ++it) {
+        float H[4][4], g[4], lam;
+        eval_at<N>(C, xt, H, g, lam);
+        if (trial_newton && lam < la - eps) {
 #pragma unroll
-            for (int i = 0; i < 4; ++i) xn[i] = x[i] + clip * eta[i];
-            normalise4(xn);
-        }
-        float Hn[4][4], gn[4], ln;
-        if (ok) {
-            eval_at<N>(C, xn, Hn, gn, ln);
-            ok = ln >= lam - eps;
-        }
-        if (!ok) {
-#pragma unroll
-            for (int i = 0; i < 4; ++i) xn[i] = g[i] + sigma * x[i];
-            normalise4(xn);
-            eval_at<N>(C, xn, Hn, gn, ln);
+            for (int i = 0; i < 4; ++i) xt[i] = ga[i] + sigma * xa[i];
+            normalise4(xt);
+            trial_newton = false;
+            continue;
         }
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
-            x[i] = xn[i];
-            g[i] = gn[i];
+            xa[i] = xt[i];
+            ga[i] = g[i];
 #pragma unroll
-            for (int j = 0; j < 4; ++j) H[i][j] = Hn[i][j];
+            for (int j = 0; j < 4; ++j) Ha[i][j] = H[i][j];
         }
-        lam = ln;
+        la = lam;
+        float eta[4];
+        if (ss_left == 0 && newton_dir<N>(Ha, ga, xa, la, sigma, eta)) {
+            const float en2 = eta[0] * eta[0] + eta[1] * eta[1] + eta[2] * eta[2] + eta[3] * eta[3];
+            const float clip = en2 > 0.0625f ? 0.25f * rsqrtf(en2) : 1.f;
+#pragma unroll
+            for (int i = 0; i < 4; ++i) xt[i] = xa[i] + clip * eta[i];
+            trial_newton = true;
+        } else {
+            if (ss_left > 0) --ss_left;
+#pragma unroll
+            for (int i = 0; i < 4; ++i) xt[i] = ga[i] + sigma * xa[i];
+            trial_newton = false;
+        }
+        normalise4(xt);
     }
-    lam_out = lam;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) x[i] = xa[i];
+    lam_out = la;
 }
 
+// Score and search: C_alpha = w Corr_alpha, score = ||C||_F, phi at every grid
+// point, best point of each region, the n_cand best regions -> candidate grid
+// indices (0xFFFF = none).  One thread per voxel; the grid table is staged in
+// shared memory and read as broadcasts.
 template <int N>
-__global__ void __launch_bounds__(kRotThreads) rotation_kernel(RotArgs a) {
+__global__ void __launch_bounds__(kRotThreads) search_simt_kernel(SearchArgs a) {
     constexpr int K = Geo<N>::K;
     constexpr int K4 = Geo<N>::K4;
     constexpr Sym<N> S{};
@@ -231,7 +273,6 @@ __global__ void __launch_bounds__(kRotThreads) rotation_kernel(RotArgs a) {
         float c = in_range ? wv * __ldg(a.corr + (size_t)k * a.nvox + v) : 0.f;
         C[k] = c;
         ss = fmaf((float)S.mu[k], c * c, ss);
-        if (a.comp_out && in_range) a.comp_out[(size_t)k * a.nvox + v] = c;
     }
     const float score = sqrtf(ss);
     const bool active = in_range && score > 0.f;
@@ -239,7 +280,7 @@ __global__ void __launch_bounds__(kRotThreads) rotation_kernel(RotArgs a) {
     float tv[kMaxCand];
     int ti[kMaxCand];
 #pragma unroll
-    for (int k = 0; k < kMaxCand; ++k) { tv[k] = -INFINITY; ti[k] = -1; }
+    for (int k = 0; k < kMaxCand; ++k) { tv[k] = -INFINITY; ti[k] = 0xFFFF; }
     float cur = -INFINITY;
     int curi = 0;
     const bool any_active = __syncthreads_or(active);
@@ -264,31 +305,48 @@ __global__ void __launch_bounds__(kRotThreads) rotation_kernel(RotArgs a) {
             }
             if (phi > cur) { cur = phi; curi = g0 + gg; }
             if (ends[gg]) {
-                float val = cur;
-                int idx = curi;
-#pragma unroll
-                for (int k = 0; k < kMaxCand; ++k) {
-                    if (val > tv[k]) {
-                        float t = tv[k]; tv[k] = val; val = t;
-                        int u = ti[k]; ti[k] = idx; idx = u;
-                    }
-                }
+                insert_candidate(tv, ti, cur, curi);
                 cur = -INFINITY;
             }
         }
     }
     if (!in_range) return;
+    a.score[v] = score;
+    store_candidates(a.cand, v, ti, active);
+}
 
+// Refinement of the candidates and the outputs: lambda = the largest refined
+// phi, q its maximiser (canonical sign), C_alpha optionally.
+template <int N>
+__global__ void __launch_bounds__(kRotThreads) polish_kernel(PolishArgs a) {
+    constexpr int K = Geo<N>::K;
+    constexpr int K4 = Geo<N>::K4;
+    const size_t v = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= a.nvox) return;
+    const float wv = __ldg(a.w + v);
+    float C[K4];
+#pragma unroll
+    for (int k = 0; k < K4; ++k) C[k] = 0.f;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        float c = wv * __ldg(a.corr + (size_t)k * a.nvox + v);
+        C[k] = c;
+        if (a.comp_out) a.comp_out[(size_t)k * a.nvox + v] = c;
+    }
+    const float score = __ldg(a.score + v);
+    const uint4 cr = __ldg(reinterpret_cast<const uint4*>(a.cand) + v);
+    const uint32_t cw[4] = {cr.x, cr.y, cr.z, cr.w};
     float best_l = 0.f;
     float best_q[4] = {1.f, 0.f, 0.f, 0.f};
-    if (active) {
+    if (score > 0.f && (cw[0] & 0xFFFFu) != 0xFFFFu) {
         const float sigma = (float)(N - 1) * score;
         best_l = -INFINITY;
         for (int k = 0; k < a.n_cand && k < kMaxCand; ++k) {
-            if (ti[k] < 0) break;
+            const int gi = (int)((cw[k >> 1] >> (16 * (k & 1))) & 0xFFFFu);
+            if (gi == 0xFFFF) break;
             float x[4];
 #pragma unroll
-            for (int i = 0; i < 4; ++i) x[i] = __ldg(a.gq + 4 * ti[k] + i);
+            for (int i = 0; i < 4; ++i) x[i] = __ldg(a.gq + 4 * gi + i);
             float l;
             refine<N>(C, sigma, a.newton, x, l);
             if (l > best_l) {
@@ -306,24 +364,37 @@ __global__ void __launch_bounds__(kRotThreads) rotation_kernel(RotArgs a) {
 #pragma unroll
         for (int i = 0; i < 4; ++i) best_q[i] *= sgn;
     }
-    a.score[v] = score;
     reinterpret_cast<float4*>(a.quat)[v] = make_float4(best_q[0], best_q[1], best_q[2], best_q[3]);
     if (a.lambda) a.lambda[v] = best_l;
 }
 
+// search_done: run only the refinement; search_only: run only the SIMT search
 template <int N>
-ttm_status launch_n(const RotArgs& a, cudaStream_t st, long long* cnt) {
-    const size_t smem = (size_t)kChunk * Geo<N>::K4 * sizeof(float) + kChunk * sizeof(int);
-    TTM_CUDA_TRY(cudaFuncSetAttribute(rotation_kernel<N>,
-                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    const unsigned blocks = (unsigned)((a.nvox + kRotThreads - 1) / kRotThreads);
-    rotation_kernel<N><<<blocks, kRotThreads, smem, st>>>(a);
+ttm_status launch_n(const SearchArgs& s, const PolishArgs& p, bool search_done, bool search_only,
+                    cudaStream_t st, long long* cnt) {
+    const unsigned blocks = (unsigned)((s.nvox + kRotThreads - 1) / kRotThreads);
+    if (!search_done) {
+        const size_t smem = (size_t)kChunk * Geo<N>::K4 * sizeof(float) + kChunk * sizeof(int);
+        TTM_CUDA_TRY(cudaFuncSetAttribute(search_simt_kernel<N>,
+                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        search_simt_kernel<N><<<blocks, kRotThreads, smem, st>>>(s);
+        TTM_TRY(after_launch(cnt));
+    }
+    if (search_only) return TTM_OK;
+    polish_kernel<N><<<blocks, kRotThreads, 0, st>>>(p);
     return after_launch(cnt);
 }
 
 }  // namespace rot
 
 template <int N>
-ttm_status launch_rotation_n(const rot::RotArgs& a, cudaStream_t st, long long* cnt);
+ttm_status launch_rotation_n(const rot::SearchArgs& s, const rot::PolishArgs& p, bool search_done,
+                             bool search_only, cudaStream_t st, long long* cnt);
+
+// tensor-core grid search for order 4 (k_search_tc.cu); returns
+// TTM_ERR_UNSUPPORTED when the grid does not have the fixed shape it needs
+ttm_status launch_search_tc4(const rot::SearchArgs& s, const uint16_t* grid_fp16,
+                             const uint32_t* end_bits, int* status, cudaStream_t st,
+                             long long* cnt);
 
 }  // namespace ttm

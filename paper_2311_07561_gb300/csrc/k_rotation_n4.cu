@@ -1,11 +1,13 @@
-// Per-voxel score and rotation kernel for tensor order n = 4.
+// Score/search and refinement kernels for tensor order n = 4.
 #include "k_rotation.cuh"
 
 namespace ttm {
 
 template <>
-ttm_status launch_rotation_n<4>(const rot::RotArgs& a, cudaStream_t st, long long* cnt) {
-    return rot::launch_n<4>(a, st, cnt);
+ttm_status launch_rotation_n<4>(const rot::SearchArgs& s, const rot::PolishArgs& p,
+                                  bool search_done, bool search_only, cudaStream_t st,
+                                  long long* cnt) {
+    return rot::launch_n<4>(s, p, search_done, search_only, st, cnt);
 }
 
 }  // namespace ttm

@@ -1,0 +1,288 @@
+// Tensor-core grid search of the per-voxel rotation for tensor order 4
+// (Sec. 3.3-3.4 of the paper: the rotation is the maximiser of
+// phi(Q) = C_n(x) . Q^(n) on the unit sphere).
+//
+// phi at the 2048 grid points of every voxel is one dense contraction,
+//   Phi[v, g] = sum_alpha Cn[v, alpha] M[g, alpha],  M[g, alpha] = mu_alpha q_g^alpha,
+// with Cn = C / ||C||_F (a positive per-voxel scale changes no ranking).  It runs
+// on the 5th-generation tensor cores: tcgen05.mma kind::f16 (FP16 operands,
+// FP32 accumulation) with M = 128 voxels, N = 256 grid points, K = 48 (35
+// components, zero padded), D in tensor memory.
+//
+// One persistent CTA per SM (128 threads, thread t = voxel t of the tile =
+// TMEM lane t).  The FP16 grid table (2048 x 48, 192 KB, K-major core-matrix
+// layout without swizzle) is copied into shared memory once per CTA.  Per
+// tile of 128 voxels: every thread writes its voxel's normalised components
+// as one FP16 row of A; thread 0 issues the MMAs of one 256-point chunk into
+// one half of a 512-column TMEM accumulator while all threads read the other
+// half (the previous chunk) with tcgen05.ld and keep, per grid region of 16
+// consecutive points, the best point, and the 8 best regions.  Waits on the MMA mbarrier are bounded:
+// on expiry the kernel records TTM_ERR_TIMEOUT, waits once more, frees its
+// TMEM and exits.
+#include <climits>
+
+#include <cuda_fp16.h>
+
+#include "k_rotation.cuh"
+
+namespace ttm {
+
+namespace {
+
+constexpr int kThreads = 128;
+constexpr int kG = 2048;             // grid points
+constexpr int kKP = 48;              // padded K
+constexpr int kKC = kKP / 8;         // core-matrix columns along K
+constexpr int kNG = kG / 8;          // core-matrix rows of B
+constexpr int kChunkN = 256;         // grid points per MMA
+constexpr int kChunks = kG / kChunkN;
+constexpr uint32_t kBBytes = (uint32_t)kKC * kNG * 128;     // 196608
+constexpr uint32_t kABytes = (uint32_t)kKC * 16 * 128;      // 12288
+constexpr uint32_t kSmem = kBBytes + kABytes + kG / 8;      // + region-end bitmask
+constexpr long kWaitLimit = 1L << 24;   // try_wait polls; well beyond any MMA latency
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+// shared-memory matrix descriptor: K-major, no swizzle; lbo = byte distance of
+// core matrices adjacent along K, sbo = along M/N
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+    uint64_t d = 0;
+    d |= (uint64_t)((addr & 0x3FFFF) >> 4);
+    d |= (uint64_t)((lbo >> 4) & 0x3FFF) << 16;
+    d |= (uint64_t)((sbo >> 4) & 0x3FFF) << 32;
+    d |= (uint64_t)1 << 46;
+    return d;
+}
+
+// kind::f16 instruction descriptor: D FP32, A and B FP16, both K-major, M = 128, N = 256
+constexpr uint32_t kIdesc = (1u << 4) | ((uint32_t)(kChunkN >> 3) << 17) | ((128u >> 4) << 24);
+
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t phase) {
+    for (long it = 0; it < kWaitLimit; ++it) {
+        uint32_t done;
+        asm volatile(
+            "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+            "selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(done)
+            : "r"(bar), "r"(phase)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+__device__ __forceinline__ void issue_chunk(uint32_t tmem_d, uint32_t a_base, uint32_t b_base,
+                                           int chunk, uint32_t bar) {
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+#pragma unroll
+    for (int s = 0; s < kKP / 16; ++s) {
+        const uint64_t ad = smem_desc(a_base + (uint32_t)(2 * s) * 16 * 128, 16 * 128, 128);
+        const uint64_t bd = smem_desc(b_base + (uint32_t)chunk * (kChunkN / 8) * 128 +
+                                          (uint32_t)(2 * s) * kNG * 128,
+                                      kNG * 128, 128);
+        asm volatile(
+            "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+            "l"(ad), "l"(bd), "r"(kIdesc), "r"(s) : "memory");
+    }
+    asm volatile(
+        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(bar)
+        : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t addr, uint32_t (&r)[32]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+          "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]),
+          "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+          "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]),
+          "=r"(r[31])
+        : "r"(addr)
+        : "memory");
+    asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+}
+
+__global__ void __launch_bounds__(kThreads, 1) search_tc4_kernel(rot::SearchArgs a,
+                                                                 const uint4* __restrict__ gtab,
+                                                                 const uint32_t* __restrict__ ends,
+                                                                 int* status) {
+    extern __shared__ __align__(1024) unsigned char sm[];
+    __shared__ __align__(8) uint64_t bars[2];
+    __shared__ uint32_t tmem_base_s;
+    constexpr int K = 35;
+    constexpr Sym<4> S{};
+    const int t = threadIdx.x;
+    const int warp = t >> 5;
+    unsigned char* Bs = sm;
+    unsigned char* As = sm + kBBytes;
+    uint32_t* endbits = reinterpret_cast<uint32_t*>(sm + kBBytes + kABytes);
+
+    // grid table and region-end bits, once per CTA
+    {
+        uint4* dst = reinterpret_cast<uint4*>(Bs);
+        for (int e = t; e < (int)(kBBytes / 16); e += kThreads) dst[e] = __ldg(gtab + e);
+        for (int e = t; e < kG / 32; e += kThreads) endbits[e] = __ldg(ends + e);
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;\n" ::"r"(
+                         smem_u32(&tmem_base_s)) : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+    }
+    if (t == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&bars[0])) : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&bars[1])) : "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    const uint32_t tmem = tmem_base_s;
+    const uint32_t a_base = smem_u32(As), b_base = smem_u32(Bs);
+    const uint32_t bar0 = smem_u32(&bars[0]), bar1 = smem_u32(&bars[1]);
+    uint32_t phase[2] = {0u, 0u};
+    bool ok = true;
+
+    const size_t ntiles = (a.nvox + 127) / 128;
+    for (size_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+        const size_t v = tile * 128 + t;
+        const bool in_range = v < a.nvox;
+        // components, score, normalised FP16 row of A
+        float C[K];
+        const float wv = in_range ? __ldg(a.w + v) : 0.f;
+        float ss = 0.f;
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            C[k] = in_range ? wv * __ldg(a.corr + (size_t)k * a.nvox + v) : 0.f;
+            ss = fmaf((float)S.mu[k], C[k] * C[k], ss);
+        }
+        const float score = sqrtf(ss);
+        const float inv = score > 0.f ? 1.f / score : 0.f;
+#pragma unroll
+        for (int kc = 0; kc < kKC; ++kc) {
+            __half h[8];
+#pragma unroll
+            for (int e = 0; e < 8; ++e) {
+                const int k = kc * 8 + e;
+                h[e] = __float2half_rn(k < K ? C[k] * inv : 0.f);
+            }
+            uint4 pk;
+            pk.x = (uint32_t)__half_as_ushort(h[0]) | ((uint32_t)__half_as_ushort(h[1]) << 16);
+            pk.y = (uint32_t)__half_as_ushort(h[2]) | ((uint32_t)__half_as_ushort(h[3]) << 16);
+            pk.z = (uint32_t)__half_as_ushort(h[4]) | ((uint32_t)__half_as_ushort(h[5]) << 16);
+            pk.w = (uint32_t)__half_as_ushort(h[6]) | ((uint32_t)__half_as_ushort(h[7]) << 16);
+            *reinterpret_cast<uint4*>(As + ((kc * 16 + (t >> 3)) * 8 + (t & 7)) * 16) = pk;
+        }
+        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+        asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+        __syncthreads();
+        if (t == 0) issue_chunk(tmem, a_base, b_base, 0, bar0);
+
+        // packed keys: an order-preserving integer image of phi with its low
+        // 11 bits replaced by (2047 - grid index), so one integer max gives the
+        // best point of a region (ties: lower index) at 2^-12 relative
+        // resolution, below the FP16 rounding of the products
+        int top[rot::kMaxCand];
+#pragma unroll
+        for (int k = 0; k < rot::kMaxCand; ++k) top[k] = INT_MIN;
+        for (int c = 0; c < kChunks; ++c) {
+            const int h = c & 1;
+            if (c + 1 < kChunks && t == 0)
+                issue_chunk(tmem + (uint32_t)((c + 1) & 1) * kChunkN, a_base, b_base, c + 1,
+                            ((c + 1) & 1) ? bar1 : bar0);
+            bool got = mbar_wait(h ? bar1 : bar0, phase[h]);
+            phase[h] ^= 1u;
+            if (!__syncthreads_and(got)) {
+                ok = false;
+                if (t == 0) atomicExch(status, TTM_ERR_TIMEOUT);
+                // let any MMA still in flight finish before TMEM is released
+                mbar_wait(h ? bar1 : bar0, phase[h] ^ 1u);
+                if (c + 1 < kChunks) mbar_wait(h ? bar0 : bar1, phase[h ^ 1]);
+                break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+            const uint32_t col0 = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)h * kChunkN;
+#pragma unroll 1
+            for (int p = 0; p < kChunkN / 32; ++p) {
+                uint32_t r[32];
+                tmem_ld32(col0 + (uint32_t)p * 32, r);
+                const int low0 = 2047 - (c * kChunkN + p * 32);   // 32 columns = 2 regions of 16
+                int key[32];
+#pragma unroll
+                for (int j = 0; j < 32; ++j) {
+                    const int b = (int)r[j];
+                    const int k = b ^ ((b >> 31) & 0x7FFFFFFF);
+                    key[j] = (k & ~2047) | (low0 - j);
+                }
+#pragma unroll
+                for (int w = 8; w >= 1; w >>= 1)
+#pragma unroll
+                    for (int j = 0; j < w; ++j) {
+                        key[j] = max(key[j], key[j + w]);
+                        key[16 + j] = max(key[16 + j], key[16 + j + w]);
+                    }
+#pragma unroll
+                for (int half = 0; half < 2; ++half) {
+                    int x = key[16 * half];
+#pragma unroll
+                    for (int k = 0; k < rot::kMaxCand; ++k) {
+                        const int hi = max(top[k], x);
+                        x = min(top[k], x);
+                        top[k] = hi;
+                    }
+                }
+            }
+            asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+            __syncthreads();     // this half may now be overwritten by chunk c + 2
+        }
+        int ti[rot::kMaxCand];
+#pragma unroll
+        for (int k = 0; k < rot::kMaxCand; ++k) ti[k] = top[k] == INT_MIN ? 0xFFFF : 2047 - (top[k] & 2047);
+        if (!ok) break;
+        if (in_range) {
+            a.score[v] = score;
+            rot::store_candidates(a.cand, v, ti, score > 0.f);
+        }
+    }
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;\n" ::"r"(tmem) : "memory");
+}
+
+}  // namespace
+
+ttm_status launch_search_tc4(const rot::SearchArgs& s, const uint16_t* grid_fp16,
+                             const uint32_t* end_bits, int* status, cudaStream_t st,
+                             long long* cnt) {
+    if (s.n_grid != kG || !grid_fp16 || !end_bits) return TTM_ERR_UNSUPPORTED;
+    TTM_CUDA_TRY(cudaFuncSetAttribute(search_tc4_kernel,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem));
+    int dev = 0, sms = 0;
+    TTM_CUDA_TRY(cudaGetDevice(&dev));
+    TTM_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const size_t ntiles = (s.nvox + 127) / 128;
+    const unsigned grid = (unsigned)(ntiles < (size_t)sms ? ntiles : (size_t)sms);
+    search_tc4_kernel<<<grid, kThreads, kSmem, st>>>(s, reinterpret_cast<const uint4*>(grid_fp16),
+                                                     end_bits, status);
+    return after_launch(cnt);
+}
+
+// FP16 grid table in the kernel's shared-memory layout: element (g, k) of the
+// 2048 x 48 matrix mu_k q_g^k (zero for k >= 35) at core matrix (k / 8, g / 8),
+// row g % 8, column k % 8, core matrices ordered k-block-major.
+void build_grid_fp16(const float* m_rows, int K4, std::vector<uint16_t>& out) {
+    out.assign((size_t)kKC * kNG * 64, 0);
+    for (int g = 0; g < kG; ++g)
+        for (int k = 0; k < kKP; ++k) {
+            float v = k < 35 ? m_rows[(size_t)g * K4 + k] : 0.f;
+            __half h = __float2half_rn(v);
+            const size_t idx = (((size_t)(k / 8) * kNG + g / 8) * 8 + g % 8) * 8 + k % 8;
+            out[idx] = __half_as_ushort(h);
+        }
+}
+
+}  // namespace ttm

@@ -95,7 +95,7 @@ ttm_status build_grid(ttm_plan_s* P) {
     const int nc = P->opts.n_cells > 0 ? P->opts.n_cells : 128;
     const int cand = P->opts.n_candidates > 0 ? P->opts.n_candidates : 8;
     const int newton = P->opts.newton_steps > 0 ? P->opts.newton_steps : 6;
-    if (n > (1 << 20) || nc > n || cand > 8 || newton > 64) return TTM_ERR_INVALID_ARG;
+    if (n > 65535 || nc > n || n % nc != 0 || cand > 8 || newton > 64) return TTM_ERR_INVALID_ARG;
     std::vector<double> pts, ctr;
     half_sphere_points(n, pts);
     half_sphere_points(nc, ctr);
@@ -129,7 +129,8 @@ ttm_status build_grid(ttm_plan_s* P) {
                 for (int r = 0; r < e[4 * a + i]; ++r) v *= q[i];
             hm[(size_t)g_i * K4 + a] = (float)v;
         }
-        ends[g_i] = (g_i == n - 1 || label[order[g_i + 1]] != label[order[g_i]]) ? 1 : 0;
+        // regions: consecutive groups of n / nc points in nearest-centre order
+        ends[g_i] = ((g_i + 1) % (n / nc) == 0) ? 1 : 0;
     }
     g.n_grid = n;
     g.n_cells = nc;
@@ -138,6 +139,15 @@ ttm_status build_grid(ttm_plan_s* P) {
     TTM_TRY(dev_upload(&g.d_q, hq));
     TTM_TRY(dev_upload(&g.d_m, hm));
     TTM_TRY(dev_upload(&g.d_cell_end, ends));
+    if (P->n_order == 4 && n == 2048 && nc == 128) {
+        std::vector<uint16_t> tab;
+        build_grid_fp16(hm.data(), K4, tab);
+        std::vector<uint32_t> bits(n / 32, 0u);
+        for (int i = 0; i < n; ++i)
+            if (ends[i]) bits[i / 32] |= 1u << (i % 32);
+        TTM_TRY(dev_upload(&g.d_gtab, tab));
+        TTM_TRY(dev_upload(&g.d_endbits, bits));
+    }
     return TTM_OK;
 }
 
@@ -315,6 +325,8 @@ void free_plan(ttm_plan_s* P) {
     cudaFree(P->grid.d_q);
     cudaFree(P->grid.d_m);
     cudaFree(P->grid.d_cell_end);
+    cudaFree(P->grid.d_gtab);
+    cudaFree(P->grid.d_endbits);
     delete P;
 }
 
@@ -325,13 +337,18 @@ constexpr int kPeakCapMax = 1 << 22;
 size_t peak_cap(size_t nvox) { return std::min(nvox, (size_t)kPeakCapMax); }
 
 // Correlation maps first (both paths), then for the FFT path the image
-// spectrum and the K product spectra.
+// spectrum and the K product spectra, then 8 candidate grid indices per voxel.
+size_t corr_region_bytes(const ttm_plan_s* P, const ProblemData& pr) {
+    size_t b = align256((size_t)P->K * pr.nvox() * sizeof(float));
+    if (pr.path == TTM_PATH_FFT)
+        b += align256(pr.fft.nspec() * sizeof(float2)) +
+             align256((size_t)P->K * pr.fft.nspec() * sizeof(float2));
+    return b;
+}
+
 size_t scratch_bytes(const ttm_plan_s* P, const ProblemData& pr) {
     const size_t nv = pr.nvox();
-    size_t corr = align256((size_t)P->K * nv * sizeof(float));
-    if (pr.path == TTM_PATH_FFT)
-        corr += align256(pr.fft.nspec() * sizeof(float2)) +
-                align256((size_t)P->K * pr.fft.nspec() * sizeof(float2));
+    size_t corr = corr_region_bytes(P, pr) + align256(nv * 16);
     size_t peaks = 2 * align256(nv * sizeof(float)) + align256(peak_cap(nv) * peak_record_bytes());
     return std::max(corr, peaks);
 }
@@ -521,6 +538,17 @@ ttm_status ttm_plan_launch_count(ttm_plan_t plan, long long* launches) {
     return TTM_OK;
 }
 
+ttm_status ttm_plan_device_status(ttm_plan_t plan, void* d_workspace, size_t workspace_bytes,
+                                  void* stream) {
+    if (!plan) return TTM_ERR_INVALID_ARG;
+    TTM_TRY(check_ws(plan, d_workspace, workspace_bytes));
+    cudaStream_t st = (cudaStream_t)stream;
+    int v = 0;
+    TTM_CUDA_TRY(cudaMemcpyAsync(&v, (char*)d_workspace + 32, sizeof(int), cudaMemcpyDeviceToHost, st));
+    TTM_CUDA_TRY(cudaStreamSynchronize(st));
+    return v == 0 ? TTM_OK : (ttm_status)v;
+}
+
 ttm_status ttm_plan_enable_timing(ttm_plan_t plan, int enable) {
     if (!plan) return TTM_ERR_INVALID_ARG;
     plan->timing = enable != 0;
@@ -554,8 +582,8 @@ ttm_status ttm_plan_timing(ttm_plan_t plan, double* ms, long long* launches, int
 
 const char* ttm_kernel_class_name(int c) {
     static const char* names[TTM_KERNEL_CLASSES] = {
-        "volume_moments", "local_stats", "direct_corr", "rotation", "fft_forward",
-        "fft_spectrum_inverse", "fft_inverse", "peaks", "template", "fft_plan", "other",
+        "volume_moments", "local_stats", "direct_corr", "rotation_search", "fft_forward",
+        "fft_spectrum_inverse", "fft_inverse", "peaks", "template", "fft_plan", "rotation_polish",
         "reserved"};
     if (c < 0 || c >= TTM_KERNEL_CLASSES) return "unknown";
     return names[c];
@@ -603,6 +631,7 @@ ttm_status ttm_correlate(ttm_plan_t plan, const float* const* d_vols, const floa
     }
     cudaStream_t st = (cudaStream_t)stream;
     float* corr = (float*)((char*)d_workspace + kHeader);
+    TTM_CUDA_TRY(cudaMemsetAsync((char*)d_workspace + 32, 0, sizeof(int), st));
     for (int p = 0; p < np; ++p) {
         const ProblemData& pr = plan->prob[p];
         const TemplateData& T = plan->tmpl[pr.tmpl];
@@ -629,12 +658,17 @@ ttm_status ttm_correlate(ttm_plan_t plan, const float* const* d_vols, const floa
                                           &plan->launches);
             }));
         }
+        uint16_t* cand = (uint16_t*)((char*)corr + corr_region_bytes(plan, pr));
+        int* d_status = (int*)((char*)d_workspace + 32);
         TTM_TRY(timed(plan, KC_ROTATION, st, [&] {
-            return launch_rotation(plan->n_order, corr, d_w[p], pr.nvox(), pr.X, pr.Y, pr.Z,
-                                   T.desc.s, plan->grid, d_score[p], d_quat[p],
-                                   d_lambda ? d_lambda[p] : nullptr,
-                                   d_components_out ? d_components_out[p] : nullptr, st,
-                                   &plan->launches);
+            return launch_rotation_search(plan->n_order, corr, d_w[p], pr.nvox(), plan->grid, cand,
+                                          d_status, d_score[p], st, &plan->launches);
+        }));
+        TTM_TRY(timed(plan, KC_POLISH, st, [&] {
+            return launch_rotation_polish(plan->n_order, corr, d_w[p], pr.nvox(), plan->grid, cand,
+                                          d_score[p], d_quat[p], d_lambda ? d_lambda[p] : nullptr,
+                                          d_components_out ? d_components_out[p] : nullptr, st,
+                                          &plan->launches);
         }));
     }
     return TTM_OK;

@@ -59,6 +59,8 @@ struct RotGrid {
     float* d_q = nullptr;        // n_grid x 4 unit quaternions, a >= 0, sorted by cell
     float* d_m = nullptr;        // n_grid x K: mu_alpha q_g^alpha
     int* d_cell_end = nullptr;   // n_grid: 1 if the next point starts a new cell
+    uint16_t* d_gtab = nullptr;  // order 4, 2048 points: FP16 table in tensor-core layout
+    uint32_t* d_endbits = nullptr;  // region ends as a bitmask (n_grid / 32 words)
 };
 
 }  // namespace ttm
@@ -66,7 +68,7 @@ struct RotGrid {
 namespace ttm {
 enum KernelClass {
     KC_MOMENTS = 0, KC_LOCAL_STATS, KC_DIRECT_CORR, KC_ROTATION, KC_FFT_FORWARD, KC_FFT_SPECTRUM,
-    KC_FFT_INVERSE, KC_PEAKS, KC_TEMPLATE, KC_FFT_PLAN, KC_OTHER, KC_RESERVED
+    KC_FFT_INVERSE, KC_PEAKS, KC_TEMPLATE, KC_FFT_PLAN, KC_POLISH, KC_RESERVED
 };
 struct TimedLaunch {
     int cls;
@@ -109,10 +111,16 @@ ttm_status launch_local_stats(const float* f, int X, int Y, int Z, const Templat
 ttm_status launch_direct_corr(const float* f, int X, int Y, int Z, const TemplateData& T,
                               int K, float* corr, cudaStream_t st, long long* cnt);
 
-ttm_status launch_rotation(int n_order, const float* corr, const float* w, size_t nvox,
-                           int X, int Y, int Z, int s, const RotGrid& g, float* score,
-                           float* quat, float* lambda, float* comp_out, cudaStream_t st,
-                           long long* cnt);
+// per-voxel score + candidate search (tensor cores for order 4 with the
+// default 2048-point grid, CUDA cores otherwise), then refinement
+ttm_status launch_rotation_search(int n_order, const float* corr, const float* w, size_t nvox,
+                                  const RotGrid& g, uint16_t* cand, int* status, float* score,
+                                  cudaStream_t st, long long* cnt);
+ttm_status launch_rotation_polish(int n_order, const float* corr, const float* w, size_t nvox,
+                                  const RotGrid& g, const uint16_t* cand, const float* score,
+                                  float* quat, float* lambda, float* comp_out, cudaStream_t st,
+                                  long long* cnt);
+void build_grid_fp16(const float* m_rows, int K4, std::vector<uint16_t>& out);
 
 // tensor template build
 ttm_status launch_rotate_normalise(const float* t, const float* m, int s, const float* quats,

@@ -52,6 +52,7 @@ def _run(ttm, wl, comp, desc, opts=None, want_comp=True):
     comps = [torch.empty((desc.K, Z, Y, X), dtype=torch.float32, device="cuda")] if want_comp else None
     m.run([vol], components_out=comps)
     torch.cuda.synchronize()
+    assert ttm.ttm_plan_device_status(m.plan, m.ws) == 0
     out = dict(w=m.w[0].cpu().numpy(), score=m.score[0].cpu().numpy(),
                quat=m.quat[0].cpu().numpy(), lam=m.lam[0].cpu().numpy(),
                comp=comps[0].cpu().numpy() if want_comp else None, matcher=m)
