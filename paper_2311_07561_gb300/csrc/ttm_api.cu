@@ -205,6 +205,7 @@ ttm_status prepare_template(ttm_plan_s* P, TemplateData& T, const float* d_mask)
         dz0[T.dz_max - T.dz_min + 1] = (int)runs.size();
     }
     (void)P;
+    TTM_TRY(dev_upload(&T.d_mask, m));
     TTM_TRY(dev_upload(&T.d_runs, runs));
     TTM_TRY(dev_upload(&T.d_run_tap0, tap0));
     TTM_TRY(dev_upload(&T.d_dz_run0, dz0));
@@ -258,7 +259,8 @@ ttm_status prepare_fft(ttm_plan_s* P, ProblemData& pr, cudaStream_t st) {
     sp.tmpl = pr.tmpl; sp.Xp = pr.fft.Xp; sp.Yp = pr.fft.Yp; sp.Zp = pr.fft.Zp;
     const size_t nspec = pr.fft.nspec();
     const size_t nreal = (size_t)pr.fft.Xp * pr.fft.Yp * pr.fft.Zp;
-    if (cudaMalloc((void**)&sp.d_spec, (size_t)P->K * nspec * sizeof(float2)) != cudaSuccess) {
+    // K component spectra and, last, the mask spectrum (local statistics)
+    if (cudaMalloc((void**)&sp.d_spec, (size_t)(P->K + 1) * nspec * sizeof(float2)) != cudaSuccess) {
         cudaGetLastError();
         return TTM_ERR_OUT_OF_MEMORY;
     }
@@ -271,6 +273,9 @@ ttm_status prepare_fft(ttm_plan_s* P, ProblemData& pr, cudaStream_t st) {
     }
     ttm_status s = launch_template_spectra(T.d_comp, P->K, T.desc.s, pr.fft, pad, sp.d_spec, st,
                                            &P->launches);
+    if (s == TTM_OK)
+        s = launch_template_spectra(T.d_mask, 1, T.desc.s, pr.fft, pad,
+                                    sp.d_spec + (size_t)P->K * nspec, st, &P->launches);
     cudaError_t e = cudaStreamSynchronize(st);
     cudaFree(pad);
     if (s != TTM_OK) return s;
@@ -315,6 +320,7 @@ void free_plan(ttm_plan_s* P) {
     for (cudaEvent_t e : P->event_pool) cudaEventDestroy(e);
     for (TemplateData& T : P->tmpl) {
         cudaFree(T.d_runs);
+        cudaFree(T.d_mask);
         cudaFree(T.d_run_tap0);
         cudaFree(T.d_dz_run0);
         cudaFree(T.d_taps);
@@ -349,6 +355,8 @@ size_t corr_region_bytes(const ttm_plan_s* P, const ProblemData& pr) {
 size_t scratch_bytes(const ttm_plan_s* P, const ProblemData& pr) {
     const size_t nv = pr.nvox();
     size_t corr = corr_region_bytes(P, pr) + align256(nv * 16);
+    if (pr.path == TTM_PATH_FFT)
+        corr = std::max(corr, 4 * pr.fft.nspec() * sizeof(float2) + 2 * nv * sizeof(float) + 256);
     size_t peaks = 2 * align256(nv * sizeof(float)) + align256(peak_cap(nv) * peak_record_bytes());
     return std::max(corr, peaks);
 }
@@ -609,10 +617,38 @@ ttm_status ttm_local_stats(ttm_plan_t plan, const float* const* d_vols, float* c
         TTM_TRY(timed(plan, KC_MOMENTS, st, [&] {
             return launch_volume_moments(d_vols[p], pr.nvox(), d_mom, st, &plan->launches);
         }));
-        TTM_TRY(timed(plan, KC_LOCAL_STATS, st, [&] {
-            return launch_local_stats(d_vols[p], pr.X, pr.Y, pr.Z, plan->tmpl[pr.tmpl], d_mom,
-                                      d_w[p], st, &plan->launches);
-        }));
+        if (pr.path == TTM_PATH_FFT && fft_template_length(pr.fft.Xp)) {
+            // Algorithm 1: window sums of (f - mean) and (f - mean)^2 as
+            // correlations with the mask, through the FFT
+            const TemplateData& T = plan->tmpl[pr.tmpl];
+            const size_t nspec = pr.fft.nspec();
+            char* base = (char*)d_workspace + kHeader;
+            float2* F1 = (float2*)base;
+            float2* F2 = F1 + nspec;
+            float2* prod = F2 + nspec;                       // two product spectra
+            float* sums = (float*)(prod + 2 * nspec);        // S1, S2 maps
+            const float2* mspec = plan->specs[pr.spec_index].d_spec + (size_t)plan->K * nspec;
+            TTM_TRY(timed(plan, KC_LOCAL_STATS, st, [&] {
+                TTM_TRY(launch_fft_forward(d_vols[p], pr.X, pr.Y, pr.Z, pr.fft, F1, st,
+                                           &plan->launches, 1, d_mom));
+                TTM_TRY(launch_fft_forward(d_vols[p], pr.X, pr.Y, pr.Z, pr.fft, F2, st,
+                                           &plan->launches, 2, d_mom));
+                TTM_TRY(launch_fft_spectrum_inverse_z(F1, mspec, 1, pr.fft, prod, st,
+                                                      &plan->launches));
+                TTM_TRY(launch_fft_spectrum_inverse_z(F2, mspec, 1, pr.fft, prod + nspec, st,
+                                                      &plan->launches));
+                TTM_TRY(launch_fft_inverse_yx(prod, 2, pr.X, pr.Y, pr.Z, pr.fft, sums, st,
+                                              &plan->launches));
+                return launch_stats_from_sums(sums, sums + pr.nvox(), d_w[p], pr.X, pr.Y, pr.Z,
+                                              T.desc.s, T.desc.mask_sum, d_mom, st,
+                                              &plan->launches);
+            }));
+        } else {
+            TTM_TRY(timed(plan, KC_LOCAL_STATS, st, [&] {
+                return launch_local_stats(d_vols[p], pr.X, pr.Y, pr.Z, plan->tmpl[pr.tmpl], d_mom,
+                                          d_w[p], st, &plan->launches);
+            }));
+        }
     }
     return TTM_OK;
 }

@@ -17,6 +17,7 @@ struct MaskRun {
 struct TemplateData {
     ttm_tt_desc desc{};
     const float* d_comp = nullptr;      // caller-owned K x s^3 components
+    float* d_mask = nullptr;            // plan copy of the mask (s^3)
     std::vector<MaskRun> runs;          // mask as x-runs, sorted by (dz, dy)
     int n_taps = 0;                     // mask voxels
     int dz_min = 0, dz_max = -1, dy_min = 0, dy_max = -1, x_min = 0, x_max = -1;
@@ -135,8 +136,14 @@ ttm_status launch_fold_components(int n_order, const float* quats, const float* 
 // FFT path
 bool fft_length_ok(int L);
 int fft_good_length(int n);
+// mode 0: F(f); 1: F(f - mean); 2: F((f - mean)^2), mean from moments (sum f first)
 ttm_status launch_fft_forward(const float* f, int X, int Y, int Z, const FftShape& S,
-                              float2* spec, cudaStream_t st, long long* cnt);
+                              float2* spec, cudaStream_t st, long long* cnt, int mode = 0,
+                              const double* moments = nullptr);
+bool fft_template_length(int L);
+ttm_status launch_stats_from_sums(const float* s1, const float* s2, float* w, int X, int Y, int Z,
+                                  int s, double mask_sum, const double* moments, cudaStream_t st,
+                                  long long* cnt);
 ttm_status launch_fft_spectrum_inverse_z(const float2* spec, const float2* tspec, int K,
                                          const FftShape& S, float2* prod, cudaStream_t st,
                                          long long* cnt);
