@@ -7,7 +7,8 @@
 // with Cn = C / ||C||_F (a positive per-voxel scale changes no ranking).  It runs
 // on the 5th-generation tensor cores: tcgen05.mma kind::f16 (FP16 operands,
 // FP32 accumulation) with M = 128 voxels, N = 256 grid points, K = 48 (35
-// components, zero padded), D in tensor memory.
+// components, a constant column that adds +1 to phi, zero padding), D in
+// tensor memory.
 //
 // One persistent CTA per SM (128 threads, thread t = voxel t of the tile =
 // TMEM lane t).  The FP16 grid table (2048 x 48, 192 KB, K-major core-matrix
@@ -29,7 +30,7 @@ namespace ttm {
 
 namespace {
 
-constexpr int kThreads = 128;
+constexpr int kThreads = 256;    // warps w and w + 4 read the same TMEM lanes, different columns
 constexpr int kG = 2048;             // grid points
 constexpr int kKP = 48;              // padded K
 constexpr int kKC = kKP / 8;         // core-matrix columns along K
@@ -38,7 +39,8 @@ constexpr int kChunkN = 256;         // grid points per MMA
 constexpr int kChunks = kG / kChunkN;
 constexpr uint32_t kBBytes = (uint32_t)kKC * kNG * 128;     // 196608
 constexpr uint32_t kABytes = (uint32_t)kKC * 16 * 128;      // 12288
-constexpr uint32_t kSmem = kBBytes + kABytes + kG / 8;      // + region-end bitmask
+constexpr uint32_t kMergeBytes = 128 * 8 * 4;                // top-8 keys of warps 4..7
+constexpr uint32_t kSmem = kBBytes + kABytes + kMergeBytes;
 constexpr long kWaitLimit = 1L << 24;   // try_wait polls; well beyond any MMA latency
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -92,6 +94,29 @@ __device__ __forceinline__ void issue_chunk(uint32_t tmem_d, uint32_t a_base, ui
         : "memory");
 }
 
+__device__ __forceinline__ void tmem_ld64(uint32_t addr, uint32_t (&r)[64]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x64.b32 "
+        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,"
+        "%32,%33,%34,%35,%36,%37,%38,%39,%40,%41,%42,%43,%44,%45,%46,%47,"
+        "%48,%49,%50,%51,%52,%53,%54,%55,%56,%57,%58,%59,%60,%61,%62,%63}, [%64];\n"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+          "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]),
+          "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+          "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]),
+          "=r"(r[31]), "=r"(r[32]), "=r"(r[33]), "=r"(r[34]), "=r"(r[35]), "=r"(r[36]),
+          "=r"(r[37]), "=r"(r[38]), "=r"(r[39]), "=r"(r[40]), "=r"(r[41]), "=r"(r[42]),
+          "=r"(r[43]), "=r"(r[44]), "=r"(r[45]), "=r"(r[46]), "=r"(r[47]), "=r"(r[48]),
+          "=r"(r[49]), "=r"(r[50]), "=r"(r[51]), "=r"(r[52]), "=r"(r[53]), "=r"(r[54]),
+          "=r"(r[55]), "=r"(r[56]), "=r"(r[57]), "=r"(r[58]), "=r"(r[59]), "=r"(r[60]),
+          "=r"(r[61]), "=r"(r[62]), "=r"(r[63])
+        : "r"(addr)
+        : "memory");
+    asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+}
+
 __device__ __forceinline__ void tmem_ld32(uint32_t addr, uint32_t (&r)[32]) {
     asm volatile(
         "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
@@ -121,13 +146,13 @@ __global__ void __launch_bounds__(kThreads, 1) search_tc4_kernel(rot::SearchArgs
     const int warp = t >> 5;
     unsigned char* Bs = sm;
     unsigned char* As = sm + kBBytes;
-    uint32_t* endbits = reinterpret_cast<uint32_t*>(sm + kBBytes + kABytes);
+    int* merge = reinterpret_cast<int*>(sm + kBBytes + kABytes);   // [8][128]
+    (void)ends;   // regions are the 128 consecutive groups of 16 points
 
-    // grid table and region-end bits, once per CTA
+    // grid table, once per CTA
     {
         uint4* dst = reinterpret_cast<uint4*>(Bs);
         for (int e = t; e < (int)(kBBytes / 16); e += kThreads) dst[e] = __ldg(gtab + e);
-        for (int e = t; e < kG / 32; e += kThreads) endbits[e] = __ldg(ends + e);
     }
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;\n" ::"r"(
@@ -147,11 +172,15 @@ __global__ void __launch_bounds__(kThreads, 1) search_tc4_kernel(rot::SearchArgs
     uint32_t phase[2] = {0u, 0u};
     bool ok = true;
 
+    const int lane_t = t & 127;            // TMEM lane = voxel of the tile
+    const int colhalf = t >> 7;            // warps 4..7 take columns 128..255 of a chunk
     const size_t ntiles = (a.nvox + 127) / 128;
     for (size_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
-        const size_t v = tile * 128 + t;
+        const size_t v = tile * 128 + lane_t;
         const bool in_range = v < a.nvox;
-        // components, score, normalised FP16 row of A
+        // components, score, normalised FP16 row of A (threads 0..127)
+        float score = 0.f;
+        if (colhalf == 0) {
         float C[K];
         const float wv = in_range ? __ldg(a.w + v) : 0.f;
         float ss = 0.f;
@@ -160,7 +189,7 @@ __global__ void __launch_bounds__(kThreads, 1) search_tc4_kernel(rot::SearchArgs
             C[k] = in_range ? wv * __ldg(a.corr + (size_t)k * a.nvox + v) : 0.f;
             ss = fmaf((float)S.mu[k], C[k] * C[k], ss);
         }
-        const float score = sqrtf(ss);
+        score = sqrtf(ss);
         const float inv = score > 0.f ? 1.f / score : 0.f;
 #pragma unroll
         for (int kc = 0; kc < kKC; ++kc) {
@@ -168,24 +197,26 @@ __global__ void __launch_bounds__(kThreads, 1) search_tc4_kernel(rot::SearchArgs
 #pragma unroll
             for (int e = 0; e < 8; ++e) {
                 const int k = kc * 8 + e;
-                h[e] = __float2half_rn(k < K ? C[k] * inv : 0.f);
+                // column K is the constant 1 that adds +1 to every phi (see below)
+                h[e] = __float2half_rn(k < K ? C[k] * inv : (k == K ? 1.f : 0.f));
             }
             uint4 pk;
             pk.x = (uint32_t)__half_as_ushort(h[0]) | ((uint32_t)__half_as_ushort(h[1]) << 16);
             pk.y = (uint32_t)__half_as_ushort(h[2]) | ((uint32_t)__half_as_ushort(h[3]) << 16);
             pk.z = (uint32_t)__half_as_ushort(h[4]) | ((uint32_t)__half_as_ushort(h[5]) << 16);
             pk.w = (uint32_t)__half_as_ushort(h[6]) | ((uint32_t)__half_as_ushort(h[7]) << 16);
-            *reinterpret_cast<uint4*>(As + ((kc * 16 + (t >> 3)) * 8 + (t & 7)) * 16) = pk;
+            *reinterpret_cast<uint4*>(As + ((kc * 16 + (lane_t >> 3)) * 8 + (lane_t & 7)) * 16) = pk;
+        }
         }
         asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
         asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
         __syncthreads();
         if (t == 0) issue_chunk(tmem, a_base, b_base, 0, bar0);
 
-        // packed keys: an order-preserving integer image of phi with its low
-        // 11 bits replaced by (2047 - grid index), so one integer max gives the
-        // best point of a region (ties: lower index) at 2^-12 relative
-        // resolution, below the FP16 rounding of the products
+        // packed keys: the float bits of phi + 1 (non-negative, so they order
+        // like the values) with the low 11 bits replaced by (2047 - grid
+        // index): one integer max gives the best point of a region (ties:
+        // lower index) at 2.4e-4 resolution of the normalised phi
         int top[rot::kMaxCand];
 #pragma unroll
         for (int k = 0; k < rot::kMaxCand; ++k) top[k] = INT_MIN;
@@ -205,29 +236,28 @@ __global__ void __launch_bounds__(kThreads, 1) search_tc4_kernel(rot::SearchArgs
                 break;
             }
             asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-            const uint32_t col0 = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)h * kChunkN;
+            const uint32_t col0 = tmem + ((uint32_t)((warp & 3) * 32) << 16) +
+                                  (uint32_t)h * kChunkN + (uint32_t)colhalf * 128;
 #pragma unroll 1
-            for (int p = 0; p < kChunkN / 32; ++p) {
-                uint32_t r[32];
-                tmem_ld32(col0 + (uint32_t)p * 32, r);
-                const int low0 = 2047 - (c * kChunkN + p * 32);   // 32 columns = 2 regions of 16
-                int key[32];
+            for (int p = 0; p < 2; ++p) {
+                uint32_t r[64];
+                tmem_ld64(col0 + (uint32_t)p * 64, r);
+                // 64 columns = 4 regions of 16
+                const int low0 = 2047 - (c * kChunkN + colhalf * 128 + p * 64);
+                // phi + 1 >= 0 (|phi| <= 1 for unit-norm C), so its float bits
+                // order like the values
+                int key[64];
 #pragma unroll
-                for (int j = 0; j < 32; ++j) {
-                    const int b = (int)r[j];
-                    const int k = b ^ ((b >> 31) & 0x7FFFFFFF);
-                    key[j] = (k & ~2047) | (low0 - j);
-                }
+                for (int j = 0; j < 64; ++j) key[j] = ((int)r[j] & ~2047) | (low0 - j);
 #pragma unroll
                 for (int w = 8; w >= 1; w >>= 1)
 #pragma unroll
-                    for (int j = 0; j < w; ++j) {
-                        key[j] = max(key[j], key[j + w]);
-                        key[16 + j] = max(key[16 + j], key[16 + j + w]);
-                    }
+                    for (int q = 0; q < 4; ++q)
 #pragma unroll
-                for (int half = 0; half < 2; ++half) {
-                    int x = key[16 * half];
+                        for (int j = 0; j < w; ++j) key[16 * q + j] = max(key[16 * q + j], key[16 * q + j + w]);
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    int x = key[16 * q];
 #pragma unroll
                     for (int k = 0; k < rot::kMaxCand; ++k) {
                         const int hi = max(top[k], x);
@@ -238,6 +268,23 @@ __global__ void __launch_bounds__(kThreads, 1) search_tc4_kernel(rot::SearchArgs
             }
             asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
             __syncthreads();     // this half may now be overwritten by chunk c + 2
+        }
+        // merge the two column halves' lists
+        if (colhalf == 1) {
+#pragma unroll
+            for (int k = 0; k < rot::kMaxCand; ++k) merge[k * 128 + lane_t] = top[k];
+        }
+        __syncthreads();
+        if (colhalf == 1) continue;
+#pragma unroll
+        for (int k2 = 0; k2 < rot::kMaxCand; ++k2) {
+            int x = merge[k2 * 128 + lane_t];
+#pragma unroll
+            for (int k = 0; k < rot::kMaxCand; ++k) {
+                const int hi = max(top[k], x);
+                x = min(top[k], x);
+                top[k] = hi;
+            }
         }
         int ti[rot::kMaxCand];
 #pragma unroll
@@ -278,7 +325,9 @@ void build_grid_fp16(const float* m_rows, int K4, std::vector<uint16_t>& out) {
     out.assign((size_t)kKC * kNG * 64, 0);
     for (int g = 0; g < kG; ++g)
         for (int k = 0; k < kKP; ++k) {
-            float v = k < 35 ? m_rows[(size_t)g * K4 + k] : 0.f;
+            // column 35 holds the constant 1 paired with A's constant column,
+            // adding +1 to every phi
+            float v = k < 35 ? m_rows[(size_t)g * K4 + k] : (k == 35 ? 1.f : 0.f);
             __half h = __float2half_rn(v);
             const size_t idx = (((size_t)(k / 8) * kNG + g / 8) * 8 + g % 8) * 8 + k % 8;
             out[idx] = __half_as_ushort(h);
