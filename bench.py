@@ -347,7 +347,7 @@ def run_ours(args) -> None:
     n_taps = int(wl.mask.sum())
     Xh = X // 2 + 1
     spec_bytes = 8.0 * Xh * Y * Z if path == 2 else 0.0
-    rf = roofline(kern, args.steps, nvox, desc.K, n_taps, 2048, 8, 6, peaks, spec_bytes)
+    rf = roofline(kern, args.steps, nvox, desc.K, n_taps, 2048, 8, 4, peaks, spec_bytes)
     cpu = None
     if not args.no_cpu_baseline and world == 1:
         cpu = cpu_baseline_obj(run_cpu_sample(args.workload, 128, 2))

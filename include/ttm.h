@@ -98,7 +98,7 @@ typedef struct ttm_plan_opts {
     int n_grid;         /* rotation search grid size; 0 = default (2048), <= 65535 */
     int n_cells;        /* regions of the grid; 0 = default (128); must divide n_grid */
     int n_candidates;   /* regions polished per voxel; 0 = default (8)         */
-    int newton_steps;   /* Newton steps per candidate; 0 = default (6)         */
+    int newton_steps;   /* Newton steps per candidate; 0 = default (4)         */
     int reserved[4];
 } ttm_plan_opts;
 

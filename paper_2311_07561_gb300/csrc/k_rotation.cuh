@@ -149,12 +149,14 @@ __device__ __forceinline__ bool newton_dir(const float H[4][4], const float g[4]
 #pragma unroll
     for (int i = 0; i < 4; ++i) Bx[i] = B[i][0] * x[0] + B[i][1] * x[1] + B[i][2] * x[2] + B[i][3] * x[3];
     const float xBx = x[0] * Bx[0] + x[1] * Bx[1] + x[2] * Bx[2] + x[3] * Bx[3];
+    // A = -B + x (Bx)^T + (Bx) x^T + (sig - x^T B x) x x^T, lower triangle only
+    const float cxx = sig - xBx;
     float A[4][4];
 #pragma unroll
     for (int i = 0; i < 4; ++i)
 #pragma unroll
-        for (int j = 0; j < 4; ++j)
-            A[i][j] = -(B[i][j] - x[i] * Bx[j] - Bx[i] * x[j] + xBx * x[i] * x[j]) + sig * x[i] * x[j];
+        for (int j = 0; j <= i; ++j)
+            A[i][j] = fmaf(cxx * x[i], x[j], fmaf(x[i], Bx[j], fmaf(Bx[i], x[j], -B[i][j])));
     float r[4];
 #pragma unroll
     for (int i = 0; i < 4; ++i) r[i] = g[i] - lam * x[i];
