@@ -411,18 +411,28 @@ __global__ void __launch_bounds__(kFftThreads) rows_r2c_t(const float* __restric
     const int row0 = blockIdx.x * NB;
     const int nrows = g.Yp * g.Zp;
     const float mean = mode ? (float)(moments[0] / ((double)X * Y * Z)) : 0.f;
-    for (int e = threadIdx.x; e < NB * L; e += blockDim.x) {
+    constexpr int PER = (NB * L + kFftThreads - 1) / kFftThreads;
+    float vv[PER];
+#pragma unroll
+    for (int i = 0; i < PER; ++i) {
+        const int e = threadIdx.x + i * kFftThreads;
         const int r = e / L, x = e & (L - 1);
         const int row = row0 + r;
         float v = 0.f;
-        if (row < nrows) {
+        if (e < NB * L && row < nrows) {
             const int y = row % g.Yp, z = row / g.Yp;
             if (x < X && y < Y && z < Z) {
                 v = __ldg(f + ((size_t)z * Y + y) * X + x) - mean;
                 if (mode == 2) v = v * v;
             }
         }
-        A[x * PITCH + r] = make_float2(v, 0.f);
+        vv[i] = v;
+    }
+#pragma unroll
+    for (int i = 0; i < PER; ++i) {
+        const int e = threadIdx.x + i * kFftThreads;
+        const int r = e / L, x = e & (L - 1);
+        if (e < NB * L) A[x * PITCH + r] = make_float2(vv[i], 0.f);
     }
     __syncthreads();
     float2* res = fft_lines_t<L, NB, PITCH, -1>(A, B, tw);
@@ -440,18 +450,29 @@ __global__ void __launch_bounds__(kFftThreads) cols_t(float2* __restrict__ data,
     extern __shared__ float2 sm[];
     float2* P = sm;
     float2* Q = sm + L * TB;
+    constexpr int PER = (L * TB + kFftThreads - 1) / kFftThreads;
     const int b0 = blockIdx.x * TB;
     const size_t base = (size_t)blockIdx.y * L * B;
     const int tb = min(TB, B - b0);
-    for (int e = threadIdx.x; e < L * TB; e += blockDim.x) {
+    float2 v[PER];
+#pragma unroll
+    for (int i = 0; i < PER; ++i) {          // all loads in flight before any store
+        const int e = threadIdx.x + i * kFftThreads;
         const int l = e / TB, bb = e & (TB - 1);
-        P[e] = bb < tb ? data[base + (size_t)l * B + b0 + bb] : make_float2(0.f, 0.f);
+        v[i] = (e < L * TB && bb < tb) ? data[base + (size_t)l * B + b0 + bb] : make_float2(0.f, 0.f);
+    }
+#pragma unroll
+    for (int i = 0; i < PER; ++i) {
+        const int e = threadIdx.x + i * kFftThreads;
+        if (e < L * TB) P[e] = v[i];
     }
     __syncthreads();
     float2* res = fft_lines_t<L, TB, TB, SIGN>(P, Q, tw);
-    for (int e = threadIdx.x; e < L * TB; e += blockDim.x) {
+#pragma unroll
+    for (int i = 0; i < PER; ++i) {
+        const int e = threadIdx.x + i * kFftThreads;
         const int l = e / TB, bb = e & (TB - 1);
-        if (bb < tb) data[base + (size_t)l * B + b0 + bb] = res[e];
+        if (e < L * TB && bb < tb) data[base + (size_t)l * B + b0 + bb] = res[e];
     }
 }
 
@@ -462,30 +483,54 @@ __global__ void __launch_bounds__(kFftThreads) cols_mul_t(const float2* __restri
                                                           const float2* __restrict__ tw) {
     constexpr int TB = cols_tb<L>();
     extern __shared__ float2 sm[];
-    float2* Fimg = sm;
-    float2* P = sm + L * TB;
-    float2* Q = sm + 2 * L * TB;
+    float2* P = sm;
+    float2* Q = sm + L * TB;
+    constexpr int PER = (L * TB + kFftThreads - 1) / kFftThreads;
     const int b0 = blockIdx.x * TB;
     const int tb = min(TB, B - b0);
     const size_t plane = (size_t)L * B;
-    for (int e = threadIdx.x; e < L * TB; e += blockDim.x) {
+    // this thread's elements of the image tile stay in registers
+    float2 fi[PER];
+#pragma unroll
+    for (int i = 0; i < PER; ++i) {
+        const int e = threadIdx.x + i * kFftThreads;
         const int l = e / TB, bb = e & (TB - 1);
-        Fimg[e] = bb < tb ? spec[(size_t)l * B + b0 + bb] : make_float2(0.f, 0.f);
+        fi[i] = (e < L * TB && bb < tb) ? spec[(size_t)l * B + b0 + bb] : make_float2(0.f, 0.f);
+    }
+    // component tiles: the next one is fetched while the current one is transformed
+    float2 tv[PER];
+#pragma unroll
+    for (int i = 0; i < PER; ++i) {
+        const int e = threadIdx.x + i * kFftThreads;
+        const int l = e / TB, bb = e & (TB - 1);
+        tv[i] = (K > 0 && e < L * TB && bb < tb) ? __ldg(tspec + (size_t)l * B + b0 + bb)
+                                                  : make_float2(0.f, 0.f);
     }
     for (int k = 0; k < K; ++k) {
         __syncthreads();
-        const float2* ts = tspec + (size_t)k * plane;
-        for (int e = threadIdx.x; e < L * TB; e += blockDim.x) {
-            const int l = e / TB, bb = e & (TB - 1);
-            float2 t = bb < tb ? __ldg(ts + (size_t)l * B + b0 + bb) : make_float2(0.f, 0.f);
-            P[e] = cmulc(Fimg[e], t);
+#pragma unroll
+        for (int i = 0; i < PER; ++i) {
+            const int e = threadIdx.x + i * kFftThreads;
+            if (e < L * TB) P[e] = cmulc(fi[i], tv[i]);
+        }
+        if (k + 1 < K) {
+            const float2* ts = tspec + (size_t)(k + 1) * plane;
+#pragma unroll
+            for (int i = 0; i < PER; ++i) {
+                const int e = threadIdx.x + i * kFftThreads;
+                const int l = e / TB, bb = e & (TB - 1);
+                tv[i] = (e < L * TB && bb < tb) ? __ldg(ts + (size_t)l * B + b0 + bb)
+                                                 : make_float2(0.f, 0.f);
+            }
         }
         __syncthreads();
         float2* res = fft_lines_t<L, TB, TB, +1>(P, Q, tw);
         float2* o = out + (size_t)k * plane;
-        for (int e = threadIdx.x; e < L * TB; e += blockDim.x) {
+#pragma unroll
+        for (int i = 0; i < PER; ++i) {
+            const int e = threadIdx.x + i * kFftThreads;
             const int l = e / TB, bb = e & (TB - 1);
-            if (bb < tb) o[(size_t)l * B + b0 + bb] = res[e];
+            if (e < L * TB && bb < tb) o[(size_t)l * B + b0 + bb] = res[e];
         }
     }
 }
@@ -500,27 +545,38 @@ __global__ void __launch_bounds__(kFftThreads) rows_c2r_t(const float2* __restri
     extern __shared__ float2 sm[];
     float2* A = sm;
     float2* Bf = sm + L * PITCH;
+    constexpr int PER = (NB * L + kFftThreads - 1) / kFftThreads;
     const size_t rows_per_item = (size_t)g.Yp * g.Zp;
     const size_t nrows = rows_per_item * n_batch;
     const size_t row0 = (size_t)blockIdx.x * NB;
-    for (int e = threadIdx.x; e < NB * L; e += blockDim.x) {
+    float2 v[PER];
+#pragma unroll
+    for (int i = 0; i < PER; ++i) {          // loads first, Hermitian extension on the fly
+        const int e = threadIdx.x + i * kFftThreads;
         const int r = e / L, x = e & (L - 1);
         const size_t row = row0 + r;
-        float2 v = make_float2(0.f, 0.f);
-        if (row < nrows) {
+        v[i] = make_float2(0.f, 0.f);
+        if (e < NB * L && row < nrows) {
             const float2* src = in + row * XH;
-            if (x < XH) v = src[x];
-            else { float2 c = src[L - x]; v = make_float2(c.x, -c.y); }
+            if (x < XH) v[i] = src[x];
+            else { float2 c = src[L - x]; v[i] = make_float2(c.x, -c.y); }
         }
-        A[x * PITCH + r] = v;
+    }
+#pragma unroll
+    for (int i = 0; i < PER; ++i) {
+        const int e = threadIdx.x + i * kFftThreads;
+        const int r = e / L, x = e & (L - 1);
+        if (e < NB * L) A[x * PITCH + r] = v[i];
     }
     __syncthreads();
     float2* res = fft_lines_t<L, NB, PITCH, +1>(A, Bf, tw);
     const size_t vox = (size_t)X * Y * Z;
-    for (int e = threadIdx.x; e < NB * L; e += blockDim.x) {
+#pragma unroll
+    for (int i = 0; i < PER; ++i) {
+        const int e = threadIdx.x + i * kFftThreads;
         const int r = e / L, x = e & (L - 1);
         const size_t row = row0 + r;
-        if (row >= nrows || x >= X) continue;
+        if (e >= NB * L || row >= nrows || x >= X) continue;
         const size_t item = row / rows_per_item;
         const int rr = (int)(row % rows_per_item);
         const int y = rr % g.Yp, z = rr / g.Yp;
@@ -546,7 +602,7 @@ struct RunColsMul {
     cudaStream_t st; cudaError_t* err;
     template <int L> void operator()() {
         constexpr int TB = cols_tb<L>();
-        const size_t smem = (size_t)3 * L * TB * sizeof(float2);
+        const size_t smem = (size_t)2 * L * TB * sizeof(float2);
         *err = cudaFuncSetAttribute(cols_mul_t<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         dim3 grid((Bz + TB - 1) / TB, 1);
         cols_mul_t<L><<<grid, kFftThreads, smem, st>>>(spec, tspec, prod, Bz, K, tw);
