@@ -412,17 +412,27 @@ __global__ void __launch_bounds__(kFftThreads) rows_r2c_t(const float* __restric
     const int nrows = g.Yp * g.Zp;
     const float mean = mode ? (float)(moments[0] / ((double)X * Y * Z)) : 0.f;
     constexpr int PER = (NB * L + kFftThreads - 1) / kFftThreads;
+    __shared__ long long row_in[NB];         // input offset of each row, -1 = zero row
+    if (threadIdx.x < NB) {
+        const int row = row0 + threadIdx.x;
+        long long off = -1;
+        if (row < nrows) {
+            const int y = row % g.Yp, z = row / g.Yp;
+            if (y < Y && z < Z) off = (long long)(((size_t)z * Y + y) * X);
+        }
+        row_in[threadIdx.x] = off;
+    }
+    __syncthreads();
     float vv[PER];
 #pragma unroll
     for (int i = 0; i < PER; ++i) {
         const int e = threadIdx.x + i * kFftThreads;
         const int r = e / L, x = e & (L - 1);
-        const int row = row0 + r;
         float v = 0.f;
-        if (e < NB * L && row < nrows) {
-            const int y = row % g.Yp, z = row / g.Yp;
-            if (x < X && y < Y && z < Z) {
-                v = __ldg(f + ((size_t)z * Y + y) * X + x) - mean;
+        if (e < NB * L && x < X) {
+            const long long off = row_in[r];
+            if (off >= 0) {
+                v = __ldg(f + off + x) - mean;
                 if (mode == 2) v = v * v;
             }
         }
@@ -546,9 +556,21 @@ __global__ void __launch_bounds__(kFftThreads) rows_c2r_t(const float2* __restri
     float2* A = sm;
     float2* Bf = sm + L * PITCH;
     constexpr int PER = (NB * L + kFftThreads - 1) / kFftThreads;
+    __shared__ long long row_out[NB];        // output offset of each row, -1 = not written
     const size_t rows_per_item = (size_t)g.Yp * g.Zp;
     const size_t nrows = rows_per_item * n_batch;
     const size_t row0 = (size_t)blockIdx.x * NB;
+    if (threadIdx.x < NB) {
+        const size_t row = row0 + threadIdx.x;
+        long long off = -1;
+        if (row < nrows) {
+            const size_t item = row / rows_per_item;
+            const int rr = (int)(row - item * rows_per_item);
+            const int y = rr % g.Yp, z = rr / g.Yp;
+            if (y < Y && z < Z) off = (long long)(item * ((size_t)X * Y * Z) + ((size_t)z * Y + y) * X);
+        }
+        row_out[threadIdx.x] = off;
+    }
     float2 v[PER];
 #pragma unroll
     for (int i = 0; i < PER; ++i) {          // loads first, Hermitian extension on the fly
@@ -569,18 +591,14 @@ __global__ void __launch_bounds__(kFftThreads) rows_c2r_t(const float2* __restri
         if (e < NB * L) A[x * PITCH + r] = v[i];
     }
     __syncthreads();
-    float2* res = fft_lines_t<L, NB, PITCH, +1>(A, Bf, tw);
-    const size_t vox = (size_t)X * Y * Z;
+    float2* res = fft_lines_t<L, NB, PITCH, +1>(A, Bf, tw);   // ends with a barrier
 #pragma unroll
     for (int i = 0; i < PER; ++i) {
         const int e = threadIdx.x + i * kFftThreads;
         const int r = e / L, x = e & (L - 1);
-        const size_t row = row0 + r;
-        if (e >= NB * L || row >= nrows || x >= X) continue;
-        const size_t item = row / rows_per_item;
-        const int rr = (int)(row % rows_per_item);
-        const int y = rr % g.Yp, z = rr / g.Yp;
-        if (y < Y && z < Z) out[item * vox + ((size_t)z * Y + y) * X + x] = res[x * PITCH + r].x;
+        if (e >= NB * L || x >= X) continue;
+        const long long off = row_out[r];
+        if (off >= 0) out[off + x] = res[x * PITCH + r].x;
     }
 }
 
