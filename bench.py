@@ -66,6 +66,8 @@ def parse():
     ap.add_argument("--path", default="auto", choices=["auto", "direct", "fft"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--classical", action=argparse.BooleanOptionalAction, default=True,
+                    help="also time classical NCC at 1000 rotations on the same volume")
     ap.add_argument("--cpu-sample", type=int, default=0,
                     help="internal: run the oracle on this many sampled voxels and print JSON")
     ap.add_argument("--sample-steps", type=int, default=1)
@@ -335,6 +337,34 @@ def run_ours(args) -> None:
         e2e = dict(value=nvox * args.steps * world / (e_ms * 1e-3), unit=UNIT,
                    h2d_bytes_per_step=nvox * 4, d2h_bytes_per_step=nvox * 4 * 6)
 
+    # classical template matching (Algorithm 1) at 1000 rotations on the same
+    # volume and GPU: the comparator of the paper's speed-up claim
+    classical = None
+    if args.classical and path == 2:
+        import synth as _s
+        qc = torch.from_numpy(_s.shoemake_quaternions(1000, 4).astype(np.float32)).to(dev)
+        tc = torch.from_numpy(wl.template).to(dev)
+        best = torch.empty((Z, Y, X), dtype=torch.float32, device=dev)
+        barg = torch.empty((Z, Y, X), dtype=torch.int32, device=dev)
+        cws = torch.empty(ttm.ttm_classical_workspace_size(matcher.plan, 0), dtype=torch.uint8,
+                          device=dev)
+        ttm.ttm_classical_ncc(matcher.plan, 0, tc, qc, 1000, vol, matcher.w[0], best, barg, cws)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        flush.zero_()
+        a.record(stream)
+        ttm.ttm_local_stats(matcher.plan, [vol], matcher.w, matcher.ws)
+        ttm.ttm_classical_ncc(matcher.plan, 0, tc, qc, 1000, vol, matcher.w[0], best, barg, cws)
+        b.record(stream)
+        b.synchronize()
+        c_ms = a.elapsed_time(b)
+        classical = dict(rotations=1000, ms_per_volume=round(c_ms, 2),
+                         voxels_per_s=nvox / (c_ms * 1e-3),
+                         ttm_speedup=round(c_ms / (t_max / args.steps), 2),
+                         note="classical NCC per rotation (rotate, normalise, FFT, conjugate "
+                              "multiply, inverse FFT, running max) vs TTM score+rotation maps")
+        del cws, best, barg
+
     if rank != 0:
         if dist:
             dist.destroy_process_group()
@@ -360,7 +390,7 @@ def run_ours(args) -> None:
                     rotation_grid=2048, l2="flushed (256 MB write) before every timed step",
                     parallelism="replicas" if world > 1 else "single GPU",
                     template_build_ms=round(build_ms, 2), quadrature_rotations=desc.n_rot),
-        roofline=rf, cpu_baseline=cpu, e2e=e2e, gpu_launches=launches,
+        roofline=rf, cpu_baseline=cpu, e2e=e2e, gpu_launches=launches, classical=classical,
         clocks=clk,
         kernels={k: dict(ms_per_step=round(v["ms"] / args.steps, 4),
                          launches_per_step=v["launches"] / args.steps,

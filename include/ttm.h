@@ -264,6 +264,29 @@ ttm_status ttm_correlate(ttm_plan_t plan, const float* const* d_vols, const floa
                          size_t workspace_bytes, void* stream);
 
 /* ------------------------------------------------------------------------
+ * Classical template matching with rotations (Algorithm 1), the comparator of
+ * TTM: for every rotation j of d_quats the template is rotated, masked and
+ * S-normalised (exactly as in ttm_build_tensor_template), transformed, and
+ * correlated with the volume through the FFT of the plan's problem; the NCC
+ * c(x, R_j) = w(x) (f * S(t)_{R_j})(x) is reduced to its maximum over j,
+ *   d_best[x] = max_j c(x, R_j),   d_best_index[x] = the first j attaining it.
+ * Outside the interior both are 0.  Rotations run in batches of 32.
+ *   problem      a problem of the plan that uses the FFT path.
+ *   d_template   s^3 float32 raw template (s of the problem's template).
+ *   d_quats      n_rot x 4 float32 unit quaternions.
+ *   d_vol, d_w   the problem's volume and its w from ttm_local_stats.
+ *   d_best       X*Y*Z float32 output; d_best_index X*Y*Z int32 output.
+ * Errors: TTM_ERR_INVALID_ARG, TTM_ERR_UNSUPPORTED (direct-path problem),
+ * TTM_ERR_WORKSPACE, TTM_ERR_NUMERIC (a rotated copy has zero variance),
+ * TTM_ERR_CUDA.
+ * ---------------------------------------------------------------------- */
+ttm_status ttm_classical_workspace_size(ttm_plan_t plan, int problem, size_t* bytes);
+ttm_status ttm_classical_ncc(ttm_plan_t plan, int problem, const float* d_template,
+                             const float* d_quats, int n_rot, const float* d_vol,
+                             const float* d_w, float* d_best, int* d_best_index,
+                             void* d_workspace, size_t workspace_bytes, void* stream);
+
+/* ------------------------------------------------------------------------
  * Peaks of the position score (Sec. 3.4).  A voxel is a peak when its score
  * exceeds threshold and beats every other voxel of the (2*radius+1)^3 cube
  * around it (equal scores: the lower linear index wins).  Up to max_peaks

@@ -28,6 +28,8 @@ from ._binding import (  # noqa: F401
     ttm_build_tensor_template,
     ttm_build_tensor_template_noalloc,
     ttm_build_workspace_size,
+    ttm_classical_ncc,
+    ttm_classical_workspace_size,
     ttm_correlate,
     ttm_device_count,
     ttm_extract_peaks,

@@ -33,7 +33,7 @@ EXPORTED = (
     "ttm_plan_problem_path", "ttm_plan_launch_count", "ttm_plan_destroy",
     "ttm_local_stats", "ttm_correlate", "ttm_extract_peaks", "ttm_plan_enable_timing",
     "ttm_plan_timing", "ttm_kernel_class_name", "ttm_build_tensor_template_noalloc",
-    "ttm_plan_device_status",
+    "ttm_plan_device_status", "ttm_classical_workspace_size", "ttm_classical_ncc",
 )
 TTM_NOALLOC_SCRATCH_BYTES = 8388608
 TTM_KERNEL_CLASSES = 12
@@ -96,6 +96,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "ttm_plan_timing": (I, [P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(L), I]),
         "ttm_kernel_class_name": (ctypes.c_char_p, [I]),
         "ttm_plan_device_status": (I, [P, P, S, P]),
+        "ttm_classical_workspace_size": (I, [P, I, ctypes.POINTER(S)]),
+        "ttm_classical_ncc": (I, [P, I, P, P, I, P, P, P, P, P, S, P]),
         "ttm_build_tensor_template_noalloc": (I, [P, P, I, I, P, P, I, P,
                                                   ctypes.POINTER(TTDesc), P]),
     }
@@ -271,6 +273,21 @@ def ttm_correlate(plan: int, vols: Sequence[Any], w: Sequence[Any], score: Seque
                                       _nbytes(workspace) if workspace is not None else 0,
                                       _stream(stream))
     _check(st, "ttm_correlate")
+
+
+def ttm_classical_workspace_size(plan: int, problem: int) -> int:
+    out = ctypes.c_size_t()
+    _check(load_library().ttm_classical_workspace_size(plan, problem, ctypes.byref(out)),
+           "ttm_classical_workspace_size")
+    return out.value
+
+
+def ttm_classical_ncc(plan: int, problem: int, template, quats, n_rot: int, vol, w, best,
+                      best_index, workspace, stream=None) -> None:
+    st = load_library().ttm_classical_ncc(plan, problem, _ptr(template), _ptr(quats), n_rot,
+                                          _ptr(vol), _ptr(w), _ptr(best), _ptr(best_index),
+                                          _ptr(workspace), _nbytes(workspace), _stream(stream))
+    _check(st, "ttm_classical_ncc")
 
 
 PEAK_DTYPE = np.dtype([("x", np.int32), ("y", np.int32), ("z", np.int32), ("score", np.float32),

@@ -93,7 +93,33 @@ __global__ void peak_z_kernel(const float* __restrict__ score, const float* __re
     list[slot] = rec;
 }
 
+// Running maximum of c_j(x) = w(x) corr_j(x) over a batch of rotations j0..j0+nb-1
+// (Algorithm 1 reduced over the rotation set); first index wins ties.
+__global__ void best_rotation_kernel(const float* __restrict__ corr, int nb, int j0,
+                                     const float* __restrict__ w, size_t nvox,
+                                     float* __restrict__ best, int* __restrict__ best_j, int first) {
+    const size_t v = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= nvox) return;
+    const float wv = w[v];
+    float b = first ? -INFINITY : best[v];
+    int bj = first ? 0 : best_j[v];
+    for (int j = 0; j < nb; ++j) {
+        const float c = wv * corr[(size_t)j * nvox + v];
+        if (c > b) { b = c; bj = j0 + j; }
+    }
+    best[v] = b;
+    best_j[v] = bj;
+}
+
 }  // namespace
+
+ttm_status launch_best_rotation(const float* corr, int nb, int j0, const float* w, size_t nvox,
+                                float* best, int* best_j, bool first, cudaStream_t st,
+                                long long* cnt) {
+    best_rotation_kernel<<<(unsigned)((nvox + 255) / 256), 256, 0, st>>>(corr, nb, j0, w, nvox, best,
+                                                                          best_j, first ? 1 : 0);
+    return after_launch(cnt);
+}
 
 size_t peak_record_bytes() { return sizeof(PeakRec); }
 

@@ -710,6 +710,90 @@ ttm_status ttm_correlate(ttm_plan_t plan, const float* const* d_vols, const floa
     return TTM_OK;
 }
 
+static constexpr int kClassicalBatch = 32;
+
+struct ClassicalLayout {
+    size_t spec, tspec, prod, maps, rot, pad, total;
+};
+
+static ClassicalLayout classical_layout(const ttm_plan_s* P, const ProblemData& pr) {
+    const TemplateData& T = P->tmpl[pr.tmpl];
+    const size_t nspec = pr.fft.nspec();
+    const size_t nreal = (size_t)pr.fft.Xp * pr.fft.Yp * pr.fft.Zp;
+    const size_t s3 = (size_t)T.desc.s * T.desc.s * T.desc.s;
+    ClassicalLayout L;
+    size_t off = kHeader;
+    L.spec = off;  off += align256(nspec * sizeof(float2));
+    L.tspec = off; off += align256((size_t)kClassicalBatch * nspec * sizeof(float2));
+    L.prod = off;  off += align256((size_t)kClassicalBatch * nspec * sizeof(float2));
+    L.maps = off;  off += align256((size_t)kClassicalBatch * pr.nvox() * sizeof(float));
+    L.rot = off;   off += align256((size_t)kClassicalBatch * s3 * sizeof(float));
+    L.pad = off;   off += align256(nreal * sizeof(float));
+    L.total = off;
+    return L;
+}
+
+ttm_status ttm_classical_workspace_size(ttm_plan_t plan, int problem, size_t* bytes) {
+    if (!plan || !bytes || problem < 0 || problem >= (int)plan->prob.size())
+        return TTM_ERR_INVALID_ARG;
+    const ProblemData& pr = plan->prob[problem];
+    if (pr.path != TTM_PATH_FFT) return TTM_ERR_UNSUPPORTED;
+    *bytes = classical_layout(plan, pr).total;
+    return TTM_OK;
+}
+
+ttm_status ttm_classical_ncc(ttm_plan_t plan, int problem, const float* d_template,
+                             const float* d_quats, int n_rot, const float* d_vol,
+                             const float* d_w, float* d_best, int* d_best_index,
+                             void* d_workspace, size_t workspace_bytes, void* stream) {
+    if (!plan || problem < 0 || problem >= (int)plan->prob.size() || !d_template || !d_quats ||
+        n_rot < 1 || !d_vol || !d_w || !d_best || !d_best_index)
+        return TTM_ERR_INVALID_ARG;
+    const ProblemData& pr = plan->prob[problem];
+    if (pr.path != TTM_PATH_FFT) return TTM_ERR_UNSUPPORTED;
+    const ClassicalLayout Lay = classical_layout(plan, pr);
+    if (!d_workspace || workspace_bytes < Lay.total) return TTM_ERR_WORKSPACE;
+    if (!aligned(d_workspace, 256)) return TTM_ERR_INVALID_ARG;
+    const TemplateData& T = plan->tmpl[pr.tmpl];
+    const int s = T.desc.s;
+    cudaStream_t st = (cudaStream_t)stream;
+    char* ws = (char*)d_workspace;
+    int* d_bad = (int*)(ws + 40);
+    float2* spec = (float2*)(ws + Lay.spec);
+    float2* tspec = (float2*)(ws + Lay.tspec);
+    float2* prod = (float2*)(ws + Lay.prod);
+    float* maps = (float*)(ws + Lay.maps);
+    float* rot = (float*)(ws + Lay.rot);
+    float* pad = (float*)(ws + Lay.pad);
+    TTM_CUDA_TRY(cudaMemsetAsync(d_bad, 0, sizeof(int), st));
+    TTM_TRY(timed(plan, KC_FFT_FORWARD, st, [&] {
+        return launch_fft_forward(d_vol, pr.X, pr.Y, pr.Z, pr.fft, spec, st, &plan->launches);
+    }));
+    for (int j0 = 0; j0 < n_rot; j0 += kClassicalBatch) {
+        const int nb = std::min(kClassicalBatch, n_rot - j0);
+        TTM_TRY(timed(plan, KC_TEMPLATE, st, [&] {
+            TTM_TRY(launch_rotate_normalise(d_template, T.d_mask, s, d_quats, j0, nb, rot,
+                                            T.desc.mask_sum, d_bad, st, &plan->launches));
+            return launch_template_spectra(rot, nb, s, pr.fft, pad, tspec, st, &plan->launches);
+        }));
+        TTM_TRY(timed(plan, KC_FFT_SPECTRUM, st, [&] {
+            return launch_fft_spectrum_inverse_z(spec, tspec, nb, pr.fft, prod, st, &plan->launches);
+        }));
+        TTM_TRY(timed(plan, KC_FFT_INVERSE, st, [&] {
+            return launch_fft_inverse_yx(prod, nb, pr.X, pr.Y, pr.Z, pr.fft, maps, st,
+                                         &plan->launches);
+        }));
+        TTM_TRY(timed(plan, KC_PEAKS, st, [&] {
+            return launch_best_rotation(maps, nb, j0, d_w, pr.nvox(), d_best, d_best_index, j0 == 0,
+                                        st, &plan->launches);
+        }));
+    }
+    int bad = 0;
+    TTM_CUDA_TRY(cudaMemcpyAsync(&bad, d_bad, sizeof(int), cudaMemcpyDeviceToHost, st));
+    TTM_CUDA_TRY(cudaStreamSynchronize(st));
+    return bad ? TTM_ERR_NUMERIC : TTM_OK;
+}
+
 ttm_status ttm_extract_peaks(ttm_plan_t plan, int problem, const float* d_score,
                              const float* d_quat, const float* d_lambda, float threshold,
                              int radius, int max_peaks, ttm_peak* h_out, int* n_out,

@@ -152,6 +152,11 @@ ttm_status launch_fft_inverse_yx(float2* prod, int K, int X, int Y, int Z, const
 ttm_status launch_template_spectra(const float* comp, int K, int s, const FftShape& S,
                                    float* pad, float2* tspec, cudaStream_t st, long long* cnt);
 
+// classical comparator
+ttm_status launch_best_rotation(const float* corr, int nb, int j0, const float* w, size_t nvox,
+                                float* best, int* best_j, bool first, cudaStream_t st,
+                                long long* cnt);
+
 // peaks
 size_t peak_record_bytes();
 ttm_status launch_peak_candidates_full(const float* score, const float* quat, const float* lam,

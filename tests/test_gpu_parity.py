@@ -289,3 +289,35 @@ def test_gpu_argument_errors(ttm):
         ttm.ttm_correlate(mt.plan, [vol], mt.w, mt.score, [bad_q], None, None, mt.ws)
     assert e.value.status == -1
     mt.close()
+
+
+def test_classical_comparator_matches_oracle(ttm, c1_oracle):
+    """Algorithm 1 over a rotation set on the GPU against the oracle's
+    classical NCC: the maximum over rotations to 1e-4, and the arg-max either
+    equal or a rotation whose NCC reaches the maximum within 1e-4."""
+    import torch
+    wl = c1_oracle["wl"]
+    q = synth.shoemake_quaternions(40, 4).astype(np.float32)
+    X = Y = Z = 64
+    m = ttm.Matcher([(c1_oracle["comp"], c1_oracle["desc"], wl.mask)], [((X, Y, Z), 0)],
+                    opts=_opts(ttm, "fft"))
+    vol = _cuda(wl.volume)
+    m.run([vol])
+    best = torch.empty((Z, Y, X), dtype=torch.float32, device="cuda")
+    arg = torch.empty((Z, Y, X), dtype=torch.int32, device="cuda")
+    ws = torch.empty(ttm.ttm_classical_workspace_size(m.plan, 0), dtype=torch.uint8, device="cuda")
+    ttm.ttm_classical_ncc(m.plan, 0, _cuda(wl.template), _cuda(q), len(q), vol, m.w[0], best, arg, ws)
+    torch.cuda.synchronize()
+    best, arg = best.cpu().numpy(), arg.cpu().numpy()
+    cj = o.classical_ncc(wl.volume, wl.template, wl.mask, q.astype(np.float64))
+    keep = o.interior_mask(wl.volume.shape, 15)
+    best_o = np.where(keep, cj.max(axis=0), 0.0)
+    assert np.abs(best - best_o).max() <= TOL
+    assert np.all(arg[~keep] == 0)
+    zi, yi, xi = np.nonzero(keep)
+    c_at = cj[arg[zi, yi, xi], zi, yi, xi]
+    assert np.all(c_at >= best_o[zi, yi, xi] - TOL)
+    srt = np.sort(cj[:, zi, yi, xi], axis=0)
+    unique = srt[-1] - srt[-2] > 2 * TOL
+    assert np.all(arg[zi, yi, xi][unique] == cj[:, zi, yi, xi].argmax(axis=0)[unique])
+    m.close()
