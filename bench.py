@@ -64,6 +64,10 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c2s"])
     ap.add_argument("--path", default="auto", choices=["auto", "direct", "fft"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "mixed"],
+                    help="storage of spectra/products/correlation maps on the FFT path")
+    ap.add_argument("--mixed-compare", action=argparse.BooleanOptionalAction, default=True,
+                    help="with fp32, also time the mixed-precision plan on the same volume")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--classical", action=argparse.BooleanOptionalAction, default=True,
@@ -266,6 +270,7 @@ def run_ours(args) -> None:
     build_ms = ev0.elapsed_time(ev1)
     opts = ttm.PlanOpts()
     opts.path = {"auto": 0, "direct": 1, "fft": 2}[args.path]
+    opts.precision = ttm.TTM_PREC_MIXED if args.precision == "mixed" else ttm.TTM_PREC_FP32
     matcher = ttm.Matcher([(comp, desc, wl.mask)], [((X, Y, Z), 0)], opts=opts)
     path = ttm.ttm_plan_problem_path(matcher.plan, 0)
     vol = torch.from_numpy(wl.volume).to(dev)
@@ -365,6 +370,33 @@ def run_ours(args) -> None:
                               "multiply, inverse FFT, running max) vs TTM score+rotation maps")
         del cws, best, barg
 
+    # the other precision on the same volume (bf16 storage), for the FP32 vs
+    # BF16 comparison of the metric
+    mixed = None
+    if args.mixed_compare and args.precision == "fp32" and path == 2:
+        o2 = ttm.PlanOpts()
+        o2.path = opts.path
+        o2.precision = ttm.TTM_PREC_MIXED
+        m2 = ttm.Matcher([(comp, desc, wl.mask)], [((X, Y, Z), 0)], opts=o2)
+        for _ in range(args.warmup):
+            m2.run([vol])
+        torch.cuda.synchronize()
+        m_ms = 0.0
+        for k in range(args.steps):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            m2.run([vol])
+            b.record(stream)
+            b.synchronize()
+            m_ms += a.elapsed_time(b)
+        dscore = float((m2.score[0] - matcher.score[0]).abs().max())
+        dlam = float((m2.lam[0] - matcher.lam[0]).abs().max())
+        mixed = dict(value=nvox * args.steps * world / (m_ms * 1e-3), unit=UNIT,
+                     ms_per_step=m_ms / args.steps, storage="bf16 spectra, products, maps",
+                     max_abs_diff_vs_fp32=dict(score=dscore, **{"lambda": dlam}))
+        m2.close()
+
     if rank != 0:
         if dist:
             dist.destroy_process_group()
@@ -384,13 +416,15 @@ def run_ours(args) -> None:
     line = dict(
         metric=METRIC, value=value, unit=UNIT, n_gpus=world, steps=args.steps,
         warmup=args.warmup, ms_per_step=t_max / args.steps, higher_is_better=True,
-        scaling="weak", vs_baseline=None, dtype="f32", data="synthetic",
+        scaling="weak", vs_baseline=None, dtype="f32" if args.precision == "fp32" else "bf16/f32",
+        data="synthetic",
         config=dict(workload=WORKLOAD[args.workload], path={1: "direct", 2: "fft"}.get(path, path),
                     voxels=nvox, tensor_order=wl.n_order, K=desc.K, mask_voxels=n_taps,
                     rotation_grid=2048, l2="flushed (256 MB write) before every timed step",
                     parallelism="replicas" if world > 1 else "single GPU",
                     template_build_ms=round(build_ms, 2), quadrature_rotations=desc.n_rot),
         roofline=rf, cpu_baseline=cpu, e2e=e2e, gpu_launches=launches, classical=classical,
+        mixed_precision=mixed,
         clocks=clk,
         kernels={k: dict(ms_per_step=round(v["ms"] / args.steps, 4),
                          launches_per_step=v["launches"] / args.steps,

@@ -88,9 +88,14 @@ typedef struct ttm_peak {
 #define TTM_PATH_DIRECT 1   /* direct sum over the mask support                */
 #define TTM_PATH_FFT    2   /* FFT with the fused K-way spectrum multiply      */
 
-/* Precision of the correlation step. */
-#define TTM_PREC_FP32   0   /* FP32 throughout                                 */
-#define TTM_PREC_MIXED  1   /* FP16/BF16 storage or products, FP32 accumulate  */
+/* Precision of the correlation step.  In both modes all arithmetic is FP32
+ * except the rotation search of order 4, which runs on the tensor cores with
+ * FP16 operands and FP32 accumulation.  TTM_PREC_MIXED stores the template
+ * spectra, the K product spectra and the K correlation maps of the FFT path
+ * in bf16 (half the memory and traffic; FFT lengths 16..1024, other problems
+ * stay FP32).  Expected error vs FP32: |dC|, |dscore|, |dlambda| <= 5e-3. */
+#define TTM_PREC_FP32   0
+#define TTM_PREC_MIXED  1
 
 typedef struct ttm_plan_opts {
     int path;           /* TTM_PATH_*                                          */

@@ -16,6 +16,10 @@
 //                 in shared memory while the K component tiles stream through
 //   rows_c2r      half-spectrum rows -> real x lines (Hermitian extension)
 // Twiddles exp(-2 pi i k / L) come from a table computed on the host in FP64.
+#include <cuda_bf16.h>
+
+#include <type_traits>
+
 #include "ttm_internal.h"
 
 namespace ttm {
@@ -37,6 +41,17 @@ __device__ __forceinline__ float2 cmulc(float2 a, float2 b) {   // a * conj(b)
     return make_float2(a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y);
 }
 __device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+
+// Storage types of spectra (float2 or bf16 pairs) and real maps (float or
+// bf16); arithmetic is always FP32.
+__device__ __forceinline__ float2 ldc(const float2* p) { return *p; }
+__device__ __forceinline__ float2 ldc(const __nv_bfloat162* p) { return __bfloat1622float2(*p); }
+__device__ __forceinline__ float2 ldgc(const float2* p) { return __ldg(p); }
+__device__ __forceinline__ float2 ldgc(const __nv_bfloat162* p) { return __bfloat1622float2(__ldg(p)); }
+__device__ __forceinline__ void stc(float2* p, float2 v) { *p = v; }
+__device__ __forceinline__ void stc(__nv_bfloat162* p, float2 v) { *p = __float22bfloat162_rn(v); }
+__device__ __forceinline__ void str(float* p, float v) { *p = v; }
+__device__ __forceinline__ void str(__nv_bfloat16* p, float v) { *p = __float2bfloat16_rn(v); }
 __device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
 
 // NB independent transforms of length L stored as buf[i * pitch + b].  The
@@ -453,8 +468,8 @@ __global__ void __launch_bounds__(kFftThreads) rows_r2c_t(const float* __restric
     }
 }
 
-template <int L, int SIGN>
-__global__ void __launch_bounds__(kFftThreads) cols_t(float2* __restrict__ data, int B,
+template <int L, int SIGN, typename PS>
+__global__ void __launch_bounds__(kFftThreads) cols_t(PS* __restrict__ data, int B,
                                                       const float2* __restrict__ tw) {
     constexpr int TB = cols_tb<L>();
     extern __shared__ float2 sm[];
@@ -469,7 +484,7 @@ __global__ void __launch_bounds__(kFftThreads) cols_t(float2* __restrict__ data,
     for (int i = 0; i < PER; ++i) {          // all loads in flight before any store
         const int e = threadIdx.x + i * kFftThreads;
         const int l = e / TB, bb = e & (TB - 1);
-        v[i] = (e < L * TB && bb < tb) ? data[base + (size_t)l * B + b0 + bb] : make_float2(0.f, 0.f);
+        v[i] = (e < L * TB && bb < tb) ? ldc(data + base + (size_t)l * B + b0 + bb) : make_float2(0.f, 0.f);
     }
 #pragma unroll
     for (int i = 0; i < PER; ++i) {
@@ -482,14 +497,14 @@ __global__ void __launch_bounds__(kFftThreads) cols_t(float2* __restrict__ data,
     for (int i = 0; i < PER; ++i) {
         const int e = threadIdx.x + i * kFftThreads;
         const int l = e / TB, bb = e & (TB - 1);
-        if (e < L * TB && bb < tb) data[base + (size_t)l * B + b0 + bb] = res[e];
+        if (e < L * TB && bb < tb) stc(data + base + (size_t)l * B + b0 + bb, res[e]);
     }
 }
 
-template <int L>
+template <int L, typename TS, typename PS>
 __global__ void __launch_bounds__(kFftThreads) cols_mul_t(const float2* __restrict__ spec,
-                                                          const float2* __restrict__ tspec,
-                                                          float2* __restrict__ out, int B, int K,
+                                                          const TS* __restrict__ tspec,
+                                                          PS* __restrict__ out, int B, int K,
                                                           const float2* __restrict__ tw) {
     constexpr int TB = cols_tb<L>();
     extern __shared__ float2 sm[];
@@ -513,7 +528,7 @@ __global__ void __launch_bounds__(kFftThreads) cols_mul_t(const float2* __restri
     for (int i = 0; i < PER; ++i) {
         const int e = threadIdx.x + i * kFftThreads;
         const int l = e / TB, bb = e & (TB - 1);
-        tv[i] = (K > 0 && e < L * TB && bb < tb) ? __ldg(tspec + (size_t)l * B + b0 + bb)
+        tv[i] = (K > 0 && e < L * TB && bb < tb) ? ldgc(tspec + (size_t)l * B + b0 + bb)
                                                   : make_float2(0.f, 0.f);
     }
     for (int k = 0; k < K; ++k) {
@@ -524,30 +539,30 @@ __global__ void __launch_bounds__(kFftThreads) cols_mul_t(const float2* __restri
             if (e < L * TB) P[e] = cmulc(fi[i], tv[i]);
         }
         if (k + 1 < K) {
-            const float2* ts = tspec + (size_t)(k + 1) * plane;
+            const TS* ts = tspec + (size_t)(k + 1) * plane;
 #pragma unroll
             for (int i = 0; i < PER; ++i) {
                 const int e = threadIdx.x + i * kFftThreads;
                 const int l = e / TB, bb = e & (TB - 1);
-                tv[i] = (e < L * TB && bb < tb) ? __ldg(ts + (size_t)l * B + b0 + bb)
+                tv[i] = (e < L * TB && bb < tb) ? ldgc(ts + (size_t)l * B + b0 + bb)
                                                  : make_float2(0.f, 0.f);
             }
         }
         __syncthreads();
         float2* res = fft_lines_t<L, TB, TB, +1>(P, Q, tw);
-        float2* o = out + (size_t)k * plane;
+        PS* o = out + (size_t)k * plane;
 #pragma unroll
         for (int i = 0; i < PER; ++i) {
             const int e = threadIdx.x + i * kFftThreads;
             const int l = e / TB, bb = e & (TB - 1);
-            if (e < L * TB && bb < tb) o[(size_t)l * B + b0 + bb] = res[e];
+            if (e < L * TB && bb < tb) stc(o + (size_t)l * B + b0 + bb, res[e]);
         }
     }
 }
 
-template <int L>
-__global__ void __launch_bounds__(kFftThreads) rows_c2r_t(const float2* __restrict__ in, int X, int Y,
-                                                          int Z, FftGeom g, float* __restrict__ out,
+template <int L, typename PS, typename RT>
+__global__ void __launch_bounds__(kFftThreads) rows_c2r_t(const PS* __restrict__ in, int X, int Y,
+                                                          int Z, FftGeom g, RT* __restrict__ out,
                                                           int n_batch, const float2* __restrict__ tw) {
     constexpr int NB = rows_nb<L>();
     constexpr int PITCH = NB + 1;
@@ -579,9 +594,9 @@ __global__ void __launch_bounds__(kFftThreads) rows_c2r_t(const float2* __restri
         const size_t row = row0 + r;
         v[i] = make_float2(0.f, 0.f);
         if (e < NB * L && row < nrows) {
-            const float2* src = in + row * XH;
-            if (x < XH) v[i] = src[x];
-            else { float2 c = src[L - x]; v[i] = make_float2(c.x, -c.y); }
+            const PS* src = in + row * XH;
+            if (x < XH) v[i] = ldc(src + x);
+            else { float2 c = ldc(src + (L - x)); v[i] = make_float2(c.x, -c.y); }
         }
     }
 #pragma unroll
@@ -598,7 +613,7 @@ __global__ void __launch_bounds__(kFftThreads) rows_c2r_t(const float2* __restri
         const int r = e / L, x = e & (L - 1);
         if (e >= NB * L || x >= X) continue;
         const long long off = row_out[r];
-        if (off >= 0) out[off + x] = res[x * PITCH + r].x;
+        if (off >= 0) str(out + off + x, res[x * PITCH + r].x);
     }
 }
 
@@ -615,43 +630,46 @@ struct RunRowsR2C {
     }
 };
 
+template <typename TS, typename PS>
 struct RunColsMul {
-    const float2* spec; const float2* tspec; float2* prod; int Bz, K; const float2* tw;
+    const float2* spec; const TS* tspec; PS* prod; int Bz, K; const float2* tw;
     cudaStream_t st; cudaError_t* err;
     template <int L> void operator()() {
         constexpr int TB = cols_tb<L>();
         const size_t smem = (size_t)2 * L * TB * sizeof(float2);
-        *err = cudaFuncSetAttribute(cols_mul_t<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        *err = cudaFuncSetAttribute(cols_mul_t<L, TS, PS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         dim3 grid((Bz + TB - 1) / TB, 1);
-        cols_mul_t<L><<<grid, kFftThreads, smem, st>>>(spec, tspec, prod, Bz, K, tw);
+        cols_mul_t<L, TS, PS><<<grid, kFftThreads, smem, st>>>(spec, tspec, prod, Bz, K, tw);
     }
 };
 
+template <typename PS, typename RT>
 struct RunRowsC2R {
-    const float2* prod; int X, Y, Z; FftGeom g; float* corr; int K; const float2* tw;
+    const PS* prod; int X, Y, Z; FftGeom g; RT* corr; int K; const float2* tw;
     cudaStream_t st; cudaError_t* err;
     template <int L> void operator()() {
         constexpr int NB = rows_nb<L>();
         const size_t smem = (size_t)2 * L * (NB + 1) * sizeof(float2);
-        *err = cudaFuncSetAttribute(rows_c2r_t<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        *err = cudaFuncSetAttribute(rows_c2r_t<L, PS, RT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         const size_t nrows = (size_t)g.Yp * g.Zp * K;
-        rows_c2r_t<L><<<(unsigned)((nrows + NB - 1) / NB), kFftThreads, smem, st>>>(
+        rows_c2r_t<L, PS, RT><<<(unsigned)((nrows + NB - 1) / NB), kFftThreads, smem, st>>>(
             prod, X, Y, Z, g, corr, K, tw);
     }
 };
 
+template <typename PS>
 struct RunCols {
-    float2* d; int B, na; const float2* tw; int sign; cudaStream_t st; cudaError_t* err;
+    PS* d; int B, na; const float2* tw; int sign; cudaStream_t st; cudaError_t* err;
     template <int LL> void operator()() {
         constexpr int TB = cols_tb<LL>();
         const size_t smem = (size_t)2 * LL * TB * sizeof(float2);
         dim3 grid((B + TB - 1) / TB, na);
         if (sign < 0) {
-            *err = cudaFuncSetAttribute(cols_t<LL, -1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            cols_t<LL, -1><<<grid, kFftThreads, smem, st>>>(d, B, tw);
+            *err = cudaFuncSetAttribute(cols_t<LL, -1, PS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            cols_t<LL, -1, PS><<<grid, kFftThreads, smem, st>>>(d, B, tw);
         } else {
-            *err = cudaFuncSetAttribute(cols_t<LL, +1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            cols_t<LL, +1><<<grid, kFftThreads, smem, st>>>(d, B, tw);
+            *err = cudaFuncSetAttribute(cols_t<LL, +1, PS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            cols_t<LL, +1, PS><<<grid, kFftThreads, smem, st>>>(d, B, tw);
         }
     }
 };
@@ -696,24 +714,33 @@ int cols_per_cta(int L) {
 }  // namespace
 
 // Column lines (length L, element stride B) of `batch` consecutive blocks.
-static ttm_status launch_cols(float2* data, int L, int B, int batch, const float2* tw, int sign,
-                              cudaStream_t st, long long* cnt) {
+template <typename PS>
+static ttm_status launch_cols_t(PS* data, int L, int B, int batch, const float2* tw, int sign,
+                                cudaStream_t st, long long* cnt) {
     for (int a0 = 0; a0 < batch; a0 += 65535) {
         const int na = batch - a0 < 65535 ? batch - a0 : 65535;
-        float2* d = data + (size_t)a0 * L * B;
+        PS* d = data + (size_t)a0 * L * B;
         cudaError_t err = cudaSuccess;
-        RunCols run{d, B, na, tw, sign, st, &err};
+        RunCols<PS> run{d, B, na, tw, sign, st, &err};
         if (!with_length(L, run)) {
-            const int TB = cols_per_cta(L);
-            const size_t smem = (size_t)2 * L * TB * sizeof(float2);
-            TTM_CUDA_TRY(cudaFuncSetAttribute(cols_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-            dim3 grid((B + TB - 1) / TB, na);
-            cols_kernel<<<grid, kFftThreads, smem, st>>>(d, L, B, radices_for(L), tw, TB, sign);
+            if constexpr (!std::is_same<PS, float2>::value) return TTM_ERR_UNSUPPORTED;
+            else {
+                const int TB = cols_per_cta(L);
+                const size_t smem = (size_t)2 * L * TB * sizeof(float2);
+                TTM_CUDA_TRY(cudaFuncSetAttribute(cols_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+                dim3 grid((B + TB - 1) / TB, na);
+                cols_kernel<<<grid, kFftThreads, smem, st>>>(d, L, B, radices_for(L), tw, TB, sign);
+            }
         }
         TTM_CUDA_TRY(err);
         TTM_TRY(after_launch(cnt));
     }
     return TTM_OK;
+}
+
+static ttm_status launch_cols(float2* data, int L, int B, int batch, const float2* tw, int sign,
+                              cudaStream_t st, long long* cnt) {
+    return launch_cols_t<float2>(data, L, B, batch, tw, sign, st, cnt);
 }
 
 bool fft_length_ok(int L) { return L >= 2 && L <= 4096 && (L & (L - 1)) == 0; }
@@ -748,40 +775,86 @@ ttm_status launch_fft_forward(const float* f, int X, int Y, int Z, const FftShap
     return TTM_OK;
 }
 
-ttm_status launch_fft_spectrum_inverse_z(const float2* spec, const float2* tspec, int K,
-                                         const FftShape& S, float2* prod, cudaStream_t st,
-                                         long long* cnt) {
+template <typename TS, typename PS>
+static ttm_status spectrum_inverse_z_t(const float2* spec, const TS* tspec, int K, const FftShape& S,
+                                       PS* prod, cudaStream_t st, long long* cnt) {
     const int Xh = S.Xp / 2 + 1;
     const int Bz = S.Yp * Xh;
     cudaError_t err = cudaSuccess;
-    RunColsMul run{spec, tspec, prod, Bz, K, S.d_tw_z, st, &err};
+    RunColsMul<TS, PS> run{spec, tspec, prod, Bz, K, S.d_tw_z, st, &err};
     if (!with_length(S.Zp, run)) {
-        const int TB = cols_per_cta(S.Zp);
-        const size_t smem = (size_t)3 * S.Zp * TB * sizeof(float2);
-        TTM_CUDA_TRY(cudaFuncSetAttribute(cols_mul_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        dim3 grid((Bz + TB - 1) / TB, 1);
-        cols_mul_kernel<<<grid, kFftThreads, smem, st>>>(spec, tspec, prod, S.Zp, Bz, K,
-                                                         radices_for(S.Zp), S.d_tw_z, TB);
+        if constexpr (!std::is_same<TS, float2>::value || !std::is_same<PS, float2>::value)
+            return TTM_ERR_UNSUPPORTED;
+        else {
+            const int TB = cols_per_cta(S.Zp);
+            const size_t smem = (size_t)3 * S.Zp * TB * sizeof(float2);
+            TTM_CUDA_TRY(cudaFuncSetAttribute(cols_mul_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            dim3 grid((Bz + TB - 1) / TB, 1);
+            cols_mul_kernel<<<grid, kFftThreads, smem, st>>>(spec, tspec, prod, S.Zp, Bz, K,
+                                                             radices_for(S.Zp), S.d_tw_z, TB);
+        }
     }
     TTM_CUDA_TRY(err);
     return after_launch(cnt);
 }
 
-ttm_status launch_fft_inverse_yx(float2* prod, int K, int X, int Y, int Z, const FftShape& S,
-                                 float* corr, cudaStream_t st, long long* cnt) {
+template <typename PS, typename RT>
+static ttm_status inverse_yx_t(PS* prod, int K, int X, int Y, int Z, const FftShape& S, RT* corr,
+                               cudaStream_t st, long long* cnt) {
     FftGeom g{S.Xp, S.Yp, S.Zp, S.Xp / 2 + 1};
-    TTM_TRY(launch_cols(prod, S.Yp, g.Xh, K * S.Zp, S.d_tw_y, +1, st, cnt));   // y lines, all components
+    TTM_TRY(launch_cols_t<PS>(prod, S.Yp, g.Xh, K * S.Zp, S.d_tw_y, +1, st, cnt));
     cudaError_t err = cudaSuccess;
-    RunRowsC2R run{prod, X, Y, Z, g, corr, K, S.d_tw_x, st, &err};
+    RunRowsC2R<PS, RT> run{prod, X, Y, Z, g, corr, K, S.d_tw_x, st, &err};
     if (!with_length(S.Xp, run)) {
-        const int NB = rows_per_cta(S.Xp);
-        const size_t smem = (size_t)2 * S.Xp * (NB + 1) * sizeof(float2);
-        TTM_CUDA_TRY(cudaFuncSetAttribute(rows_c2r_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        const size_t nrows = (size_t)S.Yp * S.Zp * K;
-        rows_c2r_kernel<<<(unsigned)((nrows + NB - 1) / NB), kFftThreads, smem, st>>>(
-            prod, X, Y, Z, g, corr, K, radices_for(S.Xp), S.d_tw_x, NB);
+        if constexpr (!std::is_same<PS, float2>::value || !std::is_same<RT, float>::value)
+            return TTM_ERR_UNSUPPORTED;
+        else {
+            const int NB = rows_per_cta(S.Xp);
+            const size_t smem = (size_t)2 * S.Xp * (NB + 1) * sizeof(float2);
+            TTM_CUDA_TRY(cudaFuncSetAttribute(rows_c2r_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            const size_t nrows = (size_t)S.Yp * S.Zp * K;
+            rows_c2r_kernel<<<(unsigned)((nrows + NB - 1) / NB), kFftThreads, smem, st>>>(
+                prod, X, Y, Z, g, corr, K, radices_for(S.Xp), S.d_tw_x, NB);
+        }
     }
     TTM_CUDA_TRY(err);
+    return after_launch(cnt);
+}
+
+ttm_status launch_fft_spectrum_inverse_z(const float2* spec, const float2* tspec, int K,
+                                         const FftShape& S, float2* prod, cudaStream_t st,
+                                         long long* cnt) {
+    return spectrum_inverse_z_t<float2, float2>(spec, tspec, K, S, prod, st, cnt);
+}
+
+ttm_status launch_fft_inverse_yx(float2* prod, int K, int X, int Y, int Z, const FftShape& S,
+                                 float* corr, cudaStream_t st, long long* cnt) {
+    return inverse_yx_t<float2, float>(prod, K, X, Y, Z, S, corr, st, cnt);
+}
+
+// mixed precision: bf16 template spectra, products and correlation maps
+ttm_status launch_fft_spectrum_inverse_z_bf16(const float2* spec, const void* tspec, int K,
+                                              const FftShape& S, void* prod, cudaStream_t st,
+                                              long long* cnt) {
+    return spectrum_inverse_z_t<__nv_bfloat162, __nv_bfloat162>(
+        spec, reinterpret_cast<const __nv_bfloat162*>(tspec), K, S,
+        reinterpret_cast<__nv_bfloat162*>(prod), st, cnt);
+}
+
+ttm_status launch_fft_inverse_yx_bf16(void* prod, int K, int X, int Y, int Z, const FftShape& S,
+                                      void* corr, cudaStream_t st, long long* cnt) {
+    return inverse_yx_t<__nv_bfloat162, __nv_bfloat16>(
+        reinterpret_cast<__nv_bfloat162*>(prod), K, X, Y, Z, S,
+        reinterpret_cast<__nv_bfloat16*>(corr), st, cnt);
+}
+
+__global__ void to_bf16_kernel(const float2* __restrict__ a, __nv_bfloat162* __restrict__ b, size_t n) {
+    size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) b[i] = __float22bfloat162_rn(a[i]);
+}
+
+ttm_status launch_spectra_to_bf16(const float2* a, void* b, size_t n, cudaStream_t st, long long* cnt) {
+    to_bf16_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(a, reinterpret_cast<__nv_bfloat162*>(b), n);
     return after_launch(cnt);
 }
 

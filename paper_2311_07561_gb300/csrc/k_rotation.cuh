@@ -16,6 +16,8 @@
 // Newton steps on the sphere, each accepted only if phi does not decrease
 // (otherwise the power step is taken).  The largest refined value wins.
 #pragma once
+#include <cuda_bf16.h>
+
 #include "ttm_internal.h"
 
 namespace ttm {
@@ -26,8 +28,12 @@ constexpr int kRotThreads = 128;
 constexpr int kChunk = 128;       // grid points staged per step
 constexpr int kMaxCand = 8;
 
+// correlation maps are float or bf16 (mixed precision)
+__device__ __forceinline__ float ldcorr(const float* p) { return __ldg(p); }
+__device__ __forceinline__ float ldcorr(const __nv_bfloat16* p) { return __bfloat162float(__ldg(p)); }
+
 struct SearchArgs {
-    const float* corr;      // K x nvox
+    const void* corr;       // K x nvox, float or bf16
     const float* w;
     size_t nvox;
     float* score;
@@ -38,7 +44,7 @@ struct SearchArgs {
 };
 
 struct PolishArgs {
-    const float* corr;
+    const void* corr;       // K x nvox, float or bf16
     const float* w;
     size_t nvox;
     const float* score;
@@ -254,8 +260,9 @@ __device__ void refine(const float (&C)[Geo<N>::K4], float sigma, int newton, fl
 // point, best point of each region, the n_cand best regions -> candidate grid
 // indices (0xFFFF = none).  One thread per voxel; the grid table is staged in
 // shared memory and read as broadcasts.
-template <int N>
+template <int N, typename CT>
 __global__ void __launch_bounds__(kRotThreads) search_simt_kernel(SearchArgs a) {
+    const CT* corr = reinterpret_cast<const CT*>(a.corr);
     constexpr int K = Geo<N>::K;
     constexpr int K4 = Geo<N>::K4;
     constexpr Sym<N> S{};
@@ -272,7 +279,7 @@ __global__ void __launch_bounds__(kRotThreads) search_simt_kernel(SearchArgs a) 
     float ss = 0.f;
 #pragma unroll
     for (int k = 0; k < K; ++k) {
-        float c = in_range ? wv * __ldg(a.corr + (size_t)k * a.nvox + v) : 0.f;
+        float c = in_range ? wv * ldcorr(corr + (size_t)k * a.nvox + v) : 0.f;
         C[k] = c;
         ss = fmaf((float)S.mu[k], c * c, ss);
     }
@@ -319,8 +326,9 @@ __global__ void __launch_bounds__(kRotThreads) search_simt_kernel(SearchArgs a) 
 
 // Refinement of the candidates and the outputs: lambda = the largest refined
 // phi, q its maximiser (canonical sign), C_alpha optionally.
-template <int N>
+template <int N, typename CT>
 __global__ void __launch_bounds__(kRotThreads) polish_kernel(PolishArgs a) {
+    const CT* corr = reinterpret_cast<const CT*>(a.corr);
     constexpr int K = Geo<N>::K;
     constexpr int K4 = Geo<N>::K4;
     const size_t v = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -331,7 +339,7 @@ __global__ void __launch_bounds__(kRotThreads) polish_kernel(PolishArgs a) {
     for (int k = 0; k < K4; ++k) C[k] = 0.f;
 #pragma unroll
     for (int k = 0; k < K; ++k) {
-        float c = wv * __ldg(a.corr + (size_t)k * a.nvox + v);
+        float c = wv * ldcorr(corr + (size_t)k * a.nvox + v);
         C[k] = c;
         if (a.comp_out) a.comp_out[(size_t)k * a.nvox + v] = c;
     }
@@ -371,32 +379,39 @@ __global__ void __launch_bounds__(kRotThreads) polish_kernel(PolishArgs a) {
 }
 
 // search_done: run only the refinement; search_only: run only the SIMT search
-template <int N>
-ttm_status launch_n(const SearchArgs& s, const PolishArgs& p, bool search_done, bool search_only,
-                    cudaStream_t st, long long* cnt) {
+template <int N, typename CT>
+ttm_status launch_n_t(const SearchArgs& s, const PolishArgs& p, bool search_done, bool search_only,
+                      cudaStream_t st, long long* cnt) {
     const unsigned blocks = (unsigned)((s.nvox + kRotThreads - 1) / kRotThreads);
     if (!search_done) {
         const size_t smem = (size_t)kChunk * Geo<N>::K4 * sizeof(float) + kChunk * sizeof(int);
-        TTM_CUDA_TRY(cudaFuncSetAttribute(search_simt_kernel<N>,
+        TTM_CUDA_TRY(cudaFuncSetAttribute(search_simt_kernel<N, CT>,
                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        search_simt_kernel<N><<<blocks, kRotThreads, smem, st>>>(s);
+        search_simt_kernel<N, CT><<<blocks, kRotThreads, smem, st>>>(s);
         TTM_TRY(after_launch(cnt));
     }
     if (search_only) return TTM_OK;
-    polish_kernel<N><<<blocks, kRotThreads, 0, st>>>(p);
+    polish_kernel<N, CT><<<blocks, kRotThreads, 0, st>>>(p);
     return after_launch(cnt);
+}
+
+template <int N>
+ttm_status launch_n(const SearchArgs& s, const PolishArgs& p, bool search_done, bool search_only,
+                    bool bf16, cudaStream_t st, long long* cnt) {
+    return bf16 ? launch_n_t<N, __nv_bfloat16>(s, p, search_done, search_only, st, cnt)
+                : launch_n_t<N, float>(s, p, search_done, search_only, st, cnt);
 }
 
 }  // namespace rot
 
 template <int N>
 ttm_status launch_rotation_n(const rot::SearchArgs& s, const rot::PolishArgs& p, bool search_done,
-                             bool search_only, cudaStream_t st, long long* cnt);
+                             bool search_only, bool bf16, cudaStream_t st, long long* cnt);
 
 // tensor-core grid search for order 4 (k_search_tc.cu); returns
 // TTM_ERR_UNSUPPORTED when the grid does not have the fixed shape it needs
 ttm_status launch_search_tc4(const rot::SearchArgs& s, const uint16_t* grid_fp16,
-                             const uint32_t* end_bits, int* status, cudaStream_t st,
+                             const uint32_t* end_bits, int* status, bool bf16, cudaStream_t st,
                              long long* cnt);
 
 }  // namespace ttm

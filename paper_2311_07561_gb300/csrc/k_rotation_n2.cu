@@ -5,9 +5,9 @@ namespace ttm {
 
 template <>
 ttm_status launch_rotation_n<2>(const rot::SearchArgs& s, const rot::PolishArgs& p,
-                                  bool search_done, bool search_only, cudaStream_t st,
-                                  long long* cnt) {
-    return rot::launch_n<2>(s, p, search_done, search_only, st, cnt);
+                                  bool search_done, bool search_only, bool bf16,
+                                  cudaStream_t st, long long* cnt) {
+    return rot::launch_n<2>(s, p, search_done, search_only, bf16, st, cnt);
 }
 
 }  // namespace ttm

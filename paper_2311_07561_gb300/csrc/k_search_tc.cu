@@ -133,6 +133,7 @@ __device__ __forceinline__ void tmem_ld32(uint32_t addr, uint32_t (&r)[32]) {
     asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
 }
 
+template <typename CT>
 __global__ void __launch_bounds__(kThreads, 1) search_tc4_kernel(rot::SearchArgs a,
                                                                  const uint4* __restrict__ gtab,
                                                                  const uint32_t* __restrict__ ends,
@@ -186,7 +187,7 @@ __global__ void __launch_bounds__(kThreads, 1) search_tc4_kernel(rot::SearchArgs
         float ss = 0.f;
 #pragma unroll
         for (int k = 0; k < K; ++k) {
-            C[k] = in_range ? wv * __ldg(a.corr + (size_t)k * a.nvox + v) : 0.f;
+            C[k] = in_range ? wv * rot::ldcorr(reinterpret_cast<const CT*>(a.corr) + (size_t)k * a.nvox + v) : 0.f;
             ss = fmaf((float)S.mu[k], C[k] * C[k], ss);
         }
         score = sqrtf(ss);
@@ -302,20 +303,28 @@ __global__ void __launch_bounds__(kThreads, 1) search_tc4_kernel(rot::SearchArgs
 
 }  // namespace
 
-ttm_status launch_search_tc4(const rot::SearchArgs& s, const uint16_t* grid_fp16,
-                             const uint32_t* end_bits, int* status, cudaStream_t st,
-                             long long* cnt) {
-    if (s.n_grid != kG || !grid_fp16 || !end_bits) return TTM_ERR_UNSUPPORTED;
-    TTM_CUDA_TRY(cudaFuncSetAttribute(search_tc4_kernel,
+template <typename CT>
+static ttm_status launch_tc4_t(const rot::SearchArgs& s, const uint16_t* grid_fp16,
+                               const uint32_t* end_bits, int* status, cudaStream_t st,
+                               long long* cnt) {
+    TTM_CUDA_TRY(cudaFuncSetAttribute(search_tc4_kernel<CT>,
                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem));
     int dev = 0, sms = 0;
     TTM_CUDA_TRY(cudaGetDevice(&dev));
     TTM_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     const size_t ntiles = (s.nvox + 127) / 128;
     const unsigned grid = (unsigned)(ntiles < (size_t)sms ? ntiles : (size_t)sms);
-    search_tc4_kernel<<<grid, kThreads, kSmem, st>>>(s, reinterpret_cast<const uint4*>(grid_fp16),
-                                                     end_bits, status);
+    search_tc4_kernel<CT><<<grid, kThreads, kSmem, st>>>(s, reinterpret_cast<const uint4*>(grid_fp16),
+                                                         end_bits, status);
     return after_launch(cnt);
+}
+
+ttm_status launch_search_tc4(const rot::SearchArgs& s, const uint16_t* grid_fp16,
+                             const uint32_t* end_bits, int* status, bool bf16, cudaStream_t st,
+                             long long* cnt) {
+    if (s.n_grid != kG || !grid_fp16 || !end_bits) return TTM_ERR_UNSUPPORTED;
+    return bf16 ? launch_tc4_t<__nv_bfloat16>(s, grid_fp16, end_bits, status, st, cnt)
+                : launch_tc4_t<float>(s, grid_fp16, end_bits, status, st, cnt);
 }
 
 // FP16 grid table in the kernel's shared-memory layout: element (g, k) of the

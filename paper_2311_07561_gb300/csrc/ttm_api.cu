@@ -249,35 +249,54 @@ ttm_status prepare_fft(ttm_plan_s* P, ProblemData& pr, cudaStream_t st) {
     pr.fft.d_tw_z = twiddle_table(P, pr.fft.Zp, &err); TTM_TRY(err);
     for (size_t i = 0; i < P->specs.size(); ++i) {
         const SpecSet& sp = P->specs[i];
-        if (sp.tmpl == pr.tmpl && sp.Xp == pr.fft.Xp && sp.Yp == pr.fft.Yp && sp.Zp == pr.fft.Zp) {
+        if (sp.tmpl == pr.tmpl && sp.Xp == pr.fft.Xp && sp.Yp == pr.fft.Yp && sp.Zp == pr.fft.Zp &&
+            sp.mixed == pr.mixed) {
             pr.spec_index = (int)i;
             return TTM_OK;
         }
     }
     const TemplateData& T = P->tmpl[pr.tmpl];
     SpecSet sp;
-    sp.tmpl = pr.tmpl; sp.Xp = pr.fft.Xp; sp.Yp = pr.fft.Yp; sp.Zp = pr.fft.Zp;
+    sp.tmpl = pr.tmpl; sp.Xp = pr.fft.Xp; sp.Yp = pr.fft.Yp; sp.Zp = pr.fft.Zp; sp.mixed = pr.mixed;
     const size_t nspec = pr.fft.nspec();
     const size_t nreal = (size_t)pr.fft.Xp * pr.fft.Yp * pr.fft.Zp;
-    // K component spectra and, last, the mask spectrum (local statistics)
-    if (cudaMalloc((void**)&sp.d_spec, (size_t)(P->K + 1) * nspec * sizeof(float2)) != cudaSuccess) {
-        cudaGetLastError();
-        return TTM_ERR_OUT_OF_MEMORY;
+    const size_t s3 = (size_t)T.desc.s * T.desc.s * T.desc.s;
+    bool oom = cudaMalloc((void**)&sp.d_mask_spec, nspec * sizeof(float2)) != cudaSuccess;
+    if (!oom) {
+        if (pr.mixed)
+            oom = cudaMalloc(&sp.d_spec_bf, (size_t)P->K * nspec * 4) != cudaSuccess;
+        else
+            oom = cudaMalloc((void**)&sp.d_spec, (size_t)P->K * nspec * sizeof(float2)) != cudaSuccess;
     }
-    P->specs.push_back(sp);
+    P->specs.push_back(sp);   // freed with the plan, also on failure
+    if (oom) { cudaGetLastError(); return TTM_ERR_OUT_OF_MEMORY; }
     pr.spec_index = (int)P->specs.size() - 1;
     float* pad = nullptr;
-    if (cudaMalloc((void**)&pad, nreal * sizeof(float)) != cudaSuccess) {
+    float2* tmp = nullptr;
+    if (cudaMalloc((void**)&pad, nreal * sizeof(float)) != cudaSuccess ||
+        (pr.mixed && cudaMalloc((void**)&tmp, nspec * sizeof(float2)) != cudaSuccess)) {
         cudaGetLastError();
+        cudaFree(pad);
         return TTM_ERR_OUT_OF_MEMORY;
     }
-    ttm_status s = launch_template_spectra(T.d_comp, P->K, T.desc.s, pr.fft, pad, sp.d_spec, st,
+    ttm_status s = launch_template_spectra(T.d_mask, 1, T.desc.s, pr.fft, pad, sp.d_mask_spec, st,
                                            &P->launches);
-    if (s == TTM_OK)
-        s = launch_template_spectra(T.d_mask, 1, T.desc.s, pr.fft, pad,
-                                    sp.d_spec + (size_t)P->K * nspec, st, &P->launches);
+    if (!pr.mixed) {
+        if (s == TTM_OK)
+            s = launch_template_spectra(T.d_comp, P->K, T.desc.s, pr.fft, pad, sp.d_spec, st,
+                                        &P->launches);
+    } else {
+        for (int k = 0; k < P->K && s == TTM_OK; ++k) {
+            s = launch_template_spectra(T.d_comp + (size_t)k * s3, 1, T.desc.s, pr.fft, pad, tmp,
+                                        st, &P->launches);
+            if (s == TTM_OK)
+                s = launch_spectra_to_bf16(tmp, (char*)sp.d_spec_bf + (size_t)k * nspec * 4, nspec,
+                                           st, &P->launches);
+        }
+    }
     cudaError_t e = cudaStreamSynchronize(st);
     cudaFree(pad);
+    cudaFree(tmp);
     if (s != TTM_OK) return s;
     if (e != cudaSuccess) { cudaGetLastError(); return TTM_ERR_CUDA; }
     return TTM_OK;
@@ -326,7 +345,11 @@ void free_plan(ttm_plan_s* P) {
         cudaFree(T.d_taps);
         cudaFree(T.d_spec);
     }
-    for (SpecSet& sp : P->specs) cudaFree(sp.d_spec);
+    for (SpecSet& sp : P->specs) {
+        cudaFree(sp.d_spec);
+        cudaFree(sp.d_spec_bf);
+        cudaFree(sp.d_mask_spec);
+    }
     for (auto& t : P->twiddles) cudaFree(t.second);
     cudaFree(P->grid.d_q);
     cudaFree(P->grid.d_m);
@@ -345,10 +368,11 @@ size_t peak_cap(size_t nvox) { return std::min(nvox, (size_t)kPeakCapMax); }
 // Correlation maps first (both paths), then for the FFT path the image
 // spectrum and the K product spectra, then 8 candidate grid indices per voxel.
 size_t corr_region_bytes(const ttm_plan_s* P, const ProblemData& pr) {
-    size_t b = align256((size_t)P->K * pr.nvox() * sizeof(float));
+    const size_t es = pr.mixed ? 2 : 4;          // bytes per stored real (corr maps)
+    size_t b = align256((size_t)P->K * pr.nvox() * es);
     if (pr.path == TTM_PATH_FFT)
         b += align256(pr.fft.nspec() * sizeof(float2)) +
-             align256((size_t)P->K * pr.fft.nspec() * sizeof(float2));
+             align256((size_t)P->K * pr.fft.nspec() * 2 * es);
     return b;
 }
 
@@ -516,6 +540,13 @@ ttm_status ttm_plan(ttm_plan_t* out, int n_problems, const int* vol_dims, const 
         if (path == TTM_PATH_FFT && !fft_ok) { free_plan(P); return TTM_ERR_UNSUPPORTED; }
         if (path != TTM_PATH_FFT && path != TTM_PATH_DIRECT) { free_plan(P); return TTM_ERR_INVALID_ARG; }
         pr.path = path;
+        pr.mixed = path == TTM_PATH_FFT && P->opts.precision == TTM_PREC_MIXED &&
+                   fft_template_length(pr.fft.Xp) && fft_template_length(pr.fft.Yp) &&
+                   fft_template_length(pr.fft.Zp);
+        if (P->opts.precision != TTM_PREC_FP32 && P->opts.precision != TTM_PREC_MIXED) {
+            free_plan(P);
+            return TTM_ERR_INVALID_ARG;
+        }
         if (path == TTM_PATH_FFT) {
             s_ = prepare_fft(P, pr, st);
             if (s_ != TTM_OK) { free_plan(P); return s_; }
@@ -627,7 +658,7 @@ ttm_status ttm_local_stats(ttm_plan_t plan, const float* const* d_vols, float* c
             float2* F2 = F1 + nspec;
             float2* prod = F2 + nspec;                       // two product spectra
             float* sums = (float*)(prod + 2 * nspec);        // S1, S2 maps
-            const float2* mspec = plan->specs[pr.spec_index].d_spec + (size_t)plan->K * nspec;
+            const float2* mspec = plan->specs[pr.spec_index].d_mask_spec;
             TTM_TRY(timed(plan, KC_LOCAL_STATS, st, [&] {
                 TTM_TRY(launch_fft_forward(d_vols[p], pr.X, pr.Y, pr.Z, pr.fft, F1, st,
                                            &plan->launches, 1, d_mom));
@@ -672,21 +703,26 @@ ttm_status ttm_correlate(ttm_plan_t plan, const float* const* d_vols, const floa
         const ProblemData& pr = plan->prob[p];
         const TemplateData& T = plan->tmpl[pr.tmpl];
         if (pr.path == TTM_PATH_FFT) {
-            char* base = (char*)corr + align256((size_t)plan->K * pr.nvox() * sizeof(float));
+            const size_t es = pr.mixed ? 2 : 4;
+            char* base = (char*)corr + align256((size_t)plan->K * pr.nvox() * es);
             float2* spec = (float2*)base;
-            float2* prod = (float2*)(base + align256(pr.fft.nspec() * sizeof(float2)));
-            const float2* tspec = plan->specs[pr.spec_index].d_spec;
+            void* prod = base + align256(pr.fft.nspec() * sizeof(float2));
+            const SpecSet& sp = plan->specs[pr.spec_index];
             TTM_TRY(timed(plan, KC_FFT_FORWARD, st, [&] {
                 return launch_fft_forward(d_vols[p], pr.X, pr.Y, pr.Z, pr.fft, spec, st,
                                           &plan->launches);
             }));
             TTM_TRY(timed(plan, KC_FFT_SPECTRUM, st, [&] {
-                return launch_fft_spectrum_inverse_z(spec, tspec, plan->K, pr.fft, prod, st,
-                                                     &plan->launches);
+                return pr.mixed ? launch_fft_spectrum_inverse_z_bf16(spec, sp.d_spec_bf, plan->K,
+                                                                     pr.fft, prod, st, &plan->launches)
+                                : launch_fft_spectrum_inverse_z(spec, sp.d_spec, plan->K, pr.fft,
+                                                                (float2*)prod, st, &plan->launches);
             }));
             TTM_TRY(timed(plan, KC_FFT_INVERSE, st, [&] {
-                return launch_fft_inverse_yx(prod, plan->K, pr.X, pr.Y, pr.Z, pr.fft, corr, st,
-                                             &plan->launches);
+                return pr.mixed ? launch_fft_inverse_yx_bf16(prod, plan->K, pr.X, pr.Y, pr.Z, pr.fft,
+                                                             corr, st, &plan->launches)
+                                : launch_fft_inverse_yx((float2*)prod, plan->K, pr.X, pr.Y, pr.Z,
+                                                        pr.fft, corr, st, &plan->launches);
             }));
         } else {
             TTM_TRY(timed(plan, KC_DIRECT_CORR, st, [&] {
@@ -697,12 +733,14 @@ ttm_status ttm_correlate(ttm_plan_t plan, const float* const* d_vols, const floa
         uint16_t* cand = (uint16_t*)((char*)corr + corr_region_bytes(plan, pr));
         int* d_status = (int*)((char*)d_workspace + 32);
         TTM_TRY(timed(plan, KC_ROTATION, st, [&] {
-            return launch_rotation_search(plan->n_order, corr, d_w[p], pr.nvox(), plan->grid, cand,
-                                          d_status, d_score[p], st, &plan->launches);
+            return launch_rotation_search(plan->n_order, corr, pr.mixed, d_w[p], pr.nvox(),
+                                          plan->grid, cand, d_status, d_score[p], st,
+                                          &plan->launches);
         }));
         TTM_TRY(timed(plan, KC_POLISH, st, [&] {
-            return launch_rotation_polish(plan->n_order, corr, d_w[p], pr.nvox(), plan->grid, cand,
-                                          d_score[p], d_quat[p], d_lambda ? d_lambda[p] : nullptr,
+            return launch_rotation_polish(plan->n_order, corr, pr.mixed, d_w[p], pr.nvox(),
+                                          plan->grid, cand, d_score[p], d_quat[p],
+                                          d_lambda ? d_lambda[p] : nullptr,
                                           d_components_out ? d_components_out[p] : nullptr, st,
                                           &plan->launches);
         }));

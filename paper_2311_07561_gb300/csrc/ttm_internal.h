@@ -44,6 +44,7 @@ struct ProblemData {
     int tmpl = 0;
     int path = TTM_PATH_DIRECT;
     FftShape fft;
+    bool mixed = false;                // bf16 spectra, products and correlation maps
     int spec_index = -1;               // template spectra set used (FFT path)
     size_t nvox() const { return (size_t)X * Y * Z; }
 };
@@ -51,7 +52,10 @@ struct ProblemData {
 // Template spectra for one (template, FFT box): K half spectra, scaled by 1/N.
 struct SpecSet {
     int tmpl = 0, Xp = 0, Yp = 0, Zp = 0;
-    float2* d_spec = nullptr;
+    bool mixed = false;
+    float2* d_spec = nullptr;          // FP32: K component spectra
+    void* d_spec_bf = nullptr;         // mixed precision: K component spectra in bf16
+    float2* d_mask_spec = nullptr;     // FP32 mask spectrum (local statistics)
 };
 
 // Rotation search grid (device tables owned by the plan).
@@ -114,13 +118,13 @@ ttm_status launch_direct_corr(const float* f, int X, int Y, int Z, const Templat
 
 // per-voxel score + candidate search (tensor cores for order 4 with the
 // default 2048-point grid, CUDA cores otherwise), then refinement
-ttm_status launch_rotation_search(int n_order, const float* corr, const float* w, size_t nvox,
-                                  const RotGrid& g, uint16_t* cand, int* status, float* score,
+ttm_status launch_rotation_search(int n_order, const void* corr, bool bf16, const float* w,
+                                  size_t nvox, const RotGrid& g, uint16_t* cand, int* status,
+                                  float* score, cudaStream_t st, long long* cnt);
+ttm_status launch_rotation_polish(int n_order, const void* corr, bool bf16, const float* w,
+                                  size_t nvox, const RotGrid& g, const uint16_t* cand,
+                                  const float* score, float* quat, float* lambda, float* comp_out,
                                   cudaStream_t st, long long* cnt);
-ttm_status launch_rotation_polish(int n_order, const float* corr, const float* w, size_t nvox,
-                                  const RotGrid& g, const uint16_t* cand, const float* score,
-                                  float* quat, float* lambda, float* comp_out, cudaStream_t st,
-                                  long long* cnt);
 void build_grid_fp16(const float* m_rows, int K4, std::vector<uint16_t>& out);
 
 // tensor template build
@@ -141,6 +145,13 @@ ttm_status launch_fft_forward(const float* f, int X, int Y, int Z, const FftShap
                               float2* spec, cudaStream_t st, long long* cnt, int mode = 0,
                               const double* moments = nullptr);
 bool fft_template_length(int L);
+// mixed precision (bf16 storage, FP32 arithmetic); lengths 16..1024 only
+ttm_status launch_fft_spectrum_inverse_z_bf16(const float2* spec, const void* tspec, int K,
+                                              const FftShape& S, void* prod, cudaStream_t st,
+                                              long long* cnt);
+ttm_status launch_fft_inverse_yx_bf16(void* prod, int K, int X, int Y, int Z, const FftShape& S,
+                                      void* corr, cudaStream_t st, long long* cnt);
+ttm_status launch_spectra_to_bf16(const float2* a, void* b, size_t n, cudaStream_t st, long long* cnt);
 ttm_status launch_stats_from_sums(const float* s1, const float* s2, float* w, int X, int Y, int Z,
                                   int s, double mask_sum, const double* moments, cudaStream_t st,
                                   long long* cnt);

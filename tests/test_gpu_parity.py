@@ -321,3 +321,25 @@ def test_classical_comparator_matches_oracle(ttm, c1_oracle):
     unique = srt[-1] - srt[-2] > 2 * TOL
     assert np.all(arg[zi, yi, xi][unique] == cj[:, zi, yi, xi].argmax(axis=0)[unique])
     m.close()
+
+
+def test_mixed_precision_within_bf16_tolerance(ttm, c1_oracle):
+    """bf16 storage of spectra, products and correlation maps: components,
+    score and lambda within 5e-3 of the FP64 oracle; w stays FP32-accurate."""
+    o_ = _opts(ttm, "fft")
+    o_.precision = ttm.TTM_PREC_MIXED
+    res = _run(ttm, c1_oracle["wl"], c1_oracle["comp"], c1_oracle["desc"], opts=o_)
+    C_o = c1_oracle["C_o"]
+    dC = np.abs(res["comp"] - C_o).max()
+    dS = np.abs(res["score"] - o.frobenius_score(C_o, 4)).max()
+    assert dC <= 5e-3 and dS <= 5e-3, (dC, dS)
+    nz = c1_oracle["w_o"] > 0
+    assert (np.abs(res["w"][nz] - c1_oracle["w_o"][nz]) / c1_oracle["w_o"][nz]).max() <= 1e-5
+    wl = c1_oracle["wl"]
+    rng = np.random.default_rng(22)
+    pts = np.concatenate([wl.positions, rng.integers(7, 57, size=(150, 3))])
+    Cp = C_o[:, pts[:, 2], pts[:, 1], pts[:, 0]].T
+    lam_o, _ = o.dominant_z_eigenpair(Cp, 4)
+    dl = np.abs(res["lam"][pts[:, 2], pts[:, 1], pts[:, 0]] - lam_o).max()
+    assert dl <= 5e-3, dl
+    print(f"mixed precision max errors: C {dC:.2e} score {dS:.2e} lambda {dl:.2e}")
