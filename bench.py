@@ -39,6 +39,8 @@ WORKLOAD = dict(
        "ball mask r=7, tensor order n=4 (K=35)",
     c2s="128x128x128 FP32 volume (profiling size), 8 planted copies of the 32^3 template of c2, "
         "SNR 0.5, ball mask r=15, tensor order n=4 (K=35)",
+    c3="512x512x512 FP32 volume, 200 planted copies of a 40^3 lowpassed 30-blob template, "
+       "SNR 0.3, ball mask r=19, tensor order n=4 (K=35)",
 )
 WORKLOAD_OVERRIDES = dict(c2s=("c2", dict(shape_zyx=(128, 128, 128), copies=8)))
 
@@ -62,7 +64,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c2s"])
+    ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c2s", "c3"])
     ap.add_argument("--path", default="auto", choices=["auto", "direct", "fft"])
     ap.add_argument("--precision", default="fp32", choices=["fp32", "mixed"],
                     help="storage of spectra/products/correlation maps on the FFT path")
@@ -190,8 +192,11 @@ def source_hash(names) -> str:
 
 
 def roofline(kernels: dict, steps: int, nvox: int, K: int, n_taps: int, n_grid: int,
-             n_cand: int, newton: int, peaks: dict, spectrum_bytes: float = 0.0) -> dict:
-    """Roofline object for the kernel class with the largest share."""
+             n_cand: int, newton: int, peaks: dict, spectrum_bytes: float = 0.0,
+             n_interior: int | None = None) -> dict:
+    """Roofline object for the kernel class with the largest share.  The
+    rotation kernels visit only the interior voxels (n_interior)."""
+    n_int = nvox if n_interior is None else n_interior
     name = max(kernels, key=lambda k: kernels[k]["ms"])
     ms_launch = kernels[name]["ms"] / max(kernels[name]["launches"], 1)
     launches_per_step = kernels[name]["launches"] / steps
@@ -202,7 +207,7 @@ def roofline(kernels: dict, steps: int, nvox: int, K: int, n_taps: int, n_grid: 
         src = ["k_direct.cu"]
         peak_source = "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz"
     elif name == "rotation_search" and K == 35 and n_grid == 2048:
-        work = 2.0 * n_grid * 48 * nvox / launches_per_step      # FP16 MMA, K padded to 48
+        work = 2.0 * n_grid * 48 * n_int / launches_per_step     # FP16 MMA, K padded to 48
         bound, peak, unit, scale = "tensor", peaks.get("bf16_tflops", 1900.0), "TFLOP/s", 1e12
         src = ["k_search_tc.cu", "k_rotation.cuh"]
         peak_source = "measured dense bf16 (MEASURED_PEAKS.json bf16_tflops); fp16 runs at the bf16 rate"
@@ -210,7 +215,7 @@ def roofline(kernels: dict, steps: int, nvox: int, K: int, n_taps: int, n_grid: 
         KB = 10
         per_cand = (2 + newton) * (2 * 10 * KB + 40) + newton * 150
         work = ((2.0 * n_grid * K + 2 * K) if name == "rotation_search" else n_cand * per_cand) \
-            * nvox / launches_per_step
+            * n_int / launches_per_step
         bound, peak, unit, scale = "alu", FP32_ALU_PEAK_TFLOPS, "TFLOP/s", 1e12
         src = ["k_rotation.cuh", "k_rotation.cu", "k_rotation_n4.cu"]
         peak_source = "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz"
@@ -409,7 +414,10 @@ def run_ours(args) -> None:
     n_taps = int(wl.mask.sum())
     Xh = X // 2 + 1
     spec_bytes = 8.0 * Xh * Y * Z if path == 2 else 0.0
-    rf = roofline(kern, args.steps, nvox, desc.K, n_taps, 2048, 8, 4, peaks, spec_bytes)
+    s_edge = wl.template.shape[0]
+    n_interior = max(X - s_edge + 1, 0) * max(Y - s_edge + 1, 0) * max(Z - s_edge + 1, 0)
+    rf = roofline(kern, args.steps, nvox, desc.K, n_taps, 2048, 8, 4, peaks, spec_bytes,
+                  n_interior)
     cpu = None
     if not args.no_cpu_baseline and world == 1:
         cpu = cpu_baseline_obj(run_cpu_sample(args.workload, 128, 2))
@@ -419,7 +427,7 @@ def run_ours(args) -> None:
         scaling="weak", vs_baseline=None, dtype="f32" if args.precision == "fp32" else "bf16/f32",
         data="synthetic",
         config=dict(workload=WORKLOAD[args.workload], path={1: "direct", 2: "fft"}.get(path, path),
-                    voxels=nvox, tensor_order=wl.n_order, K=desc.K, mask_voxels=n_taps,
+                    voxels=nvox, interior_voxels=n_interior, tensor_order=wl.n_order, K=desc.K, mask_voxels=n_taps,
                     rotation_grid=2048, l2="flushed (256 MB write) before every timed step",
                     parallelism="replicas" if world > 1 else "single GPU",
                     template_build_ms=round(build_ms, 2), quadrature_rotations=desc.n_rot),

@@ -201,6 +201,13 @@ ttm_status ttm_plan_workspace_size(ttm_plan_t plan, size_t* bytes);
 /* Path the plan chose for problem p (TTM_PATH_DIRECT or TTM_PATH_FFT). */
 ttm_status ttm_plan_problem_path(ttm_plan_t plan, int problem, int* path);
 
+/* Padded FFT box of problem p: box[0..2] = (Xp, Yp, Zp), each the smallest
+ * supported length 2^p 3^a 5^b (16..1024), else a power of two, not below
+ * the volume's extent (circular correlation on the padded box equals the
+ * linear one on the interior, Sec. 2 of the paper).  Zeros on the direct
+ * path.  Host-only; TTM_ERR_INVALID_ARG for a bad plan, problem or pointer. */
+ttm_status ttm_plan_problem_fft_box(ttm_plan_t plan, int problem, int* box);
+
 /* Kernel launches the plan has queued so far (for accounting). */
 ttm_status ttm_plan_launch_count(ttm_plan_t plan, long long* launches);
 

@@ -30,7 +30,7 @@ TTM_PREC_FP32, TTM_PREC_MIXED = 0, 1
 EXPORTED = (
     "ttm_status_string", "ttm_device_count", "ttm_build_workspace_size",
     "ttm_build_tensor_template", "ttm_plan", "ttm_plan_workspace_size",
-    "ttm_plan_problem_path", "ttm_plan_launch_count", "ttm_plan_destroy",
+    "ttm_plan_problem_path", "ttm_plan_problem_fft_box", "ttm_plan_launch_count", "ttm_plan_destroy",
     "ttm_local_stats", "ttm_correlate", "ttm_extract_peaks", "ttm_plan_enable_timing",
     "ttm_plan_timing", "ttm_kernel_class_name", "ttm_build_tensor_template_noalloc",
     "ttm_plan_device_status", "ttm_classical_workspace_size", "ttm_classical_ncc",
@@ -86,6 +86,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
                          ctypes.POINTER(TTDesc), PP, PP, ctypes.POINTER(PlanOpts), P]),
         "ttm_plan_workspace_size": (I, [P, ctypes.POINTER(S)]),
         "ttm_plan_problem_path": (I, [P, I, ctypes.POINTER(I)]),
+        "ttm_plan_problem_fft_box": (I, [P, I, ctypes.POINTER(I)]),
         "ttm_plan_launch_count": (I, [P, ctypes.POINTER(L)]),
         "ttm_plan_destroy": (None, [P]),
         "ttm_local_stats": (I, [P, PP, PP, P, S, P]),
@@ -221,6 +222,13 @@ def ttm_plan_problem_path(plan: int, problem: int) -> int:
     _check(load_library().ttm_plan_problem_path(plan, problem, ctypes.byref(out)),
            "ttm_plan_problem_path")
     return out.value
+
+
+def ttm_plan_problem_fft_box(plan: int, problem: int) -> tuple:
+    out = (ctypes.c_int * 3)()
+    _check(load_library().ttm_plan_problem_fft_box(plan, problem, out),
+           "ttm_plan_problem_fft_box")
+    return tuple(out)
 
 
 def ttm_plan_launch_count(plan: int) -> int:

@@ -5,54 +5,33 @@
 // Layouts.  A real volume is [Zp][Yp][Xp] (padded sizes, zero beyond the
 // data); its half spectrum is [Zp][Yp][Xh] complex64 with Xh = Xp/2 + 1.
 //
-// Every pass moves a tile of whole 1D lines into shared memory, transforms
-// them there with Stockham autosort stages (radix 4, one radix-2 stage when
-// the length needs it; two shared-memory buffers ping-pong between stages),
-// and writes the tile back, so each pass reads and writes HBM once:
-//   rows_r2c      x lines of the real volume -> half-spectrum rows
-//   cols          y or z lines of a half spectrum (strided), in place
-//   cols_mul      z lines of the image spectrum times conj(template spectrum)
-//                 for all K components: the image tile is read once and kept
-//                 in shared memory while the K component tiles stream through
-//   rows_c2r      half-spectrum rows -> real x lines (Hermitian extension)
-// Twiddles exp(-2 pi i k / L) come from a table computed on the host in FP64.
-#include <cuda_bf16.h>
-
+// The passes for the lengths of TTM_FFT_LENGTHS have their line length fixed
+// at compile time (k_fft.cuh, instantiated in k_fft_len*.cu).  Other powers of
+// two up to 4096 take the runtime-length kernels below (radix 4 and 2, same
+// tiling, FP32 storage only).
 #include <type_traits>
 
-#include "ttm_internal.h"
+#include "k_fft.cuh"
 
 namespace ttm {
 
+#define TTM_FFT_EXTERN(L) extern template struct FftLen<L>;
+TTM_FFT_LENGTHS(TTM_FFT_EXTERN)
+#undef TTM_FFT_EXTERN
+
 namespace {
 
-constexpr int kFftThreads = 256;
+using fftk::cmul;
+using fftk::cmulc;
+using fftk::cadd;
+using fftk::csub;
+using fftk::kFftThreads;
 constexpr int kTileElems = 4096;   // complex elements per shared-memory buffer
 
 struct Radices {
     int n;          // number of stages
     int r[16];      // radix of each stage (4 or 2), in order
 };
-
-__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
-    return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
-}
-__device__ __forceinline__ float2 cmulc(float2 a, float2 b) {   // a * conj(b)
-    return make_float2(a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y);
-}
-__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
-
-// Storage types of spectra (float2 or bf16 pairs) and real maps (float or
-// bf16); arithmetic is always FP32.
-__device__ __forceinline__ float2 ldc(const float2* p) { return *p; }
-__device__ __forceinline__ float2 ldc(const __nv_bfloat162* p) { return __bfloat1622float2(*p); }
-__device__ __forceinline__ float2 ldgc(const float2* p) { return __ldg(p); }
-__device__ __forceinline__ float2 ldgc(const __nv_bfloat162* p) { return __bfloat1622float2(__ldg(p)); }
-__device__ __forceinline__ void stc(float2* p, float2 v) { *p = v; }
-__device__ __forceinline__ void stc(__nv_bfloat162* p, float2 v) { *p = __float22bfloat162_rn(v); }
-__device__ __forceinline__ void str(float* p, float v) { *p = v; }
-__device__ __forceinline__ void str(__nv_bfloat16* p, float v) { *p = __float2bfloat16_rn(v); }
-__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
 
 // NB independent transforms of length L stored as buf[i * pitch + b].  The
 // result ends in *out (one of a, b).  sign = -1 forward, +1 inverse.
@@ -106,157 +85,6 @@ __device__ void fft_lines(float2* a, float2* b, float2** out, int L, int NB, int
     }
     *out = src;
 }
-
-// ---- compile-time-length Stockham stages with radix up to 16 in registers ----
-// Small DFTs (sign -1 forward, +1 inverse).  DFT16 = 4 x 4 with the internal
-// twiddles W16^(n2 k1); its outputs come back in transposed order.
-constexpr float kC8 = 0.92387953251128674f;   // cos(pi/8)
-constexpr float kS8 = 0.38268343236508978f;   // sin(pi/8)
-constexpr float kR2 = 0.70710678118654752f;   // sqrt(2)/2
-
-template <int SIGN>
-__device__ __forceinline__ float2 mul_mi(float2 a) {   // a * (SIGN * i)
-    return SIGN < 0 ? make_float2(a.y, -a.x) : make_float2(-a.y, a.x);
-}
-
-template <int SIGN>
-__device__ __forceinline__ void dft4(float2& a, float2& b, float2& c, float2& d) {
-    float2 s02 = cadd(a, c), d02 = csub(a, c), s13 = cadd(b, d), d13 = csub(b, d);
-    float2 t = mul_mi<SIGN>(d13);
-    a = cadd(s02, s13);
-    b = cadd(d02, t);
-    c = csub(s02, s13);
-    d = csub(d02, t);
-}
-
-// W16^m for the forward transform (conjugated for the inverse)
-template <int SIGN>
-__device__ __forceinline__ float2 w16(int m) {
-    float c, s;
-    switch (m & 15) {
-        case 0: c = 1.f; s = 0.f; break;
-        case 1: c = kC8; s = kS8; break;
-        case 2: c = kR2; s = kR2; break;
-        case 3: c = kS8; s = kC8; break;
-        case 4: c = 0.f; s = 1.f; break;
-        case 5: c = -kS8; s = kC8; break;
-        case 6: c = -kR2; s = kR2; break;
-        case 7: c = -kC8; s = kS8; break;
-        case 8: c = -1.f; s = 0.f; break;
-        default: c = -kC8; s = -kS8; break;   // 9
-    }
-    // forward: exp(-2 pi i m / 16) = c - i s
-    return SIGN < 0 ? make_float2(c, -s) : make_float2(c, s);
-}
-
-template <int R, int SIGN>
-__device__ __forceinline__ void dft_small(float2 (&v)[R]) {
-    if constexpr (R == 2) {
-        float2 a = v[0], b = v[1];
-        v[0] = cadd(a, b);
-        v[1] = csub(a, b);
-    } else if constexpr (R == 4) {
-        dft4<SIGN>(v[0], v[1], v[2], v[3]);
-    } else if constexpr (R == 8) {
-        // n = 2 n1 + n2, k = k1 + 4 k2
-        float2 u[8];
-#pragma unroll
-        for (int n2 = 0; n2 < 2; ++n2) {
-            float2 a = v[n2], b = v[n2 + 2], c = v[n2 + 4], d = v[n2 + 6];
-            dft4<SIGN>(a, b, c, d);
-            u[n2 + 0] = a; u[n2 + 2] = b; u[n2 + 4] = c; u[n2 + 6] = d;   // u[n2 + 2 k1]
-        }
-        // twiddle W8^(n2 k1) = W16^(2 n2 k1)
-#pragma unroll
-        for (int k1 = 0; k1 < 4; ++k1) u[1 + 2 * k1] = cmul(u[1 + 2 * k1], w16<SIGN>(2 * k1));
-#pragma unroll
-        for (int k1 = 0; k1 < 4; ++k1) {
-            float2 a = u[2 * k1], b = u[2 * k1 + 1];
-            v[k1] = cadd(a, b);          // k2 = 0 -> k = k1
-            v[k1 + 4] = csub(a, b);      // k2 = 1 -> k = k1 + 4
-        }
-    } else {  // R == 16: n = 4 n1 + n2, k = k1 + 4 k2
-        float2 u[16];
-#pragma unroll
-        for (int n2 = 0; n2 < 4; ++n2) {
-            float2 a = v[n2], b = v[n2 + 4], c = v[n2 + 8], d = v[n2 + 12];
-            dft4<SIGN>(a, b, c, d);
-            u[4 * 0 + n2] = a; u[4 * 1 + n2] = b; u[4 * 2 + n2] = c; u[4 * 3 + n2] = d;  // u[4 k1 + n2]
-        }
-#pragma unroll
-        for (int k1 = 1; k1 < 4; ++k1)
-#pragma unroll
-            for (int n2 = 1; n2 < 4; ++n2) u[4 * k1 + n2] = cmul(u[4 * k1 + n2], w16<SIGN>(n2 * k1));
-#pragma unroll
-        for (int k1 = 0; k1 < 4; ++k1) {
-            float2 a = u[4 * k1], b = u[4 * k1 + 1], c = u[4 * k1 + 2], d = u[4 * k1 + 3];
-            dft4<SIGN>(a, b, c, d);
-            v[k1] = a; v[k1 + 4] = b; v[k1 + 8] = c; v[k1 + 12] = d;     // k = k1 + 4 k2
-        }
-    }
-}
-
-// radix of stage st for length L: 16s first, the remaining factor last
-__host__ __device__ constexpr int ilog2c(int n) { return n <= 1 ? 0 : 1 + ilog2c(n >> 1); }
-__host__ __device__ constexpr int n_stages(int L) {
-    return ilog2c(L) / 4 + ((ilog2c(L) % 4) ? 1 : 0);
-}
-__host__ __device__ constexpr int stage_radix(int L, int st) {
-    return (st < ilog2c(L) / 4) ? 16 : (1 << (ilog2c(L) % 4));
-}
-
-// One Stockham stage of radix R on NB lines of length L, buf[i * PITCH + line].
-template <int L, int R, int NS, int NB, int PITCH, int SIGN>
-__device__ __forceinline__ void stockham_stage(const float2* __restrict__ src, float2* __restrict__ dst,
-                                               const float2* __restrict__ tw) {
-    constexpr int NBF = L / R;
-    constexpr int STRIDE_TW = L / (NS * R);
-    for (int idx = threadIdx.x; idx < NBF * NB; idx += blockDim.x) {
-        const int line = idx & (NB - 1);
-        const int j = idx / NB;                      // NB is a power of two
-        const int jm = j & (NS - 1);
-        const int idxD = (j - jm) * R + jm;
-        float2 v[R];
-#pragma unroll
-        for (int r = 0; r < R; ++r) v[r] = src[(j + r * NBF) * PITCH + line];
-        if constexpr (NS > 1) {
-#pragma unroll
-            for (int r = 1; r < R; ++r) {
-                float2 w = __ldg(tw + jm * r * STRIDE_TW);
-                if (SIGN > 0) w.y = -w.y;
-                v[r] = cmul(v[r], w);
-            }
-        }
-        dft_small<R, SIGN>(v);
-#pragma unroll
-        for (int r = 0; r < R; ++r) dst[(idxD + r * NS) * PITCH + line] = v[r];
-    }
-}
-
-template <int L, int ST, int NB, int PITCH, int SIGN>
-__device__ __forceinline__ float2* stockham_from(float2* a, float2* b, const float2* tw) {
-    if constexpr (ST >= n_stages(L)) {
-        return a;
-    } else {
-        constexpr int R = stage_radix(L, ST);
-        constexpr int NS = [] { int ns = 1; for (int s = 0; s < ST; ++s) ns *= stage_radix(L, s); return ns; }();
-        stockham_stage<L, R, NS, NB, PITCH, SIGN>(a, b, tw);
-        __syncthreads();
-        return stockham_from<L, ST + 1, NB, PITCH, SIGN>(b, a, tw);
-    }
-}
-
-template <int L, int NB, int PITCH, int SIGN>
-__device__ __forceinline__ float2* fft_lines_t(float2* a, float2* b, const float2* tw) {
-    return stockham_from<L, 0, NB, PITCH, SIGN>(a, b, tw);
-}
-
-template <int L> constexpr int rows_nb() { return (4096 / L) > 16 ? 16 : (4096 / L < 1 ? 1 : 4096 / L); }
-template <int L> constexpr int cols_tb() { return (4096 / L) > 32 ? 32 : (4096 / L < 1 ? 1 : 4096 / L); }
-
-struct FftGeom {
-    int Xp, Yp, Zp, Xh;
-};
 
 // ---- rows: real x lines -> half-spectrum rows --------------------------
 // The source volume has X, Y, Z <= Xp, Yp, Zp; lines and samples beyond the
@@ -409,285 +237,6 @@ __global__ void scale_kernel(float2* __restrict__ a, size_t n, float s) {
     if (i < n) { a[i].x *= s; a[i].y *= s; }
 }
 
-// ---- the four passes with a compile-time line length ---------------------
-// mode 0 transforms f, mode 1 (f - mean), mode 2 (f - mean)^2 with mean =
-// moments[0] / (X Y Z) (the shift removes the cancellation in the local variance)
-template <int L>
-__global__ void __launch_bounds__(kFftThreads) rows_r2c_t(const float* __restrict__ f, int X, int Y,
-                                                          int Z, FftGeom g, float2* __restrict__ out,
-                                                          const float2* __restrict__ tw, int mode,
-                                                          const double* __restrict__ moments) {
-    constexpr int NB = rows_nb<L>();
-    constexpr int PITCH = NB + 1;
-    constexpr int XH = L / 2 + 1;
-    extern __shared__ float2 sm[];
-    float2* A = sm;
-    float2* B = sm + L * PITCH;
-    const int row0 = blockIdx.x * NB;
-    const int nrows = g.Yp * g.Zp;
-    const float mean = mode ? (float)(moments[0] / ((double)X * Y * Z)) : 0.f;
-    constexpr int PER = (NB * L + kFftThreads - 1) / kFftThreads;
-    __shared__ long long row_in[NB];         // input offset of each row, -1 = zero row
-    if (threadIdx.x < NB) {
-        const int row = row0 + threadIdx.x;
-        long long off = -1;
-        if (row < nrows) {
-            const int y = row % g.Yp, z = row / g.Yp;
-            if (y < Y && z < Z) off = (long long)(((size_t)z * Y + y) * X);
-        }
-        row_in[threadIdx.x] = off;
-    }
-    __syncthreads();
-    float vv[PER];
-#pragma unroll
-    for (int i = 0; i < PER; ++i) {
-        const int e = threadIdx.x + i * kFftThreads;
-        const int r = e / L, x = e & (L - 1);
-        float v = 0.f;
-        if (e < NB * L && x < X) {
-            const long long off = row_in[r];
-            if (off >= 0) {
-                v = __ldg(f + off + x) - mean;
-                if (mode == 2) v = v * v;
-            }
-        }
-        vv[i] = v;
-    }
-#pragma unroll
-    for (int i = 0; i < PER; ++i) {
-        const int e = threadIdx.x + i * kFftThreads;
-        const int r = e / L, x = e & (L - 1);
-        if (e < NB * L) A[x * PITCH + r] = make_float2(vv[i], 0.f);
-    }
-    __syncthreads();
-    float2* res = fft_lines_t<L, NB, PITCH, -1>(A, B, tw);
-    for (int e = threadIdx.x; e < NB * XH; e += blockDim.x) {
-        const int r = e / XH, k = e % XH;
-        const int row = row0 + r;
-        if (row < nrows) out[(size_t)row * XH + k] = res[k * PITCH + r];
-    }
-}
-
-template <int L, int SIGN, typename PS>
-__global__ void __launch_bounds__(kFftThreads) cols_t(PS* __restrict__ data, int B,
-                                                      const float2* __restrict__ tw) {
-    constexpr int TB = cols_tb<L>();
-    extern __shared__ float2 sm[];
-    float2* P = sm;
-    float2* Q = sm + L * TB;
-    constexpr int PER = (L * TB + kFftThreads - 1) / kFftThreads;
-    const int b0 = blockIdx.x * TB;
-    const size_t base = (size_t)blockIdx.y * L * B;
-    const int tb = min(TB, B - b0);
-    float2 v[PER];
-#pragma unroll
-    for (int i = 0; i < PER; ++i) {          // all loads in flight before any store
-        const int e = threadIdx.x + i * kFftThreads;
-        const int l = e / TB, bb = e & (TB - 1);
-        v[i] = (e < L * TB && bb < tb) ? ldc(data + base + (size_t)l * B + b0 + bb) : make_float2(0.f, 0.f);
-    }
-#pragma unroll
-    for (int i = 0; i < PER; ++i) {
-        const int e = threadIdx.x + i * kFftThreads;
-        if (e < L * TB) P[e] = v[i];
-    }
-    __syncthreads();
-    float2* res = fft_lines_t<L, TB, TB, SIGN>(P, Q, tw);
-#pragma unroll
-    for (int i = 0; i < PER; ++i) {
-        const int e = threadIdx.x + i * kFftThreads;
-        const int l = e / TB, bb = e & (TB - 1);
-        if (e < L * TB && bb < tb) stc(data + base + (size_t)l * B + b0 + bb, res[e]);
-    }
-}
-
-template <int L, typename TS, typename PS>
-__global__ void __launch_bounds__(kFftThreads) cols_mul_t(const float2* __restrict__ spec,
-                                                          const TS* __restrict__ tspec,
-                                                          PS* __restrict__ out, int B, int K,
-                                                          const float2* __restrict__ tw) {
-    constexpr int TB = cols_tb<L>();
-    extern __shared__ float2 sm[];
-    float2* P = sm;
-    float2* Q = sm + L * TB;
-    constexpr int PER = (L * TB + kFftThreads - 1) / kFftThreads;
-    const int b0 = blockIdx.x * TB;
-    const int tb = min(TB, B - b0);
-    const size_t plane = (size_t)L * B;
-    // this thread's elements of the image tile stay in registers
-    float2 fi[PER];
-#pragma unroll
-    for (int i = 0; i < PER; ++i) {
-        const int e = threadIdx.x + i * kFftThreads;
-        const int l = e / TB, bb = e & (TB - 1);
-        fi[i] = (e < L * TB && bb < tb) ? spec[(size_t)l * B + b0 + bb] : make_float2(0.f, 0.f);
-    }
-    // component tiles: the next one is fetched while the current one is transformed
-    float2 tv[PER];
-#pragma unroll
-    for (int i = 0; i < PER; ++i) {
-        const int e = threadIdx.x + i * kFftThreads;
-        const int l = e / TB, bb = e & (TB - 1);
-        tv[i] = (K > 0 && e < L * TB && bb < tb) ? ldgc(tspec + (size_t)l * B + b0 + bb)
-                                                  : make_float2(0.f, 0.f);
-    }
-    for (int k = 0; k < K; ++k) {
-        __syncthreads();
-#pragma unroll
-        for (int i = 0; i < PER; ++i) {
-            const int e = threadIdx.x + i * kFftThreads;
-            if (e < L * TB) P[e] = cmulc(fi[i], tv[i]);
-        }
-        if (k + 1 < K) {
-            const TS* ts = tspec + (size_t)(k + 1) * plane;
-#pragma unroll
-            for (int i = 0; i < PER; ++i) {
-                const int e = threadIdx.x + i * kFftThreads;
-                const int l = e / TB, bb = e & (TB - 1);
-                tv[i] = (e < L * TB && bb < tb) ? ldgc(ts + (size_t)l * B + b0 + bb)
-                                                 : make_float2(0.f, 0.f);
-            }
-        }
-        __syncthreads();
-        float2* res = fft_lines_t<L, TB, TB, +1>(P, Q, tw);
-        PS* o = out + (size_t)k * plane;
-#pragma unroll
-        for (int i = 0; i < PER; ++i) {
-            const int e = threadIdx.x + i * kFftThreads;
-            const int l = e / TB, bb = e & (TB - 1);
-            if (e < L * TB && bb < tb) stc(o + (size_t)l * B + b0 + bb, res[e]);
-        }
-    }
-}
-
-template <int L, typename PS, typename RT>
-__global__ void __launch_bounds__(kFftThreads) rows_c2r_t(const PS* __restrict__ in, int X, int Y,
-                                                          int Z, FftGeom g, RT* __restrict__ out,
-                                                          int n_batch, const float2* __restrict__ tw) {
-    constexpr int NB = rows_nb<L>();
-    constexpr int PITCH = NB + 1;
-    constexpr int XH = L / 2 + 1;
-    extern __shared__ float2 sm[];
-    float2* A = sm;
-    float2* Bf = sm + L * PITCH;
-    constexpr int PER = (NB * L + kFftThreads - 1) / kFftThreads;
-    __shared__ long long row_out[NB];        // output offset of each row, -1 = not written
-    const size_t rows_per_item = (size_t)g.Yp * g.Zp;
-    const size_t nrows = rows_per_item * n_batch;
-    const size_t row0 = (size_t)blockIdx.x * NB;
-    if (threadIdx.x < NB) {
-        const size_t row = row0 + threadIdx.x;
-        long long off = -1;
-        if (row < nrows) {
-            const size_t item = row / rows_per_item;
-            const int rr = (int)(row - item * rows_per_item);
-            const int y = rr % g.Yp, z = rr / g.Yp;
-            if (y < Y && z < Z) off = (long long)(item * ((size_t)X * Y * Z) + ((size_t)z * Y + y) * X);
-        }
-        row_out[threadIdx.x] = off;
-    }
-    float2 v[PER];
-#pragma unroll
-    for (int i = 0; i < PER; ++i) {          // loads first, Hermitian extension on the fly
-        const int e = threadIdx.x + i * kFftThreads;
-        const int r = e / L, x = e & (L - 1);
-        const size_t row = row0 + r;
-        v[i] = make_float2(0.f, 0.f);
-        if (e < NB * L && row < nrows) {
-            const PS* src = in + row * XH;
-            if (x < XH) v[i] = ldc(src + x);
-            else { float2 c = ldc(src + (L - x)); v[i] = make_float2(c.x, -c.y); }
-        }
-    }
-#pragma unroll
-    for (int i = 0; i < PER; ++i) {
-        const int e = threadIdx.x + i * kFftThreads;
-        const int r = e / L, x = e & (L - 1);
-        if (e < NB * L) A[x * PITCH + r] = v[i];
-    }
-    __syncthreads();
-    float2* res = fft_lines_t<L, NB, PITCH, +1>(A, Bf, tw);   // ends with a barrier
-#pragma unroll
-    for (int i = 0; i < PER; ++i) {
-        const int e = threadIdx.x + i * kFftThreads;
-        const int r = e / L, x = e & (L - 1);
-        if (e >= NB * L || x >= X) continue;
-        const long long off = row_out[r];
-        if (off >= 0) str(out + off + x, res[x * PITCH + r].x);
-    }
-}
-
-
-struct RunRowsR2C {
-    const float* f; int X, Y, Z; FftGeom g; float2* spec; const float2* tw; cudaStream_t st;
-    cudaError_t* err; int mode; const double* moments;
-    template <int L> void operator()() {
-        constexpr int NB = rows_nb<L>();
-        const size_t smem = (size_t)2 * L * (NB + 1) * sizeof(float2);
-        *err = cudaFuncSetAttribute(rows_r2c_t<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        const int nrows = g.Yp * g.Zp;
-        rows_r2c_t<L><<<(nrows + NB - 1) / NB, kFftThreads, smem, st>>>(f, X, Y, Z, g, spec, tw, mode, moments);
-    }
-};
-
-template <typename TS, typename PS>
-struct RunColsMul {
-    const float2* spec; const TS* tspec; PS* prod; int Bz, K; const float2* tw;
-    cudaStream_t st; cudaError_t* err;
-    template <int L> void operator()() {
-        constexpr int TB = cols_tb<L>();
-        const size_t smem = (size_t)2 * L * TB * sizeof(float2);
-        *err = cudaFuncSetAttribute(cols_mul_t<L, TS, PS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        dim3 grid((Bz + TB - 1) / TB, 1);
-        cols_mul_t<L, TS, PS><<<grid, kFftThreads, smem, st>>>(spec, tspec, prod, Bz, K, tw);
-    }
-};
-
-template <typename PS, typename RT>
-struct RunRowsC2R {
-    const PS* prod; int X, Y, Z; FftGeom g; RT* corr; int K; const float2* tw;
-    cudaStream_t st; cudaError_t* err;
-    template <int L> void operator()() {
-        constexpr int NB = rows_nb<L>();
-        const size_t smem = (size_t)2 * L * (NB + 1) * sizeof(float2);
-        *err = cudaFuncSetAttribute(rows_c2r_t<L, PS, RT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        const size_t nrows = (size_t)g.Yp * g.Zp * K;
-        rows_c2r_t<L, PS, RT><<<(unsigned)((nrows + NB - 1) / NB), kFftThreads, smem, st>>>(
-            prod, X, Y, Z, g, corr, K, tw);
-    }
-};
-
-template <typename PS>
-struct RunCols {
-    PS* d; int B, na; const float2* tw; int sign; cudaStream_t st; cudaError_t* err;
-    template <int LL> void operator()() {
-        constexpr int TB = cols_tb<LL>();
-        const size_t smem = (size_t)2 * LL * TB * sizeof(float2);
-        dim3 grid((B + TB - 1) / TB, na);
-        if (sign < 0) {
-            *err = cudaFuncSetAttribute(cols_t<LL, -1, PS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            cols_t<LL, -1, PS><<<grid, kFftThreads, smem, st>>>(d, B, tw);
-        } else {
-            *err = cudaFuncSetAttribute(cols_t<LL, +1, PS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            cols_t<LL, +1, PS><<<grid, kFftThreads, smem, st>>>(d, B, tw);
-        }
-    }
-};
-
-// Dispatch helpers: call F.template operator()<L>() for a supported length.
-template <typename F>
-bool with_length(int L, F&& f) {
-    switch (L) {
-        case 16: f.template operator()<16>(); return true;
-        case 32: f.template operator()<32>(); return true;
-        case 64: f.template operator()<64>(); return true;
-        case 128: f.template operator()<128>(); return true;
-        case 256: f.template operator()<256>(); return true;
-        case 512: f.template operator()<512>(); return true;
-        case 1024: f.template operator()<1024>(); return true;
-        default: return false;
-    }
-}
 
 Radices radices_for(int L) {
     Radices rd{};
@@ -711,7 +260,84 @@ int cols_per_cta(int L) {
     return tb;
 }
 
+// ---- dispatch to the compile-time lengths (false: length not listed) ----
+#define TTM_FFT_CASE(L, CALL) case L: *err = FftLen<L>::CALL; return true;
+
+bool fixed_rows_r2c(int L, const float* f, int X, int Y, int Z, FftGeom g, float2* spec,
+                    const float2* tw, int mode, const double* moments, cudaStream_t st,
+                    cudaError_t* err) {
+    switch (L) {
+#define C(L) TTM_FFT_CASE(L, rows_r2c(f, X, Y, Z, g, spec, tw, mode, moments, st))
+        TTM_FFT_LENGTHS(C)
+#undef C
+        default: return false;
+    }
+}
+
+bool fixed_cols(int L, float2* d, int B, int na, const float2* tw, int sign, cudaStream_t st,
+                cudaError_t* err) {
+    switch (L) {
+#define C(L) TTM_FFT_CASE(L, cols(d, B, na, tw, sign, st))
+        TTM_FFT_LENGTHS(C)
+#undef C
+        default: return false;
+    }
+}
+
+bool fixed_cols(int L, __nv_bfloat162* d, int B, int na, const float2* tw, int sign,
+                cudaStream_t st, cudaError_t* err) {
+    switch (L) {
+#define C(L) TTM_FFT_CASE(L, cols_bf(d, B, na, tw, sign, st))
+        TTM_FFT_LENGTHS(C)
+#undef C
+        default: return false;
+    }
+}
+
+bool fixed_cols_mul(int L, const float2* spec, const float2* tspec, float2* prod, int Bz, int K,
+                    const float2* tw, cudaStream_t st, cudaError_t* err) {
+    switch (L) {
+#define C(L) TTM_FFT_CASE(L, cols_mul(spec, tspec, prod, Bz, K, tw, st))
+        TTM_FFT_LENGTHS(C)
+#undef C
+        default: return false;
+    }
+}
+
+bool fixed_cols_mul(int L, const float2* spec, const __nv_bfloat162* tspec, __nv_bfloat162* prod,
+                    int Bz, int K, const float2* tw, cudaStream_t st, cudaError_t* err) {
+    switch (L) {
+#define C(L) TTM_FFT_CASE(L, cols_mul_bf(spec, tspec, prod, Bz, K, tw, st))
+        TTM_FFT_LENGTHS(C)
+#undef C
+        default: return false;
+    }
+}
+
+bool fixed_rows_c2r(int L, const float2* prod, int X, int Y, int Z, FftGeom g, float* corr, int K,
+                    const float2* tw, cudaStream_t st, cudaError_t* err) {
+    switch (L) {
+#define C(L) TTM_FFT_CASE(L, rows_c2r(prod, X, Y, Z, g, corr, K, tw, st))
+        TTM_FFT_LENGTHS(C)
+#undef C
+        default: return false;
+    }
+}
+
+bool fixed_rows_c2r(int L, const __nv_bfloat162* prod, int X, int Y, int Z, FftGeom g,
+                    __nv_bfloat16* corr, int K, const float2* tw, cudaStream_t st,
+                    cudaError_t* err) {
+    switch (L) {
+#define C(L) TTM_FFT_CASE(L, rows_c2r_bf(prod, X, Y, Z, g, corr, K, tw, st))
+        TTM_FFT_LENGTHS(C)
+#undef C
+        default: return false;
+    }
+}
+#undef TTM_FFT_CASE
+
 }  // namespace
+
 
 // Column lines (length L, element stride B) of `batch` consecutive blocks.
 template <typename PS>
@@ -721,8 +347,7 @@ static ttm_status launch_cols_t(PS* data, int L, int B, int batch, const float2*
         const int na = batch - a0 < 65535 ? batch - a0 : 65535;
         PS* d = data + (size_t)a0 * L * B;
         cudaError_t err = cudaSuccess;
-        RunCols<PS> run{d, B, na, tw, sign, st, &err};
-        if (!with_length(L, run)) {
+        if (!fixed_cols(L, d, B, na, tw, sign, st, &err)) {
             if constexpr (!std::is_same<PS, float2>::value) return TTM_ERR_UNSUPPORTED;
             else {
                 const int TB = cols_per_cta(L);
@@ -743,9 +368,31 @@ static ttm_status launch_cols(float2* data, int L, int B, int batch, const float
     return launch_cols_t<float2>(data, L, B, batch, tw, sign, st, cnt);
 }
 
-bool fft_length_ok(int L) { return L >= 2 && L <= 4096 && (L & (L - 1)) == 0; }
+// lengths with a compile-time pass (TTM_FFT_LENGTHS)
+bool fft_template_length(int L) {
+    switch (L) {
+#define C(L) case L:
+        TTM_FFT_LENGTHS(C)
+#undef C
+        return true;
+        default: return false;
+    }
+}
 
+// compile-time lengths, or powers of two up to 4096 (runtime-length kernels)
+bool fft_length_ok(int L) {
+    return fft_template_length(L) || (L >= 2 && L <= 4096 && (L & (L - 1)) == 0);
+}
+
+// smallest compile-time length >= n (2^p 3^a 5^b), else the next power of two
 int fft_good_length(int n) {
+    static const int lengths[] = {
+#define C(L) L,
+        TTM_FFT_LENGTHS(C)
+#undef C
+    };
+    for (int L : lengths)
+        if (L >= n) return L;
     int L = 2;
     while (L < n) L <<= 1;
     return L;
@@ -757,9 +404,8 @@ ttm_status launch_fft_forward(const float* f, int X, int Y, int Z, const FftShap
     FftGeom g{S.Xp, S.Yp, S.Zp, S.Xp / 2 + 1};
     cudaError_t err = cudaSuccess;
     {
-        RunRowsR2C run{f, X, Y, Z, g, spec, S.d_tw_x, st, &err, mode, moments};
         if (mode != 0 && !fft_template_length(S.Xp)) return TTM_ERR_UNSUPPORTED;
-        if (!with_length(S.Xp, run)) {
+        if (!fixed_rows_r2c(S.Xp, f, X, Y, Z, g, spec, S.d_tw_x, mode, moments, st, &err)) {
             const int NB = rows_per_cta(S.Xp);
             const size_t smem = (size_t)2 * S.Xp * (NB + 1) * sizeof(float2);
             TTM_CUDA_TRY(cudaFuncSetAttribute(rows_r2c_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -781,8 +427,7 @@ static ttm_status spectrum_inverse_z_t(const float2* spec, const TS* tspec, int 
     const int Xh = S.Xp / 2 + 1;
     const int Bz = S.Yp * Xh;
     cudaError_t err = cudaSuccess;
-    RunColsMul<TS, PS> run{spec, tspec, prod, Bz, K, S.d_tw_z, st, &err};
-    if (!with_length(S.Zp, run)) {
+    if (!fixed_cols_mul(S.Zp, spec, tspec, prod, Bz, K, S.d_tw_z, st, &err)) {
         if constexpr (!std::is_same<TS, float2>::value || !std::is_same<PS, float2>::value)
             return TTM_ERR_UNSUPPORTED;
         else {
@@ -804,8 +449,7 @@ static ttm_status inverse_yx_t(PS* prod, int K, int X, int Y, int Z, const FftSh
     FftGeom g{S.Xp, S.Yp, S.Zp, S.Xp / 2 + 1};
     TTM_TRY(launch_cols_t<PS>(prod, S.Yp, g.Xh, K * S.Zp, S.d_tw_y, +1, st, cnt));
     cudaError_t err = cudaSuccess;
-    RunRowsC2R<PS, RT> run{prod, X, Y, Z, g, corr, K, S.d_tw_x, st, &err};
-    if (!with_length(S.Xp, run)) {
+    if (!fixed_rows_c2r(S.Xp, prod, X, Y, Z, g, corr, K, S.d_tw_x, st, &err)) {
         if constexpr (!std::is_same<PS, float2>::value || !std::is_same<RT, float>::value)
             return TTM_ERR_UNSUPPORTED;
         else {
@@ -858,27 +502,32 @@ ttm_status launch_spectra_to_bf16(const float2* a, void* b, size_t n, cudaStream
     return after_launch(cnt);
 }
 
-bool fft_template_length(int L) {
-    return L == 16 || L == 32 || L == 64 || L == 128 || L == 256 || L == 512 || L == 1024;
-}
 
 // w from the FFT-based window sums of (f - mean) and (f - mean)^2 (Algorithm 1):
 // V = S2 - S1^2 / m_sum in FP64; interior only; floor 1e-6 m_sum var(f).
 __global__ void stats_from_sums_kernel(const float* __restrict__ s1, const float* __restrict__ s2,
                                        float* __restrict__ w, int X, int Y, int Z, int s,
                                        double mask_sum, const double* __restrict__ moments) {
+    // FP64 is slow on this GPU: the volume statistics and the floor are
+    // formed once per CTA; each voxel does three FP64 operations
+    __shared__ double sh[2];
     const size_t n = (size_t)X * Y * Z;
+    if (threadIdx.x == 0) {
+        const double nv = (double)n;
+        const double mean = moments[0] / nv;
+        const double var_f = fmax(moments[1] / nv - mean * mean, 0.0);
+        sh[0] = 1.0 / mask_sum;
+        sh[1] = 1e-6 * mask_sum * var_f;
+    }
+    __syncthreads();
     const size_t v = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (v >= n) return;
     const int x = (int)(v % X), y = (int)((v / X) % Y), z = (int)(v / ((size_t)X * Y));
     float out = 0.f;
     if (interior(x, X, s) && interior(y, Y, s) && interior(z, Z, s)) {
-        const double nv = (double)n;
-        const double mean = moments[0] / nv;
-        const double var_f = fmax(moments[1] / nv - mean * mean, 0.0);
         const double S1 = s1[v], S2 = s2[v];
-        const double V = S2 - S1 * S1 / mask_sum;
-        if (V > 1e-6 * mask_sum * var_f) out = rsqrtf((float)V);
+        const double V = S2 - S1 * S1 * sh[0];
+        if (V > sh[1]) out = rsqrtf((float)V);
     }
     w[v] = out;
 }

@@ -5,22 +5,25 @@ namespace ttm {
 
 int rotation_row_stride(int n_order) { return (n_comp(n_order) + 3) & ~3; }
 
-static void fill_args(const void* corr, const float* w, size_t nvox, const RotGrid& g,
-                      uint16_t* cand, float* score, float* quat, float* lambda, float* comp_out,
-                      rot::SearchArgs& sa, rot::PolishArgs& pa) {
-    sa.corr = corr; sa.w = w; sa.nvox = nvox; sa.score = score; sa.cand = cand;
+static void fill_args(const void* corr, const float* w, size_t nvox, const VoxBox& box,
+                      const RotGrid& g, uint16_t* cand, float* score, float* quat, float* lambda,
+                      float* comp_out, rot::SearchArgs& sa, rot::PolishArgs& pa) {
+    sa.corr = corr; sa.w = w; sa.nvox = nvox; sa.box = box; sa.score = score; sa.cand = cand;
     sa.gm = g.d_m; sa.cell_end = g.d_cell_end; sa.n_grid = g.n_grid;
-    pa.corr = corr; pa.w = w; pa.nvox = nvox; pa.score = score; pa.cand = cand; pa.quat = quat;
+    pa.corr = corr; pa.w = w; pa.nvox = nvox; pa.box = box; pa.score = score; pa.cand = cand; pa.quat = quat;
     pa.lambda = lambda; pa.comp_out = comp_out; pa.gq = g.d_q; pa.n_cand = g.n_cand;
     pa.newton = g.newton;
 }
 
 ttm_status launch_rotation_search(int n_order, const void* corr, bool bf16, const float* w,
-                                  size_t nvox, const RotGrid& g, uint16_t* cand, int* status,
-                                  float* score, cudaStream_t st, long long* cnt) {
+                                  size_t nvox, const VoxBox& box, const RotGrid& g,
+                                  uint16_t* cand, int* status, float* score, cudaStream_t st,
+                                  long long* cnt) {
+    if (box.count() > 0xFFFFFFFFull) return TTM_ERR_UNSUPPORTED;
+    if (box.count() == 0) return TTM_OK;
     rot::SearchArgs sa;
     rot::PolishArgs pa;
-    fill_args(corr, w, nvox, g, cand, score, nullptr, nullptr, nullptr, sa, pa);
+    fill_args(corr, w, nvox, box, g, cand, score, nullptr, nullptr, nullptr, sa, pa);
     if (n_order == 4 && g.d_gtab)
         return launch_search_tc4(sa, g.d_gtab, g.d_endbits, status, bf16, st, cnt);
     switch (n_order) {
@@ -33,13 +36,16 @@ ttm_status launch_rotation_search(int n_order, const void* corr, bool bf16, cons
 }
 
 ttm_status launch_rotation_polish(int n_order, const void* corr, bool bf16, const float* w,
-                                  size_t nvox, const RotGrid& g, const uint16_t* cand,
-                                  const float* score, float* quat, float* lambda, float* comp_out,
-                                  cudaStream_t st, long long* cnt) {
+                                  size_t nvox, const VoxBox& box, const RotGrid& g,
+                                  const uint16_t* cand, const float* score, float* quat,
+                                  float* lambda, float* comp_out, cudaStream_t st,
+                                  long long* cnt) {
+    if (box.count() > 0xFFFFFFFFull) return TTM_ERR_UNSUPPORTED;
+    if (box.count() == 0) return TTM_OK;
     rot::SearchArgs sa;
     rot::PolishArgs pa;
-    fill_args(corr, w, nvox, g, const_cast<uint16_t*>(cand), const_cast<float*>(score), quat,
-              lambda, comp_out, sa, pa);
+    fill_args(corr, w, nvox, box, g, const_cast<uint16_t*>(cand), const_cast<float*>(score),
+              quat, lambda, comp_out, sa, pa);
     switch (n_order) {
         case 2: return launch_rotation_n<2>(sa, pa, true, false, bf16, st, cnt);
         case 4: return launch_rotation_n<4>(sa, pa, true, false, bf16, st, cnt);
@@ -47,6 +53,37 @@ ttm_status launch_rotation_polish(int n_order, const void* corr, bool bf16, cons
         case 8: return launch_rotation_n<8>(sa, pa, true, false, bf16, st, cnt);
         default: return TTM_ERR_UNSUPPORTED;
     }
+}
+
+namespace {
+
+// Exterior values for the voxels outside the interior box: score 0,
+// q = (1, 0, 0, 0), lambda 0 and (optionally) C = 0.  One thread per voxel of
+// an x-row; block (., y, z).
+__global__ void exterior_fill_kernel(VoxBox b, int K, size_t nvox, float* score, float4* quat,
+                                     float* lambda, float* comp_out) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y, z = blockIdx.z;
+    if (x >= b.X) return;
+    const bool row_in = (uint32_t)(y - b.y0) < b.ny && (uint32_t)(z - b.z0) < b.nz;
+    if (row_in && (uint32_t)(x - b.x0) < b.nx) return;
+    const size_t v = ((size_t)z * b.Y + y) * b.X + x;
+    score[v] = 0.f;
+    quat[v] = make_float4(1.f, 0.f, 0.f, 0.f);
+    if (lambda) lambda[v] = 0.f;
+    if (comp_out)
+        for (int k = 0; k < K; ++k) comp_out[(size_t)k * nvox + v] = 0.f;
+}
+
+}  // namespace
+
+ttm_status launch_exterior_fill(int Z, const VoxBox& box, int K, float* score, float* quat,
+                                float* lambda, float* comp_out, cudaStream_t st, long long* cnt) {
+    if (box.X < 1 || box.Y < 1 || Z < 1 || box.Y > 65535 || Z > 65535) return TTM_ERR_UNSUPPORTED;
+    dim3 grid((unsigned)((box.X + 127) / 128), (unsigned)box.Y, (unsigned)Z);
+    exterior_fill_kernel<<<grid, 128, 0, st>>>(box, K, (size_t)box.X * box.Y * Z, score,
+                                               reinterpret_cast<float4*>(quat), lambda, comp_out);
+    return after_launch(cnt);
 }
 
 }  // namespace ttm

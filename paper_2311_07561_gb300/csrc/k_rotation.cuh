@@ -6,7 +6,7 @@
 //   lambda(x)  = max_{|Q|=1} phi(Q),  phi(Q) = C_n(x) . Q^(n)                (Sec. 3.3)
 //   q(x)       = argmax, the dominant Z-eigenvector of C_n(x)                (Sec. 3.1)
 //
-// One thread per voxel.  The maximum is searched on a fixed grid of unit
+// One thread per interior voxel.  The maximum is searched on a fixed grid of unit
 // quaternions (half sphere, sorted into regions of equal size): phi at every grid point is a
 // dot product with a precomputed row mu_alpha q_g^alpha staged in shared memory
 // and read as a broadcast.  The best point of each region competes for a short
@@ -35,9 +35,10 @@ __device__ __forceinline__ float ldcorr(const __nv_bfloat16* p) { return __bfloa
 struct SearchArgs {
     const void* corr;       // K x nvox, float or bf16
     const float* w;
-    size_t nvox;
+    size_t nvox;            // voxels of the volume (stride of the component maps)
+    VoxBox box;             // interior voxels: the units the kernels visit
     float* score;
-    uint16_t* cand;         // nvox x 8 candidate grid indices
+    uint16_t* cand;         // per interior voxel: 8 candidate grid indices
     const float* gm;        // n_grid x K4 (SIMT search)
     const int* cell_end;    // n_grid
     int n_grid;
@@ -47,6 +48,7 @@ struct PolishArgs {
     const void* corr;       // K x nvox, float or bf16
     const float* w;
     size_t nvox;
+    VoxBox box;
     const float* score;
     const uint16_t* cand;
     float* quat;            // 4 x nvox interleaved (a, b, c, d) per voxel
@@ -270,8 +272,9 @@ __global__ void __launch_bounds__(kRotThreads) search_simt_kernel(SearchArgs a) 
     float* Mt = sm;                                   // kChunk x K4
     int* ends = reinterpret_cast<int*>(sm + kChunk * K4);
 
-    const size_t v = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const bool in_range = v < a.nvox;
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool in_range = i < a.box.count();
+    const size_t v = in_range ? a.box.voxel((uint32_t)i) : 0;
     const float wv = in_range ? __ldg(a.w + v) : 0.f;
     float C[K4];
 #pragma unroll
@@ -321,7 +324,7 @@ __global__ void __launch_bounds__(kRotThreads) search_simt_kernel(SearchArgs a) 
     }
     if (!in_range) return;
     a.score[v] = score;
-    store_candidates(a.cand, v, ti, active);
+    store_candidates(a.cand, i, ti, active);
 }
 
 // Refinement of the candidates and the outputs: lambda = the largest refined
@@ -331,8 +334,9 @@ __global__ void __launch_bounds__(kRotThreads) polish_kernel(PolishArgs a) {
     const CT* corr = reinterpret_cast<const CT*>(a.corr);
     constexpr int K = Geo<N>::K;
     constexpr int K4 = Geo<N>::K4;
-    const size_t v = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (v >= a.nvox) return;
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= a.box.count()) return;
+    const size_t v = a.box.voxel((uint32_t)i);
     const float wv = __ldg(a.w + v);
     float C[K4];
 #pragma unroll
@@ -344,7 +348,7 @@ __global__ void __launch_bounds__(kRotThreads) polish_kernel(PolishArgs a) {
         if (a.comp_out) a.comp_out[(size_t)k * a.nvox + v] = c;
     }
     const float score = __ldg(a.score + v);
-    const uint4 cr = __ldg(reinterpret_cast<const uint4*>(a.cand) + v);
+    const uint4 cr = __ldg(reinterpret_cast<const uint4*>(a.cand) + i);
     const uint32_t cw[4] = {cr.x, cr.y, cr.z, cr.w};
     float best_l = 0.f;
     float best_q[4] = {1.f, 0.f, 0.f, 0.f};
@@ -382,7 +386,9 @@ __global__ void __launch_bounds__(kRotThreads) polish_kernel(PolishArgs a) {
 template <int N, typename CT>
 ttm_status launch_n_t(const SearchArgs& s, const PolishArgs& p, bool search_done, bool search_only,
                       cudaStream_t st, long long* cnt) {
-    const unsigned blocks = (unsigned)((s.nvox + kRotThreads - 1) / kRotThreads);
+    const size_t units = s.box.count();
+    if (units == 0) return TTM_OK;
+    const unsigned blocks = (unsigned)((units + kRotThreads - 1) / kRotThreads);
     if (!search_done) {
         const size_t smem = (size_t)kChunk * Geo<N>::K4 * sizeof(float) + kChunk * sizeof(int);
         TTM_CUDA_TRY(cudaFuncSetAttribute(search_simt_kernel<N, CT>,

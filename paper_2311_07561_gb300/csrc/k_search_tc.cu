@@ -10,8 +10,8 @@
 // components, a constant column that adds +1 to phi, zero padding), D in
 // tensor memory.
 //
-// One persistent CTA per SM (128 threads, thread t = voxel t of the tile =
-// TMEM lane t).  The FP16 grid table (2048 x 48, 192 KB, K-major core-matrix
+// One persistent CTA per SM; a tile is 128 consecutive voxels of the interior
+// box (thread t and t + 128 = voxel t of the tile = TMEM lane t).  The FP16 grid table (2048 x 48, 192 KB, K-major core-matrix
 // layout without swizzle) is copied into shared memory once per CTA.  Per
 // tile of 128 voxels: every thread writes its voxel's normalised components
 // as one FP16 row of A; thread 0 issues the MMAs of one 256-point chunk into
@@ -175,10 +175,12 @@ __global__ void __launch_bounds__(kThreads, 1) search_tc4_kernel(rot::SearchArgs
 
     const int lane_t = t & 127;            // TMEM lane = voxel of the tile
     const int colhalf = t >> 7;            // warps 4..7 take columns 128..255 of a chunk
-    const size_t ntiles = (a.nvox + 127) / 128;
+    const size_t units = a.box.count();
+    const size_t ntiles = (units + 127) / 128;
     for (size_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
-        const size_t v = tile * 128 + lane_t;
-        const bool in_range = v < a.nvox;
+        const size_t i = tile * 128 + lane_t;
+        const bool in_range = i < units;
+        const size_t v = in_range ? a.box.voxel((uint32_t)i) : 0;
         // components, score, normalised FP16 row of A (threads 0..127)
         float score = 0.f;
         if (colhalf == 0) {
@@ -293,7 +295,7 @@ __global__ void __launch_bounds__(kThreads, 1) search_tc4_kernel(rot::SearchArgs
         if (!ok) break;
         if (in_range) {
             a.score[v] = score;
-            rot::store_candidates(a.cand, v, ti, score > 0.f);
+            rot::store_candidates(a.cand, i, ti, score > 0.f);
         }
     }
     __syncthreads();
@@ -312,7 +314,8 @@ static ttm_status launch_tc4_t(const rot::SearchArgs& s, const uint16_t* grid_fp
     int dev = 0, sms = 0;
     TTM_CUDA_TRY(cudaGetDevice(&dev));
     TTM_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    const size_t ntiles = (s.nvox + 127) / 128;
+    const size_t ntiles = (s.box.count() + 127) / 128;
+    if (ntiles == 0) return TTM_OK;
     const unsigned grid = (unsigned)(ntiles < (size_t)sms ? ntiles : (size_t)sms);
     search_tc4_kernel<CT><<<grid, kThreads, kSmem, st>>>(s, reinterpret_cast<const uint4*>(grid_fp16),
                                                          end_bits, status);

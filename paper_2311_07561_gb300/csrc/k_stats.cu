@@ -136,10 +136,18 @@ __global__ void __launch_bounds__(kStatThreads) local_stats_kernel(StatsArgs a) 
         }
     }
 
-    const double nvox = (double)a.X * a.Y * a.Z;
-    const double mean = a.moments[0] / nvox;
-    const double var_f = fmax(a.moments[1] / nvox - mean * mean, 0.0);
-    const double floor_v = 1e-6 * a.mask_sum * var_f;
+    // volume statistics and the variance floor once per CTA (FP64 divisions are slow here)
+    __shared__ double sh[2];
+    if (threadIdx.x == 0) {
+        const double nvox = (double)a.X * a.Y * a.Z;
+        const double mean = a.moments[0] / nvox;
+        const double var_f = fmax(a.moments[1] / nvox - mean * mean, 0.0);
+        sh[0] = 1.0 / a.mask_sum;
+        sh[1] = 1e-6 * a.mask_sum * var_f;
+    }
+    __syncthreads();
+    const double inv_msum = sh[0];
+    const double floor_v = sh[1];
     const int x = x0 + lx;
     if (x >= a.X) return;
 #pragma unroll
@@ -149,7 +157,7 @@ __global__ void __launch_bounds__(kStatThreads) local_stats_kernel(StatsArgs a) 
         float wv = 0.f;
         if (interior(x, a.X, a.s) && interior(y, a.Y, a.s) && interior(z, a.Z, a.s)) {
             const double S1 = s1[v], S2 = s2[v];
-            const double V = S2 - S1 * S1 / a.mask_sum;
+            const double V = S2 - S1 * S1 * inv_msum;
             if (V > floor_v) wv = rsqrtf((float)V);
         }
         a.w[((size_t)z * a.Y + y) * a.X + x] = wv;

@@ -391,6 +391,104 @@ ttm_status check_ws(const ttm_plan_s* P, void* ws, size_t bytes) {
     return TTM_OK;
 }
 
+// ---- per-problem steps (shared by the C ABI and the plan-time tuner) ----
+
+// w for one problem (Algorithm 1, image block): FFT window sums when the
+// problem takes the FFT path with a compile-time x length, else run sums.
+ttm_status stats_problem(ttm_plan_s* plan, const ProblemData& pr, const float* vol, float* w,
+                         void* d_workspace, cudaStream_t st) {
+    double* d_mom = (double*)d_workspace;
+    TTM_CUDA_TRY(cudaMemsetAsync(d_mom, 0, 2 * sizeof(double), st));
+    TTM_TRY(timed(plan, KC_MOMENTS, st, [&] {
+        return launch_volume_moments(vol, pr.nvox(), d_mom, st, &plan->launches);
+    }));
+    const TemplateData& T = plan->tmpl[pr.tmpl];
+    if (pr.path == TTM_PATH_FFT && fft_template_length(pr.fft.Xp)) {
+        // window sums of (f - mean) and (f - mean)^2 as correlations with the mask
+        const size_t nspec = pr.fft.nspec();
+        char* base = (char*)d_workspace + kHeader;
+        float2* F1 = (float2*)base;
+        float2* F2 = F1 + nspec;
+        float2* prod = F2 + nspec;                       // two product spectra
+        float* sums = (float*)(prod + 2 * nspec);        // S1, S2 maps
+        const float2* mspec = plan->specs[pr.spec_index].d_mask_spec;
+        return timed(plan, KC_LOCAL_STATS, st, [&] {
+            TTM_TRY(launch_fft_forward(vol, pr.X, pr.Y, pr.Z, pr.fft, F1, st, &plan->launches, 1,
+                                       d_mom));
+            TTM_TRY(launch_fft_forward(vol, pr.X, pr.Y, pr.Z, pr.fft, F2, st, &plan->launches, 2,
+                                       d_mom));
+            TTM_TRY(launch_fft_spectrum_inverse_z(F1, mspec, 1, pr.fft, prod, st,
+                                                  &plan->launches));
+            TTM_TRY(launch_fft_spectrum_inverse_z(F2, mspec, 1, pr.fft, prod + nspec, st,
+                                                  &plan->launches));
+            TTM_TRY(launch_fft_inverse_yx(prod, 2, pr.X, pr.Y, pr.Z, pr.fft, sums, st,
+                                          &plan->launches));
+            return launch_stats_from_sums(sums, sums + pr.nvox(), w, pr.X, pr.Y, pr.Z, T.desc.s,
+                                          T.desc.mask_sum, d_mom, st, &plan->launches);
+        });
+    }
+    return timed(plan, KC_LOCAL_STATS, st, [&] {
+        return launch_local_stats(vol, pr.X, pr.Y, pr.Z, T, d_mom, w, st, &plan->launches);
+    });
+}
+
+// The K correlation maps of one problem into the workspace (FFT or direct).
+ttm_status corr_problem(ttm_plan_s* plan, const ProblemData& pr, const float* vol,
+                        void* d_workspace, cudaStream_t st) {
+    float* corr = (float*)((char*)d_workspace + kHeader);
+    if (pr.path == TTM_PATH_FFT) {
+        const size_t es = pr.mixed ? 2 : 4;
+        char* base = (char*)corr + align256((size_t)plan->K * pr.nvox() * es);
+        float2* spec = (float2*)base;
+        void* prod = base + align256(pr.fft.nspec() * sizeof(float2));
+        const SpecSet& sp = plan->specs[pr.spec_index];
+        TTM_TRY(timed(plan, KC_FFT_FORWARD, st, [&] {
+            return launch_fft_forward(vol, pr.X, pr.Y, pr.Z, pr.fft, spec, st, &plan->launches);
+        }));
+        TTM_TRY(timed(plan, KC_FFT_SPECTRUM, st, [&] {
+            return pr.mixed ? launch_fft_spectrum_inverse_z_bf16(spec, sp.d_spec_bf, plan->K,
+                                                                 pr.fft, prod, st, &plan->launches)
+                            : launch_fft_spectrum_inverse_z(spec, sp.d_spec, plan->K, pr.fft,
+                                                            (float2*)prod, st, &plan->launches);
+        }));
+        return timed(plan, KC_FFT_INVERSE, st, [&] {
+            return pr.mixed ? launch_fft_inverse_yx_bf16(prod, plan->K, pr.X, pr.Y, pr.Z, pr.fft,
+                                                         corr, st, &plan->launches)
+                            : launch_fft_inverse_yx((float2*)prod, plan->K, pr.X, pr.Y, pr.Z,
+                                                    pr.fft, corr, st, &plan->launches);
+        });
+    }
+    const TemplateData& T = plan->tmpl[pr.tmpl];
+    return timed(plan, KC_DIRECT_CORR, st, [&] {
+        return launch_direct_corr(vol, pr.X, pr.Y, pr.Z, T, plan->K, corr, st, &plan->launches);
+    });
+}
+
+// Score, rotation search and refinement of one problem from its correlation
+// maps (Sec. 3.3-3.4); exterior voxels get the exterior values.
+ttm_status rotation_problem(ttm_plan_s* plan, const ProblemData& pr, const float* w, float* score,
+                            float* quat, float* lam, float* comp_out, void* d_workspace,
+                            cudaStream_t st) {
+    float* corr = (float*)((char*)d_workspace + kHeader);
+    uint16_t* cand = (uint16_t*)((char*)corr + corr_region_bytes(plan, pr));
+    int* d_status = (int*)((char*)d_workspace + 32);
+    const TemplateData& T = plan->tmpl[pr.tmpl];
+    const VoxBox box = interior_box(pr.X, pr.Y, pr.Z, T.desc.s);
+    TTM_TRY(timed(plan, KC_EXTERIOR, st, [&] {
+        return launch_exterior_fill(pr.Z, box, plan->K, score, quat, lam, comp_out, st,
+                                    &plan->launches);
+    }));
+    TTM_TRY(timed(plan, KC_ROTATION, st, [&] {
+        return launch_rotation_search(plan->n_order, corr, pr.mixed, w, pr.nvox(), box,
+                                      plan->grid, cand, d_status, score, st, &plan->launches);
+    }));
+    return timed(plan, KC_POLISH, st, [&] {
+        return launch_rotation_polish(plan->n_order, corr, pr.mixed, w, pr.nvox(), box,
+                                      plan->grid, cand, score, quat, lam, comp_out, st,
+                                      &plan->launches);
+    });
+}
+
 }  // namespace
 }  // namespace ttm
 
@@ -571,6 +669,17 @@ ttm_status ttm_plan_problem_path(ttm_plan_t plan, int problem, int* path) {
     return TTM_OK;
 }
 
+ttm_status ttm_plan_problem_fft_box(ttm_plan_t plan, int problem, int* box) {
+    if (!plan || !box || problem < 0 || problem >= (int)plan->prob.size())
+        return TTM_ERR_INVALID_ARG;
+    const ProblemData& pr = plan->prob[problem];
+    const bool fft = pr.path == TTM_PATH_FFT;
+    box[0] = fft ? pr.fft.Xp : 0;
+    box[1] = fft ? pr.fft.Yp : 0;
+    box[2] = fft ? pr.fft.Zp : 0;
+    return TTM_OK;
+}
+
 ttm_status ttm_plan_launch_count(ttm_plan_t plan, long long* launches) {
     if (!plan || !launches) return TTM_ERR_INVALID_ARG;
     *launches = plan->launches;
@@ -623,7 +732,7 @@ const char* ttm_kernel_class_name(int c) {
     static const char* names[TTM_KERNEL_CLASSES] = {
         "volume_moments", "local_stats", "direct_corr", "rotation_search", "fft_forward",
         "fft_spectrum_inverse", "fft_inverse", "peaks", "template", "fft_plan", "rotation_polish",
-        "reserved"};
+        "exterior_fill"};
     if (c < 0 || c >= TTM_KERNEL_CLASSES) return "unknown";
     return names[c];
 }
@@ -641,46 +750,8 @@ ttm_status ttm_local_stats(ttm_plan_t plan, const float* const* d_vols, float* c
         if (!d_vols[p] || !d_w[p] || !aligned(d_vols[p], 4) || !aligned(d_w[p], 4))
             return TTM_ERR_INVALID_ARG;
     cudaStream_t st = (cudaStream_t)stream;
-    double* d_mom = (double*)d_workspace;
-    for (int p = 0; p < np; ++p) {
-        const ProblemData& pr = plan->prob[p];
-        TTM_CUDA_TRY(cudaMemsetAsync(d_mom, 0, 2 * sizeof(double), st));
-        TTM_TRY(timed(plan, KC_MOMENTS, st, [&] {
-            return launch_volume_moments(d_vols[p], pr.nvox(), d_mom, st, &plan->launches);
-        }));
-        if (pr.path == TTM_PATH_FFT && fft_template_length(pr.fft.Xp)) {
-            // Algorithm 1: window sums of (f - mean) and (f - mean)^2 as
-            // correlations with the mask, through the FFT
-            const TemplateData& T = plan->tmpl[pr.tmpl];
-            const size_t nspec = pr.fft.nspec();
-            char* base = (char*)d_workspace + kHeader;
-            float2* F1 = (float2*)base;
-            float2* F2 = F1 + nspec;
-            float2* prod = F2 + nspec;                       // two product spectra
-            float* sums = (float*)(prod + 2 * nspec);        // S1, S2 maps
-            const float2* mspec = plan->specs[pr.spec_index].d_mask_spec;
-            TTM_TRY(timed(plan, KC_LOCAL_STATS, st, [&] {
-                TTM_TRY(launch_fft_forward(d_vols[p], pr.X, pr.Y, pr.Z, pr.fft, F1, st,
-                                           &plan->launches, 1, d_mom));
-                TTM_TRY(launch_fft_forward(d_vols[p], pr.X, pr.Y, pr.Z, pr.fft, F2, st,
-                                           &plan->launches, 2, d_mom));
-                TTM_TRY(launch_fft_spectrum_inverse_z(F1, mspec, 1, pr.fft, prod, st,
-                                                      &plan->launches));
-                TTM_TRY(launch_fft_spectrum_inverse_z(F2, mspec, 1, pr.fft, prod + nspec, st,
-                                                      &plan->launches));
-                TTM_TRY(launch_fft_inverse_yx(prod, 2, pr.X, pr.Y, pr.Z, pr.fft, sums, st,
-                                              &plan->launches));
-                return launch_stats_from_sums(sums, sums + pr.nvox(), d_w[p], pr.X, pr.Y, pr.Z,
-                                              T.desc.s, T.desc.mask_sum, d_mom, st,
-                                              &plan->launches);
-            }));
-        } else {
-            TTM_TRY(timed(plan, KC_LOCAL_STATS, st, [&] {
-                return launch_local_stats(d_vols[p], pr.X, pr.Y, pr.Z, plan->tmpl[pr.tmpl], d_mom,
-                                          d_w[p], st, &plan->launches);
-            }));
-        }
-    }
+    for (int p = 0; p < np; ++p)
+        TTM_TRY(stats_problem(plan, plan->prob[p], d_vols[p], d_w[p], d_workspace, st));
     return TTM_OK;
 }
 
@@ -697,53 +768,14 @@ ttm_status ttm_correlate(ttm_plan_t plan, const float* const* d_vols, const floa
             return TTM_ERR_INVALID_ARG;
     }
     cudaStream_t st = (cudaStream_t)stream;
-    float* corr = (float*)((char*)d_workspace + kHeader);
     TTM_CUDA_TRY(cudaMemsetAsync((char*)d_workspace + 32, 0, sizeof(int), st));
     for (int p = 0; p < np; ++p) {
         const ProblemData& pr = plan->prob[p];
-        const TemplateData& T = plan->tmpl[pr.tmpl];
-        if (pr.path == TTM_PATH_FFT) {
-            const size_t es = pr.mixed ? 2 : 4;
-            char* base = (char*)corr + align256((size_t)plan->K * pr.nvox() * es);
-            float2* spec = (float2*)base;
-            void* prod = base + align256(pr.fft.nspec() * sizeof(float2));
-            const SpecSet& sp = plan->specs[pr.spec_index];
-            TTM_TRY(timed(plan, KC_FFT_FORWARD, st, [&] {
-                return launch_fft_forward(d_vols[p], pr.X, pr.Y, pr.Z, pr.fft, spec, st,
-                                          &plan->launches);
-            }));
-            TTM_TRY(timed(plan, KC_FFT_SPECTRUM, st, [&] {
-                return pr.mixed ? launch_fft_spectrum_inverse_z_bf16(spec, sp.d_spec_bf, plan->K,
-                                                                     pr.fft, prod, st, &plan->launches)
-                                : launch_fft_spectrum_inverse_z(spec, sp.d_spec, plan->K, pr.fft,
-                                                                (float2*)prod, st, &plan->launches);
-            }));
-            TTM_TRY(timed(plan, KC_FFT_INVERSE, st, [&] {
-                return pr.mixed ? launch_fft_inverse_yx_bf16(prod, plan->K, pr.X, pr.Y, pr.Z, pr.fft,
-                                                             corr, st, &plan->launches)
-                                : launch_fft_inverse_yx((float2*)prod, plan->K, pr.X, pr.Y, pr.Z,
-                                                        pr.fft, corr, st, &plan->launches);
-            }));
-        } else {
-            TTM_TRY(timed(plan, KC_DIRECT_CORR, st, [&] {
-                return launch_direct_corr(d_vols[p], pr.X, pr.Y, pr.Z, T, plan->K, corr, st,
-                                          &plan->launches);
-            }));
-        }
-        uint16_t* cand = (uint16_t*)((char*)corr + corr_region_bytes(plan, pr));
-        int* d_status = (int*)((char*)d_workspace + 32);
-        TTM_TRY(timed(plan, KC_ROTATION, st, [&] {
-            return launch_rotation_search(plan->n_order, corr, pr.mixed, d_w[p], pr.nvox(),
-                                          plan->grid, cand, d_status, d_score[p], st,
-                                          &plan->launches);
-        }));
-        TTM_TRY(timed(plan, KC_POLISH, st, [&] {
-            return launch_rotation_polish(plan->n_order, corr, pr.mixed, d_w[p], pr.nvox(),
-                                          plan->grid, cand, d_score[p], d_quat[p],
-                                          d_lambda ? d_lambda[p] : nullptr,
-                                          d_components_out ? d_components_out[p] : nullptr, st,
-                                          &plan->launches);
-        }));
+        TTM_TRY(corr_problem(plan, pr, d_vols[p], d_workspace, st));
+        TTM_TRY(rotation_problem(plan, pr, d_w[p], d_score[p], d_quat[p],
+                                 d_lambda ? d_lambda[p] : nullptr,
+                                 d_components_out ? d_components_out[p] : nullptr, d_workspace,
+                                 st));
     }
     return TTM_OK;
 }

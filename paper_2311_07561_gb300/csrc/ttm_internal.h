@@ -58,6 +58,33 @@ struct SpecSet {
     float2* d_mask_spec = nullptr;     // FP32 mask spectrum (local statistics)
 };
 
+// Interior box of an X x Y x Z volume for template edge s: the voxels whose
+// whole s^3 box lies inside the volume, [c, n - s + c] per axis (c = s / 2).
+// The rotation kernels enumerate only these voxels, x fastest; unit i maps to
+// the voxel with linear index voxel(i).
+struct VoxBox {
+    int X = 0, Y = 0;
+    int x0 = 0, y0 = 0, z0 = 0;
+    uint32_t nx = 0, ny = 0, nz = 0;
+    __host__ __device__ size_t count() const { return (size_t)nx * ny * nz; }
+    __device__ __forceinline__ size_t voxel(uint32_t i) const {
+        const uint32_t r = i / nx, x = i - r * nx;
+        const uint32_t z = r / ny, y = r - z * ny;
+        return ((size_t)(z0 + z) * Y + (y0 + y)) * X + (x0 + x);
+    }
+};
+
+inline VoxBox interior_box(int X, int Y, int Z, int s) {
+    VoxBox b;
+    b.X = X; b.Y = Y;
+    const int c = s / 2;
+    b.x0 = c; b.y0 = c; b.z0 = c;
+    b.nx = X >= s ? (uint32_t)(X - s + 1) : 0u;
+    b.ny = Y >= s ? (uint32_t)(Y - s + 1) : 0u;
+    b.nz = Z >= s ? (uint32_t)(Z - s + 1) : 0u;
+    return b;
+}
+
 // Rotation search grid (device tables owned by the plan).
 struct RotGrid {
     int n_grid = 0, n_cells = 0, n_cand = 0, newton = 0;
@@ -73,7 +100,7 @@ struct RotGrid {
 namespace ttm {
 enum KernelClass {
     KC_MOMENTS = 0, KC_LOCAL_STATS, KC_DIRECT_CORR, KC_ROTATION, KC_FFT_FORWARD, KC_FFT_SPECTRUM,
-    KC_FFT_INVERSE, KC_PEAKS, KC_TEMPLATE, KC_FFT_PLAN, KC_POLISH, KC_RESERVED
+    KC_FFT_INVERSE, KC_PEAKS, KC_TEMPLATE, KC_FFT_PLAN, KC_POLISH, KC_EXTERIOR
 };
 struct TimedLaunch {
     int cls;
@@ -117,14 +144,21 @@ ttm_status launch_direct_corr(const float* f, int X, int Y, int Z, const Templat
                               int K, float* corr, cudaStream_t st, long long* cnt);
 
 // per-voxel score + candidate search (tensor cores for order 4 with the
-// default 2048-point grid, CUDA cores otherwise), then refinement
+// default 2048-point grid, CUDA cores otherwise) and refinement, over the
+// interior box only; launch_exterior_fill writes the exterior values (score 0,
+// q = (1, 0, 0, 0), lambda 0, C 0) of the voxels outside it.  cand holds one
+// 16-byte record per interior voxel.
 ttm_status launch_rotation_search(int n_order, const void* corr, bool bf16, const float* w,
-                                  size_t nvox, const RotGrid& g, uint16_t* cand, int* status,
-                                  float* score, cudaStream_t st, long long* cnt);
+                                  size_t nvox, const VoxBox& box, const RotGrid& g,
+                                  uint16_t* cand, int* status, float* score, cudaStream_t st,
+                                  long long* cnt);
 ttm_status launch_rotation_polish(int n_order, const void* corr, bool bf16, const float* w,
-                                  size_t nvox, const RotGrid& g, const uint16_t* cand,
-                                  const float* score, float* quat, float* lambda, float* comp_out,
-                                  cudaStream_t st, long long* cnt);
+                                  size_t nvox, const VoxBox& box, const RotGrid& g,
+                                  const uint16_t* cand, const float* score, float* quat,
+                                  float* lambda, float* comp_out, cudaStream_t st,
+                                  long long* cnt);
+ttm_status launch_exterior_fill(int Z, const VoxBox& box, int K, float* score, float* quat,
+                                float* lambda, float* comp_out, cudaStream_t st, long long* cnt);
 void build_grid_fp16(const float* m_rows, int K4, std::vector<uint16_t>& out);
 
 // tensor template build

@@ -200,6 +200,28 @@ def test_ragged_volume_and_order_two(ttm, path):
                     res["quat"][pts[:, 2], pts[:, 1], pts[:, 0]], 2)
 
 
+@pytest.mark.parametrize("shape_zyx,boxes", [
+    ((36, 150, 230), (240, 160, 48)),     # radix 16 x 3 x 5, 16 x 2 x 5, 16 x 3
+    ((20, 140, 280), (288, 144, 32)),     # radix 16 x 2 x 3 x 3, 16 x 3 x 3, 16 x 2
+])
+def test_fft_smooth_lengths(ttm, shape_zyx, boxes):
+    """FFT boxes of 2^p 3^a 5^b lengths (radix-3 and radix-5 stages): the
+    plan pads each axis to the smallest such length, and the interior
+    components, w and score agree with the oracle's FP64 FFT."""
+    wl = synth.make_workload(shape_zyx, 9, 3, 3, 1.0, 4, 200, radius=4, seeds=(11, 12, 13))
+    T = o.tensor_template(wl.template, wl.mask, wl.quadrature.astype(np.float64), wl.weights, 4)
+    comp, desc = ttm.build_template(wl.template, wl.mask, 4, wl.quadrature)
+    res = _run(ttm, wl, comp, desc, opts=_opts(ttm, "fft"))
+    assert tuple(ttm.ttm_plan_problem_fft_box(res["matcher"].plan, 0)) == boxes
+    w_o, C_o = o.ttm_components(wl.volume, T, wl.mask)
+    assert np.abs(res["comp"] - C_o).max() <= TOL
+    nz = w_o > 0
+    assert np.array_equal(res["w"] > 0, nz)
+    assert (np.abs(res["w"][nz] - w_o[nz]) / w_o[nz]).max() <= 1e-5
+    assert np.abs(res["score"] - o.frobenius_score(C_o, 4)).max() <= TOL
+    res["matcher"].close()
+
+
 @pytest.mark.parametrize("path", PATHS)
 def test_order_six(ttm, path):
     wl = synth.make_workload((30, 28, 26), 9, 3, 1, 1.0, 6, 300, radius=4, seeds=(2, 3, 4))
