@@ -41,7 +41,17 @@ WORKLOAD = dict(
         "SNR 0.5, ball mask r=15, tensor order n=4 (K=35)",
     c3="512x512x512 FP32 volume, 200 planted copies of a 40^3 lowpassed 30-blob template, "
        "SNR 0.3, ball mask r=19, tensor order n=4 (K=35)",
+    c5="928x928x464 FP32 volume, 2000 planted copies of a 64^3 lowpassed 30-blob template, "
+       "SNR 0.2, ball mask r=31, tensor order n=6 (K=84), quadrature of 20000 rotations; FFT box "
+       "960x960x480; mixed precision (bf16 template spectra, products and maps resident in HBM)",
+    c4="16 FP32 volumes of uneven 2*3*5-smooth sizes (128^3 to 384x384x192, 216 M voxels) x 4 "
+       "lowpassed 30-blob templates (24^3, 32^3, 40^3, 48^3; ball masks r=11,15,19,23): 64 "
+       "(volume, template) problems in one plan, 20-100 planted copies of each template per "
+       "volume, SNR 0.5, tensor order n=4 (K=35); autotuned FFT-vs-direct, one CUDA graph",
 )
+BATCH_WORKLOADS = ("c4",)
+CPU_SAMPLE_SHAPES = dict(c3=dict(shape_zyx=(160, 160, 160), copies=10),
+                         c5=dict(shape_zyx=(192, 192, 192), copies=8))
 WORKLOAD_OVERRIDES = dict(c2s=("c2", dict(shape_zyx=(128, 128, 128), copies=8)))
 
 
@@ -64,10 +74,11 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c2s", "c3"])
+    ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c2s", "c3", "c4", "c5"])
     ap.add_argument("--path", default="auto", choices=["auto", "direct", "fft"])
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "mixed"],
-                    help="storage of spectra/products/correlation maps on the FFT path")
+    ap.add_argument("--precision", default=None, choices=["fp32", "mixed"],
+                    help="storage of spectra/products/correlation maps on the FFT path "
+                         "(default fp32; mixed for c5, whose FP32 maps and spectra exceed HBM)")
     ap.add_argument("--mixed-compare", action=argparse.BooleanOptionalAction, default=True,
                     help="with fp32, also time the mixed-precision plan on the same volume")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -77,7 +88,10 @@ def parse():
     ap.add_argument("--cpu-sample", type=int, default=0,
                     help="internal: run the oracle on this many sampled voxels and print JSON")
     ap.add_argument("--sample-steps", type=int, default=1)
-    return ap.parse_args()
+    args = ap.parse_args()
+    if args.precision is None:
+        args.precision = "mixed" if args.workload == "c5" else "fp32"
+    return args
 
 
 # ---------------------------------------------------------------------------
@@ -88,7 +102,19 @@ def cpu_sample(workload: str, n_vox: int, steps: int) -> dict:
     import numpy as np
     import synth
     from oracle import ttm_oracle as o
-    wl = load_workload(workload, n_rot=300)
+    if workload in BATCH_WORKLOADS:
+        # the batch's first volume with its 32^3 template (cost per voxel is
+        # set by the template and the order, not by the data)
+        cfg = synth.BATCH_CONFIGS[workload]
+        bw = synth.batch_workload(workload, shapes_zyx=cfg["shapes_zyx"][:1], sizes=(32,),
+                                  n_rot=300)
+        wl = synth.Workload("batch-sample", bw.volumes[0], bw.templates[0], bw.masks[0],
+                            bw.radii[0], bw.n_order, bw.quadrature, bw.weights,
+                            bw.positions[0][0], bw.planted_quats[0][0], 0.0, bw.snr)
+    else:
+        # the per-voxel cost of the oracle is set by the template box and the
+        # order, so the large configs are sampled from a smaller volume
+        wl = load_workload(workload, n_rot=300, **CPU_SAMPLE_SHAPES.get(workload, {}))
     s = wl.template.shape[0]
     c = s // 2
     T = o.tensor_template(wl.template, wl.mask, wl.quadrature.astype(np.float64), wl.weights,
@@ -117,12 +143,18 @@ def run_cpu_sample(workload: str, n_vox: int, steps: int) -> dict:
     return json.loads(out.stdout.strip().splitlines()[-1])
 
 
-def cpu_baseline_obj(res: dict) -> dict:
+def cpu_baseline_obj(res: dict, workload: str = "") -> dict:
     tot = sum(res["times"])
     per_vox = tot / (res["n_vox"] * len(res["times"]))
+    where = "the same workload"
+    if workload in CPU_SAMPLE_SHAPES:
+        where = (f"a {'x'.join(map(str, CPU_SAMPLE_SHAPES[workload]['shape_zyx'][::-1]))} volume "
+                 "with the same template, order and mask")
+    elif workload in BATCH_WORKLOADS:
+        where = "the batch's first volume with its 32^3 template"
     return dict(value=1.0 / per_vox, unit=UNIT, cores=1, kind="oracle",
-                sample=f"{len(res['times'])} x {res['n_vox']} random interior voxels of the same "
-                       "workload: local statistics, K component correlations by direct sum, "
+                sample=f"{len(res['times'])} x {res['n_vox']} random interior voxels of {where}: "
+                       "local statistics, K component correlations by direct sum, "
                        "Frobenius score and dominant Z-eigenpair (FP64 numpy oracle, one BLAS "
                        f"thread); {tot:.1f} s of CPU work; tensor template built beforehand")
 
@@ -350,7 +382,7 @@ def run_ours(args) -> None:
     # classical template matching (Algorithm 1) at 1000 rotations on the same
     # volume and GPU: the comparator of the paper's speed-up claim
     classical = None
-    if args.classical and path == 2:
+    if args.classical and path == 2 and args.workload in ("c2", "c2s", "c3"):
         import synth as _s
         qc = torch.from_numpy(_s.shoemake_quaternions(1000, 4).astype(np.float32)).to(dev)
         tc = torch.from_numpy(wl.template).to(dev)
@@ -420,7 +452,7 @@ def run_ours(args) -> None:
                   n_interior)
     cpu = None
     if not args.no_cpu_baseline and world == 1:
-        cpu = cpu_baseline_obj(run_cpu_sample(args.workload, 128, 2))
+        cpu = cpu_baseline_obj(run_cpu_sample(args.workload, 128, 2), args.workload)
     line = dict(
         metric=METRIC, value=value, unit=UNIT, n_gpus=world, steps=args.steps,
         warmup=args.warmup, ms_per_step=t_max / args.steps, higher_is_better=True,
@@ -445,6 +477,189 @@ def run_ours(args) -> None:
         dist.destroy_process_group()
 
 
+def run_batch(args) -> None:
+    """Batch workload: every volume of the batch against every template, all
+    problems in one plan (autotuned paths), each step one CUDA-graph replay."""
+    import numpy as np
+    import torch
+
+    import paper_2311_07561_gb300 as ttm
+    import synth
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if not os.path.exists(ttm.LIB_PATH):
+        import __graft_entry__
+        __graft_entry__.build()
+    ttm.load_library()
+
+    bw = synth.batch_workload(args.workload)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record()
+    tmpls = []
+    for t, m in zip(bw.templates, bw.masks):
+        comp, desc = ttm.build_template(t, m, bw.n_order, bw.quadrature)
+        tmpls.append((comp, desc, m))
+    ev1.record()
+    torch.cuda.synchronize()
+    build_ms = ev0.elapsed_time(ev1)
+    opts = ttm.PlanOpts()
+    opts.path = {"auto": ttm.TTM_PATH_TUNE, "direct": 1, "fft": 2}[args.path]
+    opts.precision = ttm.TTM_PREC_MIXED if args.precision == "mixed" else ttm.TTM_PREC_FP32
+    dvols = [torch.from_numpy(v).to(dev) for v in bw.volumes]
+    problems, vols = [], []
+    for v, vol in enumerate(bw.volumes):
+        for k in range(len(bw.templates)):
+            problems.append((vol.shape[::-1], k))
+            vols.append(dvols[v])
+    t0 = time.perf_counter()
+    matcher = ttm.Matcher(tmpls, problems, opts=opts)
+    plan_s = time.perf_counter() - t0
+    paths = [ttm.ttm_plan_problem_path(matcher.plan, p) for p in range(len(problems))]
+    tuning = [ttm.ttm_plan_problem_tuning(matcher.plan, p) for p in range(len(problems))]
+    nvox_total = sum(int(np.prod(d)) for d, _ in problems)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+
+    for _ in range(args.warmup):
+        matcher.run(vols)
+    torch.cuda.synchronize()
+    l0 = matcher.launch_count()
+    graph = matcher.capture(vols)
+    launches_per_step = (matcher.launch_count() - l0) // 2      # eager warm-up + capture
+    torch.cuda.synchronize()
+    for _ in range(args.warmup):
+        graph.replay()
+    torch.cuda.synchronize()
+    clocks = Clocks(torch.cuda.current_device())
+    clocks.start()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    stops = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    for k in range(args.steps):
+        flush.zero_()
+        starts[k].record(stream)
+        graph.replay()
+        stops[k].record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clk = clocks.stop()
+    status = ttm.ttm_plan_device_status(matcher.plan, matcher.ws)
+    if status != 0:
+        raise RuntimeError(f"device status {ttm.ttm_status_string(status)}")
+    total_ms = sum(a.elapsed_time(b) for a, b in zip(starts, stops))
+    t_max = total_ms
+    if dist:
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_max = float(t.item())
+    value = nvox_total * args.steps * world / (t_max * 1e-3)
+
+    # per-kernel breakdown from one eager step outside the timed region
+    ttm.ttm_plan_timing(matcher.plan)
+    ttm.ttm_plan_enable_timing(matcher.plan, True)
+    flush.zero_()
+    matcher.run(vols)
+    torch.cuda.synchronize()
+    kern = {name: dict(ms=ms, launches=n) for name, (ms, n) in ttm.ttm_plan_timing(matcher.plan).items()}
+    ttm.ttm_plan_enable_timing(matcher.plan, False)
+
+    e2e = None
+    if not args.no_e2e:
+        pin_in = [torch.from_numpy(v).pin_memory() for v in bw.volumes]
+        pin_out = [(torch.empty(tuple(d[::-1]), dtype=torch.float32).pin_memory(),
+                    torch.empty(tuple(d[::-1]) + (4,), dtype=torch.float32).pin_memory(),
+                    torch.empty(tuple(d[::-1]), dtype=torch.float32).pin_memory())
+                   for d, _ in problems]
+        h2d = sum(v.nbytes for v in bw.volumes)
+        d2h = sum(int(np.prod(d)) * 24 for d, _ in problems)
+
+        def e2e_step():
+            for dv, hv in zip(dvols, pin_in):
+                dv.copy_(hv, non_blocking=True)
+            graph.replay()
+            for p, (so, qo, lo) in enumerate(pin_out):
+                so.copy_(matcher.score[p], non_blocking=True)
+                qo.copy_(matcher.quat[p], non_blocking=True)
+                lo.copy_(matcher.lam[p], non_blocking=True)
+        e2e_step()
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        e_ms = 0.0
+        for k in range(args.steps):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            e2e_step()
+            b.record(stream)
+            b.synchronize()
+            e_ms += a.elapsed_time(b)
+        if dist:
+            t = torch.tensor([e_ms], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e_ms = float(t.item())
+        e2e = dict(value=nvox_total * args.steps * world / (e_ms * 1e-3), unit=UNIT,
+                   h2d_bytes_per_step=h2d, d2h_bytes_per_step=d2h)
+
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        pass
+    n_int = 0
+    spec_bytes = 0.0
+    for (X, Y, Z), k in problems:
+        sk = bw.templates[k].shape[0]
+        n_int += max(X - sk + 1, 0) * max(Y - sk + 1, 0) * max(Z - sk + 1, 0)
+        spec_bytes += 8.0 * (X // 2 + 1) * Y * Z
+    rf = roofline(kern, 1, nvox_total, tmpls[0][1].K, 0, 2048, 8, 4, peaks,
+                  spec_bytes / max(1, len(problems)), n_int)
+    cpu = None
+    if not args.no_cpu_baseline and world == 1:
+        cpu = cpu_baseline_obj(run_cpu_sample(args.workload, 128, 2), args.workload)
+    n_fft = sum(1 for p in paths if p == ttm.TTM_PATH_FFT)
+    line = dict(
+        metric=METRIC, value=value, unit=UNIT, n_gpus=world, steps=args.steps,
+        warmup=args.warmup, ms_per_step=t_max / args.steps, higher_is_better=True,
+        scaling="weak", vs_baseline=None, dtype="f32" if args.precision == "fp32" else "bf16/f32",
+        data="synthetic",
+        config=dict(workload=WORKLOAD[args.workload], problems=len(problems),
+                    voxels=nvox_total, interior_voxels=n_int, tensor_order=bw.n_order,
+                    K=tmpls[0][1].K, paths=dict(fft=n_fft, direct=len(paths) - n_fft),
+                    tuned_problems=sum(1 for t in tuning if t[0] >= 0 and t[1] >= 0),
+                    plan_seconds=round(plan_s, 2), template_build_ms=round(build_ms, 2),
+                    graph="one CUDA graph replay per step (all problems)",
+                    l2="flushed (256 MB write) before every timed step",
+                    parallelism="replicas" if world > 1 else "single GPU",
+                    quadrature_rotations=int(len(bw.quadrature))),
+        roofline=rf, cpu_baseline=cpu, e2e=e2e, gpu_launches=launches_per_step * args.steps,
+        clocks=clk,
+        kernels={k: dict(ms_per_step=round(v["ms"], 4), launches_per_step=v["launches"],
+                         share=round(v["ms"] / sum(x["ms"] for x in kern.values()), 4))
+                 for k, v in kern.items()},
+        kernels_note="per-kernel times from one eager (not graph) step outside the timed region",
+    )
+    print(json.dumps(line), flush=True)
+    matcher.close()
+    if dist:
+        dist.destroy_process_group()
+
+
 def run_reference(args) -> None:
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -455,7 +670,7 @@ def run_reference(args) -> None:
     times = res["times"][args.warmup:]
     total = sum(times)
     value = n_vox * len(times) / total
-    cpu = cpu_baseline_obj(dict(times=times, n_vox=n_vox))
+    cpu = cpu_baseline_obj(dict(times=times, n_vox=n_vox), args.workload)
     line = dict(
         metric=METRIC, value=value, unit=UNIT, n_gpus=args.gpus, steps=args.steps,
         warmup=args.warmup, ms_per_step=1e3 * total / len(times), higher_is_better=True,
@@ -474,6 +689,8 @@ def main():
         return
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload in BATCH_WORKLOADS:
+        run_batch(args)
     else:
         run_ours(args)
 

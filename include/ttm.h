@@ -87,6 +87,13 @@ typedef struct ttm_peak {
 #define TTM_PATH_AUTO   0   /* planner picks FFT or direct per problem         */
 #define TTM_PATH_DIRECT 1   /* direct sum over the mask support                */
 #define TTM_PATH_FFT    2   /* FFT with the fused K-way spectrum multiply      */
+#define TTM_PATH_TUNE   3   /* planner times both paths on a random volume of  */
+                            /* each distinct problem shape (local statistics + */
+                            /* K correlations, 1 warm-up + 2 timed runs each) */
+                            /* and keeps the faster, wherever its cost model  */
+                            /* puts them within 8x of each other (else the    */
+                            /* model decides); plan creation then takes longer */
+                            /* and needs scratch memory for one problem       */
 
 /* Precision of the correlation step.  In both modes all arithmetic is FP32
  * except the rotation search of order 4, which runs on the tensor cores with
@@ -200,6 +207,11 @@ ttm_status ttm_plan_workspace_size(ttm_plan_t plan, size_t* bytes);
 
 /* Path the plan chose for problem p (TTM_PATH_DIRECT or TTM_PATH_FFT). */
 ttm_status ttm_plan_problem_path(ttm_plan_t plan, int problem, int* path);
+
+/* Autotuner timings of problem p (TTM_PATH_TUNE): ms[0] = direct path,
+ * ms[1] = FFT path (local statistics + K correlations, best of 2 runs), or
+ * -1 where a path was not timed (the cost model decided).  Host-only. */
+ttm_status ttm_plan_problem_tuning(ttm_plan_t plan, int problem, double* ms);
 
 /* Padded FFT box of problem p: box[0..2] = (Xp, Yp, Zp), each the smallest
  * supported length 2^p 3^a 5^b (16..1024), else a power of two, not below

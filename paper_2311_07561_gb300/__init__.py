@@ -18,6 +18,7 @@ from ._binding import (  # noqa: F401
     TTM_PATH_AUTO,
     TTM_PATH_DIRECT,
     TTM_PATH_FFT,
+    TTM_PATH_TUNE,
     TTM_PREC_FP32,
     TTM_PREC_MIXED,
     TTM_NOALLOC_SCRATCH_BYTES,
@@ -42,6 +43,7 @@ from ._binding import (  # noqa: F401
     ttm_plan_launch_count,
     ttm_plan_problem_path,
     ttm_plan_problem_fft_box,
+    ttm_plan_problem_tuning,
     ttm_plan_timing,
     ttm_plan_workspace_size,
     ttm_status_string,

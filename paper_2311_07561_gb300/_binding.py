@@ -23,14 +23,15 @@ STATUS_NAMES = {
     -3: "TTM_ERR_OUT_OF_MEMORY", -4: "TTM_ERR_CUDA", -5: "TTM_ERR_TIMEOUT",
     -6: "TTM_ERR_NUMERIC", -7: "TTM_ERR_WORKSPACE",
 }
-TTM_PATH_AUTO, TTM_PATH_DIRECT, TTM_PATH_FFT = 0, 1, 2
+TTM_PATH_AUTO, TTM_PATH_DIRECT, TTM_PATH_FFT, TTM_PATH_TUNE = 0, 1, 2, 3
 TTM_PREC_FP32, TTM_PREC_MIXED = 0, 1
 
 # Every symbol include/ttm.h declares.
 EXPORTED = (
     "ttm_status_string", "ttm_device_count", "ttm_build_workspace_size",
     "ttm_build_tensor_template", "ttm_plan", "ttm_plan_workspace_size",
-    "ttm_plan_problem_path", "ttm_plan_problem_fft_box", "ttm_plan_launch_count", "ttm_plan_destroy",
+    "ttm_plan_problem_path", "ttm_plan_problem_fft_box", "ttm_plan_problem_tuning",
+    "ttm_plan_launch_count", "ttm_plan_destroy",
     "ttm_local_stats", "ttm_correlate", "ttm_extract_peaks", "ttm_plan_enable_timing",
     "ttm_plan_timing", "ttm_kernel_class_name", "ttm_build_tensor_template_noalloc",
     "ttm_plan_device_status", "ttm_classical_workspace_size", "ttm_classical_ncc",
@@ -87,6 +88,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "ttm_plan_workspace_size": (I, [P, ctypes.POINTER(S)]),
         "ttm_plan_problem_path": (I, [P, I, ctypes.POINTER(I)]),
         "ttm_plan_problem_fft_box": (I, [P, I, ctypes.POINTER(I)]),
+        "ttm_plan_problem_tuning": (I, [P, I, ctypes.POINTER(ctypes.c_double)]),
         "ttm_plan_launch_count": (I, [P, ctypes.POINTER(L)]),
         "ttm_plan_destroy": (None, [P]),
         "ttm_local_stats": (I, [P, PP, PP, P, S, P]),
@@ -228,6 +230,13 @@ def ttm_plan_problem_fft_box(plan: int, problem: int) -> tuple:
     out = (ctypes.c_int * 3)()
     _check(load_library().ttm_plan_problem_fft_box(plan, problem, out),
            "ttm_plan_problem_fft_box")
+    return tuple(out)
+
+
+def ttm_plan_problem_tuning(plan: int, problem: int) -> tuple:
+    """(direct ms, FFT ms) the autotuner measured for a problem; -1 = not timed."""
+    out = (ctypes.c_double * 2)()
+    _check(load_library().ttm_plan_problem_tuning(plan, problem, out), "ttm_plan_problem_tuning")
     return tuple(out)
 
 

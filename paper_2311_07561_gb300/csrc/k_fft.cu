@@ -505,28 +505,29 @@ ttm_status launch_spectra_to_bf16(const float2* a, void* b, size_t n, cudaStream
 
 // w from the FFT-based window sums of (f - mean) and (f - mean)^2 (Algorithm 1):
 // V = S2 - S1^2 / m_sum in FP64; interior only; floor 1e-6 m_sum var(f).
+// Block (x tile, y, z): no index divisions.  The volume statistics and the
+// floor are formed once per CTA (FP64 divisions are slow on this GPU); each
+// interior voxel does two FP64 operations plus conversions.
 __global__ void stats_from_sums_kernel(const float* __restrict__ s1, const float* __restrict__ s2,
                                        float* __restrict__ w, int X, int Y, int Z, int s,
                                        double mask_sum, const double* __restrict__ moments) {
-    // FP64 is slow on this GPU: the volume statistics and the floor are
-    // formed once per CTA; each voxel does three FP64 operations
     __shared__ double sh[2];
-    const size_t n = (size_t)X * Y * Z;
     if (threadIdx.x == 0) {
-        const double nv = (double)n;
+        const double nv = (double)X * Y * Z;
         const double mean = moments[0] / nv;
         const double var_f = fmax(moments[1] / nv - mean * mean, 0.0);
         sh[0] = 1.0 / mask_sum;
         sh[1] = 1e-6 * mask_sum * var_f;
     }
     __syncthreads();
-    const size_t v = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (v >= n) return;
-    const int x = (int)(v % X), y = (int)((v / X) % Y), z = (int)(v / ((size_t)X * Y));
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y, z = blockIdx.z;
+    if (x >= X) return;
+    const size_t v = ((size_t)z * Y + y) * X + x;
     float out = 0.f;
     if (interior(x, X, s) && interior(y, Y, s) && interior(z, Z, s)) {
         const double S1 = s1[v], S2 = s2[v];
-        const double V = S2 - S1 * S1 * sh[0];
+        const double V = fma(-S1, S1 * sh[0], S2);
         if (V > sh[1]) out = rsqrtf((float)V);
     }
     w[v] = out;
@@ -535,9 +536,9 @@ __global__ void stats_from_sums_kernel(const float* __restrict__ s1, const float
 ttm_status launch_stats_from_sums(const float* s1, const float* s2, float* w, int X, int Y, int Z,
                                   int s, double mask_sum, const double* moments, cudaStream_t st,
                                   long long* cnt) {
-    const size_t n = (size_t)X * Y * Z;
-    stats_from_sums_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(s1, s2, w, X, Y, Z, s,
-                                                                        mask_sum, moments);
+    if (Y > 65535 || Z > 65535) return TTM_ERR_UNSUPPORTED;
+    dim3 grid((unsigned)((X + 127) / 128), (unsigned)Y, (unsigned)Z);
+    stats_from_sums_kernel<<<grid, 128, 0, st>>>(s1, s2, w, X, Y, Z, s, mask_sum, moments);
     return after_launch(cnt);
 }
 

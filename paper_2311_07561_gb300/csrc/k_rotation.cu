@@ -24,8 +24,8 @@ ttm_status launch_rotation_search(int n_order, const void* corr, bool bf16, cons
     rot::SearchArgs sa;
     rot::PolishArgs pa;
     fill_args(corr, w, nvox, box, g, cand, score, nullptr, nullptr, nullptr, sa, pa);
-    if (n_order == 4 && g.d_gtab)
-        return launch_search_tc4(sa, g.d_gtab, g.d_endbits, status, bf16, st, cnt);
+    if (g.d_gtab && search_tc_supported(n_order, g.n_grid, g.n_cells))
+        return launch_search_tc(n_order, sa, g.d_gtab, status, bf16, st, cnt);
     switch (n_order) {
         case 2: return launch_rotation_n<2>(sa, pa, false, true, bf16, st, cnt);
         case 4: return launch_rotation_n<4>(sa, pa, false, true, bf16, st, cnt);

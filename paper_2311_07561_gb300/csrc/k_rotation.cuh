@@ -414,10 +414,10 @@ template <int N>
 ttm_status launch_rotation_n(const rot::SearchArgs& s, const rot::PolishArgs& p, bool search_done,
                              bool search_only, bool bf16, cudaStream_t st, long long* cnt);
 
-// tensor-core grid search for order 4 (k_search_tc.cu); returns
-// TTM_ERR_UNSUPPORTED when the grid does not have the fixed shape it needs
-ttm_status launch_search_tc4(const rot::SearchArgs& s, const uint16_t* grid_fp16,
-                             const uint32_t* end_bits, int* status, bool bf16, cudaStream_t st,
-                             long long* cnt);
+// tensor-core grid search for orders 4 and 6 with the default 2048-point grid
+// in 128 regions (k_search_tc.cu); returns TTM_ERR_UNSUPPORTED otherwise
+bool search_tc_supported(int n_order, int n_grid, int n_cells);
+ttm_status launch_search_tc(int n_order, const rot::SearchArgs& s, const uint16_t* grid_fp16,
+                            int* status, bool bf16, cudaStream_t st, long long* cnt);
 
 }  // namespace ttm

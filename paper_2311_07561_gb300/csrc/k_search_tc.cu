@@ -1,4 +1,4 @@
-// Tensor-core grid search of the per-voxel rotation for tensor order 4
+// Tensor-core grid search of the per-voxel rotation for tensor orders 4 and 6
 // (Sec. 3.3-3.4 of the paper: the rotation is the maximiser of
 // phi(Q) = C_n(x) . Q^(n) on the unit sphere).
 //
@@ -6,20 +6,23 @@
 //   Phi[v, g] = sum_alpha Cn[v, alpha] M[g, alpha],  M[g, alpha] = mu_alpha q_g^alpha,
 // with Cn = C / ||C||_F (a positive per-voxel scale changes no ranking).  It runs
 // on the 5th-generation tensor cores: tcgen05.mma kind::f16 (FP16 operands,
-// FP32 accumulation) with M = 128 voxels, N = 256 grid points, K = 48 (35
-// components, a constant column that adds +1 to phi, zero padding), D in
-// tensor memory.
+// FP32 accumulation) with M = 128 voxels, N = 256 grid points and K = KP (the
+// K components, a constant column that adds +1 to phi, zero padding to a
+// multiple of 16: 48 for order 4, 96 for order 6), D in tensor memory.
 //
 // One persistent CTA per SM; a tile is 128 consecutive voxels of the interior
-// box (thread t and t + 128 = voxel t of the tile = TMEM lane t).  The FP16 grid table (2048 x 48, 192 KB, K-major core-matrix
-// layout without swizzle) is copied into shared memory once per CTA.  Per
-// tile of 128 voxels: every thread writes its voxel's normalised components
-// as one FP16 row of A; thread 0 issues the MMAs of one 256-point chunk into
-// one half of a 512-column TMEM accumulator while all threads read the other
-// half (the previous chunk) with tcgen05.ld and keep, per grid region of 16
-// consecutive points, the best point, and the 8 best regions.  Waits on the MMA mbarrier are bounded:
-// on expiry the kernel records TTM_ERR_TIMEOUT, waits once more, frees its
-// TMEM and exits.
+// box (thread t and t + 128 = voxel t of the tile = TMEM lane t).  The FP16
+// grid table (2048 x KP, K-major core-matrix layout without swizzle, stored
+// chunk by chunk of 256 points) is either copied into shared memory once per
+// CTA (order 4: 192 KB) or streamed chunk by chunk with bulk copies into two
+// shared-memory buffers (order 6: 48 KB per chunk, from L2).  Per tile: every
+// thread writes its voxel's normalised components as one FP16 row of A; thread
+// 0 issues the MMAs of one 256-point chunk into one half of a 512-column TMEM
+// accumulator while all threads read the other half (the previous chunk) with
+// tcgen05.ld and keep, per grid region of 16 consecutive points, the best
+// point, and the 8 best regions.  Waits on the mbarriers are bounded: on
+// expiry the kernel records TTM_ERR_TIMEOUT, waits once more for its MMAs and
+// copies in flight, frees its TMEM and exits.
 #include <climits>
 
 #include <cuda_fp16.h>
@@ -32,16 +35,24 @@ namespace {
 
 constexpr int kThreads = 256;    // warps w and w + 4 read the same TMEM lanes, different columns
 constexpr int kG = 2048;             // grid points
-constexpr int kKP = 48;              // padded K
-constexpr int kKC = kKP / 8;         // core-matrix columns along K
-constexpr int kNG = kG / 8;          // core-matrix rows of B
 constexpr int kChunkN = 256;         // grid points per MMA
 constexpr int kChunks = kG / kChunkN;
-constexpr uint32_t kBBytes = (uint32_t)kKC * kNG * 128;     // 196608
-constexpr uint32_t kABytes = (uint32_t)kKC * 16 * 128;      // 12288
 constexpr uint32_t kMergeBytes = 128 * 8 * 4;                // top-8 keys of warps 4..7
-constexpr uint32_t kSmem = kBBytes + kABytes + kMergeBytes;
 constexpr long kWaitLimit = 1L << 24;   // try_wait polls; well beyond any MMA latency
+
+// Shapes for K tensor components: padded K, shared-memory sizes, and whether
+// the grid table is resident or streamed.
+template <int K>
+struct TcShape {
+    static constexpr int KP = ((K + 1 + 15) / 16) * 16;          // + constant column
+    static constexpr int KC = KP / 8;                            // core-matrix columns along K
+    static constexpr uint32_t ABytes = (uint32_t)KC * 16 * 128;
+    static constexpr uint32_t ChunkBytes = (uint32_t)KC * (kChunkN / 8) * 128;
+    static constexpr bool Stream = (uint64_t)ChunkBytes * kChunks > 200u * 1024u;
+    static constexpr uint32_t BBytes = Stream ? 2 * ChunkBytes : ChunkBytes * kChunks;
+    static constexpr uint32_t Smem = BBytes + ABytes + kMergeBytes;
+    static_assert(Smem <= 227u * 1024u, "shared memory");
+};
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
     return (uint32_t)__cvta_generic_to_shared(p);
@@ -75,15 +86,17 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t phase) {
     return false;
 }
 
-__device__ __forceinline__ void issue_chunk(uint32_t tmem_d, uint32_t a_base, uint32_t b_base,
-                                           int chunk, uint32_t bar) {
+// MMAs of one 256-point chunk whose B block (KP/8 x 32 core matrices, K-block
+// major) starts at b_chunk; A is 128 x KP (KP/8 x 16 core matrices)
+template <int KP>
+__device__ __forceinline__ void issue_chunk(uint32_t tmem_d, uint32_t a_base, uint32_t b_chunk,
+                                           uint32_t bar) {
     asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
 #pragma unroll
-    for (int s = 0; s < kKP / 16; ++s) {
+    for (int s = 0; s < KP / 16; ++s) {
         const uint64_t ad = smem_desc(a_base + (uint32_t)(2 * s) * 16 * 128, 16 * 128, 128);
-        const uint64_t bd = smem_desc(b_base + (uint32_t)chunk * (kChunkN / 8) * 128 +
-                                          (uint32_t)(2 * s) * kNG * 128,
-                                      kNG * 128, 128);
+        const uint64_t bd = smem_desc(b_chunk + (uint32_t)(2 * s) * (kChunkN / 8) * 128,
+                                      (kChunkN / 8) * 128, 128);
         asm volatile(
             "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
             "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
@@ -91,6 +104,17 @@ __device__ __forceinline__ void issue_chunk(uint32_t tmem_d, uint32_t a_base, ui
     }
     asm volatile(
         "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(bar)
+        : "memory");
+}
+
+// one thread: arm the barrier for `bytes` and start a bulk copy global -> shared
+__device__ __forceinline__ void bulk_load(uint32_t dst, const void* src, uint32_t bytes,
+                                          uint32_t bar) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(bar), "r"(bytes)
+                 : "memory");
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n"
+        ::"r"(dst), "l"(src), "r"(bytes), "r"(bar)
         : "memory");
 }
 
@@ -133,27 +157,28 @@ __device__ __forceinline__ void tmem_ld32(uint32_t addr, uint32_t (&r)[32]) {
     asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
 }
 
-template <typename CT>
-__global__ void __launch_bounds__(kThreads, 1) search_tc4_kernel(rot::SearchArgs a,
-                                                                 const uint4* __restrict__ gtab,
-                                                                 const uint32_t* __restrict__ ends,
-                                                                 int* status) {
+template <typename CT, int N>
+__global__ void __launch_bounds__(kThreads, 1) search_tc_kernel(rot::SearchArgs a,
+                                                                const uint4* __restrict__ gtab,
+                                                                int* status) {
+    using Sh = TcShape<n_comp(N)>;
+    constexpr int K = n_comp(N);
+    constexpr int KP = Sh::KP;
+    constexpr bool kStream = Sh::Stream;
     extern __shared__ __align__(1024) unsigned char sm[];
-    __shared__ __align__(8) uint64_t bars[2];
+    __shared__ __align__(8) uint64_t bars[2];     // MMA completion, one per TMEM half
+    __shared__ __align__(8) uint64_t lbars[2];    // grid-chunk copies (streamed table)
     __shared__ uint32_t tmem_base_s;
-    constexpr int K = 35;
-    constexpr Sym<4> S{};
+    constexpr Sym<N> S{};
     const int t = threadIdx.x;
     const int warp = t >> 5;
     unsigned char* Bs = sm;
-    unsigned char* As = sm + kBBytes;
-    int* merge = reinterpret_cast<int*>(sm + kBBytes + kABytes);   // [8][128]
-    (void)ends;   // regions are the 128 consecutive groups of 16 points
+    unsigned char* As = sm + Sh::BBytes;
+    int* merge = reinterpret_cast<int*>(sm + Sh::BBytes + Sh::ABytes);   // [8][128]
 
-    // grid table, once per CTA
-    {
+    if constexpr (!kStream) {   // grid table, once per CTA
         uint4* dst = reinterpret_cast<uint4*>(Bs);
-        for (int e = t; e < (int)(kBBytes / 16); e += kThreads) dst[e] = __ldg(gtab + e);
+        for (int e = t; e < (int)(Sh::BBytes / 16); e += kThreads) dst[e] = __ldg(gtab + e);
     }
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;\n" ::"r"(
@@ -161,8 +186,12 @@ __global__ void __launch_bounds__(kThreads, 1) search_tc4_kernel(rot::SearchArgs
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
     }
     if (t == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&bars[0])) : "memory");
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&bars[1])) : "memory");
+        for (int b = 0; b < 2; ++b) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&bars[b])) : "memory");
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&lbars[b])) : "memory");
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
     }
     asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
     __syncthreads();
@@ -170,51 +199,81 @@ __global__ void __launch_bounds__(kThreads, 1) search_tc4_kernel(rot::SearchArgs
     const uint32_t tmem = tmem_base_s;
     const uint32_t a_base = smem_u32(As), b_base = smem_u32(Bs);
     const uint32_t bar0 = smem_u32(&bars[0]), bar1 = smem_u32(&bars[1]);
+    const uint32_t lbar[2] = {smem_u32(&lbars[0]), smem_u32(&lbars[1])};
     uint32_t phase[2] = {0u, 0u};
+    uint32_t lphase[2] = {0u, 0u};   // thread 0: phases of the copy barriers
+    int loads_pending[2] = {0, 0};   // thread 0: copies issued and not yet waited on
     bool ok = true;
+
+    const size_t units = a.box.count();
+    const size_t ntiles = (units + 127) / 128;
+    const unsigned char* gsrc = reinterpret_cast<const unsigned char*>(gtab);
+    // streamed table: chunk q (counted over the whole CTA) goes to buffer q & 1;
+    // the copy of chunk q + 2 starts once the MMAs of chunk q have completed
+    if (kStream && t == 0) {
+        for (int q = 0; q < 2; ++q) {
+            bulk_load(b_base + (uint32_t)q * Sh::ChunkBytes, gsrc + (size_t)q * Sh::ChunkBytes,
+                      Sh::ChunkBytes, lbar[q]);
+            loads_pending[q] = 1;
+        }
+    }
+    // thread 0: wait for the copy of chunk q (streamed table) and issue its MMAs
+    auto issue = [&](uint32_t tmem_d, int chunk, long q, uint32_t bar) {
+        uint32_t b_chunk;
+        if constexpr (kStream) {
+            const int buf = (int)(q & 1);
+            if (!mbar_wait(lbar[buf], lphase[buf])) return;   // no MMA: the MMA wait expires
+            lphase[buf] ^= 1u;
+            loads_pending[buf] = 0;
+            b_chunk = b_base + (uint32_t)buf * Sh::ChunkBytes;
+        } else {
+            b_chunk = b_base + (uint32_t)chunk * Sh::ChunkBytes;
+        }
+        issue_chunk<KP>(tmem_d, a_base, b_chunk, bar);
+    };
 
     const int lane_t = t & 127;            // TMEM lane = voxel of the tile
     const int colhalf = t >> 7;            // warps 4..7 take columns 128..255 of a chunk
-    const size_t units = a.box.count();
-    const size_t ntiles = (units + 127) / 128;
-    for (size_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+    long qbase = 0;                        // chunks issued by this CTA before this tile
+    for (size_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x, qbase += kChunks) {
+        const bool more_tiles = tile + gridDim.x < ntiles;
         const size_t i = tile * 128 + lane_t;
         const bool in_range = i < units;
         const size_t v = in_range ? a.box.voxel((uint32_t)i) : 0;
         // components, score, normalised FP16 row of A (threads 0..127)
         float score = 0.f;
         if (colhalf == 0) {
-        float C[K];
-        const float wv = in_range ? __ldg(a.w + v) : 0.f;
-        float ss = 0.f;
+            float C[K];
+            const float wv = in_range ? __ldg(a.w + v) : 0.f;
+            float ss = 0.f;
 #pragma unroll
-        for (int k = 0; k < K; ++k) {
-            C[k] = in_range ? wv * rot::ldcorr(reinterpret_cast<const CT*>(a.corr) + (size_t)k * a.nvox + v) : 0.f;
-            ss = fmaf((float)S.mu[k], C[k] * C[k], ss);
-        }
-        score = sqrtf(ss);
-        const float inv = score > 0.f ? 1.f / score : 0.f;
-#pragma unroll
-        for (int kc = 0; kc < kKC; ++kc) {
-            __half h[8];
-#pragma unroll
-            for (int e = 0; e < 8; ++e) {
-                const int k = kc * 8 + e;
-                // column K is the constant 1 that adds +1 to every phi (see below)
-                h[e] = __float2half_rn(k < K ? C[k] * inv : (k == K ? 1.f : 0.f));
+            for (int k = 0; k < K; ++k) {
+                C[k] = in_range ? wv * rot::ldcorr(reinterpret_cast<const CT*>(a.corr) + (size_t)k * a.nvox + v) : 0.f;
+                ss = fmaf((float)S.mu[k], C[k] * C[k], ss);
             }
-            uint4 pk;
-            pk.x = (uint32_t)__half_as_ushort(h[0]) | ((uint32_t)__half_as_ushort(h[1]) << 16);
-            pk.y = (uint32_t)__half_as_ushort(h[2]) | ((uint32_t)__half_as_ushort(h[3]) << 16);
-            pk.z = (uint32_t)__half_as_ushort(h[4]) | ((uint32_t)__half_as_ushort(h[5]) << 16);
-            pk.w = (uint32_t)__half_as_ushort(h[6]) | ((uint32_t)__half_as_ushort(h[7]) << 16);
-            *reinterpret_cast<uint4*>(As + ((kc * 16 + (lane_t >> 3)) * 8 + (lane_t & 7)) * 16) = pk;
-        }
+            score = sqrtf(ss);
+            const float inv = score > 0.f ? 1.f / score : 0.f;
+#pragma unroll
+            for (int kc = 0; kc < Sh::KC; ++kc) {
+                __half h[8];
+#pragma unroll
+                for (int e = 0; e < 8; ++e) {
+                    const int k = kc * 8 + e;
+                    // column K is the constant 1 that adds +1 to every phi (see below)
+                    h[e] = __float2half_rn(k < K ? C[k] * inv : (k == K ? 1.f : 0.f));
+                }
+                uint4 pk;
+                pk.x = (uint32_t)__half_as_ushort(h[0]) | ((uint32_t)__half_as_ushort(h[1]) << 16);
+                pk.y = (uint32_t)__half_as_ushort(h[2]) | ((uint32_t)__half_as_ushort(h[3]) << 16);
+                pk.z = (uint32_t)__half_as_ushort(h[4]) | ((uint32_t)__half_as_ushort(h[5]) << 16);
+                pk.w = (uint32_t)__half_as_ushort(h[6]) | ((uint32_t)__half_as_ushort(h[7]) << 16);
+                *reinterpret_cast<uint4*>(As + ((kc * 16 + (lane_t >> 3)) * 8 + (lane_t & 7)) * 16) = pk;
+            }
         }
         asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
         asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
         __syncthreads();
-        if (t == 0) issue_chunk(tmem, a_base, b_base, 0, bar0);
+        if (t == 0) issue(tmem, 0, qbase, bar0);
 
         // packed keys: the float bits of phi + 1 (non-negative, so they order
         // like the values) with the low 11 bits replaced by (2047 - grid
@@ -225,9 +284,10 @@ __global__ void __launch_bounds__(kThreads, 1) search_tc4_kernel(rot::SearchArgs
         for (int k = 0; k < rot::kMaxCand; ++k) top[k] = INT_MIN;
         for (int c = 0; c < kChunks; ++c) {
             const int h = c & 1;
+            const long q = qbase + c;
             if (c + 1 < kChunks && t == 0)
-                issue_chunk(tmem + (uint32_t)((c + 1) & 1) * kChunkN, a_base, b_base, c + 1,
-                            ((c + 1) & 1) ? bar1 : bar0);
+                issue(tmem + (uint32_t)((c + 1) & 1) * kChunkN, c + 1, q + 1,
+                      ((c + 1) & 1) ? bar1 : bar0);
             bool got = mbar_wait(h ? bar1 : bar0, phase[h]);
             phase[h] ^= 1u;
             if (!__syncthreads_and(got)) {
@@ -237,6 +297,15 @@ __global__ void __launch_bounds__(kThreads, 1) search_tc4_kernel(rot::SearchArgs
                 mbar_wait(h ? bar1 : bar0, phase[h] ^ 1u);
                 if (c + 1 < kChunks) mbar_wait(h ? bar0 : bar1, phase[h ^ 1]);
                 break;
+            }
+            // the MMAs of chunk q are done: its buffer takes chunk q + 2
+            if (kStream && t == 0 && (c + 2 < kChunks || more_tiles)) {
+                const int buf = (int)(q & 1);
+                const int nxt = (c + 2) % kChunks;
+                asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+                bulk_load(b_base + (uint32_t)buf * Sh::ChunkBytes,
+                          gsrc + (size_t)nxt * Sh::ChunkBytes, Sh::ChunkBytes, lbar[buf]);
+                loads_pending[buf] = 1;
             }
             asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
             const uint32_t col0 = tmem + ((uint32_t)((warp & 3) * 32) << 16) +
@@ -255,12 +324,12 @@ __global__ void __launch_bounds__(kThreads, 1) search_tc4_kernel(rot::SearchArgs
 #pragma unroll
                 for (int w = 8; w >= 1; w >>= 1)
 #pragma unroll
-                    for (int q = 0; q < 4; ++q)
+                    for (int q4 = 0; q4 < 4; ++q4)
 #pragma unroll
-                        for (int j = 0; j < w; ++j) key[16 * q + j] = max(key[16 * q + j], key[16 * q + j + w]);
+                        for (int j = 0; j < w; ++j) key[16 * q4 + j] = max(key[16 * q4 + j], key[16 * q4 + j + w]);
 #pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    int x = key[16 * q];
+                for (int q4 = 0; q4 < 4; ++q4) {
+                    int x = key[16 * q4];
 #pragma unroll
                     for (int k = 0; k < rot::kMaxCand; ++k) {
                         const int hi = max(top[k], x);
@@ -272,31 +341,38 @@ __global__ void __launch_bounds__(kThreads, 1) search_tc4_kernel(rot::SearchArgs
             asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
             __syncthreads();     // this half may now be overwritten by chunk c + 2
         }
+        if (!ok) break;
         // merge the two column halves' lists
         if (colhalf == 1) {
 #pragma unroll
             for (int k = 0; k < rot::kMaxCand; ++k) merge[k * 128 + lane_t] = top[k];
         }
         __syncthreads();
-        if (colhalf == 1) continue;
+        if (colhalf == 0) {
 #pragma unroll
-        for (int k2 = 0; k2 < rot::kMaxCand; ++k2) {
-            int x = merge[k2 * 128 + lane_t];
+            for (int k2 = 0; k2 < rot::kMaxCand; ++k2) {
+                int x = merge[k2 * 128 + lane_t];
 #pragma unroll
-            for (int k = 0; k < rot::kMaxCand; ++k) {
-                const int hi = max(top[k], x);
-                x = min(top[k], x);
-                top[k] = hi;
+                for (int k = 0; k < rot::kMaxCand; ++k) {
+                    const int hi = max(top[k], x);
+                    x = min(top[k], x);
+                    top[k] = hi;
+                }
+            }
+            int ti[rot::kMaxCand];
+#pragma unroll
+            for (int k = 0; k < rot::kMaxCand; ++k) ti[k] = top[k] == INT_MIN ? 0xFFFF : 2047 - (top[k] & 2047);
+            if (in_range) {
+                a.score[v] = score;
+                rot::store_candidates(a.cand, i, ti, score > 0.f);
             }
         }
-        int ti[rot::kMaxCand];
-#pragma unroll
-        for (int k = 0; k < rot::kMaxCand; ++k) ti[k] = top[k] == INT_MIN ? 0xFFFF : 2047 - (top[k] & 2047);
-        if (!ok) break;
-        if (in_range) {
-            a.score[v] = score;
-            rot::store_candidates(a.cand, i, ti, score > 0.f);
-        }
+        __syncthreads();     // merge buffer and A are reused by the next tile
+    }
+    // copies still in flight (only after an expired wait) land before exit
+    if (kStream && t == 0) {
+        for (int b = 0; b < 2; ++b)
+            if (loads_pending[b]) mbar_wait(lbar[b], lphase[b]);
     }
     __syncthreads();
     if (warp == 0)
@@ -305,43 +381,55 @@ __global__ void __launch_bounds__(kThreads, 1) search_tc4_kernel(rot::SearchArgs
 
 }  // namespace
 
-template <typename CT>
-static ttm_status launch_tc4_t(const rot::SearchArgs& s, const uint16_t* grid_fp16,
-                               const uint32_t* end_bits, int* status, cudaStream_t st,
-                               long long* cnt) {
-    TTM_CUDA_TRY(cudaFuncSetAttribute(search_tc4_kernel<CT>,
-                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem));
+template <typename CT, int N>
+static ttm_status launch_tc_t(const rot::SearchArgs& s, const uint16_t* grid_fp16, int* status,
+                              cudaStream_t st, long long* cnt) {
+    constexpr uint32_t smem = TcShape<n_comp(N)>::Smem;
+    TTM_CUDA_TRY(cudaFuncSetAttribute(search_tc_kernel<CT, N>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int dev = 0, sms = 0;
     TTM_CUDA_TRY(cudaGetDevice(&dev));
     TTM_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     const size_t ntiles = (s.box.count() + 127) / 128;
     if (ntiles == 0) return TTM_OK;
     const unsigned grid = (unsigned)(ntiles < (size_t)sms ? ntiles : (size_t)sms);
-    search_tc4_kernel<CT><<<grid, kThreads, kSmem, st>>>(s, reinterpret_cast<const uint4*>(grid_fp16),
-                                                         end_bits, status);
+    search_tc_kernel<CT, N><<<grid, kThreads, smem, st>>>(
+        s, reinterpret_cast<const uint4*>(grid_fp16), status);
     return after_launch(cnt);
 }
 
-ttm_status launch_search_tc4(const rot::SearchArgs& s, const uint16_t* grid_fp16,
-                             const uint32_t* end_bits, int* status, bool bf16, cudaStream_t st,
-                             long long* cnt) {
-    if (s.n_grid != kG || !grid_fp16 || !end_bits) return TTM_ERR_UNSUPPORTED;
-    return bf16 ? launch_tc4_t<__nv_bfloat16>(s, grid_fp16, end_bits, status, st, cnt)
-                : launch_tc4_t<float>(s, grid_fp16, end_bits, status, st, cnt);
+bool search_tc_supported(int n_order, int n_grid, int n_cells) {
+    return (n_order == 4 || n_order == 6) && n_grid == kG && n_cells == kG / 16;
 }
 
-// FP16 grid table in the kernel's shared-memory layout: element (g, k) of the
-// 2048 x 48 matrix mu_k q_g^k (zero for k >= 35) at core matrix (k / 8, g / 8),
-// row g % 8, column k % 8, core matrices ordered k-block-major.
-void build_grid_fp16(const float* m_rows, int K4, std::vector<uint16_t>& out) {
-    out.assign((size_t)kKC * kNG * 64, 0);
+ttm_status launch_search_tc(int n_order, const rot::SearchArgs& s, const uint16_t* grid_fp16,
+                            int* status, bool bf16, cudaStream_t st, long long* cnt) {
+    if (s.n_grid != kG || !grid_fp16) return TTM_ERR_UNSUPPORTED;
+    if (n_order == 4)
+        return bf16 ? launch_tc_t<__nv_bfloat16, 4>(s, grid_fp16, status, st, cnt)
+                    : launch_tc_t<float, 4>(s, grid_fp16, status, st, cnt);
+    if (n_order == 6)
+        return bf16 ? launch_tc_t<__nv_bfloat16, 6>(s, grid_fp16, status, st, cnt)
+                    : launch_tc_t<float, 6>(s, grid_fp16, status, st, cnt);
+    return TTM_ERR_UNSUPPORTED;
+}
+
+// FP16 grid table in the kernel's shared-memory layout, chunk by chunk of 256
+// points: element (g, k) of the 2048 x KP matrix [mu_k q_g^k | 1 | 0...] at
+// chunk g / 256, core matrix (k / 8, (g % 256) / 8), row g % 8, column k % 8,
+// core matrices ordered k-block-major within the chunk.
+void build_grid_fp16(const float* m_rows, int K, int K4, std::vector<uint16_t>& out) {
+    const int KP = ((K + 1 + 15) / 16) * 16;
+    out.assign((size_t)kG * KP, 0);
     for (int g = 0; g < kG; ++g)
-        for (int k = 0; k < kKP; ++k) {
-            // column 35 holds the constant 1 paired with A's constant column,
+        for (int k = 0; k < KP; ++k) {
+            // column K holds the constant 1 paired with A's constant column,
             // adding +1 to every phi
-            float v = k < 35 ? m_rows[(size_t)g * K4 + k] : (k == 35 ? 1.f : 0.f);
+            float v = k < K ? m_rows[(size_t)g * K4 + k] : (k == K ? 1.f : 0.f);
             __half h = __float2half_rn(v);
-            const size_t idx = (((size_t)(k / 8) * kNG + g / 8) * 8 + g % 8) * 8 + k % 8;
+            const int c = g / kChunkN, gl = g % kChunkN;
+            const size_t idx = (size_t)c * kChunkN * KP +
+                               ((((size_t)(k / 8) * (kChunkN / 8) + gl / 8) * 8 + gl % 8) * 8 + k % 8);
             out[idx] = __half_as_ushort(h);
         }
 }

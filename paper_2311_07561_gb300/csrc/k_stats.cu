@@ -164,7 +164,22 @@ __global__ void __launch_bounds__(kStatThreads) local_stats_kernel(StatsArgs a) 
     }
 }
 
+// integer hash of (index, seed) -> uniform float in [-1, 1)
+__global__ void fill_random_kernel(float* __restrict__ f, size_t n, uint32_t seed) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
+         i += (size_t)gridDim.x * blockDim.x) {
+        uint32_t h = (uint32_t)i * 0x9E3779B1u ^ (uint32_t)(i >> 32) ^ seed;
+        h ^= h >> 16; h *= 0x7FEB352Du; h ^= h >> 15; h *= 0x846CA68Bu; h ^= h >> 16;
+        f[i] = (float)(h >> 8) * (2.0f / 16777216.0f) - 1.0f;
+    }
+}
+
 }  // namespace
+
+ttm_status launch_fill_random(float* f, size_t n, uint32_t seed, cudaStream_t st, long long* cnt) {
+    fill_random_kernel<<<152 * 8, 256, 0, st>>>(f, n, seed);
+    return after_launch(cnt);
+}
 
 ttm_status launch_volume_moments(const float* f, size_t n, double* d_acc, cudaStream_t st,
                                  long long* cnt) {

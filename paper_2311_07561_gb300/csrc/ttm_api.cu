@@ -139,9 +139,9 @@ ttm_status build_grid(ttm_plan_s* P) {
     TTM_TRY(dev_upload(&g.d_q, hq));
     TTM_TRY(dev_upload(&g.d_m, hm));
     TTM_TRY(dev_upload(&g.d_cell_end, ends));
-    if (P->n_order == 4 && n == 2048 && nc == 128) {
+    if (search_tc_supported(P->n_order, n, nc)) {
         std::vector<uint16_t> tab;
-        build_grid_fp16(hm.data(), K4, tab);
+        build_grid_fp16(hm.data(), K, K4, tab);
         std::vector<uint32_t> bits(n / 32, 0u);
         for (int i = 0; i < n; ++i)
             if (ends[i]) bits[i / 32] |= 1u << (i % 32);
@@ -229,13 +229,23 @@ const float2* twiddle_table(ttm_plan_s* P, int L, ttm_status* err) {
     return d;
 }
 
-// Bytes per voxel each path moves or computes, for the automatic choice.
-bool prefer_fft(const ttm_plan_s* P, const ProblemData& pr, const TemplateData& T) {
+// Cost model of the two correlation paths (ns per voxel): the FFT path moves
+// ~40 bytes per component per padded voxel at ~5 TB/s, the direct path does
+// 2 K n_taps FLOP at ~30 TFLOP/s.
+double model_ratio(const ttm_plan_s* P, const ProblemData& pr, const TemplateData& T) {
     const double pad = (double)pr.fft.Xp * pr.fft.Yp * pr.fft.Zp / (double)pr.nvox();
-    const double fft_ns = pad * (40.0 * P->K + 40.0) / 5000.0;        // ~5 TB/s effective
-    const double direct_ns = 2.0 * P->K * T.n_taps / 30000.0;         // ~30 TFLOP/s FP32
-    return fft_ns < direct_ns;
+    const double fft_ns = pad * (40.0 * P->K + 40.0) / 5000.0;
+    const double direct_ns = 2.0 * P->K * T.n_taps / 30000.0;
+    return direct_ns / fft_ns;          // > 1: the FFT path is expected to win
 }
+
+bool prefer_fft(const ttm_plan_s* P, const ProblemData& pr, const TemplateData& T) {
+    return model_ratio(P, pr, T) > 1.0;
+}
+
+// The autotuner times both paths only where the model leaves them within
+// this factor of each other.
+constexpr double kTuneRange = 8.0;
 
 ttm_status prepare_fft(ttm_plan_s* P, ProblemData& pr, cudaStream_t st) {
     ttm_status err = TTM_OK;
@@ -367,12 +377,23 @@ size_t peak_cap(size_t nvox) { return std::min(nvox, (size_t)kPeakCapMax); }
 
 // Correlation maps first (both paths), then for the FFT path the image
 // spectrum and the K product spectra, then 8 candidate grid indices per voxel.
+// Components per inverse-FFT group: the product spectra of one group live in
+// the workspace at a time (all K while they fit in 8 GiB, fewer for large
+// boxes), so the workspace holds the K correlation maps plus one group.
+constexpr size_t kProdBudget = (size_t)8 << 30;
+
+int comp_group(const ttm_plan_s* P, const ProblemData& pr) {
+    const size_t per = pr.fft.nspec() * 2 * (pr.mixed ? 2 : 4);
+    const size_t g = per ? kProdBudget / per : (size_t)P->K;
+    return (int)std::max<size_t>(1, std::min<size_t>(g, (size_t)P->K));
+}
+
 size_t corr_region_bytes(const ttm_plan_s* P, const ProblemData& pr) {
     const size_t es = pr.mixed ? 2 : 4;          // bytes per stored real (corr maps)
     size_t b = align256((size_t)P->K * pr.nvox() * es);
     if (pr.path == TTM_PATH_FFT)
         b += align256(pr.fft.nspec() * sizeof(float2)) +
-             align256((size_t)P->K * pr.fft.nspec() * 2 * es);
+             align256((size_t)comp_group(P, pr) * pr.fft.nspec() * 2 * es);
     return b;
 }
 
@@ -445,18 +466,28 @@ ttm_status corr_problem(ttm_plan_s* plan, const ProblemData& pr, const float* vo
         TTM_TRY(timed(plan, KC_FFT_FORWARD, st, [&] {
             return launch_fft_forward(vol, pr.X, pr.Y, pr.Z, pr.fft, spec, st, &plan->launches);
         }));
-        TTM_TRY(timed(plan, KC_FFT_SPECTRUM, st, [&] {
-            return pr.mixed ? launch_fft_spectrum_inverse_z_bf16(spec, sp.d_spec_bf, plan->K,
-                                                                 pr.fft, prod, st, &plan->launches)
-                            : launch_fft_spectrum_inverse_z(spec, sp.d_spec, plan->K, pr.fft,
-                                                            (float2*)prod, st, &plan->launches);
-        }));
-        return timed(plan, KC_FFT_INVERSE, st, [&] {
-            return pr.mixed ? launch_fft_inverse_yx_bf16(prod, plan->K, pr.X, pr.Y, pr.Z, pr.fft,
-                                                         corr, st, &plan->launches)
-                            : launch_fft_inverse_yx((float2*)prod, plan->K, pr.X, pr.Y, pr.Z,
-                                                    pr.fft, corr, st, &plan->launches);
-        });
+        const int G = comp_group(plan, pr);
+        const size_t nspec = pr.fft.nspec();
+        for (int k0 = 0; k0 < plan->K; k0 += G) {
+            const int g = std::min(G, plan->K - k0);
+            TTM_TRY(timed(plan, KC_FFT_SPECTRUM, st, [&] {
+                return pr.mixed ? launch_fft_spectrum_inverse_z_bf16(
+                                      spec, (const char*)sp.d_spec_bf + (size_t)k0 * nspec * 4, g,
+                                      pr.fft, prod, st, &plan->launches)
+                                : launch_fft_spectrum_inverse_z(spec, sp.d_spec + (size_t)k0 * nspec,
+                                                                g, pr.fft, (float2*)prod, st,
+                                                                &plan->launches);
+            }));
+            TTM_TRY(timed(plan, KC_FFT_INVERSE, st, [&] {
+                return pr.mixed ? launch_fft_inverse_yx_bf16(
+                                      prod, g, pr.X, pr.Y, pr.Z, pr.fft,
+                                      (char*)corr + (size_t)k0 * pr.nvox() * 2, st, &plan->launches)
+                                : launch_fft_inverse_yx((float2*)prod, g, pr.X, pr.Y, pr.Z, pr.fft,
+                                                        corr + (size_t)k0 * pr.nvox(), st,
+                                                        &plan->launches);
+            }));
+        }
+        return TTM_OK;
     }
     const TemplateData& T = plan->tmpl[pr.tmpl];
     return timed(plan, KC_DIRECT_CORR, st, [&] {
@@ -487,6 +518,99 @@ ttm_status rotation_problem(ttm_plan_s* plan, const ProblemData& pr, const float
                                       plan->grid, cand, score, quat, lam, comp_out, st,
                                       &plan->launches);
     });
+}
+
+// ---- autotuner (TTM_PATH_TUNE) ----
+
+// Device time of local statistics + K correlations of one problem: one
+// warm-up run, then the best of two timed runs (ms), or -1 on failure.
+double time_paths_once(ttm_plan_s* P, const ProblemData& pr, const float* vol, float* w, void* ws,
+                       cudaStream_t st) {
+    cudaEvent_t a = nullptr, b = nullptr;
+    if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess) {
+        cudaGetLastError();
+        if (a) cudaEventDestroy(a);
+        return -1.0;
+    }
+    double best = -1.0;
+    for (int rep = 0; rep < 3; ++rep) {
+        if (cudaEventRecord(a, st) != cudaSuccess) break;
+        if (stats_problem(P, pr, vol, w, ws, st) != TTM_OK) break;
+        if (corr_problem(P, pr, vol, ws, st) != TTM_OK) break;
+        if (cudaEventRecord(b, st) != cudaSuccess || cudaEventSynchronize(b) != cudaSuccess) break;
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, a, b) != cudaSuccess) break;
+        if (rep > 0 && (best < 0.0 || ms < best)) best = ms;
+    }
+    cudaGetLastError();
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    return best;
+}
+
+// Times the direct and the FFT path of every distinct problem shape that can
+// take both (problems arrive here on the FFT path) and keeps the faster.
+// Problems with the same template, extents and precision share a decision.
+// Template spectra no FFT problem uses any more are freed.
+ttm_status tune_paths(ttm_plan_s* P, cudaStream_t st) {
+    const int np = (int)P->prob.size();
+    for (int p = 0; p < np; ++p) {
+        ProblemData& pr = P->prob[p];
+        if (pr.path != TTM_PATH_FFT) continue;
+        bool shared = false;
+        for (int q = 0; q < p && !shared; ++q) {
+            const ProblemData& o = P->prob[q];
+            if (o.tmpl != pr.tmpl || o.X != pr.X || o.Y != pr.Y || o.Z != pr.Z) continue;
+            if (o.tune_ms[0] < 0.0 && o.tune_ms[1] < 0.0) continue;     // not timed
+            pr.tune_ms[0] = o.tune_ms[0];
+            pr.tune_ms[1] = o.tune_ms[1];
+            if (o.path == TTM_PATH_DIRECT) { pr.path = TTM_PATH_DIRECT; pr.mixed = false; }
+            shared = true;
+        }
+        if (shared) continue;
+        const double ratio = model_ratio(P, pr, P->tmpl[pr.tmpl]);
+        if (ratio > kTuneRange) continue;                          // FFT, clearly
+        if (ratio < 1.0 / kTuneRange) { pr.path = TTM_PATH_DIRECT; pr.mixed = false; continue; }
+        ProblemData dpr = pr;
+        dpr.path = TTM_PATH_DIRECT;
+        dpr.mixed = false;
+        const size_t nv = pr.nvox();
+        const size_t wsb = kHeader + std::max(scratch_bytes(P, pr), scratch_bytes(P, dpr));
+        float* vol = nullptr;
+        float* w = nullptr;
+        void* ws = nullptr;
+        if (cudaMalloc((void**)&vol, nv * sizeof(float)) != cudaSuccess ||
+            cudaMalloc((void**)&w, nv * sizeof(float)) != cudaSuccess ||
+            cudaMalloc(&ws, wsb) != cudaSuccess) {
+            // not enough memory to tune: keep the planner's estimate
+            cudaGetLastError();
+            cudaFree(vol); cudaFree(w); cudaFree(ws);
+            if (!prefer_fft(P, pr, P->tmpl[pr.tmpl])) { pr.path = TTM_PATH_DIRECT; pr.mixed = false; }
+            continue;
+        }
+        ttm_status s = launch_fill_random(vol, nv, 0x5eedu + (uint32_t)p, st, &P->launches);
+        if (s == TTM_OK) {
+            pr.tune_ms[0] = time_paths_once(P, dpr, vol, w, ws, st);
+            pr.tune_ms[1] = time_paths_once(P, pr, vol, w, ws, st);
+        }
+        cudaError_t e = cudaStreamSynchronize(st);
+        cudaFree(vol); cudaFree(w); cudaFree(ws);
+        if (s != TTM_OK) return s;
+        if (e != cudaSuccess) return TTM_ERR_CUDA;
+        if (pr.tune_ms[1] < 0.0 || (pr.tune_ms[0] >= 0.0 && pr.tune_ms[0] < pr.tune_ms[1])) {
+            pr.path = TTM_PATH_DIRECT;
+            pr.mixed = false;
+        }
+    }
+    for (size_t i = 0; i < P->specs.size(); ++i) {
+        bool used = false;
+        for (const ProblemData& pr : P->prob) used = used || (pr.path == TTM_PATH_FFT && pr.spec_index == (int)i);
+        if (used) continue;
+        SpecSet& sp = P->specs[i];
+        cudaFree(sp.d_spec); cudaFree(sp.d_spec_bf); cudaFree(sp.d_mask_spec);
+        sp.d_spec = nullptr; sp.d_spec_bf = nullptr; sp.d_mask_spec = nullptr;
+    }
+    return TTM_OK;
 }
 
 }  // namespace
@@ -634,6 +758,7 @@ ttm_status ttm_plan(ttm_plan_t* out, int n_problems, const int* vol_dims, const 
         const bool fft_ok = fft_length_ok(pr.fft.Xp) && fft_length_ok(pr.fft.Yp) &&
                             fft_length_ok(pr.fft.Zp);
         int path = P->opts.path;
+        if (path == TTM_PATH_TUNE) path = fft_ok ? TTM_PATH_FFT : TTM_PATH_DIRECT;
         if (path == TTM_PATH_AUTO) path = (fft_ok && prefer_fft(P, pr, T)) ? TTM_PATH_FFT : TTM_PATH_DIRECT;
         if (path == TTM_PATH_FFT && !fft_ok) { free_plan(P); return TTM_ERR_UNSUPPORTED; }
         if (path != TTM_PATH_FFT && path != TTM_PATH_DIRECT) { free_plan(P); return TTM_ERR_INVALID_ARG; }
@@ -649,8 +774,12 @@ ttm_status ttm_plan(ttm_plan_t* out, int n_problems, const int* vol_dims, const 
             s_ = prepare_fft(P, pr, st);
             if (s_ != TTM_OK) { free_plan(P); return s_; }
         }
-        ws = std::max(ws, scratch_bytes(P, pr));
     }
+    if (P->opts.path == TTM_PATH_TUNE) {
+        s_ = tune_paths(P, st);
+        if (s_ != TTM_OK) { free_plan(P); return s_; }
+    }
+    for (const ProblemData& pr : P->prob) ws = std::max(ws, scratch_bytes(P, pr));
     P->ws_bytes = kHeader + ws;
     *out = P;
     return TTM_OK;
@@ -666,6 +795,14 @@ ttm_status ttm_plan_problem_path(ttm_plan_t plan, int problem, int* path) {
     if (!plan || !path || problem < 0 || problem >= (int)plan->prob.size())
         return TTM_ERR_INVALID_ARG;
     *path = plan->prob[problem].path;
+    return TTM_OK;
+}
+
+ttm_status ttm_plan_problem_tuning(ttm_plan_t plan, int problem, double* ms) {
+    if (!plan || !ms || problem < 0 || problem >= (int)plan->prob.size())
+        return TTM_ERR_INVALID_ARG;
+    ms[0] = plan->prob[problem].tune_ms[0];
+    ms[1] = plan->prob[problem].tune_ms[1];
     return TTM_OK;
 }
 

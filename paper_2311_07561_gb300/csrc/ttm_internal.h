@@ -46,6 +46,7 @@ struct ProblemData {
     FftShape fft;
     bool mixed = false;                // bf16 spectra, products and correlation maps
     int spec_index = -1;               // template spectra set used (FFT path)
+    double tune_ms[2] = {-1.0, -1.0};  // autotuner: direct, FFT (ms), -1 = not timed
     size_t nvox() const { return (size_t)X * Y * Z; }
 };
 
@@ -91,7 +92,7 @@ struct RotGrid {
     float* d_q = nullptr;        // n_grid x 4 unit quaternions, a >= 0, sorted by cell
     float* d_m = nullptr;        // n_grid x K: mu_alpha q_g^alpha
     int* d_cell_end = nullptr;   // n_grid: 1 if the next point starts a new cell
-    uint16_t* d_gtab = nullptr;  // order 4, 2048 points: FP16 table in tensor-core layout
+    uint16_t* d_gtab = nullptr;  // orders 4 and 6, 2048 points: FP16 table in tensor-core layout
     uint32_t* d_endbits = nullptr;  // region ends as a bitmask (n_grid / 32 words)
 };
 
@@ -136,6 +137,9 @@ inline size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
 ttm_status launch_volume_moments(const float* f, size_t n, double* d_acc, cudaStream_t st,
                                  long long* cnt);
 
+// deterministic pseudo-random values in [-1, 1) (autotuner input)
+ttm_status launch_fill_random(float* f, size_t n, uint32_t seed, cudaStream_t st, long long* cnt);
+
 ttm_status launch_local_stats(const float* f, int X, int Y, int Z, const TemplateData& T,
                               const double* d_moments, float* w, cudaStream_t st,
                               long long* cnt);
@@ -159,7 +163,10 @@ ttm_status launch_rotation_polish(int n_order, const void* corr, bool bf16, cons
                                   long long* cnt);
 ttm_status launch_exterior_fill(int Z, const VoxBox& box, int K, float* score, float* quat,
                                 float* lambda, float* comp_out, cudaStream_t st, long long* cnt);
-void build_grid_fp16(const float* m_rows, int K4, std::vector<uint16_t>& out);
+// FP16 grid table of the tensor-core search (2048 points, K components + the
+// constant column, padded to a multiple of 16, chunk-major core-matrix layout)
+void build_grid_fp16(const float* m_rows, int K, int K4, std::vector<uint16_t>& out);
+bool search_tc_supported(int n_order, int n_grid, int n_cells);
 
 // tensor template build
 ttm_status launch_rotate_normalise(const float* t, const float* m, int s, const float* quats,

@@ -94,6 +94,25 @@ class Matcher:
         B.ttm_correlate(self.plan, vols, self.w, self.score, self.quat,
                         self.lam if self.want_lambda else None, components_out, self.ws, stream)
 
+    def capture(self, vols: Sequence):
+        """Record run(vols) for every problem of the plan into one CUDA graph.
+
+        One eager run on a side stream first (it sets the kernels' shared-memory
+        attributes and loads the module), then the capture.  Replaying the
+        returned torch.cuda.CUDAGraph recomputes every output map from the
+        current contents of vols (same tensors, same addresses)."""
+        torch = _torch()
+        self._check_inputs(vols, None)
+        side = torch.cuda.Stream()
+        side.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(side):
+            self.run(vols)
+        torch.cuda.current_stream().wait_stream(side)
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph):
+            self.run(vols)
+        return graph
+
     def match_host(self, host_vols: Sequence[np.ndarray], pinned_in: Optional[List] = None,
                    pinned_out: Optional[List] = None, stream=None) -> Dict[str, List]:
         """End-to-end call from host memory: copy in, run, copy the maps out."""

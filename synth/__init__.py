@@ -11,12 +11,16 @@ The paper has no dataset; these volumes stand in for cryo-electron tomograms
 """
 
 from .volumes import (  # noqa: F401
+    BATCH_CONFIGS,
     CONFIGS,
+    BatchWorkload,
     Workload,
     ball_mask,
+    batch_workload,
     blob_template,
     config_workload,
     default_mask_radius,
+    make_batch,
     make_workload,
     plant_copies,
     shoemake_quaternions,

@@ -254,6 +254,112 @@ def make_workload(shape_zyx: Sequence[int], s: int, n_blobs: int, copies: int,
                     planted_quats=pq.astype(np.float32), noise_sigma=sigma, snr=snr)
 
 
+# Batch of uneven volumes x several templates (2*3*5-smooth extents).
+BATCH_CONFIGS: Dict[str, dict] = {
+    # 16 volumes (z, y, x) from 128^3 to 384 x 384 x 192, templates 24^3..48^3,
+    # copies per (volume, template) = clamp(round(100 V / V_max), 20, 100), SNR 0.5
+    "c4": dict(shapes_zyx=[(128, 128, 128), (128, 160, 160), (128, 192, 192), (192, 192, 192),
+                           (128, 240, 240), (128, 256, 256), (160, 256, 256), (192, 256, 256),
+                           (160, 288, 288), (128, 320, 320), (160, 320, 320), (192, 320, 320),
+                           (160, 360, 360), (192, 360, 360), (160, 384, 384), (192, 384, 384)],
+               sizes=(24, 32, 40, 48), n_blobs=30, lowpass=1.0, snr=0.5, n_order=4,
+               n_rot=10000, copies_min=20, copies_max=100),
+}
+
+
+@dataclasses.dataclass
+class BatchWorkload:
+    """Several volumes, each holding planted copies of every template."""
+    name: str
+    volumes: List[np.ndarray]          # float32 [z, y, x] each
+    templates: List[np.ndarray]        # float32 [s, s, s] each
+    masks: List[np.ndarray]
+    radii: List[int]
+    n_order: int
+    quadrature: np.ndarray
+    weights: np.ndarray
+    positions: List[List[np.ndarray]]  # [volume][template] -> (P, 3) centres (x, y, z)
+    planted_quats: List[List[np.ndarray]]
+    snr: float
+
+
+def _spaced_positions(shape_zyx: Sequence[int], s: int, count: int, min_dist: float,
+                      rng: np.random.Generator, taken: List[np.ndarray]) -> np.ndarray:
+    """Like _random_positions, also keeping min_dist from the points in taken."""
+    c = s // 2
+    lo = np.array([c, c, c])
+    hi = np.array([shape_zyx[2] - s + c, shape_zyx[1] - s + c, shape_zyx[0] - s + c])
+    if np.any(hi < lo):
+        raise ValueError("volume smaller than the template box")
+    pts: List[np.ndarray] = []
+    dist, tries = float(min_dist), 0
+    while len(pts) < count:
+        p = np.array([rng.integers(lo[i], hi[i] + 1) for i in range(3)])
+        if all(np.sum((p - o) ** 2) >= dist * dist for o in taken + pts):
+            pts.append(p)
+            tries = 0
+        else:
+            tries += 1
+            if tries > 500:
+                dist *= 0.9
+                tries = 0
+    return np.array(pts, dtype=np.int64).reshape(-1, 3)
+
+
+def make_batch(shapes_zyx: Sequence[Sequence[int]], sizes: Sequence[int], n_blobs: int,
+               snr: float, n_order: int, n_rot: int, copies_min: int, copies_max: int,
+               lowpass: Optional[float] = None, seed: int = 1, name: str = "batch",
+               copies: Optional[Sequence[Sequence[int]]] = None) -> BatchWorkload:
+    """Seeded batch: template k has object seed seed + k; volume v plants
+    clamp(round(copies_max V_v / V_max), copies_min, copies_max) copies of
+    every template (or copies[v][k]) at Shoemake rotations, then adds noise
+    at the given SNR (over the union of all planted mask balls)."""
+    templates = [blob_template(s, n_blobs, seed + k, lowpass) for k, s in enumerate(sizes)]
+    radii = [default_mask_radius(s) for s in sizes]
+    masks = [ball_mask(s, r) for s, r in zip(sizes, radii)]
+    vmax = max(int(np.prod(sh)) for sh in shapes_zyx)
+    vols, pos_all, quat_all = [], [], []
+    for v, shape in enumerate(shapes_zyx):
+        rng = np.random.default_rng(1000 * seed + v)
+        n_cp = int(np.clip(round(copies_max * np.prod(shape) / vmax), copies_min, copies_max))
+        clean = np.zeros(tuple(shape))
+        union = np.zeros(tuple(shape), dtype=bool)
+        taken: List[np.ndarray] = []
+        pv, qv = [], []
+        for k in sorted(range(len(sizes)), key=lambda k: -sizes[k]):
+            count = n_cp if copies is None else int(copies[v][k])
+            pos = _spaced_positions(shape, sizes[k], count, 2.0 * radii[k], rng, taken)
+            taken.extend(list(pos))
+            pq = shoemake_quaternions(count, int(rng.integers(1 << 31)))
+            clean += plant_copies(shape, templates[k], pq, pos)
+            c, sk, ball = sizes[k] // 2, sizes[k], masks[k].astype(bool)
+            for p in pos:
+                x0, y0, z0 = (int(p[0]) - c, int(p[1]) - c, int(p[2]) - c)
+                union[z0:z0 + sk, y0:y0 + sk, x0:x0 + sk] |= ball
+            pv.append((k, pos))
+            qv.append((k, pq.astype(np.float32)))
+        sigma = float(np.sqrt(np.var(clean[union]) / snr)) if union.any() and snr > 0 else 0.0
+        clean += np.random.default_rng(1000 * seed + 500 + v).normal(0.0, sigma, size=clean.shape)
+        vols.append(clean.astype(np.float32))
+        pos_all.append([p for _, p in sorted(pv, key=lambda t: t[0])])
+        quat_all.append([q for _, q in sorted(qv, key=lambda t: t[0])])
+    quad = super_fibonacci_quaternions(n_rot)
+    return BatchWorkload(name=name, volumes=vols, templates=templates, masks=masks, radii=radii,
+                         n_order=n_order, quadrature=quad.astype(np.float32),
+                         weights=np.full(n_rot, 1.0 / n_rot), positions=pos_all,
+                         planted_quats=quat_all, snr=snr)
+
+
+def batch_workload(key: str, **overrides) -> BatchWorkload:
+    """Batch workload for one of BATCH_CONFIGS, with optional overrides."""
+    cfg = dict(BATCH_CONFIGS[key])
+    cfg.update(overrides)
+    return make_batch(cfg["shapes_zyx"], cfg["sizes"], cfg["n_blobs"], cfg["snr"],
+                      cfg["n_order"], cfg["n_rot"], cfg["copies_min"], cfg["copies_max"],
+                      lowpass=cfg.get("lowpass"), seed=cfg.get("seed", 1), name=key,
+                      copies=cfg.get("copies"))
+
+
 def config_workload(key: str, **overrides) -> Workload:
     """Workload for one of CONFIGS, with optional overrides (e.g. n_rot)."""
     cfg = dict(CONFIGS[key])
