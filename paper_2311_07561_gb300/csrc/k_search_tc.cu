@@ -107,6 +107,56 @@ __device__ __forceinline__ void issue_chunk(uint32_t tmem_d, uint32_t a_base, ui
         : "memory");
 }
 
+// (c ? a : b) bit by bit: one LOP3 whose b operand is an immediate
+template <int B>
+__device__ __forceinline__ int select_bits(int a, int c) {
+    int d;
+    asm("lop3.b32 %0, %1, %2, %3, 0xE4;" : "=r"(d) : "r"(a), "n"(B), "r"(c));
+    return d;
+}
+
+// key[j] = (r[j] & ~2047) | (15 - j % 16) for j = J..63 (compile-time j)
+template <int J>
+__device__ __forceinline__ void pack_keys(int (&key)[64], const uint32_t (&r)[64], int mask) {
+    if constexpr (J < 64) {
+        key[J] = select_bits<15 - (J & 15)>((int)r[J], mask);
+        pack_keys<J + 1>(key, r, mask);
+    }
+}
+
+// compare-exchange for a descending order
+__device__ __forceinline__ void cx(int& hi, int& lo) {
+    const int a = max(hi, lo);
+    lo = min(hi, lo);
+    hi = a;
+}
+
+// top (8, descending) := the 8 largest of top and n (4, descending): the
+// element-wise max of top and reversed n is bitonic, then three half-cleaner
+// stages sort it
+__device__ __forceinline__ void merge4(int (&top)[8], int (&n)[4]) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) top[4 + i] = max(top[4 + i], n[3 - i]);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) cx(top[i], top[i + 4]);
+#pragma unroll
+    for (int i = 0; i < 8; i += 4) { cx(top[i], top[i + 2]); cx(top[i + 1], top[i + 3]); }
+#pragma unroll
+    for (int i = 0; i < 8; i += 2) cx(top[i], top[i + 1]);
+}
+
+// the same for two lists of 8
+__device__ __forceinline__ void merge8(int (&top)[8], const int (&n)[8]) {
+#pragma unroll
+    for (int i = 0; i < 8; ++i) top[i] = max(top[i], n[7 - i]);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) cx(top[i], top[i + 4]);
+#pragma unroll
+    for (int i = 0; i < 8; i += 4) { cx(top[i], top[i + 2]); cx(top[i + 1], top[i + 3]); }
+#pragma unroll
+    for (int i = 0; i < 8; i += 2) cx(top[i], top[i + 1]);
+}
+
 // one thread: arm the barrier for `bytes` and start a bulk copy global -> shared
 __device__ __forceinline__ void bulk_load(uint32_t dst, const void* src, uint32_t bytes,
                                           uint32_t bar) {
@@ -205,7 +255,7 @@ __global__ void __launch_bounds__(kThreads, 1) search_tc_kernel(rot::SearchArgs 
     int loads_pending[2] = {0, 0};   // thread 0: copies issued and not yet waited on
     bool ok = true;
 
-    const size_t units = a.box.count();
+    const size_t units = a.u1 > a.u0 ? a.u1 - a.u0 : 0;
     const size_t ntiles = (units + 127) / 128;
     const unsigned char* gsrc = reinterpret_cast<const unsigned char*>(gtab);
     // streamed table: chunk q (counted over the whole CTA) goes to buffer q & 1;
@@ -237,8 +287,8 @@ __global__ void __launch_bounds__(kThreads, 1) search_tc_kernel(rot::SearchArgs 
     long qbase = 0;                        // chunks issued by this CTA before this tile
     for (size_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x, qbase += kChunks) {
         const bool more_tiles = tile + gridDim.x < ntiles;
-        const size_t i = tile * 128 + lane_t;
-        const bool in_range = i < units;
+        const size_t i = a.u0 + tile * 128 + lane_t;
+        const bool in_range = i < a.u1;
         const size_t v = in_range ? a.box.voxel((uint32_t)i) : 0;
         // components, score, normalised FP16 row of A (threads 0..127)
         float score = 0.f;
@@ -275,10 +325,10 @@ __global__ void __launch_bounds__(kThreads, 1) search_tc_kernel(rot::SearchArgs 
         __syncthreads();
         if (t == 0) issue(tmem, 0, qbase, bar0);
 
-        // packed keys: the float bits of phi + 1 (non-negative, so they order
-        // like the values) with the low 11 bits replaced by (2047 - grid
-        // index): one integer max gives the best point of a region (ties:
-        // lower index) at 2.4e-4 resolution of the normalised phi
+        // packed keys: the float bits of phi + 1 with the low 11 bits replaced
+        // by (2047 - grid index): one integer max gives the best point of a
+        // region (ties: lower index) at 2.4e-4 resolution of the normalised
+        // phi; top holds the 8 best region keys, descending
         int top[rot::kMaxCand];
 #pragma unroll
         for (int k = 0; k < rot::kMaxCand; ++k) top[k] = INT_MIN;
@@ -314,29 +364,25 @@ __global__ void __launch_bounds__(kThreads, 1) search_tc_kernel(rot::SearchArgs 
             for (int p = 0; p < 2; ++p) {
                 uint32_t r[64];
                 tmem_ld64(col0 + (uint32_t)p * 64, r);
-                // 64 columns = 4 regions of 16
+                // 64 columns = 4 regions of 16.  phi + 1 >= 0 (|phi| <= 1 for
+                // unit-norm C), so its float bits order like the values; the
+                // low 11 bits become the code 2047 - g of the grid index g:
+                // first only the position in the region (15 - j, one LOP3 per
+                // value), the region part is added to each region's maximum
                 const int low0 = 2047 - (c * kChunkN + colhalf * 128 + p * 64);
-                // phi + 1 >= 0 (|phi| <= 1 for unit-norm C), so its float bits
-                // order like the values
                 int key[64];
-#pragma unroll
-                for (int j = 0; j < 64; ++j) key[j] = ((int)r[j] & ~2047) | (low0 - j);
+                pack_keys<0>(key, r, ~2047);
 #pragma unroll
                 for (int w = 8; w >= 1; w >>= 1)
 #pragma unroll
                     for (int q4 = 0; q4 < 4; ++q4)
 #pragma unroll
                         for (int j = 0; j < w; ++j) key[16 * q4 + j] = max(key[16 * q4 + j], key[16 * q4 + j + w]);
+                int nk[4];
 #pragma unroll
-                for (int q4 = 0; q4 < 4; ++q4) {
-                    int x = key[16 * q4];
-#pragma unroll
-                    for (int k = 0; k < rot::kMaxCand; ++k) {
-                        const int hi = max(top[k], x);
-                        x = min(top[k], x);
-                        top[k] = hi;
-                    }
-                }
+                for (int q4 = 0; q4 < 4; ++q4) nk[q4] = key[16 * q4] + (low0 - 16 * q4 - 15);
+                cx(nk[0], nk[1]); cx(nk[2], nk[3]); cx(nk[0], nk[2]); cx(nk[1], nk[3]); cx(nk[1], nk[2]);
+                merge4(top, nk);
             }
             asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
             __syncthreads();     // this half may now be overwritten by chunk c + 2
@@ -350,14 +396,11 @@ __global__ void __launch_bounds__(kThreads, 1) search_tc_kernel(rot::SearchArgs 
         __syncthreads();
         if (colhalf == 0) {
 #pragma unroll
-            for (int k2 = 0; k2 < rot::kMaxCand; ++k2) {
-                int x = merge[k2 * 128 + lane_t];
+            {
+                int other[rot::kMaxCand];
 #pragma unroll
-                for (int k = 0; k < rot::kMaxCand; ++k) {
-                    const int hi = max(top[k], x);
-                    x = min(top[k], x);
-                    top[k] = hi;
-                }
+                for (int k = 0; k < rot::kMaxCand; ++k) other[k] = merge[k * 128 + lane_t];
+                merge8(top, other);
             }
             int ti[rot::kMaxCand];
 #pragma unroll
@@ -390,7 +433,7 @@ static ttm_status launch_tc_t(const rot::SearchArgs& s, const uint16_t* grid_fp1
     int dev = 0, sms = 0;
     TTM_CUDA_TRY(cudaGetDevice(&dev));
     TTM_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    const size_t ntiles = (s.box.count() + 127) / 128;
+    const size_t ntiles = ((s.u1 > s.u0 ? s.u1 - s.u0 : 0) + 127) / 128;
     if (ntiles == 0) return TTM_OK;
     const unsigned grid = (unsigned)(ntiles < (size_t)sms ? ntiles : (size_t)sms);
     search_tc_kernel<CT, N><<<grid, kThreads, smem, st>>>(
