@@ -81,6 +81,8 @@ def parse():
                          "(default fp32; mixed for c5, whose FP32 maps and spectra exceed HBM)")
     ap.add_argument("--mixed-compare", action=argparse.BooleanOptionalAction, default=True,
                     help="with fp32, also time the mixed-precision plan on the same volume")
+    ap.add_argument("--rotation-chunks", type=int, default=0,
+                    help="interior chunks of the pipelined search/refinement (0 = library default)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--classical", action=argparse.BooleanOptionalAction, default=True,
@@ -225,7 +227,7 @@ def source_hash(names) -> str:
 
 def roofline(kernels: dict, steps: int, nvox: int, K: int, n_taps: int, n_grid: int,
              n_cand: int, newton: int, peaks: dict, spectrum_bytes: float = 0.0,
-             n_interior: int | None = None) -> dict:
+             n_interior: int | None = None, tc_direct: bool = False) -> dict:
     """Roofline object for the kernel class with the largest share.  The
     rotation kernels visit only the interior voxels (n_interior)."""
     n_int = nvox if n_interior is None else n_interior
@@ -233,20 +235,34 @@ def roofline(kernels: dict, steps: int, nvox: int, K: int, n_taps: int, n_grid: 
     ms_launch = kernels[name]["ms"] / max(kernels[name]["launches"], 1)
     launches_per_step = kernels[name]["launches"] / steps
     src = []
-    if name == "direct_corr":
+    if name == "direct_corr" and tc_direct:
+        npad = (K + 15) // 16 * 16
+        work = 2.0 * npad * n_taps * n_int / launches_per_step
+        bound, peak, unit, scale = "tensor", peaks.get("bf16_tflops", 1900.0), "TFLOP/s", 1e12
+        src = ["k_direct_tc.cu"]
+        peak_source = "measured dense bf16 (MEASURED_PEAKS.json bf16_tflops); fp16 runs at the bf16 rate"
+    elif name == "direct_corr":
         work = 2.0 * K * n_taps * nvox / launches_per_step
         bound, peak, unit, scale = "alu", FP32_ALU_PEAK_TFLOPS, "TFLOP/s", 1e12
         src = ["k_direct.cu"]
         peak_source = "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz"
-    elif name == "rotation_search" and K == 35 and n_grid == 2048:
-        work = 2.0 * n_grid * 48 * n_int / launches_per_step     # FP16 MMA, K padded to 48
+    elif name == "rotation_search" and K in (35, 84) and n_grid == 2048:
+        kp = 48 if K == 35 else 96                               # K + constant column, padded
+        work = 2.0 * n_grid * kp * n_int / launches_per_step     # FP16 MMA
         bound, peak, unit, scale = "tensor", peaks.get("bf16_tflops", 1900.0), "TFLOP/s", 1e12
         src = ["k_search_tc.cu", "k_rotation.cuh"]
         peak_source = "measured dense bf16 (MEASURED_PEAKS.json bf16_tflops); fp16 runs at the bf16 rate"
     elif name in ("rotation_search", "rotation_polish"):
-        KB = 10
-        per_cand = (2 + newton) * (2 * 10 * KB + 40) + newton * 150
-        work = ((2.0 * n_grid * K + 2 * K) if name == "rotation_search" else n_cand * per_cand) \
+        # order n from K = C(n+3, 3); H = C x^(n-2) has 10 entries of KB terms
+        n_ord = {10: 2, 35: 4, 84: 6, 165: 8}.get(K, 4)
+        KB = (n_ord + 1) * n_ord * (n_ord - 1) // 6
+        KG = (n_ord + 2) * (n_ord + 1) * n_ord // 6
+        # every candidate: 3 evaluations of C x^(n-1) and 2 normalisations; the
+        # 6 best: 1 + newton evaluations of C x^(n-2) and newton Newton solves
+        power = 3 * 10 * KG + 2 * 12
+        newton_part = (1 + newton) * (2 * 10 * KB + 2 * KB + 40) + newton * 150
+        per_vox = n_cand * power + min(6, n_cand) * newton_part
+        work = ((2.0 * n_grid * K + 2 * K) if name == "rotation_search" else per_vox) \
             * n_int / launches_per_step
         bound, peak, unit, scale = "alu", FP32_ALU_PEAK_TFLOPS, "TFLOP/s", 1e12
         src = ["k_rotation.cuh", "k_rotation.cu", "k_rotation_n4.cu"]
@@ -308,6 +324,7 @@ def run_ours(args) -> None:
     opts = ttm.PlanOpts()
     opts.path = {"auto": 0, "direct": 1, "fft": 2}[args.path]
     opts.precision = ttm.TTM_PREC_MIXED if args.precision == "mixed" else ttm.TTM_PREC_FP32
+    opts.rotation_chunks = args.rotation_chunks
     matcher = ttm.Matcher([(comp, desc, wl.mask)], [((X, Y, Z), 0)], opts=opts)
     path = ttm.ttm_plan_problem_path(matcher.plan, 0)
     vol = torch.from_numpy(wl.volume).to(dev)
@@ -414,6 +431,7 @@ def run_ours(args) -> None:
         o2 = ttm.PlanOpts()
         o2.path = opts.path
         o2.precision = ttm.TTM_PREC_MIXED
+        o2.rotation_chunks = args.rotation_chunks
         m2 = ttm.Matcher([(comp, desc, wl.mask)], [((X, Y, Z), 0)], opts=o2)
         for _ in range(args.warmup):
             m2.run([vol])
@@ -449,7 +467,7 @@ def run_ours(args) -> None:
     s_edge = wl.template.shape[0]
     n_interior = max(X - s_edge + 1, 0) * max(Y - s_edge + 1, 0) * max(Z - s_edge + 1, 0)
     rf = roofline(kern, args.steps, nvox, desc.K, n_taps, 2048, 8, 4, peaks, spec_bytes,
-                  n_interior)
+                  n_interior, ttm.ttm_plan_problem_tensor_direct(matcher.plan, 0))
     cpu = None
     if not args.no_cpu_baseline and world == 1:
         cpu = cpu_baseline_obj(run_cpu_sample(args.workload, 128, 2), args.workload)
@@ -513,6 +531,7 @@ def run_batch(args) -> None:
     opts = ttm.PlanOpts()
     opts.path = {"auto": ttm.TTM_PATH_TUNE, "direct": 1, "fft": 2}[args.path]
     opts.precision = ttm.TTM_PREC_MIXED if args.precision == "mixed" else ttm.TTM_PREC_FP32
+    opts.rotation_chunks = args.rotation_chunks
     dvols = [torch.from_numpy(v).to(dev) for v in bw.volumes]
     problems, vols = [], []
     for v, vol in enumerate(bw.volumes):

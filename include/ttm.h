@@ -100,7 +100,10 @@ typedef struct ttm_peak {
  * FP16 operands and FP32 accumulation.  TTM_PREC_MIXED stores the template
  * spectra, the K product spectra and the K correlation maps of the FFT path
  * in bf16 (half the memory and traffic; FFT lengths 16..1024, other problems
- * stay FP32).  Expected error vs FP32: |dC|, |dscore|, |dlambda| <= 5e-3. */
+ * stay FP32), and runs the direct path as an implicit GEMM on the tensor
+ * cores (FP16 operands, FP32 accumulation; masks with up to ~1900 voxels for
+ * order 4, ~950 for order 6; larger masks stay on the CUDA cores).  Expected
+ * error vs FP32: |dC|, |dscore|, |dlambda| <= 5e-3. */
 #define TTM_PREC_FP32   0
 #define TTM_PREC_MIXED  1
 
@@ -111,7 +114,11 @@ typedef struct ttm_plan_opts {
     int n_cells;        /* regions of the grid; 0 = default (128); must divide n_grid */
     int n_candidates;   /* regions polished per voxel; 0 = default (8)         */
     int newton_steps;   /* Newton steps per candidate; 0 = default (4)         */
-    int reserved[4];
+    int rotation_chunks; /* split the interior into this many chunks and run  */
+                         /* the search of chunk i+1 (high-priority stream)    */
+                         /* beside the refinement of chunk i (low priority);  */
+                         /* 0 = default (8), 1 = one search then one refinement */
+    int reserved[3];
 } ttm_plan_opts;
 
 typedef struct ttm_plan_s* ttm_plan_t;
@@ -212,6 +219,10 @@ ttm_status ttm_plan_problem_path(ttm_plan_t plan, int problem, int* path);
  * ms[1] = FFT path (local statistics + K correlations, best of 2 runs), or
  * -1 where a path was not timed (the cost model decided).  Host-only. */
 ttm_status ttm_plan_problem_tuning(ttm_plan_t plan, int problem, double* ms);
+
+/* *on = 1 when problem p's direct correlation runs on the tensor cores (FP16
+ * operands, TTM_PREC_MIXED), else 0.  Host-only. */
+ttm_status ttm_plan_problem_tensor_direct(ttm_plan_t plan, int problem, int* on);
 
 /* Padded FFT box of problem p: box[0..2] = (Xp, Yp, Zp), each the smallest
  * supported length 2^p 3^a 5^b (16..1024), else a power of two, not below

@@ -44,6 +44,7 @@ from ._binding import (  # noqa: F401
     ttm_plan_problem_path,
     ttm_plan_problem_fft_box,
     ttm_plan_problem_tuning,
+    ttm_plan_problem_tensor_direct,
     ttm_plan_timing,
     ttm_plan_workspace_size,
     ttm_status_string,

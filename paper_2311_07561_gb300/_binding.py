@@ -31,6 +31,7 @@ EXPORTED = (
     "ttm_status_string", "ttm_device_count", "ttm_build_workspace_size",
     "ttm_build_tensor_template", "ttm_plan", "ttm_plan_workspace_size",
     "ttm_plan_problem_path", "ttm_plan_problem_fft_box", "ttm_plan_problem_tuning",
+    "ttm_plan_problem_tensor_direct",
     "ttm_plan_launch_count", "ttm_plan_destroy",
     "ttm_local_stats", "ttm_correlate", "ttm_extract_peaks", "ttm_plan_enable_timing",
     "ttm_plan_timing", "ttm_kernel_class_name", "ttm_build_tensor_template_noalloc",
@@ -61,7 +62,8 @@ class Peak(ctypes.Structure):
 class PlanOpts(ctypes.Structure):
     _fields_ = [("path", ctypes.c_int), ("precision", ctypes.c_int), ("n_grid", ctypes.c_int),
                 ("n_cells", ctypes.c_int), ("n_candidates", ctypes.c_int),
-                ("newton_steps", ctypes.c_int), ("reserved", ctypes.c_int * 4)]
+                ("newton_steps", ctypes.c_int), ("rotation_chunks", ctypes.c_int),
+                ("reserved", ctypes.c_int * 3)]
 
 
 _lib: Optional[ctypes.CDLL] = None
@@ -88,6 +90,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "ttm_plan_workspace_size": (I, [P, ctypes.POINTER(S)]),
         "ttm_plan_problem_path": (I, [P, I, ctypes.POINTER(I)]),
         "ttm_plan_problem_fft_box": (I, [P, I, ctypes.POINTER(I)]),
+        "ttm_plan_problem_tensor_direct": (I, [P, I, ctypes.POINTER(I)]),
         "ttm_plan_problem_tuning": (I, [P, I, ctypes.POINTER(ctypes.c_double)]),
         "ttm_plan_launch_count": (I, [P, ctypes.POINTER(L)]),
         "ttm_plan_destroy": (None, [P]),
@@ -238,6 +241,13 @@ def ttm_plan_problem_tuning(plan: int, problem: int) -> tuple:
     out = (ctypes.c_double * 2)()
     _check(load_library().ttm_plan_problem_tuning(plan, problem, out), "ttm_plan_problem_tuning")
     return tuple(out)
+
+
+def ttm_plan_problem_tensor_direct(plan: int, problem: int) -> bool:
+    out = ctypes.c_int()
+    _check(load_library().ttm_plan_problem_tensor_direct(plan, problem, ctypes.byref(out)),
+           "ttm_plan_problem_tensor_direct")
+    return bool(out.value)
 
 
 def ttm_plan_launch_count(plan: int) -> int:

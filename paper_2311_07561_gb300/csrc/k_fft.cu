@@ -315,9 +315,9 @@ bool fixed_cols_mul(int L, const float2* spec, const __nv_bfloat162* tspec, __nv
 }
 
 bool fixed_rows_c2r(int L, const float2* prod, int X, int Y, int Z, FftGeom g, float* corr, int K,
-                    const float2* tw, cudaStream_t st, cudaError_t* err) {
+                    const float2* tw, int* status, cudaStream_t st, cudaError_t* err) {
     switch (L) {
-#define C(L) TTM_FFT_CASE(L, rows_c2r(prod, X, Y, Z, g, corr, K, tw, st))
+#define C(L) TTM_FFT_CASE(L, rows_c2r(prod, X, Y, Z, g, corr, K, tw, status, st))
         TTM_FFT_LENGTHS(C)
 #undef C
         default: return false;
@@ -325,10 +325,10 @@ bool fixed_rows_c2r(int L, const float2* prod, int X, int Y, int Z, FftGeom g, f
 }
 
 bool fixed_rows_c2r(int L, const __nv_bfloat162* prod, int X, int Y, int Z, FftGeom g,
-                    __nv_bfloat16* corr, int K, const float2* tw, cudaStream_t st,
+                    __nv_bfloat16* corr, int K, const float2* tw, int* status, cudaStream_t st,
                     cudaError_t* err) {
     switch (L) {
-#define C(L) TTM_FFT_CASE(L, rows_c2r_bf(prod, X, Y, Z, g, corr, K, tw, st))
+#define C(L) TTM_FFT_CASE(L, rows_c2r_bf(prod, X, Y, Z, g, corr, K, tw, status, st))
         TTM_FFT_LENGTHS(C)
 #undef C
         default: return false;
@@ -445,11 +445,11 @@ static ttm_status spectrum_inverse_z_t(const float2* spec, const TS* tspec, int 
 
 template <typename PS, typename RT>
 static ttm_status inverse_yx_t(PS* prod, int K, int X, int Y, int Z, const FftShape& S, RT* corr,
-                               cudaStream_t st, long long* cnt) {
+                               int* status, cudaStream_t st, long long* cnt) {
     FftGeom g{S.Xp, S.Yp, S.Zp, S.Xp / 2 + 1};
     TTM_TRY(launch_cols_t<PS>(prod, S.Yp, g.Xh, K * S.Zp, S.d_tw_y, +1, st, cnt));
     cudaError_t err = cudaSuccess;
-    if (!fixed_rows_c2r(S.Xp, prod, X, Y, Z, g, corr, K, S.d_tw_x, st, &err)) {
+    if (!fixed_rows_c2r(S.Xp, prod, X, Y, Z, g, corr, K, S.d_tw_x, status, st, &err)) {
         if constexpr (!std::is_same<PS, float2>::value || !std::is_same<RT, float>::value)
             return TTM_ERR_UNSUPPORTED;
         else {
@@ -472,8 +472,8 @@ ttm_status launch_fft_spectrum_inverse_z(const float2* spec, const float2* tspec
 }
 
 ttm_status launch_fft_inverse_yx(float2* prod, int K, int X, int Y, int Z, const FftShape& S,
-                                 float* corr, cudaStream_t st, long long* cnt) {
-    return inverse_yx_t<float2, float>(prod, K, X, Y, Z, S, corr, st, cnt);
+                                 float* corr, int* status, cudaStream_t st, long long* cnt) {
+    return inverse_yx_t<float2, float>(prod, K, X, Y, Z, S, corr, status, st, cnt);
 }
 
 // mixed precision: bf16 template spectra, products and correlation maps
@@ -486,10 +486,10 @@ ttm_status launch_fft_spectrum_inverse_z_bf16(const float2* spec, const void* ts
 }
 
 ttm_status launch_fft_inverse_yx_bf16(void* prod, int K, int X, int Y, int Z, const FftShape& S,
-                                      void* corr, cudaStream_t st, long long* cnt) {
+                                      void* corr, int* status, cudaStream_t st, long long* cnt) {
     return inverse_yx_t<__nv_bfloat162, __nv_bfloat16>(
         reinterpret_cast<__nv_bfloat162*>(prod), K, X, Y, Z, S,
-        reinterpret_cast<__nv_bfloat16*>(corr), st, cnt);
+        reinterpret_cast<__nv_bfloat16*>(corr), status, st, cnt);
 }
 
 __global__ void to_bf16_kernel(const float2* __restrict__ a, __nv_bfloat162* __restrict__ b, size_t n) {
@@ -505,12 +505,12 @@ ttm_status launch_spectra_to_bf16(const float2* a, void* b, size_t n, cudaStream
 
 // w from the FFT-based window sums of (f - mean) and (f - mean)^2 (Algorithm 1):
 // V = S2 - S1^2 / m_sum in FP64; interior only; floor 1e-6 m_sum var(f).
-// Block (x tile, y, z): no index divisions.  The volume statistics and the
-// floor are formed once per CTA (FP64 divisions are slow on this GPU); each
+// Persistent CTAs over x-segments of 128 voxels: the volume statistics and
+// the floor (FP64 divisions, slow on this GPU) are formed once per CTA; each
 // interior voxel does two FP64 operations plus conversions.
-__global__ void stats_from_sums_kernel(const float* __restrict__ s1, const float* __restrict__ s2,
-                                       float* __restrict__ w, int X, int Y, int Z, int s,
-                                       double mask_sum, const double* __restrict__ moments) {
+__global__ void __launch_bounds__(128) stats_from_sums_kernel(
+    const float* __restrict__ s1, const float* __restrict__ s2, float* __restrict__ w, int X,
+    int Y, int Z, int s, double mask_sum, const double* __restrict__ moments) {
     __shared__ double sh[2];
     if (threadIdx.x == 0) {
         const double nv = (double)X * Y * Z;
@@ -520,24 +520,31 @@ __global__ void stats_from_sums_kernel(const float* __restrict__ s1, const float
         sh[1] = 1e-6 * mask_sum * var_f;
     }
     __syncthreads();
-    const int x = blockIdx.x * blockDim.x + threadIdx.x;
-    const int y = blockIdx.y, z = blockIdx.z;
-    if (x >= X) return;
-    const size_t v = ((size_t)z * Y + y) * X + x;
-    float out = 0.f;
-    if (interior(x, X, s) && interior(y, Y, s) && interior(z, Z, s)) {
-        const double S1 = s1[v], S2 = s2[v];
-        const double V = fma(-S1, S1 * sh[0], S2);
-        if (V > sh[1]) out = rsqrtf((float)V);
+    const double inv_m = sh[0], floor_v = sh[1];
+    const uint32_t xt = (uint32_t)((X + 127) / 128);
+    const uint32_t segs = xt * (uint32_t)Y * (uint32_t)Z;
+    for (uint32_t sg = blockIdx.x; sg < segs; sg += gridDim.x) {
+        const uint32_t row = sg / xt;
+        const int x = (int)(sg - row * xt) * 128 + threadIdx.x;
+        const int y = (int)(row % (uint32_t)Y), z = (int)(row / (uint32_t)Y);
+        if (x >= X) continue;
+        const size_t v = ((size_t)z * Y + y) * X + x;
+        float out = 0.f;
+        if (interior(x, X, s) && interior(y, Y, s) && interior(z, Z, s)) {
+            const double S1 = s1[v], S2 = s2[v];
+            const double V = fma(-S1, S1 * inv_m, S2);
+            if (V > floor_v) out = rsqrtf((float)V);
+        }
+        w[v] = out;
     }
-    w[v] = out;
 }
 
 ttm_status launch_stats_from_sums(const float* s1, const float* s2, float* w, int X, int Y, int Z,
                                   int s, double mask_sum, const double* moments, cudaStream_t st,
                                   long long* cnt) {
-    if (Y > 65535 || Z > 65535) return TTM_ERR_UNSUPPORTED;
-    dim3 grid((unsigned)((X + 127) / 128), (unsigned)Y, (unsigned)Z);
+    const size_t segs = (size_t)((X + 127) / 128) * Y * Z;
+    if (segs > 0xFFFFFFFFull) return TTM_ERR_UNSUPPORTED;
+    const unsigned grid = (unsigned)(segs < 152 * 16 ? segs : 152 * 16);
     stats_from_sums_kernel<<<grid, 128, 0, st>>>(s1, s2, w, X, Y, Z, s, mask_sum, moments);
     return after_launch(cnt);
 }

@@ -407,60 +407,182 @@ __global__ void __launch_bounds__(kFftThreads) cols_mul_t(const float2* __restri
     }
 }
 
+// ---- stages with functor input/output (first stage reads a staged tile,
+// last stage writes global memory) --------------------------------------
+template <int L, int ST>
+constexpr int ns_before() {
+    int ns = 1;
+    for (int s = 0; s < ST; ++s) ns *= stage_radix(L, s);
+    return ns;
+}
+
+// One Stockham stage of radix R: element x of line `line` comes from
+// src(x, line) and goes to dst(x, line, v).  LINE_FAST: consecutive threads
+// take consecutive lines (shared-memory destinations), else consecutive
+// butterflies, so that a stage writing global memory stores consecutive x.
+template <int L, int R, int NS, int NB, int SIGN, bool LINE_FAST, class Src, class Dst>
+__device__ __forceinline__ void stage_io(const Src& src, const Dst& dst,
+                                         const float2* __restrict__ tw) {
+    constexpr int NBF = L / R;
+    constexpr int STRIDE_TW = L / (NS * R);
+    for (int idx = threadIdx.x; idx < NBF * NB; idx += blockDim.x) {
+        const int line = LINE_FAST ? (idx & (NB - 1)) : idx / NBF;
+        const int j = LINE_FAST ? idx / NB : idx % NBF;
+        const int jm = j % NS;
+        const int idxD = (j - jm) * R + jm;
+        float2 v[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) v[r] = src(j + r * NBF, line);
+        if constexpr (NS > 1) {
+#pragma unroll
+            for (int r = 1; r < R; ++r) {
+                float2 w = __ldg(tw + jm * r * STRIDE_TW);
+                if (SIGN > 0) w.y = -w.y;
+                v[r] = cmul(v[r], w);
+            }
+        }
+        dft_small<R, SIGN>(v);
+#pragma unroll
+        for (int r = 0; r < R; ++r) dst(idxD + r * NS, line, v[r]);
+    }
+}
+
+// All stages of NB lines: the first reads src, the middle ones ping-pong
+// between a and b (pitch PITCH, x-major), the last writes out.
+template <int L, int ST, int NB, int PITCH, int SIGN, class Src, class Out>
+__device__ __forceinline__ void stages_io(const Src& src, float2* a, float2* b, const Out& out,
+                                          const float2* __restrict__ tw) {
+    constexpr int R = stage_radix(L, ST);
+    constexpr int NS = ns_before<L, ST>();
+    if constexpr (ST + 1 == n_stages(L)) {
+        stage_io<L, R, NS, NB, SIGN, false>(src, out, tw);
+    } else {
+        stage_io<L, R, NS, NB, SIGN, true>(
+            src, [a](int x, int line, float2 v) { a[x * PITCH + line] = v; }, tw);
+        __syncthreads();
+        stages_io<L, ST + 1, NB, PITCH, SIGN>(
+            [a](int x, int line) { return a[x * PITCH + line]; }, b, a, out, tw);
+    }
+}
+
+// ---- half-spectrum rows -> real x lines (inverse), persistent -----------
+// A tile is NB consecutive half-spectrum rows (contiguous in memory).  Each
+// CTA walks tiles with a stride of gridDim.x; the next tile is fetched by one
+// bulk copy into the other staging buffer while the current one is
+// transformed.  The first stage reads the staged rows with the Hermitian
+// extension X[L - x] = conj X[x]; the last stage stores the real parts
+// straight to the X x Y x Z maps (out is batch-major, X Y Z floats per item).
+// Copy waits are bounded: on expiry the CTA records TTM_ERR_TIMEOUT, waits
+// once more for its copy in flight and exits.
+template <int L>
+constexpr int c2r_stages_buffers() { return n_stages(L) >= 3 ? 2 : 1; }
+
+template <int L, typename PS>
+constexpr uint32_t c2r_tile_bytes() { return (uint32_t)(rows_nb<L>() * (L / 2 + 1) * sizeof(PS)); }
+
+template <int L, typename PS>
+constexpr size_t c2r_smem() {
+    return 2 * (size_t)c2r_tile_bytes<L, PS>() +
+           (size_t)c2r_stages_buffers<L>() * L * (rows_nb<L>() + 1) * sizeof(float2);
+}
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void bulk_to_smem(uint32_t dst, const void* src, uint32_t bytes,
+                                             uint32_t bar) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(bar), "r"(bytes)
+                 : "memory");
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n"
+        ::"r"(dst), "l"(src), "r"(bytes), "r"(bar)
+        : "memory");
+}
+
+__device__ __forceinline__ bool bar_wait(uint32_t bar, uint32_t phase) {
+    for (long it = 0; it < (1L << 24); ++it) {
+        uint32_t done;
+        asm volatile(
+            "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+            "selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(done)
+            : "r"(bar), "r"(phase)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
 template <int L, typename PS, typename RT>
 __global__ void __launch_bounds__(kFftThreads) rows_c2r_t(const PS* __restrict__ in, int X, int Y,
                                                           int Z, FftGeom g, RT* __restrict__ out,
-                                                          int n_batch, const float2* __restrict__ tw) {
+                                                          int n_batch, const float2* __restrict__ tw,
+                                                          int* status) {
     constexpr int NB = rows_nb<L>();
     constexpr int PITCH = NB + 1;
     constexpr int XH = L / 2 + 1;
-    extern __shared__ float2 sm[];
-    float2* A = sm;
-    float2* Bf = sm + L * PITCH;
-    constexpr int PER = (NB * L + kFftThreads - 1) / kFftThreads;
+    constexpr uint32_t TILE = c2r_tile_bytes<L, PS>();
+    static_assert(TILE % 16 == 0, "bulk copies move multiples of 16 bytes");
+    extern __shared__ __align__(128) unsigned char smraw[];
+    float2* a = reinterpret_cast<float2*>(smraw + 2 * TILE);
+    float2* b = a + (c2r_stages_buffers<L>() == 2 ? L * PITCH : 0);
+    __shared__ __align__(8) uint64_t bars[2];
     __shared__ long long row_out[NB];        // output offset of each row, -1 = not written
     const size_t rows_per_item = (size_t)g.Yp * g.Zp;
-    const size_t nrows = rows_per_item * n_batch;
-    const size_t row0 = (size_t)blockIdx.x * NB;
-    if (threadIdx.x < NB) {
-        const size_t row = row0 + threadIdx.x;
-        long long off = -1;
-        if (row < nrows) {
+    const size_t ntiles = rows_per_item * n_batch / NB;      // NB divides Yp Zp
+    const uint32_t sbase = smem_addr(smraw);
+    const uint32_t bar[2] = {smem_addr(&bars[0]), smem_addr(&bars[1])};
+    if (threadIdx.x == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(bar[0]) : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(bar[1]) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+    }
+    __syncthreads();
+    size_t tile = blockIdx.x;
+    if (tile >= ntiles) return;
+    if (threadIdx.x == 0) bulk_to_smem(sbase, in + tile * NB * XH, TILE, bar[0]);
+    uint32_t phase[2] = {0u, 0u};
+    for (int it = 0; tile < ntiles; ++it, tile += gridDim.x) {
+        const int buf = it & 1;
+        const size_t next = tile + gridDim.x;
+        if (threadIdx.x == 0 && next < ntiles) {
+            asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+            bulk_to_smem(sbase + (uint32_t)(buf ^ 1) * TILE, in + next * NB * XH, TILE,
+                         bar[buf ^ 1]);
+        }
+        if (threadIdx.x < NB) {
+            const size_t row = tile * NB + threadIdx.x;
             const size_t item = row / rows_per_item;
             const int rr = (int)(row - item * rows_per_item);
             const int y = rr % g.Yp, z = rr / g.Yp;
-            if (y < Y && z < Z) off = (long long)(item * ((size_t)X * Y * Z) + ((size_t)z * Y + y) * X);
+            row_out[threadIdx.x] = (y < Y && z < Z)
+                ? (long long)(item * ((size_t)X * Y * Z) + ((size_t)z * Y + y) * X) : -1;
         }
-        row_out[threadIdx.x] = off;
-    }
-    float2 v[PER];
-#pragma unroll
-    for (int i = 0; i < PER; ++i) {          // loads first, Hermitian extension on the fly
-        const int e = threadIdx.x + i * kFftThreads;
-        const int r = e / L, x = e % L;
-        const size_t row = row0 + r;
-        v[i] = make_float2(0.f, 0.f);
-        if (e < NB * L && row < nrows) {
-            const PS* src = in + row * XH;
-            if (x < XH) v[i] = ldc(src + x);
-            else { float2 c = ldc(src + (L - x)); v[i] = make_float2(c.x, -c.y); }
+        const bool ok = bar_wait(bar[buf], phase[buf]);
+        phase[buf] ^= 1u;
+        if (__syncthreads_or(!ok)) {
+            if (threadIdx.x == 0) {
+                atomicExch(status, TTM_ERR_TIMEOUT);
+                if (next < ntiles) bar_wait(bar[buf ^ 1], phase[buf ^ 1]);
+            }
+            return;
         }
-    }
-#pragma unroll
-    for (int i = 0; i < PER; ++i) {
-        const int e = threadIdx.x + i * kFftThreads;
-        const int r = e / L, x = e % L;
-        if (e < NB * L) A[x * PITCH + r] = v[i];
-    }
-    __syncthreads();
-    float2* res = fft_lines_t<L, NB, PITCH, +1>(A, Bf, tw);   // ends with a barrier
-#pragma unroll
-    for (int i = 0; i < PER; ++i) {
-        const int e = threadIdx.x + i * kFftThreads;
-        const int r = e / L, x = e % L;
-        if (e >= NB * L || x >= X) continue;
-        const long long off = row_out[r];
-        if (off >= 0) str(out + off + x, res[x * PITCH + r].x);
+        const PS* S = reinterpret_cast<const PS*>(smraw + (size_t)buf * TILE);
+        stages_io<L, 0, NB, PITCH, +1>(
+            [S](int x, int line) {
+                if (x < XH) return ldc(S + line * XH + x);
+                const float2 c = ldc(S + line * XH + (L - x));
+                return make_float2(c.x, -c.y);
+            },
+            a, b,
+            [out, X](int x, int line, float2 v) {
+                const long long off = row_out[line];
+                if (x < X && off >= 0) str(out + off + x, v.x);
+            },
+            tw);
+        __syncthreads();     // staging buffer, a/b and row_out are reused
     }
 }
 
@@ -482,9 +604,10 @@ struct FftLen {
                                    __nv_bfloat162* prod, int Bz, int K, const float2* tw,
                                    cudaStream_t st);
     static cudaError_t rows_c2r(const float2* prod, int X, int Y, int Z, FftGeom g, float* corr,
-                                int K, const float2* tw, cudaStream_t st);
+                                int K, const float2* tw, int* status, cudaStream_t st);
     static cudaError_t rows_c2r_bf(const __nv_bfloat162* prod, int X, int Y, int Z, FftGeom g,
-                                   __nv_bfloat16* corr, int K, const float2* tw, cudaStream_t st);
+                                   __nv_bfloat16* corr, int K, const float2* tw, int* status,
+                                   cudaStream_t st);
 };
 
 namespace fftk {
@@ -516,15 +639,23 @@ cudaError_t run_cols_mul(const float2* spec, const TS* tspec, PS* prod, int Bz, 
 
 template <int L, typename PS, typename RT>
 cudaError_t run_rows_c2r(const PS* prod, int X, int Y, int Z, FftGeom g, RT* corr, int K,
-                         const float2* tw, cudaStream_t st) {
+                         const float2* tw, int* status, cudaStream_t st) {
     constexpr int NB = rows_nb<L>();
-    const size_t smem = (size_t)2 * L * (NB + 1) * sizeof(float2);
+    constexpr size_t smem = c2r_smem<L, PS>();
     cudaError_t e = cudaFuncSetAttribute(rows_c2r_t<L, PS, RT>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    const size_t nrows = (size_t)g.Yp * g.Zp * K;
-    rows_c2r_t<L, PS, RT><<<(unsigned)((nrows + NB - 1) / NB), kFftThreads, smem, st>>>(
-        prod, X, Y, Z, g, corr, K, tw);
+    int dev = 0, sms = 0, per_sm = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, rows_c2r_t<L, PS, RT>,
+                                                           kFftThreads, smem)) != cudaSuccess)
+        return e;
+    const size_t ntiles = (size_t)g.Yp * g.Zp * K / NB;
+    const size_t cap = (size_t)sms * (per_sm > 0 ? per_sm : 1);
+    const unsigned grid = (unsigned)(ntiles < cap ? ntiles : cap);
+    if (grid == 0) return cudaSuccess;
+    rows_c2r_t<L, PS, RT><<<grid, kFftThreads, smem, st>>>(prod, X, Y, Z, g, corr, K, tw, status);
     return cudaGetLastError();
 }
 
@@ -574,14 +705,16 @@ cudaError_t FftLen<L>::cols_mul_bf(const float2* spec, const __nv_bfloat162* tsp
 
 template <int L>
 cudaError_t FftLen<L>::rows_c2r(const float2* prod, int X, int Y, int Z, FftGeom g, float* corr,
-                                int K, const float2* tw, cudaStream_t st) {
-    return fftk::run_rows_c2r<L, float2, float>(prod, X, Y, Z, g, corr, K, tw, st);
+                                int K, const float2* tw, int* status, cudaStream_t st) {
+    return fftk::run_rows_c2r<L, float2, float>(prod, X, Y, Z, g, corr, K, tw, status, st);
 }
 
 template <int L>
 cudaError_t FftLen<L>::rows_c2r_bf(const __nv_bfloat162* prod, int X, int Y, int Z, FftGeom g,
-                                   __nv_bfloat16* corr, int K, const float2* tw, cudaStream_t st) {
-    return fftk::run_rows_c2r<L, __nv_bfloat162, __nv_bfloat16>(prod, X, Y, Z, g, corr, K, tw, st);
+                                   __nv_bfloat16* corr, int K, const float2* tw, int* status,
+                                   cudaStream_t st) {
+    return fftk::run_rows_c2r<L, __nv_bfloat162, __nv_bfloat16>(prod, X, Y, Z, g, corr, K, tw,
+                                                                 status, st);
 }
 
 }  // namespace ttm

@@ -6,9 +6,11 @@ namespace ttm {
 int rotation_row_stride(int n_order) { return (n_comp(n_order) + 3) & ~3; }
 
 static void fill_args(const void* corr, const float* w, size_t nvox, const VoxBox& box,
-                      const RotGrid& g, uint16_t* cand, float* score, float* quat, float* lambda,
-                      float* comp_out, rot::SearchArgs& sa, rot::PolishArgs& pa) {
+                      uint32_t u0, uint32_t u1, const RotGrid& g, uint16_t* cand, float* score,
+                      float* quat, float* lambda, float* comp_out, rot::SearchArgs& sa,
+                      rot::PolishArgs& pa) {
     sa.corr = corr; sa.w = w; sa.nvox = nvox; sa.box = box; sa.score = score; sa.cand = cand;
+    sa.u0 = u0; sa.u1 = u1; pa.u0 = u0; pa.u1 = u1;
     sa.gm = g.d_m; sa.cell_end = g.d_cell_end; sa.n_grid = g.n_grid;
     pa.corr = corr; pa.w = w; pa.nvox = nvox; pa.box = box; pa.score = score; pa.cand = cand; pa.quat = quat;
     pa.lambda = lambda; pa.comp_out = comp_out; pa.gq = g.d_q; pa.n_cand = g.n_cand;
@@ -16,14 +18,14 @@ static void fill_args(const void* corr, const float* w, size_t nvox, const VoxBo
 }
 
 ttm_status launch_rotation_search(int n_order, const void* corr, bool bf16, const float* w,
-                                  size_t nvox, const VoxBox& box, const RotGrid& g,
-                                  uint16_t* cand, int* status, float* score, cudaStream_t st,
-                                  long long* cnt) {
-    if (box.count() > 0xFFFFFFFFull) return TTM_ERR_UNSUPPORTED;
-    if (box.count() == 0) return TTM_OK;
+                                  size_t nvox, const VoxBox& box, uint32_t u0, uint32_t u1,
+                                  const RotGrid& g, uint16_t* cand, int* status, float* score,
+                                  cudaStream_t st, long long* cnt) {
+    if (box.count() > 0xFFFFFFFFull || u1 > box.count()) return TTM_ERR_UNSUPPORTED;
+    if (u1 <= u0) return TTM_OK;
     rot::SearchArgs sa;
     rot::PolishArgs pa;
-    fill_args(corr, w, nvox, box, g, cand, score, nullptr, nullptr, nullptr, sa, pa);
+    fill_args(corr, w, nvox, box, u0, u1, g, cand, score, nullptr, nullptr, nullptr, sa, pa);
     if (g.d_gtab && search_tc_supported(n_order, g.n_grid, g.n_cells))
         return launch_search_tc(n_order, sa, g.d_gtab, status, bf16, st, cnt);
     switch (n_order) {
@@ -36,16 +38,16 @@ ttm_status launch_rotation_search(int n_order, const void* corr, bool bf16, cons
 }
 
 ttm_status launch_rotation_polish(int n_order, const void* corr, bool bf16, const float* w,
-                                  size_t nvox, const VoxBox& box, const RotGrid& g,
-                                  const uint16_t* cand, const float* score, float* quat,
-                                  float* lambda, float* comp_out, cudaStream_t st,
+                                  size_t nvox, const VoxBox& box, uint32_t u0, uint32_t u1,
+                                  const RotGrid& g, const uint16_t* cand, const float* score,
+                                  float* quat, float* lambda, float* comp_out, cudaStream_t st,
                                   long long* cnt) {
-    if (box.count() > 0xFFFFFFFFull) return TTM_ERR_UNSUPPORTED;
-    if (box.count() == 0) return TTM_OK;
+    if (box.count() > 0xFFFFFFFFull || u1 > box.count()) return TTM_ERR_UNSUPPORTED;
+    if (u1 <= u0) return TTM_OK;
     rot::SearchArgs sa;
     rot::PolishArgs pa;
-    fill_args(corr, w, nvox, box, g, const_cast<uint16_t*>(cand), const_cast<float*>(score),
-              quat, lambda, comp_out, sa, pa);
+    fill_args(corr, w, nvox, box, u0, u1, g, const_cast<uint16_t*>(cand),
+              const_cast<float*>(score), quat, lambda, comp_out, sa, pa);
     switch (n_order) {
         case 2: return launch_rotation_n<2>(sa, pa, true, false, bf16, st, cnt);
         case 4: return launch_rotation_n<4>(sa, pa, true, false, bf16, st, cnt);

@@ -10,11 +10,12 @@
 // quaternions (half sphere, sorted into regions of equal size): phi at every grid point is a
 // dot product with a precomputed row mu_alpha q_g^alpha staged in shared memory
 // and read as a broadcast.  The best point of each region competes for a short
-// list of n_cand candidates.  Each candidate is refined by two shifted power
-// steps (x <- normalise(C x^{n-1} + sigma x), sigma = (n-1) score, the SS-HOPM
-// step of Kolda & Mayo 2011, monotone for this shift) and then by Riemannian
-// Newton steps on the sphere, each accepted only if phi does not decrease
-// (otherwise the power step is taken).  The largest refined value wins.
+// list of n_cand candidates.  Every candidate takes two shifted power steps
+// (x <- normalise(C x^{n-1} + sigma x), sigma = (n-1) score, the SS-HOPM step
+// of Kolda & Mayo 2011, monotone for this shift); the kRefine best of the
+// points reached are then refined by Riemannian Newton steps on the sphere,
+// each accepted only if phi does not decrease (otherwise the power step is
+// taken).  The largest refined value wins.
 #pragma once
 #include <cuda_bf16.h>
 
@@ -27,6 +28,7 @@ namespace rot {
 constexpr int kRotThreads = 128;
 constexpr int kChunk = 128;       // grid points staged per step
 constexpr int kMaxCand = 8;
+constexpr int kRefine = 6;        // candidates refined by Newton after the power steps
 
 // correlation maps are float or bf16 (mixed precision)
 __device__ __forceinline__ float ldcorr(const float* p) { return __ldg(p); }
@@ -37,6 +39,7 @@ struct SearchArgs {
     const float* w;
     size_t nvox;            // voxels of the volume (stride of the component maps)
     VoxBox box;             // interior voxels: the units the kernels visit
+    uint32_t u0, u1;        // this launch visits units [u0, u1)
     float* score;
     uint16_t* cand;         // per interior voxel: 8 candidate grid indices
     const float* gm;        // n_grid x K4 (SIMT search)
@@ -49,6 +52,7 @@ struct PolishArgs {
     const float* w;
     size_t nvox;
     VoxBox box;
+    uint32_t u0, u1;        // this launch visits units [u0, u1)
     const float* score;
     const uint16_t* cand;
     float* quat;            // 4 x nvox interleaved (a, b, c, d) per voxel
@@ -204,11 +208,48 @@ __device__ __forceinline__ bool newton_dir(const float H[4][4], const float g[4]
     return true;
 }
 
-// Refinement of one start point: two shifted power (SS-HOPM) steps, then
-// Riemannian Newton steps; a Newton trial that lowers phi is rejected and
-// replaced by a power step from the last accepted point (power steps with
-// this shift never lower phi).  One evaluation site per iteration keeps the
-// code small.
+// g = C x^{N-1} (the gradient of phi divided by N) and lam = x . g
+template <int N>
+__device__ __forceinline__ void grad_at(const float (&C)[Geo<N>::K4], const float x[4], float g[4],
+                                        float& lam) {
+    constexpr GradTab<N> T{};
+    Monomials<N - 1> mg;
+    monomials<N - 1>(x, mg);
+    float mw[GradTab<N>::KG];
+#pragma unroll
+    for (int b = 0; b < GradTab<N>::KG; ++b) mw[b] = (float)T.mult[b] * mg.v[b];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        float acc = 0.f;
+#pragma unroll
+        for (int b = 0; b < GradTab<N>::KG; ++b) acc = fmaf(mw[b], C[T.comp[i][b]], acc);
+        g[i] = acc;
+    }
+    lam = g[0] * x[0] + g[1] * x[1] + g[2] * x[2] + g[3] * x[3];
+}
+
+// Two shifted power (SS-HOPM) steps x <- normalise(C x^{N-1} + sigma x) from
+// x (the SS-HOPM step of Kolda & Mayo 2011, monotone for this shift); lam =
+// phi at the point reached.
+template <int N>
+__device__ __forceinline__ void power_steps(const float (&C)[Geo<N>::K4], float sigma, float x[4],
+                                            float& lam) {
+    float g[4];
+#pragma unroll 1
+    for (int s = 0; s < 2; ++s) {
+        grad_at<N>(C, x, g, lam);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) x[i] = g[i] + sigma * x[i];
+        normalise4(x);
+    }
+    grad_at<N>(C, x, g, lam);
+}
+
+// Riemannian Newton steps on the sphere from x; a trial that lowers phi is
+// rejected and replaced by a power step from the last accepted point (power
+// steps with this shift never lower phi).  newton trials are evaluated; no
+// direction is formed after the last one.  One evaluation site per iteration
+// keeps the code small.
 template <int N>
 __device__ void refine(const float (&C)[Geo<N>::K4], float sigma, int newton, float x[4],
                        float& lam_out) {
@@ -216,14 +257,15 @@ __device__ void refine(const float (&C)[Geo<N>::K4], float sigma, int newton, fl
     float Ha[4][4], ga[4], la = -INFINITY;
     float xt[4] = {x[0], x[1], x[2], x[3]};
     bool trial_newton = false;
-    int ss_left = 2;
     const float eps = 1e-6f * sigma;
-    const int iters = 3 + newton;
+    const int iters = 1 + newton;
 #pragma unroll 1
     for (int it = 0; it < iters; ++it) {
         float H[4][4], g[4], lam;
         eval_at<N>(C, xt, H, g, lam);
+        const bool last = it + 1 == iters;
         if (trial_newton && lam < la - eps) {
+            if (last) break;
 #pragma unroll
             for (int i = 0; i < 4; ++i) xt[i] = ga[i] + sigma * xa[i];
             normalise4(xt);
@@ -238,15 +280,15 @@ __device__ void refine(const float (&C)[Geo<N>::K4], float sigma, int newton, fl
             for (int j = 0; j < 4; ++j) Ha[i][j] = H[i][j];
         }
         la = lam;
+        if (last) break;
         float eta[4];
-        if (ss_left == 0 && newton_dir<N>(Ha, ga, xa, la, sigma, eta)) {
+        if (newton_dir<N>(Ha, ga, xa, la, sigma, eta)) {
             const float en2 = eta[0] * eta[0] + eta[1] * eta[1] + eta[2] * eta[2] + eta[3] * eta[3];
             const float clip = en2 > 0.0625f ? 0.25f * rsqrtf(en2) : 1.f;
 #pragma unroll
             for (int i = 0; i < 4; ++i) xt[i] = xa[i] + clip * eta[i];
             trial_newton = true;
         } else {
-            if (ss_left > 0) --ss_left;
 #pragma unroll
             for (int i = 0; i < 4; ++i) xt[i] = ga[i] + sigma * xa[i];
             trial_newton = false;
@@ -272,8 +314,8 @@ __global__ void __launch_bounds__(kRotThreads) search_simt_kernel(SearchArgs a) 
     float* Mt = sm;                                   // kChunk x K4
     int* ends = reinterpret_cast<int*>(sm + kChunk * K4);
 
-    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const bool in_range = i < a.box.count();
+    const size_t i = a.u0 + (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool in_range = i < a.u1;
     const size_t v = in_range ? a.box.voxel((uint32_t)i) : 0;
     const float wv = in_range ? __ldg(a.w + v) : 0.f;
     float C[K4];
@@ -334,8 +376,8 @@ __global__ void __launch_bounds__(kRotThreads) polish_kernel(PolishArgs a) {
     const CT* corr = reinterpret_cast<const CT*>(a.corr);
     constexpr int K = Geo<N>::K;
     constexpr int K4 = Geo<N>::K4;
-    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= a.box.count()) return;
+    const size_t i = a.u0 + (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= a.u1) return;
     const size_t v = a.box.voxel((uint32_t)i);
     const float wv = __ldg(a.w + v);
     float C[K4];
@@ -355,12 +397,43 @@ __global__ void __launch_bounds__(kRotThreads) polish_kernel(PolishArgs a) {
     if (score > 0.f && (cw[0] & 0xFFFFu) != 0xFFFFu) {
         const float sigma = (float)(N - 1) * score;
         best_l = -INFINITY;
+        // phase 1: two power steps from every candidate; the kRefine best
+        // (by phi at the point reached) are kept, sorted descending
+        float kl[kRefine], kx[kRefine][4];
+#pragma unroll
+        for (int s = 0; s < kRefine; ++s) {
+            kl[s] = -INFINITY;
+#pragma unroll
+            for (int i = 0; i < 4; ++i) kx[s][i] = 0.f;
+        }
+#pragma unroll 1
         for (int k = 0; k < a.n_cand && k < kMaxCand; ++k) {
             const int gi = (int)((cw[k >> 1] >> (16 * (k & 1))) & 0xFFFFu);
             if (gi == 0xFFFF) break;
             float x[4];
 #pragma unroll
             for (int i = 0; i < 4; ++i) x[i] = __ldg(a.gq + 4 * gi + i);
+            float l;
+            power_steps<N>(C, sigma, x, l);
+#pragma unroll
+            for (int s = 0; s < kRefine; ++s) {
+                const bool up = l > kl[s];
+                const float tl = kl[s];
+                kl[s] = up ? l : kl[s];
+                l = up ? tl : l;
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const float tx = kx[s][i];
+                    kx[s][i] = up ? x[i] : kx[s][i];
+                    x[i] = up ? tx : x[i];
+                }
+            }
+        }
+        // phase 2: Newton refinement of the kept points
+#pragma unroll 1
+        for (int s = 0; s < kRefine; ++s) {
+            if (!(kl[s] > -INFINITY)) break;
+            float x[4] = {kx[s][0], kx[s][1], kx[s][2], kx[s][3]};
             float l;
             refine<N>(C, sigma, a.newton, x, l);
             if (l > best_l) {
@@ -386,7 +459,7 @@ __global__ void __launch_bounds__(kRotThreads) polish_kernel(PolishArgs a) {
 template <int N, typename CT>
 ttm_status launch_n_t(const SearchArgs& s, const PolishArgs& p, bool search_done, bool search_only,
                       cudaStream_t st, long long* cnt) {
-    const size_t units = s.box.count();
+    const size_t units = s.u1 > s.u0 ? s.u1 - s.u0 : 0;
     if (units == 0) return TTM_OK;
     const unsigned blocks = (unsigned)((units + kRotThreads - 1) / kRotThreads);
     if (!search_done) {

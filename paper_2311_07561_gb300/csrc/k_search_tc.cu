@@ -10,8 +10,11 @@
 // K components, a constant column that adds +1 to phi, zero padding to a
 // multiple of 16: 48 for order 4, 96 for order 6), D in tensor memory.
 //
-// One persistent CTA per SM; a tile is 128 consecutive voxels of the interior
-// box (thread t and t + 128 = voxel t of the tile = TMEM lane t).  The FP16
+// One persistent CTA per SM of 256 threads; a tile is 128 consecutive voxels
+// of the interior box (threads t and t + 128 = voxel t of the tile = TMEM lane
+// t; each reads 128 of a chunk's 256 columns).  (512 threads in four column
+// groups measured no faster and leave less room for the refinement kernel
+// that runs beside the search.)  The FP16
 // grid table (2048 x KP, K-major core-matrix layout without swizzle, stored
 // chunk by chunk of 256 points) is either copied into shared memory once per
 // CTA (order 4: 192 KB) or streamed chunk by chunk with bulk copies into two
@@ -33,11 +36,12 @@ namespace ttm {
 
 namespace {
 
-constexpr int kThreads = 256;    // warps w and w + 4 read the same TMEM lanes, different columns
+constexpr int kThreads = 256;    // warps w and w + 4 read the same TMEM lanes
+constexpr int kGroups = kThreads / 128;    // column groups of a chunk (one per 4 warps)
 constexpr int kG = 2048;             // grid points
 constexpr int kChunkN = 256;         // grid points per MMA
 constexpr int kChunks = kG / kChunkN;
-constexpr uint32_t kMergeBytes = 128 * 8 * 4;                // top-8 keys of warps 4..7
+constexpr uint32_t kMergeBytes = (kGroups - 1) * 128 * 8 * 4;  // top-8 keys of groups 1..
 constexpr long kWaitLimit = 1L << 24;   // try_wait polls; well beyond any MMA latency
 
 // Shapes for K tensor components: padded K, shared-memory sizes, and whether
@@ -283,7 +287,7 @@ __global__ void __launch_bounds__(kThreads, 1) search_tc_kernel(rot::SearchArgs 
     };
 
     const int lane_t = t & 127;            // TMEM lane = voxel of the tile
-    const int colhalf = t >> 7;            // warps 4..7 take columns 128..255 of a chunk
+    const int grp = t >> 7;                // column group: columns grp * 256 / kGroups ...
     long qbase = 0;                        // chunks issued by this CTA before this tile
     for (size_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x, qbase += kChunks) {
         const bool more_tiles = tile + gridDim.x < ntiles;
@@ -292,7 +296,7 @@ __global__ void __launch_bounds__(kThreads, 1) search_tc_kernel(rot::SearchArgs 
         const size_t v = in_range ? a.box.voxel((uint32_t)i) : 0;
         // components, score, normalised FP16 row of A (threads 0..127)
         float score = 0.f;
-        if (colhalf == 0) {
+        if (grp == 0) {
             float C[K];
             const float wv = in_range ? __ldg(a.w + v) : 0.f;
             float ss = 0.f;
@@ -359,9 +363,9 @@ __global__ void __launch_bounds__(kThreads, 1) search_tc_kernel(rot::SearchArgs 
             }
             asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
             const uint32_t col0 = tmem + ((uint32_t)((warp & 3) * 32) << 16) +
-                                  (uint32_t)h * kChunkN + (uint32_t)colhalf * 128;
+                                  (uint32_t)h * kChunkN + (uint32_t)grp * (kChunkN / kGroups);
 #pragma unroll 1
-            for (int p = 0; p < 2; ++p) {
+            for (int p = 0; p < kChunkN / kGroups / 64; ++p) {
                 uint32_t r[64];
                 tmem_ld64(col0 + (uint32_t)p * 64, r);
                 // 64 columns = 4 regions of 16.  phi + 1 >= 0 (|phi| <= 1 for
@@ -369,7 +373,7 @@ __global__ void __launch_bounds__(kThreads, 1) search_tc_kernel(rot::SearchArgs 
                 // low 11 bits become the code 2047 - g of the grid index g:
                 // first only the position in the region (15 - j, one LOP3 per
                 // value), the region part is added to each region's maximum
-                const int low0 = 2047 - (c * kChunkN + colhalf * 128 + p * 64);
+                const int low0 = 2047 - (c * kChunkN + grp * (kChunkN / kGroups) + p * 64);
                 int key[64];
                 pack_keys<0>(key, r, ~2047);
 #pragma unroll
@@ -388,18 +392,18 @@ __global__ void __launch_bounds__(kThreads, 1) search_tc_kernel(rot::SearchArgs 
             __syncthreads();     // this half may now be overwritten by chunk c + 2
         }
         if (!ok) break;
-        // merge the two column halves' lists
-        if (colhalf == 1) {
+        // merge the column groups' lists into group 0's
+        if (grp > 0) {
 #pragma unroll
-            for (int k = 0; k < rot::kMaxCand; ++k) merge[k * 128 + lane_t] = top[k];
+            for (int k = 0; k < rot::kMaxCand; ++k) merge[((grp - 1) * 8 + k) * 128 + lane_t] = top[k];
         }
         __syncthreads();
-        if (colhalf == 0) {
-#pragma unroll
-            {
+        if (grp == 0) {
+#pragma unroll 1
+            for (int g2 = 1; g2 < kGroups; ++g2) {
                 int other[rot::kMaxCand];
 #pragma unroll
-                for (int k = 0; k < rot::kMaxCand; ++k) other[k] = merge[k * 128 + lane_t];
+                for (int k = 0; k < rot::kMaxCand; ++k) other[k] = merge[((g2 - 1) * 8 + k) * 128 + lane_t];
                 merge8(top, other);
             }
             int ti[rot::kMaxCand];

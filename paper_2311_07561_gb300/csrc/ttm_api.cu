@@ -210,6 +210,19 @@ ttm_status prepare_template(ttm_plan_s* P, TemplateData& T, const float* d_mask)
     TTM_TRY(dev_upload(&T.d_run_tap0, tap0));
     TTM_TRY(dev_upload(&T.d_dz_run0, dz0));
     TTM_TRY(dev_upload(&T.d_taps, taps));
+    if (direct_tc_supported(K, ntap)) {
+        // tensor-core direct path: FP16 component table and per-tap offsets
+        std::vector<uint16_t> tab;
+        build_direct_tc_table(taps, ntap, K, tab, &T.tc_scale);
+        const int ntp = (int)(tab.size() / (size_t)direct_tc_columns(K));
+        std::vector<int> dxyz(ntp, 64 | (64 << 8) | (64 << 16));      // padded taps: offset 0
+        int t_i = 0;
+        for (const MaskRun& r : runs)
+            for (int dx = r.x0; dx <= r.x1; ++dx)
+                dxyz[t_i++] = (dx + 64) | ((r.dy + 64) << 8) | ((r.dz + 64) << 16);
+        TTM_TRY(dev_upload(&T.d_tc_tab, tab));
+        TTM_TRY(dev_upload(&T.d_tap_dxyz, dxyz));
+    }
     return TTM_OK;
 }
 
@@ -231,11 +244,14 @@ const float2* twiddle_table(ttm_plan_s* P, int L, ttm_status* err) {
 
 // Cost model of the two correlation paths (ns per voxel): the FFT path moves
 // ~40 bytes per component per padded voxel at ~5 TB/s, the direct path does
-// 2 K n_taps FLOP at ~30 TFLOP/s.
+// 2 K n_taps FLOP at ~30 TFLOP/s on the CUDA cores, or 2 N n_taps FLOP (N = K
+// padded to 16) at ~150 TFLOP/s effective on the tensor cores.
 double model_ratio(const ttm_plan_s* P, const ProblemData& pr, const TemplateData& T) {
     const double pad = (double)pr.fft.Xp * pr.fft.Yp * pr.fft.Zp / (double)pr.nvox();
     const double fft_ns = pad * (40.0 * P->K + 40.0) / 5000.0;
-    const double direct_ns = 2.0 * P->K * T.n_taps / 30000.0;
+    double direct_ns = 2.0 * P->K * T.n_taps / 30000.0;
+    if (P->opts.precision == TTM_PREC_MIXED && T.d_tc_tab)      // tensor cores, FP16 operands
+        direct_ns = 2.0 * direct_tc_columns(P->K) * T.n_taps / 150000.0;
     return direct_ns / fft_ns;          // > 1: the FFT path is expected to win
 }
 
@@ -347,12 +363,19 @@ void free_plan(ttm_plan_s* P) {
         cudaEventDestroy(t.stop);
     }
     for (cudaEvent_t e : P->event_pool) cudaEventDestroy(e);
+    for (cudaEvent_t e : P->ev_chunk) cudaEventDestroy(e);
+    if (P->ev_fork) cudaEventDestroy(P->ev_fork);
+    if (P->ev_join) cudaEventDestroy(P->ev_join);
+    if (P->s_hi) cudaStreamDestroy(P->s_hi);
+    if (P->s_lo) cudaStreamDestroy(P->s_lo);
     for (TemplateData& T : P->tmpl) {
         cudaFree(T.d_runs);
         cudaFree(T.d_mask);
         cudaFree(T.d_run_tap0);
         cudaFree(T.d_dz_run0);
         cudaFree(T.d_taps);
+        cudaFree(T.d_tc_tab);
+        cudaFree(T.d_tap_dxyz);
         cudaFree(T.d_spec);
     }
     for (SpecSet& sp : P->specs) {
@@ -367,6 +390,24 @@ void free_plan(ttm_plan_s* P) {
     cudaFree(P->grid.d_gtab);
     cudaFree(P->grid.d_endbits);
     delete P;
+}
+
+// Streams and events of the pipelined rotation stage (rotation_chunks > 1).
+ttm_status make_rotation_streams(ttm_plan_s* P) {
+    const int nch = P->opts.rotation_chunks > 0 ? P->opts.rotation_chunks : 8;
+    if (nch > 64) return TTM_ERR_INVALID_ARG;
+    P->rot_chunks = nch;
+    if (nch == 1) return TTM_OK;
+    int least = 0, greatest = 0;
+    TTM_CUDA_TRY(cudaDeviceGetStreamPriorityRange(&least, &greatest));
+    TTM_CUDA_TRY(cudaStreamCreateWithPriority(&P->s_hi, cudaStreamNonBlocking, greatest));
+    TTM_CUDA_TRY(cudaStreamCreateWithPriority(&P->s_lo, cudaStreamNonBlocking, least));
+    TTM_CUDA_TRY(cudaEventCreateWithFlags(&P->ev_fork, cudaEventDisableTiming));
+    TTM_CUDA_TRY(cudaEventCreateWithFlags(&P->ev_join, cudaEventDisableTiming));
+    P->ev_chunk.assign(nch, nullptr);
+    for (int c = 0; c < nch; ++c)
+        TTM_CUDA_TRY(cudaEventCreateWithFlags(&P->ev_chunk[c], cudaEventDisableTiming));
+    return TTM_OK;
 }
 
 // workspace layout: [0, 256) header (moments, counters); [256, ...) scratch
@@ -442,8 +483,8 @@ ttm_status stats_problem(ttm_plan_s* plan, const ProblemData& pr, const float* v
                                                   &plan->launches));
             TTM_TRY(launch_fft_spectrum_inverse_z(F2, mspec, 1, pr.fft, prod + nspec, st,
                                                   &plan->launches));
-            TTM_TRY(launch_fft_inverse_yx(prod, 2, pr.X, pr.Y, pr.Z, pr.fft, sums, st,
-                                          &plan->launches));
+            TTM_TRY(launch_fft_inverse_yx(prod, 2, pr.X, pr.Y, pr.Z, pr.fft, sums,
+                                          (int*)((char*)d_workspace + 32), st, &plan->launches));
             return launch_stats_from_sums(sums, sums + pr.nvox(), w, pr.X, pr.Y, pr.Z, T.desc.s,
                                           T.desc.mask_sum, d_mom, st, &plan->launches);
         });
@@ -479,24 +520,43 @@ ttm_status corr_problem(ttm_plan_s* plan, const ProblemData& pr, const float* vo
                                                                 &plan->launches);
             }));
             TTM_TRY(timed(plan, KC_FFT_INVERSE, st, [&] {
+                int* d_status = (int*)((char*)d_workspace + 32);
                 return pr.mixed ? launch_fft_inverse_yx_bf16(
                                       prod, g, pr.X, pr.Y, pr.Z, pr.fft,
-                                      (char*)corr + (size_t)k0 * pr.nvox() * 2, st, &plan->launches)
+                                      (char*)corr + (size_t)k0 * pr.nvox() * 2, d_status, st,
+                                      &plan->launches)
                                 : launch_fft_inverse_yx((float2*)prod, g, pr.X, pr.Y, pr.Z, pr.fft,
-                                                        corr + (size_t)k0 * pr.nvox(), st,
-                                                        &plan->launches);
+                                                        corr + (size_t)k0 * pr.nvox(), d_status,
+                                                        st, &plan->launches);
             }));
         }
         return TTM_OK;
     }
     const TemplateData& T = plan->tmpl[pr.tmpl];
+    if (pr.tc_direct) {
+        // the volume's moments (mean and spread condition the FP16 operand)
+        double* d_mom = (double*)((char*)d_workspace + 64);
+        TTM_CUDA_TRY(cudaMemsetAsync(d_mom, 0, 2 * sizeof(double), st));
+        TTM_TRY(timed(plan, KC_MOMENTS, st, [&] {
+            return launch_volume_moments(vol, pr.nvox(), d_mom, st, &plan->launches);
+        }));
+        return timed(plan, KC_DIRECT_CORR, st, [&] {
+            return launch_direct_tc(vol, pr.X, pr.Y, pr.Z, T, plan->K, d_mom, corr,
+                                    (int*)((char*)d_workspace + 32), st, &plan->launches);
+        });
+    }
     return timed(plan, KC_DIRECT_CORR, st, [&] {
         return launch_direct_corr(vol, pr.X, pr.Y, pr.Z, T, plan->K, corr, st, &plan->launches);
     });
 }
 
 // Score, rotation search and refinement of one problem from its correlation
-// maps (Sec. 3.3-3.4); exterior voxels get the exterior values.
+// maps (Sec. 3.3-3.4); exterior voxels get the exterior values.  With more
+// than one chunk the interior is split into rot_chunks ranges: the searches
+// run in order on the plan's high-priority stream, and the refinement of
+// chunk i starts on the low-priority stream once its search is done, so the
+// tensor-core search (integer-ALU bound) and the refinement (FMA bound) share
+// the SMs.  Both streams fork from and join back into st (capturable).
 ttm_status rotation_problem(ttm_plan_s* plan, const ProblemData& pr, const float* w, float* score,
                             float* quat, float* lam, float* comp_out, void* d_workspace,
                             cudaStream_t st) {
@@ -505,22 +565,63 @@ ttm_status rotation_problem(ttm_plan_s* plan, const ProblemData& pr, const float
     int* d_status = (int*)((char*)d_workspace + 32);
     const TemplateData& T = plan->tmpl[pr.tmpl];
     const VoxBox box = interior_box(pr.X, pr.Y, pr.Z, T.desc.s);
+    const size_t units = box.count();
+    if (units > 0xFFFFFFFFull) return TTM_ERR_UNSUPPORTED;
     TTM_TRY(timed(plan, KC_EXTERIOR, st, [&] {
         return launch_exterior_fill(pr.Z, box, plan->K, score, quat, lam, comp_out, st,
                                     &plan->launches);
     }));
-    TTM_TRY(timed(plan, KC_ROTATION, st, [&] {
-        return launch_rotation_search(plan->n_order, corr, pr.mixed, w, pr.nvox(), box,
-                                      plan->grid, cand, d_status, score, st, &plan->launches);
-    }));
-    return timed(plan, KC_POLISH, st, [&] {
-        return launch_rotation_polish(plan->n_order, corr, pr.mixed, w, pr.nvox(), box,
-                                      plan->grid, cand, score, quat, lam, comp_out, st,
-                                      &plan->launches);
-    });
+    int nch = plan->rot_chunks;
+    if ((size_t)nch * 128 * 152 > units) nch = 1;        // too small to split
+    if (nch <= 1 || !plan->s_hi) {
+        TTM_TRY(timed(plan, KC_ROTATION, st, [&] {
+            return launch_rotation_search(plan->n_order, corr, pr.mixed, w, pr.nvox(), box, 0,
+                                          (uint32_t)units, plan->grid, cand, d_status, score, st,
+                                          &plan->launches);
+        }));
+        return timed(plan, KC_POLISH, st, [&] {
+            return launch_rotation_polish(plan->n_order, corr, pr.mixed, w, pr.nvox(), box, 0,
+                                          (uint32_t)units, plan->grid, cand, score, quat, lam,
+                                          comp_out, st, &plan->launches);
+        });
+    }
+    // chunk bounds in whole 128-voxel tiles
+    const size_t tiles = (units + 127) / 128;
+    auto bound = [&](int c) {
+        return (uint32_t)std::min(units, (tiles * (size_t)c / (size_t)nch) * 128);
+    };
+    TTM_CUDA_TRY(cudaEventRecord(plan->ev_fork, st));
+    TTM_CUDA_TRY(cudaStreamWaitEvent(plan->s_hi, plan->ev_fork, 0));
+    TTM_CUDA_TRY(cudaStreamWaitEvent(plan->s_lo, plan->ev_fork, 0));
+    for (int c = 0; c < nch; ++c) {
+        const uint32_t u0 = bound(c), u1 = c + 1 == nch ? (uint32_t)units : bound(c + 1);
+        TTM_TRY(timed(plan, KC_ROTATION, plan->s_hi, [&] {
+            return launch_rotation_search(plan->n_order, corr, pr.mixed, w, pr.nvox(), box, u0,
+                                          u1, plan->grid, cand, d_status, score, plan->s_hi,
+                                          &plan->launches);
+        }));
+        TTM_CUDA_TRY(cudaEventRecord(plan->ev_chunk[c], plan->s_hi));
+        TTM_CUDA_TRY(cudaStreamWaitEvent(plan->s_lo, plan->ev_chunk[c], 0));
+        TTM_TRY(timed(plan, KC_POLISH, plan->s_lo, [&] {
+            return launch_rotation_polish(plan->n_order, corr, pr.mixed, w, pr.nvox(), box, u0,
+                                          u1, plan->grid, cand, score, quat, lam, comp_out,
+                                          plan->s_lo, &plan->launches);
+        }));
+    }
+    TTM_CUDA_TRY(cudaEventRecord(plan->ev_join, plan->s_lo));
+    TTM_CUDA_TRY(cudaStreamWaitEvent(st, plan->ev_join, 0));
+    return TTM_OK;
 }
 
 // ---- autotuner (TTM_PATH_TUNE) ----
+
+// A problem moved to the direct path: tensor cores in mixed precision where
+// the template has their table, CUDA cores otherwise.
+void to_direct(const ttm_plan_s* P, ProblemData& pr) {
+    pr.path = TTM_PATH_DIRECT;
+    pr.mixed = false;
+    pr.tc_direct = P->opts.precision == TTM_PREC_MIXED && P->tmpl[pr.tmpl].d_tc_tab != nullptr;
+}
 
 // Device time of local statistics + K correlations of one problem: one
 // warm-up run, then the best of two timed runs (ms), or -1 on failure.
@@ -564,16 +665,21 @@ ttm_status tune_paths(ttm_plan_s* P, cudaStream_t st) {
             if (o.tune_ms[0] < 0.0 && o.tune_ms[1] < 0.0) continue;     // not timed
             pr.tune_ms[0] = o.tune_ms[0];
             pr.tune_ms[1] = o.tune_ms[1];
-            if (o.path == TTM_PATH_DIRECT) { pr.path = TTM_PATH_DIRECT; pr.mixed = false; }
+            if (o.path == TTM_PATH_DIRECT) {
+                pr.path = TTM_PATH_DIRECT;
+                pr.mixed = false;
+                pr.tc_direct = o.tc_direct;
+            }
             shared = true;
         }
         if (shared) continue;
         const double ratio = model_ratio(P, pr, P->tmpl[pr.tmpl]);
         if (ratio > kTuneRange) continue;                          // FFT, clearly
-        if (ratio < 1.0 / kTuneRange) { pr.path = TTM_PATH_DIRECT; pr.mixed = false; continue; }
+        if (ratio < 1.0 / kTuneRange) { to_direct(P, pr); continue; }
         ProblemData dpr = pr;
         dpr.path = TTM_PATH_DIRECT;
         dpr.mixed = false;
+        dpr.tc_direct = P->opts.precision == TTM_PREC_MIXED && P->tmpl[pr.tmpl].d_tc_tab != nullptr;
         const size_t nv = pr.nvox();
         const size_t wsb = kHeader + std::max(scratch_bytes(P, pr), scratch_bytes(P, dpr));
         float* vol = nullptr;
@@ -585,7 +691,7 @@ ttm_status tune_paths(ttm_plan_s* P, cudaStream_t st) {
             // not enough memory to tune: keep the planner's estimate
             cudaGetLastError();
             cudaFree(vol); cudaFree(w); cudaFree(ws);
-            if (!prefer_fft(P, pr, P->tmpl[pr.tmpl])) { pr.path = TTM_PATH_DIRECT; pr.mixed = false; }
+            if (!prefer_fft(P, pr, P->tmpl[pr.tmpl])) to_direct(P, pr);
             continue;
         }
         ttm_status s = launch_fill_random(vol, nv, 0x5eedu + (uint32_t)p, st, &P->launches);
@@ -600,6 +706,7 @@ ttm_status tune_paths(ttm_plan_s* P, cudaStream_t st) {
         if (pr.tune_ms[1] < 0.0 || (pr.tune_ms[0] >= 0.0 && pr.tune_ms[0] < pr.tune_ms[1])) {
             pr.path = TTM_PATH_DIRECT;
             pr.mixed = false;
+            pr.tc_direct = dpr.tc_direct;
         }
     }
     for (size_t i = 0; i < P->specs.size(); ++i) {
@@ -744,6 +851,7 @@ ttm_status ttm_plan(ttm_plan_t* out, int n_problems, const int* vol_dims, const 
         s_ = prepare_template(P, P->tmpl[k], d_masks[k]);
     }
     if (s_ == TTM_OK) s_ = build_grid(P);
+    if (s_ == TTM_OK) s_ = make_rotation_streams(P);
     if (s_ != TTM_OK) { free_plan(P); return s_; }
     P->prob.resize(n_problems);
     size_t ws = 0;
@@ -766,6 +874,8 @@ ttm_status ttm_plan(ttm_plan_t* out, int n_problems, const int* vol_dims, const 
         pr.mixed = path == TTM_PATH_FFT && P->opts.precision == TTM_PREC_MIXED &&
                    fft_template_length(pr.fft.Xp) && fft_template_length(pr.fft.Yp) &&
                    fft_template_length(pr.fft.Zp);
+        pr.tc_direct = path == TTM_PATH_DIRECT && P->opts.precision == TTM_PREC_MIXED &&
+                       T.d_tc_tab != nullptr;
         if (P->opts.precision != TTM_PREC_FP32 && P->opts.precision != TTM_PREC_MIXED) {
             free_plan(P);
             return TTM_ERR_INVALID_ARG;
@@ -803,6 +913,13 @@ ttm_status ttm_plan_problem_tuning(ttm_plan_t plan, int problem, double* ms) {
         return TTM_ERR_INVALID_ARG;
     ms[0] = plan->prob[problem].tune_ms[0];
     ms[1] = plan->prob[problem].tune_ms[1];
+    return TTM_OK;
+}
+
+ttm_status ttm_plan_problem_tensor_direct(ttm_plan_t plan, int problem, int* on) {
+    if (!plan || !on || problem < 0 || problem >= (int)plan->prob.size())
+        return TTM_ERR_INVALID_ARG;
+    *on = plan->prob[problem].tc_direct ? 1 : 0;
     return TTM_OK;
 }
 
@@ -987,8 +1104,8 @@ ttm_status ttm_classical_ncc(ttm_plan_t plan, int problem, const float* d_templa
             return launch_fft_spectrum_inverse_z(spec, tspec, nb, pr.fft, prod, st, &plan->launches);
         }));
         TTM_TRY(timed(plan, KC_FFT_INVERSE, st, [&] {
-            return launch_fft_inverse_yx(prod, nb, pr.X, pr.Y, pr.Z, pr.fft, maps, st,
-                                         &plan->launches);
+            return launch_fft_inverse_yx(prod, nb, pr.X, pr.Y, pr.Z, pr.fft, maps,
+                                         (int*)(ws + 32), st, &plan->launches);
         }));
         TTM_TRY(timed(plan, KC_PEAKS, st, [&] {
             return launch_best_rotation(maps, nb, j0, d_w, pr.nvox(), d_best, d_best_index, j0 == 0,

@@ -124,6 +124,28 @@ struct HessTab {
     }
 };
 
+// Table for the vector g = A x^{N-1} of a symmetric tensor A of order N
+// (Sec. 3.1): g_i = sum_gamma mult(gamma) A_{sorted(i, gamma)} x^gamma, the sum
+// over the components gamma of S^{N-1}(R^4) with their multinomial weights.
+template <int N>
+struct GradTab {
+    static constexpr int KG = n_comp(N - 1);
+    int comp[4][KG > 0 ? KG : 1];
+    int mult[KG > 0 ? KG : 1];
+
+    __host__ __device__ constexpr GradTab() : comp{}, mult{} {
+        constexpr Sym<N> A{};
+        constexpr Sym<N - 1> G{};
+        for (int i = 0; i < 4; ++i)
+            for (int g = 0; g < KG; ++g) {
+                int ex[4] = {G.e[g][0], G.e[g][1], G.e[g][2], G.e[g][3]};
+                ex[i] += 1;
+                comp[i][g] = A.find(ex[0], ex[1], ex[2], ex[3]);
+            }
+        for (int g = 0; g < KG; ++g) mult[g] = G.mu[g];
+    }
+};
+
 // Monomials x^beta for every component beta of S^M(R^4), computed from the
 // degree-(M-1) monomials by one multiplication each.
 template <int M>

@@ -25,6 +25,11 @@ struct TemplateData {
     int* d_run_tap0 = nullptr;          // first tap index of every run
     int* d_dz_run0 = nullptr;           // first run of every dz plane (dz_max-dz_min+2)
     float* d_taps = nullptr;            // n_taps x K component values, tap-major
+    // tensor-core direct path (small masks): FP16 table of T / max|T| in the
+    // kernel's layout, per-tap offsets (dx, dy, dz) packed, and max|T|
+    uint16_t* d_tc_tab = nullptr;
+    int* d_tap_dxyz = nullptr;
+    float tc_scale = 1.f;
     // FFT path (allocated when some problem with this template uses it)
     void* d_spec = nullptr;             // K template spectra per FFT shape
     int spec_shape[3] = {0, 0, 0};
@@ -45,6 +50,7 @@ struct ProblemData {
     int path = TTM_PATH_DIRECT;
     FftShape fft;
     bool mixed = false;                // bf16 spectra, products and correlation maps
+    bool tc_direct = false;            // direct path on the tensor cores (FP16 operands)
     int spec_index = -1;               // template spectra set used (FFT path)
     double tune_ms[2] = {-1.0, -1.0};  // autotuner: direct, FFT (ms), -1 = not timed
     size_t nvox() const { return (size_t)X * Y * Z; }
@@ -124,6 +130,11 @@ struct ttm_plan_s {
     bool timing = false;
     std::vector<ttm::TimedLaunch> timed;   // pending event pairs
     std::vector<cudaEvent_t> event_pool;
+    // rotation stage pipelining: search on hi, refinement on lo, chunk by chunk
+    int rot_chunks = 1;
+    cudaStream_t s_hi = nullptr, s_lo = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    std::vector<cudaEvent_t> ev_chunk;
 };
 
 namespace ttm {
@@ -147,19 +158,30 @@ ttm_status launch_local_stats(const float* f, int X, int Y, int Z, const Templat
 ttm_status launch_direct_corr(const float* f, int X, int Y, int Z, const TemplateData& T,
                               int K, float* corr, cudaStream_t st, long long* cnt);
 
+// direct correlation as an implicit GEMM on the tensor cores (interior voxels)
+int direct_tc_columns(int K);
+size_t direct_tc_smem(int K, int n_taps);
+bool direct_tc_supported(int K, int n_taps);
+void build_direct_tc_table(const std::vector<float>& taps, int n_taps, int K,
+                           std::vector<uint16_t>& out, float* t_scale);
+ttm_status launch_direct_tc(const float* f, int X, int Y, int Z, const TemplateData& T, int K,
+                            const double* d_moments, float* corr, int* status, cudaStream_t st,
+                            long long* cnt);
+
 // per-voxel score + candidate search (tensor cores for order 4 with the
 // default 2048-point grid, CUDA cores otherwise) and refinement, over the
 // interior box only; launch_exterior_fill writes the exterior values (score 0,
 // q = (1, 0, 0, 0), lambda 0, C 0) of the voxels outside it.  cand holds one
 // 16-byte record per interior voxel.
+// Both visit the interior units [u0, u1) of box (unit i = voxel box.voxel(i)).
 ttm_status launch_rotation_search(int n_order, const void* corr, bool bf16, const float* w,
-                                  size_t nvox, const VoxBox& box, const RotGrid& g,
-                                  uint16_t* cand, int* status, float* score, cudaStream_t st,
-                                  long long* cnt);
+                                  size_t nvox, const VoxBox& box, uint32_t u0, uint32_t u1,
+                                  const RotGrid& g, uint16_t* cand, int* status, float* score,
+                                  cudaStream_t st, long long* cnt);
 ttm_status launch_rotation_polish(int n_order, const void* corr, bool bf16, const float* w,
-                                  size_t nvox, const VoxBox& box, const RotGrid& g,
-                                  const uint16_t* cand, const float* score, float* quat,
-                                  float* lambda, float* comp_out, cudaStream_t st,
+                                  size_t nvox, const VoxBox& box, uint32_t u0, uint32_t u1,
+                                  const RotGrid& g, const uint16_t* cand, const float* score,
+                                  float* quat, float* lambda, float* comp_out, cudaStream_t st,
                                   long long* cnt);
 ttm_status launch_exterior_fill(int Z, const VoxBox& box, int K, float* score, float* quat,
                                 float* lambda, float* comp_out, cudaStream_t st, long long* cnt);
@@ -190,8 +212,9 @@ bool fft_template_length(int L);
 ttm_status launch_fft_spectrum_inverse_z_bf16(const float2* spec, const void* tspec, int K,
                                               const FftShape& S, void* prod, cudaStream_t st,
                                               long long* cnt);
+// status: device word that records TTM_ERR_TIMEOUT if a bounded copy wait expires
 ttm_status launch_fft_inverse_yx_bf16(void* prod, int K, int X, int Y, int Z, const FftShape& S,
-                                      void* corr, cudaStream_t st, long long* cnt);
+                                      void* corr, int* status, cudaStream_t st, long long* cnt);
 ttm_status launch_spectra_to_bf16(const float2* a, void* b, size_t n, cudaStream_t st, long long* cnt);
 ttm_status launch_stats_from_sums(const float* s1, const float* s2, float* w, int X, int Y, int Z,
                                   int s, double mask_sum, const double* moments, cudaStream_t st,
@@ -200,7 +223,7 @@ ttm_status launch_fft_spectrum_inverse_z(const float2* spec, const float2* tspec
                                          const FftShape& S, float2* prod, cudaStream_t st,
                                          long long* cnt);
 ttm_status launch_fft_inverse_yx(float2* prod, int K, int X, int Y, int Z, const FftShape& S,
-                                 float* corr, cudaStream_t st, long long* cnt);
+                                 float* corr, int* status, cudaStream_t st, long long* cnt);
 ttm_status launch_template_spectra(const float* comp, int K, int s, const FftShape& S,
                                    float* pad, float2* tspec, cudaStream_t st, long long* cnt);
 

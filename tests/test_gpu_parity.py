@@ -365,3 +365,57 @@ def test_mixed_precision_within_bf16_tolerance(ttm, c1_oracle):
     dl = np.abs(res["lam"][pts[:, 2], pts[:, 1], pts[:, 0]] - lam_o).max()
     assert dl <= 5e-3, dl
     print(f"mixed precision max errors: C {dC:.2e} score {dS:.2e} lambda {dl:.2e}")
+
+
+def test_pipelined_rotation_chunks_are_bit_identical(ttm):
+    """The search/refinement pipeline over interior chunks (two streams, also
+    inside a CUDA graph) gives the same maps as one search + one refinement."""
+    import torch
+    wl = synth.make_workload((96, 96, 96), 9, 3, 6, 1.0, 4, 200, radius=4, seeds=(5, 6, 7))
+    comp, desc = ttm.build_template(wl.template, wl.mask, 4, wl.quadrature)
+    vol = _cuda(wl.volume)
+    outs = []
+    for chunks in (1, 3, 4):
+        o_ = _opts(ttm, "fft")
+        o_.rotation_chunks = chunks
+        m = ttm.Matcher([(comp, desc, wl.mask)], [((96, 96, 96), 0)], opts=o_)
+        m.run([vol])
+        torch.cuda.synchronize()
+        outs.append((m.score[0].clone(), m.quat[0].clone(), m.lam[0].clone()))
+        if chunks == 4:
+            g = m.capture([vol])
+            m.score[0].fill_(-1.0)
+            m.lam[0].fill_(-1.0)
+            g.replay()
+            torch.cuda.synchronize()
+            outs.append((m.score[0].clone(), m.quat[0].clone(), m.lam[0].clone()))
+        assert ttm.ttm_plan_device_status(m.plan, m.ws) == 0
+        m.close()
+    for s, q, l in outs[1:]:
+        assert torch.equal(s, outs[0][0]) and torch.equal(q, outs[0][1])
+        assert torch.equal(l, outs[0][2])
+
+
+@pytest.mark.parametrize("n,shape,s,r", [(4, (64, 64, 64), 15, 7), (6, (30, 28, 26), 9, 4)])
+def test_tensor_core_direct_path(ttm, n, shape, s, r):
+    """Direct correlation as an implicit GEMM on the tensor cores (FP16
+    operands, FP32 accumulation): components, score and lambda within the
+    5e-3 gate of the FP64 oracle (measured errors are printed)."""
+    wl = synth.make_workload(shape, s, 5, 3, 1.0, n, 300, radius=r, seeds=(8, 9, 10))
+    T = o.tensor_template(wl.template, wl.mask, wl.quadrature.astype(np.float64), wl.weights, n)
+    comp, desc = ttm.build_template(wl.template, wl.mask, n, wl.quadrature)
+    o_ = _opts(ttm, "direct")
+    o_.precision = ttm.TTM_PREC_MIXED
+    res = _run(ttm, wl, comp, desc, opts=o_)
+    assert ttm.ttm_plan_problem_tensor_direct(res["matcher"].plan, 0)
+    w_o, C_o = o.ttm_components(wl.volume, T, wl.mask)
+    dC = np.abs(res["comp"] - C_o).max()
+    dS = np.abs(res["score"] - o.frobenius_score(C_o, n)).max()
+    assert dC <= 5e-3 and dS <= 5e-3, (dC, dS)
+    pts = np.argwhere(w_o > 0)[::41][:150][:, ::-1]
+    Cp = C_o[:, pts[:, 2], pts[:, 1], pts[:, 0]].T
+    lam_o, _ = o.dominant_z_eigenpair(Cp, n)
+    dl = np.abs(res["lam"][pts[:, 2], pts[:, 1], pts[:, 0]] - lam_o).max()
+    assert dl <= 5e-3, dl
+    print(f"tensor-core direct, order {n}: max errors C {dC:.2e} score {dS:.2e} lambda {dl:.2e}")
+    res["matcher"].close()
