@@ -222,6 +222,7 @@ __global__ void __launch_bounds__(kThreads, 1) search_tc_kernel(rot::SearchArgs 
     extern __shared__ __align__(1024) unsigned char sm[];
     __shared__ __align__(8) uint64_t bars[2];     // MMA completion, one per TMEM half
     __shared__ __align__(8) uint64_t lbars[2];    // grid-chunk copies (streamed table)
+    __shared__ __align__(8) uint64_t ebars[2];    // TMEM half read by every warp (count: warps)
     __shared__ uint32_t tmem_base_s;
     constexpr Sym<N> S{};
     const int t = threadIdx.x;
@@ -243,6 +244,8 @@ __global__ void __launch_bounds__(kThreads, 1) search_tc_kernel(rot::SearchArgs 
         for (int b = 0; b < 2; ++b) {
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&bars[b])) : "memory");
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&lbars[b])) : "memory");
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(&ebars[b])),
+                         "n"(kThreads / 32) : "memory");
         }
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
@@ -256,6 +259,10 @@ __global__ void __launch_bounds__(kThreads, 1) search_tc_kernel(rot::SearchArgs 
     const uint32_t lbar[2] = {smem_u32(&lbars[0]), smem_u32(&lbars[1])};
     uint32_t phase[2] = {0u, 0u};
     uint32_t lphase[2] = {0u, 0u};   // thread 0: phases of the copy barriers
+    const uint32_t ebar[2] = {smem_u32(&ebars[0]), smem_u32(&ebars[1])};
+    uint32_t ephase[2] = {0u, 0u};   // thread 0: phases of the TMEM-half barriers
+    int half_used[2] = {0, 0};       // thread 0: an epilogue of this half is still to be waited for
+    int mma_pending[2] = {0, 0};     // thread 0: MMAs committed to bars[h] and not yet seen done
     int loads_pending[2] = {0, 0};   // thread 0: copies issued and not yet waited on
     bool ok = true;
 
@@ -271,8 +278,15 @@ __global__ void __launch_bounds__(kThreads, 1) search_tc_kernel(rot::SearchArgs 
             loads_pending[q] = 1;
         }
     }
-    // thread 0: wait for the copy of chunk q (streamed table) and issue its MMAs
+    // thread 0: wait until every warp has read the TMEM half (its previous
+    // chunk), wait for the copy of chunk q (streamed table), issue the MMAs
     auto issue = [&](uint32_t tmem_d, int chunk, long q, uint32_t bar) {
+        const int hh = chunk & 1;
+        if (half_used[hh]) {
+            if (!mbar_wait(ebar[hh], ephase[hh])) return;     // no MMA: the MMA wait expires
+            ephase[hh] ^= 1u;
+            half_used[hh] = 0;
+        }
         uint32_t b_chunk;
         if constexpr (kStream) {
             const int buf = (int)(q & 1);
@@ -284,6 +298,8 @@ __global__ void __launch_bounds__(kThreads, 1) search_tc_kernel(rot::SearchArgs 
             b_chunk = b_base + (uint32_t)chunk * Sh::ChunkBytes;
         }
         issue_chunk<KP>(tmem_d, a_base, b_chunk, bar);
+        half_used[hh] = 1;
+        mma_pending[hh] = 1;
     };
 
     const int lane_t = t & 127;            // TMEM lane = voxel of the tile
@@ -342,16 +358,11 @@ __global__ void __launch_bounds__(kThreads, 1) search_tc_kernel(rot::SearchArgs 
             if (c + 1 < kChunks && t == 0)
                 issue(tmem + (uint32_t)((c + 1) & 1) * kChunkN, c + 1, q + 1,
                       ((c + 1) & 1) ? bar1 : bar0);
-            bool got = mbar_wait(h ? bar1 : bar0, phase[h]);
+            // no block barrier per chunk: warps move on independently; the
+            // TMEM-half barriers tell thread 0 when a half may be overwritten
+            if (!mbar_wait(h ? bar1 : bar0, phase[h])) { ok = false; break; }
             phase[h] ^= 1u;
-            if (!__syncthreads_and(got)) {
-                ok = false;
-                if (t == 0) atomicExch(status, TTM_ERR_TIMEOUT);
-                // let any MMA still in flight finish before TMEM is released
-                mbar_wait(h ? bar1 : bar0, phase[h] ^ 1u);
-                if (c + 1 < kChunks) mbar_wait(h ? bar0 : bar1, phase[h ^ 1]);
-                break;
-            }
+            if (t == 0) mma_pending[h] = 0;
             // the MMAs of chunk q are done: its buffer takes chunk q + 2
             if (kStream && t == 0 && (c + 2 < kChunks || more_tiles)) {
                 const int buf = (int)(q & 1);
@@ -388,10 +399,22 @@ __global__ void __launch_bounds__(kThreads, 1) search_tc_kernel(rot::SearchArgs 
                 cx(nk[0], nk[1]); cx(nk[2], nk[3]); cx(nk[0], nk[2]); cx(nk[1], nk[3]); cx(nk[1], nk[2]);
                 merge4(top, nk);
             }
+            // this warp has read half h: chunk c + 2 may overwrite it
             asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
-            __syncthreads();     // this half may now be overwritten by chunk c + 2
+            __syncwarp();
+            if ((t & 31) == 0)
+                asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(ebar[h]) : "memory");
         }
-        if (!ok) break;
+        if (!__syncthreads_and(ok)) {
+            ok = false;
+            if (t == 0) {
+                atomicExch(status, TTM_ERR_TIMEOUT);
+                // MMAs still in flight finish before the tensor memory is released
+                for (int hh = 0; hh < 2; ++hh)
+                    if (mma_pending[hh]) mbar_wait(hh ? bar1 : bar0, phase[hh]);
+            }
+            break;
+        }
         // merge the column groups' lists into group 0's
         if (grp > 0) {
 #pragma unroll
