@@ -155,3 +155,60 @@ class Matcher:
             self.close()
         except Exception:
             pass
+
+
+class HostPipeline:
+    """End-to-end matching of a stream of host volumes with the copies hidden.
+
+    ``depth`` independent matchers (each its own plan, workspace and output
+    maps) take consecutive steps on their own CUDA streams: while step k's
+    maps travel to the host, step k+1's volume is copied in and matched.  Each
+    step still copies its inputs from pinned host memory and reads its score,
+    rotation and lambda maps back into the pinned host buffers given for it.
+    Memory: ``depth`` plans and workspaces (template spectra, K correlation
+    maps); use depth 1 where one set barely fits.
+
+    templates, problems, opts: as for :class:`Matcher`.
+    """
+
+    def __init__(self, templates, problems, opts=None, depth: int = 2):
+        torch = _torch()
+        if depth < 1:
+            raise ValueError("depth must be at least 1")
+        self.matchers = [Matcher(templates, problems, opts=opts) for _ in range(depth)]
+        self.streams = [torch.cuda.Stream() for _ in range(depth)]
+        dev = torch.device("cuda")
+        self.vols = [[torch.empty((Z, Y, X), dtype=torch.float32, device=dev)
+                      for (X, Y, Z), _ in m.problems] for m in self.matchers]
+        self._next = 0
+
+    def submit(self, host_vols: Sequence, host_out: Sequence) -> None:
+        """Queue one step: host_vols[p] (pinned float32 (Z, Y, X)) in, and
+        (score, quat, lambda) of every problem out into host_out[p] (pinned
+        tensors of the map shapes).  Returns at once; the step is ordered after
+        everything queued on the current stream before the call."""
+        torch = _torch()
+        i = self._next % len(self.matchers)
+        self._next += 1
+        m, st, dv = self.matchers[i], self.streams[i], self.vols[i]
+        st.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(st):
+            for d, h in zip(dv, host_vols):
+                d.copy_(h, non_blocking=True)
+            m.run(dv)
+            for p, (so, qo, lo) in enumerate(host_out):
+                so.copy_(m.score[p], non_blocking=True)
+                qo.copy_(m.quat[p], non_blocking=True)
+                if lo is not None and m.lam[p] is not None:
+                    lo.copy_(m.lam[p], non_blocking=True)
+
+    def join(self) -> None:
+        """Make the current stream wait for every queued step."""
+        torch = _torch()
+        cur = torch.cuda.current_stream()
+        for st in self.streams:
+            cur.wait_stream(st)
+
+    def close(self) -> None:
+        for m in self.matchers:
+            m.close()

@@ -419,3 +419,33 @@ def test_tensor_core_direct_path(ttm, n, shape, s, r):
     assert dl <= 5e-3, dl
     print(f"tensor-core direct, order {n}: max errors C {dC:.2e} score {dS:.2e} lambda {dl:.2e}")
     res["matcher"].close()
+
+
+def test_host_pipeline_matches_matcher(ttm):
+    """HostPipeline (steps overlapped on two streams, host copies in and out)
+    returns exactly the maps Matcher.run computes for each volume."""
+    import torch
+    wls = [synth.make_workload((40, 44, 48), 9, 3, 3, 1.0, 4, 200, radius=4, seeds=(s, s + 1, s + 2))
+           for s in (31, 41)]
+    comp, desc = ttm.build_template(wls[0].template, wls[0].mask, 4, wls[0].quadrature)
+    prob = [((48, 44, 40), 0)]
+    ref = []
+    m = ttm.Matcher([(comp, desc, wls[0].mask)], prob, opts=_opts(ttm, "fft"))
+    for wl in wls:
+        m.run([_cuda(wl.volume)])
+        torch.cuda.synchronize()
+        ref.append((m.score[0].cpu(), m.quat[0].cpu(), m.lam[0].cpu()))
+    m.close()
+    pipe = ttm.HostPipeline([(comp, desc, wls[0].mask)], prob, opts=_opts(ttm, "fft"), depth=2)
+    order = [0, 1, 0, 1]
+    pins = [torch.from_numpy(wl.volume).pin_memory() for wl in wls]
+    outs = [[(torch.empty((40, 44, 48)).pin_memory(), torch.empty((40, 44, 48, 4)).pin_memory(),
+              torch.empty((40, 44, 48)).pin_memory())] for _ in order]
+    for k, v in enumerate(order):
+        pipe.submit([pins[v]], outs[k])
+    pipe.join()
+    torch.cuda.synchronize()
+    for k, v in enumerate(order):
+        s, q, l = outs[k][0]
+        assert torch.equal(s, ref[v][0]) and torch.equal(q, ref[v][1]) and torch.equal(l, ref[v][2])
+    pipe.close()
