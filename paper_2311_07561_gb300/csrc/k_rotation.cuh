@@ -432,8 +432,17 @@ __global__ void __launch_bounds__(kRotThreads) polish_kernel(PolishArgs a) {
         // phase 2: Newton refinement of the kept points
 #pragma unroll 1
         for (int s = 0; s < kRefine; ++s) {
-            if (!(kl[s] > -INFINITY)) break;
-            float x[4] = {kx[s][0], kx[s][1], kx[s][2], kx[s][3]};
+            // the kept point s, picked with compile-time indices (registers,
+            // no local memory)
+            float ls = -INFINITY, x[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+            for (int j = 0; j < kRefine; ++j) {
+                const bool pick = j == s;
+                ls = pick ? kl[j] : ls;
+#pragma unroll
+                for (int i = 0; i < 4; ++i) x[i] = pick ? kx[j][i] : x[i];
+            }
+            if (!(ls > -INFINITY)) break;
             float l;
             refine<N>(C, sigma, a.newton, x, l);
             if (l > best_l) {

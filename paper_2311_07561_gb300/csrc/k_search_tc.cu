@@ -256,14 +256,16 @@ __global__ void __launch_bounds__(kThreads, 1) search_tc_kernel(rot::SearchArgs 
     const uint32_t tmem = tmem_base_s;
     const uint32_t a_base = smem_u32(As), b_base = smem_u32(Bs);
     const uint32_t bar0 = smem_u32(&bars[0]), bar1 = smem_u32(&bars[1]);
-    const uint32_t lbar[2] = {smem_u32(&lbars[0]), smem_u32(&lbars[1])};
-    uint32_t phase[2] = {0u, 0u};
-    uint32_t lphase[2] = {0u, 0u};   // thread 0: phases of the copy barriers
-    const uint32_t ebar[2] = {smem_u32(&ebars[0]), smem_u32(&ebars[1])};
-    uint32_t ephase[2] = {0u, 0u};   // thread 0: phases of the TMEM-half barriers
-    int half_used[2] = {0, 0};       // thread 0: an epilogue of this half is still to be waited for
-    int mma_pending[2] = {0, 0};     // thread 0: MMAs committed to bars[h] and not yet seen done
-    int loads_pending[2] = {0, 0};   // thread 0: copies issued and not yet waited on
+    const uint32_t lbar0 = smem_u32(&lbars[0]), lbar1 = smem_u32(&lbars[1]);
+    // barrier phases and flags as bit masks (bit h for TMEM half / buffer h),
+    // so that they stay in registers
+    uint32_t phase = 0u;             // MMA barriers
+    uint32_t lphase = 0u;            // thread 0: copy barriers
+    const uint32_t ebar0 = smem_u32(&ebars[0]), ebar1 = smem_u32(&ebars[1]);
+    uint32_t ephase = 0u;            // thread 0: TMEM-half barriers
+    uint32_t half_used = 0u;         // thread 0: an epilogue of this half is still to be waited for
+    uint32_t mma_pending = 0u;       // thread 0: MMAs committed to bars[h] and not yet seen done
+    uint32_t loads_pending = 0u;     // thread 0: copies issued and not yet waited on
     bool ok = true;
 
     const size_t units = a.u1 > a.u0 ? a.u1 - a.u0 : 0;
@@ -274,32 +276,32 @@ __global__ void __launch_bounds__(kThreads, 1) search_tc_kernel(rot::SearchArgs 
     if (kStream && t == 0) {
         for (int q = 0; q < 2; ++q) {
             bulk_load(b_base + (uint32_t)q * Sh::ChunkBytes, gsrc + (size_t)q * Sh::ChunkBytes,
-                      Sh::ChunkBytes, lbar[q]);
-            loads_pending[q] = 1;
+                      Sh::ChunkBytes, ((q) ? lbar1 : lbar0));
+            loads_pending |= 1u << q;
         }
     }
     // thread 0: wait until every warp has read the TMEM half (its previous
     // chunk), wait for the copy of chunk q (streamed table), issue the MMAs
     auto issue = [&](uint32_t tmem_d, int chunk, long q, uint32_t bar) {
         const int hh = chunk & 1;
-        if (half_used[hh]) {
-            if (!mbar_wait(ebar[hh], ephase[hh])) return;     // no MMA: the MMA wait expires
-            ephase[hh] ^= 1u;
-            half_used[hh] = 0;
+        if ((half_used >> hh) & 1u) {
+            if (!mbar_wait(((hh) ? ebar1 : ebar0), (ephase >> hh) & 1u)) return;   // no MMA: the MMA wait expires
+            ephase ^= 1u << hh;
+            half_used &= ~(1u << hh);
         }
         uint32_t b_chunk;
         if constexpr (kStream) {
             const int buf = (int)(q & 1);
-            if (!mbar_wait(lbar[buf], lphase[buf])) return;   // no MMA: the MMA wait expires
-            lphase[buf] ^= 1u;
-            loads_pending[buf] = 0;
+            if (!mbar_wait(((buf) ? lbar1 : lbar0), (lphase >> buf) & 1u)) return;   // no MMA: the MMA wait expires
+            lphase ^= 1u << buf;
+            loads_pending &= ~(1u << buf);
             b_chunk = b_base + (uint32_t)buf * Sh::ChunkBytes;
         } else {
             b_chunk = b_base + (uint32_t)chunk * Sh::ChunkBytes;
         }
         issue_chunk<KP>(tmem_d, a_base, b_chunk, bar);
-        half_used[hh] = 1;
-        mma_pending[hh] = 1;
+        half_used |= 1u << hh;
+        mma_pending |= 1u << hh;
     };
 
     const int lane_t = t & 127;            // TMEM lane = voxel of the tile
@@ -360,17 +362,17 @@ __global__ void __launch_bounds__(kThreads, 1) search_tc_kernel(rot::SearchArgs 
                       ((c + 1) & 1) ? bar1 : bar0);
             // no block barrier per chunk: warps move on independently; the
             // TMEM-half barriers tell thread 0 when a half may be overwritten
-            if (!mbar_wait(h ? bar1 : bar0, phase[h])) { ok = false; break; }
-            phase[h] ^= 1u;
-            if (t == 0) mma_pending[h] = 0;
+            if (!mbar_wait(h ? bar1 : bar0, (phase >> h) & 1u)) { ok = false; break; }
+            phase ^= 1u << h;
+            if (t == 0) mma_pending &= ~(1u << h);
             // the MMAs of chunk q are done: its buffer takes chunk q + 2
             if (kStream && t == 0 && (c + 2 < kChunks || more_tiles)) {
                 const int buf = (int)(q & 1);
                 const int nxt = (c + 2) % kChunks;
                 asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
                 bulk_load(b_base + (uint32_t)buf * Sh::ChunkBytes,
-                          gsrc + (size_t)nxt * Sh::ChunkBytes, Sh::ChunkBytes, lbar[buf]);
-                loads_pending[buf] = 1;
+                          gsrc + (size_t)nxt * Sh::ChunkBytes, Sh::ChunkBytes, ((buf) ? lbar1 : lbar0));
+                loads_pending |= 1u << buf;
             }
             asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
             const uint32_t col0 = tmem + ((uint32_t)((warp & 3) * 32) << 16) +
@@ -403,7 +405,7 @@ __global__ void __launch_bounds__(kThreads, 1) search_tc_kernel(rot::SearchArgs 
             asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
             __syncwarp();
             if ((t & 31) == 0)
-                asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(ebar[h]) : "memory");
+                asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(((h) ? ebar1 : ebar0)) : "memory");
         }
         if (!__syncthreads_and(ok)) {
             ok = false;
@@ -411,7 +413,7 @@ __global__ void __launch_bounds__(kThreads, 1) search_tc_kernel(rot::SearchArgs 
                 atomicExch(status, TTM_ERR_TIMEOUT);
                 // MMAs still in flight finish before the tensor memory is released
                 for (int hh = 0; hh < 2; ++hh)
-                    if (mma_pending[hh]) mbar_wait(hh ? bar1 : bar0, phase[hh]);
+                    if ((mma_pending >> hh) & 1u) mbar_wait(hh ? bar1 : bar0, (phase >> hh) & 1u);
             }
             break;
         }
@@ -442,7 +444,7 @@ __global__ void __launch_bounds__(kThreads, 1) search_tc_kernel(rot::SearchArgs 
     // copies still in flight (only after an expired wait) land before exit
     if (kStream && t == 0) {
         for (int b = 0; b < 2; ++b)
-            if (loads_pending[b]) mbar_wait(lbar[b], lphase[b]);
+            if ((loads_pending >> b) & 1u) mbar_wait(((b) ? lbar1 : lbar0), (lphase >> b) & 1u);
     }
     __syncthreads();
     if (warp == 0)
