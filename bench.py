@@ -65,7 +65,15 @@ L2_FLUSH_BYTES = 256 << 20
 # Measured DRAM traffic of a kernel class from one ncu capture (bytes per
 # launch scaled to the bench workload) with the hash of the sources it was
 # taken on; reported only while those sources are unchanged.
-NCU_TRAFFIC: dict = {}
+NCU_TRAFFIC: dict = {
+    # ncu --set full of the 128^3 case (912 673 interior voxels, one launch
+    # each): DRAM read + write per interior voxel, scaled to the launch of the
+    # 256^3 bench workload (11 390 625 interior voxels in 8 chunks)
+    "rotation_polish": dict(bytes_per_launch=round((193.204480e6 + 13.522944e6) / 912673 * 11390625 / 8),
+                            source_sha="5186e27e7e98"),
+    "rotation_search": dict(bytes_per_launch=round((173.780224e6 + 13.099776e6) / 912673 * 11390625 / 8),
+                            source_sha="95b0d786b63a"),
+}
 
 
 def parse():
