@@ -349,7 +349,7 @@ __global__ void __launch_bounds__(kFftThreads) cols_t(PS* __restrict__ data, int
 }
 
 template <int L, typename TS, typename PS>
-__global__ void __launch_bounds__(kFftThreads) cols_mul_t(const float2* __restrict__ spec,
+__global__ void __launch_bounds__(kFftThreads, 2) cols_mul_t(const float2* __restrict__ spec,
                                                           const TS* __restrict__ tspec,
                                                           PS* __restrict__ out, int B, int K,
                                                           const float2* __restrict__ tw) {

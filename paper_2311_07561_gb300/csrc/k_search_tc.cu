@@ -389,15 +389,20 @@ __global__ void __launch_bounds__(kThreads, 1) search_tc_kernel(rot::SearchArgs 
                 const int low0 = 2047 - (c * kChunkN + grp * (kChunkN / kGroups) + p * 64);
                 int key[64];
                 pack_keys<0>(key, r, ~2047);
-#pragma unroll
-                for (int w = 8; w >= 1; w >>= 1)
-#pragma unroll
-                    for (int q4 = 0; q4 < 4; ++q4)
-#pragma unroll
-                        for (int j = 0; j < w; ++j) key[16 * q4 + j] = max(key[16 * q4 + j], key[16 * q4 + j + w]);
+                // region maxima with three-input integer maxima (16 -> 6 -> 2 -> 1)
                 int nk[4];
 #pragma unroll
-                for (int q4 = 0; q4 < 4; ++q4) nk[q4] = key[16 * q4] + (low0 - 16 * q4 - 15);
+                for (int q4 = 0; q4 < 4; ++q4) {
+                    const int* k16 = key + 16 * q4;
+                    const int m0 = __vimax3_s32(k16[0], k16[1], k16[2]);
+                    const int m1 = __vimax3_s32(k16[3], k16[4], k16[5]);
+                    const int m2 = __vimax3_s32(k16[6], k16[7], k16[8]);
+                    const int m3 = __vimax3_s32(k16[9], k16[10], k16[11]);
+                    const int m4 = __vimax3_s32(k16[12], k16[13], k16[14]);
+                    const int n0 = __vimax3_s32(m0, m1, m2);
+                    const int n1 = __vimax3_s32(m3, m4, k16[15]);
+                    nk[q4] = max(n0, n1) + (low0 - 16 * q4 - 15);
+                }
                 cx(nk[0], nk[1]); cx(nk[2], nk[3]); cx(nk[0], nk[2]); cx(nk[1], nk[3]); cx(nk[1], nk[2]);
                 merge4(top, nk);
             }
