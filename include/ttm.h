@@ -336,6 +336,27 @@ ttm_status ttm_extract_peaks(ttm_plan_t plan, int problem, const float* d_score,
                              int radius, int max_peaks, ttm_peak* h_out, int* n_out,
                              void* d_workspace, size_t workspace_bytes, void* stream);
 
+/* ---------------------------------------------------------------------------
+ * ttm_match_peaks -- the score map and the rotations at its peaks only (the
+ * paper's own use of the two outputs, Sec. 3.4: the Frobenius norm locates
+ * candidate positions, the dominant Z-eigenvector is computed there).
+ *
+ * For problem p: the K correlations of d_vol (as ttm_correlate, using the w
+ * map d_w from ttm_local_stats), the score map into d_score (X*Y*Z floats,
+ * 0 outside the interior), its local maxima exactly as ttm_extract_peaks
+ * (score > threshold, largest in the (2 nms_radius + 1)^3 cube, equal scores
+ * to the lower linear index), and then the rotation search and refinement of
+ * ttm_correlate at those voxels only.  Up to max_peaks records sorted by
+ * score go to h_out (host); *n_out is their number.  q and lambda of a record
+ * are bit-identical to the maps ttm_correlate writes at that voxel.  No
+ * rotation or lambda map is written.  Synchronises the stream.  Errors: as
+ * ttm_extract_peaks, and a device status (TTM_ERR_TIMEOUT) of this call.
+ * ------------------------------------------------------------------------ */
+ttm_status ttm_match_peaks(ttm_plan_t plan, int problem, const float* d_vol, const float* d_w,
+                           float* d_score, float threshold, int nms_radius, int max_peaks,
+                           ttm_peak* h_out, int* n_out, void* d_workspace, size_t workspace_bytes,
+                           void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -33,7 +33,8 @@ EXPORTED = (
     "ttm_plan_problem_path", "ttm_plan_problem_fft_box", "ttm_plan_problem_tuning",
     "ttm_plan_problem_tensor_direct",
     "ttm_plan_launch_count", "ttm_plan_destroy",
-    "ttm_local_stats", "ttm_correlate", "ttm_extract_peaks", "ttm_plan_enable_timing",
+    "ttm_local_stats", "ttm_correlate", "ttm_extract_peaks", "ttm_match_peaks",
+    "ttm_plan_enable_timing",
     "ttm_plan_timing", "ttm_kernel_class_name", "ttm_build_tensor_template_noalloc",
     "ttm_plan_device_status", "ttm_classical_workspace_size", "ttm_classical_ncc",
 )
@@ -98,6 +99,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "ttm_correlate": (I, [P, PP, PP, PP, PP, PP, PP, P, S, P]),
         "ttm_extract_peaks": (I, [P, I, P, P, P, ctypes.c_float, I, I, ctypes.POINTER(Peak),
                                   ctypes.POINTER(I), P, S, P]),
+        "ttm_match_peaks": (I, [P, I, P, P, P, ctypes.c_float, I, I, ctypes.POINTER(Peak),
+                                ctypes.POINTER(I), P, S, P]),
         "ttm_plan_enable_timing": (I, [P, I]),
         "ttm_plan_timing": (I, [P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(L), I]),
         "ttm_kernel_class_name": (ctypes.c_char_p, [I]),
@@ -330,5 +333,20 @@ def ttm_extract_peaks(plan: int, problem: int, score, quat, lam, threshold: floa
                                           ctypes.byref(n), _ptr(workspace), _nbytes(workspace),
                                           _stream(stream))
     _check(st, "ttm_extract_peaks")
+    raw = np.frombuffer(bytes(buf), dtype=PEAK_DTYPE, count=max(max_peaks, 1))
+    return raw[: n.value].copy()
+
+
+def ttm_match_peaks(plan: int, problem: int, vol, w, score, threshold: float, radius: int,
+                    max_peaks: int, workspace, stream=None) -> np.ndarray:
+    """Score map into `score`, then the rotation only at its peaks; returns the
+    peak records (x, y, z, score, lambda, q) sorted by score."""
+    buf = (Peak * max(max_peaks, 1))()
+    n = ctypes.c_int()
+    st = load_library().ttm_match_peaks(plan, problem, _ptr(vol), _ptr(w), _ptr(score),
+                                        float(threshold), radius, max_peaks, buf,
+                                        ctypes.byref(n), _ptr(workspace), _nbytes(workspace),
+                                        _stream(stream))
+    _check(st, "ttm_match_peaks")
     raw = np.frombuffer(bytes(buf), dtype=PEAK_DTYPE, count=max(max_peaks, 1))
     return raw[: n.value].copy()

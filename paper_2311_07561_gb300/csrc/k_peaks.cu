@@ -87,7 +87,7 @@ __global__ void peak_z_kernel(const float* __restrict__ score, const float* __re
     rec.idx = (int)v;
     rec.score = s;
     rec.lambda = lam ? lam[v] : 0.f;
-    float4 q = reinterpret_cast<const float4*>(quat)[v];
+    const float4 q = quat ? reinterpret_cast<const float4*>(quat)[v] : make_float4(1.f, 0.f, 0.f, 0.f);
     rec.q[0] = q.x; rec.q[1] = q.y; rec.q[2] = q.z; rec.q[3] = q.w;
     rec.pad = 0;
     list[slot] = rec;

@@ -8,7 +8,9 @@ int rotation_row_stride(int n_order) { return (n_comp(n_order) + 3) & ~3; }
 static void fill_args(const void* corr, const float* w, size_t nvox, const VoxBox& box,
                       uint32_t u0, uint32_t u1, const RotGrid& g, uint16_t* cand, float* score,
                       float* quat, float* lambda, float* comp_out, rot::SearchArgs& sa,
-                      rot::PolishArgs& pa) {
+                      rot::PolishArgs& pa, const UnitList& list) {
+    sa.list = list;
+    pa.list = list;
     sa.corr = corr; sa.w = w; sa.nvox = nvox; sa.box = box; sa.score = score; sa.cand = cand;
     sa.u0 = u0; sa.u1 = u1; pa.u0 = u0; pa.u1 = u1;
     sa.gm = g.d_m; sa.cell_end = g.d_cell_end; sa.n_grid = g.n_grid;
@@ -20,12 +22,12 @@ static void fill_args(const void* corr, const float* w, size_t nvox, const VoxBo
 ttm_status launch_rotation_search(int n_order, const void* corr, bool bf16, const float* w,
                                   size_t nvox, const VoxBox& box, uint32_t u0, uint32_t u1,
                                   const RotGrid& g, uint16_t* cand, int* status, float* score,
-                                  cudaStream_t st, long long* cnt) {
-    if (box.count() > 0xFFFFFFFFull || u1 > box.count()) return TTM_ERR_UNSUPPORTED;
+                                  cudaStream_t st, long long* cnt, const UnitList& list) {
+    if (box.count() > 0xFFFFFFFFull || (!list.idx && u1 > box.count())) return TTM_ERR_UNSUPPORTED;
     if (u1 <= u0) return TTM_OK;
     rot::SearchArgs sa;
     rot::PolishArgs pa;
-    fill_args(corr, w, nvox, box, u0, u1, g, cand, score, nullptr, nullptr, nullptr, sa, pa);
+    fill_args(corr, w, nvox, box, u0, u1, g, cand, score, nullptr, nullptr, nullptr, sa, pa, list);
     if (g.d_gtab && search_tc_supported(n_order, g.n_grid, g.n_cells))
         return launch_search_tc(n_order, sa, g.d_gtab, status, bf16, st, cnt);
     switch (n_order) {
@@ -41,18 +43,45 @@ ttm_status launch_rotation_polish(int n_order, const void* corr, bool bf16, cons
                                   size_t nvox, const VoxBox& box, uint32_t u0, uint32_t u1,
                                   const RotGrid& g, const uint16_t* cand, const float* score,
                                   float* quat, float* lambda, float* comp_out, cudaStream_t st,
-                                  long long* cnt) {
-    if (box.count() > 0xFFFFFFFFull || u1 > box.count()) return TTM_ERR_UNSUPPORTED;
+                                  long long* cnt, const UnitList& list) {
+    if (box.count() > 0xFFFFFFFFull || (!list.idx && u1 > box.count())) return TTM_ERR_UNSUPPORTED;
     if (u1 <= u0) return TTM_OK;
     rot::SearchArgs sa;
     rot::PolishArgs pa;
     fill_args(corr, w, nvox, box, u0, u1, g, const_cast<uint16_t*>(cand),
-              const_cast<float*>(score), quat, lambda, comp_out, sa, pa);
+              const_cast<float*>(score), quat, lambda, comp_out, sa, pa, list);
     switch (n_order) {
         case 2: return launch_rotation_n<2>(sa, pa, true, false, bf16, st, cnt);
         case 4: return launch_rotation_n<4>(sa, pa, true, false, bf16, st, cnt);
         case 6: return launch_rotation_n<6>(sa, pa, true, false, bf16, st, cnt);
         case 8: return launch_rotation_n<8>(sa, pa, true, false, bf16, st, cnt);
+        default: return TTM_ERR_UNSUPPORTED;
+    }
+}
+
+template <int N>
+static ttm_status score_only_n(const void* corr, bool bf16, const float* w, int X, int Y, int Z,
+                               const VoxBox& box, float* score, cudaStream_t st, long long* cnt) {
+    dim3 grid((unsigned)((X + 127) / 128), (unsigned)Y, (unsigned)Z);
+    const size_t nvox = (size_t)X * Y * Z;
+    if (bf16)
+        rot::score_only_kernel<N, __nv_bfloat16><<<grid, 128, 0, st>>>(
+            reinterpret_cast<const __nv_bfloat16*>(corr), w, X, Y, nvox, box, score);
+    else
+        rot::score_only_kernel<N, float><<<grid, 128, 0, st>>>(
+            reinterpret_cast<const float*>(corr), w, X, Y, nvox, box, score);
+    return after_launch(cnt);
+}
+
+ttm_status launch_score_only(int n_order, const void* corr, bool bf16, const float* w, int X,
+                             int Y, int Z, const VoxBox& box, float* score, cudaStream_t st,
+                             long long* cnt) {
+    if (Y > 65535 || Z > 65535) return TTM_ERR_UNSUPPORTED;
+    switch (n_order) {
+        case 2: return score_only_n<2>(corr, bf16, w, X, Y, Z, box, score, st, cnt);
+        case 4: return score_only_n<4>(corr, bf16, w, X, Y, Z, box, score, st, cnt);
+        case 6: return score_only_n<6>(corr, bf16, w, X, Y, Z, box, score, st, cnt);
+        case 8: return score_only_n<8>(corr, bf16, w, X, Y, Z, box, score, st, cnt);
         default: return TTM_ERR_UNSUPPORTED;
     }
 }

@@ -40,6 +40,7 @@ struct SearchArgs {
     size_t nvox;            // voxels of the volume (stride of the component maps)
     VoxBox box;             // interior voxels: the units the kernels visit
     uint32_t u0, u1;        // this launch visits units [u0, u1)
+    UnitList list;          // optional unit list (peaks)
     float* score;
     uint16_t* cand;         // per interior voxel: 8 candidate grid indices
     const float* gm;        // n_grid x K4 (SIMT search)
@@ -53,6 +54,7 @@ struct PolishArgs {
     size_t nvox;
     VoxBox box;
     uint32_t u0, u1;        // this launch visits units [u0, u1)
+    UnitList list;          // optional unit list (peaks) and strided outputs
     const float* score;
     const uint16_t* cand;
     float* quat;            // 4 x nvox interleaved (a, b, c, d) per voxel
@@ -61,6 +63,43 @@ struct PolishArgs {
     const float* gq;        // n_grid x 4
     int n_cand, newton;
 };
+
+// end of the units [.., u1) and the voxel of unit i, with an optional list
+static __device__ __forceinline__ uint32_t list_end(const UnitList& l, uint32_t u1) {
+    if (!l.count) return u1;
+    const int c = *l.count;
+    return c <= 0 ? 0u : ((uint32_t)c < u1 ? (uint32_t)c : u1);
+}
+static __device__ __forceinline__ size_t unit_voxel(const VoxBox& b, const UnitList& l, uint32_t i) {
+    return l.idx ? (size_t)l.idx[(size_t)i * l.stride] : b.voxel(i);
+}
+
+// score = ||C||_F with C = w Corr at the interior voxels, 0 elsewhere; the
+// same arithmetic as the search kernels.  Block (x segment, y, z).
+template <int N, typename CT>
+__global__ void __launch_bounds__(128) score_only_kernel(const CT* __restrict__ corr,
+                                                         const float* __restrict__ w, int X, int Y,
+                                                         size_t nvox, VoxBox box,
+                                                         float* __restrict__ score) {
+    constexpr int K = n_comp(N);
+    constexpr Sym<N> S{};
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y, z = blockIdx.z;
+    if (x >= X) return;
+    const size_t v = ((size_t)z * Y + y) * X + x;
+    const bool in = (uint32_t)(x - box.x0) < box.nx && (uint32_t)(y - box.y0) < box.ny &&
+                    (uint32_t)(z - box.z0) < box.nz;
+    float ss = 0.f;
+    if (in) {
+        const float wv = __ldg(w + v);
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            const float c = wv * ldcorr(corr + (size_t)k * nvox + v);
+            ss = fmaf((float)S.mu[k], c * c, ss);
+        }
+    }
+    score[v] = sqrtf(ss);
+}
 
 // keep the kMaxCand largest (value, index) pairs, sorted descending
 static __device__ __forceinline__ void insert_candidate(float (&tv)[kMaxCand], int (&ti)[kMaxCand],
@@ -315,8 +354,8 @@ __global__ void __launch_bounds__(kRotThreads) search_simt_kernel(SearchArgs a) 
     int* ends = reinterpret_cast<int*>(sm + kChunk * K4);
 
     const size_t i = a.u0 + (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const bool in_range = i < a.u1;
-    const size_t v = in_range ? a.box.voxel((uint32_t)i) : 0;
+    const bool in_range = i < list_end(a.list, a.u1);
+    const size_t v = in_range ? unit_voxel(a.box, a.list, (uint32_t)i) : 0;
     const float wv = in_range ? __ldg(a.w + v) : 0.f;
     float C[K4];
 #pragma unroll
@@ -377,8 +416,8 @@ __global__ void __launch_bounds__(kRotThreads) polish_kernel(PolishArgs a) {
     constexpr int K = Geo<N>::K;
     constexpr int K4 = Geo<N>::K4;
     const size_t i = a.u0 + (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= a.u1) return;
-    const size_t v = a.box.voxel((uint32_t)i);
+    if (i >= list_end(a.list, a.u1)) return;
+    const size_t v = unit_voxel(a.box, a.list, (uint32_t)i);
     const float wv = __ldg(a.w + v);
     float C[K4];
 #pragma unroll
@@ -459,6 +498,13 @@ __global__ void __launch_bounds__(kRotThreads) polish_kernel(PolishArgs a) {
         else sgn = best_q[3] < 0.f ? -1.f : 1.f;
 #pragma unroll
         for (int i = 0; i < 4; ++i) best_q[i] *= sgn;
+    }
+    if (a.list.out_stride > 0) {
+        float* qo = a.quat + i * (size_t)a.list.out_stride;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) qo[k] = best_q[k];
+        if (a.lambda) a.lambda[i * (size_t)a.list.out_stride] = best_l;
+        return;
     }
     reinterpret_cast<float4*>(a.quat)[v] = make_float4(best_q[0], best_q[1], best_q[2], best_q[3]);
     if (a.lambda) a.lambda[v] = best_l;

@@ -268,7 +268,8 @@ __global__ void __launch_bounds__(kThreads, 1) search_tc_kernel(rot::SearchArgs 
     uint32_t loads_pending = 0u;     // thread 0: copies issued and not yet waited on
     bool ok = true;
 
-    const size_t units = a.u1 > a.u0 ? a.u1 - a.u0 : 0;
+    const uint32_t uend = rot::list_end(a.list, a.u1);
+    const size_t units = uend > a.u0 ? uend - a.u0 : 0;
     const size_t ntiles = (units + 127) / 128;
     const unsigned char* gsrc = reinterpret_cast<const unsigned char*>(gtab);
     // streamed table: chunk q (counted over the whole CTA) goes to buffer q & 1;
@@ -310,8 +311,8 @@ __global__ void __launch_bounds__(kThreads, 1) search_tc_kernel(rot::SearchArgs 
     for (size_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x, qbase += kChunks) {
         const bool more_tiles = tile + gridDim.x < ntiles;
         const size_t i = a.u0 + tile * 128 + lane_t;
-        const bool in_range = i < a.u1;
-        const size_t v = in_range ? a.box.voxel((uint32_t)i) : 0;
+        const bool in_range = i < uend;
+        const size_t v = in_range ? rot::unit_voxel(a.box, a.list, (uint32_t)i) : 0;
         // components, score, normalised FP16 row of A (threads 0..127)
         float score = 0.f;
         if (grp == 0) {

@@ -444,7 +444,9 @@ size_t scratch_bytes(const ttm_plan_s* P, const ProblemData& pr) {
     if (pr.path == TTM_PATH_FFT)
         corr = std::max(corr, 4 * pr.fft.nspec() * sizeof(float2) + 2 * nv * sizeof(float) + 256);
     size_t peaks = 2 * align256(nv * sizeof(float)) + align256(peak_cap(nv) * peak_record_bytes());
-    return std::max(corr, peaks);
+    // ttm_match_peaks keeps the correlation maps and candidates while it finds peaks
+    const size_t corr_peaks = corr_region_bytes(P, pr) + align256(nv * 16) + peaks;
+    return std::max(std::max(corr, peaks), corr_peaks);
 }
 
 ttm_status check_ws(const ttm_plan_s* P, void* ws, size_t bytes) {
@@ -610,6 +612,43 @@ ttm_status rotation_problem(ttm_plan_s* plan, const ProblemData& pr, const float
     }
     TTM_CUDA_TRY(cudaEventRecord(plan->ev_join, plan->s_lo));
     TTM_CUDA_TRY(cudaStreamWaitEvent(st, plan->ev_join, 0));
+    return TTM_OK;
+}
+
+// Copies the device peak list to the host: records sorted by score
+// (descending; equal scores by voxel index), the first max_peaks kept.
+// Synchronises the stream.
+ttm_status copy_peaks_to_host(const ProblemData& pr, const int* d_count, const void* list, int cap,
+                              int max_peaks, ttm_peak* h_out, int* n_out, cudaStream_t st) {
+    int count = 0;
+    TTM_CUDA_TRY(cudaMemcpyAsync(&count, d_count, sizeof(int), cudaMemcpyDeviceToHost, st));
+    TTM_CUDA_TRY(cudaStreamSynchronize(st));
+    if (count > cap) return TTM_ERR_WORKSPACE;
+    struct Rec { int idx; float score, lambda, q[4]; int pad; };
+    static_assert(sizeof(Rec) == 32, "peak record layout");
+    if (peak_record_bytes() != sizeof(Rec)) return TTM_ERR_CUDA;
+    std::vector<Rec> recs(count);
+    if (count > 0) {
+        TTM_CUDA_TRY(cudaMemcpyAsync(recs.data(), list, (size_t)count * sizeof(Rec),
+                                     cudaMemcpyDeviceToHost, st));
+        TTM_CUDA_TRY(cudaStreamSynchronize(st));
+    }
+    std::sort(recs.begin(), recs.end(), [](const Rec& a, const Rec& b) {
+        if (a.score != b.score) return a.score > b.score;
+        return a.idx < b.idx;
+    });
+    const int nout = std::min(count, max_peaks);
+    for (int i = 0; i < nout; ++i) {
+        const Rec& r = recs[i];
+        ttm_peak& o = h_out[i];
+        o.x = (int)(r.idx % pr.X);
+        o.y = (int)((r.idx / pr.X) % pr.Y);
+        o.z = (int)(r.idx / ((size_t)pr.X * pr.Y));
+        o.score = r.score;
+        o.lambda = r.lambda;
+        for (int k = 0; k < 4; ++k) o.q[k] = r.q[k];
+    }
+    *n_out = nout;
     return TTM_OK;
 }
 
@@ -1142,36 +1181,68 @@ ttm_status ttm_extract_peaks(ttm_plan_t plan, int problem, const float* d_score,
                                            radius, tmp_a, tmp_b, list, cap, d_count, st,
                                            &plan->launches);
     }));
-    int count = 0;
-    TTM_CUDA_TRY(cudaMemcpyAsync(&count, d_count, sizeof(int), cudaMemcpyDeviceToHost, st));
-    TTM_CUDA_TRY(cudaStreamSynchronize(st));
-    if (count > cap) return TTM_ERR_WORKSPACE;
-    struct Rec { int idx; float score, lambda, q[4]; int pad; };
-    static_assert(sizeof(Rec) == 32, "peak record layout");
-    if (peak_record_bytes() != sizeof(Rec)) return TTM_ERR_CUDA;
-    std::vector<Rec> recs(count);
-    if (count > 0) {
-        TTM_CUDA_TRY(cudaMemcpyAsync(recs.data(), list, (size_t)count * sizeof(Rec),
-                                     cudaMemcpyDeviceToHost, st));
-        TTM_CUDA_TRY(cudaStreamSynchronize(st));
-    }
-    std::sort(recs.begin(), recs.end(), [](const Rec& a, const Rec& b) {
-        if (a.score != b.score) return a.score > b.score;
-        return a.idx < b.idx;
-    });
-    const int nout = std::min(count, max_peaks);
-    for (int i = 0; i < nout; ++i) {
-        const Rec& r = recs[i];
-        ttm_peak& o = h_out[i];
-        o.x = (int)(r.idx % pr.X);
-        o.y = (int)((r.idx / pr.X) % pr.Y);
-        o.z = (int)(r.idx / ((size_t)pr.X * pr.Y));
-        o.score = r.score;
-        o.lambda = r.lambda;
-        for (int k = 0; k < 4; ++k) o.q[k] = r.q[k];
-    }
-    *n_out = nout;
-    return TTM_OK;
+    return copy_peaks_to_host(pr, d_count, list, cap, max_peaks, h_out, n_out, st);
+}
+
+ttm_status ttm_match_peaks(ttm_plan_t plan, int problem, const float* d_vol, const float* d_w,
+                           float* d_score, float threshold, int radius, int max_peaks,
+                           ttm_peak* h_out, int* n_out, void* d_workspace, size_t workspace_bytes,
+                           void* stream) {
+    if (!plan || problem < 0 || problem >= (int)plan->prob.size() || !d_vol || !d_w || !d_score ||
+        !n_out || radius < 0 || radius > 32 || max_peaks < 0 || (max_peaks > 0 && !h_out))
+        return TTM_ERR_INVALID_ARG;
+    if (!aligned(d_vol, 4) || !aligned(d_w, 4) || !aligned(d_score, 4)) return TTM_ERR_INVALID_ARG;
+    TTM_TRY(check_ws(plan, d_workspace, workspace_bytes));
+    const ProblemData& pr = plan->prob[problem];
+    const TemplateData& T = plan->tmpl[pr.tmpl];
+    const size_t nv = pr.nvox();
+    cudaStream_t st = (cudaStream_t)stream;
+    char* ws = (char*)d_workspace;
+    int* d_count = (int*)(ws + 16);
+    int* d_status = (int*)(ws + 32);
+    // workspace: correlation maps and candidates as in ttm_correlate, then the
+    // peak pass's two maps and its list
+    float* corr = (float*)(ws + kHeader);
+    uint16_t* cand = (uint16_t*)((char*)corr + corr_region_bytes(plan, pr));
+    char* pk = (char*)cand + align256(nv * 16);
+    float* tmp_a = (float*)pk;
+    float* tmp_b = (float*)(pk + align256(nv * sizeof(float)));
+    char* list = pk + 2 * align256(nv * sizeof(float));
+    const int cap = (int)peak_cap(nv);
+    const VoxBox box = interior_box(pr.X, pr.Y, pr.Z, T.desc.s);
+    TTM_CUDA_TRY(cudaMemsetAsync(ws + 16, 0, 32, st));       // peak count, status word
+    TTM_TRY(corr_problem(plan, pr, d_vol, d_workspace, st));
+    TTM_TRY(timed(plan, KC_ROTATION, st, [&] {
+        return launch_score_only(plan->n_order, corr, pr.mixed, d_w, pr.X, pr.Y, pr.Z, box,
+                                 d_score, st, &plan->launches);
+    }));
+    TTM_TRY(timed(plan, KC_PEAKS, st, [&] {
+        return launch_peak_candidates_full(d_score, nullptr, nullptr, pr.X, pr.Y, pr.Z, threshold,
+                                           radius, tmp_a, tmp_b, list, cap, d_count, st,
+                                           &plan->launches);
+    }));
+    // rotations at the peaks only: the record list is the unit list (voxel
+    // index first, 8 words per record), q and lambda go into the records
+    UnitList ul;
+    ul.idx = (const int*)list;
+    ul.stride = 8;
+    ul.count = d_count;
+    ul.out_stride = 8;
+    TTM_TRY(timed(plan, KC_ROTATION, st, [&] {
+        return launch_rotation_search(plan->n_order, corr, pr.mixed, d_w, nv, box, 0,
+                                      (uint32_t)cap, plan->grid, cand, d_status, d_score, st,
+                                      &plan->launches, ul);
+    }));
+    TTM_TRY(timed(plan, KC_POLISH, st, [&] {
+        return launch_rotation_polish(plan->n_order, corr, pr.mixed, d_w, nv, box, 0,
+                                      (uint32_t)cap, plan->grid, cand, d_score,
+                                      (float*)list + 3, (float*)list + 2, nullptr, st,
+                                      &plan->launches, ul);
+    }));
+    TTM_TRY(copy_peaks_to_host(pr, d_count, list, cap, max_peaks, h_out, n_out, st));
+    int dev_status = 0;
+    TTM_CUDA_TRY(cudaMemcpy(&dev_status, d_status, sizeof(int), cudaMemcpyDeviceToHost));
+    return dev_status == 0 ? TTM_OK : (ttm_status)dev_status;
 }
 
 }  // extern "C"

@@ -81,6 +81,18 @@ struct VoxBox {
     }
 };
 
+// Optional unit list of the rotation kernels: unit i is the voxel idx[i *
+// stride] instead of box.voxel(i), the number of units is read on the device
+// from *count (clamped to the launch's u1), and with out_stride > 0 the
+// refinement writes q to quat[i * out_stride + 0..3] and lambda to
+// lambda[i * out_stride] instead of the voxel-indexed maps.
+struct UnitList {
+    const int* idx = nullptr;
+    int stride = 0;
+    const int* count = nullptr;
+    int out_stride = 0;
+};
+
 inline VoxBox interior_box(int X, int Y, int Z, int s) {
     VoxBox b;
     b.X = X; b.Y = Y;
@@ -177,12 +189,17 @@ ttm_status launch_direct_tc(const float* f, int X, int Y, int Z, const TemplateD
 ttm_status launch_rotation_search(int n_order, const void* corr, bool bf16, const float* w,
                                   size_t nvox, const VoxBox& box, uint32_t u0, uint32_t u1,
                                   const RotGrid& g, uint16_t* cand, int* status, float* score,
-                                  cudaStream_t st, long long* cnt);
+                                  cudaStream_t st, long long* cnt,
+                                  const UnitList& list = UnitList());
 ttm_status launch_rotation_polish(int n_order, const void* corr, bool bf16, const float* w,
                                   size_t nvox, const VoxBox& box, uint32_t u0, uint32_t u1,
                                   const RotGrid& g, const uint16_t* cand, const float* score,
                                   float* quat, float* lambda, float* comp_out, cudaStream_t st,
-                                  long long* cnt);
+                                  long long* cnt, const UnitList& list = UnitList());
+// score = ||w Corr||_F at the interior voxels, 0 outside (no rotation)
+ttm_status launch_score_only(int n_order, const void* corr, bool bf16, const float* w, int X,
+                             int Y, int Z, const VoxBox& box, float* score, cudaStream_t st,
+                             long long* cnt);
 ttm_status launch_exterior_fill(int Z, const VoxBox& box, int K, float* score, float* quat,
                                 float* lambda, float* comp_out, cudaStream_t st, long long* cnt);
 // FP16 grid table of the tensor-core search (2048 points, K components + the

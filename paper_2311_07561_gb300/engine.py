@@ -142,6 +142,18 @@ class Matcher:
         return B.ttm_extract_peaks(self.plan, problem, self.score[problem], self.quat[problem],
                                    self.lam[problem], threshold, radius, max_peaks, self.ws, stream)
 
+    def match_peaks(self, vols: Sequence, problem: int, threshold: float, radius: int,
+                    max_peaks: int, stream=None):
+        """Score map and the rotation at its peaks only, for one problem:
+        local statistics, correlation, score, peaks, then the search and
+        refinement at the peaks (no dense rotation maps).  Returns the peak
+        records; self.score[problem] holds the score map."""
+        self._check_inputs(vols, None)
+        B.ttm_local_stats(self.plan, vols, self.w, self.ws, stream)
+        return B.ttm_match_peaks(self.plan, problem, vols[problem], self.w[problem],
+                                 self.score[problem], threshold, radius, max_peaks, self.ws,
+                                 stream)
+
     def launch_count(self) -> int:
         return B.ttm_plan_launch_count(self.plan)
 

@@ -449,3 +449,27 @@ def test_host_pipeline_matches_matcher(ttm):
         s, q, l = outs[k][0]
         assert torch.equal(s, ref[v][0]) and torch.equal(q, ref[v][1]) and torch.equal(l, ref[v][2])
     pipe.close()
+
+
+@pytest.mark.parametrize("path", PATHS)
+def test_match_peaks_equals_dense_maps_at_peaks(ttm, path):
+    """Rotations at the score peaks only (ttm_match_peaks) are the dense maps'
+    values at those voxels, bit for bit, and the peaks are the same."""
+    import torch
+    wl = synth.make_workload((48, 52, 56), 11, 4, 6, 2.0, 4, 200, radius=5, seeds=(51, 52, 53))
+    comp, desc = ttm.build_template(wl.template, wl.mask, 4, wl.quadrature)
+    prob = [((56, 52, 48), 0)]
+    vol = _cuda(wl.volume)
+    dense = ttm.Matcher([(comp, desc, wl.mask)], prob, opts=_opts(ttm, path))
+    dense.run([vol])
+    ref = dense.peaks(0, 0.0, 5, 500)
+    score_ref = dense.score[0].clone()
+    sparse = ttm.Matcher([(comp, desc, wl.mask)], prob, opts=_opts(ttm, path))
+    got = sparse.match_peaks([vol], 0, 0.0, 5, 500)
+    torch.cuda.synchronize()
+    assert len(ref) > 6 and len(got) == len(ref)
+    assert torch.equal(sparse.score[0], score_ref)
+    for f in ("x", "y", "z", "score", "lambda", "q"):
+        assert np.array_equal(got[f], ref[f]), f
+    dense.close()
+    sparse.close()
