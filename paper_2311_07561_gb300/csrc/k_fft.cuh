@@ -255,6 +255,10 @@ __device__ __forceinline__ float2* fft_lines_t(float2* a, float2* b, const float
 __host__ __device__ constexpr int pow2_floor(int n) { return n < 2 ? 1 : 2 * pow2_floor(n / 2); }
 template <int L> constexpr int rows_nb() { return pow2_floor(4096 / L) > 16 ? 16 : pow2_floor(4096 / L); }
 template <int L> constexpr int cols_tb() { return pow2_floor(4096 / L) > 32 ? 32 : pow2_floor(4096 / L); }
+// column passes over bf16 storage (4 bytes per complex) take at least 8
+// columns, so that every row segment of a tile is a whole 32-byte sector
+template <int L, typename PS>
+constexpr int cols_tb_s() { return (sizeof(PS) < 8 && cols_tb<L>() < 8) ? 8 : cols_tb<L>(); }
 
 // ---- the four passes with a compile-time line length ---------------------
 // mode 0 transforms f, mode 1 (f - mean), mode 2 (f - mean)^2 with mean =
@@ -318,7 +322,7 @@ __global__ void __launch_bounds__(kFftThreads) rows_r2c_t(const float* __restric
 template <int L, int SIGN, typename PS>
 __global__ void __launch_bounds__(kFftThreads) cols_t(PS* __restrict__ data, int B,
                                                       const float2* __restrict__ tw) {
-    constexpr int TB = cols_tb<L>();
+    constexpr int TB = cols_tb_s<L, PS>();
     extern __shared__ float2 sm[];
     float2* P = sm;
     float2* Q = sm + L * TB;
@@ -614,7 +618,7 @@ namespace fftk {
 
 template <int L, int SIGN, typename PS>
 cudaError_t run_cols(PS* d, int B, int na, const float2* tw, cudaStream_t st) {
-    constexpr int TB = cols_tb<L>();
+    constexpr int TB = cols_tb_s<L, PS>();
     const size_t smem = (size_t)2 * L * TB * sizeof(float2);
     cudaError_t e = cudaFuncSetAttribute(cols_t<L, SIGN, PS>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
