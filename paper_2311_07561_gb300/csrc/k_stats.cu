@@ -24,20 +24,34 @@ constexpr int kStatThreads = 256;   // each thread: x = tid % 64, y = tid / 64 a
 __global__ void __launch_bounds__(256) moments_kernel(const float* __restrict__ f, size_t n,
                                                       double* acc) {
     __shared__ double r1[8], r2[8];
-    float s1 = 0.f, s2 = 0.f;
+    // float4 loads with four independent FP32 partial sums each, flushed to
+    // FP64 every 16 vectors; the scalar tail (n % 4, or an unaligned f) after
     double d1 = 0.0, d2 = 0.0;
+    const size_t tid = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+    const size_t nthr = (size_t)gridDim.x * blockDim.x;
+    const bool vec = ((uintptr_t)f & 15) == 0;
+    const size_t n4 = vec ? n / 4 : 0;
+    const float4* f4 = reinterpret_cast<const float4*>(f);
+    float4 s1 = make_float4(0.f, 0.f, 0.f, 0.f), s2 = s1;
     int cntr = 0;
-    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
-         i += (size_t)gridDim.x * blockDim.x) {
-        float v = f[i];
-        s1 += v;
-        s2 += v * v;
-        if (++cntr == 64) {          // flush the FP32 partials to FP64 regularly
-            d1 += s1; d2 += s2; s1 = 0.f; s2 = 0.f; cntr = 0;
+    for (size_t i = tid; i < n4; i += nthr) {
+        const float4 v = __ldg(f4 + i);
+        s1.x += v.x; s1.y += v.y; s1.z += v.z; s1.w += v.w;
+        s2.x = fmaf(v.x, v.x, s2.x); s2.y = fmaf(v.y, v.y, s2.y);
+        s2.z = fmaf(v.z, v.z, s2.z); s2.w = fmaf(v.w, v.w, s2.w);
+        if (++cntr == 16) {
+            d1 += (double)s1.x + s1.y + s1.z + s1.w;
+            d2 += (double)s2.x + s2.y + s2.z + s2.w;
+            s1 = make_float4(0.f, 0.f, 0.f, 0.f); s2 = s1; cntr = 0;
         }
     }
-    d1 += s1;
-    d2 += s2;
+    d1 += (double)s1.x + s1.y + s1.z + s1.w;
+    d2 += (double)s2.x + s2.y + s2.z + s2.w;
+    for (size_t i = 4 * n4 + tid; i < n; i += nthr) {
+        const float v = f[i];
+        d1 += v;
+        d2 += (double)v * v;
+    }
     for (int o = 16; o > 0; o >>= 1) {
         d1 += __shfl_down_sync(0xffffffffu, d1, o);
         d2 += __shfl_down_sync(0xffffffffu, d2, o);
