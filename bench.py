@@ -66,13 +66,14 @@ L2_FLUSH_BYTES = 256 << 20
 # launch scaled to the bench workload) with the hash of the sources it was
 # taken on; reported only while those sources are unchanged.
 NCU_TRAFFIC: dict = {
-    # ncu --set full of the 128^3 case (912 673 interior voxels, one launch
-    # each): DRAM read + write per interior voxel, scaled to the launch of the
-    # 256^3 bench workload (11 390 625 interior voxels in 8 chunks)
-    "rotation_polish": dict(bytes_per_launch=round((193.204480e6 + 13.522944e6) / 912673 * 11390625 / 8),
-                            source_sha="5186e27e7e98"),
-    "rotation_search": dict(bytes_per_launch=round((173.780224e6 + 13.099776e6) / 912673 * 11390625 / 8),
-                            source_sha="95b0d786b63a"),
+    # ncu (dram__bytes_read.sum + dram__bytes_write.sum) of the 128^3 case,
+    # 912 673 interior voxels in one launch each, scaled by interior voxels to
+    # one launch of the 256^3 bench workload (11 390 625 interior voxels in 8
+    # chunks); reported only while the kernels' sources are unchanged
+    "rotation_polish": dict(bytes_per_launch=round((193201664 + 9929728) / 912673 * 11390625 / 8),
+                            source_sha="9cb54c7dd779"),
+    "rotation_search": dict(bytes_per_launch=round((173783808 + 12625152) / 912673 * 11390625 / 8),
+                            source_sha="9aef777fc0c0"),
 }
 
 
