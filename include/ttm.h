@@ -57,7 +57,7 @@ typedef int ttm_status;
 
 #define TTM_OK                 0
 #define TTM_ERR_INVALID_ARG   -1  /* null pointer, bad size, misaligned buffer */
-#define TTM_ERR_UNSUPPORTED   -2  /* odd order n, n > 8, non-binary mask, ...   */
+#define TTM_ERR_UNSUPPORTED   -2  /* odd order n, n > 8, soft mask off the FFT path */
 #define TTM_ERR_OUT_OF_MEMORY -3  /* a plan-owned allocation failed            */
 #define TTM_ERR_CUDA          -4  /* a CUDA runtime call or launch failed       */
 #define TTM_ERR_TIMEOUT       -5  /* a bounded device-side wait ran out         */
@@ -200,7 +200,13 @@ ttm_status ttm_build_tensor_template_noalloc(const float* d_template, const floa
  * caller-owned, read during ttm_plan only when the FFT path is chosen and
  * kept referenced by the direct path: they must stay valid until
  * ttm_plan_destroy) and its mask by d_masks[k] (s^3, read during ttm_plan).
- * The mask must be binary (0 or 1); soft masks return TTM_ERR_UNSUPPORTED.
+ * Mask values lie in [0, 1] (else TTM_ERR_INVALID_ARG).  A binary mask
+ * (0 or 1) allows every path.  A soft mask (weights, e.g. a raised-cosine
+ * edge; the NCC becomes the m-weighted Pearson correlation of Sec. 2's
+ * S-inner product) runs on the FFT path only, with FFT window sums: its
+ * problems need an FFT box whose x length is one of the compiled lengths
+ * 16 32 48 64 80 96 128 144 160 192 240 256 288 320 384 480 512 576 640 768
+ * 960 1024, and TTM_PATH_DIRECT returns TTM_ERR_UNSUPPORTED.
  * opts may be NULL (defaults).  The plan allocates and owns only its tables
  * and precomputed template spectra.  Synchronises the stream.
  * ---------------------------------------------------------------------- */

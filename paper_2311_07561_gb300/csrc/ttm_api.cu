@@ -159,10 +159,23 @@ ttm_status prepare_template(ttm_plan_s* P, TemplateData& T, const float* d_mask)
     TTM_CUDA_TRY(cudaMemcpy(m.data(), d_mask, s3 * sizeof(float), cudaMemcpyDeviceToHost));
     TTM_CUDA_TRY(cudaMemcpy(comp.data(), T.d_comp, comp.size() * sizeof(float),
                             cudaMemcpyDeviceToHost));
-    for (float v : m)
-        if (!(v == 0.f || v == 1.f)) return TTM_ERR_UNSUPPORTED;
+    bool any = false;
+    T.soft = false;
+    for (float v : m) {
+        if (!(v >= 0.f && v <= 1.f)) return TTM_ERR_INVALID_ARG;      // also NaN
+        if (v != 0.f && v != 1.f) T.soft = true;
+        any = any || v > 0.f;
+    }
+    if (!any) return TTM_ERR_INVALID_ARG;
     for (float v : comp)
         if (!std::isfinite(v)) return TTM_ERR_NUMERIC;
+    if (T.soft) {
+        // a soft (weighting) mask: the correlations and the window sums run
+        // through the FFT only; no runs or taps for the direct paths
+        (void)P;
+        TTM_TRY(dev_upload(&T.d_mask, m));
+        return TTM_OK;
+    }
     std::vector<MaskRun> runs;
     std::vector<int> tap0;
     std::vector<float> taps;
@@ -696,7 +709,7 @@ ttm_status tune_paths(ttm_plan_s* P, cudaStream_t st) {
     const int np = (int)P->prob.size();
     for (int p = 0; p < np; ++p) {
         ProblemData& pr = P->prob[p];
-        if (pr.path != TTM_PATH_FFT) continue;
+        if (pr.path != TTM_PATH_FFT || P->tmpl[pr.tmpl].soft) continue;
         bool shared = false;
         for (int q = 0; q < p && !shared; ++q) {
             const ProblemData& o = P->prob[q];
@@ -905,6 +918,14 @@ ttm_status ttm_plan(ttm_plan_t* out, int n_problems, const int* vol_dims, const 
         const bool fft_ok = fft_length_ok(pr.fft.Xp) && fft_length_ok(pr.fft.Yp) &&
                             fft_length_ok(pr.fft.Zp);
         int path = P->opts.path;
+        if (T.soft) {
+            // soft masks: FFT correlations and FFT window sums only
+            if (path == TTM_PATH_DIRECT || !fft_ok || !fft_template_length(pr.fft.Xp)) {
+                free_plan(P);
+                return TTM_ERR_UNSUPPORTED;
+            }
+            path = TTM_PATH_FFT;
+        }
         if (path == TTM_PATH_TUNE) path = fft_ok ? TTM_PATH_FFT : TTM_PATH_DIRECT;
         if (path == TTM_PATH_AUTO) path = (fft_ok && prefer_fft(P, pr, T)) ? TTM_PATH_FFT : TTM_PATH_DIRECT;
         if (path == TTM_PATH_FFT && !fft_ok) { free_plan(P); return TTM_ERR_UNSUPPORTED; }

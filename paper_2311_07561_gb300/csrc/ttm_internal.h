@@ -18,6 +18,7 @@ struct TemplateData {
     ttm_tt_desc desc{};
     const float* d_comp = nullptr;      // caller-owned K x s^3 components
     float* d_mask = nullptr;            // plan copy of the mask (s^3)
+    bool soft = false;                  // mask values in (0, 1) occur: FFT path only
     std::vector<MaskRun> runs;          // mask as x-runs, sorted by (dz, dy)
     int n_taps = 0;                     // mask voxels
     int dz_min = 0, dz_max = -1, dy_min = 0, dy_max = -1, x_min = 0, x_max = -1;

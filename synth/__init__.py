@@ -24,5 +24,6 @@ from .volumes import (  # noqa: F401
     make_workload,
     plant_copies,
     shoemake_quaternions,
+    soft_ball_mask,
     super_fibonacci_quaternions,
 )

@@ -94,6 +94,16 @@ def ball_mask(s: int, r: Optional[float] = None) -> np.ndarray:
     return ((x * x + y * y + z * z) <= r * r + 1e-9).astype(np.float32)
 
 
+def soft_ball_mask(s: int, r: float, edge: float) -> np.ndarray:
+    """Raised-cosine ball about the box centre: 1 within r - edge of it,
+    falling as cos^2 to 0 at r (a soft mask: weights in [0, 1])."""
+    c = s // 2
+    zz, yy, xx = np.meshgrid(np.arange(s), np.arange(s), np.arange(s), indexing="ij")
+    d = np.sqrt((xx - c) ** 2 + (yy - c) ** 2 + (zz - c) ** 2)
+    t = np.clip((d - (r - edge)) / edge, 0.0, 1.0)
+    return np.where(t >= 1.0, 0.0, np.cos(0.5 * np.pi * t) ** 2).astype(np.float32)
+
+
 def blob_template(s: int, n_blobs: int, seed: int,
                   lowpass_sigma: Optional[float] = None) -> np.ndarray:
     """Asymmetric object: a sum of anisotropic Gaussian blobs (float32 s^3).

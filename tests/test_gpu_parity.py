@@ -294,11 +294,14 @@ def test_gpu_argument_errors(ttm):
     m = synth.ball_mask(s, 4)
     q = synth.super_fibonacci_quaternions(50).astype(np.float32)
     comp, desc = ttm.build_template(t, m, 4, q)
-    # soft mask is not supported by the plan
+    # a soft mask runs on the FFT path only; values outside [0, 1] are rejected
     soft = m * 0.5
     with pytest.raises(ttm.TTMError) as e:
-        ttm.Matcher([(comp, desc, soft)], [((20, 20, 20), 0)])
+        ttm.Matcher([(comp, desc, soft)], [((20, 20, 20), 0)], opts=_opts(ttm, "direct"))
     assert e.value.status == -2
+    with pytest.raises(ttm.TTMError) as e:
+        ttm.Matcher([(comp, desc, m * 2.0)], [((20, 20, 20), 0)])
+    assert e.value.status == -1
     mt = ttm.Matcher([(comp, desc, m)], [((20, 20, 20), 0)])
     vol = _cuda(np.random.default_rng(1).normal(size=(20, 20, 20)))
     small_ws = torch.empty(64, dtype=torch.uint8, device="cuda")
@@ -473,3 +476,29 @@ def test_match_peaks_equals_dense_maps_at_peaks(ttm, path):
         assert np.array_equal(got[f], ref[f]), f
     dense.close()
     sparse.close()
+
+
+def test_soft_mask_fft_path(ttm):
+    """A raised-cosine (soft) mask: the template build, the FFT window sums
+    and the FFT correlations take the mask as weights; w, the components, the
+    score and lambda agree with the oracle, which takes any mask."""
+    wl = synth.make_workload((40, 44, 48), 13, 4, 3, 1.0, 4, 300, radius=6, seeds=(61, 62, 63))
+    m = synth.soft_ball_mask(13, 6, 2.0)
+    assert np.any((m > 0) & (m < 1))
+    T = o.tensor_template(wl.template, m, wl.quadrature.astype(np.float64), wl.weights, 4)
+    comp, desc = ttm.build_template(wl.template, m, 4, wl.quadrature)
+    wl_soft = synth.Workload("soft", wl.volume, wl.template, m, wl.radius, 4, wl.quadrature,
+                             wl.weights, wl.positions, wl.planted_quats, wl.noise_sigma, wl.snr)
+    res = _run(ttm, wl_soft, comp, desc)
+    assert ttm.ttm_plan_problem_path(res["matcher"].plan, 0) == ttm.TTM_PATH_FFT
+    w_o, C_o = o.ttm_components(wl.volume, T, m)
+    nz = w_o > 0
+    assert np.array_equal(res["w"] > 0, nz)
+    assert (np.abs(res["w"][nz] - w_o[nz]) / w_o[nz]).max() <= 1e-5
+    assert np.abs(res["comp"] - C_o).max() <= TOL
+    assert np.abs(res["score"] - o.frobenius_score(C_o, 4)).max() <= TOL
+    pts = np.argwhere(nz)[::61][:150][:, ::-1]
+    _rotation_check(C_o[:, pts[:, 2], pts[:, 1], pts[:, 0]].T,
+                    res["lam"][pts[:, 2], pts[:, 1], pts[:, 0]],
+                    res["quat"][pts[:, 2], pts[:, 1], pts[:, 0]], 4)
+    res["matcher"].close()
