@@ -409,3 +409,32 @@ def test_peaks_match_brute_force_with_ties():
             expect.append((-v, lin))
     expect.sort()
     assert list(got) == [lin for _, lin in expect]
+
+
+def _weighted_corr(a, b, wts):
+    """Weighted Pearson correlation from numpy's weighted covariance."""
+    cv = np.cov(np.stack([a, b]), aweights=wts, bias=True)
+    return cv[0, 1] / math.sqrt(cv[0, 0] * cv[1, 1])
+
+
+def test_soft_mask_ncc_is_weighted_pearson():
+    """With a soft mask m (weights in [0, 1]) the NCC of Sec. 2's S-inner
+    product is the m-weighted Pearson correlation of the window and the
+    rotated template (numpy's weighted covariance as the reference), and it
+    stays in [-1, 1]."""
+    rng = np.random.default_rng(12)
+    f = rng.normal(size=(20, 20, 20))
+    t = synth.blob_template(9, 3, seed=12)
+    m = synth.soft_ball_mask(9, 4, 1.5)
+    assert np.any((m > 0) & (m < 1))
+    q = _rand_quats(2, 12)
+    c = o.classical_ncc(f, t, m, q)
+    assert np.abs(c).max() <= 1.0 + 1e-12
+    wts = m.ravel().astype(np.float64)
+    sel = wts > 0
+    for j in range(2):
+        tr = o.rotate_template(t, q[j]).ravel()
+        for (x, y, z) in [(4, 4, 4), (9, 11, 12), (15, 15, 15)]:
+            win = f[z - 4:z + 5, y - 4:y + 5, x - 4:x + 5].ravel()
+            ref = _weighted_corr(win[sel], tr[sel], wts[sel])
+            assert c[j, z, y, x] == pytest.approx(ref, abs=1e-12)
