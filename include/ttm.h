@@ -118,7 +118,12 @@ typedef struct ttm_plan_opts {
                          /* the search of chunk i+1 (high-priority stream)    */
                          /* beside the refinement of chunk i (low priority);  */
                          /* 0 = default (8), 1 = one search then one refinement */
-    int reserved[3];
+    float lowpass_sigma; /* > 0: the volume is prefiltered by a Gaussian of   */
+                         /* this sigma (voxels, <= 7.9; ttm_lowpass) inside   */
+                         /* ttm_local_stats, ttm_correlate, ttm_match_peaks;  */
+                         /* filter the template the same way before           */
+                         /* ttm_build_tensor_template.  0 = none (h = identity) */
+    int reserved[2];
 } ttm_plan_opts;
 
 typedef struct ttm_plan_s* ttm_plan_t;
@@ -341,6 +346,20 @@ ttm_status ttm_extract_peaks(ttm_plan_t plan, int problem, const float* d_score,
                              const float* d_quat, const float* d_lambda, float threshold,
                              int radius, int max_peaks, ttm_peak* h_out, int* n_out,
                              void* d_workspace, size_t workspace_bytes, void* stream);
+
+/* ---------------------------------------------------------------------------
+ * ttm_lowpass -- the optional isotropic prefilter h of Sec. 2 (t' = h * t,
+ * f' = h * f, h * 1 = 1): a sampled Gaussian of unit sum, radius
+ * int(4 sigma + 0.5) <= 32, applied along x, y and z in turn as a linear
+ * convolution with zero outside the X*Y*Z array (as scipy's gaussian_filter
+ * with mode "constant" and truncate 4).  d_in, d_tmp (scratch) and d_out are
+ * distinct device arrays of X*Y*Z floats.  Use it on a template before
+ * ttm_build_tensor_template when the plan's lowpass_sigma is set; the plan
+ * filters the volumes itself.  Asynchronous.  TTM_ERR_INVALID_ARG for a bad
+ * pointer, size or sigma.
+ * ------------------------------------------------------------------------ */
+ttm_status ttm_lowpass(const float* d_in, int X, int Y, int Z, float sigma, float* d_tmp,
+                       float* d_out, void* stream);
 
 /* ---------------------------------------------------------------------------
  * ttm_match_peaks -- the score map and the rotations at its peaks only (the

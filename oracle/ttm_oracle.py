@@ -12,8 +12,9 @@ Every function cites the passage of Almira, Phelippeau & Martinez-Sanchez,
 
 Readings taken where the paper is silent (each is also listed in the design doc):
 
-* the low-pass filter h is the identity (the paper allows any isotropic h with
-  h*1 = 1, Sec. 2); the mask m is binary or soft, given as an array;
+* the low-pass filter h is the identity unless a Gaussian is asked for
+  (lowpass: sampled, unit sum, zero outside the array; the paper allows any
+  isotropic h with h*1 = 1, Sec. 2); the mask m is binary or soft;
 * rotated templates use trilinear interpolation about the box centre
   floor(s/2), zero outside the box;
 * each rotated copy is masked and S-normalised after rotation (Algorithm 1
@@ -169,6 +170,43 @@ def phi_full(A: np.ndarray, Q: np.ndarray, n: int) -> np.ndarray:
 def frobenius(A: np.ndarray, n: int) -> np.ndarray:
     """Frobenius norm of a full tensor (..., 4, ..., 4) (Sec. 3.4)."""
     return np.sqrt(np.sum(A.reshape(A.shape[:A.ndim - n] + (-1,)) ** 2, axis=-1))
+
+
+# ==========================================================================
+# Optional isotropic low-pass filter h (Sec. 2: t' = h * t and f' = h * f with
+# h * 1 = 1; identity unless asked for)
+# ==========================================================================
+
+def gaussian_kernel(sigma: float) -> np.ndarray:
+    """Sampled Gaussian exp(-d^2 / (2 sigma^2)), d = -r..r with
+    r = int(4 sigma + 0.5), normalised to unit sum (unit DC gain)."""
+    r = int(4.0 * sigma + 0.5)
+    d = np.arange(-r, r + 1, dtype=np.float64)
+    k = np.exp(-0.5 * (d / sigma) ** 2)
+    return k / k.sum()
+
+
+def lowpass(x: np.ndarray, sigma: float) -> np.ndarray:
+    """h * x for the Gaussian h of gaussian_kernel: the same 1D kernel along
+    each axis in turn, linear convolution with zero outside the array."""
+    y = np.asarray(x, dtype=np.float64)
+    k = gaussian_kernel(sigma)
+    r = (len(k) - 1) // 2
+    for axis in range(y.ndim):
+        n = y.shape[axis]
+        out = np.zeros_like(y)
+        for j, kj in enumerate(k):
+            d = j - r                                  # out[i] += k[j] * y[i + d]
+            lo, hi = max(0, -d), min(n, n - d)
+            if hi <= lo:
+                continue
+            src = [slice(None)] * y.ndim
+            dst = [slice(None)] * y.ndim
+            src[axis] = slice(lo + d, hi + d)
+            dst[axis] = slice(lo, hi)
+            out[tuple(dst)] += kj * y[tuple(src)]
+        y = out
+    return y
 
 
 # ==========================================================================

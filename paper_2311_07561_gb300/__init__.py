@@ -35,6 +35,7 @@ from ._binding import (  # noqa: F401
     ttm_device_count,
     ttm_extract_peaks,
     ttm_match_peaks,
+    ttm_lowpass,
     ttm_kernel_class_name,
     ttm_local_stats,
     ttm_plan,

@@ -33,7 +33,7 @@ EXPORTED = (
     "ttm_plan_problem_path", "ttm_plan_problem_fft_box", "ttm_plan_problem_tuning",
     "ttm_plan_problem_tensor_direct",
     "ttm_plan_launch_count", "ttm_plan_destroy",
-    "ttm_local_stats", "ttm_correlate", "ttm_extract_peaks", "ttm_match_peaks",
+    "ttm_local_stats", "ttm_correlate", "ttm_extract_peaks", "ttm_match_peaks", "ttm_lowpass",
     "ttm_plan_enable_timing",
     "ttm_plan_timing", "ttm_kernel_class_name", "ttm_build_tensor_template_noalloc",
     "ttm_plan_device_status", "ttm_classical_workspace_size", "ttm_classical_ncc",
@@ -64,7 +64,7 @@ class PlanOpts(ctypes.Structure):
     _fields_ = [("path", ctypes.c_int), ("precision", ctypes.c_int), ("n_grid", ctypes.c_int),
                 ("n_cells", ctypes.c_int), ("n_candidates", ctypes.c_int),
                 ("newton_steps", ctypes.c_int), ("rotation_chunks", ctypes.c_int),
-                ("reserved", ctypes.c_int * 3)]
+                ("lowpass_sigma", ctypes.c_float), ("reserved", ctypes.c_int * 2)]
 
 
 _lib: Optional[ctypes.CDLL] = None
@@ -101,6 +101,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
                                   ctypes.POINTER(I), P, S, P]),
         "ttm_match_peaks": (I, [P, I, P, P, P, ctypes.c_float, I, I, ctypes.POINTER(Peak),
                                 ctypes.POINTER(I), P, S, P]),
+        "ttm_lowpass": (I, [P, I, I, I, ctypes.c_float, P, P, P]),
         "ttm_plan_enable_timing": (I, [P, I]),
         "ttm_plan_timing": (I, [P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(L), I]),
         "ttm_kernel_class_name": (ctypes.c_char_p, [I]),
@@ -350,3 +351,17 @@ def ttm_match_peaks(plan: int, problem: int, vol, w, score, threshold: float, ra
     _check(st, "ttm_match_peaks")
     raw = np.frombuffer(bytes(buf), dtype=PEAK_DTYPE, count=max(max_peaks, 1))
     return raw[: n.value].copy()
+
+
+def ttm_lowpass(x, sigma: float, tmp=None, out=None, stream=None):
+    """Gaussian prefilter of a float32 cuda array (Z, Y, X) or (s, s, s);
+    returns the filtered array (allocated with torch unless out is given)."""
+    import torch
+    if out is None:
+        out = torch.empty_like(x)
+    if tmp is None:
+        tmp = torch.empty_like(x)
+    Z, Y, X = x.shape
+    _check(load_library().ttm_lowpass(_ptr(x), X, Y, Z, float(sigma), _ptr(tmp), _ptr(out),
+                                      _stream(stream)), "ttm_lowpass")
+    return out

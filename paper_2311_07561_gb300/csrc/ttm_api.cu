@@ -470,6 +470,22 @@ ttm_status check_ws(const ttm_plan_s* P, void* ws, size_t bytes) {
 
 // ---- per-problem steps (shared by the C ABI and the plan-time tuner) ----
 
+// The volume the method works on: vol itself, or h * vol (the plan's
+// Gaussian prefilter, Sec. 2) in the problem's workspace slot.
+ttm_status prefilter(ttm_plan_s* plan, const ProblemData& pr, const float* vol, void* d_workspace,
+                     cudaStream_t st, const float** out) {
+    if (!(plan->opts.lowpass_sigma > 0.f)) {
+        *out = vol;
+        return TTM_OK;
+    }
+    float* dst = (float*)((char*)d_workspace + pr.lp_off);
+    float* tmp = (float*)((char*)dst + align256(pr.nvox() * sizeof(float)));
+    TTM_TRY(launch_lowpass(vol, pr.X, pr.Y, pr.Z, plan->opts.lowpass_sigma, tmp, dst, st,
+                           &plan->launches));
+    *out = dst;
+    return TTM_OK;
+}
+
 // w for one problem (Algorithm 1, image block): FFT window sums when the
 // problem takes the FFT path with a compile-time x length, else run sums.
 ttm_status stats_problem(ttm_plan_s* plan, const ProblemData& pr, const float* vol, float* w,
@@ -888,6 +904,8 @@ ttm_status ttm_plan(ttm_plan_t* out, int n_problems, const int* vol_dims, const 
         if (X < s || Y < s || Z < s) return TTM_ERR_INVALID_ARG;
         if ((size_t)X * Y * Z >= ((size_t)1 << 31)) return TTM_ERR_UNSUPPORTED;
     }
+    if (opts && opts->lowpass_sigma != 0.f && !lowpass_sigma_ok(opts->lowpass_sigma))
+        return TTM_ERR_INVALID_ARG;
     ttm_plan_s* P = new (std::nothrow) ttm_plan_s();
     if (!P) return TTM_ERR_OUT_OF_MEMORY;
     if (opts) P->opts = *opts;
@@ -949,7 +967,13 @@ ttm_status ttm_plan(ttm_plan_t* out, int n_problems, const int* vol_dims, const 
         s_ = tune_paths(P, st);
         if (s_ != TTM_OK) { free_plan(P); return s_; }
     }
-    for (const ProblemData& pr : P->prob) ws = std::max(ws, scratch_bytes(P, pr));
+    const bool lp = P->opts.lowpass_sigma > 0.f;
+    for (ProblemData& pr : P->prob) {
+        // the prefiltered volume and its scratch sit after the problem's scratch
+        const size_t sb = align256(scratch_bytes(P, pr));
+        pr.lp_off = kHeader + sb;
+        ws = std::max(ws, sb + (lp ? 2 * align256(pr.nvox() * sizeof(float)) : 0));
+    }
     P->ws_bytes = kHeader + ws;
     *out = P;
     return TTM_OK;
@@ -1064,8 +1088,11 @@ ttm_status ttm_local_stats(ttm_plan_t plan, const float* const* d_vols, float* c
         if (!d_vols[p] || !d_w[p] || !aligned(d_vols[p], 4) || !aligned(d_w[p], 4))
             return TTM_ERR_INVALID_ARG;
     cudaStream_t st = (cudaStream_t)stream;
-    for (int p = 0; p < np; ++p)
-        TTM_TRY(stats_problem(plan, plan->prob[p], d_vols[p], d_w[p], d_workspace, st));
+    for (int p = 0; p < np; ++p) {
+        const float* vol = nullptr;
+        TTM_TRY(prefilter(plan, plan->prob[p], d_vols[p], d_workspace, st, &vol));
+        TTM_TRY(stats_problem(plan, plan->prob[p], vol, d_w[p], d_workspace, st));
+    }
     return TTM_OK;
 }
 
@@ -1085,7 +1112,9 @@ ttm_status ttm_correlate(ttm_plan_t plan, const float* const* d_vols, const floa
     TTM_CUDA_TRY(cudaMemsetAsync((char*)d_workspace + 32, 0, sizeof(int), st));
     for (int p = 0; p < np; ++p) {
         const ProblemData& pr = plan->prob[p];
-        TTM_TRY(corr_problem(plan, pr, d_vols[p], d_workspace, st));
+        const float* vol = nullptr;
+        TTM_TRY(prefilter(plan, pr, d_vols[p], d_workspace, st, &vol));
+        TTM_TRY(corr_problem(plan, pr, vol, d_workspace, st));
         TTM_TRY(rotation_problem(plan, pr, d_w[p], d_score[p], d_quat[p],
                                  d_lambda ? d_lambda[p] : nullptr,
                                  d_components_out ? d_components_out[p] : nullptr, d_workspace,
@@ -1205,6 +1234,16 @@ ttm_status ttm_extract_peaks(ttm_plan_t plan, int problem, const float* d_score,
     return copy_peaks_to_host(pr, d_count, list, cap, max_peaks, h_out, n_out, st);
 }
 
+ttm_status ttm_lowpass(const float* d_in, int X, int Y, int Z, float sigma, float* d_tmp,
+                       float* d_out, void* stream) {
+    if (!d_in || !d_tmp || !d_out || X < 1 || Y < 1 || Z < 1) return TTM_ERR_INVALID_ARG;
+    if (d_in == d_out || d_in == d_tmp || d_tmp == d_out) return TTM_ERR_INVALID_ARG;
+    if (!aligned(d_in, 4) || !aligned(d_tmp, 4) || !aligned(d_out, 4)) return TTM_ERR_INVALID_ARG;
+    if (!lowpass_sigma_ok(sigma)) return TTM_ERR_INVALID_ARG;
+    long long cnt = 0;
+    return launch_lowpass(d_in, X, Y, Z, sigma, d_tmp, d_out, (cudaStream_t)stream, &cnt);
+}
+
 ttm_status ttm_match_peaks(ttm_plan_t plan, int problem, const float* d_vol, const float* d_w,
                            float* d_score, float threshold, int radius, int max_peaks,
                            ttm_peak* h_out, int* n_out, void* d_workspace, size_t workspace_bytes,
@@ -1232,7 +1271,9 @@ ttm_status ttm_match_peaks(ttm_plan_t plan, int problem, const float* d_vol, con
     const int cap = (int)peak_cap(nv);
     const VoxBox box = interior_box(pr.X, pr.Y, pr.Z, T.desc.s);
     TTM_CUDA_TRY(cudaMemsetAsync(ws + 16, 0, 32, st));       // peak count, status word
-    TTM_TRY(corr_problem(plan, pr, d_vol, d_workspace, st));
+    const float* vol = nullptr;
+    TTM_TRY(prefilter(plan, pr, d_vol, d_workspace, st, &vol));
+    TTM_TRY(corr_problem(plan, pr, vol, d_workspace, st));
     TTM_TRY(timed(plan, KC_ROTATION, st, [&] {
         return launch_score_only(plan->n_order, corr, pr.mixed, d_w, pr.X, pr.Y, pr.Z, box,
                                  d_score, st, &plan->launches);

@@ -54,6 +54,7 @@ struct ProblemData {
     bool tc_direct = false;            // direct path on the tensor cores (FP16 operands)
     int spec_index = -1;               // template spectra set used (FFT path)
     double tune_ms[2] = {-1.0, -1.0};  // autotuner: direct, FFT (ms), -1 = not timed
+    size_t lp_off = 0;                 // workspace offset of the prefiltered volume (+ scratch)
     size_t nvox() const { return (size_t)X * Y * Z; }
 };
 
@@ -160,6 +161,12 @@ inline size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
 // sum f and sum f^2 over a whole volume into d_acc[0..1] (FP64, must be zeroed)
 ttm_status launch_volume_moments(const float* f, size_t n, double* d_acc, cudaStream_t st,
                                  long long* cnt);
+
+// Gaussian prefilter (k_lowpass.cu): out = h * in, tmp is scratch of the
+// same size; in, tmp and out must be distinct
+bool lowpass_sigma_ok(float sigma);
+ttm_status launch_lowpass(const float* in, int X, int Y, int Z, float sigma, float* tmp,
+                          float* out, cudaStream_t st, long long* cnt);
 
 // deterministic pseudo-random values in [-1, 1) (autotuner input)
 ttm_status launch_fill_random(float* f, size_t n, uint32_t seed, cudaStream_t st, long long* cnt);

@@ -502,3 +502,27 @@ def test_soft_mask_fft_path(ttm):
                     res["lam"][pts[:, 2], pts[:, 1], pts[:, 0]],
                     res["quat"][pts[:, 2], pts[:, 1], pts[:, 0]], 4)
     res["matcher"].close()
+
+
+@pytest.mark.parametrize("path", PATHS)
+def test_gaussian_prefilter(ttm, path):
+    """The optional prefilter h (Sec. 2): ttm_lowpass on the template and the
+    plan's lowpass_sigma on the volume give the oracle's components of h * f
+    against the tensor template of h * t."""
+    wl = synth.make_workload((40, 44, 48), 11, 4, 3, 1.0, 4, 300, radius=5, seeds=(71, 72, 73))
+    sigma = 1.2
+    tf = ttm.ttm_lowpass(_cuda(wl.template), sigma).cpu().numpy()
+    t_o = o.lowpass(wl.template, sigma)
+    assert np.abs(tf - t_o).max() <= 1e-6 * np.abs(t_o).max()
+    comp, desc = ttm.build_template(tf, wl.mask, 4, wl.quadrature)
+    o_ = _opts(ttm, path)
+    o_.lowpass_sigma = sigma
+    res = _run(ttm, wl, comp, desc, opts=o_)
+    T = o.tensor_template(t_o, wl.mask, wl.quadrature.astype(np.float64), wl.weights, 4)
+    w_o, C_o = o.ttm_components(o.lowpass(wl.volume, sigma), T, wl.mask)
+    nz = w_o > 0
+    assert np.array_equal(res["w"] > 0, nz)
+    assert (np.abs(res["w"][nz] - w_o[nz]) / w_o[nz]).max() <= 1e-5
+    assert np.abs(res["comp"] - C_o).max() <= TOL
+    assert np.abs(res["score"] - o.frobenius_score(C_o, 4)).max() <= TOL
+    res["matcher"].close()

@@ -438,3 +438,20 @@ def test_soft_mask_ncc_is_weighted_pearson():
             win = f[z - 4:z + 5, y - 4:y + 5, x - 4:x + 5].ravel()
             ref = _weighted_corr(win[sel], tr[sel], wts[sel])
             assert c[j, z, y, x] == pytest.approx(ref, abs=1e-12)
+
+
+def test_lowpass_is_scipy_gaussian_filter_with_unit_gain():
+    """The optional prefilter h of Sec. 2: the oracle's separable Gaussian
+    equals scipy.ndimage.gaussian_filter (zero outside, truncated at 4 sigma);
+    h * 1 = 1 away from the borders (unit DC gain, Sec. 2) and h is even."""
+    from scipy import ndimage
+    rng = np.random.default_rng(21)
+    x = rng.normal(size=(14, 17, 19))
+    for sigma in (0.8, 1.0, 2.3):
+        ref = ndimage.gaussian_filter(x, sigma, mode="constant", cval=0.0, truncate=4.0)
+        assert np.abs(o.lowpass(x, sigma) - ref).max() <= 1e-12
+        k = o.gaussian_kernel(sigma)
+        assert k.sum() == pytest.approx(1.0, abs=1e-15) and np.allclose(k, k[::-1])
+    ones = o.lowpass(np.ones((30, 30, 30)), 1.5)
+    r = int(4 * 1.5 + 0.5)
+    assert np.abs(ones[r:-r, r:-r, r:-r] - 1.0).max() <= 1e-12
