@@ -119,12 +119,12 @@ __device__ __forceinline__ int select_bits(int a, int c) {
     return d;
 }
 
-// key[j] = (r[j] & ~2047) | (15 - j % 16) for j = J..63 (compile-time j)
-template <int J>
-__device__ __forceinline__ void pack_keys(int (&key)[64], const uint32_t (&r)[64], int mask) {
-    if constexpr (J < 64) {
+// key[j] = (r[j] & ~2047) | (15 - j % 16) for j = J..M-1 (compile-time j)
+template <int J, int M>
+__device__ __forceinline__ void pack_keys(int (&key)[M], const uint32_t (&r)[M], int mask) {
+    if constexpr (J < M) {
         key[J] = select_bits<15 - (J & 15)>((int)r[J], mask);
-        pack_keys<J + 1>(key, r, mask);
+        pack_keys<J + 1, M>(key, r, mask);
     }
 }
 
@@ -172,43 +172,59 @@ __device__ __forceinline__ void bulk_load(uint32_t dst, const void* src, uint32_
         : "memory");
 }
 
-__device__ __forceinline__ void tmem_ld64(uint32_t addr, uint32_t (&r)[64]) {
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x64.b32 "
-        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,"
-        "%32,%33,%34,%35,%36,%37,%38,%39,%40,%41,%42,%43,%44,%45,%46,%47,"
-        "%48,%49,%50,%51,%52,%53,%54,%55,%56,%57,%58,%59,%60,%61,%62,%63}, [%64];\n"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
-          "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]),
-          "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
-          "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]),
-          "=r"(r[31]), "=r"(r[32]), "=r"(r[33]), "=r"(r[34]), "=r"(r[35]), "=r"(r[36]),
-          "=r"(r[37]), "=r"(r[38]), "=r"(r[39]), "=r"(r[40]), "=r"(r[41]), "=r"(r[42]),
-          "=r"(r[43]), "=r"(r[44]), "=r"(r[45]), "=r"(r[46]), "=r"(r[47]), "=r"(r[48]),
-          "=r"(r[49]), "=r"(r[50]), "=r"(r[51]), "=r"(r[52]), "=r"(r[53]), "=r"(r[54]),
-          "=r"(r[55]), "=r"(r[56]), "=r"(r[57]), "=r"(r[58]), "=r"(r[59]), "=r"(r[60]),
-          "=r"(r[61]), "=r"(r[62]), "=r"(r[63])
-        : "r"(addr)
-        : "memory");
-    asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
-}
-
+// 32 TMEM columns of this warp's 32 lanes into r; the copy completes at
+// tmem_wait32, which names r as modified so nothing reads r before it
 __device__ __forceinline__ void tmem_ld32(uint32_t addr, uint32_t (&r)[32]) {
     asm volatile(
         "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
         "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
         "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
-          "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]),
-          "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
-          "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]),
-          "=r"(r[31])
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]),
+          "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]),
+          "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]),
+          "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]),
+          "=r"(r[30]), "=r"(r[31])
         : "r"(addr)
         : "memory");
-    asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_wait32(uint32_t (&r)[32]) {
+    asm volatile("tcgen05.wait::ld.sync.aligned;\n"
+                 : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]),
+                   "+r"(r[6]), "+r"(r[7]), "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]),
+                   "+r"(r[12]), "+r"(r[13]), "+r"(r[14]), "+r"(r[15]), "+r"(r[16]), "+r"(r[17]),
+                   "+r"(r[18]), "+r"(r[19]), "+r"(r[20]), "+r"(r[21]), "+r"(r[22]), "+r"(r[23]),
+                   "+r"(r[24]), "+r"(r[25]), "+r"(r[26]), "+r"(r[27]), "+r"(r[28]), "+r"(r[29]),
+                   "+r"(r[30]), "+r"(r[31])
+                 :
+                 : "memory");
+}
+
+// 32 columns = 2 regions of 16 -> their best keys n0, n1.  phi + 1 >= 0
+// (|phi| <= 1 for unit-norm C), so its float bits order like the values; the
+// low 11 bits become the code 2047 - g of the grid index g: first only the
+// position in the region (15 - j, one LOP3 per value), the region part (low0 =
+// 2047 - grid index of column 0) is added to each region's maximum
+__device__ __forceinline__ void region_max32(const uint32_t (&r)[32], int low0, int& n0, int& n1) {
+    int key[32];
+    pack_keys<0, 32>(key, r, ~2047);
+    int nk[2];
+#pragma unroll
+    for (int q2 = 0; q2 < 2; ++q2) {
+        // three-input integer maxima, 16 -> 6 -> 2 -> 1
+        const int* k16 = key + 16 * q2;
+        const int m0 = __vimax3_s32(k16[0], k16[1], k16[2]);
+        const int m1 = __vimax3_s32(k16[3], k16[4], k16[5]);
+        const int m2 = __vimax3_s32(k16[6], k16[7], k16[8]);
+        const int m3 = __vimax3_s32(k16[9], k16[10], k16[11]);
+        const int m4 = __vimax3_s32(k16[12], k16[13], k16[14]);
+        const int a0 = __vimax3_s32(m0, m1, m2);
+        const int a1 = __vimax3_s32(m3, m4, k16[15]);
+        nk[q2] = max(a0, a1) + (low0 - 16 * q2 - 15);
+    }
+    n0 = nk[0];
+    n1 = nk[1];
 }
 
 template <typename CT, int N>
@@ -355,63 +371,67 @@ __global__ void __launch_bounds__(kThreads, 1) search_tc_kernel(rot::SearchArgs 
         int top[rot::kMaxCand];
 #pragma unroll
         for (int k = 0; k < rot::kMaxCand; ++k) top[k] = INT_MIN;
-        for (int c = 0; c < kChunks; ++c) {
-            const int h = c & 1;
-            const long q = qbase + c;
-            if (c + 1 < kChunks && t == 0)
-                issue(tmem + (uint32_t)((c + 1) & 1) * kChunkN, c + 1, q + 1,
-                      ((c + 1) & 1) ? bar1 : bar0);
-            // no block barrier per chunk: warps move on independently; the
-            // TMEM-half barriers tell thread 0 when a half may be overwritten
-            if (!mbar_wait(h ? bar1 : bar0, (phase >> h) & 1u)) { ok = false; break; }
-            phase ^= 1u << h;
-            if (t == 0) mma_pending &= ~(1u << h);
-            // the MMAs of chunk q are done: its buffer takes chunk q + 2
-            if (kStream && t == 0 && (c + 2 < kChunks || more_tiles)) {
-                const int buf = (int)(q & 1);
-                const int nxt = (c + 2) % kChunks;
+        // MMAs of chunk cc done (bounded wait); with a streamed table its
+        // buffer then takes chunk cc + 2
+        auto wait_chunk = [&](int cc) -> bool {
+            const int hh = cc & 1;
+            if (!mbar_wait(hh ? bar1 : bar0, (phase >> hh) & 1u)) return false;
+            phase ^= 1u << hh;
+            if (t == 0) mma_pending &= ~(1u << hh);
+            if (kStream && t == 0 && (cc + 2 < kChunks || more_tiles)) {
+                const int buf = (int)((qbase + cc) & 1);
+                const int nxt = (cc + 2) % kChunks;
                 asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
                 bulk_load(b_base + (uint32_t)buf * Sh::ChunkBytes,
                           gsrc + (size_t)nxt * Sh::ChunkBytes, Sh::ChunkBytes, ((buf) ? lbar1 : lbar0));
                 loads_pending |= 1u << buf;
             }
             asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-            const uint32_t col0 = tmem + ((uint32_t)((warp & 3) * 32) << 16) +
-                                  (uint32_t)h * kChunkN + (uint32_t)grp * (kChunkN / kGroups);
+            return true;
+        };
+        // this warp's 32 lanes, its column group, TMEM half hh
+        auto cols = [&](int hh) {
+            return tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)hh * kChunkN +
+                   (uint32_t)grp * (kChunkN / kGroups);
+        };
+        // each chunk is read as four loads of 32 columns, the next one in
+        // flight while the previous one is reduced (a load of the next chunk
+        // during the last one measured faster alone but needs ~160 registers,
+        // which leaves no room for the refinement kernel running beside this
+        // one); four region maxima at a time go into the top-8 list
+        static_assert(kChunkN / kGroups == 128, "four 32-column loads per chunk");
+        uint32_t ra[32], rb[32];
 #pragma unroll 1
-            for (int p = 0; p < kChunkN / kGroups / 64; ++p) {
-                uint32_t r[64];
-                tmem_ld64(col0 + (uint32_t)p * 64, r);
-                // 64 columns = 4 regions of 16.  phi + 1 >= 0 (|phi| <= 1 for
-                // unit-norm C), so its float bits order like the values; the
-                // low 11 bits become the code 2047 - g of the grid index g:
-                // first only the position in the region (15 - j, one LOP3 per
-                // value), the region part is added to each region's maximum
-                const int low0 = 2047 - (c * kChunkN + grp * (kChunkN / kGroups) + p * 64);
-                int key[64];
-                pack_keys<0>(key, r, ~2047);
-                // region maxima with three-input integer maxima (16 -> 6 -> 2 -> 1)
-                int nk[4];
-#pragma unroll
-                for (int q4 = 0; q4 < 4; ++q4) {
-                    const int* k16 = key + 16 * q4;
-                    const int m0 = __vimax3_s32(k16[0], k16[1], k16[2]);
-                    const int m1 = __vimax3_s32(k16[3], k16[4], k16[5]);
-                    const int m2 = __vimax3_s32(k16[6], k16[7], k16[8]);
-                    const int m3 = __vimax3_s32(k16[9], k16[10], k16[11]);
-                    const int m4 = __vimax3_s32(k16[12], k16[13], k16[14]);
-                    const int n0 = __vimax3_s32(m0, m1, m2);
-                    const int n1 = __vimax3_s32(m3, m4, k16[15]);
-                    nk[q4] = max(n0, n1) + (low0 - 16 * q4 - 15);
-                }
-                cx(nk[0], nk[1]); cx(nk[2], nk[3]); cx(nk[0], nk[2]); cx(nk[1], nk[3]); cx(nk[1], nk[2]);
-                merge4(top, nk);
-            }
-            // this warp has read half h: chunk c + 2 may overwrite it
+        for (int c = 0; c < kChunks && ok; ++c) {
+            const int h = c & 1;
+            if (c + 1 < kChunks && t == 0)
+                issue(tmem + (uint32_t)((c + 1) & 1) * kChunkN, c + 1, qbase + c + 1,
+                      ((c + 1) & 1) ? bar1 : bar0);
+            if (!wait_chunk(c)) { ok = false; break; }
+            tmem_ld32(cols(h), ra);
+            const int low0 = 2047 - (c * kChunkN + grp * (kChunkN / kGroups));
+            int nk[4];
+            tmem_wait32(ra);
+            tmem_ld32(cols(h) + 32, rb);
+            region_max32(ra, low0, nk[0], nk[1]);
+            tmem_wait32(rb);
+            tmem_ld32(cols(h) + 64, ra);
+            region_max32(rb, low0 - 32, nk[2], nk[3]);
+            cx(nk[0], nk[1]); cx(nk[2], nk[3]); cx(nk[0], nk[2]); cx(nk[1], nk[3]); cx(nk[1], nk[2]);
+            merge4(top, nk);
+            tmem_wait32(ra);
+            tmem_ld32(cols(h) + 96, rb);
+            region_max32(ra, low0 - 64, nk[0], nk[1]);
+            tmem_wait32(rb);
+            // no block barrier per chunk: warps move on independently; this
+            // warp has read half h, so chunk c + 2 may overwrite it
             asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
             __syncwarp();
             if ((t & 31) == 0)
                 asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(((h) ? ebar1 : ebar0)) : "memory");
+            region_max32(rb, low0 - 96, nk[2], nk[3]);
+            cx(nk[0], nk[1]); cx(nk[2], nk[3]); cx(nk[0], nk[2]); cx(nk[1], nk[3]); cx(nk[1], nk[2]);
+            merge4(top, nk);
         }
         if (!__syncthreads_and(ok)) {
             ok = false;
