@@ -72,8 +72,8 @@ NCU_TRAFFIC: dict = {
     # chunks); reported only while the kernels' sources are unchanged
     "rotation_polish": dict(bytes_per_launch=round((193201664 + 9929728) / 912673 * 11390625 / 8),
                             source_sha="9cb54c7dd779"),
-    "rotation_search": dict(bytes_per_launch=round((173783808 + 12625152) / 912673 * 11390625 / 8),
-                            source_sha="9aef777fc0c0"),
+    "rotation_search": dict(bytes_per_launch=round((173783808 + 12853504) / 912673 * 11390625 / 8),
+                            source_sha="5838b9469595"),
 }
 
 
@@ -103,6 +103,10 @@ def parse():
     ap.add_argument("--cpu-sample", type=int, default=0,
                     help="internal: run the oracle on this many sampled voxels and print JSON")
     ap.add_argument("--sample-steps", type=int, default=1)
+    ap.add_argument("--order-sweep", action="store_true",
+                    help="rotation error at the planted copies of the 256^3 volume against the "
+                         "tensor order n and the quadrature size, beside classical NCC at 1000 "
+                         "and 7112 sampled rotations; prints its own JSON line")
     args = ap.parse_args()
     if args.precision is None:
         args.precision = "mixed" if args.workload == "c5" else "fp32"
@@ -775,6 +779,114 @@ def run_reference(args) -> None:
     print(json.dumps(line), flush=True)
 
 
+# ---------------------------------------------------------------------------
+# order / quadrature sweep (Sec. 3: the tensor order n and the quadrature of
+# the tensor template set the rotation accuracy; Sec. 5 compares against
+# classical matching at 7112 and 45123 sampled rotations)
+# ---------------------------------------------------------------------------
+
+SWEEP_TTM = ((2, 10000), (4, 1000), (4, 10000), (4, 20000), (6, 10000), (6, 20000), (8, 10000))
+SWEEP_CLASSICAL = (1000, 7112)
+
+
+def _angle_deg(q1, q2):
+    """Angle of the rotation q1^-1 q2 for unit quaternions (q and -q alike)."""
+    import numpy as np
+    d = np.abs(np.sum(np.asarray(q1, np.float64) * np.asarray(q2, np.float64), axis=-1))
+    return np.degrees(2.0 * np.arccos(np.clip(d, 0.0, 1.0)))
+
+
+def _err_stats(ang):
+    import numpy as np
+    return dict(median_deg=round(float(np.median(ang)), 3),
+                p90_deg=round(float(np.percentile(ang, 90)), 3),
+                max_deg=round(float(np.max(ang)), 3),
+                within_1deg=round(float(np.mean(ang <= 1.0)), 3),
+                within_5deg=round(float(np.mean(ang <= 5.0)), 3))
+
+
+def run_order_sweep(args) -> None:
+    import numpy as np
+    import torch
+
+    import paper_2311_07561_gb300 as ttm
+    import synth
+
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(0)
+    if not os.path.exists(ttm.LIB_PATH):
+        import __graft_entry__
+        __graft_entry__.build()
+    ttm.load_library()
+    wl = load_workload("c2")
+    Z, Y, X = wl.volume.shape
+    nvox = X * Y * Z
+    pos = wl.positions                       # (P, 3) as (x, y, z)
+    truth = wl.planted_quats
+    vol = torch.from_numpy(wl.volume).to(dev)
+    stream = torch.cuda.current_stream()
+    steps = max(1, args.steps)
+    rows = []
+    for n, n_rot in SWEEP_TTM:
+        quad = synth.super_fibonacci_quaternions(n_rot).astype(np.float32)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        comp, desc = ttm.build_template(wl.template, wl.mask, n, quad)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        build_ms = e0.elapsed_time(e1)
+        m = ttm.Matcher([(comp, desc, wl.mask)], [((X, Y, Z), 0)])
+        for _ in range(max(1, args.warmup)):
+            m.run([vol])
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(steps):
+            m.run([vol])
+        b.record(stream)
+        b.synchronize()
+        ms = a.elapsed_time(b) / steps
+        status = ttm.ttm_plan_device_status(m.plan, m.ws)
+        if status != 0:
+            raise RuntimeError(f"device status {ttm.ttm_status_string(status)}")
+        q = m.quat[0].cpu().numpy()[pos[:, 2], pos[:, 1], pos[:, 0]]
+        rows.append(dict(n=n, K=desc.K, quadrature_rotations=n_rot, template_build_ms=round(build_ms, 1),
+                         ms_per_step=round(ms, 3), voxels_per_s=nvox / (ms * 1e-3),
+                         rotation_error=_err_stats(_angle_deg(q, truth))))
+        m.close()
+        del comp
+        torch.cuda.empty_cache()
+    # classical matching on the same volume: the best of R sampled rotations
+    opts = ttm.PlanOpts()
+    opts.path = ttm.TTM_PATH_FFT
+    comp, desc = ttm.build_template(wl.template, wl.mask, 4, wl.quadrature)
+    m = ttm.Matcher([(comp, desc, wl.mask)], [((X, Y, Z), 0)], opts=opts)
+    ttm.ttm_local_stats(m.plan, [vol], m.w, m.ws)
+    tc = torch.from_numpy(wl.template).to(dev)
+    best = torch.empty((Z, Y, X), dtype=torch.float32, device=dev)
+    barg = torch.empty((Z, Y, X), dtype=torch.int32, device=dev)
+    cws = torch.empty(ttm.ttm_classical_workspace_size(m.plan, 0), dtype=torch.uint8, device=dev)
+    classical = []
+    for R in SWEEP_CLASSICAL:
+        qs = synth.shoemake_quaternions(R, 4).astype(np.float32)
+        qc = torch.from_numpy(qs).to(dev)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        ttm.ttm_classical_ncc(m.plan, 0, tc, qc, R, vol, m.w[0], best, barg, cws)
+        b.record(stream)
+        b.synchronize()
+        j = barg.cpu().numpy()[pos[:, 2], pos[:, 1], pos[:, 0]]
+        classical.append(dict(rotations=R, ms_per_volume=round(a.elapsed_time(b), 2),
+                              rotation_error=_err_stats(_angle_deg(qs[j], truth))))
+    m.close()
+    line = dict(metric="rotation error at planted copies vs tensor order and quadrature size",
+                unit="degrees", data="synthetic",
+                config=dict(workload=WORKLOAD["c2"], copies=int(len(pos)), path="auto",
+                            rotation_grid=2048, classical_rotations="Shoemake-uniform random"),
+                ttm=rows, classical=classical)
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.cpu_sample:
@@ -782,6 +894,8 @@ def main():
         return
     if args.impl == "reference":
         run_reference(args)
+    elif args.order_sweep:
+        run_order_sweep(args)
     elif args.workload in BATCH_WORKLOADS:
         run_batch(args)
     else:

@@ -125,8 +125,8 @@ def test_components_and_score_match_oracle(c1):
     assert np.all(c1["res"]["lam"][~keep] == 0)
 
 
-def _rotation_check(C_o_pts, lam, q, n, planted=()):
-    lam_o, q_o = o.dominant_z_eigenpair(C_o_pts, n)
+def _rotation_check(C_o_pts, lam, q, n, planted=(), eig_o=None):
+    lam_o, q_o = o.dominant_z_eigenpair(C_o_pts, n) if eig_o is None else eig_o
     dl = np.abs(lam - lam_o)
     assert dl.max() <= TOL, (dl.max(), np.argmax(dl))
     # the reported rotation attains the reported value and the maximum
@@ -235,6 +235,33 @@ def test_order_six(ttm, path):
     _rotation_check(C_o[:, pts[:, 2], pts[:, 1], pts[:, 0]].T,
                     res["lam"][pts[:, 2], pts[:, 1], pts[:, 0]],
                     res["quat"][pts[:, 2], pts[:, 1], pts[:, 0]], 6)
+
+
+@pytest.fixture(scope="module")
+def order8_oracle():
+    """n = 8 (K = 165), the largest supported order: the oracle's maps, and
+    its rotation at five sampled voxels (SS-HOPM converges slowly at this
+    order, ~7 s per voxel, so both paths share them)."""
+    wl = synth.make_workload((26, 24, 22), 7, 3, 1, 1.0, 8, 400, radius=3, seeds=(5, 6, 7))
+    T = o.tensor_template(wl.template, wl.mask, wl.quadrature.astype(np.float64), wl.weights, 8)
+    w_o, C_o = o.ttm_components(wl.volume, T, wl.mask)
+    pts = np.argwhere(w_o > 0)[::1151][:5][:, ::-1]
+    C_pts = C_o[:, pts[:, 2], pts[:, 1], pts[:, 0]].T
+    return dict(wl=wl, C_o=C_o, pts=pts, C_pts=C_pts, eig=o.dominant_z_eigenpair(C_pts, 8))
+
+
+@pytest.mark.parametrize("path", PATHS)
+def test_order_eight(ttm, order8_oracle, path):
+    d = order8_oracle
+    wl, C_o, pts = d["wl"], d["C_o"], d["pts"]
+    comp, desc = ttm.build_template(wl.template, wl.mask, 8, wl.quadrature)
+    assert desc.K == 165
+    res = _run(ttm, wl, comp, desc, opts=_opts(ttm, path))
+    assert np.abs(res["comp"] - C_o).max() <= TOL
+    assert np.abs(res["score"] - o.frobenius_score(C_o, 8)).max() <= TOL
+    _rotation_check(d["C_pts"], res["lam"][pts[:, 2], pts[:, 1], pts[:, 0]],
+                    res["quat"][pts[:, 2], pts[:, 1], pts[:, 0]], 8, eig_o=d["eig"])
+    res["matcher"].close()
 
 
 @pytest.mark.parametrize("path", PATHS)
