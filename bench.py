@@ -242,6 +242,22 @@ def source_hash(names) -> str:
     return h.hexdigest()[:12]
 
 
+def max_over_ranks(ms: float, dist=None, device="cpu") -> float:
+    """The largest of every rank's value (a replicated job ends with its
+    slowest rank); the value itself on a single process."""
+    if dist is None:
+        return ms
+    import torch
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(units_per_rank: float, steps: int, world: int, t_max_ms: float) -> float:
+    """Units all ranks processed per second of the slowest rank's time."""
+    return units_per_rank * steps * world / (t_max_ms * 1e-3)
+
+
 def roofline(kernels: dict, steps: int, nvox: int, K: int, n_taps: int, n_grid: int,
              n_cand: int, newton: int, peaks: dict, spectrum_bytes: float = 0.0,
              n_interior: int | None = None, tc_direct: bool = False) -> dict:
@@ -378,12 +394,8 @@ def run_ours(args) -> None:
     launches = matcher.launch_count() - launches0
     kern = {name: dict(ms=ms, launches=n) for name, (ms, n) in ttm.ttm_plan_timing(matcher.plan).items()}
     ttm.ttm_plan_enable_timing(matcher.plan, False)
-    t_max = total_ms
-    if dist:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_max = float(t.item())
-    value = nvox * args.steps * world / (t_max * 1e-3)
+    t_max = max_over_ranks(total_ms, dist, dev)
+    value = job_rate(nvox, args.steps, world, t_max)
 
     # end to end through the public API: pinned host volume in, maps out.
     # With depth > 1 consecutive steps run on HostPipeline's streams, so step
@@ -440,11 +452,8 @@ def run_ours(args) -> None:
                     raise RuntimeError(f"device status {ttm.ttm_status_string(st_)}")
             pipe.close()
             del outs
-        if dist:
-            t = torch.tensor([e_ms], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e_ms = float(t.item())
-        e2e = dict(value=nvox * args.steps * world / (e_ms * 1e-3), unit=UNIT,
+        e_ms = max_over_ranks(e_ms, dist, dev)
+        e2e = dict(value=job_rate(nvox, args.steps, world, e_ms), unit=UNIT,
                    h2d_bytes_per_step=nvox * 4, d2h_bytes_per_step=nvox * 4 * 6,
                    pipeline_depth=depth,
                    note="pinned host volume in, score + quaternion + lambda maps out, every step"
@@ -497,7 +506,8 @@ def run_ours(args) -> None:
             b.record(stream)
             b.synchronize()
             p_ms += a.elapsed_time(b)
-        peaks_only = dict(value=nvox * args.steps * world / (p_ms * 1e-3), unit=UNIT,
+        p_ms = max_over_ranks(p_ms, dist, dev)
+        peaks_only = dict(value=job_rate(nvox, args.steps, world, p_ms), unit=UNIT,
                           ms_per_step=p_ms / args.steps, peaks=int(len(recs)),
                           threshold=0.0, nms_radius=radius,
                           note="local statistics, K correlations, score map, peaks "
@@ -525,7 +535,8 @@ def run_ours(args) -> None:
             m_ms += a.elapsed_time(b)
         dscore = float((m2.score[0] - matcher.score[0]).abs().max())
         dlam = float((m2.lam[0] - matcher.lam[0]).abs().max())
-        mixed = dict(value=nvox * args.steps * world / (m_ms * 1e-3), unit=UNIT,
+        m_ms = max_over_ranks(m_ms, dist, dev)
+        mixed = dict(value=job_rate(nvox, args.steps, world, m_ms), unit=UNIT,
                      ms_per_step=m_ms / args.steps, storage="bf16 spectra, products, maps",
                      max_abs_diff_vs_fp32=dict(score=dscore, **{"lambda": dlam}))
         m2.close()
@@ -655,12 +666,8 @@ def run_batch(args) -> None:
     if status != 0:
         raise RuntimeError(f"device status {ttm.ttm_status_string(status)}")
     total_ms = sum(a.elapsed_time(b) for a, b in zip(starts, stops))
-    t_max = total_ms
-    if dist:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_max = float(t.item())
-    value = nvox_total * args.steps * world / (t_max * 1e-3)
+    t_max = max_over_ranks(total_ms, dist, dev)
+    value = job_rate(nvox_total, args.steps, world, t_max)
 
     # per-kernel breakdown from one eager step outside the timed region
     ttm.ttm_plan_timing(matcher.plan)
@@ -702,11 +709,8 @@ def run_batch(args) -> None:
             b.record(stream)
             b.synchronize()
             e_ms += a.elapsed_time(b)
-        if dist:
-            t = torch.tensor([e_ms], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e_ms = float(t.item())
-        e2e = dict(value=nvox_total * args.steps * world / (e_ms * 1e-3), unit=UNIT,
+        e_ms = max_over_ranks(e_ms, dist, dev)
+        e2e = dict(value=job_rate(nvox_total, args.steps, world, e_ms), unit=UNIT,
                    h2d_bytes_per_step=h2d, d2h_bytes_per_step=d2h)
 
     if rank != 0:
