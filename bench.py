@@ -62,17 +62,16 @@ def load_workload(name: str, **extra):
 FP32_ALU_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # SMs x FP32 lanes x FMA x max clock
 L2_FLUSH_BYTES = 256 << 20
 
-# Measured DRAM traffic of a kernel class from one ncu capture (bytes per
-# launch scaled to the bench workload) with the hash of the sources it was
-# taken on; reported only while those sources are unchanged.
+# Measured DRAM traffic of a kernel class from one ncu capture, per interior
+# voxel, with the hash of the sources it was taken on; reported (times the
+# interior voxels of one launch) only while those sources are unchanged and
+# for the captured kind of launch: order 4 (K = 35) over FP32 maps.
 NCU_TRAFFIC: dict = {
     # ncu (dram__bytes_read.sum + dram__bytes_write.sum) of the 128^3 case,
-    # 912 673 interior voxels in one launch each, scaled by interior voxels to
-    # one launch of the 256^3 bench workload (11 390 625 interior voxels in 8
-    # chunks); reported only while the kernels' sources are unchanged
-    "rotation_polish": dict(bytes_per_launch=round((193201664 + 9929728) / 912673 * 11390625 / 8),
+    # 912 673 interior voxels in one launch each
+    "rotation_polish": dict(bytes_per_voxel=(193201664 + 9929728) / 912673, K=35,
                             source_sha="9cb54c7dd779"),
-    "rotation_search": dict(bytes_per_launch=round((173783808 + 12853504) / 912673 * 11390625 / 8),
+    "rotation_search": dict(bytes_per_voxel=(173783808 + 12853504) / 912673, K=35,
                             source_sha="5838b9469595"),
 }
 
@@ -260,7 +259,8 @@ def job_rate(units_per_rank: float, steps: int, world: int, t_max_ms: float) -> 
 
 def roofline(kernels: dict, steps: int, nvox: int, K: int, n_taps: int, n_grid: int,
              n_cand: int, newton: int, peaks: dict, spectrum_bytes: float = 0.0,
-             n_interior: int | None = None, tc_direct: bool = False) -> dict:
+             n_interior: int | None = None, tc_direct: bool = False,
+             fp32_maps: bool = True) -> dict:
     """Roofline object for the kernel class with the largest share.  The
     rotation kernels visit only the interior voxels (n_interior)."""
     n_int = nvox if n_interior is None else n_interior
@@ -316,8 +316,9 @@ def roofline(kernels: dict, steps: int, nvox: int, K: int, n_taps: int, n_grid: 
     achieved = work / (ms_launch * 1e-3) / scale
     traffic = None
     rec = NCU_TRAFFIC.get(name)
-    if rec and src and rec.get("source_sha") == source_hash(src):
-        traffic = rec["bytes_per_launch"]
+    if (rec and src and fp32_maps and rec["K"] == K
+            and rec.get("source_sha") == source_hash(src)):
+        traffic = round(rec["bytes_per_voxel"] * n_int / launches_per_step)
     return dict(kernel=name, bound=bound, achieved=round(achieved, 3), peak=round(peak, 2),
                 unit=unit, frac=round(achieved / peak, 4), traffic=traffic,
                 ms_per_launch=round(ms_launch, 4), peak_source=peak_source)
@@ -556,7 +557,8 @@ def run_ours(args) -> None:
     s_edge = wl.template.shape[0]
     n_interior = max(X - s_edge + 1, 0) * max(Y - s_edge + 1, 0) * max(Z - s_edge + 1, 0)
     rf = roofline(kern, args.steps, nvox, desc.K, n_taps, 2048, 8, 4, peaks, spec_bytes,
-                  n_interior, ttm.ttm_plan_problem_tensor_direct(matcher.plan, 0))
+                  n_interior, ttm.ttm_plan_problem_tensor_direct(matcher.plan, 0),
+                  fp32_maps=args.precision == "fp32")
     cpu = None
     if not args.no_cpu_baseline and world == 1:
         cpu = cpu_baseline_obj(run_cpu_sample(args.workload, 128, 2), args.workload)
@@ -729,7 +731,7 @@ def run_batch(args) -> None:
         n_int += max(X - sk + 1, 0) * max(Y - sk + 1, 0) * max(Z - sk + 1, 0)
         spec_bytes += 8.0 * (X // 2 + 1) * Y * Z
     rf = roofline(kern, 1, nvox_total, tmpls[0][1].K, 0, 2048, 8, 4, peaks,
-                  spec_bytes / max(1, len(problems)), n_int)
+                  spec_bytes / max(1, len(problems)), n_int, fp32_maps=args.precision == "fp32")
     cpu = None
     if not args.no_cpu_baseline and world == 1:
         cpu = cpu_baseline_obj(run_cpu_sample(args.workload, 128, 2), args.workload)

@@ -58,8 +58,16 @@ def test_traffic_only_while_sources_unchanged(monkeypatch):
     rec = dict(bench.NCU_TRAFFIC[name])
     src = ["k_rotation.cuh", "k_rotation.cu", "k_rotation_n4.cu"]
     monkeypatch.setitem(bench.NCU_TRAFFIC, name, dict(rec, source_sha=bench.source_hash(src)))
-    rf = bench.roofline(_one(name), 1, 10 ** 6, 35, 0, 2048, 8, 4, PEAKS, n_interior=10 ** 6)
-    assert rf["traffic"] == rec["bytes_per_launch"]
+    # 8 launches per step share 2 million interior voxels
+    rf = bench.roofline(_one(name, ms=8.0, launches=8), 1, 4 * 10 ** 6, 35, 0, 2048, 8, 4, PEAKS,
+                        n_interior=2 * 10 ** 6)
+    assert rf["traffic"] == round(rec["bytes_per_voxel"] * 2 * 10 ** 6 / 8)
+    # another kind of launch than the captured one: no figure
+    rf = bench.roofline(_one(name), 1, 10 ** 6, 84, 0, 2048, 8, 4, PEAKS, n_interior=10 ** 6)
+    assert rf["traffic"] is None
+    rf = bench.roofline(_one(name), 1, 10 ** 6, 35, 0, 2048, 8, 4, PEAKS, n_interior=10 ** 6,
+                        fp32_maps=False)
+    assert rf["traffic"] is None
     monkeypatch.setitem(bench.NCU_TRAFFIC, name, dict(rec, source_sha="000000000000"))
     rf = bench.roofline(_one(name), 1, 10 ** 6, 35, 0, 2048, 8, 4, PEAKS, n_interior=10 ** 6)
     assert rf["traffic"] is None
