@@ -96,8 +96,8 @@ typedef struct ttm_peak {
                             /* and needs scratch memory for one problem       */
 
 /* Precision of the correlation step.  In both modes all arithmetic is FP32
- * except the rotation search of order 4, which runs on the tensor cores with
- * FP16 operands and FP32 accumulation.  TTM_PREC_MIXED stores the template
+ * except the rotation search of orders 4 and 6, which runs on the tensor cores
+ * with FP16 operands and FP32 accumulation.  TTM_PREC_MIXED stores the template
  * spectra, the K product spectra and the K correlation maps of the FFT path
  * in bf16 (half the memory and traffic; FFT lengths 16..1024, other problems
  * stay FP32), and runs the direct path as an implicit GEMM on the tensor
@@ -291,11 +291,12 @@ ttm_status ttm_local_stats(ttm_plan_t plan, const float* const* d_vols, float* c
  *   lambda(x)  = max_{|Q|=1} phi(Q), phi(Q) = sum_alpha mu_alpha C_alpha Q^alpha
  *   q(x)       = its maximiser, the dominant Z-eigenvector     (Sec. 3.3)
  * The maximum is searched on a fixed grid of n_grid unit quaternions split
- * into n_cells regions of equal size (for order 4 with the default grid this
- * search runs on the tensor cores in FP16 with FP32 accumulation); the best
- * grid point of each of the n_candidates best regions is refined by shifted power iterations (shift (n-1) score,
- * Kolda & Mayo 2011) and Riemannian Newton steps, and the largest refined
- * value is kept.  q is canonical: a >= 0.
+ * into n_cells regions of equal size (for orders 4 and 6 with the default
+ * grid this search runs on the tensor cores in FP16 with FP32 accumulation;
+ * orders 2 and 8 search on the CUDA cores); the best grid point of each of the
+ * n_candidates best regions is refined by shifted power iterations (shift
+ * (n-1) score, Kolda & Mayo 2011), the best of them by Riemannian Newton
+ * steps, and the largest refined value is kept.  q is canonical: a >= 0.
  *   d_w          from ttm_local_stats.
  *   d_score      X*Y*Z float32 per problem (required).
  *   d_quat       X*Y*Z*4 float32 per problem, (a,b,c,d) per voxel (required).
