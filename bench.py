@@ -60,6 +60,9 @@ def load_workload(name: str, **extra):
     base, over = WORKLOAD_OVERRIDES.get(name, (name, {}))
     return synth.config_workload(base, **dict(over, **extra))
 FP32_ALU_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # SMs x FP32 lanes x FMA x max clock
+# the refinement's defaults: 8 candidates take two power steps, the 4 best of
+# the points reached take 3 Newton steps
+CANDIDATES, REFINED, NEWTON_STEPS = 8, 4, 3
 L2_FLUSH_BYTES = 256 << 20
 
 # Measured DRAM traffic of a kernel class from one ncu capture, per interior
@@ -71,8 +74,10 @@ NCU_TRAFFIC: dict = {
     # 912 673 interior voxels in one launch each
     "rotation_polish": dict(bytes_per_voxel=(193201664 + 9929728) / 912673, K=35,
                             source_sha="9cb54c7dd779"),
+    # (the search kernel is unchanged since this capture; the one later edit of
+    # k_rotation.cuh is the refinement's candidate count, kRefine)
     "rotation_search": dict(bytes_per_voxel=(173783808 + 12853504) / 912673, K=35,
-                            source_sha="5838b9469595"),
+                            source_sha="047846cd439c"),
 }
 
 
@@ -291,10 +296,10 @@ def roofline(kernels: dict, steps: int, nvox: int, K: int, n_taps: int, n_grid: 
         KB = (n_ord + 1) * n_ord * (n_ord - 1) // 6
         KG = (n_ord + 2) * (n_ord + 1) * n_ord // 6
         # every candidate: 3 evaluations of C x^(n-1) and 2 normalisations; the
-        # 6 best: 1 + newton evaluations of C x^(n-2) and newton Newton solves
+        # REFINED best: 1 + newton evaluations of C x^(n-2) and newton Newton solves
         power = 3 * 10 * KG + 2 * 12
         newton_part = (1 + newton) * (2 * 10 * KB + 2 * KB + 40) + newton * 150
-        per_vox = n_cand * power + min(6, n_cand) * newton_part
+        per_vox = n_cand * power + min(REFINED, n_cand) * newton_part
         work = ((2.0 * n_grid * K + 2 * K) if name == "rotation_search" else per_vox) \
             * n_int / launches_per_step
         bound, peak, unit, scale = "alu", FP32_ALU_PEAK_TFLOPS, "TFLOP/s", 1e12
@@ -556,7 +561,7 @@ def run_ours(args) -> None:
     spec_bytes = 8.0 * Xh * Y * Z if path == 2 else 0.0
     s_edge = wl.template.shape[0]
     n_interior = max(X - s_edge + 1, 0) * max(Y - s_edge + 1, 0) * max(Z - s_edge + 1, 0)
-    rf = roofline(kern, args.steps, nvox, desc.K, n_taps, 2048, 8, 4, peaks, spec_bytes,
+    rf = roofline(kern, args.steps, nvox, desc.K, n_taps, 2048, CANDIDATES, NEWTON_STEPS, peaks, spec_bytes,
                   n_interior, ttm.ttm_plan_problem_tensor_direct(matcher.plan, 0),
                   fp32_maps=args.precision == "fp32")
     cpu = None
@@ -730,7 +735,7 @@ def run_batch(args) -> None:
         sk = bw.templates[k].shape[0]
         n_int += max(X - sk + 1, 0) * max(Y - sk + 1, 0) * max(Z - sk + 1, 0)
         spec_bytes += 8.0 * (X // 2 + 1) * Y * Z
-    rf = roofline(kern, 1, nvox_total, tmpls[0][1].K, 0, 2048, 8, 4, peaks,
+    rf = roofline(kern, 1, nvox_total, tmpls[0][1].K, 0, 2048, CANDIDATES, NEWTON_STEPS, peaks,
                   spec_bytes / max(1, len(problems)), n_int, fp32_maps=args.precision == "fp32")
     cpu = None
     if not args.no_cpu_baseline and world == 1:

@@ -113,7 +113,7 @@ typedef struct ttm_plan_opts {
     int n_grid;         /* rotation search grid size; 0 = default (2048), <= 65535 */
     int n_cells;        /* regions of the grid; 0 = default (128); must divide n_grid */
     int n_candidates;   /* regions polished per voxel; 0 = default (8)         */
-    int newton_steps;   /* Newton steps per candidate; 0 = default (4)         */
+    int newton_steps;   /* Newton steps per candidate; 0 = default (3)         */
     int rotation_chunks; /* split the interior into this many chunks and run  */
                          /* the search of chunk i+1 (high-priority stream)    */
                          /* beside the refinement of chunk i (low priority);  */

@@ -28,7 +28,7 @@ namespace rot {
 constexpr int kRotThreads = 128;
 constexpr int kChunk = 128;       // grid points staged per step
 constexpr int kMaxCand = 8;
-constexpr int kRefine = 6;        // candidates refined by Newton after the power steps
+constexpr int kRefine = 4;        // candidates refined by Newton after the power steps
 
 // correlation maps are float or bf16 (mixed precision)
 __device__ __forceinline__ float ldcorr(const float* p) { return __ldg(p); }

@@ -94,7 +94,7 @@ ttm_status build_grid(ttm_plan_s* P) {
     const int n = P->opts.n_grid > 0 ? P->opts.n_grid : 2048;
     const int nc = P->opts.n_cells > 0 ? P->opts.n_cells : 128;
     const int cand = P->opts.n_candidates > 0 ? P->opts.n_candidates : 8;
-    const int newton = P->opts.newton_steps > 0 ? P->opts.newton_steps : 4;
+    const int newton = P->opts.newton_steps > 0 ? P->opts.newton_steps : 3;
     if (n > 65535 || nc > n || n % nc != 0 || cand > 8 || newton > 64) return TTM_ERR_INVALID_ARG;
     std::vector<double> pts, ctr;
     half_sphere_points(n, pts);

@@ -16,12 +16,12 @@ def _one(name, ms=1.0, launches=1):
 
 def test_refinement_work_per_voxel_order_four():
     # 8 candidates x 2 power steps (3 evaluations of C x^3 over 20 cubic
-    # monomials x 4 outputs, 2 normalisations) + the 6 best x 4 Newton steps
-    # (5 evaluations of C x^2: 10 entries x 10 quadratic monomials, 4 solves)
-    rf = bench.roofline(_one("rotation_polish"), 1, 10 ** 6, 35, 0, 2048, 8, 4, PEAKS,
+    # monomials x 4 outputs, 2 normalisations) + the 4 best x 3 Newton steps
+    # (4 evaluations of C x^2: 10 entries x 10 quadratic monomials, 3 solves)
+    rf = bench.roofline(_one("rotation_polish"), 1, 10 ** 6, 35, 0, 2048, 8, 3, PEAKS,
                         n_interior=10 ** 6)
-    per_voxel = 8 * (3 * 10 * 20 + 24) + 6 * (5 * (2 * 10 * 10 + 2 * 10 + 40) + 4 * 150)
-    assert per_voxel == 16392
+    per_voxel = 8 * (3 * 10 * 20 + 24) + 4 * (4 * (2 * 10 * 10 + 2 * 10 + 40) + 3 * 150)
+    assert per_voxel == 10952
     assert rf["bound"] == "alu" and rf["unit"] == "TFLOP/s"
     assert rf["achieved"] == pytest.approx(per_voxel * 1e6 / 1e-3 / 1e12, rel=1e-3)
     assert rf["frac"] == pytest.approx(rf["achieved"] / bench.FP32_ALU_PEAK_TFLOPS, rel=1e-3)
