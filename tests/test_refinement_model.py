@@ -125,3 +125,15 @@ def test_refinement_budget_meets_the_lambda_gate(c1_voxels):
     assert (lam_o - lam).max() <= 2e-5
     # never above the true maximum (beyond the oracle's own convergence)
     assert (lam - lam_o).max() <= 1e-9
+
+
+def test_refinement_budget_order_six():
+    wl = synth.config_workload("c1", n_rot=4000)
+    T = o.tensor_template(wl.template, wl.mask, wl.quadrature.astype(np.float64), wl.weights, 6)
+    rng = np.random.default_rng(6)
+    pts = np.concatenate([wl.positions, rng.integers(7, 64 - 15 + 7 + 1, size=(36, 3))])
+    _, C = o.components_at(wl.volume, T, wl.mask, pts)
+    lam_o, _ = o.dominant_z_eigenpair(C, 6)
+    lam = model_lambda(C, 6, refined=4, newton=3)
+    assert (lam_o - lam).max() <= 2e-5
+    assert (lam - lam_o).max() <= 1e-9
