@@ -63,6 +63,8 @@ FP32_ALU_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # SMs x FP32 lanes x FMA
 # the refinement's defaults: 8 candidates take two power steps, the 4 best of
 # the points reached take 3 Newton steps
 CANDIDATES, REFINED, NEWTON_STEPS = 8, 4, 3
+REFINEMENT = (f"{CANDIDATES} candidates x 2 power steps, the {REFINED} best x "
+              f"{NEWTON_STEPS} Newton steps")
 L2_FLUSH_BYTES = 256 << 20
 
 # Measured DRAM traffic of a kernel class from one ncu capture, per interior
@@ -574,7 +576,8 @@ def run_ours(args) -> None:
         data="synthetic",
         config=dict(workload=WORKLOAD[args.workload], path={1: "direct", 2: "fft"}.get(path, path),
                     voxels=nvox, interior_voxels=n_interior, tensor_order=wl.n_order, K=desc.K, mask_voxels=n_taps,
-                    rotation_grid=2048, l2="flushed (256 MB write) before every timed step",
+                    rotation_grid=2048, refinement=REFINEMENT,
+                    l2="flushed (256 MB write) before every timed step",
                     parallelism="replicas" if world > 1 else "single GPU",
                     template_build_ms=round(build_ms, 2), quadrature_rotations=desc.n_rot),
         roofline=rf, cpu_baseline=cpu, e2e=e2e, gpu_launches=launches, classical=classical,
@@ -752,6 +755,7 @@ def run_batch(args) -> None:
                     tuned_problems=sum(1 for t in tuning if t[0] >= 0 and t[1] >= 0),
                     plan_seconds=round(plan_s, 2), template_build_ms=round(build_ms, 2),
                     graph="one CUDA graph replay per step (all problems)",
+                    rotation_grid=2048, refinement=REFINEMENT,
                     l2="flushed (256 MB write) before every timed step",
                     parallelism="replicas" if world > 1 else "single GPU",
                     quadrature_rotations=int(len(bw.quadrature))),
