@@ -214,6 +214,14 @@ ttm_status ttm_build_tensor_template_noalloc(const float* d_template, const floa
  * 960 1024, and TTM_PATH_DIRECT returns TTM_ERR_UNSUPPORTED.
  * opts may be NULL (defaults).  The plan allocates and owns only its tables
  * and precomputed template spectra.  Synchronises the stream.
+ * Errors: TTM_ERR_INVALID_ARG (null pointer, volume smaller than its box,
+ * template index out of range, mask values outside [0, 1], or an option out
+ * of range: path, precision, negative counts, n_grid > 65535, n_cells not
+ * dividing n_grid, n_candidates > 8, newton_steps > 64, lowpass_sigma; all
+ * checked before any device work), TTM_ERR_UNSUPPORTED (odd order or mixed
+ * orders, n > 8, soft mask off the FFT path, volume of 2^31 voxels or more),
+ * TTM_ERR_NUMERIC (non-finite components), TTM_ERR_OUT_OF_MEMORY,
+ * TTM_ERR_CUDA.
  * ---------------------------------------------------------------------- */
 ttm_status ttm_plan(ttm_plan_t* out, int n_problems, const int* vol_dims, const int* tmpl_index,
                     int n_templates, const ttm_tt_desc* descs, const float* const* d_components,

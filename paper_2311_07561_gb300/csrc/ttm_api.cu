@@ -906,6 +906,18 @@ ttm_status ttm_plan(ttm_plan_t* out, int n_problems, const int* vol_dims, const 
     }
     if (opts && opts->lowpass_sigma != 0.f && !lowpass_sigma_ok(opts->lowpass_sigma))
         return TTM_ERR_INVALID_ARG;
+    if (opts) {
+        // plan options, checked before any device work
+        const ttm_plan_opts& o = *opts;
+        if (o.path < TTM_PATH_AUTO || o.path > TTM_PATH_TUNE) return TTM_ERR_INVALID_ARG;
+        if (o.precision != TTM_PREC_FP32 && o.precision != TTM_PREC_MIXED) return TTM_ERR_INVALID_ARG;
+        if (o.n_grid < 0 || o.n_cells < 0 || o.n_candidates < 0 || o.newton_steps < 0 ||
+            o.rotation_chunks < 0)
+            return TTM_ERR_INVALID_ARG;
+        const int n = o.n_grid > 0 ? o.n_grid : 2048, nc = o.n_cells > 0 ? o.n_cells : 128;
+        if (n > 65535 || nc > n || n % nc != 0 || o.n_candidates > 8 || o.newton_steps > 64)
+            return TTM_ERR_INVALID_ARG;
+    }
     ttm_plan_s* P = new (std::nothrow) ttm_plan_s();
     if (!P) return TTM_ERR_OUT_OF_MEMORY;
     if (opts) P->opts = *opts;

@@ -89,6 +89,16 @@ def test_null_and_invalid_arguments_are_rejected_on_host(lib):
     bad = (ctypes.c_int * 1)(1)
     assert lib.ttm_plan(ctypes.byref(handle), 1, dims, bad, 1, ctypes.byref(d), ptrs, ptrs,
                         None, None) == -1
+    # plan options out of range, rejected before any device work
+    dims = (ctypes.c_int * 3)(64, 64, 64)
+    for field, value in (("path", 4), ("path", -1), ("precision", 2), ("n_grid", 70000),
+                         ("n_grid", 1000), ("n_cells", 3000), ("n_candidates", 9),
+                         ("newton_steps", 65), ("rotation_chunks", -1), ("n_cells", -4),
+                         ("lowpass_sigma", 9.0)):
+        o_ = ttm.PlanOpts()
+        setattr(o_, field, value)
+        assert lib.ttm_plan(ctypes.byref(handle), 1, dims, tix, 1, ctypes.byref(d), ptrs, ptrs,
+                            ctypes.byref(o_), None) == -1, (field, value)
     # calls on a null plan
     n = ctypes.c_int()
     assert lib.ttm_local_stats(None, None, None, None, 0, None) == -1
