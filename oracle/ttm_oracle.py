@@ -10,7 +10,7 @@ Every function cites the passage of Almira, Phelippeau & Martinez-Sanchez,
 "Fast Normalized Cross-Correlation for Template Matching with Rotations"
 (arXiv 2311.07561) that it follows.  Arithmetic is float64 throughout.
 
-Readings taken where the paper is silent (each is also listed in the design doc):
+Readings taken where the paper is silent:
 
 * the low-pass filter h is the identity unless a Gaussian is asked for
   (lowpass: sampled, unit sum, zero outside the array; the paper allows any
