@@ -455,3 +455,95 @@ def test_lowpass_is_scipy_gaussian_filter_with_unit_gain():
     ones = o.lowpass(np.ones((30, 30, 30)), 1.5)
     r = int(4 * 1.5 + 0.5)
     assert np.abs(ones[r:-r, r:-r, r:-r] - 1.0).max() <= 1e-12
+
+
+# --------------------------------------------------------------------------
+# Sec. 3.2: the per-point components C_alpha(x) = w(x) <tau_x f, T_alpha>,
+# which the full-size and sampled GPU tests use as their only checker
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("s,shape", [(7, (17, 13, 19)), (8, (16, 21, 14)), (9, (18, 18, 23))])
+def test_components_at_matches_whole_interior_and_explicit_loops(s, shape):
+    """components_at (one box per point) equals ttm_components (whole-volume
+    direct correlation) and local_stats_direct at the same voxels, for odd and
+    even s on ragged volumes; at the first and last interior voxel it equals
+    the definition written as loops: C_alpha(x) = w(x) sum_u f(x + u - c)
+    T_alpha(u) with w = 1 / (sqrt(m_sum) * population std over the ball)."""
+    rng = np.random.default_rng(40 + s)
+    f = rng.normal(size=shape) + 2.0
+    r = synth.default_mask_radius(s)
+    m = synth.ball_mask(s, r).astype(np.float64)
+    T = rng.normal(size=(3, s, s, s))
+    c = s // 2
+    Z, Y, X = shape
+    lo = (c, c, c)                                        # (x, y, z) of the first interior voxel
+    hi = (X - s + c, Y - s + c, Z - s + c)                # and of the last one
+    inner = rng.integers(lo, np.array(hi) + 1, size=(6, 3))
+    pts = np.array([lo, hi, (lo[0], hi[1], lo[2]), (hi[0], lo[1], hi[2])] + inner.tolist())
+    w_p, C_p = o.components_at(f, T, m, pts)
+    w_all, C_all = o.ttm_components(f, T, m, use_fft=False)
+    _, _, w_ls = o.local_stats_direct(f, m)
+    for i, (x, y, z) in enumerate(pts):
+        assert w_p[i] == pytest.approx(w_all[z, y, x], rel=1e-12)
+        assert w_p[i] == pytest.approx(w_ls[z, y, x], rel=1e-12)
+        assert np.allclose(C_p[i], C_all[:, z, y, x], rtol=1e-12, atol=1e-12)
+    # the patch is the box whose voxel u sits at x + u - c
+    P = o.patches_at(f, pts[:2], s)
+    for i, (x, y, z) in enumerate(pts[:2]):
+        assert P[i][0] == f[z - c, y - c, x - c]
+        assert P[i][-1] == f[z - c + s - 1, y - c + s - 1, x - c + s - 1]
+        ball = m.astype(bool)
+        win = f[z - c:z - c + s, y - c:y - c + s, x - c:x - c + s]
+        w_ref = 1.0 / (math.sqrt(ball.sum()) * np.std(win[ball]))
+        assert w_p[i] == pytest.approx(w_ref, rel=1e-12)
+        for k in range(T.shape[0]):
+            acc = 0.0
+            for uz, uy, ux in itertools.product(range(s), repeat=3):
+                acc += f[z + uz - c, y + uy - c, x + ux - c] * T[k, uz, uy, ux]
+            assert C_p[i, k] == pytest.approx(w_ref * acc, rel=1e-11, abs=1e-12)
+
+
+def test_components_at_variance_floor_uses_whole_volume_variance():
+    """The default var_f of components_at is the whole volume's variance (the
+    degenerate-variance rule of the interior maps): a window on a flat patch
+    gets w = 0, exactly as in ttm_components."""
+    rng = np.random.default_rng(47)
+    f = rng.normal(size=(16, 16, 20))
+    f[:, :, :9] = 1.5                                     # flat slab in x < 9
+    m = synth.ball_mask(5, 2)
+    T = rng.normal(size=(2, 5, 5, 5))
+    pts = np.array([[3, 7, 7], [14, 8, 9]])
+    w_p, _ = o.components_at(f, T, m, pts)
+    w_all, _ = o.ttm_components(f, T, m, use_fft=False)
+    assert w_p[0] == 0.0 and w_all[7, 7, 3] == 0.0
+    assert w_p[1] == pytest.approx(w_all[9, 8, 14], rel=1e-12) and w_p[1] > 0
+    # an explicit var_f overrides it (the sampled tests pass the volume's own)
+    w_big, _ = o.components_at(f, T, m, pts, var_f=1e9)
+    assert np.all(w_big == 0.0)
+
+
+def test_rotation_angle_closed_forms():
+    """rotation_angle_deg against axis-angle closed forms: the quaternion
+    (cos(theta/2), sin(theta/2) u) is a turn by theta about u; q and -q are
+    the same rotation; and the angle equals acos((tr(R1 R2^T) - 1) / 2)
+    computed from the textbook rotation matrices."""
+    ident = np.array([1.0, 0.0, 0.0, 0.0])
+    rng = np.random.default_rng(48)
+    for theta in (0.0, 0.5, 1.0, 13.0, 90.0, 123.4, 179.0, 180.0):
+        u = rng.normal(size=3)
+        u /= np.linalg.norm(u)
+        h = math.radians(theta) / 2
+        q = np.concatenate([[math.cos(h)], math.sin(h) * u])
+        assert o.rotation_angle_deg(q, ident) == pytest.approx(theta, abs=1e-6)
+        assert o.rotation_angle_deg(ident, q) == pytest.approx(theta, abs=1e-6)
+        assert o.rotation_angle_deg(-q, ident) == pytest.approx(theta, abs=1e-6)
+        assert o.rotation_angle_deg(q, -q) == pytest.approx(0.0, abs=1e-6)
+    # quarter turn about z
+    qz = np.array([math.cos(math.pi / 4), 0.0, 0.0, math.sin(math.pi / 4)])
+    assert o.rotation_angle_deg(qz, ident) == pytest.approx(90.0, abs=1e-9)
+    P, Q = _rand_quats(50, 49), _rand_quats(50, 50)
+    got = o.rotation_angle_deg(P, Q)
+    for i in range(50):
+        R = _closed_form_rotation(P[i]) @ _closed_form_rotation(Q[i]).T
+        ref = math.degrees(math.acos(np.clip((np.trace(R) - 1.0) / 2.0, -1.0, 1.0)))
+        assert got[i] == pytest.approx(ref, abs=1e-5)
