@@ -17,8 +17,10 @@ arithmetic):
 
 from __future__ import annotations
 
+import concurrent.futures
 import dataclasses
 import math
+import os
 from typing import Dict, List, Optional, Sequence, Tuple
 
 import numpy as np
@@ -161,9 +163,17 @@ def plant_copies(shape_zyx: Sequence[int], t: np.ndarray, quats: np.ndarray,
     vol = np.zeros(tuple(shape_zyx))
     s = t.shape[0]
     c = s // 2
-    for q, p in zip(quats, positions_xyz):
-        x0, y0, z0 = (int(p[0]) - c, int(p[1]) - c, int(p[2]) - c)
-        vol[z0:z0 + s, y0:y0 + s, x0:x0 + s] += rotated_copy(t, q)
+    quats = np.asarray(quats).reshape(-1, 4)
+    positions_xyz = np.asarray(positions_xyz).reshape(-1, 3)
+    # the copies are resampled in worker threads, a bounded window ahead, and
+    # added in their own order (the sum is the same as one copy at a time)
+    workers = min(8, os.cpu_count() or 1)
+    with concurrent.futures.ThreadPoolExecutor(max_workers=workers) as ex:
+        for i0 in range(0, len(quats), 4 * workers):
+            chunk = list(ex.map(lambda q: rotated_copy(t, q), quats[i0:i0 + 4 * workers]))
+            for copy, p in zip(chunk, positions_xyz[i0:i0 + 4 * workers]):
+                x0, y0, z0 = (int(p[0]) - c, int(p[1]) - c, int(p[2]) - c)
+                vol[z0:z0 + s, y0:y0 + s, x0:x0 + s] += copy
     return vol
 
 
@@ -175,20 +185,22 @@ def _random_positions(shape_zyx: Sequence[int], s: int, count: int,
     hi = np.array([shape_zyx[2] - s + c, shape_zyx[1] - s + c, shape_zyx[0] - s + c])
     if np.any(hi < lo):
         raise ValueError("volume smaller than the template box")
-    pts: List[np.ndarray] = []
+    pts = np.zeros((count, 3), dtype=np.int64)
+    n = 0
     tries = 0
     dist = float(min_dist)
-    while len(pts) < count:
+    while n < count:
         p = np.array([rng.integers(lo[i], hi[i] + 1) for i in range(3)])
-        if all(np.sum((p - o) ** 2) >= dist * dist for o in pts):
-            pts.append(p)
+        if n == 0 or np.min(np.sum((pts[:n] - p) ** 2, axis=1)) >= dist * dist:
+            pts[n] = p
+            n += 1
             tries = 0
         else:
             tries += 1
             if tries > 2000:           # crowded: relax the spacing a little
                 dist *= 0.9
                 tries = 0
-    return np.array(pts, dtype=np.int64).reshape(-1, 3)
+    return pts
 
 
 @dataclasses.dataclass
@@ -301,19 +313,23 @@ def _spaced_positions(shape_zyx: Sequence[int], s: int, count: int, min_dist: fl
     hi = np.array([shape_zyx[2] - s + c, shape_zyx[1] - s + c, shape_zyx[0] - s + c])
     if np.any(hi < lo):
         raise ValueError("volume smaller than the template box")
-    pts: List[np.ndarray] = []
+    pts = np.zeros((len(taken) + count, 3), dtype=np.int64)
+    if taken:
+        pts[:len(taken)] = np.asarray(taken, dtype=np.int64).reshape(-1, 3)
+    n = len(taken)
     dist, tries = float(min_dist), 0
-    while len(pts) < count:
+    while n < len(pts):
         p = np.array([rng.integers(lo[i], hi[i] + 1) for i in range(3)])
-        if all(np.sum((p - o) ** 2) >= dist * dist for o in taken + pts):
-            pts.append(p)
+        if n == 0 or np.min(np.sum((pts[:n] - p) ** 2, axis=1)) >= dist * dist:
+            pts[n] = p
+            n += 1
             tries = 0
         else:
             tries += 1
             if tries > 500:
                 dist *= 0.9
                 tries = 0
-    return np.array(pts, dtype=np.int64).reshape(-1, 3)
+    return pts[len(taken):]
 
 
 def make_batch(shapes_zyx: Sequence[Sequence[int]], sizes: Sequence[int], n_blobs: int,
