@@ -571,26 +571,30 @@ def rotation_angle_deg(q1: np.ndarray, q2: np.ndarray) -> np.ndarray:
 def extract_peaks(score: np.ndarray, threshold: float, radius: int,
                   max_peaks: int) -> np.ndarray:
     """Voxels whose score exceeds ``threshold`` and beats every other voxel of
-    the (2*radius+1)^3 cube around it (a tie goes to the lower linear index).
-    Returns up to ``max_peaks`` linear indices, highest score first (ties:
-    lower index first)."""
+    the (2*radius+1)^3 cube around it (a tie goes to the lower linear index;
+    the cube is clipped to the array).  Returns up to ``max_peaks`` linear
+    indices, highest score first (ties: lower index first).
+
+    Every voxel above the threshold is a candidate; each candidate is checked
+    against every voxel of its cube, one cube offset at a time."""
     score = np.asarray(score, dtype=np.float64)
     Z, Y, X = score.shape
-    lin = np.arange(score.size).reshape(score.shape)
-    big = -np.inf
-    pad = np.pad(score, radius, mode="constant", constant_values=big)
-    padlin = np.pad(lin, radius, mode="constant", constant_values=-1)
-    ok = score > threshold
+    flat = score.ravel()
+    cand = np.nonzero(flat > threshold)[0]
+    cz, rem = np.divmod(cand, Y * X)
+    cy, cx = np.divmod(rem, X)
+    ok = np.ones(len(cand), dtype=bool)
     for dz in range(-radius, radius + 1):
         for dy in range(-radius, radius + 1):
             for dx in range(-radius, radius + 1):
                 if dz == 0 and dy == 0 and dx == 0:
                     continue
-                nb = pad[radius + dz:radius + dz + Z, radius + dy:radius + dy + Y,
-                         radius + dx:radius + dx + X]
-                nbl = padlin[radius + dz:radius + dz + Z, radius + dy:radius + dy + Y,
-                             radius + dx:radius + dx + X]
-                ok &= (nb < score) | ((nb == score) & (nbl > lin))
-    idx = np.nonzero(ok.ravel())[0]
-    order = np.lexsort((idx, -score.ravel()[idx]))
+                nz, ny, nx = cz + dz, cy + dy, cx + dx
+                inside = (nz >= 0) & (nz < Z) & (ny >= 0) & (ny < Y) & (nx >= 0) & (nx < X)
+                nb = (np.clip(nz, 0, Z - 1) * Y + np.clip(ny, 0, Y - 1)) * X + np.clip(nx, 0, X - 1)
+                u = flat[nb]
+                beaten = inside & ((u > flat[cand]) | ((u == flat[cand]) & (nb < cand)))
+                ok &= ~beaten
+    idx = cand[ok]
+    order = np.lexsort((idx, -flat[idx]))
     return idx[order][:max_peaks]
