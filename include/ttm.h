@@ -186,7 +186,10 @@ ttm_status ttm_build_tensor_template(const float* d_template, const float* d_mas
  * array, so s <= 127; a larger s returns TTM_ERR_WORKSPACE before any work.
  * The first call on a device looks up the array's device address with
  * cudaGetSymbolAddress (once per device, with that device current) and
- * caches it; make that first call before any stream capture.
+ * caches it; make that first call before any stream capture.  The cached
+ * address is never looked up again, so after cudaDeviceReset on a device the
+ * entry point must not be called there for the rest of the process.
+ * Pointers must be 4-byte aligned (else TTM_ERR_INVALID_ARG, before any work).
  * Every call uses the same array and it keeps the previous call's contents
  * (the call clears what must start at zero).  Calls that overlap on the GPU
  * -- on two streams, or from two host threads -- race on the array.

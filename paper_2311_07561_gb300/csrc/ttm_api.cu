@@ -843,7 +843,7 @@ ttm_status ttm_build_tensor_template(const float* d_template, const float* d_mas
     TTM_TRY(ttm_build_workspace_size(s, n_order, n_rot, &need));
     if (!d_workspace || workspace_bytes < need) return TTM_ERR_WORKSPACE;
     if (!aligned(d_workspace, 256) || !aligned(d_template, 4) || !aligned(d_mask, 4) ||
-        !aligned(d_quats, 4) || !aligned(d_components, 4))
+        !aligned(d_quats, 4) || !aligned(d_components, 4) || !aligned(d_weights, 4))
         return TTM_ERR_INVALID_ARG;
     cudaStream_t st = (cudaStream_t)stream;
     long long cnt = 0;

@@ -9,6 +9,7 @@
 // chunk of rotated, normalised template copies) from one fixed array that
 // lives in this file.  The caller still provides the inputs and the output
 // components; nothing is allocated, neither here nor by any library routine.
+#include <cstdint>
 #include <mutex>
 
 #include "ttm_internal.h"
@@ -17,6 +18,8 @@ namespace ttm {
 namespace {
 
 constexpr size_t kNoallocHeader = 256;
+
+bool aligned4(const void* p) { return ((uintptr_t)p % 4) == 0; }
 
 // The fixed scratch.  Every GPU that loads the library holds these bytes until
 // the process exits.  In host code this name is only a stand-in for the symbol,
@@ -28,7 +31,8 @@ std::mutex g_mu;
 void* g_scratch_addr[kMaxDevices] = {nullptr};
 
 // Device address of the fixed scratch on the current device, looked up once
-// per device (with that device current) and cached.
+// per device (with that device current) and cached.  The cached address is
+// not refreshed: after cudaDeviceReset on a device it is stale.
 ttm_status scratch_address(void** out) {
     int dev = -1;
     TTM_CUDA_TRY(cudaGetDevice(&dev));
@@ -61,6 +65,11 @@ extern "C" ttm_status ttm_build_tensor_template_noalloc(const float* d_template,
     const size_t per_rot = s3 * sizeof(float);
     // one rotated copy must fit next to the header
     if (kNoallocHeader + per_rot > (size_t)TTM_NOALLOC_SCRATCH_BYTES) return TTM_ERR_WORKSPACE;
+    // the same pointer checks as the regular build: the kernels read and write
+    // these arrays as float
+    if (!aligned4(d_template) || !aligned4(d_mask) || !aligned4(d_quats) ||
+        !aligned4(d_components) || !aligned4(d_weights))
+        return TTM_ERR_INVALID_ARG;
     void* base = nullptr;
     TTM_TRY(scratch_address(&base));
     cudaStream_t st = (cudaStream_t)stream;

@@ -76,3 +76,33 @@ def test_noalloc_build_rejects_boxes_beyond_its_scratch(ttm):
     assert st == -7
     assert lib.ttm_build_tensor_template_noalloc(None, None, 32, 4, None, None, 10, None,
                                                  ctypes.byref(desc), None) == -1
+    # a float array that is not 4-byte aligned is refused on the host, before
+    # the scratch address is looked up or anything is queued
+    for bad in range(4):
+        ptrs = [256, 256, 256, 256, None]
+        ptrs[bad] = 257
+        t, m, q, out, wts = ptrs
+        assert lib.ttm_build_tensor_template_noalloc(t, m, 32, 4, q, wts, 10, out,
+                                                     ctypes.byref(desc), None) == -1
+    assert lib.ttm_build_tensor_template_noalloc(256, 256, 32, 4, 256, 258, 10, 256,
+                                                 ctypes.byref(desc), None) == -1
+
+
+def test_noalloc_build_allocates_no_device_memory(ttm):
+    """Once the library's kernels are loaded (the calls above, or a first
+    call here), a further call leaves the device's free memory unchanged: the
+    outputs are the caller's and the scratch is the library's fixed array."""
+    import torch
+    s, r, n, n_rot = 24, 11, 4, 500
+    t, m, q = _inputs(s, r, n_rot, 3)
+    K = (n + 1) * (n + 2) * (n + 3) // 6
+    out = torch.empty((K, s, s, s), dtype=torch.float32, device="cuda")
+    ttm.ttm_build_tensor_template_noalloc(t, m, s, n, q, None, n_rot, out)
+    torch.cuda.synchronize()
+    first = out.clone()
+    free0, _ = torch.cuda.mem_get_info()
+    ttm.ttm_build_tensor_template_noalloc(t, m, s, n, q, None, n_rot, out)
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0
+    assert torch.equal(out, first)
