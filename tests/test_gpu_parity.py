@@ -503,6 +503,13 @@ def test_match_peaks_equals_dense_maps_at_peaks(ttm, path):
         assert np.array_equal(got[f], ref[f]), f
     dense.close()
     sparse.close()
+    # the records against the oracle: its C at the peak voxels, the score,
+    # the dominant Z-eigenvalue, and q a maximiser of the oracle's phi
+    T = o.tensor_template(wl.template, wl.mask, wl.quadrature.astype(np.float64), wl.weights, 4)
+    pts = np.stack([got["x"], got["y"], got["z"]], 1).astype(np.int64)
+    _, C_o = o.components_at(wl.volume, T, wl.mask, pts)
+    assert np.abs(got["score"] - o.frobenius_score(C_o.T, 4)).max() <= TOL
+    _rotation_check(C_o, got["lambda"], got["q"], 4, planted=range(len(pts)))
 
 
 def test_soft_mask_fft_path(ttm):
