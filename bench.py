@@ -4,11 +4,19 @@ the TTM score + rotation maps.
 
 One step = local statistics + correlation with the K tensor components +
 per-voxel Frobenius score and dominant Z-eigenvector rotation, over one
-synthetic 256^3 FP32 tomogram (50 planted copies of a 32^3 lowpassed blob
-template, SNR 0.5, mask radius 15, order n = 4, K = 35).  The tensor template
-is built once before timing (reported separately).  Inputs are resident in
-HBM when the timed region starts; L2 is flushed (256 MB write) before every
-timed step, outside the step's events.
+synthetic tomogram.  The default workload is the largest single-GPU
+configuration: a 928 x 928 x 464 FP32 volume with 2000 planted copies of a
+64^3 lowpassed blob template (SNR 0.2, mask radius 31), tensor order n = 6
+(K = 84), bf16 storage of the template spectra, product spectra and
+correlation maps (FP32 arithmetic).  The tensor template is built once before
+timing (reported separately).  Inputs are resident in HBM when the timed
+region starts; L2 is flushed (256 MB write) before every timed step, outside
+the step's events.
+
+Beside the timing the line states the error of the maps against the FP64
+oracle at sampled voxels, FP32 against bf16 storage at 512^3 (each against the
+oracle), the oracle's own rate on all host cores, and the end-to-end rate with
+host copies.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 Under torchrun every rank runs an independent replica (weak scaling); rank 0
@@ -41,6 +49,9 @@ WORKLOAD = dict(
         "SNR 0.5, ball mask r=15, tensor order n=4 (K=35)",
     c3="512x512x512 FP32 volume, 200 planted copies of a 40^3 lowpassed 30-blob template, "
        "SNR 0.3, ball mask r=19, tensor order n=4 (K=35)",
+    c5s="256x256x192 FP32 volume (profiling size), 40 planted copies of the 64^3 template of c5, "
+        "SNR 0.2, ball mask r=31, tensor order n=6 (K=84), quadrature of 20000 rotations, "
+        "mixed precision",
     c5="928x928x464 FP32 volume, 2000 planted copies of a 64^3 lowpassed 30-blob template, "
        "SNR 0.2, ball mask r=31, tensor order n=6 (K=84), quadrature of 20000 rotations; FFT box "
        "960x960x480; mixed precision (bf16 template spectra, products and maps resident in HBM)",
@@ -52,7 +63,8 @@ WORKLOAD = dict(
 BATCH_WORKLOADS = ("c4",)
 CPU_SAMPLE_SHAPES = dict(c3=dict(shape_zyx=(160, 160, 160), copies=10),
                          c5=dict(shape_zyx=(192, 192, 192), copies=8))
-WORKLOAD_OVERRIDES = dict(c2s=("c2", dict(shape_zyx=(128, 128, 128), copies=8)))
+WORKLOAD_OVERRIDES = dict(c2s=("c2", dict(shape_zyx=(128, 128, 128), copies=8)),
+                          c5s=("c5", dict(shape_zyx=(192, 256, 256), copies=40)))
 
 
 def load_workload(name: str, **extra):
@@ -68,18 +80,18 @@ REFINEMENT = (f"{CANDIDATES} candidates x 2 power steps, the {REFINED} best x "
 L2_FLUSH_BYTES = 256 << 20
 
 # Measured DRAM traffic of a kernel class from one ncu capture, per interior
-# voxel, with the hash of the sources it was taken on; reported (times the
-# interior voxels of one launch) only while those sources are unchanged and
-# for the captured kind of launch: order 4 (K = 35) over FP32 maps.
+# voxel, for one order (K) and map storage, with the hash of the sources it
+# was taken on; reported (times the interior voxels of a step) only while
+# those sources are unchanged.
 NCU_TRAFFIC: dict = {
     # ncu (dram__bytes_read.sum + dram__bytes_write.sum) of the 128^3 case,
     # 912 673 interior voxels in one launch each
-    "rotation_polish": dict(bytes_per_voxel=(193201664 + 9929728) / 912673, K=35,
-                            source_sha="9cb54c7dd779"),
-    # (the search kernel is unchanged since this capture; the one later edit of
-    # k_rotation.cuh is the refinement's candidate count, kRefine)
-    "rotation_search": dict(bytes_per_voxel=(173783808 + 12853504) / 912673, K=35,
-                            source_sha="047846cd439c"),
+    "rotation_polish": [dict(bytes_per_voxel=(193201664 + 9929728) / 912673, K=35, storage="f32",
+                             source_sha="9cb54c7dd779",
+                             sources=["k_rotation.cuh", "k_rotation.cu", "k_rotation_n4.cu"])],
+    "rotation_search": [dict(bytes_per_voxel=(173783808 + 12853504) / 912673, K=35, storage="f32",
+                             source_sha="047846cd439c",
+                             sources=["k_search_tc.cu", "k_rotation.cuh"])],
 }
 
 
@@ -89,7 +101,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c2s", "c3", "c4", "c5"])
+    ap.add_argument("--workload", default="c5", choices=["c1", "c2", "c2s", "c3", "c4", "c5", "c5s"])
     ap.add_argument("--path", default="auto", choices=["auto", "direct", "fft"])
     ap.add_argument("--precision", default=None, choices=["fp32", "mixed"],
                     help="storage of spectra/products/correlation maps on the FFT path "
@@ -106,82 +118,303 @@ def parse():
                     help="steps in flight in the end-to-end measurement (0 = 2, or 1 for c5)")
     ap.add_argument("--classical", action=argparse.BooleanOptionalAction, default=True,
                     help="also time classical NCC at 1000 rotations on the same volume")
-    ap.add_argument("--cpu-sample", type=int, default=0,
-                    help="internal: run the oracle on this many sampled voxels and print JSON")
-    ap.add_argument("--sample-steps", type=int, default=1)
+    ap.add_argument("--oracle-errors", action=argparse.BooleanOptionalAction, default=True,
+                    help="state the error of the maps against the FP64 oracle at sampled voxels")
+    ap.add_argument("--precision-pair", action=argparse.BooleanOptionalAction, default=True,
+                    help="with the 928x928x464 workload, also time FP32 and bf16 storage at "
+                         "512^3, each with its error against the oracle")
     ap.add_argument("--order-sweep", action="store_true",
                     help="rotation error at the planted copies of the 256^3 volume against the "
                          "tensor order n and the quadrature size, beside classical NCC at 1000 "
                          "and 7112 sampled rotations; prints its own JSON line")
     args = ap.parse_args()
     if args.precision is None:
-        args.precision = "mixed" if args.workload == "c5" else "fp32"
+        args.precision = "mixed" if args.workload in ("c5", "c5s") else "fp32"
     return args
 
 
 # ---------------------------------------------------------------------------
-# oracle timing (CPU baseline / reference arm); runs without touching the GPU
+# the FP64 oracle on the host cores: timing (CPU baseline / reference arm) and
+# the error of the GPU maps.  Work is spread over spawned worker processes
+# (one BLAS thread each); every worker warms the oracle's cached tables before
+# anything is timed.
 # ---------------------------------------------------------------------------
 
-def cpu_sample(workload: str, n_vox: int, steps: int) -> dict:
+ORACLE_TEMPLATE_ROTATIONS = 64      # the per-voxel cost does not depend on it
+ERROR_ROTATIONS = 300               # quadrature of the error runs, both sides
+
+
+def oracle_cores() -> int:
+    try:
+        return max(1, len(os.sched_getaffinity(0)))
+    except AttributeError:
+        return max(1, os.cpu_count() or 1)
+
+
+def _oracle_init(n_order, barrier):
+    """Worker start: import the oracle and fill its cached tables (the search
+    set and its neighbour lists, the index tables of order n) on a dummy
+    voxel, then wait until every worker is ready."""
     import numpy as np
-    import synth
     from oracle import ttm_oracle as o
+    K = len(o.multi_indices(n_order))
+    o.dominant_z_eigenpair(np.random.default_rng(0).normal(size=(2, K)), n_order)
+    o.frobenius_score(np.zeros((K, 1)), n_order)
+    if barrier is not None:
+        barrier.wait()
+
+
+def _oracle_voxels(job):
+    """Worker: the oracle's per-voxel steps (local statistics, the K
+    components by direct sums, score, dominant Z-eigenpair) at the voxels."""
+    import numpy as np
+    from oracle import ttm_oracle as o
+    tdir, pts, n_order, var_f = job
+    vol = np.load(os.path.join(tdir, "vol.npy"), mmap_mode="r")
+    T = np.load(os.path.join(tdir, "T.npy"), mmap_mode="r")
+    m = np.load(os.path.join(tdir, "mask.npy"))
+    t0 = time.perf_counter()
+    w, C = o.components_at(vol, np.asarray(T), m, pts, var_f=var_f)
+    score = o.frobenius_score(C.T, n_order)
+    lam, q = o.dominant_z_eigenpair(C, n_order)
+    return dict(w=w, C=C, score=score, lam=lam, q=q, seconds=time.perf_counter() - t0)
+
+
+def _oracle_template_part(job):
+    """Worker: the oracle's tensor template over a slice of the quadrature
+    (the template is linear in the weights, so the slices add up)."""
+    import numpy as np
+    from oracle import ttm_oracle as o
+    tdir, t, m, quats, weights, n_order, part = job
+    T = o.tensor_template(t, m, quats, weights, n_order)
+    path = os.path.join(tdir, f"Tpart{part}.npy")
+    np.save(path, T)
+    return path
+
+
+class OraclePool:
+    """Spawned worker processes running the oracle (one BLAS thread each)."""
+
+    def __init__(self, n_order: int, cores: int | None = None):
+        import multiprocessing as mp
+        self.cores = cores or oracle_cores()
+        self.n_order = n_order
+        ctx = mp.get_context("spawn")
+        saved = {k: os.environ.get(k) for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS",
+                                                "MKL_NUM_THREADS", "CUDA_VISIBLE_DEVICES")}
+        os.environ.update(OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
+                          CUDA_VISIBLE_DEVICES="")
+        try:
+            barrier = ctx.Barrier(self.cores + 1)
+            self.pool = ctx.Pool(self.cores, initializer=_oracle_init,
+                                 initargs=(n_order, barrier))
+            barrier.wait()
+        finally:
+            for k, v in saved.items():
+                if v is None:
+                    os.environ.pop(k, None)
+                else:
+                    os.environ[k] = v
+        self.tdir = tempfile.mkdtemp(prefix="ttm_oracle_")
+
+    def tensor_template(self, t, m, quats, weights, name: str):
+        """The oracle's tensor template, quadrature slices in parallel."""
+        import numpy as np
+        n = len(quats)
+        parts = min(self.cores, max(1, n // 8))
+        bounds = np.linspace(0, n, parts + 1).astype(int)
+        jobs = [(self.tdir, t, m, quats[a:b], weights[a:b], self.n_order, f"{name}{i}")
+                for i, (a, b) in enumerate(zip(bounds[:-1], bounds[1:])) if b > a]
+        T = None
+        for path in self.pool.map(_oracle_template_part, jobs, chunksize=1):
+            part = np.load(path)
+            T = part if T is None else T + part
+            os.unlink(path)
+        return T
+
+    def stage(self, vol, T, mask) -> None:
+        import numpy as np
+        np.save(os.path.join(self.tdir, "vol.npy"), np.ascontiguousarray(vol))
+        np.save(os.path.join(self.tdir, "T.npy"), np.ascontiguousarray(T))
+        np.save(os.path.join(self.tdir, "mask.npy"), np.ascontiguousarray(mask))
+
+    def voxels(self, pts, var_f: float) -> dict:
+        """The oracle at the voxels (x, y, z) of the staged volume, split over
+        the workers; returns the merged results and the wall seconds."""
+        import numpy as np
+        chunks = [c for c in np.array_split(np.asarray(pts), 2 * self.cores) if len(c)]
+        t0 = time.perf_counter()
+        res = self.pool.map(_oracle_voxels, [(self.tdir, c, self.n_order, var_f) for c in chunks],
+                            chunksize=1)
+        wall = time.perf_counter() - t0
+        out = {k: np.concatenate([r[k] for r in res]) for k in ("w", "C", "score", "lam", "q")}
+        out["wall"] = wall
+        return out
+
+    def close(self) -> None:
+        self.pool.close()
+        self.pool.join()
+        import shutil
+        shutil.rmtree(self.tdir, ignore_errors=True)
+
+
+def cpu_sample_workload(workload: str):
+    """The volume the oracle is timed on: the workload itself, or for the
+    large configurations a smaller volume with the same template, mask and
+    order (the oracle's cost per voxel is set by those)."""
+    import synth
     if workload in BATCH_WORKLOADS:
-        # the batch's first volume with its 32^3 template (cost per voxel is
-        # set by the template and the order, not by the data)
         cfg = synth.BATCH_CONFIGS[workload]
         bw = synth.batch_workload(workload, shapes_zyx=cfg["shapes_zyx"][:1], sizes=(32,),
-                                  n_rot=300)
-        wl = synth.Workload("batch-sample", bw.volumes[0], bw.templates[0], bw.masks[0],
-                            bw.radii[0], bw.n_order, bw.quadrature, bw.weights,
-                            bw.positions[0][0], bw.planted_quats[0][0], 0.0, bw.snr)
-    else:
-        # the per-voxel cost of the oracle is set by the template box and the
-        # order, so the large configs are sampled from a smaller volume
-        wl = load_workload(workload, n_rot=300, **CPU_SAMPLE_SHAPES.get(workload, {}))
-    s = wl.template.shape[0]
+                                  n_rot=ORACLE_TEMPLATE_ROTATIONS)
+        return synth.Workload("batch-sample", bw.volumes[0], bw.templates[0], bw.masks[0],
+                              bw.radii[0], bw.n_order, bw.quadrature, bw.weights,
+                              bw.positions[0][0], bw.planted_quats[0][0], 0.0, bw.snr)
+    return load_workload(workload, n_rot=ORACLE_TEMPLATE_ROTATIONS,
+                         **CPU_SAMPLE_SHAPES.get(workload, {}))
+
+
+def random_interior(shape_zyx, s: int, n: int, rng):
+    import numpy as np
     c = s // 2
-    T = o.tensor_template(wl.template, wl.mask, wl.quadrature.astype(np.float64), wl.weights,
-                          wl.n_order)
-    var_f = float(np.var(wl.volume.astype(np.float64)))
-    rng = np.random.default_rng(11)
-    Z, Y, X = wl.volume.shape
-    times = []
-    for _ in range(steps):
-        pts = np.stack([rng.integers(c, X - s + c + 1, n_vox), rng.integers(c, Y - s + c + 1, n_vox),
-                        rng.integers(c, Z - s + c + 1, n_vox)], axis=1)
-        t0 = time.perf_counter()
-        w, C = o.components_at(wl.volume, T, wl.mask, pts, var_f=var_f)
-        o.frobenius_score(C.T, wl.n_order)
-        o.dominant_z_eigenpair(C, wl.n_order)
-        times.append(time.perf_counter() - t0)
-    return dict(times=times, n_vox=n_vox)
+    Z, Y, X = shape_zyx
+    return np.stack([rng.integers(c, X - s + c + 1, n), rng.integers(c, Y - s + c + 1, n),
+                     rng.integers(c, Z - s + c + 1, n)], axis=1)
 
 
-def run_cpu_sample(workload: str, n_vox: int, steps: int) -> dict:
-    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
-               CUDA_VISIBLE_DEVICES="")
-    cmd = [sys.executable, os.path.abspath(__file__), "--workload", workload,
-           "--cpu-sample", str(n_vox), "--sample-steps", str(steps)]
-    out = subprocess.run(cmd, env=env, capture_output=True, text=True, check=True)
-    return json.loads(out.stdout.strip().splitlines()[-1])
+def oracle_timing(workload: str, n_vox: int, steps: int, cores: int | None = None) -> dict:
+    """Wall time of the oracle over `steps` samples of `n_vox` random interior
+    voxels each, on all host cores (after every worker has warmed up)."""
+    import numpy as np
+    wl = cpu_sample_workload(workload)
+    pool = OraclePool(wl.n_order, cores)
+    try:
+        T = pool.tensor_template(wl.template, wl.mask, wl.quadrature.astype(np.float64),
+                                 wl.weights, "t")
+        pool.stage(wl.volume, T, wl.mask)
+        var_f = float(np.var(wl.volume.astype(np.float64)))
+        rng = np.random.default_rng(11)
+        pool.voxels(random_interior(wl.volume.shape, wl.template.shape[0], pool.cores, rng), var_f)
+        times = []
+        for _ in range(steps):
+            pts = random_interior(wl.volume.shape, wl.template.shape[0], n_vox, rng)
+            times.append(pool.voxels(pts, var_f)["wall"])
+    finally:
+        pool.close()
+    return dict(times=times, n_vox=n_vox, cores=pool.cores, shape=wl.volume.shape[::-1])
 
 
-def cpu_baseline_obj(res: dict, workload: str = "") -> dict:
+def cpu_baseline_obj(res: dict, workload: str = "", warmup_steps: int = 1) -> dict:
     tot = sum(res["times"])
-    per_vox = tot / (res["n_vox"] * len(res["times"]))
+    n = res["n_vox"] * len(res["times"])
     where = "the same workload"
     if workload in CPU_SAMPLE_SHAPES:
-        where = (f"a {'x'.join(map(str, CPU_SAMPLE_SHAPES[workload]['shape_zyx'][::-1]))} volume "
-                 "with the same template, order and mask")
+        where = (f"a {'x'.join(map(str, res['shape']))} volume with the same template, order "
+                 "and mask (the oracle's cost per voxel is set by those)")
     elif workload in BATCH_WORKLOADS:
         where = "the batch's first volume with its 32^3 template"
-    return dict(value=1.0 / per_vox, unit=UNIT, cores=1, kind="oracle",
+    return dict(value=n / tot, unit=UNIT, cores=res["cores"], kind="oracle",
                 sample=f"{len(res['times'])} x {res['n_vox']} random interior voxels of {where}: "
-                       "local statistics, K component correlations by direct sum, "
-                       "Frobenius score and dominant Z-eigenpair (FP64 numpy oracle, one BLAS "
-                       f"thread); {tot:.1f} s of CPU work; tensor template built beforehand")
+                       "local statistics, K component correlations by direct sums, Frobenius "
+                       "score and dominant Z-eigenpair (FP64 numpy oracle), one process per core "
+                       f"with one BLAS thread; {tot:.1f} s wall after {warmup_steps} untimed "
+                       "warm-up sample per worker; tensor template built beforehand")
+
+
+def run_reference(args) -> None:
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    cores = oracle_cores()
+    n_vox = 4 * cores
+    res = oracle_timing(args.workload, n_vox, args.warmup + args.steps, cores)
+    times = res["times"][args.warmup:]
+    total = sum(times)
+    value = n_vox * len(times) / total
+    cpu = cpu_baseline_obj(dict(res, times=times), args.workload, args.warmup)
+    line = dict(
+        metric=METRIC, value=value, unit=UNIT, n_gpus=args.gpus, steps=args.steps,
+        warmup=args.warmup, ms_per_step=1e3 * total / len(times), higher_is_better=True,
+        scaling="weak", vs_baseline=None, dtype="f64", data="synthetic",
+        config=dict(workload=WORKLOAD[args.workload], step=f"{n_vox} sampled interior voxels"),
+        impl="reference", cpu_baseline=cpu,
+        e2e=dict(value=value, unit=UNIT, h2d_bytes_per_step=0, d2h_bytes_per_step=0),
+    )
+    print(json.dumps(line), flush=True)
+
+
+def gpu_maps_at(matcher, pts) -> dict:
+    """w, score, lambda and q of problem 0 at the voxels (x, y, z)."""
+    import torch
+    zi, yi, xi = (torch.as_tensor(pts[:, k]).cuda() for k in (2, 1, 0))
+    return dict(w=matcher.w[0][zi, yi, xi].cpu().numpy(),
+                score=matcher.score[0][zi, yi, xi].cpu().numpy(),
+                lam=matcher.lam[0][zi, yi, xi].cpu().numpy(),
+                quat=matcher.quat[0][zi, yi, xi].cpu().numpy())
+
+
+def error_stats(got: dict, ora: dict, n_order: int, n_planted: int, tol: float) -> dict:
+    """Errors of the GPU maps against the oracle at the sampled voxels."""
+    import numpy as np
+    from oracle import ttm_oracle as o
+    dscore = np.abs(got["score"] - ora["score"])
+    dlam = np.abs(got["lam"] - ora["lam"])
+    relw = np.abs(got["w"] - ora["w"]) / np.where(ora["w"] > 0, ora["w"], 1.0)
+    phi = o.phi_unique(ora["C"], got["quat"].astype(np.float64), n_order)
+    ang = o.rotation_angle_deg(got["quat"][:n_planted], ora["q"][:n_planted])
+    # planted voxels where phi has a unique maximiser to the gate: there the
+    # rotation itself is compared (else any maximiser is a valid answer)
+    valid = phi >= ora["lam"] - tol
+    return dict(voxels=int(len(dscore)), planted=int(n_planted),
+                max_abs_score=float(dscore.max()), max_abs_lambda=float(dlam.max()),
+                max_rel_w=float(relw.max()), max_phi_shortfall=float((ora["lam"] - phi).max()),
+                rotation_deg_planted=dict(median=float(np.median(ang)), max=float(ang.max()),
+                                          within_1deg=float(np.mean(ang <= 1.0))),
+                tolerance=tol,
+                within_tolerance=bool(dscore.max() <= tol and dlam.max() <= tol and valid.all()
+                                      and relw.max() <= 1e-5))
+
+
+def oracle_error_runs(ttm, wl, plans: dict, pool, n_planted: int = 32, n_random: int = 32,
+                      seed: int = 5) -> dict:
+    """GPU maps of the volume under each plan option set of `plans` (name ->
+    (PlanOpts, tolerance)), with the tensor template of ERROR_ROTATIONS
+    quadrature rotations on both sides, against the oracle at the planted
+    centres and random interior voxels."""
+    import numpy as np
+    import synth
+    import torch
+    quad = synth.super_fibonacci_quaternions(ERROR_ROTATIONS)
+    wts = np.full(len(quad), 1.0 / len(quad))
+    s = wl.template.shape[0]
+    rng = np.random.default_rng(seed)
+    pts = np.concatenate([wl.positions[:n_planted],
+                          random_interior(wl.volume.shape, s, n_random, rng)]).astype(np.int64)
+    n_pl = min(n_planted, len(wl.positions))
+    Z, Y, X = wl.volume.shape
+    comp, desc = ttm.build_template(wl.template, wl.mask, wl.n_order, quad.astype(np.float32))
+    vol = torch.from_numpy(wl.volume).cuda()
+    got = {}
+    for name, (opts, _) in plans.items():
+        m = ttm.Matcher([(comp, desc, wl.mask)], [((X, Y, Z), 0)], opts=opts)
+        m.run([vol])
+        torch.cuda.synchronize()
+        if ttm.ttm_plan_device_status(m.plan, m.ws) != 0:
+            raise RuntimeError("device status of the error run")
+        got[name] = gpu_maps_at(m, pts)
+        m.close()
+        del m
+        torch.cuda.empty_cache()
+    del vol, comp
+    torch.cuda.empty_cache()
+    T = pool.tensor_template(wl.template, wl.mask, quad, wts, "e")
+    pool.stage(wl.volume, T, wl.mask)
+    ora = pool.voxels(pts, float(np.var(wl.volume.astype(np.float64))))
+    out = {name: error_stats(got[name], ora, wl.n_order, n_pl, tol)
+           for name, (_, tol) in plans.items()}
+    for v in out.values():
+        v["quadrature_rotations"] = ERROR_ROTATIONS
+    return out
 
 
 # ---------------------------------------------------------------------------
@@ -264,71 +497,127 @@ def job_rate(units_per_rank: float, steps: int, world: int, t_max_ms: float) -> 
     return units_per_rank * steps * world / (t_max_ms * 1e-3)
 
 
-def roofline(kernels: dict, steps: int, nvox: int, K: int, n_taps: int, n_grid: int,
-             n_cand: int, newton: int, peaks: dict, spectrum_bytes: float = 0.0,
-             n_interior: int | None = None, tc_direct: bool = False,
-             fp32_maps: bool = True) -> dict:
-    """Roofline object for the kernel class with the largest share.  The
-    rotation kernels visit only the interior voxels (n_interior)."""
-    n_int = nvox if n_interior is None else n_interior
-    name = max(kernels, key=lambda k: kernels[k]["ms"])
-    ms_launch = kernels[name]["ms"] / max(kernels[name]["launches"], 1)
-    launches_per_step = kernels[name]["launches"] / steps
-    src = []
-    if name == "direct_corr" and tc_direct:
-        npad = (K + 15) // 16 * 16
-        work = 2.0 * npad * n_taps * n_int / launches_per_step
-        bound, peak, unit, scale = "tensor", peaks.get("bf16_tflops", 1900.0), "TFLOP/s", 1e12
-        src = ["k_direct_tc.cu"]
-        peak_source = "measured dense bf16 (MEASURED_PEAKS.json bf16_tflops); fp16 runs at the bf16 rate"
+def a5_flop_per_voxel(K: int) -> float:
+    """Planned work of the score + rotation step per interior voxel: 32 start
+    evaluations of phi (5 FP32 FLOP per component) and ~30 power iterations
+    (8 FLOP per component): K x (32 x 5 + 30 x 8) = 400 K (14 k at n = 4,
+    33.6 k at n = 6)."""
+    return 400.0 * K
+
+
+def refinement_flop_per_voxel(K: int, n_cand: int = CANDIDATES, newton: int = NEWTON_STEPS) -> float:
+    """FP32 FLOP of this build's refinement per interior voxel: every candidate
+    takes 3 evaluations of C x^(n-1) (10 ops per term of its 4 sums of KG
+    terms) and 2 normalisations; the REFINED best take 1 + newton evaluations
+    of C x^(n-2) (10 sums of KB terms) and newton 4x4 solves."""
+    n_ord = {10: 2, 35: 4, 84: 6, 165: 8}.get(K, 4)
+    KB = (n_ord + 1) * n_ord * (n_ord - 1) // 6
+    KG = (n_ord + 2) * (n_ord + 1) * n_ord // 6
+    power = 3 * 10 * KG + 2 * 12
+    newton_part = (1 + newton) * (2 * 10 * KB + 2 * KB + 40) + newton * 150
+    return float(n_cand * power + min(REFINED, n_cand) * newton_part)
+
+
+def stage_traffic(name: str, K: int, storage: str, n_int: int):
+    """ncu DRAM bytes per step of a stage, from the records whose sources are
+    unchanged (None when there is no current record)."""
+    total = 0.0
+    for cls in STAGE_CLASSES.get(name, (name,)):
+        rec = next((r for r in NCU_TRAFFIC.get(cls, ())
+                    if r["K"] == K and r["storage"] == storage
+                    and r["source_sha"] == source_hash(r["sources"])), None)
+        if rec is None:
+            return None
+        total += rec["bytes_per_voxel"] * n_int
+    return total
+
+
+# the score + rotation step runs as two kernel classes (grid search and
+# refinement) on two streams; its roofline is taken over both
+STAGE_CLASSES = {"score_rotation": ("rotation_search", "rotation_polish")}
+
+
+def roofline(kernels: dict, steps: int, geo: dict, peaks: dict) -> dict:
+    """Roofline object of the stage with the largest share of the step.
+
+    Work is algorithmic: FLOP for the score + rotation step (the planned a5
+    count), bytes for the memory-bound stages (what each pass must read and
+    write at the plan's storage precision), never a count of what the kernel
+    happens to execute.  The score + rotation stage is timed as the sum of its
+    two kernel classes' CUDA-event times (they overlap on two streams, so the
+    sum is an upper bound of the stage's share of the step)."""
+    K, nvox, n_int = geo["K"], geo["nvox"], geo["n_interior"]
+    per_step = {k: v["ms"] / steps for k, v in kernels.items()}
+    stages = dict(per_step)
+    if all(c in per_step for c in STAGE_CLASSES["score_rotation"]):
+        stages["score_rotation"] = sum(per_step.pop(c) for c in STAGE_CLASSES["score_rotation"])
+        for c in STAGE_CLASSES["score_rotation"]:
+            stages.pop(c)
+    name = max(stages, key=stages.get)
+    ms = stages[name]
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    bf16 = peaks.get("bf16_tflops", 1900.0)
+    cs = 4.0 if geo["mixed"] else 8.0           # bytes per stored complex value
+    msz = 2.0 if geo["mixed"] else 4.0          # bytes per stored map value
+    nh = geo["spectrum_values"]                 # half-spectrum values of the FFT box
+    extra = {}
+    if name == "score_rotation":
+        work, scale, unit = a5_flop_per_voxel(K) * n_int, 1e12, "TFLOP/s"
+        bound, peak = "alu", FP32_ALU_PEAK_TFLOPS
+        peak_source = "derived: 152 SMs x 128 FP32 lanes x 2 FLOP x 2070 MHz"
+        ks = kernels.get("rotation_search", {}).get("ms", 0.0) / steps
+        kp_ = kernels.get("rotation_polish", {}).get("ms", 0.0) / steps
+        if ks > 0 and K in (35, 84):
+            kp = 48 if K == 35 else 96
+            mma = 2.0 * 2048 * kp * n_int / (ks * 1e-3) / 1e12
+            extra["tensor_pipe"] = dict(kernel="rotation_search", achieved=round(mma, 2),
+                                        peak=round(bf16, 1), unit="TFLOP/s", frac=round(mma / bf16, 4),
+                                        work="dense FP16 grid contraction 2 x 2048 x KP per voxel")
+        if kp_ > 0:
+            ref = refinement_flop_per_voxel(K) * n_int / (kp_ * 1e-3) / 1e12
+            extra["refinement_alu"] = dict(kernel="rotation_polish", achieved=round(ref, 2),
+                                           peak=round(FP32_ALU_PEAK_TFLOPS, 2), unit="TFLOP/s",
+                                           frac=round(ref / FP32_ALU_PEAK_TFLOPS, 4),
+                                           work=f"{refinement_flop_per_voxel(K):.0f} FLOP per voxel "
+                                                f"({REFINEMENT})")
+        work_note = f"{a5_flop_per_voxel(K):.0f} FLOP per interior voxel (400 K)"
     elif name == "direct_corr":
-        work = 2.0 * K * n_taps * nvox / launches_per_step
-        bound, peak, unit, scale = "alu", FP32_ALU_PEAK_TFLOPS, "TFLOP/s", 1e12
-        src = ["k_direct.cu"]
-        peak_source = "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz"
-    elif name == "rotation_search" and K in (35, 84) and n_grid == 2048:
-        kp = 48 if K == 35 else 96                               # K + constant column, padded
-        work = 2.0 * n_grid * kp * n_int / launches_per_step     # FP16 MMA
-        bound, peak, unit, scale = "tensor", peaks.get("bf16_tflops", 1900.0), "TFLOP/s", 1e12
-        src = ["k_search_tc.cu", "k_rotation.cuh"]
-        peak_source = "measured dense bf16 (MEASURED_PEAKS.json bf16_tflops); fp16 runs at the bf16 rate"
-    elif name in ("rotation_search", "rotation_polish"):
-        # order n from K = C(n+3, 3); H = C x^(n-2) has 10 entries of KB terms
-        n_ord = {10: 2, 35: 4, 84: 6, 165: 8}.get(K, 4)
-        KB = (n_ord + 1) * n_ord * (n_ord - 1) // 6
-        KG = (n_ord + 2) * (n_ord + 1) * n_ord // 6
-        # every candidate: 3 evaluations of C x^(n-1) and 2 normalisations; the
-        # REFINED best: 1 + newton evaluations of C x^(n-2) and newton Newton solves
-        power = 3 * 10 * KG + 2 * 12
-        newton_part = (1 + newton) * (2 * 10 * KB + 2 * KB + 40) + newton * 150
-        per_vox = n_cand * power + min(REFINED, n_cand) * newton_part
-        work = ((2.0 * n_grid * K + 2 * K) if name == "rotation_search" else per_vox) \
-            * n_int / launches_per_step
-        bound, peak, unit, scale = "alu", FP32_ALU_PEAK_TFLOPS, "TFLOP/s", 1e12
-        src = ["k_rotation.cuh", "k_rotation.cu", "k_rotation_n4.cu"]
-        peak_source = "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz"
-    else:
-        # memory-bound stage: algorithmic bytes
-        if name == "local_stats":
-            per = 8.0 * nvox
-        elif name == "fft_spectrum_inverse":
-            per = spectrum_bytes * (1 + 2 * K)
-        elif name == "fft_inverse":
-            per = spectrum_bytes * 3 * K + 4.0 * K * nvox
+        if geo.get("tc_direct"):
+            npad = (K + 15) // 16 * 16
+            work, scale, unit = 2.0 * npad * geo["n_taps"] * n_int, 1e12, "TFLOP/s"
+            bound, peak = "tensor", bf16
+            peak_source = "measured dense bf16 (bf16_tflops); fp16 runs at the bf16 rate"
         else:
-            per = 8.0 * nvox
-        work = per / launches_per_step
-        bound, peak, unit, scale = "hbm", peaks.get("hbm_gbs", 6800.0), "GB/s", 1e9
-        peak_source = "measured (MEASURED_PEAKS.json hbm_gbs)"
-    achieved = work / (ms_launch * 1e-3) / scale
-    traffic = None
-    rec = NCU_TRAFFIC.get(name)
-    if (rec and src and fp32_maps and rec["K"] == K
-            and rec.get("source_sha") == source_hash(src)):
-        traffic = round(rec["bytes_per_voxel"] * n_int / launches_per_step)
-    return dict(kernel=name, bound=bound, achieved=round(achieved, 3), peak=round(peak, 2),
-                unit=unit, frac=round(achieved / peak, 4), traffic=traffic,
-                ms_per_launch=round(ms_launch, 4), peak_source=peak_source)
+            work, scale, unit = 2.0 * K * geo["n_taps"] * nvox, 1e12, "TFLOP/s"
+            bound, peak = "alu", FP32_ALU_PEAK_TFLOPS
+            peak_source = "derived: 152 SMs x 128 FP32 lanes x 2 FLOP x 2070 MHz"
+        work_note = "2 x K x mask voxels per voxel"
+    else:
+        if name == "fft_inverse":
+            # y pass: read + write every product spectrum; x pass: read it,
+            # write the real map
+            work = K * (3.0 * nh * cs + nvox * msz)
+            work_note = "K x (3 x half spectrum + map)"
+        elif name == "fft_spectrum_inverse":
+            # image spectrum once, every template spectrum read, every product written
+            work = nh * (8.0 + 2.0 * K * cs)
+            work_note = "image spectrum + K x (template spectrum + product)"
+        elif name == "fft_forward":
+            work = 4.0 * nvox + 40.0 * nh
+            work_note = "volume read + three passes over the FP32 half spectrum"
+        else:
+            work = 8.0 * nvox
+            work_note = "one read of the volume, one write of a map"
+        scale, unit, bound, peak = 1e9, "GB/s", "hbm", hbm
+        peak_source = "measured copy bandwidth (hbm_gbs)"
+    achieved = work / (ms * 1e-3) / scale
+    traffic = stage_traffic(name, K, "bf16" if geo["mixed"] else "f32", n_int)
+    out = dict(kernel=name, bound=bound, achieved=round(achieved, 3), peak=round(peak, 2),
+               unit=unit, frac=round(achieved / peak, 4),
+               traffic=None if traffic is None else round(traffic),
+               ms_per_step=round(ms, 4), work=work_note, peak_source=peak_source)
+    out.update(extra)
+    return out
 
 
 def run_ours(args) -> None:
@@ -550,37 +839,62 @@ def run_ours(args) -> None:
         m2.close()
 
     if rank != 0:
+        matcher.close()
         if dist:
             dist.destroy_process_group()
         return
-    peaks = {}
-    try:
-        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
-    except (OSError, ValueError):
-        pass
+    peaks = load_peaks()
+    box = tuple(ttm.ttm_plan_problem_fft_box(matcher.plan, 0)) if path == 2 else (X, Y, Z)
     n_taps = int(wl.mask.sum())
-    Xh = X // 2 + 1
-    spec_bytes = 8.0 * Xh * Y * Z if path == 2 else 0.0
     s_edge = wl.template.shape[0]
     n_interior = max(X - s_edge + 1, 0) * max(Y - s_edge + 1, 0) * max(Z - s_edge + 1, 0)
-    rf = roofline(kern, args.steps, nvox, desc.K, n_taps, 2048, CANDIDATES, NEWTON_STEPS, peaks, spec_bytes,
-                  n_interior, ttm.ttm_plan_problem_tensor_direct(matcher.plan, 0),
-                  fp32_maps=args.precision == "fp32")
-    cpu = None
+    geo = dict(K=desc.K, nvox=nvox, n_interior=n_interior, n_taps=n_taps,
+               mixed=args.precision == "mixed",
+               spectrum_values=float((box[0] // 2 + 1) * box[1] * box[2]),
+               tc_direct=bool(ttm.ttm_plan_problem_tensor_direct(matcher.plan, 0)))
+    rf = roofline(kern, args.steps, geo, peaks)
+    matcher.close()
+    del matcher, vol, flush
+    torch.cuda.empty_cache()
+
+    # the error of the maps against the FP64 oracle, and (for the headline
+    # configuration) FP32 against bf16 storage at 512^3, both against the oracle
+    errors, pair, cpu = None, None, None
+    pool = None
+    if world == 1 and (args.oracle_errors or not args.no_cpu_baseline):
+        pool = OraclePool(wl.n_order)
+    try:
+        if pool is not None and args.oracle_errors:
+            tol = 5e-3 if args.precision == "mixed" else 1e-4
+            errors = oracle_error_runs(ttm, wl, {args.precision: (opts, tol)}, pool)[args.precision]
+        if pool is not None and args.precision_pair and args.workload == "c5":
+            pool.n_order = 4
+            pair = precision_pair(ttm, args, pool, stream)
+            pool.n_order = wl.n_order
+    finally:
+        if pool is not None:
+            pool.close()
     if not args.no_cpu_baseline and world == 1:
-        cpu = cpu_baseline_obj(run_cpu_sample(args.workload, 128, 2), args.workload)
+        cores = oracle_cores()
+        res = oracle_timing(args.workload, 8 * cores, 1, cores)
+        cpu = cpu_baseline_obj(res, args.workload)
     line = dict(
         metric=METRIC, value=value, unit=UNIT, n_gpus=world, steps=args.steps,
         warmup=args.warmup, ms_per_step=t_max / args.steps, higher_is_better=True,
         scaling="weak", vs_baseline=None, dtype="f32" if args.precision == "fp32" else "bf16/f32",
         data="synthetic",
         config=dict(workload=WORKLOAD[args.workload], path={1: "direct", 2: "fft"}.get(path, path),
-                    voxels=nvox, interior_voxels=n_interior, tensor_order=wl.n_order, K=desc.K, mask_voxels=n_taps,
-                    rotation_grid=2048, refinement=REFINEMENT,
+                    precision=("FP32 storage and arithmetic" if args.precision == "fp32" else
+                               "bf16 storage of template spectra, product spectra and "
+                               "correlation maps; FP32 arithmetic"),
+                    fft_box=list(box) if path == 2 else None,
+                    voxels=nvox, interior_voxels=n_interior, tensor_order=wl.n_order, K=desc.K,
+                    mask_voxels=n_taps, rotation_grid=2048, refinement=REFINEMENT,
                     l2="flushed (256 MB write) before every timed step",
                     parallelism="replicas" if world > 1 else "single GPU",
                     template_build_ms=round(build_ms, 2), quadrature_rotations=desc.n_rot),
-        roofline=rf, cpu_baseline=cpu, e2e=e2e, gpu_launches=launches, classical=classical,
+        roofline=rf, cpu_baseline=cpu, e2e=e2e, gpu_launches=launches,
+        error_vs_oracle=errors, precision_pair=pair, classical=classical,
         mixed_precision=mixed, peaks_only=peaks_only,
         clocks=clk,
         kernels={k: dict(ms_per_step=round(v["ms"] / args.steps, 4),
@@ -589,9 +903,67 @@ def run_ours(args) -> None:
                  for k, v in kern.items()},
     )
     print(json.dumps(line), flush=True)
-    matcher.close()
     if dist:
         dist.destroy_process_group()
+
+
+def load_peaks() -> dict:
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        return {}
+
+
+def time_steps(matcher, vol, steps: int, warmup: int, stream) -> float:
+    """Mean CUDA-event milliseconds of `steps` runs after `warmup` runs, L2
+    flushed before each."""
+    import torch
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=vol.device)
+    for _ in range(warmup):
+        matcher.run([vol])
+    torch.cuda.synchronize()
+    tot = 0.0
+    for _ in range(steps):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        matcher.run([vol])
+        b.record(stream)
+        b.synchronize()
+        tot += a.elapsed_time(b)
+    return tot / steps
+
+
+def precision_pair(ttm, args, pool, stream) -> dict:
+    """The 512^3 configuration (200 copies of a 40^3 template, SNR 0.3, order 4)
+    matched with FP32 storage and with bf16 storage on the same GPU: voxels/s
+    of each, and each one's error against the oracle (error runs with the
+    ERROR_ROTATIONS quadrature on both sides)."""
+    import torch
+    wl = load_workload("c3")
+    Z, Y, X = wl.volume.shape
+    comp, desc = ttm.build_template(wl.template, wl.mask, wl.n_order, wl.quadrature)
+    vol = torch.from_numpy(wl.volume).cuda()
+    plans, out = {}, {}
+    for name, prec, tol in (("fp32", ttm.TTM_PREC_FP32, 1e-4), ("bf16", ttm.TTM_PREC_MIXED, 5e-3)):
+        o_ = ttm.PlanOpts()
+        o_.path = ttm.TTM_PATH_FFT
+        o_.precision = prec
+        plans[name] = (o_, tol)
+        m = ttm.Matcher([(comp, desc, wl.mask)], [((X, Y, Z), 0)], opts=o_)
+        ms = time_steps(m, vol, 5, 2, stream)
+        if ttm.ttm_plan_device_status(m.plan, m.ws) != 0:
+            raise RuntimeError("device status of the 512^3 run")
+        out[name] = dict(value=X * Y * Z / (ms * 1e-3), unit=UNIT, ms_per_step=round(ms, 3))
+        m.close()
+        del m
+        torch.cuda.empty_cache()
+    del vol, comp
+    torch.cuda.empty_cache()
+    errs = oracle_error_runs(ttm, wl, plans, pool)
+    for name in out:
+        out[name]["error_vs_oracle"] = errs[name]
+    return dict(workload=WORKLOAD["c3"], steps=5, warmup=2, **out)
 
 
 def run_batch(args) -> None:
@@ -727,22 +1099,22 @@ def run_batch(args) -> None:
         if dist:
             dist.destroy_process_group()
         return
-    peaks = {}
-    try:
-        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
-    except (OSError, ValueError):
-        pass
+    peaks = load_peaks()
     n_int = 0
-    spec_bytes = 0.0
-    for (X, Y, Z), k in problems:
+    spec_vals = 0.0
+    for p, ((X, Y, Z), k) in enumerate(problems):
         sk = bw.templates[k].shape[0]
         n_int += max(X - sk + 1, 0) * max(Y - sk + 1, 0) * max(Z - sk + 1, 0)
-        spec_bytes += 8.0 * (X // 2 + 1) * Y * Z
-    rf = roofline(kern, 1, nvox_total, tmpls[0][1].K, 0, 2048, CANDIDATES, NEWTON_STEPS, peaks,
-                  spec_bytes / max(1, len(problems)), n_int, fp32_maps=args.precision == "fp32")
+        if paths[p] == ttm.TTM_PATH_FFT:
+            bx = ttm.ttm_plan_problem_fft_box(matcher.plan, p)
+            spec_vals += float((bx[0] // 2 + 1) * bx[1] * bx[2])
+    geo = dict(K=tmpls[0][1].K, nvox=nvox_total, n_interior=n_int, n_taps=0,
+               mixed=args.precision == "mixed", spectrum_values=spec_vals, tc_direct=False)
+    rf = roofline(kern, 1, geo, peaks)
     cpu = None
     if not args.no_cpu_baseline and world == 1:
-        cpu = cpu_baseline_obj(run_cpu_sample(args.workload, 128, 2), args.workload)
+        cores = oracle_cores()
+        cpu = cpu_baseline_obj(oracle_timing(args.workload, 8 * cores, 1, cores), args.workload)
     n_fft = sum(1 for p in paths if p == ttm.TTM_PATH_FFT)
     line = dict(
         metric=METRIC, value=value, unit=UNIT, n_gpus=world, steps=args.steps,
@@ -770,28 +1142,6 @@ def run_batch(args) -> None:
     matcher.close()
     if dist:
         dist.destroy_process_group()
-
-
-def run_reference(args) -> None:
-    rank = int(os.environ.get("RANK", "0"))
-    if rank != 0:
-        return
-    n_vox = 128
-    steps = args.warmup + args.steps
-    res = run_cpu_sample(args.workload, n_vox, steps)
-    times = res["times"][args.warmup:]
-    total = sum(times)
-    value = n_vox * len(times) / total
-    cpu = cpu_baseline_obj(dict(times=times, n_vox=n_vox), args.workload)
-    line = dict(
-        metric=METRIC, value=value, unit=UNIT, n_gpus=args.gpus, steps=args.steps,
-        warmup=args.warmup, ms_per_step=1e3 * total / len(times), higher_is_better=True,
-        scaling="weak", vs_baseline=None, dtype="f64", data="synthetic",
-        config=dict(workload=WORKLOAD[args.workload], step=f"{n_vox} sampled voxels"),
-        impl="reference", cpu_baseline=cpu,
-        e2e=dict(value=value, unit=UNIT, h2d_bytes_per_step=0, d2h_bytes_per_step=0),
-    )
-    print(json.dumps(line), flush=True)
 
 
 # ---------------------------------------------------------------------------
@@ -904,9 +1254,6 @@ def run_order_sweep(args) -> None:
 
 def main():
     args = parse()
-    if args.cpu_sample:
-        print(json.dumps(cpu_sample(args.workload, args.cpu_sample, args.sample_steps)))
-        return
     if args.impl == "reference":
         run_reference(args)
     elif args.order_sweep:
