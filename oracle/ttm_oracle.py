@@ -598,3 +598,91 @@ def extract_peaks(score: np.ndarray, threshold: float, radius: int,
     idx = cand[ok]
     order = np.lexsort((idx, -flat[idx]))
     return idx[order][:max_peaks]
+
+
+# ==========================================================================
+# The S'-consistent normalisation (Sec. 3.3, proof of Theorem 3.1, and the
+# false-positive discussion of Sec. 3.4).
+#
+# The proof of Theorem 3.1 shows phi(Q) = C_n(x) . Q^(n) = w(x) <tau_x f, t_Q>_S'
+# with S' = S_2 o S and S_2(t) = (t (*) K)(I_d), K(R) = Re(R)^n: S_2 averages
+# the rotated copies t_R of its argument with weight Re(R)^n (Re(R^-1) =
+# Re(R)), so <f, g>_S' = int Re(R)^n <f, g_R>_S dR for a rotation-invariant
+# mask.  TTM normalises with S (w(x) = 1/||P_S tau_x f||_S, ||t||_S = 1); the
+# S'-consistent value divides phi(Q) / w(x) by ||P_S' tau_x f||_S' ||t_Q||_S'
+# instead, which keeps it in [-1, 1] with 1 at a match.  Discretised with the
+# caller's quadrature {q_j, w_j} and trilinear rotation (the readings above);
+# h is the identity.
+# ==========================================================================
+
+
+def s2_apply(u: np.ndarray, quats: np.ndarray, weights: np.ndarray, n: int) -> np.ndarray:
+    """S_2(u) = sum_j w_j Re(q_j)^n u_{R_j}: the Re(R)^n-weighted average of
+    the rotated copies of the s^3 box u (rotate_template)."""
+    u = np.asarray(u, dtype=np.float64)
+    out = np.zeros_like(u)
+    for q, wj in zip(np.asarray(quats, dtype=np.float64), np.asarray(weights, dtype=np.float64)):
+        a = q[0] / np.linalg.norm(q)
+        out += wj * a ** n * rotate_template(u, q)
+    return out
+
+
+def sprime_inner(f: np.ndarray, g: np.ndarray, m: np.ndarray, quats: np.ndarray,
+                 weights: np.ndarray, n: int) -> float:
+    """<f, g>_S' = <f, S'(g)> with S'(g) = S_2(S(g)) = S_2(m g) (h = identity)."""
+    m = np.asarray(m, dtype=np.float64)
+    return float(np.sum(np.asarray(f, dtype=np.float64)
+                        * s2_apply(m * np.asarray(g, dtype=np.float64), quats, weights, n)))
+
+
+def sprime_projected_norm(patch: np.ndarray, m: np.ndarray, quats: np.ndarray,
+                          weights: np.ndarray, n: int) -> float:
+    """||P_S' p||_S' of an s^3 patch: P_S' p = p - (<p, 1>_S' / <1, 1>_S') 1
+    removes the S'-mean (the projection of Sec. 2, taken in S')."""
+    p = np.asarray(patch, dtype=np.float64)
+    one = np.ones_like(p)
+    mean = sprime_inner(p, one, m, quats, weights, n) / sprime_inner(one, one, m, quats, weights, n)
+    g = p - mean
+    return math.sqrt(max(sprime_inner(g, g, m, quats, weights, n), 0.0))
+
+
+def sprime_ncc_at(f: np.ndarray, t: np.ndarray, m: np.ndarray, quats: np.ndarray,
+                  weights: np.ndarray, n: int, points_xyz: np.ndarray,
+                  Q: np.ndarray) -> np.ndarray:
+    """The S'-consistent normalised correlation at each point x and rotation Q
+    (one Q per point):  <P_S' tau_x f, t~_Q>_S' / (||P_S' tau_x f||_S' ||t~_Q||_S'),
+    t~_Q the masked, S-normalised template rotated by Q (rotated_normalised)."""
+    s = np.asarray(m).shape[0]
+    P = patches_at(f, points_xyz, s).reshape(-1, s, s, s)
+    out = np.empty(len(P))
+    for i, (p, q) in enumerate(zip(P, np.asarray(Q, dtype=np.float64).reshape(-1, 4))):
+        tq = rotated_normalised(t, m, q)
+        one = np.ones_like(p)
+        mean = sprime_inner(p, one, m, quats, weights, n) / sprime_inner(one, one, m, quats, weights, n)
+        g = p - mean
+        num = 0.5 * (sprime_inner(g, tq, m, quats, weights, n) + sprime_inner(tq, g, m, quats, weights, n))
+        den = math.sqrt(max(sprime_inner(g, g, m, quats, weights, n), 0.0)
+                        * max(sprime_inner(tq, tq, m, quats, weights, n), 0.0))
+        out[i] = num / den if den > 0 else 0.0
+    return out
+
+
+def sprime_rescale_at(f: np.ndarray, t: np.ndarray, m: np.ndarray, quats: np.ndarray,
+                      weights: np.ndarray, n: int, points_xyz: np.ndarray,
+                      var_f: Optional[float] = None) -> np.ndarray:
+    """The factor that turns TTM's S-normalised C_n(x) into the S'-consistent
+    one at each point: rho(x) = ||P_S tau_x f||_S / (||P_S' tau_x f||_S' ||t~||_S'),
+    so that rho(x) phi(Q) is phi(Q) / (w(x) ||P_S' tau_x f||_S' ||t~||_S') (the
+    template's S'-norm is taken unrotated; it does not depend on Q in the
+    continuum).  Scaling C_n(x) by rho(x) > 0 leaves its maximiser q unchanged
+    and scales the score and lambda."""
+    s = np.asarray(m).shape[0]
+    P = patches_at(f, points_xyz, s).reshape(-1, s, s, s)
+    w, _ = components_at(f, np.zeros((1, s, s, s)), m, points_xyz, var_f=var_f)
+    tt = normalise_under_mask(t, m)
+    tnorm = math.sqrt(max(sprime_inner(tt, tt, m, quats, weights, n), 0.0))
+    out = np.zeros(len(P))
+    for i, p in enumerate(P):
+        if w[i] > 0:
+            out[i] = (1.0 / w[i]) / (sprime_projected_norm(p, m, quats, weights, n) * tnorm)
+    return out
