@@ -52,6 +52,11 @@ WORKLOAD = dict(
     c5s="256x256x192 FP32 volume (profiling size), 40 planted copies of the 64^3 template of c5, "
         "SNR 0.2, ball mask r=31, tensor order n=6 (K=84), quadrature of 20000 rotations, "
         "mixed precision",
+    c5x="928x96x464 FP32 slab (profiling the length-960 x and length-480 z passes), 10 planted "
+        "copies of the 64^3 template of c5, SNR 0.2, ball mask r=31, tensor order n=2 (K=10), "
+        "mixed precision",
+    c5y="928x928x96 FP32 slab (profiling the length-960 y pass), 20 planted copies of the 64^3 "
+        "template of c5, SNR 0.2, ball mask r=31, tensor order n=2 (K=10), mixed precision",
     c5="928x928x464 FP32 volume, 2000 planted copies of a 64^3 lowpassed 30-blob template, "
        "SNR 0.2, ball mask r=31, tensor order n=6 (K=84), quadrature of 20000 rotations; FFT box "
        "960x960x480; mixed precision (bf16 template spectra, products and maps resident in HBM)",
@@ -64,7 +69,11 @@ BATCH_WORKLOADS = ("c4",)
 CPU_SAMPLE_SHAPES = dict(c3=dict(shape_zyx=(160, 160, 160), copies=10),
                          c5=dict(shape_zyx=(192, 192, 192), copies=8))
 WORKLOAD_OVERRIDES = dict(c2s=("c2", dict(shape_zyx=(128, 128, 128), copies=8)),
-                          c5s=("c5", dict(shape_zyx=(192, 256, 256), copies=40)))
+                          c5s=("c5", dict(shape_zyx=(192, 256, 256), copies=40)),
+                          c5x=("c5", dict(shape_zyx=(464, 96, 928), copies=10, n_order=2,
+                                          n_rot=2000)),
+                          c5y=("c5", dict(shape_zyx=(96, 928, 928), copies=20, n_order=2,
+                                          n_rot=2000)))
 
 
 def load_workload(name: str, **extra):
@@ -72,11 +81,22 @@ def load_workload(name: str, **extra):
     base, over = WORKLOAD_OVERRIDES.get(name, (name, {}))
     return synth.config_workload(base, **dict(over, **extra))
 FP32_ALU_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # SMs x FP32 lanes x FMA x max clock
-# the refinement's defaults: 8 candidates take two power steps, the 4 best of
-# the points reached take 3 Newton steps
-CANDIDATES, REFINED, NEWTON_STEPS = 8, 4, 3
-REFINEMENT = (f"{CANDIDATES} candidates x 2 power steps, the {REFINED} best x "
-              f"{NEWTON_STEPS} Newton steps")
+# the refinement's defaults (candidates taking two power steps, the best
+# points reached taking Newton steps, Newton steps): by tensor order
+REFINE_BUDGET = {6: (4, 2, 2)}
+DEFAULT_BUDGET = (8, 4, 3)
+
+
+def budget(K: int):
+    n_ord = {10: 2, 35: 4, 84: 6, 165: 8}.get(K, 4)
+    return REFINE_BUDGET.get(n_ord, DEFAULT_BUDGET)
+
+
+def refinement_text(K: int) -> str:
+    c, r, nw = budget(K)
+    return f"{c} candidates x 2 power steps, the {r} best x {nw} Newton steps"
+
+
 L2_FLUSH_BYTES = 256 << 20
 
 # Measured DRAM traffic of a kernel class from one ncu capture, per interior
@@ -101,7 +121,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="c5", choices=["c1", "c2", "c2s", "c3", "c4", "c5", "c5s"])
+    ap.add_argument("--workload", default="c5", choices=["c1", "c2", "c2s", "c3", "c4", "c5", "c5s", "c5x", "c5y"])
     ap.add_argument("--path", default="auto", choices=["auto", "direct", "fft"])
     ap.add_argument("--precision", default=None, choices=["fp32", "mixed"],
                     help="storage of spectra/products/correlation maps on the FFT path "
@@ -129,7 +149,7 @@ def parse():
                          "and 7112 sampled rotations; prints its own JSON line")
     args = ap.parse_args()
     if args.precision is None:
-        args.precision = "mixed" if args.workload in ("c5", "c5s") else "fp32"
+        args.precision = "mixed" if args.workload.startswith("c5") else "fp32"
     return args
 
 
@@ -353,8 +373,10 @@ def gpu_maps_at(matcher, pts) -> dict:
                 quat=matcher.quat[0][zi, yi, xi].cpu().numpy())
 
 
-def error_stats(got: dict, ora: dict, n_order: int, n_planted: int, tol: float) -> dict:
-    """Errors of the GPU maps against the oracle at the sampled voxels."""
+def error_stats(got: dict, ora: dict, n_order: int, n_planted: int, tol: float,
+                truth=None) -> dict:
+    """Errors of the GPU maps against the oracle at the sampled voxels (the
+    first n_planted are planted centres; truth: their planted rotations)."""
     import numpy as np
     from oracle import ttm_oracle as o
     dscore = np.abs(got["score"] - ora["score"])
@@ -365,7 +387,7 @@ def error_stats(got: dict, ora: dict, n_order: int, n_planted: int, tol: float) 
     # planted voxels where phi has a unique maximiser to the gate: there the
     # rotation itself is compared (else any maximiser is a valid answer)
     valid = phi >= ora["lam"] - tol
-    return dict(voxels=int(len(dscore)), planted=int(n_planted),
+    out = dict(voxels=int(len(dscore)), planted=int(n_planted),
                 max_abs_score=float(dscore.max()), max_abs_lambda=float(dlam.max()),
                 max_rel_w=float(relw.max()), max_phi_shortfall=float((ora["lam"] - phi).max()),
                 rotation_deg_planted=dict(median=float(np.median(ang)), max=float(ang.max()),
@@ -373,6 +395,14 @@ def error_stats(got: dict, ora: dict, n_order: int, n_planted: int, tol: float) 
                 tolerance=tol,
                 within_tolerance=bool(dscore.max() <= tol and dlam.max() <= tol and valid.all()
                                       and relw.max() <= 1e-5))
+    if truth is not None and n_planted:
+        def stats(a):
+            return dict(median=float(np.median(a)), max=float(a.max()),
+                        within_1deg=float(np.mean(a <= 1.0)), within_5deg=float(np.mean(a <= 5.0)))
+        out["rotation_deg_vs_planted_truth"] = dict(
+            gpu=stats(o.rotation_angle_deg(got["quat"][:n_planted], truth[:n_planted])),
+            oracle=stats(o.rotation_angle_deg(ora["q"][:n_planted], truth[:n_planted])))
+    return out
 
 
 def oracle_error_runs(ttm, wl, plans: dict, pool, n_planted: int = 32, n_random: int = 32,
@@ -410,7 +440,8 @@ def oracle_error_runs(ttm, wl, plans: dict, pool, n_planted: int = 32, n_random:
     T = pool.tensor_template(wl.template, wl.mask, quad, wts, "e")
     pool.stage(wl.volume, T, wl.mask)
     ora = pool.voxels(pts, float(np.var(wl.volume.astype(np.float64))))
-    out = {name: error_stats(got[name], ora, wl.n_order, n_pl, tol)
+    truth = np.asarray(wl.planted_quats[:n_pl], dtype=np.float64)
+    out = {name: error_stats(got[name], ora, wl.n_order, n_pl, tol, truth)
            for name, (_, tol) in plans.items()}
     for v in out.values():
         v["quadrature_rotations"] = ERROR_ROTATIONS
@@ -505,17 +536,23 @@ def a5_flop_per_voxel(K: int) -> float:
     return 400.0 * K
 
 
-def refinement_flop_per_voxel(K: int, n_cand: int = CANDIDATES, newton: int = NEWTON_STEPS) -> float:
+def refinement_flop_per_voxel(K: int, n_cand: int | None = None, newton: int | None = None,
+                              refined: int | None = None) -> float:
     """FP32 FLOP of this build's refinement per interior voxel: every candidate
     takes 3 evaluations of C x^(n-1) (10 ops per term of its 4 sums of KG
-    terms) and 2 normalisations; the REFINED best take 1 + newton evaluations
-    of C x^(n-2) (10 sums of KB terms) and newton 4x4 solves."""
+    terms) and 2 normalisations; the refined best take 1 + newton evaluations
+    of C x^(n-2) (10 sums of KB terms) and newton 4x4 solves.  Defaults: the
+    order's budget."""
+    c0, r0, nw0 = budget(K)
+    n_cand = c0 if n_cand is None else n_cand
+    newton = nw0 if newton is None else newton
+    refined = r0 if refined is None else refined
     n_ord = {10: 2, 35: 4, 84: 6, 165: 8}.get(K, 4)
     KB = (n_ord + 1) * n_ord * (n_ord - 1) // 6
     KG = (n_ord + 2) * (n_ord + 1) * n_ord // 6
     power = 3 * 10 * KG + 2 * 12
     newton_part = (1 + newton) * (2 * 10 * KB + 2 * KB + 40) + newton * 150
-    return float(n_cand * power + min(REFINED, n_cand) * newton_part)
+    return float(n_cand * power + min(refined, n_cand) * newton_part)
 
 
 def stage_traffic(name: str, K: int, storage: str, n_int: int):
@@ -579,7 +616,7 @@ def roofline(kernels: dict, steps: int, geo: dict, peaks: dict) -> dict:
                                            peak=round(FP32_ALU_PEAK_TFLOPS, 2), unit="TFLOP/s",
                                            frac=round(ref / FP32_ALU_PEAK_TFLOPS, 4),
                                            work=f"{refinement_flop_per_voxel(K):.0f} FLOP per voxel "
-                                                f"({REFINEMENT})")
+                                                f"({refinement_text(K)})")
         work_note = f"{a5_flop_per_voxel(K):.0f} FLOP per interior voxel (400 K)"
     elif name == "direct_corr":
         if geo.get("tc_direct"):
@@ -889,7 +926,7 @@ def run_ours(args) -> None:
                                "correlation maps; FP32 arithmetic"),
                     fft_box=list(box) if path == 2 else None,
                     voxels=nvox, interior_voxels=n_interior, tensor_order=wl.n_order, K=desc.K,
-                    mask_voxels=n_taps, rotation_grid=2048, refinement=REFINEMENT,
+                    mask_voxels=n_taps, rotation_grid=2048, refinement=refinement_text(desc.K),
                     l2="flushed (256 MB write) before every timed step",
                     parallelism="replicas" if world > 1 else "single GPU",
                     template_build_ms=round(build_ms, 2), quadrature_rotations=desc.n_rot),
@@ -1127,7 +1164,7 @@ def run_batch(args) -> None:
                     tuned_problems=sum(1 for t in tuning if t[0] >= 0 and t[1] >= 0),
                     plan_seconds=round(plan_s, 2), template_build_ms=round(build_ms, 2),
                     graph="one CUDA graph replay per step (all problems)",
-                    rotation_grid=2048, refinement=REFINEMENT,
+                    rotation_grid=2048, refinement=refinement_text(tmpls[0][1].K),
                     l2="flushed (256 MB write) before every timed step",
                     parallelism="replicas" if world > 1 else "single GPU",
                     quadrature_rotations=int(len(bw.quadrature))),

@@ -112,8 +112,10 @@ typedef struct ttm_plan_opts {
     int precision;      /* TTM_PREC_*                                          */
     int n_grid;         /* rotation search grid size; 0 = default (2048), <= 65535 */
     int n_cells;        /* regions of the grid; 0 = default (128); must divide n_grid */
-    int n_candidates;   /* regions polished per voxel; 0 = default (8)         */
-    int newton_steps;   /* Newton steps per candidate; 0 = default (3)         */
+    int n_candidates;   /* regions polished per voxel; 0 = default (8, or 4 at */
+                        /* order 6)                                            */
+    int newton_steps;   /* Newton steps per refined point; 0 = default (3, or  */
+                        /* 2 at order 6)                                       */
     int rotation_chunks; /* split the interior into this many chunks and run  */
                          /* the search of chunk i+1 (high-priority stream)    */
                          /* beside the refinement of chunk i (low priority);  */
@@ -123,7 +125,9 @@ typedef struct ttm_plan_opts {
                          /* ttm_local_stats, ttm_correlate, ttm_match_peaks;  */
                          /* filter the template the same way before           */
                          /* ttm_build_tensor_template.  0 = none (h = identity) */
-    int reserved[2];
+    int n_refined;       /* best points after the power steps that take the  */
+                         /* Newton steps; 0 = default (4, or 2 at order 6), <= 4 */
+    int reserved;
 } ttm_plan_opts;
 
 typedef struct ttm_plan_s* ttm_plan_t;
@@ -220,7 +224,8 @@ ttm_status ttm_build_tensor_template_noalloc(const float* d_template, const floa
  * Errors: TTM_ERR_INVALID_ARG (null pointer, volume smaller than its box,
  * template index out of range, mask values outside [0, 1], or an option out
  * of range: path, precision, negative counts, n_grid > 65535, n_cells not
- * dividing n_grid, n_candidates > 8, newton_steps > 64, lowpass_sigma; all
+ * dividing n_grid, n_candidates > 8, newton_steps > 64, n_refined > 4,
+ * lowpass_sigma; all
  * checked before any device work), TTM_ERR_UNSUPPORTED (odd order or mixed
  * orders, n > 8, soft mask off the FFT path, volume of 2^31 voxels or more),
  * TTM_ERR_NUMERIC (non-finite components), TTM_ERR_OUT_OF_MEMORY,

@@ -64,7 +64,8 @@ class PlanOpts(ctypes.Structure):
     _fields_ = [("path", ctypes.c_int), ("precision", ctypes.c_int), ("n_grid", ctypes.c_int),
                 ("n_cells", ctypes.c_int), ("n_candidates", ctypes.c_int),
                 ("newton_steps", ctypes.c_int), ("rotation_chunks", ctypes.c_int),
-                ("lowpass_sigma", ctypes.c_float), ("reserved", ctypes.c_int * 2)]
+                ("lowpass_sigma", ctypes.c_float), ("n_refined", ctypes.c_int),
+                ("reserved", ctypes.c_int)]
 
 
 _lib: Optional[ctypes.CDLL] = None

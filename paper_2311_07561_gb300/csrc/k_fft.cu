@@ -9,6 +9,7 @@
 // at compile time (k_fft.cuh, instantiated in k_fft_len*.cu).  Other powers of
 // two up to 4096 take the runtime-length kernels below (radix 4 and 2, same
 // tiling, FP32 storage only).
+#include <cmath>
 #include <type_traits>
 
 #include "k_fft.cuh"
@@ -264,7 +265,7 @@ int cols_per_cta(int L) {
 #define TTM_FFT_CASE(L, CALL) case L: *err = FftLen<L>::CALL; return true;
 
 bool fixed_rows_r2c(int L, const float* f, int X, int Y, int Z, FftGeom g, float2* spec,
-                    const float2* tw, int mode, const double* moments, cudaStream_t st,
+                    const float2* tw, int mode, double* moments, cudaStream_t st,
                     cudaError_t* err) {
     switch (L) {
 #define C(L) TTM_FFT_CASE(L, rows_r2c(f, X, Y, Z, g, spec, tw, mode, moments, st))
@@ -274,20 +275,20 @@ bool fixed_rows_r2c(int L, const float* f, int X, int Y, int Z, FftGeom g, float
     }
 }
 
-bool fixed_cols(int L, float2* d, int B, int na, const float2* tw, int sign, cudaStream_t st,
-                cudaError_t* err) {
+bool fixed_cols(int L, float2* d, int B, int na, ColsMap mp, const float2* tw, int sign,
+                cudaStream_t st, cudaError_t* err) {
     switch (L) {
-#define C(L) TTM_FFT_CASE(L, cols(d, B, na, tw, sign, st))
+#define C(L) TTM_FFT_CASE(L, cols(d, B, na, mp, tw, sign, st))
         TTM_FFT_LENGTHS(C)
 #undef C
         default: return false;
     }
 }
 
-bool fixed_cols(int L, __nv_bfloat162* d, int B, int na, const float2* tw, int sign,
+bool fixed_cols(int L, __nv_bfloat162* d, int B, int na, ColsMap mp, const float2* tw, int sign,
                 cudaStream_t st, cudaError_t* err) {
     switch (L) {
-#define C(L) TTM_FFT_CASE(L, cols_bf(d, B, na, tw, sign, st))
+#define C(L) TTM_FFT_CASE(L, cols_bf(d, B, na, mp, tw, sign, st))
         TTM_FFT_LENGTHS(C)
 #undef C
         default: return false;
@@ -295,9 +296,9 @@ bool fixed_cols(int L, __nv_bfloat162* d, int B, int na, const float2* tw, int s
 }
 
 bool fixed_cols_mul(int L, const float2* spec, const float2* tspec, float2* prod, int Bz, int K,
-                    const float2* tw, cudaStream_t st, cudaError_t* err) {
+                    const float2* tw, int lo, int hi, cudaStream_t st, cudaError_t* err) {
     switch (L) {
-#define C(L) TTM_FFT_CASE(L, cols_mul(spec, tspec, prod, Bz, K, tw, st))
+#define C(L) TTM_FFT_CASE(L, cols_mul(spec, tspec, prod, Bz, K, tw, lo, hi, st))
         TTM_FFT_LENGTHS(C)
 #undef C
         default: return false;
@@ -305,9 +306,10 @@ bool fixed_cols_mul(int L, const float2* spec, const float2* tspec, float2* prod
 }
 
 bool fixed_cols_mul(int L, const float2* spec, const __nv_bfloat162* tspec, __nv_bfloat162* prod,
-                    int Bz, int K, const float2* tw, cudaStream_t st, cudaError_t* err) {
+                    int Bz, int K, const float2* tw, int lo, int hi, cudaStream_t st,
+                    cudaError_t* err) {
     switch (L) {
-#define C(L) TTM_FFT_CASE(L, cols_mul_bf(spec, tspec, prod, Bz, K, tw, st))
+#define C(L) TTM_FFT_CASE(L, cols_mul_bf(spec, tspec, prod, Bz, K, tw, lo, hi, st))
         TTM_FFT_LENGTHS(C)
 #undef C
         default: return false;
@@ -315,9 +317,10 @@ bool fixed_cols_mul(int L, const float2* spec, const __nv_bfloat162* tspec, __nv
 }
 
 bool fixed_rows_c2r(int L, const float2* prod, int X, int Y, int Z, FftGeom g, float* corr, int K,
-                    const float2* tw, int* status, cudaStream_t st, cudaError_t* err) {
+                    const float2* tw, int* status, FftKeep keep, cudaStream_t st,
+                    cudaError_t* err) {
     switch (L) {
-#define C(L) TTM_FFT_CASE(L, rows_c2r(prod, X, Y, Z, g, corr, K, tw, status, st))
+#define C(L) TTM_FFT_CASE(L, rows_c2r(prod, X, Y, Z, g, corr, K, tw, status, keep, st))
         TTM_FFT_LENGTHS(C)
 #undef C
         default: return false;
@@ -325,10 +328,10 @@ bool fixed_rows_c2r(int L, const float2* prod, int X, int Y, int Z, FftGeom g, f
 }
 
 bool fixed_rows_c2r(int L, const __nv_bfloat162* prod, int X, int Y, int Z, FftGeom g,
-                    __nv_bfloat16* corr, int K, const float2* tw, int* status, cudaStream_t st,
-                    cudaError_t* err) {
+                    __nv_bfloat16* corr, int K, const float2* tw, int* status, FftKeep keep,
+                    cudaStream_t st, cudaError_t* err) {
     switch (L) {
-#define C(L) TTM_FFT_CASE(L, rows_c2r_bf(prod, X, Y, Z, g, corr, K, tw, status, st))
+#define C(L) TTM_FFT_CASE(L, rows_c2r_bf(prod, X, Y, Z, g, corr, K, tw, status, keep, st))
         TTM_FFT_LENGTHS(C)
 #undef C
         default: return false;
@@ -339,33 +342,42 @@ bool fixed_rows_c2r(int L, const __nv_bfloat162* prod, int X, int Y, int Z, FftG
 }  // namespace
 
 
-// Column lines (length L, element stride B) of `batch` consecutive blocks.
+// Column lines (length L, element stride B): planes z0 .. z0 + nz - 1 of each
+// of n_items items (items zstride planes apart), storing line samples lo..hi.
 template <typename PS>
-static ttm_status launch_cols_t(PS* data, int L, int B, int batch, const float2* tw, int sign,
-                                cudaStream_t st, long long* cnt) {
-    for (int a0 = 0; a0 < batch; a0 += 65535) {
-        const int na = batch - a0 < 65535 ? batch - a0 : 65535;
-        PS* d = data + (size_t)a0 * L * B;
-        cudaError_t err = cudaSuccess;
-        if (!fixed_cols(L, d, B, na, tw, sign, st, &err)) {
-            if constexpr (!std::is_same<PS, float2>::value) return TTM_ERR_UNSUPPORTED;
-            else {
-                const int TB = cols_per_cta(L);
-                const size_t smem = (size_t)2 * L * TB * sizeof(float2);
-                TTM_CUDA_TRY(cudaFuncSetAttribute(cols_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+static ttm_status launch_cols_t(PS* data, int L, int B, int n_items, int zstride, int z0, int nz,
+                                int lo, int hi, const float2* tw, int sign, cudaStream_t st,
+                                long long* cnt) {
+    if (n_items <= 0 || nz <= 0) return TTM_OK;
+    cudaError_t err = cudaSuccess;
+    const ColsMap mp{0, nz, zstride, z0, lo, hi};
+    if (fixed_cols(L, data, B, n_items * nz, mp, tw, sign, st, &err)) {
+        TTM_CUDA_TRY(err);
+        return after_launch(cnt);
+    }
+    if constexpr (!std::is_same<PS, float2>::value) {
+        return TTM_ERR_UNSUPPORTED;
+    } else {
+        // runtime-length kernel: every sample of the selected planes is stored
+        const int TB = cols_per_cta(L);
+        const size_t smem = (size_t)2 * L * TB * sizeof(float2);
+        TTM_CUDA_TRY(cudaFuncSetAttribute(cols_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        for (int item = 0; item < n_items; ++item) {
+            for (int a0 = 0; a0 < nz; a0 += 65535) {
+                const int na = nz - a0 < 65535 ? nz - a0 : 65535;
+                PS* d = data + ((size_t)item * zstride + z0 + a0) * L * B;
                 dim3 grid((B + TB - 1) / TB, na);
                 cols_kernel<<<grid, kFftThreads, smem, st>>>(d, L, B, radices_for(L), tw, TB, sign);
+                TTM_TRY(after_launch(cnt));
             }
         }
-        TTM_CUDA_TRY(err);
-        TTM_TRY(after_launch(cnt));
+        return TTM_OK;
     }
-    return TTM_OK;
 }
 
 static ttm_status launch_cols(float2* data, int L, int B, int batch, const float2* tw, int sign,
                               cudaStream_t st, long long* cnt) {
-    return launch_cols_t<float2>(data, L, B, batch, tw, sign, st, cnt);
+    return launch_cols_t<float2>(data, L, B, 1, batch, 0, batch, 0, L - 1, tw, sign, st, cnt);
 }
 
 // lengths with a compile-time pass (TTM_FFT_LENGTHS)
@@ -400,7 +412,7 @@ int fft_good_length(int n) {
 
 ttm_status launch_fft_forward(const float* f, int X, int Y, int Z, const FftShape& S,
                               float2* spec, cudaStream_t st, long long* cnt, int mode,
-                              const double* moments) {
+                              double* moments) {
     FftGeom g{S.Xp, S.Yp, S.Zp, S.Xp / 2 + 1};
     cudaError_t err = cudaSuccess;
     {
@@ -423,11 +435,12 @@ ttm_status launch_fft_forward(const float* f, int X, int Y, int Z, const FftShap
 
 template <typename TS, typename PS>
 static ttm_status spectrum_inverse_z_t(const float2* spec, const TS* tspec, int K, const FftShape& S,
-                                       PS* prod, cudaStream_t st, long long* cnt) {
+                                       PS* prod, const FftKeep& keep, cudaStream_t st,
+                                       long long* cnt) {
     const int Xh = S.Xp / 2 + 1;
     const int Bz = S.Yp * Xh;
     cudaError_t err = cudaSuccess;
-    if (!fixed_cols_mul(S.Zp, spec, tspec, prod, Bz, K, S.d_tw_z, st, &err)) {
+    if (!fixed_cols_mul(S.Zp, spec, tspec, prod, Bz, K, S.d_tw_z, keep.z0, keep.z1, st, &err)) {
         if constexpr (!std::is_same<TS, float2>::value || !std::is_same<PS, float2>::value)
             return TTM_ERR_UNSUPPORTED;
         else {
@@ -445,11 +458,13 @@ static ttm_status spectrum_inverse_z_t(const float2* spec, const TS* tspec, int 
 
 template <typename PS, typename RT>
 static ttm_status inverse_yx_t(PS* prod, int K, int X, int Y, int Z, const FftShape& S, RT* corr,
-                               int* status, cudaStream_t st, long long* cnt) {
+                               int* status, const FftKeep& keep, cudaStream_t st, long long* cnt) {
     FftGeom g{S.Xp, S.Yp, S.Zp, S.Xp / 2 + 1};
-    TTM_TRY(launch_cols_t<PS>(prod, S.Yp, g.Xh, K * S.Zp, S.d_tw_y, +1, st, cnt));
+    // y lines of the kept z planes; the kept rows y are the ones stored
+    TTM_TRY(launch_cols_t<PS>(prod, S.Yp, g.Xh, K, S.Zp, keep.z0, keep.z1 - keep.z0 + 1, keep.y0,
+                              keep.y1, S.d_tw_y, +1, st, cnt));
     cudaError_t err = cudaSuccess;
-    if (!fixed_rows_c2r(S.Xp, prod, X, Y, Z, g, corr, K, S.d_tw_x, status, st, &err)) {
+    if (!fixed_rows_c2r(S.Xp, prod, X, Y, Z, g, corr, K, S.d_tw_x, status, keep, st, &err)) {
         if constexpr (!std::is_same<PS, float2>::value || !std::is_same<RT, float>::value)
             return TTM_ERR_UNSUPPORTED;
         else {
@@ -466,30 +481,32 @@ static ttm_status inverse_yx_t(PS* prod, int K, int X, int Y, int Z, const FftSh
 }
 
 ttm_status launch_fft_spectrum_inverse_z(const float2* spec, const float2* tspec, int K,
-                                         const FftShape& S, float2* prod, cudaStream_t st,
-                                         long long* cnt) {
-    return spectrum_inverse_z_t<float2, float2>(spec, tspec, K, S, prod, st, cnt);
+                                         const FftShape& S, float2* prod, const FftKeep& keep,
+                                         cudaStream_t st, long long* cnt) {
+    return spectrum_inverse_z_t<float2, float2>(spec, tspec, K, S, prod, keep, st, cnt);
 }
 
 ttm_status launch_fft_inverse_yx(float2* prod, int K, int X, int Y, int Z, const FftShape& S,
-                                 float* corr, int* status, cudaStream_t st, long long* cnt) {
-    return inverse_yx_t<float2, float>(prod, K, X, Y, Z, S, corr, status, st, cnt);
+                                 float* corr, int* status, const FftKeep& keep, cudaStream_t st,
+                                 long long* cnt) {
+    return inverse_yx_t<float2, float>(prod, K, X, Y, Z, S, corr, status, keep, st, cnt);
 }
 
 // mixed precision: bf16 template spectra, products and correlation maps
 ttm_status launch_fft_spectrum_inverse_z_bf16(const float2* spec, const void* tspec, int K,
-                                              const FftShape& S, void* prod, cudaStream_t st,
-                                              long long* cnt) {
+                                              const FftShape& S, void* prod, const FftKeep& keep,
+                                              cudaStream_t st, long long* cnt) {
     return spectrum_inverse_z_t<__nv_bfloat162, __nv_bfloat162>(
         spec, reinterpret_cast<const __nv_bfloat162*>(tspec), K, S,
-        reinterpret_cast<__nv_bfloat162*>(prod), st, cnt);
+        reinterpret_cast<__nv_bfloat162*>(prod), keep, st, cnt);
 }
 
 ttm_status launch_fft_inverse_yx_bf16(void* prod, int K, int X, int Y, int Z, const FftShape& S,
-                                      void* corr, int* status, cudaStream_t st, long long* cnt) {
+                                      void* corr, int* status, const FftKeep& keep,
+                                      cudaStream_t st, long long* cnt) {
     return inverse_yx_t<__nv_bfloat162, __nv_bfloat16>(
         reinterpret_cast<__nv_bfloat162*>(prod), K, X, Y, Z, S,
-        reinterpret_cast<__nv_bfloat16*>(corr), status, st, cnt);
+        reinterpret_cast<__nv_bfloat16*>(corr), status, keep, st, cnt);
 }
 
 __global__ void to_bf16_kernel(const float2* __restrict__ a, __nv_bfloat162* __restrict__ b, size_t n) {
@@ -505,24 +522,37 @@ ttm_status launch_spectra_to_bf16(const float2* a, void* b, size_t n, cudaStream
 
 // w from the FFT-based window sums of (f - mean) and (f - mean)^2 (Algorithm 1):
 // V = S2 - S1^2 / m_sum in FP64; interior only; floor 1e-6 m_sum var(f).
+//
+// The FP32 FFT window sums carry a rounding error set by the whole volume,
+// not by the window: |dS| <= kappa eps m_sum rms(a) for a = f - mean (S1) and
+// a = (f - mean)^2 (S2), eps = 2^-24, kappa = 2 log2(N) (measured worst cases
+// stay near log2(N)).  A window whose bound on |dV| exceeds 2e-5 V (the 1e-5
+// tolerance of w), or which lies within the bound of the floor, is flagged
+// (w = -1, counted in *flagged) and recomputed exactly by direct FP64 sums
+// (launch_exact_stats).  Large offsets never flag (the mean is removed); a
+// quiet window in a volume of large dynamic range does.
 // Persistent CTAs over x-segments of 128 voxels: the volume statistics and
-// the floor (FP64 divisions, slow on this GPU) are formed once per CTA; each
-// interior voxel does two FP64 operations plus conversions.
+// the bounds (FP64 divisions, slow on this GPU) are formed once per CTA.
 __global__ void __launch_bounds__(128) stats_from_sums_kernel(
     const float* __restrict__ s1, const float* __restrict__ s2, float* __restrict__ w, int X,
-    int Y, int Z, int s, double mask_sum, const double* __restrict__ moments) {
-    __shared__ double sh[2];
+    int Y, int Z, int s, double mask_sum, const double* __restrict__ moments, double kappa,
+    unsigned int* __restrict__ flagged) {
+    __shared__ double sh[4];
     if (threadIdx.x == 0) {
         const double nv = (double)X * Y * Z;
         const double mean = moments[0] / nv;
         const double var_f = fmax(moments[1] / nv - mean * mean, 0.0);
+        const double eps = 5.9604644775390625e-8;          // 2^-24
         sh[0] = 1.0 / mask_sum;
         sh[1] = 1e-6 * mask_sum * var_f;
+        sh[2] = kappa * eps * mask_sum * sqrt(var_f);       // bound on |dS1|
+        sh[3] = kappa * eps * mask_sum * sqrt(fmax(moments[2], 0.0) / nv);   // on |dS2|
     }
     __syncthreads();
-    const double inv_m = sh[0], floor_v = sh[1];
+    const double inv_m = sh[0], floor_v = sh[1], e1 = sh[2], e2 = sh[3];
     const uint32_t xt = (uint32_t)((X + 127) / 128);
     const uint32_t segs = xt * (uint32_t)Y * (uint32_t)Z;
+    unsigned int nflag = 0;
     for (uint32_t sg = blockIdx.x; sg < segs; sg += gridDim.x) {
         const uint32_t row = sg / xt;
         const int x = (int)(sg - row * xt) * 128 + threadIdx.x;
@@ -533,19 +563,29 @@ __global__ void __launch_bounds__(128) stats_from_sums_kernel(
         if (interior(x, X, s) && interior(y, Y, s) && interior(z, Z, s)) {
             const double S1 = s1[v], S2 = s2[v];
             const double V = fma(-S1, S1 * inv_m, S2);
-            if (V > floor_v) out = rsqrtf((float)V);
+            const double dv = e2 + (2.0 * fabs(S1) * e1 + e1 * e1) * inv_m;
+            if (dv > 2e-5 * V || fabs(V - floor_v) <= dv) {
+                out = -1.f;
+                ++nflag;
+            } else if (V > floor_v) {
+                out = rsqrtf((float)V);
+            }
         }
         w[v] = out;
     }
+    for (int o = 16; o > 0; o >>= 1) nflag += __shfl_down_sync(0xffffffffu, nflag, o);
+    if ((threadIdx.x & 31) == 0 && nflag) atomicAdd(flagged, nflag);
 }
 
 ttm_status launch_stats_from_sums(const float* s1, const float* s2, float* w, int X, int Y, int Z,
-                                  int s, double mask_sum, const double* moments, cudaStream_t st,
-                                  long long* cnt) {
+                                  int s, double mask_sum, const double* moments,
+                                  unsigned int* flagged, cudaStream_t st, long long* cnt) {
     const size_t segs = (size_t)((X + 127) / 128) * Y * Z;
     if (segs > 0xFFFFFFFFull) return TTM_ERR_UNSUPPORTED;
     const unsigned grid = (unsigned)(segs < 152 * 16 ? segs : 152 * 16);
-    stats_from_sums_kernel<<<grid, 128, 0, st>>>(s1, s2, w, X, Y, Z, s, mask_sum, moments);
+    const double kappa = 2.0 * std::log2((double)X * Y * Z);
+    stats_from_sums_kernel<<<grid, 128, 0, st>>>(s1, s2, w, X, Y, Z, s, mask_sum, moments, kappa,
+                                                 flagged);
     return after_launch(cnt);
 }
 

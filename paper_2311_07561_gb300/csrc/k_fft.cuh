@@ -31,6 +31,13 @@ struct FftGeom {
     int Xp, Yp, Zp, Xh;
 };
 
+// Lines of a column pass: plane p = p0 + blockIdx.y (or the persistent tile's
+// plane) is plane z0 + (p % nz) of item p / nz, items zstride planes apart;
+// line samples lo..hi are stored (the rest are computed and dropped).
+struct ColsMap {
+    int p0, nz, zstride, z0, lo, hi;
+};
+
 namespace fftk {
 
 constexpr int kFftThreads = 256;
@@ -262,12 +269,14 @@ constexpr int cols_tb_s() { return (sizeof(PS) < 8 && cols_tb<L>() < 8) ? 8 : co
 
 // ---- the four passes with a compile-time line length ---------------------
 // mode 0 transforms f, mode 1 (f - mean), mode 2 (f - mean)^2 with mean =
-// moments[0] / (X Y Z) (the shift removes the cancellation in the local variance)
+// moments[0] / (X Y Z) (the shift removes the cancellation in the local
+// variance); mode 2 also adds sum (f - mean)^4 into moments[2] (the size of
+// the FFT rounding error of the window sums, see stats_from_sums_kernel)
 template <int L>
 __global__ void __launch_bounds__(kFftThreads) rows_r2c_t(const float* __restrict__ f, int X, int Y,
                                                           int Z, FftGeom g, float2* __restrict__ out,
                                                           const float2* __restrict__ tw, int mode,
-                                                          const double* __restrict__ moments) {
+                                                          double* __restrict__ moments) {
     constexpr int NB = rows_nb<L>();
     constexpr int PITCH = NB + 1;
     constexpr int XH = L / 2 + 1;
@@ -310,6 +319,21 @@ __global__ void __launch_bounds__(kFftThreads) rows_r2c_t(const float* __restric
         const int r = e / L, x = e % L;
         if (e < NB * L) A[x * PITCH + r] = make_float2(vv[i], 0.f);
     }
+    if (mode == 2) {
+        __shared__ double part[kFftThreads / 32];
+        float q = 0.f;
+#pragma unroll
+        for (int i = 0; i < PER; ++i) q = fmaf(vv[i], vv[i], q);
+        double d = q;
+        for (int o = 16; o > 0; o >>= 1) d += __shfl_down_sync(0xffffffffu, d, o);
+        if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = d;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double t = 0.0;
+            for (int k = 0; k < kFftThreads / 32; ++k) t += part[k];
+            if (t != 0.0) atomicAdd(moments + 2, t);
+        }
+    }
     __syncthreads();
     float2* res = fft_lines_t<L, NB, PITCH, -1>(A, B, tw);
     for (int e = threadIdx.x; e < NB * XH; e += blockDim.x) {
@@ -319,16 +343,22 @@ __global__ void __launch_bounds__(kFftThreads) rows_r2c_t(const float* __restric
     }
 }
 
+__device__ __forceinline__ size_t cols_plane_base(const ColsMap& mp, size_t p, int L, int B) {
+    const size_t item = p / (size_t)mp.nz;
+    const size_t zz = p - item * (size_t)mp.nz;
+    return (item * (size_t)mp.zstride + (size_t)mp.z0 + zz) * (size_t)L * (size_t)B;
+}
+
 template <int L, int SIGN, typename PS>
 __global__ void __launch_bounds__(kFftThreads) cols_t(PS* __restrict__ data, int B,
-                                                      const float2* __restrict__ tw) {
+                                                      const float2* __restrict__ tw, ColsMap mp) {
     constexpr int TB = cols_tb_s<L, PS>();
     extern __shared__ float2 sm[];
     float2* P = sm;
     float2* Q = sm + L * TB;
     constexpr int PER = (L * TB + kFftThreads - 1) / kFftThreads;
     const int b0 = blockIdx.x * TB;
-    const size_t base = (size_t)blockIdx.y * L * B;
+    const size_t base = cols_plane_base(mp, (size_t)mp.p0 + blockIdx.y, L, B);
     const int tb = min(TB, B - b0);
     float2 v[PER];
 #pragma unroll
@@ -348,7 +378,62 @@ __global__ void __launch_bounds__(kFftThreads) cols_t(PS* __restrict__ data, int
     for (int i = 0; i < PER; ++i) {
         const int e = threadIdx.x + i * kFftThreads;
         const int l = e / TB, bb = e & (TB - 1);
-        if (e < L * TB && bb < tb) stc(data + base + (size_t)l * B + b0 + bb, res[e]);
+        if (e < L * TB && bb < tb && l >= mp.lo && l <= mp.hi)
+            stc(data + base + (size_t)l * B + b0 + bb, res[e]);
+    }
+}
+
+// The same pass for long lines (one or two CTAs per SM): persistent CTAs walk
+// the (column tile, plane) tiles with a stride of gridDim.x, and the raw
+// elements of the next tile are loaded into registers while the current one
+// is transformed, so loads stay in flight through the Stockham stages.
+template <int L, int SIGN, typename PS>
+__global__ void __launch_bounds__(kFftThreads, 1) cols_pf_t(PS* __restrict__ data, int B,
+                                                            const float2* __restrict__ tw,
+                                                            ColsMap mp, int ntb, size_t ntiles) {
+    constexpr int TB = cols_tb_s<L, PS>();
+    extern __shared__ float2 sm[];
+    float2* P = sm;
+    float2* Q = sm + L * TB;
+    constexpr int PER = (L * TB + kFftThreads - 1) / kFftThreads;
+    PS nv[PER];
+    auto load = [&](size_t tile) {
+        const size_t plane = tile / (size_t)ntb;
+        const int b0 = (int)(tile - plane * (size_t)ntb) * TB;
+        const size_t base = cols_plane_base(mp, (size_t)mp.p0 + plane, L, B);
+        const int tb = min(TB, B - b0);
+#pragma unroll
+        for (int i = 0; i < PER; ++i) {
+            const int e = threadIdx.x + i * kFftThreads;
+            const int l = e / TB, bb = e & (TB - 1);
+            if (e < L * TB && bb < tb) nv[i] = data[base + (size_t)l * B + b0 + bb];
+        }
+    };
+    size_t tile = blockIdx.x;
+    if (tile >= ntiles) return;
+    load(tile);
+    for (; tile < ntiles; tile += gridDim.x) {
+        const size_t plane = tile / (size_t)ntb;
+        const int b0 = (int)(tile - plane * (size_t)ntb) * TB;
+        const size_t base = cols_plane_base(mp, (size_t)mp.p0 + plane, L, B);
+        const int tb = min(TB, B - b0);
+        __syncthreads();                      // the previous tile's result is stored
+#pragma unroll
+        for (int i = 0; i < PER; ++i) {
+            const int e = threadIdx.x + i * kFftThreads;
+            const int bb = e & (TB - 1);
+            if (e < L * TB) P[e] = bb < tb ? ldc(&nv[i]) : make_float2(0.f, 0.f);
+        }
+        if (tile + gridDim.x < ntiles) load(tile + gridDim.x);
+        __syncthreads();
+        float2* res = fft_lines_t<L, TB, TB, SIGN>(P, Q, tw);
+#pragma unroll
+        for (int i = 0; i < PER; ++i) {
+            const int e = threadIdx.x + i * kFftThreads;
+            const int l = e / TB, bb = e & (TB - 1);
+            if (e < L * TB && bb < tb && l >= mp.lo && l <= mp.hi)
+                stc(data + base + (size_t)l * B + b0 + bb, res[e]);
+        }
     }
 }
 
@@ -356,7 +441,8 @@ template <int L, typename TS, typename PS>
 __global__ void __launch_bounds__(kFftThreads, 2) cols_mul_t(const float2* __restrict__ spec,
                                                           const TS* __restrict__ tspec,
                                                           PS* __restrict__ out, int B, int K,
-                                                          const float2* __restrict__ tw) {
+                                                          const float2* __restrict__ tw, int lo,
+                                                          int hi) {
     constexpr int TB = cols_tb<L>();
     extern __shared__ float2 sm[];
     float2* P = sm;
@@ -406,7 +492,7 @@ __global__ void __launch_bounds__(kFftThreads, 2) cols_mul_t(const float2* __res
         for (int i = 0; i < PER; ++i) {
             const int e = threadIdx.x + i * kFftThreads;
             const int l = e / TB, bb = e & (TB - 1);
-            if (e < L * TB && bb < tb) stc(o + (size_t)l * B + b0 + bb, res[e]);
+            if (e < L * TB && bb < tb && l >= lo && l <= hi) stc(o + (size_t)l * B + b0 + bb, res[e]);
         }
     }
 }
@@ -470,24 +556,39 @@ __device__ __forceinline__ void stages_io(const Src& src, float2* a, float2* b, 
 }
 
 // ---- half-spectrum rows -> real x lines (inverse), persistent -----------
-// A tile is NB consecutive half-spectrum rows (contiguous in memory).  Each
-// CTA walks tiles with a stride of gridDim.x; the next tile is fetched by one
-// bulk copy into the other staging buffer while the current one is
+// A tile is NB consecutive half-spectrum rows (contiguous in memory) of one z
+// plane of one batch item; only the planes z0..z1 and the rows y0..y1 of the
+// keep box are visited (tiles start at multiples of NB rows, so every tile is
+// one aligned bulk copy).  Each CTA walks tiles with a stride of gridDim.x;
+// the next NST - 1 tiles are in flight in a ring of staging buffers (bulk
+// copies completing on one mbarrier each) while the current one is
 // transformed.  The first stage reads the staged rows with the Hermitian
-// extension X[L - x] = conj X[x]; the last stage stores the real parts
-// straight to the X x Y x Z maps (out is batch-major, X Y Z floats per item).
-// Copy waits are bounded: on expiry the CTA records TTM_ERR_TIMEOUT, waits
-// once more for its copy in flight and exits.
+// extension X[L - x] = conj X[x]; the last stage stores the real parts of the
+// kept samples x0..x1 straight to the X x Y x Z maps (out is batch-major,
+// X Y Z floats per item).  Copy waits are bounded: on expiry the CTA records
+// TTM_ERR_TIMEOUT, waits once more for its copies in flight and exits.
 template <int L>
 constexpr int c2r_stages_buffers() { return n_stages(L) >= 3 ? 2 : 1; }
 
 template <int L, typename PS>
 constexpr uint32_t c2r_tile_bytes() { return (uint32_t)(rows_nb<L>() * (L / 2 + 1) * sizeof(PS)); }
 
+template <int L>
+constexpr size_t c2r_fft_bytes() {
+    return (size_t)c2r_stages_buffers<L>() * L * (rows_nb<L>() + 1) * sizeof(float2);
+}
+
+// staging ring depth: as deep as 4 while two CTAs still fit on an SM
+template <int L, typename PS>
+constexpr int c2r_ring() {
+    constexpr size_t budget = 113u * 1024u;
+    return (4 * (size_t)c2r_tile_bytes<L, PS>() + c2r_fft_bytes<L>() <= budget) ? 4
+         : (3 * (size_t)c2r_tile_bytes<L, PS>() + c2r_fft_bytes<L>() <= budget) ? 3 : 2;
+}
+
 template <int L, typename PS>
 constexpr size_t c2r_smem() {
-    return 2 * (size_t)c2r_tile_bytes<L, PS>() +
-           (size_t)c2r_stages_buffers<L>() * L * (rows_nb<L>() + 1) * sizeof(float2);
+    return (size_t)c2r_ring<L, PS>() * c2r_tile_bytes<L, PS>() + c2r_fft_bytes<L>();
 }
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p) {
@@ -522,58 +623,91 @@ template <int L, typename PS, typename RT>
 __global__ void __launch_bounds__(kFftThreads) rows_c2r_t(const PS* __restrict__ in, int X, int Y,
                                                           int Z, FftGeom g, RT* __restrict__ out,
                                                           int n_batch, const float2* __restrict__ tw,
-                                                          int* status) {
+                                                          int* status, FftKeep keep) {
     constexpr int NB = rows_nb<L>();
     constexpr int PITCH = NB + 1;
     constexpr int XH = L / 2 + 1;
+    constexpr int NST = c2r_ring<L, PS>();
     constexpr uint32_t TILE = c2r_tile_bytes<L, PS>();
     static_assert(TILE % 16 == 0, "bulk copies move multiples of 16 bytes");
     extern __shared__ __align__(128) unsigned char smraw[];
-    float2* a = reinterpret_cast<float2*>(smraw + 2 * TILE);
+    float2* a = reinterpret_cast<float2*>(smraw + NST * TILE);
     float2* b = a + (c2r_stages_buffers<L>() == 2 ? L * PITCH : 0);
-    __shared__ __align__(8) uint64_t bars[2];
+    __shared__ __align__(8) uint64_t bars[NST];
     __shared__ long long row_out[NB];        // output offset of each row, -1 = not written
-    const size_t rows_per_item = (size_t)g.Yp * g.Zp;
-    const size_t ntiles = rows_per_item * n_batch / NB;      // NB divides Yp Zp
+    // kept rows: planes z0..z1, rows from y0 rounded down to a multiple of NB
+    // (every tile starts on a 16-byte boundary) up to y1
+    const int y_first = keep.y0 & ~(NB - 1);
+    const int nty = (keep.y1 - y_first) / NB + 1;
+    const int nz = keep.z1 - keep.z0 + 1;
+    const size_t ntiles = (size_t)n_batch * nz * nty;
+    auto tile_src = [&](size_t t, int& y_start, size_t& item, int& z) {
+        const size_t per_item = (size_t)nz * nty;
+        item = t / per_item;
+        const size_t r = t - item * per_item;
+        const int zz = (int)(r / (size_t)nty);
+        y_start = y_first + (int)(r - (size_t)zz * nty) * NB;
+        z = keep.z0 + zz;
+        return in + ((item * (size_t)g.Zp + (size_t)z) * (size_t)g.Yp + (size_t)y_start) * XH;
+    };
     const uint32_t sbase = smem_addr(smraw);
-    const uint32_t bar[2] = {smem_addr(&bars[0]), smem_addr(&bars[1])};
     if (threadIdx.x == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(bar[0]) : "memory");
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(bar[1]) : "memory");
+        for (int q = 0; q < NST; ++q)
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_addr(&bars[q])) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
     }
     __syncthreads();
-    size_t tile = blockIdx.x;
-    if (tile >= ntiles) return;
-    if (threadIdx.x == 0) bulk_to_smem(sbase, in + tile * NB * XH, TILE, bar[0]);
-    uint32_t phase[2] = {0u, 0u};
-    for (int it = 0; tile < ntiles; ++it, tile += gridDim.x) {
-        const int buf = it & 1;
-        const size_t next = tile + gridDim.x;
-        if (threadIdx.x == 0 && next < ntiles) {
-            asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-            bulk_to_smem(sbase + (uint32_t)(buf ^ 1) * TILE, in + next * NB * XH, TILE,
-                         bar[buf ^ 1]);
+    if ((size_t)blockIdx.x >= ntiles) return;
+    uint32_t pending = 0u;                   // thread 0: buffers with a copy in flight
+    if (threadIdx.x == 0) {
+        for (int q = 0; q < NST - 1; ++q) {
+            const size_t t = blockIdx.x + (size_t)q * gridDim.x;
+            if (t >= ntiles) break;
+            int ys, z;
+            size_t item;
+            bulk_to_smem(sbase + (uint32_t)q * TILE, tile_src(t, ys, item, z), TILE,
+                         smem_addr(&bars[q]));
+            pending |= 1u << q;
+        }
+    }
+    uint32_t phase = 0u;
+    int it = 0;
+    for (size_t tile = blockIdx.x; tile < ntiles; ++it, tile += gridDim.x) {
+        const int buf = it % NST;
+        if (threadIdx.x == 0) {
+            const size_t ahead = tile + (size_t)(NST - 1) * gridDim.x;
+            if (ahead < ntiles) {
+                const int nb = (it + NST - 1) % NST;
+                int ys, z;
+                size_t item;
+                asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+                bulk_to_smem(sbase + (uint32_t)nb * TILE, tile_src(ahead, ys, item, z), TILE,
+                             smem_addr(&bars[nb]));
+                pending |= 1u << nb;
+            }
         }
         if (threadIdx.x < NB) {
-            const size_t row = tile * NB + threadIdx.x;
-            const size_t item = row / rows_per_item;
-            const int rr = (int)(row - item * rows_per_item);
-            const int y = rr % g.Yp, z = rr / g.Yp;
-            row_out[threadIdx.x] = (y < Y && z < Z)
+            int ys, z;
+            size_t item;
+            tile_src(tile, ys, item, z);
+            const int y = ys + threadIdx.x;
+            row_out[threadIdx.x] = (y >= keep.y0 && y <= keep.y1 && y < Y && z < Z)
                 ? (long long)(item * ((size_t)X * Y * Z) + ((size_t)z * Y + y) * X) : -1;
         }
-        const bool ok = bar_wait(bar[buf], phase[buf]);
-        phase[buf] ^= 1u;
+        const bool ok = bar_wait(smem_addr(&bars[buf]), (phase >> buf) & 1u);
+        phase ^= 1u << buf;
+        if (threadIdx.x == 0) pending &= ~(1u << buf);
         if (__syncthreads_or(!ok)) {
             if (threadIdx.x == 0) {
                 atomicExch(status, TTM_ERR_TIMEOUT);
-                if (next < ntiles) bar_wait(bar[buf ^ 1], phase[buf ^ 1]);
+                for (int q = 0; q < NST; ++q)
+                    if ((pending >> q) & 1u) bar_wait(smem_addr(&bars[q]), (phase >> q) & 1u);
             }
             return;
         }
         const PS* S = reinterpret_cast<const PS*>(smraw + (size_t)buf * TILE);
+        const int xk0 = keep.x0, xk1 = min(keep.x1, X - 1);
         stages_io<L, 0, NB, PITCH, +1>(
             [S](int x, int line) {
                 if (x < XH) return ldc(S + line * XH + x);
@@ -581,9 +715,9 @@ __global__ void __launch_bounds__(kFftThreads) rows_c2r_t(const PS* __restrict__
                 return make_float2(c.x, -c.y);
             },
             a, b,
-            [out, X](int x, int line, float2 v) {
+            [out, xk0, xk1](int x, int line, float2 v) {
                 const long long off = row_out[line];
-                if (x < X && off >= 0) str(out + off + x, v.x);
+                if (x >= xk0 && x <= xk1 && off >= 0) str(out + off + x, v.x);
             },
             tw);
         __syncthreads();     // staging buffer, a/b and row_out are reused
@@ -594,72 +728,108 @@ __global__ void __launch_bounds__(kFftThreads) rows_c2r_t(const PS* __restrict__
 
 // Launchers of the four passes for one compile-time length L.  Each returns
 // the CUDA error of its attribute call or launch.  Defined out of line so that
-// `extern template` keeps the kernels in the k_fft_len*.cu objects.
+// `extern template` keeps the kernels in the k_fft_len*.cu objects.  The
+// column passes take a ColsMap (na planes), the fused multiply the range of
+// stored z, the row inverse the keep box.
 template <int L>
 struct FftLen {
     static cudaError_t rows_r2c(const float* f, int X, int Y, int Z, FftGeom g, float2* spec,
-                                const float2* tw, int mode, const double* moments, cudaStream_t st);
-    static cudaError_t cols(float2* d, int B, int na, const float2* tw, int sign, cudaStream_t st);
-    static cudaError_t cols_bf(__nv_bfloat162* d, int B, int na, const float2* tw, int sign,
-                               cudaStream_t st);
+                                const float2* tw, int mode, double* moments, cudaStream_t st);
+    static cudaError_t cols(float2* d, int B, int na, ColsMap mp, const float2* tw, int sign,
+                            cudaStream_t st);
+    static cudaError_t cols_bf(__nv_bfloat162* d, int B, int na, ColsMap mp, const float2* tw,
+                               int sign, cudaStream_t st);
     static cudaError_t cols_mul(const float2* spec, const float2* tspec, float2* prod, int Bz, int K,
-                                const float2* tw, cudaStream_t st);
+                                const float2* tw, int lo, int hi, cudaStream_t st);
     static cudaError_t cols_mul_bf(const float2* spec, const __nv_bfloat162* tspec,
-                                   __nv_bfloat162* prod, int Bz, int K, const float2* tw,
-                                   cudaStream_t st);
+                                   __nv_bfloat162* prod, int Bz, int K, const float2* tw, int lo,
+                                   int hi, cudaStream_t st);
     static cudaError_t rows_c2r(const float2* prod, int X, int Y, int Z, FftGeom g, float* corr,
-                                int K, const float2* tw, int* status, cudaStream_t st);
+                                int K, const float2* tw, int* status, FftKeep keep, cudaStream_t st);
     static cudaError_t rows_c2r_bf(const __nv_bfloat162* prod, int X, int Y, int Z, FftGeom g,
                                    __nv_bfloat16* corr, int K, const float2* tw, int* status,
-                                   cudaStream_t st);
+                                   FftKeep keep, cudaStream_t st);
 };
 
 namespace fftk {
 
+inline cudaError_t sm_count(int* sms) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    return cudaDeviceGetAttribute(sms, cudaDevAttrMultiProcessorCount, dev);
+}
+
+// lengths whose column tiles leave one CTA per SM take the persistent pass
+template <int L, typename PS>
+constexpr bool cols_persistent() { return 2 * (size_t)L * cols_tb_s<L, PS>() * sizeof(float2) > 100u * 1024u; }
+
 template <int L, int SIGN, typename PS>
-cudaError_t run_cols(PS* d, int B, int na, const float2* tw, cudaStream_t st) {
+cudaError_t run_cols(PS* d, int B, int na, ColsMap mp, const float2* tw, cudaStream_t st) {
     constexpr int TB = cols_tb_s<L, PS>();
     const size_t smem = (size_t)2 * L * TB * sizeof(float2);
-    cudaError_t e = cudaFuncSetAttribute(cols_t<L, SIGN, PS>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    dim3 grid((B + TB - 1) / TB, na);
-    cols_t<L, SIGN, PS><<<grid, kFftThreads, smem, st>>>(d, B, tw);
-    return cudaGetLastError();
+    const int ntb = (B + TB - 1) / TB;
+    if constexpr (cols_persistent<L, PS>()) {
+        cudaError_t e = cudaFuncSetAttribute(cols_pf_t<L, SIGN, PS>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        int sms = 0;
+        if ((e = sm_count(&sms)) != cudaSuccess) return e;
+        const size_t ntiles = (size_t)ntb * na;
+        const unsigned grid = (unsigned)(ntiles < (size_t)sms ? ntiles : (size_t)sms);
+        if (grid == 0) return cudaSuccess;
+        cols_pf_t<L, SIGN, PS><<<grid, kFftThreads, smem, st>>>(d, B, tw, mp, ntb, ntiles);
+        return cudaGetLastError();
+    } else {
+        cudaError_t e = cudaFuncSetAttribute(cols_t<L, SIGN, PS>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        for (int a0 = 0; a0 < na; a0 += 65535) {
+            const int n = na - a0 < 65535 ? na - a0 : 65535;
+            ColsMap m2 = mp;
+            m2.p0 = mp.p0 + a0;
+            dim3 grid(ntb, n);
+            cols_t<L, SIGN, PS><<<grid, kFftThreads, smem, st>>>(d, B, tw, m2);
+            if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        }
+        return cudaSuccess;
+    }
 }
 
 template <int L, typename TS, typename PS>
 cudaError_t run_cols_mul(const float2* spec, const TS* tspec, PS* prod, int Bz, int K,
-                         const float2* tw, cudaStream_t st) {
+                         const float2* tw, int lo, int hi, cudaStream_t st) {
     constexpr int TB = cols_tb<L>();
     const size_t smem = (size_t)2 * L * TB * sizeof(float2);
     cudaError_t e = cudaFuncSetAttribute(cols_mul_t<L, TS, PS>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     dim3 grid((Bz + TB - 1) / TB, 1);
-    cols_mul_t<L, TS, PS><<<grid, kFftThreads, smem, st>>>(spec, tspec, prod, Bz, K, tw);
+    cols_mul_t<L, TS, PS><<<grid, kFftThreads, smem, st>>>(spec, tspec, prod, Bz, K, tw, lo, hi);
     return cudaGetLastError();
 }
 
 template <int L, typename PS, typename RT>
 cudaError_t run_rows_c2r(const PS* prod, int X, int Y, int Z, FftGeom g, RT* corr, int K,
-                         const float2* tw, int* status, cudaStream_t st) {
+                         const float2* tw, int* status, FftKeep keep, cudaStream_t st) {
     constexpr int NB = rows_nb<L>();
     constexpr size_t smem = c2r_smem<L, PS>();
     cudaError_t e = cudaFuncSetAttribute(rows_c2r_t<L, PS, RT>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    int dev = 0, sms = 0, per_sm = 0;
-    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
-    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    int sms = 0, per_sm = 0;
+    if ((e = sm_count(&sms)) != cudaSuccess) return e;
     if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, rows_c2r_t<L, PS, RT>,
                                                            kFftThreads, smem)) != cudaSuccess)
         return e;
-    const size_t ntiles = (size_t)g.Yp * g.Zp * K / NB;
+    if (keep.z1 < keep.z0 || keep.y1 < keep.y0 || keep.x1 < keep.x0) return cudaSuccess;
+    const int nty = (keep.y1 - (keep.y0 & ~(NB - 1))) / NB + 1;
+    const size_t ntiles = (size_t)K * (keep.z1 - keep.z0 + 1) * nty;
     const size_t cap = (size_t)sms * (per_sm > 0 ? per_sm : 1);
     const unsigned grid = (unsigned)(ntiles < cap ? ntiles : cap);
     if (grid == 0) return cudaSuccess;
-    rows_c2r_t<L, PS, RT><<<grid, kFftThreads, smem, st>>>(prod, X, Y, Z, g, corr, K, tw, status);
+    rows_c2r_t<L, PS, RT><<<grid, kFftThreads, smem, st>>>(prod, X, Y, Z, g, corr, K, tw, status,
+                                                          keep);
     return cudaGetLastError();
 }
 
@@ -667,7 +837,7 @@ cudaError_t run_rows_c2r(const PS* prod, int X, int Y, int Z, FftGeom g, RT* cor
 
 template <int L>
 cudaError_t FftLen<L>::rows_r2c(const float* f, int X, int Y, int Z, FftGeom g, float2* spec,
-                                const float2* tw, int mode, const double* moments,
+                                const float2* tw, int mode, double* moments,
                                 cudaStream_t st) {
     constexpr int NB = fftk::rows_nb<L>();
     const size_t smem = (size_t)2 * L * (NB + 1) * sizeof(float2);
@@ -681,44 +851,47 @@ cudaError_t FftLen<L>::rows_r2c(const float* f, int X, int Y, int Z, FftGeom g, 
 }
 
 template <int L>
-cudaError_t FftLen<L>::cols(float2* d, int B, int na, const float2* tw, int sign, cudaStream_t st) {
-    return sign < 0 ? fftk::run_cols<L, -1, float2>(d, B, na, tw, st)
-                    : fftk::run_cols<L, +1, float2>(d, B, na, tw, st);
+cudaError_t FftLen<L>::cols(float2* d, int B, int na, ColsMap mp, const float2* tw, int sign,
+                            cudaStream_t st) {
+    return sign < 0 ? fftk::run_cols<L, -1, float2>(d, B, na, mp, tw, st)
+                    : fftk::run_cols<L, +1, float2>(d, B, na, mp, tw, st);
 }
 
 template <int L>
-cudaError_t FftLen<L>::cols_bf(__nv_bfloat162* d, int B, int na, const float2* tw, int sign,
-                               cudaStream_t st) {
+cudaError_t FftLen<L>::cols_bf(__nv_bfloat162* d, int B, int na, ColsMap mp, const float2* tw,
+                               int sign, cudaStream_t st) {
     // bf16 storage is used by the inverse passes only
     if (sign < 0) return cudaErrorInvalidValue;
-    return fftk::run_cols<L, +1, __nv_bfloat162>(d, B, na, tw, st);
+    return fftk::run_cols<L, +1, __nv_bfloat162>(d, B, na, mp, tw, st);
 }
 
 template <int L>
 cudaError_t FftLen<L>::cols_mul(const float2* spec, const float2* tspec, float2* prod, int Bz,
-                                int K, const float2* tw, cudaStream_t st) {
-    return fftk::run_cols_mul<L, float2, float2>(spec, tspec, prod, Bz, K, tw, st);
+                                int K, const float2* tw, int lo, int hi, cudaStream_t st) {
+    return fftk::run_cols_mul<L, float2, float2>(spec, tspec, prod, Bz, K, tw, lo, hi, st);
 }
 
 template <int L>
 cudaError_t FftLen<L>::cols_mul_bf(const float2* spec, const __nv_bfloat162* tspec,
-                                   __nv_bfloat162* prod, int Bz, int K, const float2* tw,
-                                   cudaStream_t st) {
-    return fftk::run_cols_mul<L, __nv_bfloat162, __nv_bfloat162>(spec, tspec, prod, Bz, K, tw, st);
+                                   __nv_bfloat162* prod, int Bz, int K, const float2* tw, int lo,
+                                   int hi, cudaStream_t st) {
+    return fftk::run_cols_mul<L, __nv_bfloat162, __nv_bfloat162>(spec, tspec, prod, Bz, K, tw, lo,
+                                                                 hi, st);
 }
 
 template <int L>
 cudaError_t FftLen<L>::rows_c2r(const float2* prod, int X, int Y, int Z, FftGeom g, float* corr,
-                                int K, const float2* tw, int* status, cudaStream_t st) {
-    return fftk::run_rows_c2r<L, float2, float>(prod, X, Y, Z, g, corr, K, tw, status, st);
+                                int K, const float2* tw, int* status, FftKeep keep,
+                                cudaStream_t st) {
+    return fftk::run_rows_c2r<L, float2, float>(prod, X, Y, Z, g, corr, K, tw, status, keep, st);
 }
 
 template <int L>
 cudaError_t FftLen<L>::rows_c2r_bf(const __nv_bfloat162* prod, int X, int Y, int Z, FftGeom g,
                                    __nv_bfloat16* corr, int K, const float2* tw, int* status,
-                                   cudaStream_t st) {
+                                   FftKeep keep, cudaStream_t st) {
     return fftk::run_rows_c2r<L, __nv_bfloat162, __nv_bfloat16>(prod, X, Y, Z, g, corr, K, tw,
-                                                                 status, st);
+                                                                 status, keep, st);
 }
 
 }  // namespace ttm

@@ -17,6 +17,7 @@ static void fill_args(const void* corr, const float* w, size_t nvox, const VoxBo
     pa.corr = corr; pa.w = w; pa.nvox = nvox; pa.box = box; pa.score = score; pa.cand = cand; pa.quat = quat;
     pa.lambda = lambda; pa.comp_out = comp_out; pa.gq = g.d_q; pa.n_cand = g.n_cand;
     pa.newton = g.newton;
+    pa.n_refine = g.n_refine;
 }
 
 ttm_status launch_rotation_search(int n_order, const void* corr, bool bf16, const float* w,

@@ -12,8 +12,8 @@
 // and read as a broadcast.  The best point of each region competes for a short
 // list of n_cand candidates.  Every candidate takes two shifted power steps
 // (x <- normalise(C x^{n-1} + sigma x), sigma = (n-1) score, the SS-HOPM step
-// of Kolda & Mayo 2011, monotone for this shift); the kRefine best of the
-// points reached are then refined by Riemannian Newton steps on the sphere,
+// of Kolda & Mayo 2011, monotone for this shift); the n_refine (<= kRefine)
+// best of the points reached are then refined by Riemannian Newton steps on the sphere,
 // each accepted only if phi does not decrease (otherwise the power step is
 // taken).  The largest refined value wins.
 #pragma once
@@ -61,7 +61,7 @@ struct PolishArgs {
     float* lambda;          // nullable
     float* comp_out;        // nullable, K x nvox
     const float* gq;        // n_grid x 4
-    int n_cand, newton;
+    int n_cand, newton, n_refine;
 };
 
 // end of the units [.., u1) and the voxel of unit i, with an optional list
@@ -468,9 +468,10 @@ __global__ void __launch_bounds__(kRotThreads) polish_kernel(PolishArgs a) {
                 }
             }
         }
-        // phase 2: Newton refinement of the kept points
+        // phase 2: Newton refinement of the n_refine best kept points
 #pragma unroll 1
         for (int s = 0; s < kRefine; ++s) {
+            if (s >= a.n_refine) break;
             // the kept point s, picked with compile-time indices (registers,
             // no local memory)
             float ls = -INFINITY, x[4] = {0.f, 0.f, 0.f, 0.f};

@@ -8,9 +8,11 @@
 // a constant shift and the shift removes the cancellation of large offsets),
 // and builds exclusive prefix sums of (f - mu) and (f - mu)^2 along x in
 // shared memory.  Each x-run of the mask then costs two prefix lookups per
-// statistic.  S1 and S2 accumulate in FP32; V = S2 - S1^2/m_sum is formed in
-// FP64.  The degenerate-variance floor is 1e-6 * m_sum * var(f) with var(f)
-// from launch_volume_moments.
+// statistic.  The prefix sums and S1, S2 are FP64: a difference of two prefix
+// sums cancels whatever the row holds before the run, which in FP32 loses a
+// quiet run next to a bright one.  V = S2 - S1^2/m_sum is formed in FP64.
+// The degenerate-variance floor is 1e-6 * m_sum * var(f) with var(f) from
+// launch_volume_moments.
 #include "ttm_internal.h"
 
 namespace ttm {
@@ -79,12 +81,12 @@ struct StatsArgs {
 };
 
 __global__ void __launch_bounds__(kStatThreads) local_stats_kernel(StatsArgs a) {
-    extern __shared__ float smem[];
+    extern __shared__ double smem[];
     const int rows = kTY + (a.dy_max - a.dy_min);
     const int width = kTX + (a.x_max - a.x_min);     // staged values per row
     const int pitch = width + 1;                     // exclusive prefix length
-    float* P1 = smem;
-    float* P2 = smem + rows * pitch;
+    double* P1 = smem;
+    double* P2 = smem + rows * pitch;
 
     const int x0 = blockIdx.x * kTX;
     const int y0 = blockIdx.y * kTY;
@@ -94,9 +96,9 @@ __global__ void __launch_bounds__(kStatThreads) local_stats_kernel(StatsArgs a) 
 
     // reference value: the input voxel nearest the tile centre (clamped)
     const int cx = min(x0 + kTX / 2, a.X - 1), cy = min(y0 + kTY / 2, a.Y - 1);
-    const float mu = __ldg(a.f + ((size_t)z * a.Y + cy) * a.X + cx);
+    const double mu = __ldg(a.f + ((size_t)z * a.Y + cy) * a.X + cx);
 
-    float s1[2] = {0.f, 0.f}, s2[2] = {0.f, 0.f};
+    double s1[2] = {0.0, 0.0}, s2[2] = {0.0, 0.0};
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int nwarps = kStatThreads / 32;
 
@@ -108,19 +110,19 @@ __global__ void __launch_bounds__(kStatThreads) local_stats_kernel(StatsArgs a) 
             const int yy = y0 + a.dy_min + r;
             const bool row_ok = zz >= 0 && zz < a.Z && yy >= 0 && yy < a.Y;
             const float* src = a.f + ((size_t)(row_ok ? zz : 0) * a.Y + (row_ok ? yy : 0)) * a.X;
-            float run1 = 0.f, run2 = 0.f;
+            double run1 = 0.0, run2 = 0.0;
             for (int base = 0; base < width; base += 32) {
                 const int i = base + lane;
                 const int xx = x0 + a.x_min + i;
-                float v = 0.f;
-                if (i < width && row_ok && xx >= 0 && xx < a.X) v = __ldg(src + xx) - mu;
-                float v2 = v * v;
+                double v = 0.0;
+                if (i < width && row_ok && xx >= 0 && xx < a.X) v = (double)__ldg(src + xx) - mu;
+                double v2 = v * v;
                 // inclusive warp scan
-                float c1 = v, c2 = v2;
+                double c1 = v, c2 = v2;
 #pragma unroll
                 for (int o = 1; o < 32; o <<= 1) {
-                    float t1 = __shfl_up_sync(0xffffffffu, c1, o);
-                    float t2 = __shfl_up_sync(0xffffffffu, c2, o);
+                    double t1 = __shfl_up_sync(0xffffffffu, c1, o);
+                    double t2 = __shfl_up_sync(0xffffffffu, c2, o);
                     if (lane >= o) { c1 += t1; c2 += t2; }
                 }
                 if (i < width) {
@@ -131,8 +133,8 @@ __global__ void __launch_bounds__(kStatThreads) local_stats_kernel(StatsArgs a) 
                 run2 += __shfl_sync(0xffffffffu, c2, 31);
             }
             if (lane == 0) {
-                P1[r * pitch] = 0.f;
-                P2[r * pitch] = 0.f;
+                P1[r * pitch] = 0.0;
+                P2[r * pitch] = 0.0;
             }
         }
         __syncthreads();
@@ -178,6 +180,59 @@ __global__ void __launch_bounds__(kStatThreads) local_stats_kernel(StatsArgs a) 
     }
 }
 
+// Exact local statistics at the voxels flagged by the FFT window sums (w = -1
+// there; flagged voxels are interior).  One warp per flagged voxel: the lanes
+// split the s^3 mask box and accumulate m (f - f(x)) and m (f - f(x))^2 in
+// FP64 (a shift by the voxel's own value; the variance does not change under
+// it), then V = S2 - S1^2 / m_sum and w as in every other path.  Warps scan
+// the w map 32 voxels at a time; with no flagged voxel the kernel returns at
+// once.
+__global__ void __launch_bounds__(256) exact_stats_kernel(
+    const float* __restrict__ f, float* __restrict__ w, int X, int Y, int Z, int s,
+    const float* __restrict__ mask, double mask_sum, const double* __restrict__ moments,
+    const unsigned int* __restrict__ flagged) {
+    if (*flagged == 0u) return;
+    const double nvox = (double)X * Y * Z;
+    const double mean = moments[0] / nvox;
+    const double floor_v = 1e-6 * mask_sum * fmax(moments[1] / nvox - mean * mean, 0.0);
+    const int lane = threadIdx.x & 31;
+    const size_t n = (size_t)X * Y * Z;
+    const size_t warp0 = ((size_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const size_t nwarps = ((size_t)gridDim.x * blockDim.x) >> 5;
+    const int c = s / 2, s3 = s * s * s;
+    for (size_t base = warp0 * 32; base < n; base += nwarps * 32) {
+        const size_t v = base + lane;
+        uint32_t bits = __ballot_sync(0xffffffffu, v < n && w[v] < 0.f);
+        while (bits) {
+            const int src = __ffs(bits) - 1;
+            bits &= bits - 1;
+            const size_t vv = base + src;
+            const int x = (int)(vv % (size_t)X);
+            const int y = (int)((vv / (size_t)X) % (size_t)Y);
+            const int z = (int)(vv / ((size_t)X * Y));
+            const double ref = f[vv];
+            double a1 = 0.0, a2 = 0.0;
+            for (int u = lane; u < s3; u += 32) {
+                const float mu = __ldg(mask + u);
+                if (mu == 0.f) continue;
+                const int ux = u % s, uy = (u / s) % s, uz = u / (s * s);
+                const double d = (double)__ldg(f + ((size_t)(z + uz - c) * Y + (y + uy - c)) * X +
+                                               (x + ux - c)) - ref;
+                a1 = fma((double)mu, d, a1);
+                a2 = fma((double)mu * d, d, a2);
+            }
+            for (int o = 16; o > 0; o >>= 1) {
+                a1 += __shfl_down_sync(0xffffffffu, a1, o);
+                a2 += __shfl_down_sync(0xffffffffu, a2, o);
+            }
+            if (lane == 0) {
+                const double V = a2 - a1 * a1 / mask_sum;
+                w[vv] = V > floor_v ? (float)(1.0 / sqrt(V)) : 0.f;
+            }
+        }
+    }
+}
+
 // integer hash of (index, seed) -> uniform float in [-1, 1)
 __global__ void fill_random_kernel(float* __restrict__ f, size_t n, uint32_t seed) {
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
@@ -204,6 +259,14 @@ ttm_status launch_volume_moments(const float* f, size_t n, double* d_acc, cudaSt
     return after_launch(cnt);
 }
 
+ttm_status launch_exact_stats(const float* f, float* w, int X, int Y, int Z,
+                              const TemplateData& T, const double* moments,
+                              const unsigned int* flagged, cudaStream_t st, long long* cnt) {
+    exact_stats_kernel<<<152 * 8, 256, 0, st>>>(f, w, X, Y, Z, T.desc.s, T.d_mask,
+                                                T.desc.mask_sum, moments, flagged);
+    return after_launch(cnt);
+}
+
 ttm_status launch_local_stats(const float* f, int X, int Y, int Z, const TemplateData& T,
                               const double* d_moments, float* w, cudaStream_t st,
                               long long* cnt) {
@@ -216,7 +279,7 @@ ttm_status launch_local_stats(const float* f, int X, int Y, int Z, const Templat
     a.moments = d_moments;
     const int rows = kTY + (T.dy_max - T.dy_min);
     const int pitch = kTX + (T.x_max - T.x_min) + 1;
-    const size_t smem = (size_t)2 * rows * pitch * sizeof(float);
+    const size_t smem = (size_t)2 * rows * pitch * sizeof(double);
     if (smem > 200 * 1024) return TTM_ERR_UNSUPPORTED;
     TTM_CUDA_TRY(cudaFuncSetAttribute(local_stats_kernel,
                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));

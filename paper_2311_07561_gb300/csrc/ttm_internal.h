@@ -106,9 +106,20 @@ inline VoxBox interior_box(int X, int Y, int Z, int s) {
     return b;
 }
 
+// Voxels whose inverse-FFT outputs are used (inclusive bounds): the inverse
+// passes skip the z planes, y rows and x samples outside it.
+struct FftKeep {
+    int x0, x1, y0, y1, z0, z1;
+};
+inline FftKeep fft_keep_interior(int X, int Y, int Z, int s) {
+    const int c = s / 2;
+    return FftKeep{c, X - s + c, c, Y - s + c, c, Z - s + c};
+}
+inline FftKeep fft_keep_all(int X, int Y, int Z) { return FftKeep{0, X - 1, 0, Y - 1, 0, Z - 1}; }
+
 // Rotation search grid (device tables owned by the plan).
 struct RotGrid {
-    int n_grid = 0, n_cells = 0, n_cand = 0, newton = 0;
+    int n_grid = 0, n_cells = 0, n_cand = 0, newton = 0, n_refine = 0;
     float* d_q = nullptr;        // n_grid x 4 unit quaternions, a >= 0, sorted by cell
     float* d_m = nullptr;        // n_grid x K: mu_alpha q_g^alpha
     int* d_cell_end = nullptr;   // n_grid: 1 if the next point starts a new cell
@@ -231,24 +242,33 @@ int fft_good_length(int n);
 // mode 0: F(f); 1: F(f - mean); 2: F((f - mean)^2), mean from moments (sum f first)
 ttm_status launch_fft_forward(const float* f, int X, int Y, int Z, const FftShape& S,
                               float2* spec, cudaStream_t st, long long* cnt, int mode = 0,
-                              const double* moments = nullptr);
+                              double* moments = nullptr);
 bool fft_template_length(int L);
 // mixed precision (bf16 storage, FP32 arithmetic); lengths 16..1024 only
 ttm_status launch_fft_spectrum_inverse_z_bf16(const float2* spec, const void* tspec, int K,
-                                              const FftShape& S, void* prod, cudaStream_t st,
-                                              long long* cnt);
+                                              const FftShape& S, void* prod, const FftKeep& keep,
+                                              cudaStream_t st, long long* cnt);
 // status: device word that records TTM_ERR_TIMEOUT if a bounded copy wait expires
 ttm_status launch_fft_inverse_yx_bf16(void* prod, int K, int X, int Y, int Z, const FftShape& S,
-                                      void* corr, int* status, cudaStream_t st, long long* cnt);
+                                      void* corr, int* status, const FftKeep& keep,
+                                      cudaStream_t st, long long* cnt);
 ttm_status launch_spectra_to_bf16(const float2* a, void* b, size_t n, cudaStream_t st, long long* cnt);
+// w from FP32 FFT window sums; windows whose FP32 rounding bound exceeds the
+// tolerance get w = -1 and are counted in *flagged for launch_exact_stats
 ttm_status launch_stats_from_sums(const float* s1, const float* s2, float* w, int X, int Y, int Z,
-                                  int s, double mask_sum, const double* moments, cudaStream_t st,
-                                  long long* cnt);
+                                  int s, double mask_sum, const double* moments,
+                                  unsigned int* flagged, cudaStream_t st, long long* cnt);
+// exact FP64 window sums and w at the voxels flagged by launch_stats_from_sums
+ttm_status launch_exact_stats(const float* f, float* w, int X, int Y, int Z,
+                              const TemplateData& T, const double* moments,
+                              const unsigned int* flagged, cudaStream_t st, long long* cnt);
+// keep: the voxels whose outputs are used (z range for the multiply pass)
 ttm_status launch_fft_spectrum_inverse_z(const float2* spec, const float2* tspec, int K,
-                                         const FftShape& S, float2* prod, cudaStream_t st,
-                                         long long* cnt);
+                                         const FftShape& S, float2* prod, const FftKeep& keep,
+                                         cudaStream_t st, long long* cnt);
 ttm_status launch_fft_inverse_yx(float2* prod, int K, int X, int Y, int Z, const FftShape& S,
-                                 float* corr, int* status, cudaStream_t st, long long* cnt);
+                                 float* corr, int* status, const FftKeep& keep, cudaStream_t st,
+                                 long long* cnt);
 ttm_status launch_template_spectra(const float* comp, int K, int s, const FftShape& S,
                                    float* pad, float2* tspec, cudaStream_t st, long long* cnt);
 

@@ -44,7 +44,7 @@ def test_refinement_work_per_voxel_order_four():
     # monomials x 4 outputs, 2 normalisations) + the 4 best x 3 Newton steps
     # (4 evaluations of C x^2: 10 entries x 10 quadratic monomials, 3 solves)
     per_voxel = 8 * (3 * 10 * 20 + 24) + 4 * (4 * (2 * 10 * 10 + 2 * 10 + 40) + 3 * 150)
-    assert per_voxel == 10952 == bench.refinement_flop_per_voxel(35, 8, 3)
+    assert per_voxel == 10952 == bench.refinement_flop_per_voxel(35, 8, 3, 4)
 
 
 def test_order_six_search_pads_to_96():
