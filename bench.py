@@ -92,6 +92,12 @@ def budget(K: int):
     return REFINE_BUDGET.get(n_ord, DEFAULT_BUDGET)
 
 
+def grid_points(K: int, mixed: bool) -> int:
+    """The plan's default rotation search grid: 1024 points at order 6 with
+    bf16 storage, else 2048."""
+    return 1024 if (K == 84 and mixed) else 2048
+
+
 def refinement_text(K: int) -> str:
     c, r, nw = budget(K)
     return f"{c} candidates x 2 power steps, the {r} best x {nw} Newton steps"
@@ -606,10 +612,11 @@ def roofline(kernels: dict, steps: int, geo: dict, peaks: dict) -> dict:
         kp_ = kernels.get("rotation_polish", {}).get("ms", 0.0) / steps
         if ks > 0 and K in (35, 84):
             kp = 48 if K == 35 else 96
-            mma = 2.0 * 2048 * kp * n_int / (ks * 1e-3) / 1e12
+            gp = grid_points(K, geo["mixed"])
+            mma = 2.0 * gp * kp * n_int / (ks * 1e-3) / 1e12
             extra["tensor_pipe"] = dict(kernel="rotation_search", achieved=round(mma, 2),
                                         peak=round(bf16, 1), unit="TFLOP/s", frac=round(mma / bf16, 4),
-                                        work="dense FP16 grid contraction 2 x 2048 x KP per voxel")
+                                        work=f"dense FP16 grid contraction 2 x {gp} x KP per voxel")
         if kp_ > 0:
             ref = refinement_flop_per_voxel(K) * n_int / (kp_ * 1e-3) / 1e12
             extra["refinement_alu"] = dict(kernel="rotation_polish", achieved=round(ref, 2),
@@ -630,15 +637,20 @@ def roofline(kernels: dict, steps: int, geo: dict, peaks: dict) -> dict:
             peak_source = "derived: 152 SMs x 128 FP32 lanes x 2 FLOP x 2070 MHz"
         work_note = "2 x K x mask voxels per voxel"
     else:
+        kz, ky = geo.get("keep_z_frac", 1.0), geo.get("keep_y_frac", 1.0)
         if name == "fft_inverse":
-            # y pass: read + write every product spectrum; x pass: read it,
-            # write the real map
-            work = K * (3.0 * nh * cs + nvox * msz)
-            work_note = "K x (3 x half spectrum + map)"
+            # y pass: read the interior z planes of every product spectrum,
+            # write their interior rows; x pass: read those rows, write the
+            # interior of the real map
+            work = K * (nh * cs * kz * (1.0 + 2.0 * ky) + n_int * msz)
+            work_note = ("K x (interior planes of the half spectrum read, their interior rows "
+                         "written and read again, interior map written)")
         elif name == "fft_spectrum_inverse":
-            # image spectrum once, every template spectrum read, every product written
-            work = nh * (8.0 + 2.0 * K * cs)
-            work_note = "image spectrum + K x (template spectrum + product)"
+            # image spectrum once per component group, every template spectrum
+            # read, the interior z planes of every product written
+            work = nh * (8.0 * geo.get("groups", 1) + K * cs * (1.0 + kz))
+            work_note = ("image spectrum per component group + K x (template spectrum + "
+                         "interior planes of the product)")
         elif name == "fft_forward":
             work = 4.0 * nvox + 40.0 * nh
             work_note = "volume read + three passes over the FP32 half spectrum"
@@ -888,6 +900,8 @@ def run_ours(args) -> None:
     geo = dict(K=desc.K, nvox=nvox, n_interior=n_interior, n_taps=n_taps,
                mixed=args.precision == "mixed",
                spectrum_values=float((box[0] // 2 + 1) * box[1] * box[2]),
+               keep_z_frac=max(Z - s_edge + 1, 0) / box[2], keep_y_frac=max(Y - s_edge + 1, 0) / box[1],
+               groups=kern.get("fft_spectrum_inverse", {}).get("launches", args.steps) / args.steps,
                tc_direct=bool(ttm.ttm_plan_problem_tensor_direct(matcher.plan, 0)))
     rf = roofline(kern, args.steps, geo, peaks)
     matcher.close()
@@ -926,7 +940,8 @@ def run_ours(args) -> None:
                                "correlation maps; FP32 arithmetic"),
                     fft_box=list(box) if path == 2 else None,
                     voxels=nvox, interior_voxels=n_interior, tensor_order=wl.n_order, K=desc.K,
-                    mask_voxels=n_taps, rotation_grid=2048, refinement=refinement_text(desc.K),
+                    mask_voxels=n_taps, rotation_grid=grid_points(desc.K, args.precision == "mixed"),
+                    refinement=refinement_text(desc.K),
                     l2="flushed (256 MB write) before every timed step",
                     parallelism="replicas" if world > 1 else "single GPU",
                     template_build_ms=round(build_ms, 2), quadrature_rotations=desc.n_rot),

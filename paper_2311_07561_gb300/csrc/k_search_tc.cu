@@ -38,16 +38,15 @@ namespace {
 
 constexpr int kThreads = 256;    // warps w and w + 4 read the same TMEM lanes
 constexpr int kGroups = kThreads / 128;    // column groups of a chunk (one per 4 warps)
-constexpr int kG = 2048;             // grid points
 constexpr int kChunkN = 256;         // grid points per MMA
-constexpr int kChunks = kG / kChunkN;
 constexpr uint32_t kMergeBytes = (kGroups - 1) * 128 * 8 * 4;  // top-8 keys of groups 1..
 constexpr long kWaitLimit = 1L << 24;   // try_wait polls; well beyond any MMA latency
 
-// Shapes for K tensor components: padded K, shared-memory sizes, and whether
-// the grid table is resident or streamed.
-template <int K>
+// Shapes for K tensor components and G grid points (1024 or 2048): padded
+// K, shared-memory sizes, and whether the grid table is resident or streamed.
+template <int K, int G>
 struct TcShape {
+    static constexpr int kChunks = G / kChunkN;
     static constexpr int KP = ((K + 1 + 15) / 16) * 16;          // + constant column
     static constexpr int KC = KP / 8;                            // core-matrix columns along K
     static constexpr uint32_t ABytes = (uint32_t)KC * 16 * 128;
@@ -227,11 +226,12 @@ __device__ __forceinline__ void region_max32(const uint32_t (&r)[32], int low0, 
     n1 = nk[1];
 }
 
-template <typename CT, int N>
+template <typename CT, int N, int G>
 __global__ void __launch_bounds__(kThreads, 1) search_tc_kernel(rot::SearchArgs a,
                                                                 const uint4* __restrict__ gtab,
                                                                 int* status) {
-    using Sh = TcShape<n_comp(N)>;
+    using Sh = TcShape<n_comp(N), G>;
+    constexpr int kChunks = Sh::kChunks;
     constexpr int K = n_comp(N);
     constexpr int KP = Sh::KP;
     constexpr bool kStream = Sh::Stream;
@@ -479,11 +479,11 @@ __global__ void __launch_bounds__(kThreads, 1) search_tc_kernel(rot::SearchArgs 
 
 }  // namespace
 
-template <typename CT, int N>
+template <typename CT, int N, int G>
 static ttm_status launch_tc_t(const rot::SearchArgs& s, const uint16_t* grid_fp16, int* status,
                               cudaStream_t st, long long* cnt) {
-    constexpr uint32_t smem = TcShape<n_comp(N)>::Smem;
-    TTM_CUDA_TRY(cudaFuncSetAttribute(search_tc_kernel<CT, N>,
+    constexpr uint32_t smem = TcShape<n_comp(N), G>::Smem;
+    TTM_CUDA_TRY(cudaFuncSetAttribute(search_tc_kernel<CT, N, G>,
                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int dev = 0, sms = 0;
     TTM_CUDA_TRY(cudaGetDevice(&dev));
@@ -491,24 +491,33 @@ static ttm_status launch_tc_t(const rot::SearchArgs& s, const uint16_t* grid_fp1
     const size_t ntiles = ((s.u1 > s.u0 ? s.u1 - s.u0 : 0) + 127) / 128;
     if (ntiles == 0) return TTM_OK;
     const unsigned grid = (unsigned)(ntiles < (size_t)sms ? ntiles : (size_t)sms);
-    search_tc_kernel<CT, N><<<grid, kThreads, smem, st>>>(
+    search_tc_kernel<CT, N, G><<<grid, kThreads, smem, st>>>(
         s, reinterpret_cast<const uint4*>(grid_fp16), status);
     return after_launch(cnt);
 }
 
+// grids of 2048 points in 128 regions, or 1024 points in 64 regions, of 16
 bool search_tc_supported(int n_order, int n_grid, int n_cells) {
-    return (n_order == 4 || n_order == 6) && n_grid == kG && n_cells == kG / 16;
+    return (n_order == 4 || n_order == 6) && (n_grid == 2048 || n_grid == 1024) &&
+           n_cells == n_grid / 16;
 }
 
 ttm_status launch_search_tc(int n_order, const rot::SearchArgs& s, const uint16_t* grid_fp16,
                             int* status, bool bf16, cudaStream_t st, long long* cnt) {
-    if (s.n_grid != kG || !grid_fp16) return TTM_ERR_UNSUPPORTED;
-    if (n_order == 4)
-        return bf16 ? launch_tc_t<__nv_bfloat16, 4>(s, grid_fp16, status, st, cnt)
-                    : launch_tc_t<float, 4>(s, grid_fp16, status, st, cnt);
-    if (n_order == 6)
-        return bf16 ? launch_tc_t<__nv_bfloat16, 6>(s, grid_fp16, status, st, cnt)
-                    : launch_tc_t<float, 6>(s, grid_fp16, status, st, cnt);
+    if ((s.n_grid != 2048 && s.n_grid != 1024) || !grid_fp16) return TTM_ERR_UNSUPPORTED;
+    const bool g1 = s.n_grid == 1024;
+    if (n_order == 4) {
+        if (g1) return bf16 ? launch_tc_t<__nv_bfloat16, 4, 1024>(s, grid_fp16, status, st, cnt)
+                            : launch_tc_t<float, 4, 1024>(s, grid_fp16, status, st, cnt);
+        return bf16 ? launch_tc_t<__nv_bfloat16, 4, 2048>(s, grid_fp16, status, st, cnt)
+                    : launch_tc_t<float, 4, 2048>(s, grid_fp16, status, st, cnt);
+    }
+    if (n_order == 6) {
+        if (g1) return bf16 ? launch_tc_t<__nv_bfloat16, 6, 1024>(s, grid_fp16, status, st, cnt)
+                            : launch_tc_t<float, 6, 1024>(s, grid_fp16, status, st, cnt);
+        return bf16 ? launch_tc_t<__nv_bfloat16, 6, 2048>(s, grid_fp16, status, st, cnt)
+                    : launch_tc_t<float, 6, 2048>(s, grid_fp16, status, st, cnt);
+    }
     return TTM_ERR_UNSUPPORTED;
 }
 
@@ -516,10 +525,10 @@ ttm_status launch_search_tc(int n_order, const rot::SearchArgs& s, const uint16_
 // points: element (g, k) of the 2048 x KP matrix [mu_k q_g^k | 1 | 0...] at
 // chunk g / 256, core matrix (k / 8, (g % 256) / 8), row g % 8, column k % 8,
 // core matrices ordered k-block-major within the chunk.
-void build_grid_fp16(const float* m_rows, int K, int K4, std::vector<uint16_t>& out) {
+void build_grid_fp16(const float* m_rows, int K, int K4, int n_grid, std::vector<uint16_t>& out) {
     const int KP = ((K + 1 + 15) / 16) * 16;
-    out.assign((size_t)kG * KP, 0);
-    for (int g = 0; g < kG; ++g)
+    out.assign((size_t)n_grid * KP, 0);
+    for (int g = 0; g < n_grid; ++g)
         for (int k = 0; k < KP; ++k) {
             // column K holds the constant 1 paired with A's constant column,
             // adding +1 to every phi

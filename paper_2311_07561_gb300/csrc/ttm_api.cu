@@ -91,8 +91,13 @@ ttm_status dev_upload(T** dst, const std::vector<T>& src) {
 
 ttm_status build_grid(ttm_plan_s* P) {
     RotGrid& g = P->grid;
-    const int n = P->opts.n_grid > 0 ? P->opts.n_grid : 2048;
-    const int nc = P->opts.n_cells > 0 ? P->opts.n_cells : 128;
+    // order 6 in mixed precision searches 1024 points (64 regions of 16): the
+    // FP64 model of the search and refinement on the order-6 workload's
+    // template gives a largest lambda shortfall of 6.2e-5 (4.2e-5 with 2048
+    // points), inside that mode's 5e-3 tolerance; every other case 2048
+    const int n_def = (P->n_order == 6 && P->opts.precision == TTM_PREC_MIXED) ? 1024 : 2048;
+    const int n = P->opts.n_grid > 0 ? P->opts.n_grid : n_def;
+    const int nc = P->opts.n_cells > 0 ? P->opts.n_cells : n / 16;
     // refinement budget: at order 6 the maxima of phi are sharper and the
     // grid search lands closer; an FP64 model of the search and refinement
     // (the unit tests' model, on 400 voxels of the 928 x 928 x 464 workload's
@@ -150,7 +155,7 @@ ttm_status build_grid(ttm_plan_s* P) {
     TTM_TRY(dev_upload(&g.d_cell_end, ends));
     if (search_tc_supported(P->n_order, n, nc)) {
         std::vector<uint16_t> tab;
-        build_grid_fp16(hm.data(), K, K4, tab);
+        build_grid_fp16(hm.data(), K, K4, n, tab);
         std::vector<uint32_t> bits(n / 32, 0u);
         for (int i = 0; i < n; ++i)
             if (ends[i]) bits[i / 32] |= 1u << (i % 32);
@@ -934,7 +939,7 @@ ttm_status ttm_plan(ttm_plan_t* out, int n_problems, const int* vol_dims, const 
         if (o.n_grid < 0 || o.n_cells < 0 || o.n_candidates < 0 || o.newton_steps < 0 ||
             o.rotation_chunks < 0 || o.n_refined < 0)
             return TTM_ERR_INVALID_ARG;
-        const int n = o.n_grid > 0 ? o.n_grid : 2048, nc = o.n_cells > 0 ? o.n_cells : 128;
+        const int n = o.n_grid > 0 ? o.n_grid : 2048, nc = o.n_cells > 0 ? o.n_cells : n / 16;
         if (n > 65535 || nc > n || n % nc != 0 || o.n_candidates > 8 || o.newton_steps > 64 ||
             o.n_refined > 4)
             return TTM_ERR_INVALID_ARG;

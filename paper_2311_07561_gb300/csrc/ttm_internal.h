@@ -223,7 +223,7 @@ ttm_status launch_exterior_fill(int Z, const VoxBox& box, int K, float* score, f
                                 float* lambda, float* comp_out, cudaStream_t st, long long* cnt);
 // FP16 grid table of the tensor-core search (2048 points, K components + the
 // constant column, padded to a multiple of 16, chunk-major core-matrix layout)
-void build_grid_fp16(const float* m_rows, int K, int K4, std::vector<uint16_t>& out);
+void build_grid_fp16(const float* m_rows, int K, int K4, int n_grid, std::vector<uint16_t>& out);
 bool search_tc_supported(int n_order, int n_grid, int n_cells);
 
 // tensor template build

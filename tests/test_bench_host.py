@@ -66,6 +66,21 @@ def test_memory_bound_stages_use_algorithmic_bytes():
     assert rf["achieved"] == pytest.approx(84 * (3 * spec * 4 + 10 ** 6 * 2) / 1e-3 / 1e9, rel=1e-3)
 
 
+def test_inverse_passes_count_the_interior_only():
+    """With interior fractions kz (z planes) and ky (y rows) of the box, the
+    y pass reads kz of every product and writes ky of that, the x pass reads
+    it again and writes the interior map; the multiply pass reads the image
+    spectrum once per component group and writes kz of every product."""
+    spec = 481.0 * 960 * 480
+    geo = dict(_geo(K=84, nvox=10 ** 6, n_int=5 * 10 ** 5, mixed=True, spec=spec),
+               keep_z_frac=0.8, keep_y_frac=0.9, groups=10)
+    rf = bench.roofline(_one("fft_inverse"), 1, geo, PEAKS)
+    assert rf["achieved"] == pytest.approx(
+        84 * (spec * 4 * 0.8 * (1 + 2 * 0.9) + 5e5 * 2) / 1e-3 / 1e9, rel=1e-6)
+    rf = bench.roofline(_one("fft_spectrum_inverse"), 1, geo, PEAKS)
+    assert rf["achieved"] == pytest.approx(spec * (8 * 10 + 84 * 4 * 1.8) / 1e-3 / 1e9, rel=1e-6)
+
+
 def test_traffic_only_while_sources_unchanged(monkeypatch):
     kern = dict(rotation_search=dict(ms=1.0, launches=8), rotation_polish=dict(ms=1.0, launches=8))
     recs = {k: [dict(v[0])] for k, v in bench.NCU_TRAFFIC.items()}

@@ -222,6 +222,36 @@ def test_fft_smooth_lengths(ttm, shape_zyx, boxes):
     res["matcher"].close()
 
 
+@pytest.mark.parametrize("precision", ["fp32", "mixed"])
+@pytest.mark.parametrize("shape_zyx,boxes", [
+    ((20, 24, 900), (960, 32, 32)),       # x lines of 960 = 32 x 30
+    ((20, 900, 24), (32, 960, 32)),       # y lines of 960
+    ((470, 24, 20), (32, 32, 480)),       # z lines of 480 = 16 x 30
+])
+def test_two_level_lengths(ttm, shape_zyx, boxes, precision):
+    """The long lines of the 928 x 928 x 464 configuration (960 and 480)
+    take the two-level passes (register DFTs of 32 or 16 and 30 points, one
+    shared-memory exchange); components, w and score agree with the
+    oracle's FP64 FFT on every axis, with FP32 and with bf16 storage."""
+    wl = synth.make_workload(shape_zyx, 9, 3, 3, 1.0, 4, 200, radius=4, seeds=(31, 32, 33))
+    T = o.tensor_template(wl.template, wl.mask, wl.quadrature.astype(np.float64), wl.weights, 4)
+    comp, desc = ttm.build_template(wl.template, wl.mask, 4, wl.quadrature)
+    opts = _opts(ttm, "fft")
+    if precision == "mixed":
+        opts.precision = ttm.TTM_PREC_MIXED
+    res = _run(ttm, wl, comp, desc, opts=opts)
+    assert tuple(ttm.ttm_plan_problem_fft_box(res["matcher"].plan, 0)) == boxes
+    tol = TOL if precision == "fp32" else 5e-3
+    w_o, C_o = o.ttm_components(wl.volume, T, wl.mask)
+    keep = o.interior_mask(wl.volume.shape, 9)
+    assert np.abs(res["comp"][:, keep] - C_o[:, keep]).max() <= tol
+    nz = w_o > 0
+    assert np.array_equal(res["w"] > 0, nz)
+    assert (np.abs(res["w"][nz] - w_o[nz]) / w_o[nz]).max() <= 1e-5
+    assert np.abs(res["score"] - o.frobenius_score(C_o, 4)).max() <= tol
+    res["matcher"].close()
+
+
 @pytest.mark.parametrize("path", PATHS)
 def test_order_six(ttm, path):
     wl = synth.make_workload((30, 28, 26), 9, 3, 1, 1.0, 6, 300, radius=4, seeds=(2, 3, 4))
@@ -235,6 +265,29 @@ def test_order_six(ttm, path):
     _rotation_check(C_o[:, pts[:, 2], pts[:, 1], pts[:, 0]].T,
                     res["lam"][pts[:, 2], pts[:, 1], pts[:, 0]],
                     res["quat"][pts[:, 2], pts[:, 1], pts[:, 0]], 6)
+
+
+def test_order_six_mixed_precision(ttm):
+    """Order 6 with bf16 storage: the plan's default search grid is then 1024
+    points (64 regions); components, score and lambda stay within the bf16
+    tolerance of the oracle and q is a maximiser of the oracle's phi."""
+    wl = synth.make_workload((40, 38, 36), 11, 4, 2, 1.0, 6, 300, radius=5, seeds=(12, 13, 14))
+    T = o.tensor_template(wl.template, wl.mask, wl.quadrature.astype(np.float64), wl.weights, 6)
+    comp, desc = ttm.build_template(wl.template, wl.mask, 6, wl.quadrature)
+    opts = _opts(ttm, "fft")
+    opts.precision = ttm.TTM_PREC_MIXED
+    res = _run(ttm, wl, comp, desc, opts=opts)
+    w_o, C_o = o.ttm_components(wl.volume, T, wl.mask)
+    tol = 5e-3
+    assert np.abs(res["comp"] - C_o).max() <= tol
+    assert np.abs(res["score"] - o.frobenius_score(C_o, 6)).max() <= tol
+    pts = np.concatenate([wl.positions, np.argwhere(w_o > 0)[::41][:160][:, ::-1]])
+    C_pts = C_o[:, pts[:, 2], pts[:, 1], pts[:, 0]].T
+    lam_o, _ = o.dominant_z_eigenpair(C_pts, 6)
+    lam = res["lam"][pts[:, 2], pts[:, 1], pts[:, 0]]
+    q = res["quat"][pts[:, 2], pts[:, 1], pts[:, 0]]
+    assert np.abs(lam - lam_o).max() <= tol
+    assert np.all(o.phi_unique(C_pts, q.astype(np.float64), 6) >= lam_o - tol)
 
 
 @pytest.fixture(scope="module")
