@@ -725,6 +725,11 @@ __global__ void __launch_bounds__(kFftThreads) rows_c2r_t(const PS* __restrict__
 }
 
 }  // namespace fftk
+}  // namespace ttm
+
+#include "k_fft2.cuh"
+
+namespace ttm {
 
 // Launchers of the four passes for one compile-time length L.  Each returns
 // the CUDA error of its attribute call or launch.  Defined out of line so that
@@ -764,8 +769,37 @@ inline cudaError_t sm_count(int* sms) {
 template <int L, typename PS>
 constexpr bool cols_persistent() { return 2 * (size_t)L * cols_tb_s<L, PS>() * sizeof(float2) > 100u * 1024u; }
 
+// persistent grid of a kernel: SMs x resident CTAs per SM, at most `work`
+template <class Kern>
+inline cudaError_t persistent_grid(Kern kern, size_t smem, size_t work, unsigned* grid) {
+    int sms = 0, per_sm = 0;
+    cudaError_t e = sm_count(&sms);
+    if (e != cudaSuccess) return e;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kTwoThreads, smem);
+    if (e != cudaSuccess) return e;
+    const size_t cap = (size_t)sms * (per_sm > 0 ? per_sm : 1);
+    *grid = (unsigned)(work < cap ? work : cap);
+    return cudaSuccess;
+}
+
 template <int L, int SIGN, typename PS>
 cudaError_t run_cols(PS* d, int B, int na, ColsMap mp, const float2* tw, cudaStream_t st) {
+    if constexpr (two_level<L>()) {
+        constexpr int L1 = TwoLevel<L>::L1, L2 = TwoLevel<L>::L2;
+        constexpr int TB = kTwoThreads / L1;
+        constexpr size_t smem = two_cols_smem<L1, L2>();
+        auto kern = cols2_t<L1, L2, SIGN, PS>;
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
+        if (e != cudaSuccess) return e;
+        const int ntb = (B + TB - 1) / TB;
+        const size_t ntiles = (size_t)ntb * na;
+        unsigned grid = 0;
+        if ((e = persistent_grid(kern, smem, ntiles, &grid)) != cudaSuccess) return e;
+        if (grid == 0) return cudaSuccess;
+        kern<<<grid, kTwoThreads, smem, st>>>(d, B, tw, mp, ntb, ntiles);
+        return cudaGetLastError();
+    }
     constexpr int TB = cols_tb_s<L, PS>();
     const size_t smem = (size_t)2 * L * TB * sizeof(float2);
     const int ntb = (B + TB - 1) / TB;
@@ -799,6 +833,18 @@ cudaError_t run_cols(PS* d, int B, int na, ColsMap mp, const float2* tw, cudaStr
 template <int L, typename TS, typename PS>
 cudaError_t run_cols_mul(const float2* spec, const TS* tspec, PS* prod, int Bz, int K,
                          const float2* tw, int lo, int hi, cudaStream_t st) {
+    if constexpr (two_level<L>()) {
+        constexpr int L1 = TwoLevel<L>::L1, L2 = TwoLevel<L>::L2;
+        constexpr int TB = kTwoThreads / L1;
+        constexpr size_t smem = two_cols_smem<L1, L2>();
+        auto kern = cols_mul2_t<L1, L2, TS, PS>;
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
+        if (e != cudaSuccess) return e;
+        dim3 grid((Bz + TB - 1) / TB, 1);
+        kern<<<grid, kTwoThreads, smem, st>>>(spec, tspec, prod, Bz, K, tw, lo, hi);
+        return cudaGetLastError();
+    }
     constexpr int TB = cols_tb<L>();
     const size_t smem = (size_t)2 * L * TB * sizeof(float2);
     cudaError_t e = cudaFuncSetAttribute(cols_mul_t<L, TS, PS>,
@@ -812,6 +858,23 @@ cudaError_t run_cols_mul(const float2* spec, const TS* tspec, PS* prod, int Bz, 
 template <int L, typename PS, typename RT>
 cudaError_t run_rows_c2r(const PS* prod, int X, int Y, int Z, FftGeom g, RT* corr, int K,
                          const float2* tw, int* status, FftKeep keep, cudaStream_t st) {
+    if constexpr (two_level<L>()) {
+        constexpr int L1 = TwoLevel<L>::L1, L2 = TwoLevel<L>::L2;
+        constexpr int NR = kTwoThreads / L1;
+        constexpr size_t smem = two_rows_smem<L1, L2>();
+        auto kern = rows_c2r2_t<L1, L2, PS, RT>;
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
+        if (e != cudaSuccess) return e;
+        if (keep.z1 < keep.z0 || keep.y1 < keep.y0 || keep.x1 < keep.x0) return cudaSuccess;
+        const size_t nrows = (size_t)K * (keep.z1 - keep.z0 + 1) * (keep.y1 - keep.y0 + 1);
+        unsigned grid = 0;
+        if ((e = persistent_grid(kern, smem, (nrows + NR - 1) / NR, &grid)) != cudaSuccess) return e;
+        if (grid == 0) return cudaSuccess;
+        (void)status;                       // no device-side waits in this pass
+        kern<<<grid, kTwoThreads, smem, st>>>(prod, X, Y, Z, g, corr, K, tw, keep);
+        return cudaGetLastError();
+    }
     constexpr int NB = rows_nb<L>();
     constexpr size_t smem = c2r_smem<L, PS>();
     cudaError_t e = cudaFuncSetAttribute(rows_c2r_t<L, PS, RT>,

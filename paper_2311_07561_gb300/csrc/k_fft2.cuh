@@ -1,0 +1,368 @@
+// Two-level line FFTs for the long lines of the correlation path.
+//
+// A line of length L = L1 L2 is transformed with one shared-memory exchange:
+// with n = n1 + L1 n2 and k = k2 + L2 k1,
+//   X[k2 + L2 k1] = sum_n1 W_L^(n1 k2) W_L1^(n1 k1) sum_n2 x[n1 + L1 n2] W_L2^(n2 k2),
+// so thread n1 loads its L2 samples x[n1 + L1 n2] straight from global memory
+// into registers, transforms them (DFT of length L2 in registers), multiplies
+// by W_L^(n1 k2) and writes them to shared memory; after one barrier thread k2
+// reads the L1 values of its column k2, transforms them (DFT of length L1 in
+// registers) and stores X[k2 + L2 k1] straight to global memory.  Each point
+// crosses shared memory once (a write and a read) instead of once per
+// Stockham stage, and the layouts below are free of bank conflicts.
+//
+// The register DFTs are mixed-radix Cooley-Tukey splits N = P Q down to the
+// radices of dft_small (2, 3, 4, 5, 8, 16); their internal twiddles are
+// compile-time constants from a constexpr table (cos and sin of 2 pi m / N
+// by Taylor series in double precision, rounded to float).  The twiddles
+// W_L^(n1 k2) come from the FP64-computed table of the pass.
+#pragma once
+
+namespace ttm {
+namespace fftk {
+
+// ---- compile-time cos / sin of 2 pi m / N --------------------------------
+constexpr double kTwoPi = 6.283185307179586476925287;
+
+constexpr double taylor_sin(double x) {
+    double term = x, sum = x;
+    for (int k = 1; k < 16; ++k) {
+        term *= -x * x / ((2.0 * k) * (2.0 * k + 1.0));
+        sum += term;
+    }
+    return sum;
+}
+
+constexpr double taylor_cos(double x) {
+    double term = 1.0, sum = 1.0;
+    for (int k = 1; k < 16; ++k) {
+        term *= -x * x / ((2.0 * k - 1.0) * (2.0 * k));
+        sum += term;
+    }
+    return sum;
+}
+
+// angle 2 pi m / N brought into (-pi, pi] with exact integer arithmetic
+constexpr double angle_2pi(int m, int N) {
+    m %= N;
+    if (m < 0) m += N;
+    if (2 * m > N) m -= N;
+    return kTwoPi * (double)m / (double)N;
+}
+
+template <int N>
+struct TwTable {
+    float c[N], s[N];
+    constexpr TwTable() : c(), s() {
+        for (int m = 0; m < N; ++m) {
+            c[m] = (float)taylor_cos(angle_2pi(m, N));
+            s[m] = (float)taylor_sin(angle_2pi(m, N));
+        }
+    }
+};
+
+// exp(SIGN 2 pi i m / N) for a compile-time m after unrolling
+template <int N, int SIGN>
+__device__ __forceinline__ float2 tw_const(int m) {
+    constexpr TwTable<N> T{};
+    const int r = ((m % N) + N) % N;
+    return make_float2(T.c[r], SIGN < 0 ? -T.s[r] : T.s[r]);
+}
+
+// ---- register DFTs of compile-time length ---------------------------------
+__host__ __device__ constexpr bool base_radix(int n) {
+    return n == 2 || n == 3 || n == 4 || n == 5 || n == 8 || n == 16;
+}
+// first factor of a split N = P Q: the largest base radix dividing N
+__host__ __device__ constexpr int split_p(int n) {
+    return n % 16 == 0 ? 16 : n % 8 == 0 ? 8 : n % 5 == 0 ? 5 : n % 4 == 0 ? 4 : n % 3 == 0 ? 3 : 2;
+}
+
+template <int N, int SIGN>
+__device__ __forceinline__ void dft_reg(float2 (&v)[N]);
+
+// N = P Q: for each q the P samples v[Q p + q] are transformed, multiplied
+// by W_N^(q k1), and for each k1 the Q values are transformed into
+// X[k1 + P k2]
+template <int N, int P, int SIGN>
+__device__ __forceinline__ void dft_split(float2 (&v)[N]) {
+    constexpr int Q = N / P;
+    float2 t[N];
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+        float2 a[P];
+#pragma unroll
+        for (int p = 0; p < P; ++p) a[p] = v[Q * p + q];
+        dft_reg<P, SIGN>(a);
+#pragma unroll
+        for (int k1 = 0; k1 < P; ++k1)
+            t[k1 * Q + q] = (q == 0 || k1 == 0) ? a[k1] : cmul(a[k1], tw_const<N, SIGN>(q * k1));
+    }
+#pragma unroll
+    for (int k1 = 0; k1 < P; ++k1) {
+        float2 b[Q];
+#pragma unroll
+        for (int q = 0; q < Q; ++q) b[q] = t[k1 * Q + q];
+        dft_reg<Q, SIGN>(b);
+#pragma unroll
+        for (int k2 = 0; k2 < Q; ++k2) v[k1 + P * k2] = b[k2];
+    }
+}
+
+template <int N, int SIGN>
+__device__ __forceinline__ void dft_reg(float2 (&v)[N]) {
+    if constexpr (N == 1) {
+        return;
+    } else if constexpr (base_radix(N)) {
+        dft_small<N, SIGN>(v);
+    } else {
+        dft_split<N, split_p(N), SIGN>(v);
+    }
+}
+
+// ---- line lengths that take the two-level passes ---------------------------
+// L = L1 L2 with L1 threads per line in the first step: 960 = 32 x 30 and
+// 480 = 16 x 30 (the padded boxes of the 928 x 928 x 464 configuration)
+template <int L> struct TwoLevel { static constexpr int L1 = 0, L2 = 0; };
+template <> struct TwoLevel<960> { static constexpr int L1 = 32, L2 = 30; };
+template <> struct TwoLevel<480> { static constexpr int L1 = 16, L2 = 30; };
+template <int L> constexpr bool two_level() { return TwoLevel<L>::L1 > 0; }
+
+constexpr int kTwoThreads = 256;
+
+// exchange buffer bytes of the column passes: L2 rows of (L1 + 1) x TB values
+template <int L1, int L2>
+constexpr size_t two_cols_smem() { return (size_t)L2 * (L1 + 1) * (kTwoThreads / L1) * sizeof(float2); }
+
+// ---- column pass: lines of length L1 L2, element stride B ---------------
+// Tile = TB = 256 / L1 consecutive columns of one plane (ColsMap); persistent
+// CTAs, the raw samples of the next tile are loaded into registers while the
+// current one is transformed.  Line samples lo..hi are stored.
+template <int L1, int L2, int SIGN, typename PS>
+__global__ void __launch_bounds__(kTwoThreads, 1) cols2_t(PS* __restrict__ data, int B,
+                                                          const float2* __restrict__ tw,
+                                                          ColsMap mp, int ntb, size_t ntiles) {
+    constexpr int L = L1 * L2;
+    constexpr int TB = kTwoThreads / L1;
+    constexpr int ZP = L1 + 1;
+    extern __shared__ float2 zx[];                    // [k2][n1 (padded)][column]
+    const int t = threadIdx.x;
+    const int n1 = t / TB, ca = t % TB;
+    PS raw[L2];
+    auto load = [&](size_t tile) {
+        const size_t plane = tile / (size_t)ntb;
+        const int b = (int)(tile - plane * (size_t)ntb) * TB + ca;
+        const size_t base = cols_plane_base(mp, (size_t)mp.p0 + plane, L, B);
+        if (b < B) {
+#pragma unroll
+            for (int n2 = 0; n2 < L2; ++n2) raw[n2] = data[base + (size_t)(n1 + L1 * n2) * B + b];
+        }
+    };
+    size_t tile = blockIdx.x;
+    if (tile >= ntiles) return;
+    load(tile);
+    for (; tile < ntiles; tile += gridDim.x) {
+        const size_t plane = tile / (size_t)ntb;
+        const int b0 = (int)(tile - plane * (size_t)ntb) * TB;
+        const size_t base = cols_plane_base(mp, (size_t)mp.p0 + plane, L, B);
+        float2 v[L2];
+        const bool in_a = b0 + ca < B;
+#pragma unroll
+        for (int n2 = 0; n2 < L2; ++n2) v[n2] = in_a ? ldc(&raw[n2]) : make_float2(0.f, 0.f);
+        if (tile + gridDim.x < ntiles) load(tile + gridDim.x);
+        dft_reg<L2, SIGN>(v);
+#pragma unroll
+        for (int k2 = 1; k2 < L2; ++k2) {
+            float2 w = __ldg(tw + n1 * k2);            // n1 k2 < L
+            if (SIGN > 0) w.y = -w.y;
+            v[k2] = cmul(v[k2], w);
+        }
+        __syncthreads();                               // the previous tile's reads are done
+#pragma unroll
+        for (int k2 = 0; k2 < L2; ++k2) zx[(k2 * ZP + n1) * TB + ca] = v[k2];
+        __syncthreads();
+        for (int it = t; it < L2 * TB; it += kTwoThreads) {
+            const int k2 = it / TB, col = it % TB;
+            float2 u[L1];
+#pragma unroll
+            for (int m = 0; m < L1; ++m) u[m] = zx[(k2 * ZP + m) * TB + col];
+            dft_reg<L1, SIGN>(u);
+            const int b = b0 + col;
+            if (b < B) {
+#pragma unroll
+                for (int k1 = 0; k1 < L1; ++k1) {
+                    const int l = k2 + L2 * k1;
+                    if (l >= mp.lo && l <= mp.hi) stc(data + base + (size_t)l * B + b, u[k1]);
+                }
+            }
+        }
+    }
+}
+
+// ---- z lines of F(f) conj(T_k) for all K components, inverse ----------------
+// One tile of TB columns per CTA: the image samples of this thread stay in
+// registers, the next component's samples are loaded while the current
+// product is transformed; z samples lo..hi of every product are stored.
+template <int L1, int L2, typename TS, typename PS>
+__global__ void __launch_bounds__(kTwoThreads, 1) cols_mul2_t(const float2* __restrict__ spec,
+                                                              const TS* __restrict__ tspec,
+                                                              PS* __restrict__ out, int B, int K,
+                                                              const float2* __restrict__ tw,
+                                                              int lo, int hi) {
+    constexpr int L = L1 * L2;
+    constexpr int TB = kTwoThreads / L1;
+    constexpr int ZP = L1 + 1;
+    extern __shared__ float2 zx[];
+    const int t = threadIdx.x;
+    const int n1 = t / TB, ca = t % TB;
+    const int b0 = blockIdx.x * TB;
+    const size_t plane = (size_t)L * B;
+    const bool in_a = b0 + ca < B;
+    float2 fi[L2];
+    TS tr[L2];
+#pragma unroll
+    for (int n2 = 0; n2 < L2; ++n2) {
+        const size_t e = (size_t)(n1 + L1 * n2) * B + b0 + ca;
+        fi[n2] = in_a ? spec[e] : make_float2(0.f, 0.f);
+        if (in_a && K > 0) tr[n2] = tspec[e];
+    }
+    for (int k = 0; k < K; ++k) {
+        float2 v[L2];
+#pragma unroll
+        for (int n2 = 0; n2 < L2; ++n2) v[n2] = in_a ? cmulc(fi[n2], ldc(&tr[n2])) : make_float2(0.f, 0.f);
+        if (in_a && k + 1 < K) {
+            const TS* ts = tspec + (size_t)(k + 1) * plane;
+#pragma unroll
+            for (int n2 = 0; n2 < L2; ++n2) tr[n2] = ts[(size_t)(n1 + L1 * n2) * B + b0 + ca];
+        }
+        dft_reg<L2, +1>(v);
+#pragma unroll
+        for (int k2 = 1; k2 < L2; ++k2) {
+            float2 w = __ldg(tw + n1 * k2);
+            w.y = -w.y;
+            v[k2] = cmul(v[k2], w);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int k2 = 0; k2 < L2; ++k2) zx[(k2 * ZP + n1) * TB + ca] = v[k2];
+        __syncthreads();
+        PS* o = out + (size_t)k * plane;
+        for (int it = t; it < L2 * TB; it += kTwoThreads) {
+            const int k2 = it / TB, col = it % TB;
+            float2 u[L1];
+#pragma unroll
+            for (int m = 0; m < L1; ++m) u[m] = zx[(k2 * ZP + m) * TB + col];
+            dft_reg<L1, +1>(u);
+            const int b = b0 + col;
+            if (b < B) {
+#pragma unroll
+                for (int k1 = 0; k1 < L1; ++k1) {
+                    const int l = k2 + L2 * k1;
+                    if (l >= lo && l <= hi) stc(o + (size_t)l * B + b, u[k1]);
+                }
+            }
+        }
+    }
+}
+
+// ---- half-spectrum rows -> real x lines, two-level ------------------------
+// A tile is NR = 256 / L1 kept rows (z in keep.z0..z1, y in keep.y0..y1 of
+// every batch item, in that order); thread (row, n1) loads its L2 samples of
+// the Hermitian extension X[L - x] = conj X[x] straight from global memory;
+// the next tile's samples are loaded while the current one is transformed.
+// The real parts of the kept samples x0..x1 go to the X x Y x Z maps.
+template <int L1, int L2>
+constexpr size_t two_rows_smem() { return (size_t)(kTwoThreads / L1) * L2 * (L1 + 1) * sizeof(float2); }
+
+template <int L1, int L2, typename PS, typename RT>
+__global__ void __launch_bounds__(kTwoThreads, 1) rows_c2r2_t(const PS* __restrict__ in, int X,
+                                                              int Y, int Z, FftGeom g,
+                                                              RT* __restrict__ out, int n_batch,
+                                                              const float2* __restrict__ tw,
+                                                              FftKeep keep) {
+    constexpr int L = L1 * L2;
+    constexpr int XH = L / 2 + 1;
+    constexpr int NR = kTwoThreads / L1;
+    constexpr int ZP = L1 + 1;
+    extern __shared__ float2 zx[];                    // [row][k2][n1 (padded)]
+    const int t = threadIdx.x;
+    const int ra = t / L1, n1 = t % L1;
+    const int ny = keep.y1 - keep.y0 + 1, nz = keep.z1 - keep.z0 + 1;
+    const size_t nrows = (size_t)n_batch * nz * ny;
+    const size_t ntiles = (nrows + NR - 1) / NR;
+    // row q of the kept rows: its half-spectrum row and its output offset
+    auto row_of = [&](size_t q, size_t& src_row, long long& dst) {
+        const size_t per_item = (size_t)nz * ny;
+        const size_t item = q / per_item;
+        const size_t r = q - item * per_item;
+        const int z = keep.z0 + (int)(r / (size_t)ny);
+        const int y = keep.y0 + (int)(r % (size_t)ny);
+        src_row = (item * (size_t)g.Zp + (size_t)z) * (size_t)g.Yp + (size_t)y;
+        dst = (y < Y && z < Z) ? (long long)(item * ((size_t)X * Y * Z) + ((size_t)z * Y + y) * X)
+                               : -1;
+    };
+    PS raw[L2];
+    auto load = [&](size_t tile) {
+        const size_t q = tile * NR + ra;
+        if (q < nrows) {
+            size_t src;
+            long long dst;
+            row_of(q, src, dst);
+            const PS* rowp = in + src * XH;
+#pragma unroll
+            for (int n2 = 0; n2 < L2; ++n2) {
+                const int n = n1 + L1 * n2;
+                raw[n2] = rowp[n < XH ? n : L - n];
+            }
+        }
+    };
+    size_t tile = blockIdx.x;
+    if (tile >= ntiles) return;
+    load(tile);
+    const int xk0 = keep.x0, xk1 = min(keep.x1, X - 1);
+    for (; tile < ntiles; tile += gridDim.x) {
+        float2 v[L2];
+        const bool in_a = tile * NR + ra < nrows;
+#pragma unroll
+        for (int n2 = 0; n2 < L2; ++n2) {
+            const int n = n1 + L1 * n2;
+            float2 c = in_a ? ldc(&raw[n2]) : make_float2(0.f, 0.f);
+            if (n >= XH) c.y = -c.y;                   // conj X[L - n]
+            v[n2] = c;
+        }
+        if (tile + gridDim.x < ntiles) load(tile + gridDim.x);
+        dft_reg<L2, +1>(v);
+#pragma unroll
+        for (int k2 = 1; k2 < L2; ++k2) {
+            float2 w = __ldg(tw + n1 * k2);
+            w.y = -w.y;
+            v[k2] = cmul(v[k2], w);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int k2 = 0; k2 < L2; ++k2) zx[(ra * L2 + k2) * ZP + n1] = v[k2];
+        __syncthreads();
+        for (int it = t; it < NR * L2; it += kTwoThreads) {
+            const int rb = it / L2, k2 = it % L2;
+            const size_t q = tile * NR + rb;
+            if (q >= nrows) continue;
+            size_t src;
+            long long dst;
+            row_of(q, src, dst);
+            float2 u[L1];
+#pragma unroll
+            for (int m = 0; m < L1; ++m) u[m] = zx[(rb * L2 + k2) * ZP + m];
+            dft_reg<L1, +1>(u);
+            if (dst >= 0) {
+#pragma unroll
+                for (int k1 = 0; k1 < L1; ++k1) {
+                    const int x = k2 + L2 * k1;
+                    if (x >= xk0 && x <= xk1) str(out + dst + x, u[k1].x);
+                }
+            }
+        }
+    }
+}
+
+}  // namespace fftk
+}  // namespace ttm
