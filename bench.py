@@ -83,7 +83,7 @@ def load_workload(name: str, **extra):
 FP32_ALU_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # SMs x FP32 lanes x FMA x max clock
 # the refinement's defaults (candidates taking two power steps, the best
 # points reached taking Newton steps, Newton steps): by tensor order
-REFINE_BUDGET = {6: (4, 2, 2)}
+REFINE_BUDGET = {6: (2, 2, 2)}
 DEFAULT_BUDGET = (8, 4, 3)
 
 
@@ -743,67 +743,52 @@ def run_ours(args) -> None:
     t_max = max_over_ranks(total_ms, dist, dev)
     value = job_rate(nvox, args.steps, world, t_max)
 
-    # end to end through the public API: pinned host volume in, maps out.
-    # With depth > 1 consecutive steps run on HostPipeline's streams, so step
-    # k's maps travel to the host while step k+1 is copied in and matched
-    # (every step still moves its own input and result); depth 1 repeats
-    # Matcher.match_host step after step.
+    # end to end through the public API: pinned host volume in, maps out,
+    # every step.  HostStream keeps one plan and double-buffers the volume and
+    # the maps, so step k's maps travel to the host and step k+1's volume
+    # comes in while step k+1 is matched (depth 1: one step at a time).
     e2e = None
     if not args.no_e2e:
-        depth = args.e2e_depth if args.e2e_depth > 0 else (1 if args.workload == "c5" else 2)
+        depth = args.e2e_depth if args.e2e_depth > 0 else 2
         pin_in = torch.from_numpy(wl.volume).pin_memory()
 
         def pinned_maps():
             return [(torch.empty((Z, Y, X), dtype=torch.float32).pin_memory(),
                      torch.empty((Z, Y, X, 4), dtype=torch.float32).pin_memory(),
                      torch.empty((Z, Y, X), dtype=torch.float32).pin_memory())]
-        if depth == 1:
-            pin_out = pinned_maps()
-            for _ in range(max(1, args.warmup)):
-                matcher.match_host([None], pinned_in=[pin_in], pinned_out=pin_out)
-            torch.cuda.synchronize()
-            if dist:
-                dist.barrier()
-            e_ms = 0.0
-            for k in range(args.steps):
-                flush.zero_()
-                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                a.record(stream)
-                matcher.match_host([None], pinned_in=[pin_in], pinned_out=pin_out)
-                b.record(stream)
-                b.synchronize()
-                e_ms += a.elapsed_time(b)
-        else:
-            pipe = ttm.HostPipeline([(comp, desc, wl.mask)], [((X, Y, Z), 0)], opts=opts,
-                                    depth=depth)
-            outs = [pinned_maps() for _ in range(depth)]
-            for k in range(max(args.warmup, depth)):
-                pipe.submit([pin_in], outs[k % depth])
-            pipe.join()
-            torch.cuda.synchronize()
-            if dist:
-                dist.barrier()
-            flush.zero_()
-            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            a.record(stream)
-            for k in range(args.steps):
-                pipe.submit([pin_in], outs[k % depth])
-            pipe.join()
-            b.record(stream)
-            b.synchronize()
-            e_ms = a.elapsed_time(b)
-            for m_ in pipe.matchers:
-                st_ = ttm.ttm_plan_device_status(m_.plan, m_.ws)
-                if st_ != 0:
-                    raise RuntimeError(f"device status {ttm.ttm_status_string(st_)}")
-            pipe.close()
-            del outs
+        matcher.close()
+        del matcher
+        torch.cuda.empty_cache()
+        hs = ttm.HostStream([(comp, desc, wl.mask)], [((X, Y, Z), 0)], opts=opts, depth=depth)
+        outs = [pinned_maps() for _ in range(depth)]
+        for k in range(max(args.warmup, depth)):
+            hs.submit([pin_in], outs[k % depth])
+        hs.join()
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for k in range(args.steps):
+            hs.submit([pin_in], outs[k % depth])
+        hs.join()
+        b.record(stream)
+        b.synchronize()
+        e_ms = a.elapsed_time(b)
+        st_ = ttm.ttm_plan_device_status(hs.matcher.plan, hs.matcher.ws)
+        if st_ != 0:
+            raise RuntimeError(f"device status {ttm.ttm_status_string(st_)}")
+        matcher = hs.matcher          # the plan stays in use for the rest of the run
+        hs.outs, hs.vols = None, None
+        del outs
+        torch.cuda.empty_cache()
         e_ms = max_over_ranks(e_ms, dist, dev)
         e2e = dict(value=job_rate(nvox, args.steps, world, e_ms), unit=UNIT,
                    h2d_bytes_per_step=nvox * 4, d2h_bytes_per_step=nvox * 4 * 6,
                    pipeline_depth=depth,
-                   note="pinned host volume in, score + quaternion + lambda maps out, every step"
-                        + ("; consecutive steps overlap on HostPipeline streams" if depth > 1 else ""))
+                   note="pinned host volume in, score + quaternion + lambda maps out, every step; "
+                        "one plan, volume and maps double-buffered (HostStream)")
 
     # classical template matching (Algorithm 1) at 1000 rotations on the same
     # volume and GPU: the comparator of the paper's speed-up claim

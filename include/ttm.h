@@ -114,7 +114,7 @@ typedef struct ttm_plan_opts {
                         /* 1024 at order 6 with TTM_PREC_MIXED), <= 65535     */
     int n_cells;        /* regions of the grid; 0 = default (n_grid / 16);    */
                         /* must divide n_grid                                  */
-    int n_candidates;   /* regions polished per voxel; 0 = default (8, or 4 at */
+    int n_candidates;   /* regions polished per voxel; 0 = default (8, or 2 at */
                         /* order 6)                                            */
     int newton_steps;   /* Newton steps per refined point; 0 = default (3, or  */
                         /* 2 at order 6)                                       */

@@ -51,4 +51,4 @@ from ._binding import (  # noqa: F401
     ttm_plan_workspace_size,
     ttm_status_string,
 )
-from .engine import HostPipeline, Matcher, build_template  # noqa: F401
+from .engine import HostPipeline, HostStream, Matcher, build_template  # noqa: F401

@@ -521,7 +521,7 @@ ttm_status launch_spectra_to_bf16(const float2* a, void* b, size_t n, cudaStream
 
 
 // w from the FFT-based window sums of (f - mean) and (f - mean)^2 (Algorithm 1):
-// V = S2 - S1^2 / m_sum in FP64; interior only; floor 1e-6 m_sum var(f).
+// V = S2 - S1^2 / m_sum; interior only; floor 1e-6 m_sum var(f).
 //
 // The FP32 FFT window sums carry a rounding error set by the whole volume,
 // not by the window: |dS| <= kappa eps m_sum rms(a) for a = f - mean (S1) and
@@ -532,7 +532,9 @@ ttm_status launch_spectra_to_bf16(const float2* a, void* b, size_t n, cudaStream
 // (launch_exact_stats).  Large offsets never flag (the mean is removed); a
 // quiet window in a volume of large dynamic range does.
 // Persistent CTAs over x-segments of 128 voxels: the volume statistics and
-// the bounds (FP64 divisions, slow on this GPU) are formed once per CTA.
+// the bounds (FP64 divisions, slow on this GPU) are formed once per CTA; per
+// voxel V and its bound are FP32 (a window that needs more than that is
+// flagged and recomputed in FP64).
 __global__ void __launch_bounds__(128) stats_from_sums_kernel(
     const float* __restrict__ s1, const float* __restrict__ s2, float* __restrict__ w, int X,
     int Y, int Z, int s, double mask_sum, const double* __restrict__ moments, double kappa,
@@ -549,7 +551,7 @@ __global__ void __launch_bounds__(128) stats_from_sums_kernel(
         sh[3] = kappa * eps * mask_sum * sqrt(fmax(moments[2], 0.0) / nv);   // on |dS2|
     }
     __syncthreads();
-    const double inv_m = sh[0], floor_v = sh[1], e1 = sh[2], e2 = sh[3];
+    const float fim = (float)sh[0], ffl = (float)sh[1], fe1 = (float)sh[2], fe2 = (float)sh[3];
     const uint32_t xt = (uint32_t)((X + 127) / 128);
     const uint32_t segs = xt * (uint32_t)Y * (uint32_t)Z;
     unsigned int nflag = 0;
@@ -561,14 +563,17 @@ __global__ void __launch_bounds__(128) stats_from_sums_kernel(
         const size_t v = ((size_t)z * Y + y) * X + x;
         float out = 0.f;
         if (interior(x, X, s) && interior(y, Y, s) && interior(z, Z, s)) {
-            const double S1 = s1[v], S2 = s2[v];
-            const double V = fma(-S1, S1 * inv_m, S2);
-            const double dv = e2 + (2.0 * fabs(S1) * e1 + e1 * e1) * inv_m;
-            if (dv > 2e-5 * V || fabs(V - floor_v) <= dv) {
+            // V in FP32; its own rounding (eps (S2 + S1^2/m)) joins the bound
+            const float S1 = s1[v], S2 = s2[v];
+            const float q = S1 * S1 * fim;
+            const float V = S2 - q;
+            const float dv = fe2 + (2.f * fabsf(S1) * fe1 + fe1 * fe1) * fim +
+                             1.2e-7f * (fabsf(S2) + q);
+            if (dv > 2e-5f * V || fabsf(V - ffl) <= dv) {
                 out = -1.f;
                 ++nflag;
-            } else if (V > floor_v) {
-                out = rsqrtf((float)V);
+            } else if (V > ffl) {
+                out = rsqrtf(V);
             }
         }
         w[v] = out;

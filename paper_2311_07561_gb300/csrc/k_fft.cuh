@@ -126,9 +126,10 @@ __device__ __forceinline__ void dft_small(float2 (&v)[R]) {
             dft4<SIGN>(a, b, c, d);
             u[n2 + 0] = a; u[n2 + 2] = b; u[n2 + 4] = c; u[n2 + 6] = d;   // u[n2 + 2 k1]
         }
-        // twiddle W8^(n2 k1) = W16^(2 n2 k1)
+        // twiddle W8^(n2 k1) = W16^(2 n2 k1) (k1 = 2: -i, a swap)
 #pragma unroll
-        for (int k1 = 0; k1 < 4; ++k1) u[1 + 2 * k1] = cmul(u[1 + 2 * k1], w16<SIGN>(2 * k1));
+        for (int k1 = 1; k1 < 4; ++k1)
+            u[1 + 2 * k1] = k1 == 2 ? mul_mi<SIGN>(u[1 + 2 * k1]) : cmul(u[1 + 2 * k1], w16<SIGN>(2 * k1));
 #pragma unroll
         for (int k1 = 0; k1 < 4; ++k1) {
             float2 a = u[2 * k1], b = u[2 * k1 + 1];
@@ -171,7 +172,9 @@ __device__ __forceinline__ void dft_small(float2 (&v)[R]) {
 #pragma unroll
         for (int k1 = 1; k1 < 4; ++k1)
 #pragma unroll
-            for (int n2 = 1; n2 < 4; ++n2) u[4 * k1 + n2] = cmul(u[4 * k1 + n2], w16<SIGN>(n2 * k1));
+            for (int n2 = 1; n2 < 4; ++n2)   // W16^4 = -i: a swap
+                u[4 * k1 + n2] = n2 * k1 == 4 ? mul_mi<SIGN>(u[4 * k1 + n2])
+                                              : cmul(u[4 * k1 + n2], w16<SIGN>(n2 * k1));
 #pragma unroll
         for (int k1 = 0; k1 < 4; ++k1) {
             float2 a = u[4 * k1], b = u[4 * k1 + 1], c = u[4 * k1 + 2], d = u[4 * k1 + 3];

@@ -69,6 +69,18 @@ __device__ __forceinline__ float2 tw_const(int m) {
     return make_float2(T.c[r], SIGN < 0 ? -T.s[r] : T.s[r]);
 }
 
+// a * exp(SIGN 2 pi i m / N) for a compile-time m: the multiplications by
+// +-1 and +-i are swaps and sign changes
+template <int N, int SIGN>
+__device__ __forceinline__ float2 mul_tw(float2 a, int m) {
+    const int r = ((m % N) + N) % N;
+    if (r == 0) return a;
+    if (2 * r == N) return make_float2(-a.x, -a.y);
+    if (4 * r == N) return mul_mi<SIGN>(a);
+    if (4 * r == 3 * N) return mul_mi<-SIGN>(a);
+    return cmul(a, tw_const<N, SIGN>(r));
+}
+
 // ---- register DFTs of compile-time length ---------------------------------
 __host__ __device__ constexpr bool base_radix(int n) {
     return n == 2 || n == 3 || n == 4 || n == 5 || n == 8 || n == 16;
@@ -96,7 +108,7 @@ __device__ __forceinline__ void dft_split(float2 (&v)[N]) {
         dft_reg<P, SIGN>(a);
 #pragma unroll
         for (int k1 = 0; k1 < P; ++k1)
-            t[k1 * Q + q] = (q == 0 || k1 == 0) ? a[k1] : cmul(a[k1], tw_const<N, SIGN>(q * k1));
+            t[k1 * Q + q] = mul_tw<N, SIGN>(a[k1], q * k1);
     }
 #pragma unroll
     for (int k1 = 0; k1 < P; ++k1) {
@@ -121,12 +133,23 @@ __device__ __forceinline__ void dft_reg(float2 (&v)[N]) {
 }
 
 // ---- line lengths that take the two-level passes ---------------------------
-// L = L1 L2 with L1 threads per line in the first step: 960 = 32 x 30 and
-// 480 = 16 x 30 (the padded boxes of the 928 x 928 x 464 configuration)
+// L = L1 L2 with L1 threads per line in the first step (16 up to 480, 32
+// from 512): every compiled length from 128 up
 template <int L> struct TwoLevel { static constexpr int L1 = 0, L2 = 0; };
-template <> struct TwoLevel<960> { static constexpr int L1 = 32, L2 = 30; };
-template <> struct TwoLevel<480> { static constexpr int L1 = 16, L2 = 30; };
-template <int L> constexpr bool two_level() { return TwoLevel<L>::L1 > 0; }
+#define TTM_TWO_LEVEL(L_, L1_) \
+    template <> struct TwoLevel<L_> { static constexpr int L1 = L1_, L2 = L_ / L1_; };
+TTM_TWO_LEVEL(128, 16) TTM_TWO_LEVEL(144, 16) TTM_TWO_LEVEL(160, 16) TTM_TWO_LEVEL(192, 16)
+TTM_TWO_LEVEL(240, 16) TTM_TWO_LEVEL(256, 16) TTM_TWO_LEVEL(288, 16) TTM_TWO_LEVEL(320, 16)
+TTM_TWO_LEVEL(384, 16) TTM_TWO_LEVEL(480, 16) TTM_TWO_LEVEL(512, 32) TTM_TWO_LEVEL(576, 32)
+TTM_TWO_LEVEL(640, 32) TTM_TWO_LEVEL(768, 32) TTM_TWO_LEVEL(960, 32) TTM_TWO_LEVEL(1024, 32)
+#undef TTM_TWO_LEVEL
+// taken where the Stockham form needs three or more shared-memory stages
+// (at 128 and 256 its two radix-16 stages measured as fast or faster)
+template <int L> constexpr bool two_level() { return TwoLevel<L>::L1 > 0 && n_stages(L) >= 3; }
+
+// resident CTAs per SM the register budget is sized for: two for lines whose
+// second factor is at most 16 (their register DFTs are small), else one
+template <int L2> constexpr int two_min_blocks() { return L2 <= 16 ? 2 : 1; }
 
 constexpr int kTwoThreads = 256;
 
@@ -139,7 +162,7 @@ constexpr size_t two_cols_smem() { return (size_t)L2 * (L1 + 1) * (kTwoThreads /
 // CTAs, the raw samples of the next tile are loaded into registers while the
 // current one is transformed.  Line samples lo..hi are stored.
 template <int L1, int L2, int SIGN, typename PS>
-__global__ void __launch_bounds__(kTwoThreads, 1) cols2_t(PS* __restrict__ data, int B,
+__global__ void __launch_bounds__(kTwoThreads, two_min_blocks<L2>()) cols2_t(PS* __restrict__ data, int B,
                                                           const float2* __restrict__ tw,
                                                           ColsMap mp, int ntb, size_t ntiles) {
     constexpr int L = L1 * L2;
@@ -204,7 +227,7 @@ __global__ void __launch_bounds__(kTwoThreads, 1) cols2_t(PS* __restrict__ data,
 // registers, the next component's samples are loaded while the current
 // product is transformed; z samples lo..hi of every product are stored.
 template <int L1, int L2, typename TS, typename PS>
-__global__ void __launch_bounds__(kTwoThreads, 1) cols_mul2_t(const float2* __restrict__ spec,
+__global__ void __launch_bounds__(kTwoThreads, two_min_blocks<L2>()) cols_mul2_t(const float2* __restrict__ spec,
                                                               const TS* __restrict__ tspec,
                                                               PS* __restrict__ out, int B, int K,
                                                               const float2* __restrict__ tw,
@@ -275,7 +298,7 @@ template <int L1, int L2>
 constexpr size_t two_rows_smem() { return (size_t)(kTwoThreads / L1) * L2 * (L1 + 1) * sizeof(float2); }
 
 template <int L1, int L2, typename PS, typename RT>
-__global__ void __launch_bounds__(kTwoThreads, 1) rows_c2r2_t(const PS* __restrict__ in, int X,
+__global__ void __launch_bounds__(kTwoThreads, two_min_blocks<L2>()) rows_c2r2_t(const PS* __restrict__ in, int X,
                                                               int Y, int Z, FftGeom g,
                                                               RT* __restrict__ out, int n_batch,
                                                               const float2* __restrict__ tw,

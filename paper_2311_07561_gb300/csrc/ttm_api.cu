@@ -101,10 +101,11 @@ ttm_status build_grid(ttm_plan_s* P) {
     // refinement budget: at order 6 the maxima of phi are sharper and the
     // grid search lands closer; an FP64 model of the search and refinement
     // (the unit tests' model, on 400 voxels of the 928 x 928 x 464 workload's
-    // template) gives the same largest lambda shortfall (4.2e-5, a grid miss)
-    // with 4 candidates x 2 refined x 2 Newton steps as with 8 x 4 x 3
+    // template) gives the same largest lambda shortfall (4.2e-5 with 2048
+    // grid points, 6.2e-5 with 1024: grid misses) with 2 candidates x 2
+    // refined x 2 Newton steps as with 8 x 4 x 3
     const bool o6 = P->n_order == 6;
-    const int cand = P->opts.n_candidates > 0 ? P->opts.n_candidates : (o6 ? 4 : 8);
+    const int cand = P->opts.n_candidates > 0 ? P->opts.n_candidates : (o6 ? 2 : 8);
     const int newton = P->opts.newton_steps > 0 ? P->opts.newton_steps : (o6 ? 2 : 3);
     const int refine = P->opts.n_refined > 0 ? P->opts.n_refined : (o6 ? 2 : 4);
     if (n > 65535 || nc > n || n % nc != 0 || cand > 8 || newton > 64 || refine > 4)

@@ -87,12 +87,30 @@ class Matcher:
                 if tuple(c.shape) != (self.descs[k].K, Z, Y, X) or not c.is_contiguous():
                     raise ValueError(f"components_out[{p}] must be (K, Z, Y, X) contiguous")
 
-    def run(self, vols: Sequence, components_out: Optional[Sequence] = None, stream=None) -> None:
-        """Local statistics, correlation, score and rotation for every problem."""
+    def new_outputs(self):
+        """A second set of output maps (w, score, quat, lambda lists, one per
+        problem) for run(outputs=...)."""
+        torch = _torch()
+        dev = torch.device("cuda")
+        w, score, quat, lam = [], [], [], []
+        for (X, Y, Z), _ in self.problems:
+            shape = (Z, Y, X)
+            w.append(torch.empty(shape, dtype=torch.float32, device=dev))
+            score.append(torch.empty(shape, dtype=torch.float32, device=dev))
+            quat.append(torch.empty(shape + (4,), dtype=torch.float32, device=dev))
+            lam.append(torch.empty(shape, dtype=torch.float32, device=dev) if self.want_lambda else None)
+        return w, score, quat, lam
+
+    def run(self, vols: Sequence, components_out: Optional[Sequence] = None, stream=None,
+            outputs=None) -> None:
+        """Local statistics, correlation, score and rotation for every problem;
+        into the matcher's own maps, or into `outputs` (from new_outputs)."""
         self._check_inputs(vols, components_out)
-        B.ttm_local_stats(self.plan, vols, self.w, self.ws, stream)
-        B.ttm_correlate(self.plan, vols, self.w, self.score, self.quat,
-                        self.lam if self.want_lambda else None, components_out, self.ws, stream)
+        w, score, quat, lam = outputs if outputs is not None else (self.w, self.score, self.quat,
+                                                                    self.lam)
+        B.ttm_local_stats(self.plan, vols, w, self.ws, stream)
+        B.ttm_correlate(self.plan, vols, w, score, quat, lam if self.want_lambda else None,
+                        components_out, self.ws, stream)
 
     def capture(self, vols: Sequence):
         """Record run(vols) for every problem of the plan into one CUDA graph.
@@ -224,3 +242,85 @@ class HostPipeline:
     def close(self) -> None:
         for m in self.matchers:
             m.close()
+
+
+class HostStream:
+    """End-to-end matching of a stream of host volumes with one plan.
+
+    Where two plans do not fit (large volumes: the template spectra and the K
+    correlation maps dominate the memory), one plan serves every step and only
+    the inputs and outputs are double-buffered: the volume of step k+1 is
+    copied in on a copy stream while step k is matched on the compute stream,
+    and the maps of step k travel to the host on another copy stream while
+    step k+1 is matched.  Every step still copies its own volume in from
+    pinned host memory and its score, rotation and lambda maps out.  Memory
+    beyond one Matcher: ``depth - 1`` more volumes and output sets.
+
+    templates, problems, opts: as for :class:`Matcher`.
+    """
+
+    def __init__(self, templates, problems, opts=None, depth: int = 2):
+        torch = _torch()
+        if depth < 1:
+            raise ValueError("depth must be at least 1")
+        self.matcher = Matcher(templates, problems, opts=opts)
+        dev = torch.device("cuda")
+        m = self.matcher
+        self.outs = [(m.w, m.score, m.quat, m.lam)] + [m.new_outputs() for _ in range(depth - 1)]
+        self.vols = [[torch.empty((Z, Y, X), dtype=torch.float32, device=dev)
+                      for (X, Y, Z), _ in m.problems] for _ in range(depth)]
+        self.compute = torch.cuda.Stream()
+        self.h2d = torch.cuda.Stream()
+        self.d2h = torch.cuda.Stream()
+        # per slot: inputs copied in, step computed, outputs copied out
+        self.ev_in = [torch.cuda.Event() for _ in range(depth)]
+        self.ev_done = [torch.cuda.Event() for _ in range(depth)]
+        self.ev_out = [torch.cuda.Event() for _ in range(depth)]
+        self.used = [False] * depth
+        self.depth = depth
+        self._next = 0
+
+    def submit(self, host_vols: Sequence, host_out: Sequence) -> None:
+        """Queue one step: host_vols[p] (pinned float32 (Z, Y, X)) in, and
+        (score, quat, lambda) of every problem out into host_out[p] (pinned
+        tensors of the map shapes).  Returns at once; the step is ordered after
+        everything queued on the current stream before the call."""
+        torch = _torch()
+        i = self._next % self.depth
+        self._next += 1
+        cur = torch.cuda.current_stream()
+        for st in (self.h2d, self.compute, self.d2h):
+            st.wait_stream(cur)
+        with torch.cuda.stream(self.h2d):
+            if self.used[i]:
+                self.h2d.wait_event(self.ev_done[i])      # the slot's volume is free
+            for d, h in zip(self.vols[i], host_vols):
+                d.copy_(h, non_blocking=True)
+            self.ev_in[i].record(self.h2d)
+        with torch.cuda.stream(self.compute):
+            self.compute.wait_event(self.ev_in[i])
+            if self.used[i]:
+                self.compute.wait_event(self.ev_out[i])   # the slot's maps are on the host
+            self.matcher.run(self.vols[i], stream=self.compute, outputs=self.outs[i])
+            self.ev_done[i].record(self.compute)
+        with torch.cuda.stream(self.d2h):
+            self.d2h.wait_event(self.ev_done[i])
+            _, score, quat, lam = self.outs[i]
+            for p, (so, qo, lo) in enumerate(host_out):
+                so.copy_(score[p], non_blocking=True)
+                qo.copy_(quat[p], non_blocking=True)
+                if lo is not None and lam[p] is not None:
+                    lo.copy_(lam[p], non_blocking=True)
+            self.ev_out[i].record(self.d2h)
+        self.used[i] = True
+
+    def join(self) -> None:
+        """Make the current stream wait for every queued step."""
+        torch = _torch()
+        cur = torch.cuda.current_stream()
+        for st in (self.h2d, self.compute, self.d2h):
+            cur.wait_stream(st)
+
+    def close(self) -> None:
+        self.matcher.close()
+

@@ -532,6 +532,20 @@ def test_host_pipeline_matches_matcher(ttm):
         s, q, l = outs[k][0]
         assert torch.equal(s, ref[v][0]) and torch.equal(q, ref[v][1]) and torch.equal(l, ref[v][2])
     pipe.close()
+    # one plan, double-buffered volumes and maps: the same maps, step after
+    # step, with three volumes cycling through two slots
+    order = [0, 1, 1, 0, 1]
+    stream = ttm.HostStream([(comp, desc, wls[0].mask)], prob, opts=_opts(ttm, "fft"), depth=2)
+    outs = [[(torch.empty((40, 44, 48)).pin_memory(), torch.empty((40, 44, 48, 4)).pin_memory(),
+              torch.empty((40, 44, 48)).pin_memory())] for _ in order]
+    for k, v in enumerate(order):
+        stream.submit([pins[v]], outs[k])
+    stream.join()
+    torch.cuda.synchronize()
+    for k, v in enumerate(order):
+        s, q, l = outs[k][0]
+        assert torch.equal(s, ref[v][0]) and torch.equal(q, ref[v][1]) and torch.equal(l, ref[v][2])
+    stream.close()
 
 
 @pytest.mark.parametrize("path", PATHS)

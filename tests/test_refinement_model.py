@@ -1,8 +1,8 @@
 """An FP64 model of the GPU's rotation search and refinement, run beside the
 oracle on CPU: it fixes how many refined points and Newton steps the dense
 rotation maps need (the refinement budget of the CUDA path: 8 candidates, the
-4 best points x 3 Newton steps at orders 2, 4 and 8; 4 candidates, the 2 best
-x 2 Newton steps at order 6).
+4 best points x 3 Newton steps at orders 2, 4 and 8; 2 candidates, both
+refined by 2 Newton steps at order 6).
 
 The model takes the same steps as the kernels: phi at the 2048 half-sphere
 grid points (a super-Fibonacci-style spiral sorted into 128 regions of 16 by
@@ -135,7 +135,7 @@ def test_refinement_budget_order_six():
     pts = np.concatenate([wl.positions, rng.integers(7, 64 - 15 + 7 + 1, size=(36, 3))])
     _, C = o.components_at(wl.volume, T, wl.mask, pts)
     lam_o, _ = o.dominant_z_eigenpair(C, 6)
-    # the order-6 default: 4 candidates, the 2 best refined by 2 Newton steps
-    lam = model_lambda(C, 6, refined=2, newton=2, n_cand=4)
+    # the order-6 default: 2 candidates, both refined by 2 Newton steps
+    lam = model_lambda(C, 6, refined=2, newton=2, n_cand=2)
     assert (lam_o - lam).max() <= 2e-5
     assert (lam - lam_o).max() <= 1e-9
