@@ -64,6 +64,14 @@ struct PolishArgs {
     int n_cand, newton, n_refine;
 };
 
+// The score sum_alpha mu_alpha C_alpha^2 is accumulated in two halves, the
+// components below score_split<N>() and the rest, added at the end: the
+// tensor-core search loads the two halves of a voxel's components in two
+// threads, and every kernel that writes a score map sums in this same order,
+// so the maps agree bit for bit.
+template <int N>
+__host__ __device__ constexpr int score_split() { return ((n_comp(N) + 1 + 15) / 16) * 8; }
+
 // end of the units [.., u1) and the voxel of unit i, with an optional list
 static __device__ __forceinline__ uint32_t list_end(const UnitList& l, uint32_t u1) {
     if (!l.count) return u1;
@@ -89,16 +97,17 @@ __global__ void __launch_bounds__(128) score_only_kernel(const CT* __restrict__ 
     const size_t v = ((size_t)z * Y + y) * X + x;
     const bool in = (uint32_t)(x - box.x0) < box.nx && (uint32_t)(y - box.y0) < box.ny &&
                     (uint32_t)(z - box.z0) < box.nz;
-    float ss = 0.f;
+    float ss0 = 0.f, ss1 = 0.f;
     if (in) {
         const float wv = __ldg(w + v);
 #pragma unroll
         for (int k = 0; k < K; ++k) {
             const float c = wv * ldcorr(corr + (size_t)k * nvox + v);
-            ss = fmaf((float)S.mu[k], c * c, ss);
+            if (k < score_split<N>()) ss0 = fmaf((float)S.mu[k], c * c, ss0);
+            else ss1 = fmaf((float)S.mu[k], c * c, ss1);
         }
     }
-    score[v] = sqrtf(ss);
+    score[v] = sqrtf(ss0 + ss1);
 }
 
 // keep the kMaxCand largest (value, index) pairs, sorted descending
@@ -360,14 +369,15 @@ __global__ void __launch_bounds__(kRotThreads) search_simt_kernel(SearchArgs a) 
     float C[K4];
 #pragma unroll
     for (int k = 0; k < K4; ++k) C[k] = 0.f;
-    float ss = 0.f;
+    float ss0 = 0.f, ss1 = 0.f;
 #pragma unroll
     for (int k = 0; k < K; ++k) {
         float c = in_range ? wv * ldcorr(corr + (size_t)k * a.nvox + v) : 0.f;
         C[k] = c;
-        ss = fmaf((float)S.mu[k], c * c, ss);
+        if (k < score_split<N>()) ss0 = fmaf((float)S.mu[k], c * c, ss0);
+        else ss1 = fmaf((float)S.mu[k], c * c, ss1);
     }
-    const float score = sqrtf(ss);
+    const float score = sqrtf(ss0 + ss1);
     const bool active = in_range && score > 0.f;
 
     float tv[kMaxCand];

@@ -226,6 +226,60 @@ __device__ __forceinline__ void region_max32(const uint32_t (&r)[32], int low0, 
     n1 = nk[1];
 }
 
+// Half G (0 or 1) of the KP columns of a voxel's A row: columns
+// G KP/2 .. (G+1) KP/2 - 1 of [w Corr_0 .. w Corr_{K-1}, 1, 0 ...].  Loads
+// them into C (all loads issued before any is used) and returns the half of
+// sum mu_k C_k^2 they carry.
+template <int N, int G, int KP, typename CT>
+__device__ __forceinline__ float a_half_load(const CT* __restrict__ corr, size_t nvox, size_t v,
+                                             bool in_range, float wv, float (&C)[KP / 2]) {
+    constexpr int K = n_comp(N);
+    constexpr int KH = KP / 2;
+    constexpr Sym<N> S{};
+#pragma unroll
+    for (int j = 0; j < KH; ++j) {
+        constexpr int k0 = G * KH;
+        C[j] = (in_range && k0 + j < K) ? rot::ldcorr(corr + (size_t)(k0 + j) * nvox + v) : 0.f;
+    }
+    float ss = 0.f;
+#pragma unroll
+    for (int j = 0; j < KH; ++j) {
+        constexpr int k0 = G * KH;
+        if (k0 + j < K) {
+            C[j] *= wv;
+            ss = fmaf((float)S.mu[k0 + j], C[j] * C[j], ss);
+        }
+    }
+    return ss;
+}
+
+// The FP16 columns of half G of the row, normalised by 1/score, into the
+// K-major core-matrix layout of A (column K is the constant 1 that adds +1
+// to every phi, see below)
+template <int N, int G, int KP>
+__device__ __forceinline__ void a_half_store(const float (&C)[KP / 2], float inv,
+                                             unsigned char* As, int lane_t) {
+    constexpr int K = n_comp(N);
+    constexpr int KH = KP / 2;
+#pragma unroll
+    for (int kc = 0; kc < KH / 8; ++kc) {
+        __half h[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+            const int j = kc * 8 + e;
+            const int k = G * KH + j;
+            h[e] = __float2half_rn(k < K ? C[j] * inv : (k == K ? 1.f : 0.f));
+        }
+        uint4 pk;
+        pk.x = (uint32_t)__half_as_ushort(h[0]) | ((uint32_t)__half_as_ushort(h[1]) << 16);
+        pk.y = (uint32_t)__half_as_ushort(h[2]) | ((uint32_t)__half_as_ushort(h[3]) << 16);
+        pk.z = (uint32_t)__half_as_ushort(h[4]) | ((uint32_t)__half_as_ushort(h[5]) << 16);
+        pk.w = (uint32_t)__half_as_ushort(h[6]) | ((uint32_t)__half_as_ushort(h[7]) << 16);
+        const int kcg = G * (KH / 8) + kc;
+        *reinterpret_cast<uint4*>(As + ((kcg * 16 + (lane_t >> 3)) * 8 + (lane_t & 7)) * 16) = pk;
+    }
+}
+
 template <typename CT, int N, int G>
 __global__ void __launch_bounds__(kThreads, 1) search_tc_kernel(rot::SearchArgs a,
                                                                 const uint4* __restrict__ gtab,
@@ -329,35 +383,31 @@ __global__ void __launch_bounds__(kThreads, 1) search_tc_kernel(rot::SearchArgs 
         const size_t i = a.u0 + tile * 128 + lane_t;
         const bool in_range = i < uend;
         const size_t v = in_range ? rot::unit_voxel(a.box, a.list, (uint32_t)i) : 0;
-        // components, score, normalised FP16 row of A (threads 0..127)
+        // components, score, normalised FP16 row of A: threads t and t + 128
+        // share voxel t of the tile, each loading and writing half of the KP
+        // columns (all its loads in flight at once); the two halves of the
+        // sum of squares meet in the merge buffer (free until the tile's end)
         float score = 0.f;
-        if (grp == 0) {
-            float C[K];
+        {
+            constexpr int KH = KP / 2;
+            float C[KH];
             const float wv = in_range ? __ldg(a.w + v) : 0.f;
-            float ss = 0.f;
-#pragma unroll
-            for (int k = 0; k < K; ++k) {
-                C[k] = in_range ? wv * rot::ldcorr(reinterpret_cast<const CT*>(a.corr) + (size_t)k * a.nvox + v) : 0.f;
-                ss = fmaf((float)S.mu[k], C[k] * C[k], ss);
-            }
-            score = sqrtf(ss);
-            const float inv = score > 0.f ? 1.f / score : 0.f;
-#pragma unroll
-            for (int kc = 0; kc < Sh::KC; ++kc) {
-                __half h[8];
-#pragma unroll
-                for (int e = 0; e < 8; ++e) {
-                    const int k = kc * 8 + e;
-                    // column K is the constant 1 that adds +1 to every phi (see below)
-                    h[e] = __float2half_rn(k < K ? C[k] * inv : (k == K ? 1.f : 0.f));
-                }
-                uint4 pk;
-                pk.x = (uint32_t)__half_as_ushort(h[0]) | ((uint32_t)__half_as_ushort(h[1]) << 16);
-                pk.y = (uint32_t)__half_as_ushort(h[2]) | ((uint32_t)__half_as_ushort(h[3]) << 16);
-                pk.z = (uint32_t)__half_as_ushort(h[4]) | ((uint32_t)__half_as_ushort(h[5]) << 16);
-                pk.w = (uint32_t)__half_as_ushort(h[6]) | ((uint32_t)__half_as_ushort(h[7]) << 16);
-                *reinterpret_cast<uint4*>(As + ((kc * 16 + (lane_t >> 3)) * 8 + (lane_t & 7)) * 16) = pk;
-            }
+            const CT* corr = reinterpret_cast<const CT*>(a.corr);
+            const float part = grp == 0 ? a_half_load<N, 0, KP>(corr, a.nvox, v, in_range, wv, C)
+                                        : a_half_load<N, 1, KP>(corr, a.nvox, v, in_range, wv, C);
+            float* ssx = reinterpret_cast<float*>(merge);
+            if (grp == 1) ssx[lane_t] = part;
+            __syncthreads();
+            // the two halves in the order of rot::score_split (KP / 2 == the split)
+            static_assert(KH == rot::score_split<N>(), "score halves");
+            const float ss = grp == 0 ? part + ssx[lane_t] : 0.f;
+            score = sqrtf(ss);                      // group 0 keeps the score
+            if (grp == 0) ssx[128 + lane_t] = score;
+            __syncthreads();
+            const float sc = grp == 0 ? score : ssx[128 + lane_t];
+            const float inv = sc > 0.f ? 1.f / sc : 0.f;
+            if (grp == 0) a_half_store<N, 0, KP>(C, inv, As, lane_t);
+            else a_half_store<N, 1, KP>(C, inv, As, lane_t);
         }
         asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
         asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");

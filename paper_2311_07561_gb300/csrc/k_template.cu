@@ -132,7 +132,8 @@ __global__ void __launch_bounds__(kFoldThreads) fold_kernel(
     int nj, const float* __restrict__ rot, int s3, float* __restrict__ comp, int a0, int na,
     int first) {
     constexpr Sym<N> S{};
-    __shared__ float coef[kFoldJ][kFoldA];
+    __shared__ __align__(16) float coef[kFoldJ][kFoldA];
+    static_assert(kFoldA % 4 == 0, "coefficients are read as float4");
     const int u = blockIdx.x * blockDim.x + threadIdx.x;
     float acc[kFoldA];
 #pragma unroll
@@ -160,8 +161,16 @@ __global__ void __launch_bounds__(kFoldThreads) fold_kernel(
             const int jn = min(kFoldJ, nj - jb);
             for (int jj = 0; jj < jn; ++jj) {
                 float r = __ldg(rot + (size_t)(jb + jj) * s3 + u);
+                // one 16-byte broadcast read per four FMAs
+                const float4* c4 = reinterpret_cast<const float4*>(&coef[jj][0]);
 #pragma unroll
-                for (int a = 0; a < kFoldA; ++a) acc[a] = fmaf(coef[jj][a], r, acc[a]);
+                for (int a4 = 0; a4 < kFoldA / 4; ++a4) {
+                    const float4 c = c4[a4];
+                    acc[4 * a4 + 0] = fmaf(c.x, r, acc[4 * a4 + 0]);
+                    acc[4 * a4 + 1] = fmaf(c.y, r, acc[4 * a4 + 1]);
+                    acc[4 * a4 + 2] = fmaf(c.z, r, acc[4 * a4 + 2]);
+                    acc[4 * a4 + 3] = fmaf(c.w, r, acc[4 * a4 + 3]);
+                }
             }
         }
     }
