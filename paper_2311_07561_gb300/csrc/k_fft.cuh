@@ -861,7 +861,23 @@ cudaError_t run_cols_mul(const float2* spec, const TS* tspec, PS* prod, int Bz, 
 template <int L, typename PS, typename RT>
 cudaError_t run_rows_c2r(const PS* prod, int X, int Y, int Z, FftGeom g, RT* corr, int K,
                          const float2* tw, int* status, FftKeep keep, cudaStream_t st) {
-    if constexpr (two_level<L>()) {
+    if constexpr (c2r_half<L>()) {
+        constexpr int L1 = TwoLevel<L / 2>::L1, L2 = TwoLevel<L / 2>::L2;
+        constexpr int NR = kTwoThreads / L1;
+        constexpr size_t smem = two_rows_smem<L1, L2>();
+        auto kern = rows_c2r_half_t<L1, L2, PS, RT>;
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
+        if (e != cudaSuccess) return e;
+        if (keep.z1 < keep.z0 || keep.y1 < keep.y0 || keep.x1 < keep.x0) return cudaSuccess;
+        const size_t nrows = (size_t)K * (keep.z1 - keep.z0 + 1) * (keep.y1 - keep.y0 + 1);
+        unsigned grid = 0;
+        if ((e = persistent_grid(kern, smem, (nrows + NR - 1) / NR, &grid)) != cudaSuccess) return e;
+        if (grid == 0) return cudaSuccess;
+        (void)status;                       // no device-side waits in this pass
+        kern<<<grid, kTwoThreads, smem, st>>>(prod, X, Y, Z, g, corr, K, tw, keep);
+        return cudaGetLastError();
+    } else if constexpr (two_level<L>()) {
         constexpr int L1 = TwoLevel<L>::L1, L2 = TwoLevel<L>::L2;
         constexpr int NR = kTwoThreads / L1;
         constexpr size_t smem = two_rows_smem<L1, L2>();

@@ -387,5 +387,116 @@ __global__ void __launch_bounds__(kTwoThreads, two_min_blocks<L2>()) rows_c2r2_t
     }
 }
 
+// ---- half-spectrum rows -> real x lines through a half-length transform -----
+// A real line y[n] = sum_k X[k] W_L^(-n k) of even length L = 2M is the
+// complex transform of length M of
+//   Z[k] = X[k] + conj X[M-k] + i (X[k] - conj X[M-k]) W_L^(-k),   k < M,
+// read as z[m] = y[2m] + i y[2m+1]: half the transform work of the full-length
+// pass, and the outputs leave in pairs.  M = L1 L2 takes the two-level form
+// (thread (row, n1) holds Z[n1 + L1 n2]; the twiddles of length M are
+// W_M^j = W_L^(2j) from the pass's table).  The samples X[k] of the next tile
+// are loaded into registers while the current one is transformed; X[M-k]
+// (another thread's X[k'] of the same row) is read when needed.
+template <int L> constexpr bool c2r_half() { return L >= 256 && TwoLevel<L / 2>::L1 > 0; }
+
+template <int L1, int L2, typename PS, typename RT>
+__global__ void __launch_bounds__(kTwoThreads, two_min_blocks<L2>()) rows_c2r_half_t(
+    const PS* __restrict__ in, int X, int Y, int Z, FftGeom g, RT* __restrict__ out, int n_batch,
+    const float2* __restrict__ tw, FftKeep keep) {
+    constexpr int M = L1 * L2;
+    constexpr int L = 2 * M;
+    constexpr int XH = M + 1;
+    constexpr int NR = kTwoThreads / L1;
+    constexpr int ZP = L1 + 1;
+    extern __shared__ float2 zx[];                    // [row][k2][n1 (padded)]
+    const int t = threadIdx.x;
+    const int ra = t / L1, n1 = t % L1;
+    const int ny = keep.y1 - keep.y0 + 1, nz = keep.z1 - keep.z0 + 1;
+    const size_t nrows = (size_t)n_batch * nz * ny;
+    const size_t ntiles = (nrows + NR - 1) / NR;
+    auto row_of = [&](size_t q, size_t& src_row, long long& dst) {
+        const size_t per_item = (size_t)nz * ny;
+        const size_t item = q / per_item;
+        const size_t r = q - item * per_item;
+        const int z = keep.z0 + (int)(r / (size_t)ny);
+        const int y = keep.y0 + (int)(r % (size_t)ny);
+        src_row = (item * (size_t)g.Zp + (size_t)z) * (size_t)g.Yp + (size_t)y;
+        dst = (y < Y && z < Z) ? (long long)(item * ((size_t)X * Y * Z) + ((size_t)z * Y + y) * X)
+                               : -1;
+    };
+    PS raw[L2];
+    auto load = [&](size_t tile) {
+        const size_t q = tile * NR + ra;
+        if (q < nrows) {
+            size_t src;
+            long long dst;
+            row_of(q, src, dst);
+            const PS* rowp = in + src * XH;
+#pragma unroll
+            for (int n2 = 0; n2 < L2; ++n2) raw[n2] = rowp[n1 + L1 * n2];
+        }
+    };
+    size_t tile = blockIdx.x;
+    if (tile >= ntiles) return;
+    load(tile);
+    const int xk0 = keep.x0, xk1 = min(keep.x1, X - 1);
+    for (; tile < ntiles; tile += gridDim.x) {
+        const size_t qa = tile * NR + ra;
+        const bool in_a = qa < nrows;
+        size_t src_a = 0;
+        long long dst_a;
+        if (in_a) row_of(qa, src_a, dst_a);
+        const PS* rowa = in + src_a * XH;
+        float2 v[L2];
+#pragma unroll
+        for (int n2 = 0; n2 < L2; ++n2) {
+            const int k = n1 + L1 * n2;
+            float2 zk = make_float2(0.f, 0.f);
+            if (in_a) {
+                const float2 a = ldc(&raw[n2]);
+                float2 b = ldc(rowa + (M - k));
+                b.y = -b.y;                            // conj X[M - k]
+                float2 w = __ldg(tw + k);
+                w.y = -w.y;                            // W_L^(-k)
+                const float2 d = cmul(csub(a, b), w);
+                zk = make_float2(a.x + b.x - d.y, a.y + b.y + d.x);   // (a + b) + i d
+            }
+            v[n2] = zk;
+        }
+        if (tile + gridDim.x < ntiles) load(tile + gridDim.x);
+        dft_reg<L2, +1>(v);
+#pragma unroll
+        for (int k2 = 1; k2 < L2; ++k2) {
+            float2 w = __ldg(tw + 2 * n1 * k2);        // W_M^(n1 k2) = W_L^(2 n1 k2)
+            w.y = -w.y;
+            v[k2] = cmul(v[k2], w);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int k2 = 0; k2 < L2; ++k2) zx[(ra * L2 + k2) * ZP + n1] = v[k2];
+        __syncthreads();
+        for (int it = t; it < NR * L2; it += kTwoThreads) {
+            const int rb = it / L2, k2 = it % L2;
+            const size_t q = tile * NR + rb;
+            if (q >= nrows) continue;
+            size_t src;
+            long long dst;
+            row_of(q, src, dst);
+            float2 u[L1];
+#pragma unroll
+            for (int m = 0; m < L1; ++m) u[m] = zx[(rb * L2 + k2) * ZP + m];
+            dft_reg<L1, +1>(u);
+            if (dst >= 0) {
+#pragma unroll
+                for (int k1 = 0; k1 < L1; ++k1) {
+                    const int x = 2 * (k2 + L2 * k1);   // z[m] = (y[2m], y[2m+1])
+                    if (x >= xk0 && x <= xk1) str(out + dst + x, u[k1].x);
+                    if (x + 1 >= xk0 && x + 1 <= xk1) str(out + dst + x + 1, u[k1].y);
+                }
+            }
+        }
+    }
+}
+
 }  // namespace fftk
 }  // namespace ttm
