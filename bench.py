@@ -114,9 +114,17 @@ NCU_TRAFFIC: dict = {
     # 912 673 interior voxels in one launch each
     "rotation_polish": [dict(bytes_per_voxel=(193201664 + 9929728) / 912673, K=35, storage="f32",
                              source_sha="9cb54c7dd779",
-                             sources=["k_rotation.cuh", "k_rotation.cu", "k_rotation_n4.cu"])],
+                             sources=["k_rotation.cuh", "k_rotation.cu", "k_rotation_n4.cu"]),
+                        # the 256x256x192 case of the order-6 template (c5s), bf16
+                        # maps, 4 805 121 interior voxels in one launch
+                        dict(bytes_per_voxel=(1193809664 + 89346048) / 4805121, K=84,
+                             storage="bf16", source_sha="ff504cc20f88",
+                             sources=["k_rotation.cuh", "k_rotation.cu", "k_rotation_n6.cu"])],
     "rotation_search": [dict(bytes_per_voxel=(173783808 + 12853504) / 912673, K=35, storage="f32",
                              source_sha="047846cd439c",
+                             sources=["k_search_tc.cu", "k_rotation.cuh"]),
+                        dict(bytes_per_voxel=(1094236928 + 93430016) / 4805121, K=84,
+                             storage="bf16", source_sha="3a1b983169e4",
                              sources=["k_search_tc.cu", "k_rotation.cuh"])],
 }
 

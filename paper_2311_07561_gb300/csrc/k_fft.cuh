@@ -837,7 +837,7 @@ template <int L, typename TS, typename PS>
 cudaError_t run_cols_mul(const float2* spec, const TS* tspec, PS* prod, int Bz, int K,
                          const float2* tw, int lo, int hi, cudaStream_t st) {
     if constexpr (two_level<L>()) {
-        constexpr int L1 = TwoLevel<L>::L1, L2 = TwoLevel<L>::L2;
+        constexpr int L1 = MulSplit<L>::L1, L2 = MulSplit<L>::L2;
         constexpr int TB = kTwoThreads / L1;
         constexpr size_t smem = two_cols_smem<L1, L2>();
         auto kern = cols_mul2_t<L1, L2, TS, PS>;
@@ -862,7 +862,7 @@ template <int L, typename PS, typename RT>
 cudaError_t run_rows_c2r(const PS* prod, int X, int Y, int Z, FftGeom g, RT* corr, int K,
                          const float2* tw, int* status, FftKeep keep, cudaStream_t st) {
     if constexpr (c2r_half<L>()) {
-        constexpr int L1 = TwoLevel<L / 2>::L1, L2 = TwoLevel<L / 2>::L2;
+        constexpr int L1 = RowSplit<L / 2>::L1, L2 = RowSplit<L / 2>::L2;
         constexpr int NR = kTwoThreads / L1;
         constexpr size_t smem = two_rows_smem<L1, L2>();
         auto kern = rows_c2r_half_t<L1, L2, PS, RT>;
@@ -921,6 +921,22 @@ template <int L>
 cudaError_t FftLen<L>::rows_r2c(const float* f, int X, int Y, int Z, FftGeom g, float2* spec,
                                 const float2* tw, int mode, double* moments,
                                 cudaStream_t st) {
+    if constexpr (fftk::r2c_half<L>()) {
+        constexpr int L1 = fftk::RowSplit<L / 2>::L1, L2 = fftk::RowSplit<L / 2>::L2;
+        constexpr int NR = fftk::kTwoThreads / L1;
+        constexpr size_t smem = fftk::two_rows_smem<L1, L2>();
+        auto kern = fftk::rows_r2c_half_t<L1, L2>;
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
+        if (e != cudaSuccess) return e;
+        const size_t nrows = (size_t)g.Yp * g.Zp;
+        unsigned grid = 0;
+        if ((e = fftk::persistent_grid(kern, smem, (nrows + NR - 1) / NR, &grid)) != cudaSuccess)
+            return e;
+        if (grid == 0) return cudaSuccess;
+        kern<<<grid, fftk::kTwoThreads, smem, st>>>(f, X, Y, Z, g, spec, tw, mode, moments);
+        return cudaGetLastError();
+    }
     constexpr int NB = fftk::rows_nb<L>();
     const size_t smem = (size_t)2 * L * (NB + 1) * sizeof(float2);
     cudaError_t e = cudaFuncSetAttribute(fftk::rows_r2c_t<L>,

@@ -399,6 +399,15 @@ __global__ void __launch_bounds__(kTwoThreads, two_min_blocks<L2>()) rows_c2r2_t
 // (another thread's X[k'] of the same row) is read when needed.
 template <int L> constexpr bool c2r_half() { return L >= 256 && TwoLevel<L / 2>::L1 > 0; }
 
+// split of the half length M = L1 L2 in the row pass: the column passes' split,
+// except 480 = 32 x 15 (register DFTs of 15 and 32 points instead of 30 and 16
+// leave room for two CTAs per SM)
+template <int M> struct RowSplit { static constexpr int L1 = TwoLevel<M>::L1, L2 = TwoLevel<M>::L2; };
+template <> struct RowSplit<480> { static constexpr int L1 = 32, L2 = 15; };
+
+// split of the fused multiply's z lines (the column passes' split by default)
+template <int L> struct MulSplit { static constexpr int L1 = TwoLevel<L>::L1, L2 = TwoLevel<L>::L2; };
+
 template <int L1, int L2, typename PS, typename RT>
 __global__ void __launch_bounds__(kTwoThreads, two_min_blocks<L2>()) rows_c2r_half_t(
     const PS* __restrict__ in, int X, int Y, int Z, FftGeom g, RT* __restrict__ out, int n_batch,
@@ -494,6 +503,114 @@ __global__ void __launch_bounds__(kTwoThreads, two_min_blocks<L2>()) rows_c2r_ha
                     if (x + 1 >= xk0 && x + 1 <= xk1) str(out + dst + x + 1, u[k1].y);
                 }
             }
+        }
+    }
+}
+
+// ---- real x lines -> half-spectrum rows through a half-length transform ------
+// The forward counterpart: z[m] = x[2m] + i x[2m+1] (m < M, L = 2M), Z = the
+// complex transform of length M (two-level, RowSplit), then
+//   X[k] = (Z[k] + conj Z[M-k]) / 2 - i W_L^k (Z[k] - conj Z[M-k]) / 2,  k = 0..M
+// (Z[M] = Z[0]) through a second exchange in shared memory.  Every row of the
+// padded box is written (rows beyond the data are zero).  mode 0 transforms
+// f, mode 1 (f - mean), mode 2 (f - mean)^2 and adds sum (f - mean)^4 into
+// moments[2], mean = moments[0] / (X Y Z), as the Stockham pass does.
+template <int L> constexpr bool r2c_half() { return L >= 256 && TwoLevel<L / 2>::L1 > 0; }
+
+template <int L1, int L2>
+__global__ void __launch_bounds__(kTwoThreads, two_min_blocks<L2>()) rows_r2c_half_t(
+    const float* __restrict__ f, int X, int Y, int Z, FftGeom g, float2* __restrict__ out,
+    const float2* __restrict__ tw, int mode, double* __restrict__ moments) {
+    constexpr int M = L1 * L2;
+    constexpr int XH = M + 1;
+    constexpr int NR = kTwoThreads / L1;
+    constexpr int ZP = L1 + 1;
+    extern __shared__ float2 zx[];                    // exchange, then the rows' Z
+    __shared__ double part[kTwoThreads / 32];
+    const int t = threadIdx.x;
+    const int ra = t / L1, n1 = t % L1;
+    const size_t nrows = (size_t)g.Yp * g.Zp;
+    const size_t ntiles = (nrows + NR - 1) / NR;
+    const float mean = mode ? (float)(moments[0] / ((double)X * Y * Z)) : 0.f;
+    // input offset of row q of the padded box, -1 for a zero row
+    auto src_of = [&](size_t q) -> long long {
+        if (q >= nrows) return -1;
+        const int y = (int)(q % (size_t)g.Yp), z = (int)(q / (size_t)g.Yp);
+        return (y < Y && z < Z) ? (long long)(((size_t)z * Y + y) * X) : -1;
+    };
+    float q4 = 0.f;                                   // mode 2: this thread's sum of (f - mean)^4
+    for (size_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const long long sa = src_of(tile * NR + ra);
+        float2 v[L2];
+#pragma unroll
+        for (int n2 = 0; n2 < L2; ++n2) {
+            const int x = 2 * (n1 + L1 * n2);
+            float a = 0.f, b = 0.f;
+            if (sa >= 0) {
+                if (x < X) a = __ldg(f + sa + x) - mean;
+                if (x + 1 < X) b = __ldg(f + sa + x + 1) - mean;
+                if (mode == 2) {
+                    a *= a;
+                    b *= b;
+                    q4 = fmaf(a, a, fmaf(b, b, q4));
+                }
+            }
+            v[n2] = make_float2(a, b);
+        }
+        dft_reg<L2, -1>(v);
+#pragma unroll
+        for (int k2 = 1; k2 < L2; ++k2) v[k2] = cmul(v[k2], __ldg(tw + 2 * n1 * k2));   // W_M^(n1 k2)
+        __syncthreads();                              // the previous tile's rows are stored
+#pragma unroll
+        for (int k2 = 0; k2 < L2; ++k2) zx[(ra * L2 + k2) * ZP + n1] = v[k2];
+        __syncthreads();
+        // step B: NI items per thread, kept in registers until the exchange
+        // buffer is free
+        constexpr int NI = (NR * L2 + kTwoThreads - 1) / kTwoThreads;
+        static_assert(NI <= 2, "at most two step-B items per thread");
+        float2 zk[NI][L1];
+#pragma unroll
+        for (int i = 0; i < NI; ++i) {
+            const int it = t + i * kTwoThreads;
+            if (it < NR * L2) {
+                const int rb = it / L2, k2 = it % L2;
+#pragma unroll
+                for (int m = 0; m < L1; ++m) zk[i][m] = zx[(rb * L2 + k2) * ZP + m];
+                dft_reg<L1, -1>(zk[i]);
+            }
+        }
+        __syncthreads();                              // the exchange buffer is free
+#pragma unroll
+        for (int i = 0; i < NI; ++i) {
+            const int it = t + i * kTwoThreads;
+            if (it < NR * L2) {
+                const int rb = it / L2, k2 = it % L2;
+#pragma unroll
+                for (int k1 = 0; k1 < L1; ++k1) zx[rb * M + k2 + L2 * k1] = zk[i][k1];
+            }
+        }
+        __syncthreads();
+        for (int it = t; it < NR * XH; it += kTwoThreads) {
+            const int rb = it / XH, k = it % XH;
+            const size_t q = tile * NR + rb;
+            if (q >= nrows) continue;
+            const float2 a = zx[rb * M + (k == M ? 0 : k)];
+            float2 b = zx[rb * M + (k == 0 ? 0 : M - k)];
+            b.y = -b.y;                               // conj Z[M - k]
+            const float2 e = make_float2(0.5f * (a.x + b.x), 0.5f * (a.y + b.y));
+            const float2 d = cmul(make_float2(0.5f * (a.x - b.x), 0.5f * (a.y - b.y)), __ldg(tw + k));
+            out[q * XH + k] = make_float2(e.x + d.y, e.y - d.x);      // e - i d
+        }
+    }
+    if (mode == 2) {
+        double d = q4;
+        for (int o = 16; o > 0; o >>= 1) d += __shfl_down_sync(0xffffffffu, d, o);
+        if ((t & 31) == 0) part[t >> 5] = d;
+        __syncthreads();
+        if (t == 0) {
+            double s4 = 0.0;
+            for (int k = 0; k < kTwoThreads / 32; ++k) s4 += part[k];
+            if (s4 != 0.0) atomicAdd(moments + 2, s4);
         }
     }
 }
