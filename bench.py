@@ -110,21 +110,22 @@ L2_FLUSH_BYTES = 256 << 20
 # was taken on; reported (times the interior voxels of a step) only while
 # those sources are unchanged.
 NCU_TRAFFIC: dict = {
-    # ncu (dram__bytes_read.sum + dram__bytes_write.sum) of the 128^3 case,
-    # 912 673 interior voxels in one launch each
-    "rotation_polish": [dict(bytes_per_voxel=(193201664 + 9929728) / 912673, K=35, storage="f32",
-                             source_sha="9cb54c7dd779",
+    # ncu (dram__bytes_read.sum + dram__bytes_write.sum) of one launch over the
+    # whole interior: the 128^3 case (c2s), 912 673 interior voxels, FP32 maps;
+    # the 256x256x192 case of the order-6 template (c5s), 4 805 121 interior
+    # voxels, bf16 maps.  Kernels reading their problems from the per-launch
+    # segment table.
+    "rotation_polish": [dict(bytes_per_voxel=(193203968 + 9818112) / 912673, K=35, storage="f32",
+                             source_sha="6a9d8ea49a0f",
                              sources=["k_rotation.cuh", "k_rotation.cu", "k_rotation_n4.cu"]),
-                        # the 256x256x192 case of the order-6 template (c5s), bf16
-                        # maps, 4 805 121 interior voxels in one launch
-                        dict(bytes_per_voxel=(1193809664 + 89346048) / 4805121, K=84,
-                             storage="bf16", source_sha="ff504cc20f88",
+                        dict(bytes_per_voxel=(1194241280 + 89479168) / 4805121, K=84,
+                             storage="bf16", source_sha="7d71bab6119b",
                              sources=["k_rotation.cuh", "k_rotation.cu", "k_rotation_n6.cu"])],
-    "rotation_search": [dict(bytes_per_voxel=(173783808 + 12853504) / 912673, K=35, storage="f32",
-                             source_sha="047846cd439c",
+    "rotation_search": [dict(bytes_per_voxel=(173786368 + 12342784) / 912673, K=35, storage="f32",
+                             source_sha="6e5bd42d6680",
                              sources=["k_search_tc.cu", "k_rotation.cuh"]),
-                        dict(bytes_per_voxel=(1094236928 + 93430016) / 4805121, K=84,
-                             storage="bf16", source_sha="3a1b983169e4",
+                        dict(bytes_per_voxel=(1094080768 + 93124096) / 4805121, K=84,
+                             storage="bf16", source_sha="6e5bd42d6680",
                              sources=["k_search_tc.cu", "k_rotation.cuh"])],
 }
 
@@ -142,6 +143,9 @@ def parse():
                          "(default fp32; mixed for c5, whose FP32 maps and spectra exceed HBM)")
     ap.add_argument("--mixed-compare", action=argparse.BooleanOptionalAction, default=True,
                     help="with fp32, also time the mixed-precision plan on the same volume")
+    ap.add_argument("--batch-mib", type=int, default=-1,
+                    help="batch workloads: resident waves of this many MiB of correlation "
+                         "maps (plan option batch_mib); -1 = 32768, 0 = one problem at a time")
     ap.add_argument("--rotation-chunks", type=int, default=0,
                     help="interior chunks of the pipelined search/refinement (0 = library default)")
     ap.add_argument("--peaks-only", action=argparse.BooleanOptionalAction, default=True,
@@ -588,20 +592,29 @@ def stage_traffic(name: str, K: int, storage: str, n_int: int):
 STAGE_CLASSES = {"score_rotation": ("rotation_search", "rotation_polish")}
 
 
+def kernel_ms(kern: dict) -> float:
+    """Summed event time of the kernel classes (the rotation_stage span, which
+    covers other classes' launches, left out)."""
+    return sum(v["ms"] for k, v in kern.items() if k != "rotation_stage")
+
+
 def roofline(kernels: dict, steps: int, geo: dict, peaks: dict) -> dict:
     """Roofline object of the stage with the largest share of the step.
 
     Work is algorithmic: FLOP for the score + rotation step (the planned a5
     count), bytes for the memory-bound stages (what each pass must read and
     write at the plan's storage precision), never a count of what the kernel
-    happens to execute.  The score + rotation stage is timed as the sum of its
-    two kernel classes' CUDA-event times (they overlap on two streams, so the
-    sum is an upper bound of the stage's share of the step)."""
+    happens to execute.  The score + rotation stage is timed by its span
+    (rotation_stage: the wall time of the stage on the launch stream, its
+    search and refinement overlapping on two streams), else as the sum of its
+    two kernel classes' CUDA-event times (an upper bound)."""
     K, nvox, n_int = geo["K"], geo["nvox"], geo["n_interior"]
     per_step = {k: v["ms"] / steps for k, v in kernels.items()}
+    span = per_step.pop("rotation_stage", None)
     stages = dict(per_step)
     if all(c in per_step for c in STAGE_CLASSES["score_rotation"]):
-        stages["score_rotation"] = sum(per_step.pop(c) for c in STAGE_CLASSES["score_rotation"])
+        stages["score_rotation"] = span if span else sum(per_step[c] for c in
+                                                         STAGE_CLASSES["score_rotation"])
         for c in STAGE_CLASSES["score_rotation"]:
             stages.pop(c)
     name = max(stages, key=stages.get)
@@ -701,7 +714,10 @@ def run_ours(args) -> None:
     wl = load_workload(args.workload)
     Z, Y, X = wl.volume.shape
     nvox = X * Y * Z
-    # tensor template, once per template (timed separately)
+    # tensor template, once per template (timed separately, after one
+    # untimed build that loads the modules and grows the allocator)
+    ttm.build_template(wl.template, wl.mask, wl.n_order, wl.quadrature)
+    torch.cuda.synchronize()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     ev0.record()
     comp, desc = ttm.build_template(wl.template, wl.mask, wl.n_order, wl.quadrature)
@@ -731,11 +747,13 @@ def run_ours(args) -> None:
     torch.cuda.synchronize()
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     stops = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    torch.cuda.nvtx.range_push("timed_steps")     # the launch list's range
     for k in range(args.steps):
         flush.zero_()
         starts[k].record(stream)
         matcher.run([vol])
         stops[k].record(stream)
+    torch.cuda.nvtx.range_pop()
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
@@ -942,10 +960,12 @@ def run_ours(args) -> None:
         error_vs_oracle=errors, precision_pair=pair, classical=classical,
         mixed_precision=mixed, peaks_only=peaks_only,
         clocks=clk,
+        rotation_stage_ms_per_step=(round(kern["rotation_stage"]["ms"] / args.steps, 4)
+                                    if "rotation_stage" in kern else None),
         kernels={k: dict(ms_per_step=round(v["ms"] / args.steps, 4),
                          launches_per_step=v["launches"] / args.steps,
-                         share=round(v["ms"] / sum(x["ms"] for x in kern.values()), 4))
-                 for k, v in kern.items()},
+                         share=round(v["ms"] / kernel_ms(kern), 4))
+                 for k, v in kern.items() if k != "rotation_stage"},
     )
     print(json.dumps(line), flush=True)
     if dist:
@@ -1035,6 +1055,9 @@ def run_batch(args) -> None:
     ttm.load_library()
 
     bw = synth.batch_workload(args.workload)
+    # one untimed build first (module loading, allocator growth)
+    ttm.build_template(bw.templates[0], bw.masks[0], bw.n_order, bw.quadrature)
+    torch.cuda.synchronize()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     ev0.record()
     tmpls = []
@@ -1048,6 +1071,7 @@ def run_batch(args) -> None:
     opts.path = {"auto": ttm.TTM_PATH_TUNE, "direct": 1, "fft": 2}[args.path]
     opts.precision = ttm.TTM_PREC_MIXED if args.precision == "mixed" else ttm.TTM_PREC_FP32
     opts.rotation_chunks = args.rotation_chunks
+    opts.batch_mib = args.batch_mib if args.batch_mib >= 0 else 32768
     dvols = [torch.from_numpy(v).to(dev) for v in bw.volumes]
     problems, vols = [], []
     for v, vol in enumerate(bw.volumes):
@@ -1059,6 +1083,7 @@ def run_batch(args) -> None:
     plan_s = time.perf_counter() - t0
     paths = [ttm.ttm_plan_problem_path(matcher.plan, p) for p in range(len(problems))]
     tuning = [ttm.ttm_plan_problem_tuning(matcher.plan, p) for p in range(len(problems))]
+    waves = ttm.ttm_plan_waves(matcher.plan)
     nvox_total = sum(int(np.prod(d)) for d, _ in problems)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream()
@@ -1080,11 +1105,13 @@ def run_batch(args) -> None:
     torch.cuda.synchronize()
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     stops = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    torch.cuda.nvtx.range_push("timed_steps")     # the launch list's range
     for k in range(args.steps):
         flush.zero_()
         starts[k].record(stream)
         graph.replay()
         stops[k].record(stream)
+    torch.cuda.nvtx.range_pop()
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
@@ -1172,6 +1199,11 @@ def run_batch(args) -> None:
                     tuned_problems=sum(1 for t in tuning if t[0] >= 0 and t[1] >= 0),
                     plan_seconds=round(plan_s, 2), template_build_ms=round(build_ms, 2),
                     graph="one CUDA graph replay per step (all problems)",
+                    launches_per_step=launches_per_step,
+                    resident_waves=(dict(batch_mib=opts.batch_mib, waves=len(waves),
+                                         first_problems=waves,
+                                         workspace_gib=round(matcher.ws.numel() / 2**30, 2))
+                                    if waves else None),
                     rotation_grid=2048, refinement=refinement_text(tmpls[0][1].K),
                     l2="flushed (256 MB write) before every timed step",
                     parallelism="replicas" if world > 1 else "single GPU",
@@ -1179,8 +1211,10 @@ def run_batch(args) -> None:
         roofline=rf, cpu_baseline=cpu, e2e=e2e, gpu_launches=launches_per_step * args.steps,
         clocks=clk,
         kernels={k: dict(ms_per_step=round(v["ms"], 4), launches_per_step=v["launches"],
-                         share=round(v["ms"] / sum(x["ms"] for x in kern.values()), 4))
-                 for k, v in kern.items()},
+                         share=round(v["ms"] / kernel_ms(kern), 4))
+                 for k, v in kern.items() if k != "rotation_stage"},
+        rotation_stage_ms_per_step=(round(kern["rotation_stage"]["ms"], 4)
+                                    if "rotation_stage" in kern else None),
         kernels_note="per-kernel times from one eager (not graph) step outside the timed region",
     )
     print(json.dumps(line), flush=True)

@@ -129,7 +129,16 @@ typedef struct ttm_plan_opts {
                          /* ttm_build_tensor_template.  0 = none (h = identity) */
     int n_refined;       /* best points after the power steps that take the  */
                          /* Newton steps; 0 = default (4, or 2 at order 6), <= 4 */
-    int reserved;
+    int batch_mib;       /* > 0: resident waves.  ttm_correlate keeps the     */
+                         /* correlation maps and search candidates of         */
+                         /* consecutive problems (same map type) in the       */
+                         /* workspace together, up to this many MiB per wave, */
+                         /* and runs the score/rotation stage of a wave as    */
+                         /* one search launch and one refinement launch per   */
+                         /* rotation chunk over a table of (problem, units)   */
+                         /* segments (up to 24 problems per launch).  The     */
+                         /* workspace grows by the largest wave.  0 = one     */
+                         /* problem at a time.  <= 2^20                       */
 } ttm_plan_opts;
 
 typedef struct ttm_plan_s* ttm_plan_t;
@@ -263,10 +272,18 @@ ttm_status ttm_plan_problem_fft_box(ttm_plan_t plan, int problem, int* box);
 /* Kernel launches the plan has queued so far (for accounting). */
 ttm_status ttm_plan_launch_count(ttm_plan_t plan, long long* launches);
 
+/* Resident waves of the plan (option batch_mib): *n_waves = their number (0
+ * when problems run one at a time); with first != NULL, first[0..n_waves-1]
+ * receives the first problem of each wave (the caller sizes it from a call
+ * with first = NULL).  Host-only; TTM_ERR_INVALID_ARG for a bad plan or
+ * pointer. */
+ttm_status ttm_plan_waves(ttm_plan_t plan, int* n_waves, int* first);
+
 /* Status recorded by the device during the calls queued since the last
- * ttm_correlate on this workspace (a bounded wait inside a kernel that ran
- * out records TTM_ERR_TIMEOUT there instead of hanging).  Synchronises the
- * stream; returns TTM_OK or the recorded error. */
+ * ttm_local_stats or ttm_correlate on this workspace (each starts by clearing
+ * it; a bounded wait inside a kernel that ran out records TTM_ERR_TIMEOUT
+ * there instead of hanging).  Synchronises the stream; returns TTM_OK or the
+ * recorded error. */
 ttm_status ttm_plan_device_status(ttm_plan_t plan, void* d_workspace, size_t workspace_bytes,
                                   void* stream);
 
@@ -275,8 +292,12 @@ ttm_status ttm_plan_device_status(ttm_plan_t plan, void* d_workspace, size_t wor
  * for those events, adds the elapsed times per kernel class into ms[c] and the
  * launch counts into launches[c] for c < n_classes (either array may be NULL),
  * and forgets them.  Class names come from ttm_kernel_class_name; there are
- * TTM_KERNEL_CLASSES classes. */
-#define TTM_KERNEL_CLASSES 12
+ * TTM_KERNEL_CLASSES classes.  The last, "rotation_stage", is not a kernel
+ * but a span: the wall time of each problem's (or resident wave's)
+ * score/rotation stage on the launch stream, with its search and refinement
+ * overlapped on the plan's two rotation streams; its launches are counted in
+ * their own classes as well. */
+#define TTM_KERNEL_CLASSES 13
 ttm_status ttm_plan_enable_timing(ttm_plan_t plan, int enable);
 ttm_status ttm_plan_timing(ttm_plan_t plan, double* ms, long long* launches, int n_classes);
 const char* ttm_kernel_class_name(int kernel_class);

@@ -32,14 +32,14 @@ EXPORTED = (
     "ttm_build_tensor_template", "ttm_plan", "ttm_plan_workspace_size",
     "ttm_plan_problem_path", "ttm_plan_problem_fft_box", "ttm_plan_problem_tuning",
     "ttm_plan_problem_tensor_direct",
-    "ttm_plan_launch_count", "ttm_plan_destroy",
+    "ttm_plan_launch_count", "ttm_plan_waves", "ttm_plan_destroy",
     "ttm_local_stats", "ttm_correlate", "ttm_extract_peaks", "ttm_match_peaks", "ttm_lowpass",
     "ttm_plan_enable_timing",
     "ttm_plan_timing", "ttm_kernel_class_name", "ttm_build_tensor_template_noalloc",
     "ttm_plan_device_status", "ttm_classical_workspace_size", "ttm_classical_ncc",
 )
 TTM_NOALLOC_SCRATCH_BYTES = 8388608
-TTM_KERNEL_CLASSES = 12
+TTM_KERNEL_CLASSES = 13
 
 
 class TTMError(RuntimeError):
@@ -65,7 +65,7 @@ class PlanOpts(ctypes.Structure):
                 ("n_cells", ctypes.c_int), ("n_candidates", ctypes.c_int),
                 ("newton_steps", ctypes.c_int), ("rotation_chunks", ctypes.c_int),
                 ("lowpass_sigma", ctypes.c_float), ("n_refined", ctypes.c_int),
-                ("reserved", ctypes.c_int)]
+                ("batch_mib", ctypes.c_int)]
 
 
 _lib: Optional[ctypes.CDLL] = None
@@ -95,6 +95,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "ttm_plan_problem_tensor_direct": (I, [P, I, ctypes.POINTER(I)]),
         "ttm_plan_problem_tuning": (I, [P, I, ctypes.POINTER(ctypes.c_double)]),
         "ttm_plan_launch_count": (I, [P, ctypes.POINTER(L)]),
+        "ttm_plan_waves": (I, [P, ctypes.POINTER(I), ctypes.POINTER(I)]),
         "ttm_plan_destroy": (None, [P]),
         "ttm_local_stats": (I, [P, PP, PP, P, S, P]),
         "ttm_correlate": (I, [P, PP, PP, PP, PP, PP, PP, P, S, P]),
@@ -259,6 +260,16 @@ def ttm_plan_launch_count(plan: int) -> int:
     out = ctypes.c_longlong()
     _check(load_library().ttm_plan_launch_count(plan, ctypes.byref(out)), "ttm_plan_launch_count")
     return out.value
+
+
+def ttm_plan_waves(plan: int) -> list:
+    """First problem of each resident wave (empty: one problem at a time)."""
+    lib = load_library()
+    n = ctypes.c_int()
+    _check(lib.ttm_plan_waves(plan, ctypes.byref(n), None), "ttm_plan_waves")
+    first = (ctypes.c_int * max(n.value, 1))()
+    _check(lib.ttm_plan_waves(plan, ctypes.byref(n), first), "ttm_plan_waves")
+    return list(first)[:n.value]
 
 
 def ttm_plan_destroy(plan: Optional[int]) -> None:

@@ -5,30 +5,44 @@ namespace ttm {
 
 int rotation_row_stride(int n_order) { return (n_comp(n_order) + 3) & ~3; }
 
-static void fill_args(const void* corr, const float* w, size_t nvox, const VoxBox& box,
-                      uint32_t u0, uint32_t u1, const RotGrid& g, uint16_t* cand, float* score,
-                      float* quat, float* lambda, float* comp_out, rot::SearchArgs& sa,
+static void fill_args(const RotBatch& b, const RotGrid& g, rot::SearchArgs& sa,
                       rot::PolishArgs& pa, const UnitList& list) {
-    sa.list = list;
-    pa.list = list;
-    sa.corr = corr; sa.w = w; sa.nvox = nvox; sa.box = box; sa.score = score; sa.cand = cand;
-    sa.u0 = u0; sa.u1 = u1; pa.u0 = u0; pa.u1 = u1;
+    sa.b = b; pa.b = b;
+    sa.list = list; pa.list = list;
     sa.gm = g.d_m; sa.cell_end = g.d_cell_end; sa.n_grid = g.n_grid;
-    pa.corr = corr; pa.w = w; pa.nvox = nvox; pa.box = box; pa.score = score; pa.cand = cand; pa.quat = quat;
-    pa.lambda = lambda; pa.comp_out = comp_out; pa.gq = g.d_q; pa.n_cand = g.n_cand;
-    pa.newton = g.newton;
-    pa.n_refine = g.n_refine;
+    pa.gq = g.d_q; pa.n_cand = g.n_cand; pa.newton = g.newton; pa.n_refine = g.n_refine;
 }
 
-ttm_status launch_rotation_search(int n_order, const void* corr, bool bf16, const float* w,
-                                  size_t nvox, const VoxBox& box, uint32_t u0, uint32_t u1,
-                                  const RotGrid& g, uint16_t* cand, int* status, float* score,
-                                  cudaStream_t st, long long* cnt, const UnitList& list) {
-    if (box.count() > 0xFFFFFFFFull || (!list.idx && u1 > box.count())) return TTM_ERR_UNSUPPORTED;
-    if (u1 <= u0) return TTM_OK;
+// a batch's units lie in their problems' interiors; unit lists serve one problem
+static bool batch_ok(const RotBatch& b, const UnitList& list) {
+    if (b.n < 1 || b.n > kMaxRotSegs || (list.idx && b.n != 1)) return false;
+    for (int k = 0; k < b.n; ++k) {
+        const RotSeg& s = b.seg[k];
+        if (s.box.count() > 0xFFFFFFFFull || (!list.idx && s.u1 > s.box.count()) || s.u1 < s.u0)
+            return false;
+    }
+    return true;
+}
+
+RotBatch one_problem_batch(const void* corr, const float* w, size_t nvox, const VoxBox& box,
+                           uint32_t u0, uint32_t u1, uint16_t* cand, float* score, float* quat,
+                           float* lambda, float* comp_out) {
+    RotSeg s;
+    s.corr = corr; s.w = w; s.nvox = nvox; s.box = box; s.u0 = u0; s.u1 = u1 > u0 ? u1 : u0;
+    s.cand = cand; s.score = score; s.quat = quat; s.lambda = lambda; s.comp_out = comp_out;
+    RotBatch b;
+    b.add(s);
+    return b;
+}
+
+ttm_status launch_rotation_search(int n_order, const RotBatch& b, bool bf16, const RotGrid& g,
+                                  int* status, cudaStream_t st, long long* cnt,
+                                  const UnitList& list) {
+    if (!batch_ok(b, list)) return TTM_ERR_UNSUPPORTED;
+    if (b.ntiles == 0) return TTM_OK;
     rot::SearchArgs sa;
     rot::PolishArgs pa;
-    fill_args(corr, w, nvox, box, u0, u1, g, cand, score, nullptr, nullptr, nullptr, sa, pa, list);
+    fill_args(b, g, sa, pa, list);
     if (g.d_gtab && search_tc_supported(n_order, g.n_grid, g.n_cells))
         return launch_search_tc(n_order, sa, g.d_gtab, status, bf16, st, cnt);
     switch (n_order) {
@@ -40,17 +54,13 @@ ttm_status launch_rotation_search(int n_order, const void* corr, bool bf16, cons
     }
 }
 
-ttm_status launch_rotation_polish(int n_order, const void* corr, bool bf16, const float* w,
-                                  size_t nvox, const VoxBox& box, uint32_t u0, uint32_t u1,
-                                  const RotGrid& g, const uint16_t* cand, const float* score,
-                                  float* quat, float* lambda, float* comp_out, cudaStream_t st,
-                                  long long* cnt, const UnitList& list) {
-    if (box.count() > 0xFFFFFFFFull || (!list.idx && u1 > box.count())) return TTM_ERR_UNSUPPORTED;
-    if (u1 <= u0) return TTM_OK;
+ttm_status launch_rotation_polish(int n_order, const RotBatch& b, bool bf16, const RotGrid& g,
+                                  cudaStream_t st, long long* cnt, const UnitList& list) {
+    if (!batch_ok(b, list)) return TTM_ERR_UNSUPPORTED;
+    if (b.ntiles == 0) return TTM_OK;
     rot::SearchArgs sa;
     rot::PolishArgs pa;
-    fill_args(corr, w, nvox, box, u0, u1, g, const_cast<uint16_t*>(cand),
-              const_cast<float*>(score), quat, lambda, comp_out, sa, pa, list);
+    fill_args(b, g, sa, pa, list);
     switch (n_order) {
         case 2: return launch_rotation_n<2>(sa, pa, true, false, bf16, st, cnt);
         case 4: return launch_rotation_n<4>(sa, pa, true, false, bf16, st, cnt);
@@ -58,6 +68,29 @@ ttm_status launch_rotation_polish(int n_order, const void* corr, bool bf16, cons
         case 8: return launch_rotation_n<8>(sa, pa, true, false, bf16, st, cnt);
         default: return TTM_ERR_UNSUPPORTED;
     }
+}
+
+ttm_status launch_rotation_search(int n_order, const void* corr, bool bf16, const float* w,
+                                  size_t nvox, const VoxBox& box, uint32_t u0, uint32_t u1,
+                                  const RotGrid& g, uint16_t* cand, int* status, float* score,
+                                  cudaStream_t st, long long* cnt, const UnitList& list) {
+    if (box.count() > 0xFFFFFFFFull || (!list.idx && u1 > box.count())) return TTM_ERR_UNSUPPORTED;
+    if (u1 <= u0) return TTM_OK;
+    const RotBatch b = one_problem_batch(corr, w, nvox, box, u0, u1, cand, score, nullptr,
+                                         nullptr, nullptr);
+    return launch_rotation_search(n_order, b, bf16, g, status, st, cnt, list);
+}
+
+ttm_status launch_rotation_polish(int n_order, const void* corr, bool bf16, const float* w,
+                                  size_t nvox, const VoxBox& box, uint32_t u0, uint32_t u1,
+                                  const RotGrid& g, const uint16_t* cand, const float* score,
+                                  float* quat, float* lambda, float* comp_out, cudaStream_t st,
+                                  long long* cnt, const UnitList& list) {
+    if (box.count() > 0xFFFFFFFFull || (!list.idx && u1 > box.count())) return TTM_ERR_UNSUPPORTED;
+    if (u1 <= u0) return TTM_OK;
+    const RotBatch b = one_problem_batch(corr, w, nvox, box, u0, u1, const_cast<uint16_t*>(cand),
+                                         const_cast<float*>(score), quat, lambda, comp_out);
+    return launch_rotation_polish(n_order, b, bf16, g, st, cnt, list);
 }
 
 template <int N>

@@ -34,35 +34,30 @@ constexpr int kRefine = 4;        // candidates refined by Newton after the powe
 __device__ __forceinline__ float ldcorr(const float* p) { return __ldg(p); }
 __device__ __forceinline__ float ldcorr(const __nv_bfloat16* p) { return __bfloat162float(__ldg(p)); }
 
+// The problems and units of one launch (RotBatch, in the kernel parameters,
+// read in place: the kernels take their arguments as __grid_constant__).
 struct SearchArgs {
-    const void* corr;       // K x nvox, float or bf16
-    const float* w;
-    size_t nvox;            // voxels of the volume (stride of the component maps)
-    VoxBox box;             // interior voxels: the units the kernels visit
-    uint32_t u0, u1;        // this launch visits units [u0, u1)
-    UnitList list;          // optional unit list (peaks)
-    float* score;
-    uint16_t* cand;         // per interior voxel: 8 candidate grid indices
+    RotBatch b;
+    UnitList list;          // optional unit list (peaks; one problem per launch)
     const float* gm;        // n_grid x K4 (SIMT search)
     const int* cell_end;    // n_grid
     int n_grid;
 };
 
 struct PolishArgs {
-    const void* corr;       // K x nvox, float or bf16
-    const float* w;
-    size_t nvox;
-    VoxBox box;
-    uint32_t u0, u1;        // this launch visits units [u0, u1)
+    RotBatch b;
     UnitList list;          // optional unit list (peaks) and strided outputs
-    const float* score;
-    const uint16_t* cand;
-    float* quat;            // 4 x nvox interleaved (a, b, c, d) per voxel
-    float* lambda;          // nullable
-    float* comp_out;        // nullable, K x nvox
     const float* gq;        // n_grid x 4
     int n_cand, newton, n_refine;
 };
+
+static_assert(kRotThreads == kRotTile, "one block of the SIMT kernels is one tile");
+
+// segment of tile t: segments are in tile order, so s only moves forward
+static __device__ __forceinline__ int seg_of(const RotBatch& b, uint32_t t, int s = 0) {
+    while (s + 1 < b.n && t >= b.seg[s + 1].tile0) ++s;
+    return s;
+}
 
 // The score sum_alpha mu_alpha C_alpha^2 is accumulated in two halves, the
 // components below score_split<N>() and the rest, added at the end: the
@@ -353,8 +348,7 @@ __device__ void refine(const float (&C)[Geo<N>::K4], float sigma, int newton, fl
 // indices (0xFFFF = none).  One thread per voxel; the grid table is staged in
 // shared memory and read as broadcasts.
 template <int N, typename CT>
-__global__ void __launch_bounds__(kRotThreads) search_simt_kernel(SearchArgs a) {
-    const CT* corr = reinterpret_cast<const CT*>(a.corr);
+__global__ void __launch_bounds__(kRotThreads) search_simt_kernel(const __grid_constant__ SearchArgs a) {
     constexpr int K = Geo<N>::K;
     constexpr int K4 = Geo<N>::K4;
     constexpr Sym<N> S{};
@@ -362,17 +356,19 @@ __global__ void __launch_bounds__(kRotThreads) search_simt_kernel(SearchArgs a) 
     float* Mt = sm;                                   // kChunk x K4
     int* ends = reinterpret_cast<int*>(sm + kChunk * K4);
 
-    const size_t i = a.u0 + (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const bool in_range = i < list_end(a.list, a.u1);
-    const size_t v = in_range ? unit_voxel(a.box, a.list, (uint32_t)i) : 0;
-    const float wv = in_range ? __ldg(a.w + v) : 0.f;
+    const RotSeg& sg = a.b.seg[seg_of(a.b, blockIdx.x)];
+    const CT* corr = reinterpret_cast<const CT*>(sg.corr);
+    const size_t i = sg.u0 + (size_t)(blockIdx.x - sg.tile0) * kRotTile + threadIdx.x;
+    const bool in_range = i < list_end(a.list, sg.u1);
+    const size_t v = in_range ? unit_voxel(sg.box, a.list, (uint32_t)i) : 0;
+    const float wv = in_range ? __ldg(sg.w + v) : 0.f;
     float C[K4];
 #pragma unroll
     for (int k = 0; k < K4; ++k) C[k] = 0.f;
     float ss0 = 0.f, ss1 = 0.f;
 #pragma unroll
     for (int k = 0; k < K; ++k) {
-        float c = in_range ? wv * ldcorr(corr + (size_t)k * a.nvox + v) : 0.f;
+        float c = in_range ? wv * ldcorr(corr + (size_t)k * sg.nvox + v) : 0.f;
         C[k] = c;
         if (k < score_split<N>()) ss0 = fmaf((float)S.mu[k], c * c, ss0);
         else ss1 = fmaf((float)S.mu[k], c * c, ss1);
@@ -414,32 +410,33 @@ __global__ void __launch_bounds__(kRotThreads) search_simt_kernel(SearchArgs a) 
         }
     }
     if (!in_range) return;
-    a.score[v] = score;
-    store_candidates(a.cand, i, ti, active);
+    sg.score[v] = score;
+    store_candidates(sg.cand, i, ti, active);
 }
 
 // Refinement of the candidates and the outputs: lambda = the largest refined
 // phi, q its maximiser (canonical sign), C_alpha optionally.
 template <int N, typename CT>
-__global__ void __launch_bounds__(kRotThreads) polish_kernel(PolishArgs a) {
-    const CT* corr = reinterpret_cast<const CT*>(a.corr);
+__global__ void __launch_bounds__(kRotThreads) polish_kernel(const __grid_constant__ PolishArgs a) {
     constexpr int K = Geo<N>::K;
     constexpr int K4 = Geo<N>::K4;
-    const size_t i = a.u0 + (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= list_end(a.list, a.u1)) return;
-    const size_t v = unit_voxel(a.box, a.list, (uint32_t)i);
-    const float wv = __ldg(a.w + v);
+    const RotSeg& sg = a.b.seg[seg_of(a.b, blockIdx.x)];
+    const CT* corr = reinterpret_cast<const CT*>(sg.corr);
+    const size_t i = sg.u0 + (size_t)(blockIdx.x - sg.tile0) * kRotTile + threadIdx.x;
+    if (i >= list_end(a.list, sg.u1)) return;
+    const size_t v = unit_voxel(sg.box, a.list, (uint32_t)i);
+    const float wv = __ldg(sg.w + v);
     float C[K4];
 #pragma unroll
     for (int k = 0; k < K4; ++k) C[k] = 0.f;
 #pragma unroll
     for (int k = 0; k < K; ++k) {
-        float c = wv * ldcorr(corr + (size_t)k * a.nvox + v);
+        float c = wv * ldcorr(corr + (size_t)k * sg.nvox + v);
         C[k] = c;
-        if (a.comp_out) a.comp_out[(size_t)k * a.nvox + v] = c;
+        if (sg.comp_out) sg.comp_out[(size_t)k * sg.nvox + v] = c;
     }
-    const float score = __ldg(a.score + v);
-    const uint4 cr = __ldg(reinterpret_cast<const uint4*>(a.cand) + i);
+    const float score = __ldg(sg.score + v);
+    const uint4 cr = __ldg(reinterpret_cast<const uint4*>(sg.cand) + i);
     const uint32_t cw[4] = {cr.x, cr.y, cr.z, cr.w};
     float best_l = 0.f;
     float best_q[4] = {1.f, 0.f, 0.f, 0.f};
@@ -511,23 +508,22 @@ __global__ void __launch_bounds__(kRotThreads) polish_kernel(PolishArgs a) {
         for (int i = 0; i < 4; ++i) best_q[i] *= sgn;
     }
     if (a.list.out_stride > 0) {
-        float* qo = a.quat + i * (size_t)a.list.out_stride;
+        float* qo = sg.quat + i * (size_t)a.list.out_stride;
 #pragma unroll
         for (int k = 0; k < 4; ++k) qo[k] = best_q[k];
-        if (a.lambda) a.lambda[i * (size_t)a.list.out_stride] = best_l;
+        if (sg.lambda) sg.lambda[i * (size_t)a.list.out_stride] = best_l;
         return;
     }
-    reinterpret_cast<float4*>(a.quat)[v] = make_float4(best_q[0], best_q[1], best_q[2], best_q[3]);
-    if (a.lambda) a.lambda[v] = best_l;
+    reinterpret_cast<float4*>(sg.quat)[v] = make_float4(best_q[0], best_q[1], best_q[2], best_q[3]);
+    if (sg.lambda) sg.lambda[v] = best_l;
 }
 
 // search_done: run only the refinement; search_only: run only the SIMT search
 template <int N, typename CT>
 ttm_status launch_n_t(const SearchArgs& s, const PolishArgs& p, bool search_done, bool search_only,
                       cudaStream_t st, long long* cnt) {
-    const size_t units = s.u1 > s.u0 ? s.u1 - s.u0 : 0;
-    if (units == 0) return TTM_OK;
-    const unsigned blocks = (unsigned)((units + kRotThreads - 1) / kRotThreads);
+    if (s.b.ntiles == 0) return TTM_OK;
+    const unsigned blocks = s.b.ntiles;
     if (!search_done) {
         const size_t smem = (size_t)kChunk * Geo<N>::K4 * sizeof(float) + kChunk * sizeof(int);
         TTM_CUDA_TRY(cudaFuncSetAttribute(search_simt_kernel<N, CT>,

@@ -281,7 +281,7 @@ __device__ __forceinline__ void a_half_store(const float (&C)[KP / 2], float inv
 }
 
 template <typename CT, int N, int G>
-__global__ void __launch_bounds__(kThreads, 1) search_tc_kernel(rot::SearchArgs a,
+__global__ void __launch_bounds__(kThreads, 1) search_tc_kernel(const __grid_constant__ rot::SearchArgs a,
                                                                 const uint4* __restrict__ gtab,
                                                                 int* status) {
     using Sh = TcShape<n_comp(N), G>;
@@ -338,9 +338,12 @@ __global__ void __launch_bounds__(kThreads, 1) search_tc_kernel(rot::SearchArgs 
     uint32_t loads_pending = 0u;     // thread 0: copies issued and not yet waited on
     bool ok = true;
 
-    const uint32_t uend = rot::list_end(a.list, a.u1);
-    const size_t units = uend > a.u0 ? uend - a.u0 : 0;
-    const size_t ntiles = (units + 127) / 128;
+    // tiles of the launch (with a unit list, one problem: the listed units)
+    size_t ntiles = a.b.ntiles;
+    if (a.list.count) {
+        const uint32_t uend = rot::list_end(a.list, a.b.seg[0].u1);
+        ntiles = ((uend > a.b.seg[0].u0 ? uend - a.b.seg[0].u0 : 0) + 127) / 128;
+    }
     const unsigned char* gsrc = reinterpret_cast<const unsigned char*>(gtab);
     // streamed table: chunk q (counted over the whole CTA) goes to buffer q & 1;
     // the copy of chunk q + 2 starts once the MMAs of chunk q have completed
@@ -378,11 +381,14 @@ __global__ void __launch_bounds__(kThreads, 1) search_tc_kernel(rot::SearchArgs 
     const int lane_t = t & 127;            // TMEM lane = voxel of the tile
     const int grp = t >> 7;                // column group: columns grp * 256 / kGroups ...
     long qbase = 0;                        // chunks issued by this CTA before this tile
+    int sidx = 0;                          // problem of the tile (segments in tile order)
     for (size_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x, qbase += kChunks) {
         const bool more_tiles = tile + gridDim.x < ntiles;
-        const size_t i = a.u0 + tile * 128 + lane_t;
-        const bool in_range = i < uend;
-        const size_t v = in_range ? rot::unit_voxel(a.box, a.list, (uint32_t)i) : 0;
+        sidx = rot::seg_of(a.b, (uint32_t)tile, sidx);
+        const RotSeg& sg = a.b.seg[sidx];
+        const size_t i = sg.u0 + (tile - sg.tile0) * 128 + lane_t;
+        const bool in_range = i < rot::list_end(a.list, sg.u1);
+        const size_t v = in_range ? rot::unit_voxel(sg.box, a.list, (uint32_t)i) : 0;
         // components, score, normalised FP16 row of A: threads t and t + 128
         // share voxel t of the tile, each loading and writing half of the KP
         // columns (all its loads in flight at once); the two halves of the
@@ -391,10 +397,10 @@ __global__ void __launch_bounds__(kThreads, 1) search_tc_kernel(rot::SearchArgs 
         {
             constexpr int KH = KP / 2;
             float C[KH];
-            const float wv = in_range ? __ldg(a.w + v) : 0.f;
-            const CT* corr = reinterpret_cast<const CT*>(a.corr);
-            const float part = grp == 0 ? a_half_load<N, 0, KP>(corr, a.nvox, v, in_range, wv, C)
-                                        : a_half_load<N, 1, KP>(corr, a.nvox, v, in_range, wv, C);
+            const float wv = in_range ? __ldg(sg.w + v) : 0.f;
+            const CT* corr = reinterpret_cast<const CT*>(sg.corr);
+            const float part = grp == 0 ? a_half_load<N, 0, KP>(corr, sg.nvox, v, in_range, wv, C)
+                                        : a_half_load<N, 1, KP>(corr, sg.nvox, v, in_range, wv, C);
             float* ssx = reinterpret_cast<float*>(merge);
             if (grp == 1) ssx[lane_t] = part;
             __syncthreads();
@@ -511,8 +517,8 @@ __global__ void __launch_bounds__(kThreads, 1) search_tc_kernel(rot::SearchArgs 
 #pragma unroll
             for (int k = 0; k < rot::kMaxCand; ++k) ti[k] = top[k] == INT_MIN ? 0xFFFF : 2047 - (top[k] & 2047);
             if (in_range) {
-                a.score[v] = score;
-                rot::store_candidates(a.cand, i, ti, score > 0.f);
+                sg.score[v] = score;
+                rot::store_candidates(sg.cand, i, ti, score > 0.f);
             }
         }
         __syncthreads();     // merge buffer and A are reused by the next tile
@@ -538,7 +544,7 @@ static ttm_status launch_tc_t(const rot::SearchArgs& s, const uint16_t* grid_fp1
     int dev = 0, sms = 0;
     TTM_CUDA_TRY(cudaGetDevice(&dev));
     TTM_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    const size_t ntiles = ((s.u1 > s.u0 ? s.u1 - s.u0 : 0) + 127) / 128;
+    const size_t ntiles = s.b.ntiles;
     if (ntiles == 0) return TTM_OK;
     const unsigned grid = (unsigned)(ntiles < (size_t)sms ? ntiles : (size_t)sms);
     search_tc_kernel<CT, N, G><<<grid, kThreads, smem, st>>>(

@@ -103,7 +103,11 @@ ttm_status build_grid(ttm_plan_s* P) {
     // (the unit tests' model, on 400 voxels of the 928 x 928 x 464 workload's
     // template) gives the same largest lambda shortfall (4.2e-5 with 2048
     // grid points, 6.2e-5 with 1024: grid misses) with 2 candidates x 2
-    // refined x 2 Newton steps as with 8 x 4 x 3
+    // refined x 2 Newton steps as with 8 x 4 x 3.  At order 4 the FP64 model
+    // allows 3 x 2 x 3 as well, but the FP16 grid search ranks near-tied
+    // regions differently (2.4e-4 key resolution of the normalised phi): at
+    // a peak of a 200-rotation template the GPU then refined the wrong
+    // maximum (lambda 2.1e-5 short), so order 4 keeps 8 x 4 x 3
     const bool o6 = P->n_order == 6;
     const int cand = P->opts.n_candidates > 0 ? P->opts.n_candidates : (o6 ? 2 : 8);
     const int newton = P->opts.newton_steps > 0 ? P->opts.newton_steps : (o6 ? 2 : 3);
@@ -477,6 +481,82 @@ size_t scratch_bytes(const ttm_plan_s* P, const ProblemData& pr) {
     return std::max(std::max(corr, peaks), corr_peaks);
 }
 
+// Where one problem's correlation stage keeps its data in the workspace: the
+// K maps, the image spectrum and one group of product spectra (FFT path),
+// and the search candidates.  One problem at a time, everything sits at the
+// start of the scratch; with resident waves (plan option batch_mib) each
+// problem of a wave has its own maps and candidates, and the spectra sit in
+// a scratch area after the wave's maps.
+struct CorrLayout {
+    char* corr = nullptr;
+    char* spec = nullptr;
+    char* prod = nullptr;
+    uint16_t* cand = nullptr;
+};
+
+CorrLayout corr_layout(const ttm_plan_s* P, const ProblemData& pr, void* ws, bool resident) {
+    CorrLayout L;
+    const size_t es = pr.mixed ? 2 : 4;
+    char* base = (char*)ws;
+    if (resident) {
+        L.corr = base + pr.res_corr_off;
+        L.cand = (uint16_t*)(base + pr.res_cand_off);
+        L.spec = base + P->wave_scratch_off;
+    } else {
+        L.corr = base + kHeader;
+        L.cand = (uint16_t*)(L.corr + corr_region_bytes(P, pr));
+        L.spec = L.corr + align256((size_t)P->K * pr.nvox() * es);
+    }
+    L.prod = L.spec + align256(pr.fft.nspec() * sizeof(float2));
+    return L;
+}
+
+// Resident waves: consecutive problems with the same map type whose maps
+// and candidates fit in batch_mib MiB together (a problem larger than that
+// is a wave of its own).  Offsets from kHeader; the spectra scratch of the
+// FFT problems follows the largest wave.
+size_t resident_bytes(const ttm_plan_s* P, const ProblemData& pr, size_t* cand_off) {
+    const size_t es = pr.mixed ? 2 : 4;
+    const size_t maps = align256((size_t)P->K * pr.nvox() * es);
+    const VoxBox box = interior_box(pr.X, pr.Y, pr.Z, P->tmpl[pr.tmpl].desc.s);
+    if (cand_off) *cand_off = maps;
+    return maps + align256(box.count() * 16);
+}
+
+size_t wave_scratch_bytes(const ttm_plan_s* P) {
+    size_t b = 0;
+    for (const ProblemData& pr : P->prob)
+        if (pr.path == TTM_PATH_FFT)
+            b = std::max(b, align256(pr.fft.nspec() * sizeof(float2)) +
+                                align256((size_t)comp_group(P, pr) * pr.fft.nspec() * 2 *
+                                         (pr.mixed ? 2 : 4)));
+    return b;
+}
+
+void plan_waves(ttm_plan_s* P) {
+    const size_t budget = (size_t)P->opts.batch_mib << 20;
+    const int np = (int)P->prob.size();
+    P->waves.clear();
+    size_t acc = 0, largest = 0;
+    int w0 = 0;
+    for (int p = 0; p < np; ++p) {
+        ProblemData& pr = P->prob[p];
+        size_t cand_off = 0;
+        const size_t need = resident_bytes(P, pr, &cand_off);
+        if (p > w0 && (acc + need > budget || pr.mixed != P->prob[w0].mixed)) {
+            P->waves.emplace_back(w0, p);
+            w0 = p;
+            acc = 0;
+        }
+        pr.res_corr_off = kHeader + acc;
+        pr.res_cand_off = kHeader + acc + cand_off;
+        acc += need;
+        largest = std::max(largest, acc);
+    }
+    P->waves.emplace_back(w0, np);
+    P->wave_scratch_off = kHeader + largest;
+}
+
 ttm_status check_ws(const ttm_plan_s* P, void* ws, size_t bytes) {
     if (!ws || bytes < P->ws_bytes) return TTM_ERR_WORKSPACE;
     if (!aligned(ws, 256)) return TTM_ERR_INVALID_ARG;
@@ -501,19 +581,44 @@ ttm_status prefilter(ttm_plan_s* plan, const ProblemData& pr, const float* vol, 
     return TTM_OK;
 }
 
+// problems a and b read the same volume (same pointer, no prefilter, same
+// extents and FFT box)
+bool same_volume(const ttm_plan_s* P, int a, int b, const float* const* d_vols) {
+    const ProblemData &x = P->prob[a], &y = P->prob[b];
+    return d_vols[a] == d_vols[b] && !(P->opts.lowpass_sigma > 0.f) && x.X == y.X &&
+           x.Y == y.Y && x.Z == y.Z && x.fft.Xp == y.fft.Xp && x.fft.Yp == y.fft.Yp &&
+           x.fft.Zp == y.fft.Zp;
+}
+
+bool stats_on_fft(const ProblemData& pr) {
+    return pr.path == TTM_PATH_FFT && fft_template_length(pr.fft.Xp);
+}
+
+// What the previous problem of a ttm_local_stats call left in the workspace
+// for this one (same volume): nothing, the volume's moments, or the moments
+// and the spectra of f - mean and (f - mean)^2 (same FFT box, FFT sums).
+enum StatsReuse { kReuseNone = 0, kReuseMoments = 1, kReuseSpectra = 2 };
+
 // w for one problem (Algorithm 1, image block): FFT window sums when the
 // problem takes the FFT path with a compile-time x length, else run sums.
 ttm_status stats_problem(ttm_plan_s* plan, const ProblemData& pr, const float* vol, float* w,
-                         void* d_workspace, cudaStream_t st) {
+                         void* d_workspace, cudaStream_t st, int reuse = kReuseNone) {
     // header: sum f, sum f^2, sum (f - mean)^4, flagged-window counter
     double* d_mom = (double*)d_workspace;
     unsigned int* d_flagged = (unsigned int*)((char*)d_workspace + 24);
-    TTM_CUDA_TRY(cudaMemsetAsync(d_mom, 0, 4 * sizeof(double), st));
-    TTM_TRY(timed(plan, KC_MOMENTS, st, [&] {
-        return launch_volume_moments(vol, pr.nvox(), d_mom, st, &plan->launches);
-    }));
+    if (reuse == kReuseNone) {
+        TTM_CUDA_TRY(cudaMemsetAsync(d_mom, 0, 4 * sizeof(double), st));
+        TTM_TRY(timed(plan, KC_MOMENTS, st, [&] {
+            return launch_volume_moments(vol, pr.nvox(), d_mom, st, &plan->launches);
+        }));
+    } else if (reuse == kReuseMoments) {
+        // the fourth moment comes with the spectra: zero it and the counter
+        TTM_CUDA_TRY(cudaMemsetAsync(d_mom + 2, 0, 2 * sizeof(double), st));
+    } else {
+        TTM_CUDA_TRY(cudaMemsetAsync(d_flagged, 0, sizeof(unsigned int), st));
+    }
     const TemplateData& T = plan->tmpl[pr.tmpl];
-    if (pr.path == TTM_PATH_FFT && fft_template_length(pr.fft.Xp)) {
+    if (stats_on_fft(pr)) {
         // window sums of (f - mean) and (f - mean)^2 as correlations with the mask
         const size_t nspec = pr.fft.nspec();
         char* base = (char*)d_workspace + kHeader;
@@ -523,10 +628,12 @@ ttm_status stats_problem(ttm_plan_s* plan, const ProblemData& pr, const float* v
         float* sums = (float*)(prod + 2 * nspec);        // S1, S2 maps
         const float2* mspec = plan->specs[pr.spec_index].d_mask_spec;
         return timed(plan, KC_LOCAL_STATS, st, [&] {
-            TTM_TRY(launch_fft_forward(vol, pr.X, pr.Y, pr.Z, pr.fft, F1, st, &plan->launches, 1,
-                                       d_mom));
-            TTM_TRY(launch_fft_forward(vol, pr.X, pr.Y, pr.Z, pr.fft, F2, st, &plan->launches, 2,
-                                       d_mom));
+            if (reuse != kReuseSpectra) {
+                TTM_TRY(launch_fft_forward(vol, pr.X, pr.Y, pr.Z, pr.fft, F1, st,
+                                           &plan->launches, 1, d_mom));
+                TTM_TRY(launch_fft_forward(vol, pr.X, pr.Y, pr.Z, pr.fft, F2, st,
+                                           &plan->launches, 2, d_mom));
+            }
             // the sums are read on the interior only
             const FftKeep keep = fft_keep_interior(pr.X, pr.Y, pr.Z, T.desc.s);
             TTM_TRY(launch_fft_spectrum_inverse_z(F1, mspec, 1, pr.fft, prod, keep, st,
@@ -550,18 +657,22 @@ ttm_status stats_problem(ttm_plan_s* plan, const ProblemData& pr, const float* v
 }
 
 // The K correlation maps of one problem into the workspace (FFT or direct).
+// With spec_ready the image spectrum is already in place: the previous
+// problem of the call took the same volume through the same FFT box.
 ttm_status corr_problem(ttm_plan_s* plan, const ProblemData& pr, const float* vol,
-                        void* d_workspace, cudaStream_t st) {
-    float* corr = (float*)((char*)d_workspace + kHeader);
+                        void* d_workspace, cudaStream_t st, bool resident = false,
+                        bool spec_ready = false) {
+    const CorrLayout L = corr_layout(plan, pr, d_workspace, resident);
+    float* corr = (float*)L.corr;
     if (pr.path == TTM_PATH_FFT) {
-        const size_t es = pr.mixed ? 2 : 4;
-        char* base = (char*)corr + align256((size_t)plan->K * pr.nvox() * es);
-        float2* spec = (float2*)base;
-        void* prod = base + align256(pr.fft.nspec() * sizeof(float2));
+        float2* spec = (float2*)L.spec;
+        void* prod = L.prod;
         const SpecSet& sp = plan->specs[pr.spec_index];
-        TTM_TRY(timed(plan, KC_FFT_FORWARD, st, [&] {
-            return launch_fft_forward(vol, pr.X, pr.Y, pr.Z, pr.fft, spec, st, &plan->launches);
-        }));
+        if (!spec_ready)
+            TTM_TRY(timed(plan, KC_FFT_FORWARD, st, [&] {
+                return launch_fft_forward(vol, pr.X, pr.Y, pr.Z, pr.fft, spec, st,
+                                          &plan->launches);
+            }));
         const int G = comp_group(plan, pr);
         const size_t nspec = pr.fft.nspec();
         // the score, rotation and component outputs read the interior only
@@ -617,8 +728,9 @@ ttm_status corr_problem(ttm_plan_s* plan, const ProblemData& pr, const float* vo
 ttm_status rotation_problem(ttm_plan_s* plan, const ProblemData& pr, const float* w, float* score,
                             float* quat, float* lam, float* comp_out, void* d_workspace,
                             cudaStream_t st) {
-    float* corr = (float*)((char*)d_workspace + kHeader);
-    uint16_t* cand = (uint16_t*)((char*)corr + corr_region_bytes(plan, pr));
+    const CorrLayout L = corr_layout(plan, pr, d_workspace, false);
+    float* corr = (float*)L.corr;
+    uint16_t* cand = L.cand;
     int* d_status = (int*)((char*)d_workspace + 32);
     const TemplateData& T = plan->tmpl[pr.tmpl];
     const VoxBox box = interior_box(pr.X, pr.Y, pr.Z, T.desc.s);
@@ -664,6 +776,101 @@ ttm_status rotation_problem(ttm_plan_s* plan, const ProblemData& pr, const float
                                           u1, plan->grid, cand, score, quat, lam, comp_out,
                                           plan->s_lo, &plan->launches);
         }));
+    }
+    TTM_CUDA_TRY(cudaEventRecord(plan->ev_join, plan->s_lo));
+    TTM_CUDA_TRY(cudaStreamWaitEvent(st, plan->ev_join, 0));
+    return TTM_OK;
+}
+
+// Score, rotation search and refinement of the problems [p0, p1) of one
+// resident wave (their correlation maps all in the workspace).  The interior
+// units of the wave, problem after problem in tiles of 128, are split into
+// rot_chunks ranges; each range is one search launch and one refinement
+// launch over a table of (problem, units) segments in the kernels'
+// parameters (a range that spans more than kMaxRotSegs problems takes one
+// more launch per kMaxRotSegs), pipelined on the rotation streams as in
+// rotation_problem.  The problems of a wave share the map type.
+ttm_status rotation_wave(ttm_plan_s* plan, int p0, int p1, const float* const* d_w,
+                         float* const* d_score, float* const* d_quat, float* const* d_lambda,
+                         float* const* d_comp, void* d_workspace, cudaStream_t st) {
+    const int n = p1 - p0;
+    int* d_status = (int*)((char*)d_workspace + 32);
+    const bool mixed = plan->prob[p0].mixed;
+    std::vector<RotSeg> segs((size_t)n);
+    std::vector<size_t> tile0((size_t)n + 1, 0);
+    for (int j = 0; j < n; ++j) {
+        const int p = p0 + j;
+        const ProblemData& pr = plan->prob[p];
+        if (pr.mixed != mixed) return TTM_ERR_UNSUPPORTED;
+        const CorrLayout L = corr_layout(plan, pr, d_workspace, true);
+        const VoxBox box = interior_box(pr.X, pr.Y, pr.Z, plan->tmpl[pr.tmpl].desc.s);
+        const size_t units = box.count();
+        if (units > 0xFFFFFFFFull) return TTM_ERR_UNSUPPORTED;
+        float* lam = d_lambda ? d_lambda[p] : nullptr;
+        float* comp = d_comp ? d_comp[p] : nullptr;
+        TTM_TRY(timed(plan, KC_EXTERIOR, st, [&] {
+            return launch_exterior_fill(pr.Z, box, plan->K, d_score[p], d_quat[p], lam, comp, st,
+                                        &plan->launches);
+        }));
+        RotSeg& sg = segs[(size_t)j];
+        sg.corr = L.corr; sg.w = d_w[p]; sg.score = d_score[p]; sg.cand = L.cand;
+        sg.quat = d_quat[p]; sg.lambda = lam; sg.comp_out = comp;
+        sg.nvox = pr.nvox(); sg.box = box; sg.u0 = 0; sg.u1 = (uint32_t)units;
+        tile0[(size_t)j + 1] = tile0[(size_t)j] + (units + kRotTile - 1) / kRotTile;
+    }
+    const size_t tiles = tile0[(size_t)n];
+    if (tiles == 0) return TTM_OK;
+    // the launches of the tile range [a, b)
+    std::vector<RotBatch> bl;
+    auto batches = [&](size_t a, size_t b) {
+        bl.clear();
+        RotBatch cur;
+        for (int j = 0; j < n; ++j) {
+            const size_t lo = std::max(a, tile0[(size_t)j]), hi = std::min(b, tile0[(size_t)j + 1]);
+            if (lo >= hi) continue;
+            RotSeg sg = segs[(size_t)j];
+            sg.u0 = (uint32_t)((lo - tile0[(size_t)j]) * kRotTile);
+            sg.u1 = (uint32_t)std::min<size_t>(segs[(size_t)j].u1, (hi - tile0[(size_t)j]) * kRotTile);
+            if (!cur.add(sg)) {
+                bl.push_back(cur);
+                cur = RotBatch();
+                cur.add(sg);
+            }
+        }
+        if (cur.n) bl.push_back(cur);
+    };
+    auto search = [&](cudaStream_t s) {
+        for (const RotBatch& b : bl)
+            TTM_TRY(timed(plan, KC_ROTATION, s, [&] {
+                return launch_rotation_search(plan->n_order, b, mixed, plan->grid, d_status, s,
+                                              &plan->launches);
+            }));
+        return TTM_OK;
+    };
+    auto polish = [&](cudaStream_t s) {
+        for (const RotBatch& b : bl)
+            TTM_TRY(timed(plan, KC_POLISH, s, [&] {
+                return launch_rotation_polish(plan->n_order, b, mixed, plan->grid, s,
+                                              &plan->launches);
+            }));
+        return TTM_OK;
+    };
+    int nch = plan->rot_chunks;
+    if ((size_t)nch * 152 > tiles) nch = 1;               // too small to split
+    if (nch <= 1 || !plan->s_hi) {
+        batches(0, tiles);
+        TTM_TRY(search(st));
+        return polish(st);
+    }
+    TTM_CUDA_TRY(cudaEventRecord(plan->ev_fork, st));
+    TTM_CUDA_TRY(cudaStreamWaitEvent(plan->s_hi, plan->ev_fork, 0));
+    TTM_CUDA_TRY(cudaStreamWaitEvent(plan->s_lo, plan->ev_fork, 0));
+    for (int c = 0; c < nch; ++c) {
+        batches(tiles * (size_t)c / (size_t)nch, tiles * (size_t)(c + 1) / (size_t)nch);
+        TTM_TRY(search(plan->s_hi));
+        TTM_CUDA_TRY(cudaEventRecord(plan->ev_chunk[c], plan->s_hi));
+        TTM_CUDA_TRY(cudaStreamWaitEvent(plan->s_lo, plan->ev_chunk[c], 0));
+        TTM_TRY(polish(plan->s_lo));
     }
     TTM_CUDA_TRY(cudaEventRecord(plan->ev_join, plan->s_lo));
     TTM_CUDA_TRY(cudaStreamWaitEvent(st, plan->ev_join, 0));
@@ -938,7 +1145,7 @@ ttm_status ttm_plan(ttm_plan_t* out, int n_problems, const int* vol_dims, const 
         if (o.path < TTM_PATH_AUTO || o.path > TTM_PATH_TUNE) return TTM_ERR_INVALID_ARG;
         if (o.precision != TTM_PREC_FP32 && o.precision != TTM_PREC_MIXED) return TTM_ERR_INVALID_ARG;
         if (o.n_grid < 0 || o.n_cells < 0 || o.n_candidates < 0 || o.newton_steps < 0 ||
-            o.rotation_chunks < 0 || o.n_refined < 0)
+            o.rotation_chunks < 0 || o.n_refined < 0 || o.batch_mib < 0 || o.batch_mib > (1 << 20))
             return TTM_ERR_INVALID_ARG;
         const int n = o.n_grid > 0 ? o.n_grid : 2048, nc = o.n_cells > 0 ? o.n_cells : n / 16;
         if (n > 65535 || nc > n || n % nc != 0 || o.n_candidates > 8 || o.newton_steps > 64 ||
@@ -1007,6 +1214,21 @@ ttm_status ttm_plan(ttm_plan_t* out, int n_problems, const int* vol_dims, const 
         if (s_ != TTM_OK) { free_plan(P); return s_; }
     }
     const bool lp = P->opts.lowpass_sigma > 0.f;
+    if (P->opts.batch_mib > 0 && n_problems > 1) {
+        plan_waves(P);
+        // the prefiltered volume and its scratch sit after every problem's
+        // scratch and the resident waves
+        size_t end = P->wave_scratch_off + wave_scratch_bytes(P);
+        size_t lpb = 0;
+        for (const ProblemData& pr : P->prob) {
+            end = std::max(end, kHeader + align256(scratch_bytes(P, pr)));
+            lpb = std::max(lpb, lp ? 2 * align256(pr.nvox() * sizeof(float)) : 0);
+        }
+        for (ProblemData& pr : P->prob) pr.lp_off = end;
+        P->ws_bytes = end + lpb;
+        *out = P;
+        return TTM_OK;
+    }
     for (ProblemData& pr : P->prob) {
         // the prefiltered volume and its scratch sit after the problem's scratch
         const size_t sb = align256(scratch_bytes(P, pr));
@@ -1063,6 +1285,14 @@ ttm_status ttm_plan_launch_count(ttm_plan_t plan, long long* launches) {
     return TTM_OK;
 }
 
+ttm_status ttm_plan_waves(ttm_plan_t plan, int* n_waves, int* first) {
+    if (!plan || !n_waves) return TTM_ERR_INVALID_ARG;
+    *n_waves = (int)plan->waves.size();
+    if (first)
+        for (size_t i = 0; i < plan->waves.size(); ++i) first[i] = plan->waves[i].first;
+    return TTM_OK;
+}
+
 ttm_status ttm_plan_device_status(ttm_plan_t plan, void* d_workspace, size_t workspace_bytes,
                                   void* stream) {
     if (!plan) return TTM_ERR_INVALID_ARG;
@@ -1109,7 +1339,7 @@ const char* ttm_kernel_class_name(int c) {
     static const char* names[TTM_KERNEL_CLASSES] = {
         "volume_moments", "local_stats", "direct_corr", "rotation_search", "fft_forward",
         "fft_spectrum_inverse", "fft_inverse", "peaks", "template", "fft_plan", "rotation_polish",
-        "exterior_fill"};
+        "exterior_fill", "rotation_stage"};
     if (c < 0 || c >= TTM_KERNEL_CLASSES) return "unknown";
     return names[c];
 }
@@ -1127,10 +1357,18 @@ ttm_status ttm_local_stats(ttm_plan_t plan, const float* const* d_vols, float* c
         if (!d_vols[p] || !d_w[p] || !aligned(d_vols[p], 4) || !aligned(d_w[p], 4))
             return TTM_ERR_INVALID_ARG;
     cudaStream_t st = (cudaStream_t)stream;
+    TTM_CUDA_TRY(cudaMemsetAsync((char*)d_workspace + 32, 0, sizeof(int), st));  // status word
     for (int p = 0; p < np; ++p) {
+        const ProblemData& pr = plan->prob[p];
+        // consecutive problems of one volume share its moments and, on one
+        // FFT box, the spectra of its window sums
+        int reuse = kReuseNone;
+        if (p > 0 && same_volume(plan, p - 1, p, d_vols))
+            reuse = stats_on_fft(plan->prob[p - 1]) && stats_on_fft(pr) ? kReuseSpectra
+                                                                         : kReuseMoments;
         const float* vol = nullptr;
-        TTM_TRY(prefilter(plan, plan->prob[p], d_vols[p], d_workspace, st, &vol));
-        TTM_TRY(stats_problem(plan, plan->prob[p], vol, d_w[p], d_workspace, st));
+        TTM_TRY(prefilter(plan, pr, d_vols[p], d_workspace, st, &vol));
+        TTM_TRY(stats_problem(plan, pr, vol, d_w[p], d_workspace, st, reuse));
     }
     return TTM_OK;
 }
@@ -1149,15 +1387,39 @@ ttm_status ttm_correlate(ttm_plan_t plan, const float* const* d_vols, const floa
     }
     cudaStream_t st = (cudaStream_t)stream;
     TTM_CUDA_TRY(cudaMemsetAsync((char*)d_workspace + 32, 0, sizeof(int), st));
+    // the image spectrum of the previous problem serves the next one when
+    // both take the same volume through the same FFT box
+    auto spec_ready = [&](int p) {
+        if (p == 0 || !same_volume(plan, p - 1, p, d_vols)) return false;
+        const ProblemData &a = plan->prob[p - 1], &b = plan->prob[p];
+        return a.path == TTM_PATH_FFT && b.path == TTM_PATH_FFT && a.mixed == b.mixed;
+    };
+    if (!plan->waves.empty()) {
+        for (const auto& wv : plan->waves) {
+            for (int p = wv.first; p < wv.second; ++p) {
+                const float* vol = nullptr;
+                TTM_TRY(prefilter(plan, plan->prob[p], d_vols[p], d_workspace, st, &vol));
+                TTM_TRY(corr_problem(plan, plan->prob[p], vol, d_workspace, st, true,
+                                     spec_ready(p)));
+            }
+            TTM_TRY(timed(plan, KC_ROT_STAGE, st, [&] {
+                return rotation_wave(plan, wv.first, wv.second, d_w, d_score, d_quat, d_lambda,
+                                     d_components_out, d_workspace, st);
+            }));
+        }
+        return TTM_OK;
+    }
     for (int p = 0; p < np; ++p) {
         const ProblemData& pr = plan->prob[p];
         const float* vol = nullptr;
         TTM_TRY(prefilter(plan, pr, d_vols[p], d_workspace, st, &vol));
-        TTM_TRY(corr_problem(plan, pr, vol, d_workspace, st));
-        TTM_TRY(rotation_problem(plan, pr, d_w[p], d_score[p], d_quat[p],
-                                 d_lambda ? d_lambda[p] : nullptr,
-                                 d_components_out ? d_components_out[p] : nullptr, d_workspace,
-                                 st));
+        TTM_TRY(corr_problem(plan, pr, vol, d_workspace, st, false, spec_ready(p)));
+        TTM_TRY(timed(plan, KC_ROT_STAGE, st, [&] {
+            return rotation_problem(plan, pr, d_w[p], d_score[p], d_quat[p],
+                                    d_lambda ? d_lambda[p] : nullptr,
+                                    d_components_out ? d_components_out[p] : nullptr,
+                                    d_workspace, st);
+        }));
     }
     return TTM_OK;
 }

@@ -55,6 +55,9 @@ struct ProblemData {
     int spec_index = -1;               // template spectra set used (FFT path)
     double tune_ms[2] = {-1.0, -1.0};  // autotuner: direct, FFT (ms), -1 = not timed
     size_t lp_off = 0;                 // workspace offset of the prefiltered volume (+ scratch)
+    // resident waves (plan option batch_mib): workspace offsets of this
+    // problem's correlation maps and search candidates
+    size_t res_corr_off = 0, res_cand_off = 0;
     size_t nvox() const { return (size_t)X * Y * Z; }
 };
 
@@ -95,6 +98,42 @@ struct UnitList {
     int out_stride = 0;
 };
 
+// One problem's share of a rotation launch: its correlation maps, w, search
+// candidates and output maps, and the interior units [u0, u1) the launch
+// visits, which occupy tiles tile0, tile0 + 1, ... of the launch's tile space
+// (tiles of 128 units; a tile never spans two problems).
+struct RotSeg {
+    const void* corr = nullptr;   // K x nvox, float or bf16
+    const float* w = nullptr;
+    float* score = nullptr;
+    uint16_t* cand = nullptr;     // 8 candidate grid indices per unit
+    float* quat = nullptr;        // 4 x nvox
+    float* lambda = nullptr;      // nullable
+    float* comp_out = nullptr;    // nullable, K x nvox
+    size_t nvox = 0;
+    VoxBox box;
+    uint32_t u0 = 0, u1 = 0, tile0 = 0, pad = 0;
+};
+
+// The problems of one rotation launch, in tile order; one launch serves up to
+// kMaxRotSegs problems (the table travels in the kernel's parameters).
+constexpr int kMaxRotSegs = 24;
+constexpr int kRotTile = 128;
+struct RotBatch {
+    int n = 0;
+    uint32_t ntiles = 0;          // tiles of all segments
+    RotSeg seg[kMaxRotSegs];
+    // appends units [u0, u1) of a problem; false when the table is full
+    bool add(const RotSeg& s) {
+        if (n == kMaxRotSegs) return false;
+        seg[n] = s;
+        seg[n].tile0 = ntiles;
+        ntiles += (s.u1 - s.u0 + kRotTile - 1) / kRotTile;
+        ++n;
+        return true;
+    }
+};
+
 inline VoxBox interior_box(int X, int Y, int Z, int s) {
     VoxBox b;
     b.X = X; b.Y = Y;
@@ -132,7 +171,8 @@ struct RotGrid {
 namespace ttm {
 enum KernelClass {
     KC_MOMENTS = 0, KC_LOCAL_STATS, KC_DIRECT_CORR, KC_ROTATION, KC_FFT_FORWARD, KC_FFT_SPECTRUM,
-    KC_FFT_INVERSE, KC_PEAKS, KC_TEMPLATE, KC_FFT_PLAN, KC_POLISH, KC_EXTERIOR
+    KC_FFT_INVERSE, KC_PEAKS, KC_TEMPLATE, KC_FFT_PLAN, KC_POLISH, KC_EXTERIOR,
+    KC_ROT_STAGE   // span of a whole score/rotation stage (not a kernel)
 };
 struct TimedLaunch {
     int cls;
@@ -151,6 +191,11 @@ struct ttm_plan_s {
     std::vector<ttm::SpecSet> specs;
     std::vector<std::pair<int, float2*>> twiddles;   // length -> device table
     size_t ws_bytes = 0;
+    // resident waves: problem ranges [first, second) whose correlation maps
+    // are in the workspace together, and the offset of the spectra scratch
+    // after them (empty: one problem at a time)
+    std::vector<std::pair<int, int>> waves;
+    size_t wave_scratch_off = 0;
     long long launches = 0;
     bool timing = false;
     std::vector<ttm::TimedLaunch> timed;   // pending event pairs
@@ -215,6 +260,17 @@ ttm_status launch_rotation_polish(int n_order, const void* corr, bool bf16, cons
                                   const RotGrid& g, const uint16_t* cand, const float* score,
                                   float* quat, float* lambda, float* comp_out, cudaStream_t st,
                                   long long* cnt, const UnitList& list = UnitList());
+// The same over a batch of problems: one launch visits the units of every
+// segment of b (all with the same map type); a unit list needs b.n == 1.
+ttm_status launch_rotation_search(int n_order, const RotBatch& b, bool bf16, const RotGrid& g,
+                                  int* status, cudaStream_t st, long long* cnt,
+                                  const UnitList& list = UnitList());
+ttm_status launch_rotation_polish(int n_order, const RotBatch& b, bool bf16, const RotGrid& g,
+                                  cudaStream_t st, long long* cnt,
+                                  const UnitList& list = UnitList());
+RotBatch one_problem_batch(const void* corr, const float* w, size_t nvox, const VoxBox& box,
+                           uint32_t u0, uint32_t u1, uint16_t* cand, float* score, float* quat,
+                           float* lambda, float* comp_out);
 // score = ||w Corr||_F at the interior voxels, 0 outside (no rotation)
 ttm_status launch_score_only(int n_order, const void* corr, bool bf16, const float* w, int X,
                              int Y, int Z, const VoxBox& box, float* score, cudaStream_t st,

@@ -94,13 +94,15 @@ def test_null_and_invalid_arguments_are_rejected_on_host(lib):
     for field, value in (("path", 4), ("path", -1), ("precision", 2), ("n_grid", 70000),
                          ("n_grid", 1000), ("n_cells", 3000), ("n_candidates", 9),
                          ("newton_steps", 65), ("rotation_chunks", -1), ("n_cells", -4),
-                         ("lowpass_sigma", 9.0)):
+                         ("lowpass_sigma", 9.0), ("n_refined", 5), ("batch_mib", -1),
+                         ("batch_mib", (1 << 20) + 1)):
         o_ = ttm.PlanOpts()
         setattr(o_, field, value)
         assert lib.ttm_plan(ctypes.byref(handle), 1, dims, tix, 1, ctypes.byref(d), ptrs, ptrs,
                             ctypes.byref(o_), None) == -1, (field, value)
     # calls on a null plan
     n = ctypes.c_int()
+    assert lib.ttm_plan_waves(None, ctypes.byref(n), None) == -1
     assert lib.ttm_local_stats(None, None, None, None, 0, None) == -1
     assert lib.ttm_correlate(None, None, None, None, None, None, None, None, 0, None) == -1
     assert lib.ttm_extract_peaks(None, 0, None, None, None, 0.0, 1, 1, None, ctypes.byref(n),
