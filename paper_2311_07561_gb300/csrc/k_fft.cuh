@@ -863,8 +863,8 @@ cudaError_t run_rows_c2r(const PS* prod, int X, int Y, int Z, FftGeom g, RT* cor
                          const float2* tw, int* status, FftKeep keep, cudaStream_t st) {
     if constexpr (c2r_half<L>()) {
         constexpr int L1 = RowSplit<L / 2>::L1, L2 = RowSplit<L / 2>::L2;
-        constexpr int NR = kTwoThreads / L1;
-        constexpr size_t smem = two_rows_smem<L1, L2>();
+        constexpr int NR = kTwoThreads / L1 * c2r_groups<L1, L2, PS>();   // rows per tile
+        constexpr size_t smem = c2r_half_smem<L1, L2, PS>();
         auto kern = rows_c2r_half_t<L1, L2, PS, RT>;
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)smem);

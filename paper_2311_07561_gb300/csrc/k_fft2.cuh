@@ -408,21 +408,59 @@ template <> struct RowSplit<480> { static constexpr int L1 = 32, L2 = 15; };
 // split of the fused multiply's z lines (the column passes' split by default)
 template <int L> struct MulSplit { static constexpr int L1 = TwoLevel<L>::L1, L2 = TwoLevel<L>::L2; };
 
+// row groups per tile of the half-length row pass: two when one group's
+// second-step items (NR rows x L2) would leave threads idle and the samples
+// are bf16 pairs (two groups of FP32 samples do not fit the registers)
+template <int L1, int L2, typename PS> constexpr int c2r_groups() {
+    return sizeof(PS) == 4 && (kTwoThreads / L1) * L2 < kTwoThreads ? 2 : 1;
+}
+template <int L1, int L2, typename PS> constexpr size_t c2r_half_smem() {
+    return (size_t)c2r_groups<L1, L2, PS>() * two_rows_smem<L1, L2>();
+}
+
+// the sample of lane src of a row's L1 lanes (a row is one warp or half of one)
+template <int W>
+__device__ __forceinline__ float2 shfl_row(float2 v, int src) {
+    return make_float2(__shfl_sync(0xffffffffu, v.x, src, W), __shfl_sync(0xffffffffu, v.y, src, W));
+}
+template <int W>
+__device__ __forceinline__ __nv_bfloat162 shfl_row(__nv_bfloat162 v, int src) {
+    unsigned u;
+    memcpy(&u, &v, sizeof(u));
+    u = __shfl_sync(0xffffffffu, u, src, W);
+    memcpy(&v, &u, sizeof(u));
+    return v;
+}
+
+// two adjacent real outputs in one store (p aligned to two elements)
+__device__ __forceinline__ void str2(float* p, float a, float b) {
+    *reinterpret_cast<float2*>(p) = make_float2(a, b);
+}
+__device__ __forceinline__ void str2(__nv_bfloat16* p, float a, float b) {
+    *reinterpret_cast<__nv_bfloat162*>(p) = __floats2bfloat162_rn(a, b);
+}
+
+// A tile is NG groups of NR rows.  Thread (row, n1) holds X[n1 + L1 n2] of
+// its row; X[M - k] of its sample k is sample L2 - 1 - n2 of lane L1 - n1 of
+// the same row (sample L2 - n2 of lane 0, or X[M], for lane 0), read by a
+// shuffle.  The outputs z[m] = (y[2m], y[2m + 1]) are stored as pairs.
 template <int L1, int L2, typename PS, typename RT>
 __global__ void __launch_bounds__(kTwoThreads, two_min_blocks<L2>()) rows_c2r_half_t(
     const PS* __restrict__ in, int X, int Y, int Z, FftGeom g, RT* __restrict__ out, int n_batch,
     const float2* __restrict__ tw, FftKeep keep) {
     constexpr int M = L1 * L2;
-    constexpr int L = 2 * M;
     constexpr int XH = M + 1;
     constexpr int NR = kTwoThreads / L1;
+    constexpr int NG = c2r_groups<L1, L2, PS>();
     constexpr int ZP = L1 + 1;
-    extern __shared__ float2 zx[];                    // [row][k2][n1 (padded)]
+    static_assert(L1 == 16 || L1 == 32, "a row is one warp or half of one");
+    extern __shared__ float2 zx[];                    // [group row][k2][n1 (padded)]
     const int t = threadIdx.x;
     const int ra = t / L1, n1 = t % L1;
+    const int partner = (L1 - n1) & (L1 - 1);
     const int ny = keep.y1 - keep.y0 + 1, nz = keep.z1 - keep.z0 + 1;
     const size_t nrows = (size_t)n_batch * nz * ny;
-    const size_t ntiles = (nrows + NR - 1) / NR;
+    const size_t ntiles = (nrows + NG * NR - 1) / (NG * NR);
     auto row_of = [&](size_t q, size_t& src_row, long long& dst) {
         const size_t per_item = (size_t)nz * ny;
         const size_t item = q / per_item;
@@ -433,16 +471,27 @@ __global__ void __launch_bounds__(kTwoThreads, two_min_blocks<L2>()) rows_c2r_ha
         dst = (y < Y && z < Z) ? (long long)(item * ((size_t)X * Y * Z) + ((size_t)z * Y + y) * X)
                                : -1;
     };
-    PS raw[L2];
-    auto load = [&](size_t tile) {
-        const size_t q = tile * NR + ra;
-        if (q < nrows) {
-            size_t src;
-            long long dst;
-            row_of(q, src, dst);
-            const PS* rowp = in + src * XH;
+    PS raw[NG][L2];
+    PS xm[NG];                                        // X[M] of the row
 #pragma unroll
-            for (int n2 = 0; n2 < L2; ++n2) raw[n2] = rowp[n1 + L1 * n2];
+    for (int h = 0; h < NG; ++h) {
+        memset(&xm[h], 0, sizeof(PS));
+#pragma unroll
+        for (int n2 = 0; n2 < L2; ++n2) memset(&raw[h][n2], 0, sizeof(PS));
+    }
+    auto load = [&](size_t tile) {
+#pragma unroll
+        for (int h = 0; h < NG; ++h) {
+            const size_t q = (tile * NG + h) * NR + ra;
+            if (q < nrows) {
+                size_t src;
+                long long dst;
+                row_of(q, src, dst);
+                const PS* rowp = in + src * XH;
+#pragma unroll
+                for (int n2 = 0; n2 < L2; ++n2) raw[h][n2] = rowp[n1 + L1 * n2];
+                xm[h] = rowp[M];
+            }
         }
     };
     size_t tile = blockIdx.x;
@@ -450,43 +499,43 @@ __global__ void __launch_bounds__(kTwoThreads, two_min_blocks<L2>()) rows_c2r_ha
     load(tile);
     const int xk0 = keep.x0, xk1 = min(keep.x1, X - 1);
     for (; tile < ntiles; tile += gridDim.x) {
-        const size_t qa = tile * NR + ra;
-        const bool in_a = qa < nrows;
-        size_t src_a = 0;
-        long long dst_a;
-        if (in_a) row_of(qa, src_a, dst_a);
-        const PS* rowa = in + src_a * XH;
-        float2 v[L2];
+        __syncthreads();                               // the previous tile's reads are done
 #pragma unroll
-        for (int n2 = 0; n2 < L2; ++n2) {
-            const int k = n1 + L1 * n2;
-            float2 zk = make_float2(0.f, 0.f);
-            if (in_a) {
-                const float2 a = ldc(&raw[n2]);
-                float2 b = ldc(rowa + (M - k));
-                b.y = -b.y;                            // conj X[M - k]
-                float2 w = __ldg(tw + k);
-                w.y = -w.y;                            // W_L^(-k)
-                const float2 d = cmul(csub(a, b), w);
-                zk = make_float2(a.x + b.x - d.y, a.y + b.y + d.x);   // (a + b) + i d
+        for (int h = 0; h < NG; ++h) {
+            const bool in_a = (tile * NG + h) * NR + ra < nrows;
+            float2 v[L2];
+#pragma unroll
+            for (int n2 = 0; n2 < L2; ++n2) {
+                const int k = n1 + L1 * n2;
+                PS mb = shfl_row<L1>(raw[h][L2 - 1 - n2], partner);
+                if (n1 == 0) mb = n2 == 0 ? xm[h] : raw[h][(L2 - n2) % L2];
+                float2 zk = make_float2(0.f, 0.f);
+                if (in_a) {
+                    const float2 a = ldc(&raw[h][n2]);
+                    float2 b = ldc(&mb);
+                    b.y = -b.y;                        // conj X[M - k]
+                    float2 w = __ldg(tw + k);
+                    w.y = -w.y;                        // W_L^(-k)
+                    const float2 d = cmul(csub(a, b), w);
+                    zk = make_float2(a.x + b.x - d.y, a.y + b.y + d.x);   // (a + b) + i d
+                }
+                v[n2] = zk;
             }
-            v[n2] = zk;
+            dft_reg<L2, +1>(v);
+#pragma unroll
+            for (int k2 = 1; k2 < L2; ++k2) {
+                float2 w = __ldg(tw + 2 * n1 * k2);    // W_M^(n1 k2) = W_L^(2 n1 k2)
+                w.y = -w.y;
+                v[k2] = cmul(v[k2], w);
+            }
+#pragma unroll
+            for (int k2 = 0; k2 < L2; ++k2) zx[((h * NR + ra) * L2 + k2) * ZP + n1] = v[k2];
         }
         if (tile + gridDim.x < ntiles) load(tile + gridDim.x);
-        dft_reg<L2, +1>(v);
-#pragma unroll
-        for (int k2 = 1; k2 < L2; ++k2) {
-            float2 w = __ldg(tw + 2 * n1 * k2);        // W_M^(n1 k2) = W_L^(2 n1 k2)
-            w.y = -w.y;
-            v[k2] = cmul(v[k2], w);
-        }
         __syncthreads();
-#pragma unroll
-        for (int k2 = 0; k2 < L2; ++k2) zx[(ra * L2 + k2) * ZP + n1] = v[k2];
-        __syncthreads();
-        for (int it = t; it < NR * L2; it += kTwoThreads) {
+        for (int it = t; it < NG * NR * L2; it += kTwoThreads) {
             const int rb = it / L2, k2 = it % L2;
-            const size_t q = tile * NR + rb;
+            const size_t q = tile * NG * NR + rb;
             if (q >= nrows) continue;
             size_t src;
             long long dst;
@@ -496,11 +545,17 @@ __global__ void __launch_bounds__(kTwoThreads, two_min_blocks<L2>()) rows_c2r_ha
             for (int m = 0; m < L1; ++m) u[m] = zx[(rb * L2 + k2) * ZP + m];
             dft_reg<L1, +1>(u);
             if (dst >= 0) {
+                RT* o = out + dst;
+                const bool pair_ok = (reinterpret_cast<uintptr_t>(o) & (2 * sizeof(RT) - 1)) == 0;
 #pragma unroll
                 for (int k1 = 0; k1 < L1; ++k1) {
                     const int x = 2 * (k2 + L2 * k1);   // z[m] = (y[2m], y[2m+1])
-                    if (x >= xk0 && x <= xk1) str(out + dst + x, u[k1].x);
-                    if (x + 1 >= xk0 && x + 1 <= xk1) str(out + dst + x + 1, u[k1].y);
+                    if (pair_ok && x >= xk0 && x + 1 <= xk1) {
+                        str2(o + x, u[k1].x, u[k1].y);
+                    } else {
+                        if (x >= xk0 && x <= xk1) str(o + x, u[k1].x);
+                        if (x + 1 >= xk0 && x + 1 <= xk1) str(o + x + 1, u[k1].y);
+                    }
                 }
             }
         }
