@@ -76,17 +76,7 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint3
 constexpr uint32_t kIdesc = (1u << 4) | ((uint32_t)(kChunkN >> 3) << 17) | ((128u >> 4) << 24);
 
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t phase) {
-    for (long it = 0; it < kWaitLimit; ++it) {
-        uint32_t done;
-        asm volatile(
-            "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-            "selp.u32 %0, 1, 0, p;\n}\n"
-            : "=r"(done)
-            : "r"(bar), "r"(phase)
-            : "memory");
-        if (done) return true;
-    }
-    return false;
+    return mbar_wait_bounded(bar, phase, kWaitLimit);
 }
 
 // MMAs of one 256-point chunk whose B block (KP/8 x 32 core matrices, K-block
@@ -227,26 +217,37 @@ __device__ __forceinline__ void region_max32(const uint32_t (&r)[32], int low0, 
 }
 
 // Half G (0 or 1) of the KP columns of a voxel's A row: columns
-// G KP/2 .. (G+1) KP/2 - 1 of [w Corr_0 .. w Corr_{K-1}, 1, 0 ...].  Loads
-// them into C (all loads issued before any is used) and returns the half of
-// sum mu_k C_k^2 they carry.
+// G KP/2 .. (G+1) KP/2 - 1 of [w Corr_0 .. w Corr_{K-1}, 1, 0 ...].
+// The raw components of half G of a voxel's A row (all loads issued at
+// once, used a tile later: the next tile's loads are in flight while this
+// tile's epilogue runs)
 template <int N, int G, int KP, typename CT>
-__device__ __forceinline__ float a_half_load(const CT* __restrict__ corr, size_t nvox, size_t v,
-                                             bool in_range, float wv, float (&C)[KP / 2]) {
+__device__ __forceinline__ void a_half_fetch(const CT* __restrict__ corr, size_t nvox, size_t v,
+                                             bool in_range, CT (&raw)[KP / 2]) {
     constexpr int K = n_comp(N);
     constexpr int KH = KP / 2;
-    constexpr Sym<N> S{};
 #pragma unroll
     for (int j = 0; j < KH; ++j) {
         constexpr int k0 = G * KH;
-        C[j] = (in_range && k0 + j < K) ? rot::ldcorr(corr + (size_t)(k0 + j) * nvox + v) : 0.f;
+        raw[j] = (in_range && k0 + j < K) ? __ldg(corr + (size_t)(k0 + j) * nvox + v) : CT(0.f);
     }
+}
+
+// C = w * the fetched components (zero beyond K); returns the half of
+// sum mu_k C_k^2 they carry
+template <int N, int G, int KP, typename CT>
+__device__ __forceinline__ float a_half_finish(const CT (&raw)[KP / 2], float wv,
+                                               float (&C)[KP / 2]) {
+    constexpr int K = n_comp(N);
+    constexpr int KH = KP / 2;
+    constexpr Sym<N> S{};
     float ss = 0.f;
 #pragma unroll
     for (int j = 0; j < KH; ++j) {
         constexpr int k0 = G * KH;
+        C[j] = 0.f;
         if (k0 + j < K) {
-            C[j] *= wv;
+            C[j] = (float)raw[j] * wv;
             ss = fmaf((float)S.mu[k0 + j], C[j] * C[j], ss);
         }
     }
@@ -280,8 +281,11 @@ __device__ __forceinline__ void a_half_store(const float (&C)[KP / 2], float inv
     }
 }
 
+// 168 registers: the next tile's components stay in registers through the
+// epilogue, and one CTA of this kernel (256 threads) still leaves room for a
+// CTA of the refinement kernel (128 threads x 168) on the same SM
 template <typename CT, int N, int G>
-__global__ void __launch_bounds__(kThreads, 1) search_tc_kernel(const __grid_constant__ rot::SearchArgs a,
+__global__ void __maxnreg__(168) search_tc_kernel(const __grid_constant__ rot::SearchArgs a,
                                                                 const uint4* __restrict__ gtab,
                                                                 int* status) {
     using Sh = TcShape<n_comp(N), G>;
@@ -381,26 +385,39 @@ __global__ void __launch_bounds__(kThreads, 1) search_tc_kernel(const __grid_con
     const int lane_t = t & 127;            // TMEM lane = voxel of the tile
     const int grp = t >> 7;                // column group: columns grp * 256 / kGroups ...
     long qbase = 0;                        // chunks issued by this CTA before this tile
-    int sidx = 0;                          // problem of the tile (segments in tile order)
+    // the next tile's problem (segments in tile order), unit, voxel, w and
+    // raw components: threads t and t + 128 share voxel t of the tile, each
+    // fetching half of the KP columns
+    constexpr int KH = KP / 2;
+    int sidx = 0;
+    size_t i_n = 0, v_n = 0;
+    bool in_n = false;
+    float wv_n = 0.f;
+    CT raw[KH];
+    auto fetch = [&](size_t tl) {
+        sidx = rot::seg_of(a.b, (uint32_t)tl, sidx);
+        const RotSeg& sg = a.b.seg[sidx];
+        i_n = sg.u0 + (tl - sg.tile0) * 128 + lane_t;
+        in_n = i_n < rot::list_end(a.list, sg.u1);
+        v_n = in_n ? rot::unit_voxel(sg.box, a.list, (uint32_t)i_n) : 0;
+        wv_n = in_n ? __ldg(sg.w + v_n) : 0.f;
+        const CT* corr = reinterpret_cast<const CT*>(sg.corr);
+        if (grp == 0) a_half_fetch<N, 0, KP>(corr, sg.nvox, v_n, in_n, raw);
+        else a_half_fetch<N, 1, KP>(corr, sg.nvox, v_n, in_n, raw);
+    };
+    if (blockIdx.x < ntiles) fetch(blockIdx.x);
     for (size_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x, qbase += kChunks) {
         const bool more_tiles = tile + gridDim.x < ntiles;
-        sidx = rot::seg_of(a.b, (uint32_t)tile, sidx);
-        const RotSeg& sg = a.b.seg[sidx];
-        const size_t i = sg.u0 + (tile - sg.tile0) * 128 + lane_t;
-        const bool in_range = i < rot::list_end(a.list, sg.u1);
-        const size_t v = in_range ? rot::unit_voxel(sg.box, a.list, (uint32_t)i) : 0;
-        // components, score, normalised FP16 row of A: threads t and t + 128
-        // share voxel t of the tile, each loading and writing half of the KP
-        // columns (all its loads in flight at once); the two halves of the
+        const int cur = sidx;
+        const size_t i = i_n, v = v_n;
+        const bool in_range = in_n;
+        // components, score, normalised FP16 row of A; the two halves of the
         // sum of squares meet in the merge buffer (free until the tile's end)
         float score = 0.f;
         {
-            constexpr int KH = KP / 2;
             float C[KH];
-            const float wv = in_range ? __ldg(sg.w + v) : 0.f;
-            const CT* corr = reinterpret_cast<const CT*>(sg.corr);
-            const float part = grp == 0 ? a_half_load<N, 0, KP>(corr, sg.nvox, v, in_range, wv, C)
-                                        : a_half_load<N, 1, KP>(corr, sg.nvox, v, in_range, wv, C);
+            const float part = grp == 0 ? a_half_finish<N, 0, KP>(raw, wv_n, C)
+                                        : a_half_finish<N, 1, KP>(raw, wv_n, C);
             float* ssx = reinterpret_cast<float*>(merge);
             if (grp == 1) ssx[lane_t] = part;
             __syncthreads();
@@ -419,6 +436,7 @@ __global__ void __launch_bounds__(kThreads, 1) search_tc_kernel(const __grid_con
         asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
         __syncthreads();
         if (t == 0) issue(tmem, 0, qbase, bar0);
+        if (more_tiles) fetch(tile + gridDim.x);      // lands during the epilogue
 
         // packed keys: the float bits of phi + 1 with the low 11 bits replaced
         // by (2047 - grid index): one integer max gives the best point of a
@@ -517,6 +535,7 @@ __global__ void __launch_bounds__(kThreads, 1) search_tc_kernel(const __grid_con
 #pragma unroll
             for (int k = 0; k < rot::kMaxCand; ++k) ti[k] = top[k] == INT_MIN ? 0xFFFF : 2047 - (top[k] & 2047);
             if (in_range) {
+                const RotSeg& sg = a.b.seg[cur];
                 sg.score[v] = score;
                 rot::store_candidates(sg.cand, i, ti, score > 0.f);
             }
