@@ -557,10 +557,12 @@ def a5_flop_per_voxel(K: int) -> float:
 def refinement_flop_per_voxel(K: int, n_cand: int | None = None, newton: int | None = None,
                               refined: int | None = None) -> float:
     """FP32 FLOP of this build's refinement per interior voxel: every candidate
-    takes 3 evaluations of C x^(n-1) (10 ops per term of its 4 sums of KG
-    terms) and 2 normalisations; the refined best take 1 + newton evaluations
-    of C x^(n-2) (10 sums of KB terms) and newton 4x4 solves.  Defaults: the
-    order's budget."""
+    takes 2 normalised power steps, each an evaluation of C x^(n-1) (10 ops
+    per term of its 4 sums of KG terms), plus a third evaluation for phi when
+    the candidates are ranked (more candidates than refined points); each
+    refined point takes 1 + newton evaluations of C x^(n-2) (10 sums of KB
+    terms) and newton 4x4 solves, the last of them an evaluation of
+    C x^(n-1) instead from order 6 on.  Defaults: the order's budget."""
     c0, r0, nw0 = budget(K)
     n_cand = c0 if n_cand is None else n_cand
     newton = nw0 if newton is None else newton
@@ -568,8 +570,11 @@ def refinement_flop_per_voxel(K: int, n_cand: int | None = None, newton: int | N
     n_ord = {10: 2, 35: 4, 84: 6, 165: 8}.get(K, 4)
     KB = (n_ord + 1) * n_ord * (n_ord - 1) // 6
     KG = (n_ord + 2) * (n_ord + 1) * n_ord // 6
-    power = 3 * 10 * KG + 2 * 12
-    newton_part = (1 + newton) * (2 * 10 * KB + 2 * KB + 40) + newton * 150
+    hess = 2 * 10 * KB + 2 * KB + 40
+    power = (3 if n_cand > refined else 2) * 10 * KG + 2 * 12
+    # from order 6 on the last trial is an evaluation of C x^(n-1)
+    last_grad = n_ord >= 6 and newton > 0
+    newton_part = (newton * hess + 10 * KG if last_grad else (1 + newton) * hess) + newton * 150
     return float(n_cand * power + min(refined, n_cand) * newton_part)
 
 

@@ -269,6 +269,16 @@ ttm_status ttm_plan_problem_tensor_direct(ttm_plan_t plan, int problem, int* on)
  * path.  Host-only; TTM_ERR_INVALID_ARG for a bad plan, problem or pointer. */
 ttm_status ttm_plan_problem_fft_box(ttm_plan_t plan, int problem, int* box);
 
+/* Self-check of the bounded device-side waits.  Launches one CTA that waits,
+ * with the poll loop every tensor-core kernel waits with, on an mbarrier
+ * phase: with arrive = 1 the CTA completes that phase itself first; with
+ * arrive = 0 nothing does, so the wait must run out after `polls` polls
+ * (1 .. 2^24).  *status_out receives TTM_OK (the phase completed) or
+ * TTM_ERR_TIMEOUT (the wait ran out).  The kernel returns either way, so the
+ * context stays usable.  Synchronises the stream.  Errors:
+ * TTM_ERR_INVALID_ARG (polls out of range, null status_out), TTM_ERR_CUDA. */
+ttm_status ttm_probe_bounded_wait(long long polls, int arrive, int* status_out, void* stream);
+
 /* Kernel launches the plan has queued so far (for accounting). */
 ttm_status ttm_plan_launch_count(ttm_plan_t plan, long long* launches);
 

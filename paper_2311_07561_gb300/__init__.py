@@ -44,6 +44,7 @@ from ._binding import (  # noqa: F401
     ttm_plan_enable_timing,
     ttm_plan_launch_count,
     ttm_plan_waves,
+    ttm_probe_bounded_wait,
     ttm_plan_problem_path,
     ttm_plan_problem_fft_box,
     ttm_plan_problem_tuning,

@@ -32,7 +32,7 @@ EXPORTED = (
     "ttm_build_tensor_template", "ttm_plan", "ttm_plan_workspace_size",
     "ttm_plan_problem_path", "ttm_plan_problem_fft_box", "ttm_plan_problem_tuning",
     "ttm_plan_problem_tensor_direct",
-    "ttm_plan_launch_count", "ttm_plan_waves", "ttm_plan_destroy",
+    "ttm_plan_launch_count", "ttm_plan_waves", "ttm_probe_bounded_wait", "ttm_plan_destroy",
     "ttm_local_stats", "ttm_correlate", "ttm_extract_peaks", "ttm_match_peaks", "ttm_lowpass",
     "ttm_plan_enable_timing",
     "ttm_plan_timing", "ttm_kernel_class_name", "ttm_build_tensor_template_noalloc",
@@ -96,6 +96,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "ttm_plan_problem_tuning": (I, [P, I, ctypes.POINTER(ctypes.c_double)]),
         "ttm_plan_launch_count": (I, [P, ctypes.POINTER(L)]),
         "ttm_plan_waves": (I, [P, ctypes.POINTER(I), ctypes.POINTER(I)]),
+        "ttm_probe_bounded_wait": (I, [L, I, ctypes.POINTER(I), P]),
         "ttm_plan_destroy": (None, [P]),
         "ttm_local_stats": (I, [P, PP, PP, P, S, P]),
         "ttm_correlate": (I, [P, PP, PP, PP, PP, PP, PP, P, S, P]),
@@ -270,6 +271,16 @@ def ttm_plan_waves(plan: int) -> list:
     first = (ctypes.c_int * max(n.value, 1))()
     _check(lib.ttm_plan_waves(plan, ctypes.byref(n), first), "ttm_plan_waves")
     return list(first)[:n.value]
+
+
+def ttm_probe_bounded_wait(polls: int, arrive: bool, stream=None) -> int:
+    """Status of one bounded device-side wait on an mbarrier phase that the
+    probe completes itself (arrive) or that nothing completes: TTM_OK or
+    TTM_ERR_TIMEOUT."""
+    out = ctypes.c_int()
+    _check(load_library().ttm_probe_bounded_wait(polls, 1 if arrive else 0, ctypes.byref(out),
+                                                 _stream(stream)), "ttm_probe_bounded_wait")
+    return out.value
 
 
 def ttm_plan_destroy(plan: Optional[int]) -> None:

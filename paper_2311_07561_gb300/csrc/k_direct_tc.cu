@@ -35,7 +35,6 @@ namespace {
 constexpr int kThreads = 256;
 constexpr int kStageTaps = 32;                      // taps per A buffer (two MMAs)
 constexpr uint32_t kABytes = 128 * kStageTaps * 2;  // 8 KB
-constexpr long kWaitLimit = 1L << 24;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
     return (uint32_t)__cvta_generic_to_shared(p);
@@ -51,17 +50,7 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint3
 }
 
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t phase) {
-    for (long it = 0; it < kWaitLimit; ++it) {
-        uint32_t done;
-        asm volatile(
-            "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-            "selp.u32 %0, 1, 0, p;\n}\n"
-            : "=r"(done)
-            : "r"(bar), "r"(phase)
-            : "memory");
-        if (done) return true;
-    }
-    return false;
+    return mbar_wait_bounded(bar, phase, kMbarWaitPolls);
 }
 
 __device__ __forceinline__ void tmem_ld8(uint32_t addr, uint32_t (&r)[8]) {

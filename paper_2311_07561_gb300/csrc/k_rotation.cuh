@@ -272,11 +272,11 @@ __device__ __forceinline__ void grad_at(const float (&C)[Geo<N>::K4], const floa
 }
 
 // Two shifted power (SS-HOPM) steps x <- normalise(C x^{N-1} + sigma x) from
-// x (the SS-HOPM step of Kolda & Mayo 2011, monotone for this shift); lam =
-// phi at the point reached.
+// x (the SS-HOPM step of Kolda & Mayo 2011, monotone for this shift); with
+// want_lam, lam = phi at the point reached (one more evaluation).
 template <int N>
 __device__ __forceinline__ void power_steps(const float (&C)[Geo<N>::K4], float sigma, float x[4],
-                                            float& lam) {
+                                            float& lam, bool want_lam) {
     float g[4];
 #pragma unroll 1
     for (int s = 0; s < 2; ++s) {
@@ -285,7 +285,7 @@ __device__ __forceinline__ void power_steps(const float (&C)[Geo<N>::K4], float 
         for (int i = 0; i < 4; ++i) x[i] = g[i] + sigma * x[i];
         normalise4(x);
     }
-    grad_at<N>(C, x, g, lam);
+    if (want_lam) grad_at<N>(C, x, g, lam);
 }
 
 // Riemannian Newton steps on the sphere from x; a trial that lowers phi is
@@ -297,7 +297,7 @@ template <int N>
 __device__ void refine(const float (&C)[Geo<N>::K4], float sigma, int newton, float x[4],
                        float& lam_out) {
     float xa[4] = {x[0], x[1], x[2], x[3]};
-    float Ha[4][4], ga[4], la = -INFINITY;
+    float ga[4], la = -INFINITY;
     float xt[4] = {x[0], x[1], x[2], x[3]};
     bool trial_newton = false;
     const float eps = 1e-6f * sigma;
@@ -305,8 +305,11 @@ __device__ void refine(const float (&C)[Geo<N>::K4], float sigma, int newton, fl
 #pragma unroll 1
     for (int it = 0; it < iters; ++it) {
         float H[4][4], g[4], lam;
-        eval_at<N>(C, xt, H, g, lam);
         const bool last = it + 1 == iters;
+        // the last trial needs only phi: from order 6 on C x^(n-1) (4 sums)
+        // is cheaper than C x^(n-2) (10 sums)
+        if (N >= 6 && last && it > 0) grad_at<N>(C, xt, g, lam);
+        else eval_at<N>(C, xt, H, g, lam);
         if (trial_newton && lam < la - eps) {
             if (last) break;
 #pragma unroll
@@ -319,13 +322,11 @@ __device__ void refine(const float (&C)[Geo<N>::K4], float sigma, int newton, fl
         for (int i = 0; i < 4; ++i) {
             xa[i] = xt[i];
             ga[i] = g[i];
-#pragma unroll
-            for (int j = 0; j < 4; ++j) Ha[i][j] = H[i][j];
         }
         la = lam;
         if (last) break;
         float eta[4];
-        if (newton_dir<N>(Ha, ga, xa, la, sigma, eta)) {
+        if (newton_dir<N>(H, ga, xa, la, sigma, eta)) {
             const float en2 = eta[0] * eta[0] + eta[1] * eta[1] + eta[2] * eta[2] + eta[3] * eta[3];
             const float clip = en2 > 0.0625f ? 0.25f * rsqrtf(en2) : 1.f;
 #pragma unroll
@@ -444,7 +445,10 @@ __global__ void __launch_bounds__(kRotThreads) polish_kernel(const __grid_consta
         const float sigma = (float)(N - 1) * score;
         best_l = -INFINITY;
         // phase 1: two power steps from every candidate; the kRefine best
-        // (by phi at the point reached) are kept, sorted descending
+        // (by phi at the point reached) are kept, sorted descending.  When
+        // every candidate is refined the ranking only orders the refinement:
+        // the candidates keep the search's order and phi is not evaluated
+        const bool rank = a.n_cand > a.n_refine;
         float kl[kRefine], kx[kRefine][4];
 #pragma unroll
         for (int s = 0; s < kRefine; ++s) {
@@ -460,7 +464,8 @@ __global__ void __launch_bounds__(kRotThreads) polish_kernel(const __grid_consta
 #pragma unroll
             for (int i = 0; i < 4; ++i) x[i] = __ldg(a.gq + 4 * gi + i);
             float l;
-            power_steps<N>(C, sigma, x, l);
+            power_steps<N>(C, sigma, x, l, rank);
+            if (!rank) l = -(float)k;
 #pragma unroll
             for (int s = 0; s < kRefine; ++s) {
                 const bool up = l > kl[s];

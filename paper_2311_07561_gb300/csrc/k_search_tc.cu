@@ -40,7 +40,6 @@ constexpr int kThreads = 256;    // warps w and w + 4 read the same TMEM lanes
 constexpr int kGroups = kThreads / 128;    // column groups of a chunk (one per 4 warps)
 constexpr int kChunkN = 256;         // grid points per MMA
 constexpr uint32_t kMergeBytes = (kGroups - 1) * 128 * 8 * 4;  // top-8 keys of groups 1..
-constexpr long kWaitLimit = 1L << 24;   // try_wait polls; well beyond any MMA latency
 
 // Shapes for K tensor components and G grid points (1024 or 2048): padded
 // K, shared-memory sizes, and whether the grid table is resident or streamed.
@@ -76,7 +75,7 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint3
 constexpr uint32_t kIdesc = (1u << 4) | ((uint32_t)(kChunkN >> 3) << 17) | ((128u >> 4) << 24);
 
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t phase) {
-    return mbar_wait_bounded(bar, phase, kWaitLimit);
+    return mbar_wait_bounded(bar, phase, kMbarWaitPolls);
 }
 
 // MMAs of one 256-point chunk whose B block (KP/8 x 32 core matrices, K-block

@@ -126,41 +126,60 @@ constexpr int kFoldThreads = 256;
 constexpr int kFoldJ = 32;        // quadrature nodes staged per step
 constexpr int kFoldA = 40;        // components per pass (registers per thread)
 
-template <int N>
-__global__ void __launch_bounds__(kFoldThreads) fold_kernel(
+// Components A0 .. A0 + kFoldA - 1 (a compile-time range, so the exponent
+// table is indexed by constants and stays out of local memory).
+template <int N, int A0>
+__global__ void __launch_bounds__(kFoldThreads, 2) fold_kernel(
     const float* __restrict__ quats, const float* __restrict__ weights, float inv_nrot, int j0,
-    int nj, const float* __restrict__ rot, int s3, float* __restrict__ comp, int a0, int na,
-    int first) {
+    int nj, const float* __restrict__ rot, int s3, float* __restrict__ comp, int first) {
     constexpr Sym<N> S{};
+    constexpr int K = n_comp(N);
+    constexpr int na = K - A0 < kFoldA ? K - A0 : kFoldA;
+    const int a0 = A0;
     __shared__ __align__(16) float coef[kFoldJ][kFoldA];
     static_assert(kFoldA % 4 == 0, "coefficients are read as float4");
+    static_assert(kFoldJ <= kFoldThreads, "one thread per staged node");
     const int u = blockIdx.x * blockDim.x + threadIdx.x;
     float acc[kFoldA];
 #pragma unroll
     for (int a = 0; a < kFoldA; ++a) acc[a] = 0.0f;
     for (int jb = 0; jb < nj; jb += kFoldJ) {
         __syncthreads();
-        for (int e = threadIdx.x; e < kFoldJ * kFoldA; e += blockDim.x) {
-            int jj = e / kFoldA, a = e % kFoldA;
-            float v = 0.0f;
-            if (jb + jj < nj && a < na) {
-                int j = j0 + jb + jj;
-                float q[4] = {quats[4 * j], quats[4 * j + 1], quats[4 * j + 2], quats[4 * j + 3]};
-                float inv = rsqrtf(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
-                float p = weights ? weights[j] : inv_nrot;
-                const int k = a0 + a;
+        if (threadIdx.x < kFoldJ) {
+            // thread jj: w_j q_j^alpha of its node for the pass's components
+            const int jj = threadIdx.x;
+            const bool live = jb + jj < nj;
+            const int j = j0 + jb + (live ? jj : 0);
+            float q[4] = {quats[4 * j], quats[4 * j + 1], quats[4 * j + 2], quats[4 * j + 3]};
+            const float inv = rsqrtf(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
 #pragma unroll
-                for (int i = 0; i < 4; ++i)
-                    for (int r = 0; r < S.e[k][i]; ++r) p *= q[i] * inv;
-                v = p;
+            for (int i = 0; i < 4; ++i) q[i] *= inv;
+            const float w = weights ? weights[j] : inv_nrot;
+#pragma unroll
+            for (int a = 0; a < kFoldA; ++a) {
+                float p = 0.0f;
+                if (live && a < na) {
+                    p = w;
+#pragma unroll
+                    for (int i = 0; i < 4; ++i)
+#pragma unroll
+                        for (int r = 0; r < S.e[(A0 + a) % K][i]; ++r) p *= q[i];
+                }
+                coef[jj][a] = p;
             }
-            coef[jj][a] = v;
         }
         __syncthreads();
         if (u < s3) {
             const int jn = min(kFoldJ, nj - jb);
-            for (int jj = 0; jj < jn; ++jj) {
-                float r = __ldg(rot + (size_t)(jb + jj) * s3 + u);
+            // the block's kFoldJ samples of this voxel, all loads in flight at
+            // once (nodes past jn carry zero coefficients)
+            float rr[kFoldJ];
+#pragma unroll
+            for (int jj = 0; jj < kFoldJ; ++jj)
+                rr[jj] = jj < jn ? __ldg(rot + (size_t)(jb + jj) * s3 + u) : 0.f;
+#pragma unroll
+            for (int jj = 0; jj < kFoldJ; ++jj) {
+                const float r = rr[jj];
                 // one 16-byte broadcast read per four FMAs
                 const float4* c4 = reinterpret_cast<const float4*>(&coef[jj][0]);
 #pragma unroll
@@ -197,24 +216,34 @@ ttm_status launch_rotate_normalise(const float* t, const float* m, int s, const 
     return after_launch(cnt);
 }
 
+// one launch per kFoldA components: A0 = 0, kFoldA, ... below K
+template <int N, int A0 = 0>
+static ttm_status fold_passes(const float* quats, const float* weights, float inv, int j0, int nj,
+                              const float* rot, int s3, float* comp, bool first, dim3 grid,
+                              cudaStream_t st, long long* cnt) {
+    if constexpr (A0 < n_comp(N)) {
+        fold_kernel<N, A0><<<grid, kFoldThreads, 0, st>>>(quats, weights, inv, j0, nj, rot, s3, comp,
+                                                         first);
+        TTM_TRY(after_launch(cnt));
+        return fold_passes<N, A0 + kFoldA>(quats, weights, inv, j0, nj, rot, s3, comp, first, grid,
+                                          st, cnt);
+    } else {
+        return TTM_OK;
+    }
+}
+
 ttm_status launch_fold_components(int n_order, const float* quats, const float* weights,
                                   int n_rot_total, int j0, int nj, const float* rot, int s3,
                                   float* comp, bool first, cudaStream_t st, long long* cnt) {
-    const int K = n_comp(n_order);
     const float inv = 1.0f / (float)n_rot_total;
-    dim3 grid((s3 + kFoldThreads - 1) / kFoldThreads);
-    for (int a0 = 0; a0 < K; a0 += kFoldA) {
-        int na = K - a0 < kFoldA ? K - a0 : kFoldA;
-        switch (n_order) {
-            case 2: fold_kernel<2><<<grid, kFoldThreads, 0, st>>>(quats, weights, inv, j0, nj, rot, s3, comp, a0, na, first); break;
-            case 4: fold_kernel<4><<<grid, kFoldThreads, 0, st>>>(quats, weights, inv, j0, nj, rot, s3, comp, a0, na, first); break;
-            case 6: fold_kernel<6><<<grid, kFoldThreads, 0, st>>>(quats, weights, inv, j0, nj, rot, s3, comp, a0, na, first); break;
-            case 8: fold_kernel<8><<<grid, kFoldThreads, 0, st>>>(quats, weights, inv, j0, nj, rot, s3, comp, a0, na, first); break;
-            default: return TTM_ERR_UNSUPPORTED;
-        }
-        TTM_TRY(after_launch(cnt));
+    const dim3 grid((s3 + kFoldThreads - 1) / kFoldThreads);
+    switch (n_order) {
+        case 2: return fold_passes<2>(quats, weights, inv, j0, nj, rot, s3, comp, first, grid, st, cnt);
+        case 4: return fold_passes<4>(quats, weights, inv, j0, nj, rot, s3, comp, first, grid, st, cnt);
+        case 6: return fold_passes<6>(quats, weights, inv, j0, nj, rot, s3, comp, first, grid, st, cnt);
+        case 8: return fold_passes<8>(quats, weights, inv, j0, nj, rot, s3, comp, first, grid, st, cnt);
+        default: return TTM_ERR_UNSUPPORTED;
     }
-    return TTM_OK;
 }
 
 }  // namespace ttm

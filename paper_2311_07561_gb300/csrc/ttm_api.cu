@@ -1285,6 +1285,26 @@ ttm_status ttm_plan_launch_count(ttm_plan_t plan, long long* launches) {
     return TTM_OK;
 }
 
+ttm_status ttm_probe_bounded_wait(long long polls, int arrive, int* status_out, void* stream) {
+    if (polls < 1 || polls > (1LL << 24) || !status_out) return TTM_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    int* d = nullptr;
+    TTM_CUDA_TRY(cudaMalloc((void**)&d, sizeof(int)));
+    long long cnt = 0;
+    ttm_status s = launch_wait_probe((long)polls, arrive ? 1 : 0, d, st, &cnt);
+    int h = TTM_ERR_CUDA;
+    if (s == TTM_OK &&
+        (cudaMemcpyAsync(&h, d, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+         cudaStreamSynchronize(st) != cudaSuccess)) {
+        cudaGetLastError();
+        s = TTM_ERR_CUDA;
+    }
+    cudaFree(d);
+    if (s != TTM_OK) return s;
+    *status_out = h;
+    return TTM_OK;
+}
+
 ttm_status ttm_plan_waves(ttm_plan_t plan, int* n_waves, int* first) {
     if (!plan || !n_waves) return TTM_ERR_INVALID_ARG;
     *n_waves = (int)plan->waves.size();

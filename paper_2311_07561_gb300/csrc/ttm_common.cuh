@@ -37,6 +37,36 @@ void note_cuda_error(cudaError_t e, const char* what, const char* file, int line
 ttm_status after_launch(long long* counter);
 
 // --------------------------------------------------------------------------
+// bounded waits
+// --------------------------------------------------------------------------
+
+// Polls phase `phase` of the shared-memory mbarrier at `bar` at most `limit`
+// times (mbarrier.try_wait, which itself suspends for a while between
+// polls); false when the phase never completed.  Every device-side wait of
+// the tensor-core kernels goes through this loop, so none can hang: a wait
+// that runs out makes the kernel record TTM_ERR_TIMEOUT and return.
+// The kernels' limit: 2^18 polls, about one second at the ~3.7 us a poll
+// that does not complete takes on GB300 (measured by ttm_probe_bounded_wait),
+// far beyond any MMA or bulk-copy latency.
+constexpr long kMbarWaitPolls = 1L << 18;
+
+#ifdef __CUDACC__
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t phase, long limit) {
+    for (long it = 0; it < limit; ++it) {
+        uint32_t done;
+        asm volatile(
+            "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+            "selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(done)
+            : "r"(bar), "r"(phase)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+#endif
+
+// --------------------------------------------------------------------------
 // symmetric tensor tables
 // --------------------------------------------------------------------------
 

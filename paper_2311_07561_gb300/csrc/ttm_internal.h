@@ -244,6 +244,11 @@ ttm_status launch_direct_tc(const float* f, int X, int Y, int Z, const TemplateD
                             const double* d_moments, float* corr, int* status, cudaStream_t st,
                             long long* cnt);
 
+// one CTA waiting `polls` polls on an mbarrier phase (arrive = 1: the CTA
+// completes it first); *d_status = TTM_OK or TTM_ERR_TIMEOUT
+ttm_status launch_wait_probe(long polls, int arrive, int* d_status, cudaStream_t st,
+                             long long* cnt);
+
 // per-voxel score + candidate search (tensor cores for order 4 with the
 // default 2048-point grid, CUDA cores otherwise) and refinement, over the
 // interior box only; launch_exterior_fill writes the exterior values (score 0,

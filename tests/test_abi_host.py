@@ -103,6 +103,10 @@ def test_null_and_invalid_arguments_are_rejected_on_host(lib):
     # calls on a null plan
     n = ctypes.c_int()
     assert lib.ttm_plan_waves(None, ctypes.byref(n), None) == -1
+    # the bounded-wait probe: poll limit 1 .. 2^24, a status pointer
+    assert lib.ttm_probe_bounded_wait(0, 0, ctypes.byref(n), None) == -1
+    assert lib.ttm_probe_bounded_wait((1 << 24) + 1, 0, ctypes.byref(n), None) == -1
+    assert lib.ttm_probe_bounded_wait(100, 0, None, None) == -1
     assert lib.ttm_local_stats(None, None, None, None, 0, None) == -1
     assert lib.ttm_correlate(None, None, None, None, None, None, None, None, 0, None) == -1
     assert lib.ttm_extract_peaks(None, 0, None, None, None, 0.0, 1, 1, None, ctypes.byref(n),

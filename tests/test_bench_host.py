@@ -40,11 +40,20 @@ def test_score_rotation_stage_uses_the_planned_a5_count():
 
 
 def test_refinement_work_per_voxel_order_four():
-    # 8 candidates x 2 power steps (3 evaluations of C x^3 over 20 cubic
-    # monomials x 4 outputs, 2 normalisations) + the 4 best x 3 Newton steps
-    # (4 evaluations of C x^2: 10 entries x 10 quadratic monomials, 3 solves)
+    # 8 candidates x 2 power steps, ranked (3 evaluations of C x^3 over 20
+    # cubic monomials x 4 outputs, 2 normalisations) + the 4 best x 3 Newton
+    # steps (4 evaluations of C x^2: 10 entries x 10 quadratic monomials, 3
+    # solves)
     per_voxel = 8 * (3 * 10 * 20 + 24) + 4 * (4 * (2 * 10 * 10 + 2 * 10 + 40) + 3 * 150)
     assert per_voxel == 10952 == bench.refinement_flop_per_voxel(35, 8, 3, 4)
+
+
+def test_refinement_work_per_voxel_order_six():
+    # 2 candidates, both refined: no ranking evaluation (2 of C x^5 over 56
+    # monomials each), then 2 Newton steps (2 evaluations of C x^4 over 35
+    # monomials, 2 solves, the last trial one evaluation of C x^5)
+    per_voxel = 2 * (2 * 10 * 56 + 24) + 2 * (2 * (2 * 10 * 35 + 2 * 35 + 40) + 10 * 56 + 2 * 150)
+    assert per_voxel == bench.refinement_flop_per_voxel(84, 2, 2, 2) == 7248
 
 
 def test_order_six_search_pads_to_96():
