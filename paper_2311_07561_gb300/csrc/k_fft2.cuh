@@ -150,6 +150,12 @@ template <int L> constexpr bool two_level() { return TwoLevel<L>::L1 > 0 && n_st
 // resident CTAs per SM the register budget is sized for: two for lines whose
 // second factor is at most 16 (their register DFTs are small), else one
 template <int L2> constexpr int two_min_blocks() { return L2 <= 16 ? 2 : 1; }
+// the column pass also with bf16 samples up to L2 = 30: its register DFTs
+// and the prefetched bf16 pairs fit 128 registers (FP32 samples, twice the
+// prefetch registers, and 32-point DFTs spill)
+template <int L2, typename PS> constexpr int cols_min_blocks() {
+    return L2 <= 16 || (sizeof(PS) == 4 && L2 <= 30) ? 2 : 1;
+}
 
 constexpr int kTwoThreads = 256;
 
@@ -162,7 +168,7 @@ constexpr size_t two_cols_smem() { return (size_t)L2 * (L1 + 1) * (kTwoThreads /
 // CTAs, the raw samples of the next tile are loaded into registers while the
 // current one is transformed.  Line samples lo..hi are stored.
 template <int L1, int L2, int SIGN, typename PS>
-__global__ void __launch_bounds__(kTwoThreads, two_min_blocks<L2>()) cols2_t(PS* __restrict__ data, int B,
+__global__ void __launch_bounds__(kTwoThreads, cols_min_blocks<L2, PS>()) cols2_t(PS* __restrict__ data, int B,
                                                           const float2* __restrict__ tw,
                                                           ColsMap mp, int ntb, size_t ntiles) {
     constexpr int L = L1 * L2;
