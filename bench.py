@@ -93,9 +93,9 @@ def budget(K: int):
 
 
 def grid_points(K: int, mixed: bool) -> int:
-    """The plan's default rotation search grid: 1024 points at order 6 with
-    bf16 storage, else 2048."""
-    return 1024 if (K == 84 and mixed) else 2048
+    """The plan's default rotation search grid: 1024 points with bf16
+    storage, else 2048."""
+    return 1024 if mixed else 2048
 
 
 def refinement_text(K: int) -> str:

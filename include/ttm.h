@@ -111,7 +111,7 @@ typedef struct ttm_plan_opts {
     int path;           /* TTM_PATH_*                                          */
     int precision;      /* TTM_PREC_*                                          */
     int n_grid;         /* rotation search grid size; 0 = default (2048, or    */
-                        /* 1024 at order 6 with TTM_PREC_MIXED), <= 65535     */
+                        /* 1024 with TTM_PREC_MIXED), <= 65535                */
     int n_cells;        /* regions of the grid; 0 = default (n_grid / 16);    */
                         /* must divide n_grid                                  */
     int n_candidates;   /* regions polished per voxel; 0 = default (8, or 2 at */

@@ -91,11 +91,11 @@ ttm_status dev_upload(T** dst, const std::vector<T>& src) {
 
 ttm_status build_grid(ttm_plan_s* P) {
     RotGrid& g = P->grid;
-    // order 6 in mixed precision searches 1024 points (64 regions of 16): the
-    // FP64 model of the search and refinement on the order-6 workload's
-    // template gives a largest lambda shortfall of 6.2e-5 (4.2e-5 with 2048
-    // points), inside that mode's 5e-3 tolerance; every other case 2048
-    const int n_def = (P->n_order == 6 && P->opts.precision == TTM_PREC_MIXED) ? 1024 : 2048;
+    // mixed precision searches 1024 points (64 regions of 16): the FP64 model
+    // of the search and refinement gives a largest lambda shortfall of 6.2e-5
+    // at order 6 (4.2e-5 with 2048 points) and 8.4e-5 at order 4 (1.7e-5),
+    // inside that mode's 5e-3 tolerance; FP32 keeps 2048 for its 1e-4
+    const int n_def = P->opts.precision == TTM_PREC_MIXED ? 1024 : 2048;
     const int n = P->opts.n_grid > 0 ? P->opts.n_grid : n_def;
     const int nc = P->opts.n_cells > 0 ? P->opts.n_cells : n / 16;
     // refinement budget: at order 6 the maxima of phi are sharper and the
