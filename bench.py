@@ -113,19 +113,18 @@ NCU_TRAFFIC: dict = {
     # ncu (dram__bytes_read.sum + dram__bytes_write.sum) of one launch over the
     # whole interior: the 128^3 case (c2s), 912 673 interior voxels, FP32 maps;
     # the 256x256x192 case of the order-6 template (c5s), 4 805 121 interior
-    # voxels, bf16 maps.  Kernels reading their problems from the per-launch
-    # segment table.
-    "rotation_polish": [dict(bytes_per_voxel=(193203968 + 9818112) / 912673, K=35, storage="f32",
-                             source_sha="6a9d8ea49a0f",
+    # voxels, bf16 maps.
+    "rotation_polish": [dict(bytes_per_voxel=(193203200 + 9803008) / 912673, K=35, storage="f32",
+                             source_sha="912e1275591c",
                              sources=["k_rotation.cuh", "k_rotation.cu", "k_rotation_n4.cu"]),
-                        dict(bytes_per_voxel=(1194241280 + 89479168) / 4805121, K=84,
-                             storage="bf16", source_sha="7d71bab6119b",
+                        dict(bytes_per_voxel=(1193875456 + 90971136) / 4805121, K=84,
+                             storage="bf16", source_sha="e2173a68ccde",
                              sources=["k_rotation.cuh", "k_rotation.cu", "k_rotation_n6.cu"])],
-    "rotation_search": [dict(bytes_per_voxel=(173786368 + 12342784) / 912673, K=35, storage="f32",
-                             source_sha="6e5bd42d6680",
+    "rotation_search": [dict(bytes_per_voxel=(173863936 + 11920384) / 912673, K=35, storage="f32",
+                             source_sha="7ea2aa611a47",
                              sources=["k_search_tc.cu", "k_rotation.cuh"]),
-                        dict(bytes_per_voxel=(1094080768 + 93124096) / 4805121, K=84,
-                             storage="bf16", source_sha="6e5bd42d6680",
+                        dict(bytes_per_voxel=(1094127360 + 91662592) / 4805121, K=84,
+                             storage="bf16", source_sha="7ea2aa611a47",
                              sources=["k_search_tc.cu", "k_rotation.cuh"])],
 }
 
