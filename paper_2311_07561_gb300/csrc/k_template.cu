@@ -41,7 +41,10 @@ __global__ void __launch_bounds__(kRotThreads) mask_sum_kernel(const float* __re
     if (threadIdx.x == 0) *out = s;
 }
 
-// t_R(u) = t(c + R^-1 (u - c)), trilinear, zero outside the s^3 box.
+// t_R(u) = t(c + R^-1 (u - c)), trilinear, zero outside the s^3 box.  The
+// eight taps are read unconditionally from clamped indices, a tap outside
+// the box carrying weight zero (the same sum, term by term, as skipping it),
+// so that every load of a voxel can be in flight at once.
 __device__ __forceinline__ float sample_rotated(const float* __restrict__ t, int s, float c,
                                                 const float Rt[9], int ux, int uy, int uz) {
     float vx = ux - c, vy = uy - c, vz = uz - c;
@@ -52,26 +55,34 @@ __device__ __forceinline__ float sample_rotated(const float* __restrict__ t, int
     float fx0 = floorf(px), fy0 = floorf(py), fz0 = floorf(pz);
     int x0 = (int)fx0, y0 = (int)fy0, z0 = (int)fz0;
     float ax = px - fx0, ay = py - fy0, az = pz - fz0;
-    float acc = 0.0f;
+    float tap[8], wt[8];
 #pragma unroll
     for (int dz = 0; dz < 2; ++dz) {
-        int zz = z0 + dz;
-        if (zz < 0 || zz >= s) continue;
-        float wz = dz ? az : 1.0f - az;
+        const int zz = z0 + dz;
+        const bool iz = zz >= 0 && zz < s;
+        const int zc = min(max(zz, 0), s - 1);
+        const float wz = dz ? az : 1.0f - az;
 #pragma unroll
         for (int dy = 0; dy < 2; ++dy) {
-            int yy = y0 + dy;
-            if (yy < 0 || yy >= s) continue;
-            float wy = dy ? ay : 1.0f - ay;
+            const int yy = y0 + dy;
+            const bool iy = yy >= 0 && yy < s;
+            const int yc = min(max(yy, 0), s - 1);
+            const float wy = dy ? ay : 1.0f - ay;
 #pragma unroll
             for (int dx = 0; dx < 2; ++dx) {
-                int xx = x0 + dx;
-                if (xx < 0 || xx >= s) continue;
-                float wx = dx ? ax : 1.0f - ax;
-                acc += wz * wy * wx * __ldg(t + ((size_t)zz * s + yy) * s + xx);
+                const int xx = x0 + dx;
+                const bool ix = xx >= 0 && xx < s;
+                const int xc = min(max(xx, 0), s - 1);
+                const float wx = dx ? ax : 1.0f - ax;
+                const int k = (dz * 2 + dy) * 2 + dx;
+                tap[k] = __ldg(t + ((size_t)zc * s + yc) * s + xc);
+                wt[k] = (iz && iy && ix) ? wz * wy * wx : 0.0f;
             }
         }
     }
+    float acc = 0.0f;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) acc += wt[k] * tap[k];
     return acc;
 }
 
@@ -102,6 +113,7 @@ __global__ void __launch_bounds__(kRotThreads) rotate_normalise_kernel(
     const float c = (float)(s / 2);
     float* o = out + (size_t)blockIdx.x * s3;
     double t1 = 0.0, t2 = 0.0;
+#pragma unroll 4
     for (int u = threadIdx.x; u < s3; u += blockDim.x) {
         int ux = u % s, uy = (u / s) % s, uz = u / (s * s);
         float v = sample_rotated(t, s, c, R, ux, uy, uz);

@@ -1051,9 +1051,13 @@ int ttm_device_count(void) {
     return n;
 }
 
+// quadrature nodes rotated per chunk: 128 MiB of rotated copies, at least
+// two per SM (one CTA rotates one node), at most 1 GiB
 static int build_chunk(int s, int n_rot) {
     const size_t s3 = (size_t)s * s * s;
     size_t nj = ((size_t)128 << 20) / (s3 * sizeof(float));
+    nj = std::max<size_t>(nj, 304);
+    nj = std::min<size_t>(nj, ((size_t)1 << 30) / (s3 * sizeof(float)));
     if (nj < 1) nj = 1;
     if (nj > (size_t)n_rot) nj = (size_t)n_rot;
     return (int)nj;
