@@ -786,10 +786,7 @@ def run_ours(args) -> None:
             return [(torch.empty((Z, Y, X), dtype=torch.float32).pin_memory(),
                      torch.empty((Z, Y, X, 4), dtype=torch.float32).pin_memory(),
                      torch.empty((Z, Y, X), dtype=torch.float32).pin_memory())]
-        matcher.close()
-        del matcher
-        torch.cuda.empty_cache()
-        hs = ttm.HostStream([(comp, desc, wl.mask)], [((X, Y, Z), 0)], opts=opts, depth=depth)
+        hs = ttm.HostStream(matcher=matcher, depth=depth)
         outs = [pinned_maps() for _ in range(depth)]
         for k in range(max(args.warmup, depth)):
             hs.submit([pin_in], outs[k % depth])
@@ -1136,40 +1133,52 @@ def run_batch(args) -> None:
     kern = {name: dict(ms=ms, launches=n) for name, (ms, n) in ttm.ttm_plan_timing(matcher.plan).items()}
     ttm.ttm_plan_enable_timing(matcher.plan, False)
 
+    # end to end: every step copies the 16 pinned host volumes in and the
+    # score, quaternion and lambda maps of all 64 problems out, through
+    # HostStream on the same plan (one device copy per volume, so its
+    # problems still share its spectra; volumes and maps double-buffered)
     e2e = None
     if not args.no_e2e:
+        depth = args.e2e_depth if args.e2e_depth > 0 else 2
+        n_t = len(bw.templates)
         pin_in = [torch.from_numpy(v).pin_memory() for v in bw.volumes]
-        pin_out = [(torch.empty(tuple(d[::-1]), dtype=torch.float32).pin_memory(),
-                    torch.empty(tuple(d[::-1]) + (4,), dtype=torch.float32).pin_memory(),
-                    torch.empty(tuple(d[::-1]), dtype=torch.float32).pin_memory())
-                   for d, _ in problems]
+
+        def pinned_maps():
+            return [(torch.empty(tuple(d[::-1]), dtype=torch.float32).pin_memory(),
+                     torch.empty(tuple(d[::-1]) + (4,), dtype=torch.float32).pin_memory(),
+                     torch.empty(tuple(d[::-1]), dtype=torch.float32).pin_memory())
+                    for d, _ in problems]
+        outs = [pinned_maps() for _ in range(depth)]
         h2d = sum(v.nbytes for v in bw.volumes)
         d2h = sum(int(np.prod(d)) * 24 for d, _ in problems)
-
-        def e2e_step():
-            for dv, hv in zip(dvols, pin_in):
-                dv.copy_(hv, non_blocking=True)
-            graph.replay()
-            for p, (so, qo, lo) in enumerate(pin_out):
-                so.copy_(matcher.score[p], non_blocking=True)
-                qo.copy_(matcher.quat[p], non_blocking=True)
-                lo.copy_(matcher.lam[p], non_blocking=True)
-        e2e_step()
+        hs = ttm.HostStream(matcher=matcher, depth=depth,
+                            volume_of=[p // n_t for p in range(len(problems))])
+        for k in range(max(args.warmup, depth)):
+            hs.submit(pin_in, outs[k % depth])
+        hs.join()
         torch.cuda.synchronize()
         if dist:
             dist.barrier()
-        e_ms = 0.0
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
         for k in range(args.steps):
-            flush.zero_()
-            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            a.record(stream)
-            e2e_step()
-            b.record(stream)
-            b.synchronize()
-            e_ms += a.elapsed_time(b)
-        e_ms = max_over_ranks(e_ms, dist, dev)
+            hs.submit(pin_in, outs[k % depth])
+        hs.join()
+        b.record(stream)
+        b.synchronize()
+        e_ms = max_over_ranks(a.elapsed_time(b), dist, dev)
+        st_ = ttm.ttm_plan_device_status(matcher.plan, matcher.ws)
+        if st_ != 0:
+            raise RuntimeError(f"device status {ttm.ttm_status_string(st_)}")
+        hs.outs, hs.vols = None, None
+        del outs
+        torch.cuda.empty_cache()
         e2e = dict(value=job_rate(nvox_total, args.steps, world, e_ms), unit=UNIT,
-                   h2d_bytes_per_step=h2d, d2h_bytes_per_step=d2h)
+                   h2d_bytes_per_step=h2d, d2h_bytes_per_step=d2h, pipeline_depth=depth,
+                   note="pinned host volumes in, score + quaternion + lambda maps of every "
+                        "problem out, every step; one plan, volumes and maps double-buffered "
+                        "(HostStream, one device copy per volume)")
 
     if rank != 0:
         if dist:

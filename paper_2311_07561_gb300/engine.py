@@ -213,10 +213,11 @@ class HostPipeline:
         self._next = 0
 
     def submit(self, host_vols: Sequence, host_out: Sequence) -> None:
-        """Queue one step: host_vols[p] (pinned float32 (Z, Y, X)) in, and
-        (score, quat, lambda) of every problem out into host_out[p] (pinned
-        tensors of the map shapes).  Returns at once; the step is ordered after
-        everything queued on the current stream before the call."""
+        """Queue one step: host_vols[v] (pinned float32 (Z, Y, X), one per
+        volume index) in, and (score, quat, lambda) of every problem out into
+        host_out[p] (pinned tensors of the map shapes).  Returns at once; the
+        step is ordered after everything queued on the current stream before
+        the call."""
         torch = _torch()
         i = self._next % len(self.matchers)
         self._next += 1
@@ -256,19 +257,40 @@ class HostStream:
     pinned host memory and its score, rotation and lambda maps out.  Memory
     beyond one Matcher: ``depth - 1`` more volumes and output sets.
 
-    templates, problems, opts: as for :class:`Matcher`.
+    templates, problems, opts: as for :class:`Matcher`; or matcher: an
+    existing Matcher to drive (its plan, workspace and maps are then shared
+    with its other users).  volume_of: optional problem -> volume index; the
+    problems of one volume then read one device copy of it (a batch of
+    volumes x templates: one copy in per volume, and the plan shares the
+    volume's spectra between its problems), and submit takes one host volume
+    per index.
     """
 
-    def __init__(self, templates, problems, opts=None, depth: int = 2):
+    def __init__(self, templates=None, problems=None, opts=None, depth: int = 2, matcher=None,
+                 volume_of: Optional[Sequence[int]] = None):
         torch = _torch()
         if depth < 1:
             raise ValueError("depth must be at least 1")
-        self.matcher = Matcher(templates, problems, opts=opts)
+        self.matcher = matcher if matcher is not None else Matcher(templates, problems, opts=opts)
+        self._own = matcher is None
         dev = torch.device("cuda")
         m = self.matcher
+        n_prob = len(m.problems)
+        self.volume_of = list(range(n_prob)) if volume_of is None else [int(v) for v in volume_of]
+        if len(self.volume_of) != n_prob:
+            raise ValueError("volume_of needs one volume index per problem")
+        shapes = {}
+        for p, v in enumerate(self.volume_of):
+            (X, Y, Z), _ = m.problems[p]
+            if shapes.setdefault(v, (Z, Y, X)) != (Z, Y, X):
+                raise ValueError(f"problems of volume {v} differ in size")
+        self.n_vol = max(self.volume_of) + 1
+        if sorted(shapes) != list(range(self.n_vol)):
+            raise ValueError("volume indices must be 0 .. n-1")
         self.outs = [(m.w, m.score, m.quat, m.lam)] + [m.new_outputs() for _ in range(depth - 1)]
-        self.vols = [[torch.empty((Z, Y, X), dtype=torch.float32, device=dev)
-                      for (X, Y, Z), _ in m.problems] for _ in range(depth)]
+        # per slot: one device copy per volume
+        self.vols = [[torch.empty(shapes[v], dtype=torch.float32, device=dev)
+                      for v in range(self.n_vol)] for _ in range(depth)]
         self.compute = torch.cuda.Stream()
         self.h2d = torch.cuda.Stream()
         self.d2h = torch.cuda.Stream()
@@ -301,7 +323,8 @@ class HostStream:
             self.compute.wait_event(self.ev_in[i])
             if self.used[i]:
                 self.compute.wait_event(self.ev_out[i])   # the slot's maps are on the host
-            self.matcher.run(self.vols[i], stream=self.compute, outputs=self.outs[i])
+            self.matcher.run([self.vols[i][v] for v in self.volume_of], stream=self.compute,
+                             outputs=self.outs[i])
             self.ev_done[i].record(self.compute)
         with torch.cuda.stream(self.d2h):
             self.d2h.wait_event(self.ev_done[i])
@@ -322,5 +345,6 @@ class HostStream:
             cur.wait_stream(st)
 
     def close(self) -> None:
-        self.matcher.close()
+        if self._own:
+            self.matcher.close()
 

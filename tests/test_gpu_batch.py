@@ -235,3 +235,33 @@ def test_shared_volume_spectra_change_nothing(ttm, many):
     for p, (a, b) in enumerate(zip(shared, separate)):
         assert torch_equal(a, b), p
     m.close()
+
+
+def test_host_stream_with_shared_volume_copies(ttm, many):
+    """End to end on a batch: HostStream driving an existing plan with one
+    device copy per volume (its problems share the volume's spectra) gives
+    the maps of Matcher.run, bit for bit, on two consecutive steps."""
+    import torch
+    tm, pb, vols = many["tmpls"], many["problems"], many["vols"]
+    m = ttm.Matcher(tm, pb)
+    ref = _maps(ttm, m, vols)
+    n_t = 3
+    host_vols = [vols[p].cpu().pin_memory() for p in range(0, len(pb), n_t)]
+    outs = [[(torch.empty_like(m.score[p], device="cpu").pin_memory(),
+              torch.empty_like(m.quat[p], device="cpu").pin_memory(),
+              torch.empty_like(m.lam[p], device="cpu").pin_memory()) for p in range(len(pb))]
+            for _ in range(2)]
+    hs = ttm.HostStream(matcher=m, depth=2, volume_of=[p // n_t for p in range(len(pb))])
+    for k in range(2):
+        hs.submit(host_vols, outs[k])
+    hs.join()
+    torch.cuda.synchronize()
+    assert ttm.ttm_plan_device_status(m.plan, m.ws) == 0
+    n = len(pb)
+    for k in range(2):
+        for p, (so, qo, lo) in enumerate(outs[k]):
+            assert torch.equal(so, ref[n + p].cpu()), (k, p)
+            assert torch.equal(qo, ref[2 * n + p].cpu()), (k, p)
+            assert torch.equal(lo, ref[3 * n + p].cpu()), (k, p)
+    hs.close()
+    m.close()
