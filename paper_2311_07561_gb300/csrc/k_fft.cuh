@@ -839,7 +839,7 @@ cudaError_t run_cols_mul(const float2* spec, const TS* tspec, PS* prod, int Bz, 
     if constexpr (two_level<L>()) {
         constexpr int L1 = MulSplit<L>::L1, L2 = MulSplit<L>::L2;
         constexpr int TB = kTwoThreads / L1;
-        constexpr size_t smem = two_cols_smem<L1, L2>();
+        constexpr size_t smem = mul2_smem<L1, L2, TS>();
         auto kern = cols_mul2_t<L1, L2, TS, PS>;
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)smem);

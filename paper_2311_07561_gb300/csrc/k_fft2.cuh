@@ -230,10 +230,34 @@ __global__ void __launch_bounds__(kTwoThreads, cols_min_blocks<L2, PS>()) cols2_
 
 // ---- z lines of F(f) conj(T_k) for all K components, inverse ----------------
 // One tile of TB columns per CTA: the image samples of this thread stay in
-// registers, the next component's samples are loaded while the current
+// registers, the next component's samples are fetched while the current
 // product is transformed; z samples lo..hi of every product are stored.
+// With FP32 template spectra the fetch goes to registers; with bf16 ones it
+// is a cp.async copy into a staging buffer (each thread its own slots), which
+// frees those registers for a second CTA per SM.
+
+// 4-byte asynchronous copy global -> shared, its commit and wait
+__device__ __forceinline__ void cp_async4(uint32_t dst, const void* src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(dst), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+}
+
+// CTAs per SM the fused multiply's registers are sized for, and its shared
+// memory: the exchange buffer, plus the staging buffer for bf16 samples
+template <typename TS> constexpr int mul_min_blocks(int l2) {
+    return sizeof(TS) == 4 ? 2 : (l2 <= 16 ? 2 : 1);
+}
+template <int L1, int L2, typename TS> constexpr size_t mul2_smem() {
+    return two_cols_smem<L1, L2>() + (sizeof(TS) == 4 ? (size_t)L2 * kTwoThreads * 4 : 0);
+}
+
 template <int L1, int L2, typename TS, typename PS>
-__global__ void __launch_bounds__(kTwoThreads, two_min_blocks<L2>()) cols_mul2_t(const float2* __restrict__ spec,
+__global__ void __launch_bounds__(kTwoThreads, mul_min_blocks<TS>(L2)) cols_mul2_t(const float2* __restrict__ spec,
                                                               const TS* __restrict__ tspec,
                                                               PS* __restrict__ out, int B, int K,
                                                               const float2* __restrict__ tw,
@@ -241,28 +265,48 @@ __global__ void __launch_bounds__(kTwoThreads, two_min_blocks<L2>()) cols_mul2_t
     constexpr int L = L1 * L2;
     constexpr int TB = kTwoThreads / L1;
     constexpr int ZP = L1 + 1;
+    constexpr bool kAsync = sizeof(TS) == 4;
     extern __shared__ float2 zx[];
+    TS* stg = reinterpret_cast<TS*>(zx + L2 * ZP * TB);      // [n2][thread] (async form)
     const int t = threadIdx.x;
     const int n1 = t / TB, ca = t % TB;
     const int b0 = blockIdx.x * TB;
     const size_t plane = (size_t)L * B;
     const bool in_a = b0 + ca < B;
+    const size_t e0 = (size_t)n1 * B + b0 + ca;
     float2 fi[L2];
-    TS tr[L2];
+    TS tr[kAsync ? 1 : L2];
+    auto stage = [&](int k) {
+        if (!in_a) return;
+        const TS* ts = tspec + (size_t)k * plane + e0;
+#pragma unroll
+        for (int n2 = 0; n2 < L2; ++n2)
+            cp_async4((uint32_t)__cvta_generic_to_shared(stg + n2 * kTwoThreads + t), ts + (size_t)n2 * L1 * B);
+        cp_async_commit();
+    };
 #pragma unroll
     for (int n2 = 0; n2 < L2; ++n2) {
-        const size_t e = (size_t)(n1 + L1 * n2) * B + b0 + ca;
+        const size_t e = e0 + (size_t)n2 * L1 * B;
         fi[n2] = in_a ? spec[e] : make_float2(0.f, 0.f);
-        if (in_a && K > 0) tr[n2] = tspec[e];
+        if constexpr (!kAsync) { if (in_a && K > 0) tr[n2] = tspec[e]; }
     }
+    if constexpr (kAsync) { if (K > 0) stage(0); }
     for (int k = 0; k < K; ++k) {
         float2 v[L2];
+        if constexpr (kAsync) {
+            cp_async_wait_all();
 #pragma unroll
-        for (int n2 = 0; n2 < L2; ++n2) v[n2] = in_a ? cmulc(fi[n2], ldc(&tr[n2])) : make_float2(0.f, 0.f);
-        if (in_a && k + 1 < K) {
-            const TS* ts = tspec + (size_t)(k + 1) * plane;
+            for (int n2 = 0; n2 < L2; ++n2)
+                v[n2] = in_a ? cmulc(fi[n2], ldc(stg + n2 * kTwoThreads + t)) : make_float2(0.f, 0.f);
+            if (k + 1 < K) stage(k + 1);
+        } else {
 #pragma unroll
-            for (int n2 = 0; n2 < L2; ++n2) tr[n2] = ts[(size_t)(n1 + L1 * n2) * B + b0 + ca];
+            for (int n2 = 0; n2 < L2; ++n2) v[n2] = in_a ? cmulc(fi[n2], ldc(&tr[n2])) : make_float2(0.f, 0.f);
+            if (in_a && k + 1 < K) {
+                const TS* ts = tspec + (size_t)(k + 1) * plane;
+#pragma unroll
+                for (int n2 = 0; n2 < L2; ++n2) tr[n2] = ts[(size_t)(n1 + L1 * n2) * B + b0 + ca];
+            }
         }
         dft_reg<L2, +1>(v);
 #pragma unroll
@@ -292,6 +336,7 @@ __global__ void __launch_bounds__(kTwoThreads, two_min_blocks<L2>()) cols_mul2_t
             }
         }
     }
+    if constexpr (kAsync) cp_async_wait_all();
 }
 
 // ---- half-spectrum rows -> real x lines, two-level ------------------------
