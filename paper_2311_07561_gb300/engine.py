@@ -268,12 +268,10 @@ class HostStream:
 
     def __init__(self, templates=None, problems=None, opts=None, depth: int = 2, matcher=None,
                  volume_of: Optional[Sequence[int]] = None):
-        torch = _torch()
         if depth < 1:
             raise ValueError("depth must be at least 1")
         self.matcher = matcher if matcher is not None else Matcher(templates, problems, opts=opts)
         self._own = matcher is None
-        dev = torch.device("cuda")
         m = self.matcher
         n_prob = len(m.problems)
         self.volume_of = list(range(n_prob)) if volume_of is None else [int(v) for v in volume_of]
@@ -287,6 +285,8 @@ class HostStream:
         self.n_vol = max(self.volume_of) + 1
         if sorted(shapes) != list(range(self.n_vol)):
             raise ValueError("volume indices must be 0 .. n-1")
+        torch = _torch()
+        dev = torch.device("cuda")
         self.outs = [(m.w, m.score, m.quat, m.lam)] + [m.new_outputs() for _ in range(depth - 1)]
         # per slot: one device copy per volume
         self.vols = [[torch.empty(shapes[v], dtype=torch.float32, device=dev)
