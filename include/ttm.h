@@ -269,7 +269,8 @@ ttm_status ttm_plan_problem_tensor_direct(ttm_plan_t plan, int problem, int* on)
  * path.  Host-only; TTM_ERR_INVALID_ARG for a bad plan, problem or pointer. */
 ttm_status ttm_plan_problem_fft_box(ttm_plan_t plan, int problem, int* box);
 
-/* Self-check of the bounded device-side waits.  Launches one CTA that waits,
+/* Self-check of the bounded device-side waits (no counterpart in the paper:
+ * engine infrastructure).  Launches one CTA that waits,
  * with the poll loop every tensor-core kernel waits with, on an mbarrier
  * phase: with arrive = 1 the CTA completes that phase itself first; with
  * arrive = 0 nothing does, so the wait must run out after `polls` polls
@@ -282,7 +283,8 @@ ttm_status ttm_probe_bounded_wait(long long polls, int arrive, int* status_out, 
 /* Kernel launches the plan has queued so far (for accounting). */
 ttm_status ttm_plan_launch_count(ttm_plan_t plan, long long* launches);
 
-/* Resident waves of the plan (option batch_mib): *n_waves = their number (0
+/* Resident waves of the plan (option batch_mib; batching has no counterpart
+ * in the paper, which matches one volume at a time): *n_waves = their number (0
  * when problems run one at a time); with first != NULL, first[0..n_waves-1]
  * receives the first problem of each wave (the caller sizes it from a call
  * with first = NULL).  Host-only; TTM_ERR_INVALID_ARG for a bad plan or
