@@ -143,3 +143,18 @@ def test_sweep_angle():
         assert bench._angle_deg(p, pq) == pytest.approx(deg, abs=1e-6)
     st = bench._err_stats(np.array([0.5, 2.0, 6.0, 10.0]))
     assert st["within_1deg"] == 0.25 and st["within_5deg"] == 0.5 and st["max_deg"] == 10.0
+
+
+def test_score_rotation_stage_takes_its_wall_time_span():
+    """With the rotation_stage span recorded, the stage's time is the span
+    (the two classes overlap on two streams, so their sum overstates it), and
+    the span is left out of the per-class shares."""
+    kern = dict(rotation_search=dict(ms=3.0, launches=8), rotation_polish=dict(ms=2.0, launches=8),
+                rotation_stage=dict(ms=4.0, launches=16), fft_inverse=dict(ms=2.5, launches=2))
+    rf = bench.roofline(kern, 1, _geo(K=84, n_int=10 ** 6), PEAKS)
+    assert rf["kernel"] == "score_rotation" and rf["ms_per_step"] == pytest.approx(4.0)
+    assert rf["achieved"] == pytest.approx(33600 * 1e6 / 4e-3 / 1e12, rel=1e-3)
+    assert bench.kernel_ms(kern) == pytest.approx(7.5)
+    # the inverse passes win when the span is short enough
+    kern["rotation_stage"]["ms"] = 2.0
+    assert bench.roofline(kern, 1, _geo(K=84, n_int=10 ** 6), PEAKS)["kernel"] == "fft_inverse"
